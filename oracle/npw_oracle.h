@@ -1,0 +1,67 @@
+/*
+ * npw_oracle.h -- interface of the FP64 CPU oracle (test infrastructure only; see
+ * npw_oracle.c).  Private to oracle/: the CUDA library neither includes nor links it.
+ *
+ * Layouts: 1D fields are [m][n] (field-major); face arrays are [m][n+1] with face f
+ * between cell f-1 and cell f; 2D fields are [m][ny][nx].
+ */
+#ifndef NPW_ORACLE_H
+#define NPW_ORACLE_H
+#include <stdint.h>
+
+enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ENONFINITE = -5 };
+enum { ORC_ENO = 0, ORC_WENO_JS = 1, ORC_RBF_ENO = 2, ORC_RBF_WENO = 3 };
+enum { ORC_RBF_MQ = 0, ORC_RBF_GA = 1 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_TRANSMISSIVE = 1, ORC_BC_INFLOW = 2 };
+enum { ORC_FLUX_ADVECTION = 0, ORC_FLUX_BURGERS = 1, ORC_FLUX_EULER1D = 2, ORC_FLUX_EULER2D = 3 };
+
+/* per-face flag byte */
+#define ORC_FLAG_SWITCH 0x01     /* monotone switch fired: eta forced to 0 */
+#define ORC_FLAG_SWITCH_TIE 0x02 /* a switch quantity lies within tie_tol of its threshold */
+/* bits 2-3: ENO stencil r of the left cell (for v^-); bits 4-5: of the right cell (v^+) */
+#define ORC_FLAG_ENO_TIE_L 0x40
+#define ORC_FLAG_ENO_TIE_R 0x80
+
+typedef struct {
+    int scheme;          /* ORC_ENO .. ORC_RBF_WENO */
+    int rbf;             /* ORC_RBF_MQ / ORC_RBF_GA */
+    int monotone_switch; /* 0/1 */
+    int switch_variant;  /* 0: cubic on the 4-cell eta stencil; 1: k=2 ratio test on both 3-cell halves */
+    int characteristic;  /* 1D Euler: reconstruct characteristic fields */
+    int pad_;
+    double eps_M;     /* additive guard of the eta denominator */
+    double eps_weno;  /* WENO epsilon (1e-6) */
+    double gamma;     /* ratio of specific heats */
+    double adv_speed; /* advection speed, x */
+    double adv_speed_y;
+    double inflow[4]; /* ghost state for the inflow boundary */
+    double tie_tol;   /* relative margin that marks a decision as a near tie */
+} orc_params;
+
+typedef struct {
+    long steps;
+    double t;
+    double alpha_max;
+    int status;
+    int pad_;
+} orc_solve_stats;
+
+double orc_table_coef(int rbf, int r, int j, double eta);
+int orc_switch_k3(const double w[4], int variant, double tol, int* near_tie);
+int orc_eno_choice(const double c[5], double tol, int* near_tie);
+void orc_beta_k3(const double c[5], double beta[3]);
+int orc_euler_eigvec(const double UL[3], const double UR[3], double gamma, double R[3][3], double L[3][3]);
+int orc_reconstruct(const double* u, long n, int m, int bc, const orc_params* p, double* vm, double* vp,
+                    uint8_t* flags, double* eta, const uint8_t* replay);
+int orc_flux(const double* vm, const double* vp, long nf, int m, int kind, int dir, double alpha,
+             const orc_params* p, double* h);
+double orc_max_speed(const double* u, long ncell, int m, int kind, int dir, const orc_params* p);
+int orc_rk3_step(double* u, long n, int m, double dx, double dt, int kind, int bc, const orc_params* p,
+                 double* alpha_out);
+int orc_rk3_step_2d(double* u, long nx, long ny, int m, double dx, double dy, double dt, int kind, int bc,
+                    const orc_params* p);
+int orc_solve(double* u, long n, int m, double dx, double t_end, double cfl, int kind, int bc, const orc_params* p,
+              long max_steps, orc_solve_stats* out);
+int orc_solve_2d(double* u, long nx, long ny, int m, double dx, double dy, double t_end, double cfl, int kind,
+                 int bc, const orc_params* p, long max_steps, orc_solve_stats* out);
+#endif

@@ -1,0 +1,192 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test targets a part of the oracle so that a plausible mistake (a dropped term, a wrong
+sign, a transposed row, a wrong weight) fails at least one of them:
+  * P1  eta -> 0 limit: ENO/WENO-JS equal the exact-rational reconstruction built from the
+        definition (polynomial interpolation of the primitive), Sec. 2 / Table k3 (left);
+  * P2  exactness on cell averages of quadratics for every scheme (eta = 0 there, Table k3);
+  * P3  Taylor order of every perturbed row with the table's eta: 4 (poly rows: 3);
+  * P4  the perturbation rows are the flat limit of the MQ / Gaussian RBF interpolant;
+  * P6  the monotone switch on hand cases of eq. root_value and against exact root location;
+  * P11 whole-grid brute force (fractions) for every scheme, with and without the switch;
+  * the WENO pieces (d_r, beta_r) against their definitions.
+"""
+import numpy as np
+import pytest
+from fractions import Fraction as F
+
+import oracle as O
+from tests import bruteforce as B
+
+
+def _smooth_avgs(edges):
+    # averages of f(x) = sin(x + 0.3) + 2 (exact antiderivative)
+    a, b = edges[:-1], edges[1:]
+    return (-np.cos(b + 0.3) + np.cos(a + 0.3)) / (b - a) + 2.0
+
+
+# --------------------------------------------------------------------------------------- P1
+def test_linear_weights_match_definition():
+    assert B.linear_weights(0) == [F(3, 10), F(3, 5), F(1, 10)]
+    assert B.linear_weights(1) == [F(1, 10), F(3, 5), F(3, 10)]
+
+
+@pytest.mark.parametrize("r", [-1, 0, 1, 2])
+def test_poly_rows_are_primitive_interpolation(r):
+    # Table k3 (left) with 11/6 in row r = -1: the eta = 0 coefficient of the oracle equals the
+    # derivative of the interpolant of the primitive (right face of cell 0, stencil with r
+    # cells to the left; row -1 = left face of the r = 0 stencil shifted by one cell).
+    if r >= 0:
+        exact = B.poly_row(r, 0)
+    else:
+        exact = B.poly_row(0, 1)
+    for j in range(3):
+        assert O.table_coef(O.MQ, r, j, 0.0) == pytest.approx(float(exact[j]), abs=1e-15)
+        assert O.table_coef(O.GA, r, j, 0.0) == pytest.approx(float(exact[j]), abs=1e-15)
+
+
+def test_beta_matches_integral_definition():
+    g = np.random.default_rng(5)
+    for _ in range(20):
+        c = [F(int(x), 97) for x in g.integers(-300, 300, size=5)]
+        v = {k - 2: c[k] for k in range(5)}
+        got = O.beta_k3([float(x) for x in c])
+        for r in range(3):
+            assert got[r] == pytest.approx(float(B.beta(v, 0, r)), rel=1e-13, abs=1e-15)
+
+
+def test_eno_choice_matches_divided_differences():
+    g = np.random.default_rng(6)
+    for _ in range(300):
+        c = [F(int(x), 13) for x in g.integers(-40, 40, size=5)]
+        v = {k - 2: c[k] for k in range(5)}
+        r, _near = O.eno_choice([float(x) for x in c], tol=0.0)
+        assert r == B.eno_r(v, 0)
+
+
+# --------------------------------------------------------------------------------------- P2
+@pytest.mark.parametrize("scheme", [O.ENO, O.WENO_JS, O.RBF_ENO, O.RBF_WENO])
+@pytest.mark.parametrize("rbf", [O.MQ, O.GA])
+@pytest.mark.parametrize("switch", [0, 1])
+def test_quadratics_reconstructed_exactly(scheme, rbf, switch):
+    g = np.random.default_rng(7)
+    n = 24
+    edges = np.linspace(0.0, 3.0, n + 1)
+    for _ in range(4):
+        c0, c1, c2 = g.normal(size=3)
+        P = lambda x: c0 * x + c1 * x ** 2 / 2 + c2 * x ** 3 / 3  # antiderivative
+        avg = (P(edges[1:]) - P(edges[:-1])) / np.diff(edges)
+        vm, vp, fl, eta = O.reconstruct(avg, O.TRANSMISSIVE, O.Params(scheme=scheme, rbf=rbf, monotone_switch=switch))
+        exact = c0 + c1 * edges + c2 * edges ** 2
+        # faces whose stencil stays inside the domain (the transmissive ghosts are not quadratic)
+        inner = slice(3, n - 2)
+        np.testing.assert_allclose(vm[inner], exact[inner], rtol=0, atol=1e-12 * (1 + np.abs(exact).max()))
+        np.testing.assert_allclose(vp[inner], exact[inner], rtol=0, atol=1e-12 * (1 + np.abs(exact).max()))
+        assert np.all(np.abs(eta[inner]) < 1e-9)
+
+
+# --------------------------------------------------------------------------------------- P3
+@pytest.mark.parametrize("rbf", [O.MQ, O.GA])
+@pytest.mark.parametrize("r", [0, 1, 2])
+def test_perturbed_rows_are_fourth_order(rbf, r):
+    """RBF-ENO with the stencil forced to r (replay flags): v^- and v^+ converge at order 4
+    with the table's eta; ENO (eta = 0) at order 3.  A wrong coefficient, a wrong row for v^+
+    or a wrong eta formula drops the order to 3."""
+    def errs(scheme):
+        out_m, out_p = [], []
+        for n in (40, 80, 160):
+            edges = np.linspace(0.0, 2.0, n + 1)
+            avg = _smooth_avgs(edges)
+            replay = np.full(n + 1, (r << 2) | (r << 4), dtype=np.uint8)
+            vm, vp, _, _ = O.reconstruct(avg, O.TRANSMISSIVE, O.Params(scheme=scheme, rbf=rbf, monotone_switch=0),
+                                         replay=replay)
+            ex = np.sin(edges + 0.3) + 2.0
+            inner = slice(4, n - 3)
+            out_m.append(np.abs(vm[inner] - ex[inner]).max())
+            out_p.append(np.abs(vp[inner] - ex[inner]).max())
+        return np.array(out_m), np.array(out_p)
+
+    em, ep = errs(O.RBF_ENO)
+    for e in (em, ep):
+        orders = np.log2(e[:-1] / e[1:])
+        assert np.all(orders > 3.8), orders
+    pm, pp = errs(O.ENO)
+    for e in (pm, pp):
+        orders = np.log2(e[:-1] / e[1:])
+        assert np.all(np.abs(orders - 3.0) < 0.2), orders
+
+
+# --------------------------------------------------------------------------------------- P4
+@pytest.mark.parametrize("kind,rbf", [("mq", O.MQ), ("ga", O.GA)])
+def test_perturbation_rows_are_rbf_flat_limit(kind, rbf):
+    pytest.importorskip("mpmath")
+    rows = B.rbf_rows(kind)
+    for r in (-1, 0, 1, 2):
+        for j in range(3):
+            q = O.table_coef(rbf, r, j, 1.0) - O.table_coef(rbf, r, j, 0.0)
+            assert q == pytest.approx(float(rows[r][j]), abs=1e-12), (kind, r, j)
+
+
+# --------------------------------------------------------------------------------------- P6
+def test_switch_k2_hand_cases():
+    # eq. root_value on three cells (variant 1 tests both 3-cell halves of the 4-cell stencil)
+    assert O.switch_k3([0, 1, 0, -1], variant=1)[0]  # (0,1,0): extremum inside
+    assert not O.switch_k3([0, 1, 2, 3], variant=1)[0]  # linear: zero denominator, monotone
+    assert O.switch_k3([0, 0, 1, 2], variant=1)[0]  # (0,0,1): ratio 1 -> non-monotone
+    assert not O.switch_k3([1, 2, 4, 8], variant=1)[0]  # convex increasing: ratio outside (0,3)
+
+
+def test_switch_cubic_against_exact_roots():
+    g = np.random.default_rng(11)
+    fired = 0
+    for k in range(400):
+        ints = g.integers(-30, 30, size=4)
+        if k % 2:
+            ints = np.sort(ints)  # increasing data: both outcomes common
+        w = [F(int(x), 7) for x in ints]
+        fires, near = O.switch_k3([float(x) for x in w], variant=0, tol=1e-9)
+        if near:
+            continue
+        assert fires == B.switch_fires(w), w
+        fired += fires
+    assert 40 < fired < 340  # both outcomes exercised
+
+
+def test_switch_monotone_smooth_data_does_not_fire():
+    # cubic x^3 + x: p' > 0 everywhere
+    edges = np.arange(-2.0, 3.0)
+    P = lambda x: x ** 4 / 4 + x ** 2 / 2
+    w = (P(edges[1:]) - P(edges[:-1]))
+    assert not O.switch_k3(w)[0]
+
+
+# --------------------------------------------------------------------------------------- P11
+@pytest.mark.parametrize("scheme", ["eno", "weno_js", "rbf_eno", "rbf_weno"])
+@pytest.mark.parametrize("rbf", ["mq", "ga"])
+@pytest.mark.parametrize("switch", [False, True])
+def test_bruteforce_tiny_grid(scheme, rbf, switch):
+    pytest.importorskip("mpmath")
+    g = np.random.default_rng([len(scheme), ord(scheme[0]), ord(rbf[0]), int(switch)])
+    checked = 0
+    for trial in range(6):
+        n = 8
+        vals = [F(int(x), 16) for x in g.integers(-32, 33, size=n)]
+        vmx, vpx = B.reconstruct_periodic(vals, scheme, rbf=rbf, monotone_switch=switch)
+        p = O.Params(scheme=O.SCHEMES[scheme], rbf=O.MQ if rbf == "mq" else O.GA, monotone_switch=int(switch),
+                     tie_tol=1e-9)
+        vm, vp, fl, eta = O.reconstruct(np.array([float(x) for x in vals]), O.PERIODIC, p)
+        ties = (fl & (O.FLAG_SWITCH_TIE | O.FLAG_ENO_TIE_L | O.FLAG_ENO_TIE_R)) != 0
+        for f in range(n + 1):
+            if ties[f]:
+                continue
+            assert vm[f] == pytest.approx(float(vmx[f]), rel=1e-11, abs=1e-11), (trial, f)
+            assert vp[f] == pytest.approx(float(vpx[f]), rel=1e-11, abs=1e-11), (trial, f)
+            checked += 1
+    assert checked > 20
+
+
+def test_periodic_faces_coincide():
+    g = np.random.default_rng(3)
+    u = g.normal(size=37)
+    vm, vp, fl, eta = O.reconstruct(u, O.PERIODIC, O.Params())
+    assert vm[0] == vm[-1] and vp[0] == vp[-1] and eta[0] == eta[-1]
