@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Benchmark: batched 1D Burgers with the non-polynomial RBF-WENO5 method on one GB300 per rank.
+
+Workload (one "step" = one whole solve of the batch): 4096 periodic Burgers instances on
+[0, 2 pi], N log-uniform in [64, 8192] (seeded), u0 = 1 + four Fourier modes + up to two
+jumps, Gaussian perturbation with the monotone switch, Lax-Friedrichs flux, TVD-RK3 at
+CFL 0.5, run past shock formation to T = 1.5; float state, shape parameter / switch /
+smoothness indicators in double.  Each instance keeps its own dt; the batch runs through
+the fused per-stage kernels of libnpweno over a work list of (instance, tile) pairs.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead, on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1602_00182_gb300 import inputs as I  # noqa: E402
+
+WORKLOAD = ("batched 1D Burgers u_t+(u^2/2)_x=0 on [0,2pi], periodic: 4096 instances, N log-uniform [64,8192], "
+            "u0=1+4 Fourier modes+<=2 jumps, RBF-WENO5 Gaussian + monotone switch, LF flux, TVD-RK3 CFL 0.5 to T=1.5")
+T_END = 1.5
+CFL = 0.5
+SAMPLE_STRIDE = 64     # cpu sample: every 64th instance of the N-sorted batch
+SAMPLE_STEPS = 20      # RK3 steps per sampled instance
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------- CPU oracle leg
+def _oracle_job(args):
+    u0, dx, steps = args
+    import oracle as O
+    t0 = time.perf_counter()
+    O.solve(u0, dx, T_END, CFL, O.BURGERS, O.PERIODIC, O.Params(rbf=O.GA), max_steps=steps)
+    return time.perf_counter() - t0
+
+
+def cpu_sample(inst, cores: int):
+    """The FP64 oracle on a bounded sample: every SAMPLE_STRIDE-th instance (sorted by N), the
+    first SAMPLE_STEPS RK3 steps each, spread over `cores` spawned processes."""
+    import multiprocessing as mp
+    import oracle as O
+    O.build()
+    order = sorted(range(len(inst)), key=lambda i: inst[i].n)
+    pick = order[SAMPLE_STRIDE // 2::SAMPLE_STRIDE]
+    jobs = [(inst[i].u0[0].astype(np.float64), inst[i].dx, SAMPLE_STEPS) for i in pick]
+    cells = sum(inst[i].n for i in pick) * SAMPLE_STEPS
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_job, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    return cells / wall, wall, (f"{len(pick)} instances (every {SAMPLE_STRIDE}th by N, N={inst[pick[0]].n}.."
+                                f"{inst[pick[-1]].n}), first {SAMPLE_STEPS} RK3 steps each, FP64 oracle, "
+                                f"{cores} spawned processes")
+
+
+# ------------------------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self, gpu_index: int):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or not f[0].isdigit() or int(f[0]) != gpu_index:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------- GPU leg
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_1602_00182_gb300.npweno as npw
+    from paper_1602_00182_gb300 import build as b
+
+    if local_rank == 0 or not os.path.exists(npw.LIB_PATH):
+        b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    lib = npw.load()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+
+    inst = I.burgers_batch(count=args.instances, seed_index=1 + 1000 * rank)
+    # largest instances first in the arena (the work list follows the arena order)
+    order = sorted(range(len(inst)), key=lambda i: -inst[i].n)
+    ns = [inst[i].n for i in order]
+    table, total = npw.make_instances(ns, [inst[i].dx for i in order], [T_END] * len(order), [CFL] * len(order),
+                                      [npw.NPW_BC_PERIODIC] * len(order))
+    host0 = np.concatenate([inst[i].u0[0] for i in order]).astype(np.float32)
+    params = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED)
+    pristine = torch.tensor(host0, device=dev)
+    arena = pristine.clone()
+    ws = torch.empty(npw.npw_batch_workspace_size(table, 1, params), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    stream = torch.cuda.current_stream()
+
+    def one_solve():
+        st, stats = npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, params, workspace=ws)
+        if st != 0:
+            raise RuntimeError(f"batch solve failed with status {st}")
+        return stats
+
+    # warm-up (also yields the per-instance step counts: the work of one step)
+    for _ in range(args.warmup):
+        arena.copy_(pristine)
+        stats = one_solve()
+    cell_updates = sum(n * s["steps"] for n, s in zip(ns, stats))
+
+    pr = npw_profile()
+    lib.npw_profile_reset()
+    lib.npw_profile_enable(1)
+    times = []
+    clocks = Clocks(os.path.join(args.out_dir, f"clocks_rank{rank}.csv"))
+    with clocks:
+        for _ in range(args.steps):
+            arena.copy_(pristine)
+            flush.fill_(1.0)  # evict the working set from L2 between timed steps
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    lib.npw_profile_read(ctypes.byref(pr))
+    lib.npw_profile_enable(0)
+    total_ms = sum(times)
+    tmax = total_ms
+    cu_all = cell_updates * args.steps
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tmax = t.item()
+        c = torch.tensor([float(cu_all)], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(c, op=torch.distributed.ReduceOp.SUM)
+        cu_all = c.item()
+    value = cu_all / (tmax / 1e3)
+
+    # roofline of the fused stage kernel: algorithmic bytes = per cell-update 8 float accesses
+    # (stage 1: read u^n, write u1; stages 2, 3: read u^(k), read u^n, write)
+    alg_bytes = cell_updates * args.steps * 8 * 4
+    stage_s = pr.stage_ms / 1e3
+    achieved = alg_bytes / stage_s / 1e9 if stage_s > 0 else None
+    peak, peak_kind = _peaks()
+    traffic = _ncu_traffic()
+
+    # end to end through the C ABI with host buffers: H2D of the initial state, the solve,
+    # D2H of the result, per step
+    pinned_in = torch.from_numpy(host0).pin_memory()
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        arena.copy_(pinned_in, non_blocking=True)
+        one_solve()
+        pinned_out.copy_(arena, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = cell_updates * args.steps / sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_value * world], dtype=torch.float64, device=dev)
+        e2e_value = t.item()
+
+    out = {
+        "metric": "cell-updates/s",
+        "value": value,
+        "unit": "cell-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": tmax / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded)",
+        "impl": "ours",
+        "config": {
+            "workload": WORKLOAD,
+            "instances": len(ns),
+            "cells": int(sum(ns)),
+            "cell_updates_per_step": int(cell_updates),
+            "precision": "NPW_FP32_MIXED: f32 state/candidates/weights/flux/update; f64 eta, switch, ENO choice, beta",
+            "l2": "flushed (256 MB write) before every timed step; working set 3 x 4 B x cells",
+            "parallelism": f"independent instance batches, one per rank (x{world})",
+        },
+        "roofline": {
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic,
+            "kernel": "stage1d_kernel<float,double,BURGERS>",
+            "stage_launches": int(pr.stage_launches),
+            "stage_ms": pr.stage_ms,
+            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+        },
+        "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": int(host0.nbytes),
+                "d2h_bytes_per_step": int(host0.nbytes)},
+        "gpu_launches": int(pr.kernel_launches),
+        "clocks": clocks.summary(local_rank),
+    }
+    return out, inst
+
+
+class npw_profile(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("stage_launches", ctypes.c_int64), ("stage_ms", ctypes.c_double),
+                ("timed_launches", ctypes.c_int64)]
+
+
+def _ncu_traffic():
+    """DRAM bytes per stage launch from the committed ncu summary, when it matches the
+    current kernel (null otherwise)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("stage1d_burgers_f32_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--instances", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
+    args = ap.parse_args()
+    os.makedirs(args.out_dir, exist_ok=True)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    cores = os.cpu_count() or 1
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        inst = I.burgers_batch(count=args.instances, seed_index=1)
+        vals = []
+        for _ in range(args.warmup):
+            cpu_sample(inst, cores)
+        walls = []
+        for _ in range(args.steps):
+            v, wall, desc = cpu_sample(inst, cores)
+            vals.append(v)
+            walls.append(wall)
+        value = float(np.mean(vals))
+        print(json.dumps({
+            "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(walls)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "impl": "reference",
+            "config": {"workload": WORKLOAD, "instances": args.instances, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out, inst = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            v, wall, desc = cpu_sample(inst, cores)
+            out["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                                   "sample": desc}
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

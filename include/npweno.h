@@ -1,0 +1,204 @@
+/*
+ * npweno.h -- C ABI of the GB300 (sm_103a) library for the non-polynomial (RBF-perturbed)
+ * ENO3 / WENO5 finite-volume method of Guo & Jung, arXiv 1602.00182.
+ *
+ * The method (paper Sec. 2-5): cell averages vbar_i on a uniform grid are reconstructed to
+ * the two one-sided values v^-_{i+1/2}, v^+_{i-1/2} at every face by the polynomial ENO3 or
+ * WENO5 coefficients perturbed by an RBF shape parameter eta = eps^2 dx^2 (Table k3; the
+ * multiquadric rows are printed, the Gaussian rows follow Sec. 3.3's recipe).  eta is set per
+ * face by the optimisation condition of Table k3 and forced to 0 by the monotone-polynomial
+ * switch of Sec. 4 (eq. adaptation).  The face values feed the Lax-Friedrichs flux, the
+ * conservative difference of eq. PDE1 and the TVD Runge-Kutta 3 update (Sec. 5.1).
+ *
+ * Conventions shared by every entry point:
+ *   - Array pointers are DEVICE pointers owned by the caller unless stated otherwise.
+ *     Element type: double when params->precision == NPW_FP64, float when NPW_FP32_MIXED.
+ *   - 1D fields are laid out field-major, [m][n] contiguous; 2D fields are [m][ny][nx].
+ *     Face arrays are [m][n+1]: face f lies between cell f-1 and cell f (faces 1/2 .. n+1/2
+ *     of the paper, shifted to start at 0).
+ *   - The library allocates no device memory.  Entry points that need scratch take a
+ *     caller-owned device `workspace` of at least the size returned by the matching
+ *     npw_*_workspace_size() call; its contents on entry are ignored.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
+ *     asynchronous on that stream except where a result must reach the host (the solve
+ *     calls poll a 4-byte completion word between launches and return when done).
+ *   - Errors are returned as npw_status and never abort; npw_last_error() gives the text
+ *     of the most recent failure on the calling thread.
+ *   - n >= 6 cells (3 ghost cells per side feed the WENO5 stencil); dx > 0; k must be 3.
+ */
+#ifndef NPWENO_H
+#define NPWENO_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NPW_OK = 0,
+    NPW_EINVAL = -1,      /* bad argument (size, enum, null pointer, workspace too small) */
+    NPW_ENOMEM = -2,      /* reserved: the library itself never allocates */
+    NPW_ECUDA = -3,       /* a CUDA runtime call failed; see npw_last_error() */
+    NPW_ETIMEOUT = -4,    /* a bounded wait ran out */
+    NPW_ENONFINITE = -5,  /* the state became non-finite (per instance in batch mode) */
+    NPW_EBUSY = -6        /* server: request does not fit the memory budget now */
+} npw_status;
+
+/* Flux functions of the paper's examples: f = a u (Sec. 5.2 Ex. 1, 2), f = u^2/2 (Ex. 3),
+ * 1D Euler (Ex. 4, m = 3), 2D Euler (Sec. 7 form, m = 4). */
+typedef enum { NPW_FLUX_ADVECTION = 0, NPW_FLUX_BURGERS = 1, NPW_FLUX_EULER1D = 2, NPW_FLUX_EULER2D = 3 } npw_flux_kind;
+/* Boundary conditions: periodic (Ex. 1, 3), transmissive = zero-gradient ghost cells
+ * (Ex. 4), inflow = constant left ghost state params->inflow (Ex. 2), right transmissive. */
+typedef enum { NPW_BC_PERIODIC = 0, NPW_BC_TRANSMISSIVE = 1, NPW_BC_INFLOW = 2 } npw_bc;
+/* Schemes compared in the paper (Sec. 5.2): ENO3, WENO-JS5 (eta = 0), RBF-ENO3, RBF-WENO5. */
+typedef enum { NPW_ENO = 0, NPW_WENO_JS = 1, NPW_RBF_ENO = 2, NPW_RBF_WENO = 3 } npw_scheme;
+typedef enum { NPW_RBF_MQ = 0, NPW_RBF_GA = 1 } npw_rbf;
+/* NPW_FP64: everything in double.  NPW_FP32_MIXED: float state, candidates, weights, flux
+ * and update; the shape parameter, the monotone switch and the smoothness indicators are
+ * evaluated in double from the float cell averages. */
+typedef enum { NPW_FP64 = 0, NPW_FP32_MIXED = 1 } npw_precision;
+
+typedef struct {
+    int32_t k;               /* reconstruction order parameter; only 3 is supported */
+    int32_t scheme;          /* npw_scheme */
+    int32_t rbf;             /* npw_rbf: perturbation rows of Table k3 (MQ) or Sec. 3.3 (GA) */
+    int32_t monotone_switch; /* 1: eta = 0 where the stencil polynomial is non-monotone */
+    int32_t switch_variant;  /* 0: cubic on the 4-cell eta stencil; 1: eq. root_value on both 3-cell halves */
+    int32_t characteristic;  /* 1D Euler only: reconstruct Roe characteristic fields */
+    int32_t precision;       /* npw_precision */
+    int32_t pad_;
+    double eps_M;            /* additive guard of the eta denominator (Table k3), e.g. 1e-12 */
+    double eps_weno;         /* WENO epsilon of Sec. 2, 1e-6 */
+    double gamma;            /* ratio of specific heats, 1.4 */
+    double adv_speed;        /* advection speed a (x) for NPW_FLUX_ADVECTION */
+    double adv_speed_y;      /* advection speed (y) for 2D advection */
+    double inflow[4];        /* ghost state of NPW_BC_INFLOW (conserved variables) */
+} npw_params;
+
+typedef struct {
+    int64_t steps;    /* RK3 steps taken */
+    double t;         /* time reached (== t_end on success) */
+    double alpha_max; /* largest Lax-Friedrichs alpha seen */
+    int32_t status;   /* npw_status of this problem */
+    int32_t pad_;
+} npw_solve_stats;
+
+/* One problem of a batch: a 1D field set of n cells at element `offset` of the arena,
+ * [m][n] contiguous.  The time step of each instance is its own. */
+typedef struct {
+    int64_t offset;  /* element offset of the instance in the arena */
+    int64_t n;       /* cells */
+    double dx;       /* cell width */
+    double t_end;    /* final time */
+    double cfl;      /* dt = cfl * dx / alpha^n */
+    int32_t bc;      /* npw_bc */
+    int32_t pad_;
+} npw_instance;
+
+/* Fill *p with the defaults: k = 3, RBF-WENO5, multiquadric, switch on (variant 0),
+ * component-wise, FP64, eps_M = 1e-12, eps_weno = 1e-6, gamma = 1.4, a = (1, 1). */
+void npw_default_params(npw_params* p);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char* npw_last_error(void);
+
+/* ABI version (major*10000 + minor*100 + patch). */
+int32_t npw_version(void);
+
+/*
+ * Reconstruction only (paper Sec. 2 and 3.5, eq. weno_re, Table k3, Sec. 4 eq. adaptation):
+ * for each of the n+1 faces, the left/right states v^-, v^+ of every field.
+ *   vbar    [m][n] cell averages (device)
+ *   v_minus [m][n+1] out: v^-_f from cell f-1;  v_plus [m][n+1] out: v^+_f from cell f
+ *   flags   [m][n+1] out, may be NULL: bit0 = monotone switch fired (eta set to 0),
+ *           bits 2-3 = ENO stencil r of cell f-1, bits 4-5 = ENO stencil r of cell f.
+ * m = 1, or m = 3 with params->characteristic for the 1D Euler characteristic fields.
+ * Returns NPW_EINVAL for n < 6, m outside 1..4, characteristic with m != 3, null pointers.
+ */
+npw_status npweno_reconstruct(const void* vbar, int64_t n, int32_t m, int32_t bc, const npw_params* params,
+                              void* v_minus, void* v_plus, uint8_t* flags, void* stream);
+
+/*
+ * Lax-Friedrichs numerical flux (Sec. 5.1): h = (f(v^-) + f(v^+) - alpha (v^+ - v^-)) / 2
+ * for every face and field.  v_minus, v_plus, h are [m][nfaces] (device); m must match the
+ * flux kind (1, 3 for 1D Euler); alpha >= 0 is the constant of Sec. 5.1.
+ */
+npw_status npweno_flux(const void* v_minus, const void* v_plus, int64_t nfaces, int32_t m, int32_t flux_kind,
+                       double alpha, const npw_params* params, void* h, void* stream);
+
+/* Bytes of device workspace npweno_rk3_step / npweno_solve need for n cells, m fields. */
+size_t npw_workspace_size(int64_t n, int32_t m, const npw_params* params);
+
+/*
+ * One TVD-RK3 step (Sec. 5.1, Shu-Osher form) of u [m][n] (device, in/out) with the given
+ * dt.  alpha of the Lax-Friedrichs flux is max_i |f'(u_i^n)| over the field, frozen over the
+ * three stages.  Each stage is one fused kernel: halo load, shape parameter, switch,
+ * candidates, weights, flux, flux difference (eq. PDE1) and the stage combination.
+ * If alpha_out is not NULL the alpha used is written there (host double; the call then
+ * synchronises the stream).
+ */
+npw_status npweno_rk3_step(void* u, int64_t n, int32_t m, double dx, double dt, int32_t flux_kind, int32_t bc,
+                           const npw_params* params, void* workspace, size_t workspace_bytes, double* alpha_out,
+                           void* stream);
+
+/*
+ * Advance u [m][n] (device, in/out) from t = 0 to t_end with dt = cfl * dx / alpha^n, alpha^n
+ * = max_i |f'(u_i^n)| (Sec. 5.1 with the CFL rule of Sec. 5.2); the step that reaches t_end to
+ * within 1e-10 of a step is shortened to end exactly at t_end.  Time control runs on the
+ * device; the host polls a completion word between launches.  out (host) may be NULL.
+ * Returns NPW_ENONFINITE if the state stops being finite.
+ */
+npw_status npweno_solve(void* u, int64_t n, int32_t m, double dx, double t_end, double cfl, int32_t flux_kind,
+                        int32_t bc, const npw_params* params, void* workspace, size_t workspace_bytes,
+                        npw_solve_stats* out, void* stream);
+
+/*
+ * Many independent 1D problems in one arena (device), advanced together by the same fused
+ * stage kernels over a work list of (instance, tile) pairs; each instance keeps its own t,
+ * dt and alpha on the device and drops out of the work when it reaches its t_end.
+ * inst (host, count entries) describes the instances; out (host, count entries, may be
+ * NULL) receives per-instance statistics.  The returned status is NPW_OK when every
+ * instance finished; otherwise the first failing instance's status.
+ */
+size_t npw_batch_workspace_size(const npw_instance* inst, int32_t count, int32_t m, const npw_params* params);
+npw_status npweno_batch_solve(void* arena, const npw_instance* inst, int32_t count, int32_t m, int32_t flux_kind,
+                              const npw_params* params, void* workspace, size_t workspace_bytes,
+                              npw_solve_stats* out, void* stream);
+
+/*
+ * 2D dimension-by-dimension form (Sec. 7, eq. 2DIntegral with one midpoint quadrature point
+ * per face): the x faces are reconstructed along grid rows and the y faces along columns;
+ * L = -(h^x_{i+1/2,j} - h^x_{i-1/2,j})/dx - (h^y_{i,j+1/2} - h^y_{i,j-1/2})/dy; one fused
+ * kernel per stage.  u is [m][ny][nx] (device); m = 4 for NPW_FLUX_EULER2D, m = 1 for scalar
+ * advection / Burgers.  dt of npweno_solve_2d = cfl / (alpha_x/dx + alpha_y/dy).
+ */
+size_t npw_workspace_size_2d(int64_t nx, int64_t ny, int32_t m, const npw_params* params);
+npw_status npweno_rk3_step_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx, double dy, double dt,
+                              int32_t flux_kind, int32_t bc, const npw_params* params, void* workspace,
+                              size_t workspace_bytes, void* stream);
+npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx, double dy, double t_end,
+                           double cfl, int32_t flux_kind, int32_t bc, const npw_params* params, void* workspace,
+                           size_t workspace_bytes, npw_solve_stats* out, void* stream);
+
+/*
+ * Process-wide launch counters and stage-kernel timing (no counterpart in the paper; used to
+ * put each kernel against its roofline).  When enabled, every launch of the fused stage
+ * kernel is bracketed by two CUDA events recorded on the launching stream; the elapsed times
+ * are summed at the next point where the runtime waits for its stream.  Counters are
+ * cumulative until npw_profile_reset().
+ */
+typedef struct {
+    int64_t kernel_launches; /* every kernel this library launched */
+    int64_t stage_launches;  /* launches of the fused stage kernel (1D and 2D) */
+    double stage_ms;         /* summed device time of the timed stage launches (enabled only) */
+    int64_t timed_launches;  /* stage launches that were timed */
+} npw_profile;
+void npw_profile_enable(int32_t on);
+void npw_profile_reset(void);
+void npw_profile_read(npw_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NPWENO_H */

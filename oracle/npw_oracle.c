@@ -324,7 +324,7 @@ static double line_get(const double* u, long n, long stride, long k, int bc, dou
 /* Euler eigen-structure for the characteristic-wise variant.  The paper reconstructs     */
 /* the conserved variables of Example 4; the characteristic projection is an option of   */
 /* this implementation: Roe average at the face, right eigenvectors R of dF/dU, and       */
-/* L = R^{-1} obtained by numerical inversion.                                            */
+/* L = R^{-1} in closed form (L R = I is checked by a test).                              */
 /* ------------------------------------------------------------------------------------ */
 int orc_euler_eigvec(const double UL[3], const double UR[3], double gamma, double R[3][3], double L[3][3]) {
     double rl = UL[0], rr = UR[0];
@@ -347,15 +347,20 @@ int orc_euler_eigvec(const double UL[3], const double UR[3], double gamma, doubl
     R[2][0] = h - u * c;
     R[2][1] = 0.5 * u * u;
     R[2][2] = h + u * c;
-    /* L = R^{-1}, column by column */
-    for (int col = 0; col < 3; ++col) {
-        double A[4][4] = {{0}}, b[4] = {0}, x[4] = {0};
-        for (int a = 0; a < 3; ++a)
-            for (int k = 0; k < 3; ++k) A[a][k] = R[a][k];
-        b[col] = 1.0;
-        if (small_solve(3, A, b, x) != 0) return -1;
-        for (int a = 0; a < 3; ++a) L[a][col] = x[a];
-    }
+    /* L = R^{-1} in closed form, with b1 = (gamma - 1)/c^2 and b2 = b1 u^2 / 2 (the rows are
+     * the left eigenvectors of the Euler Jacobian at the Roe state; L R = I is pinned by a test) */
+    double b1 = (gamma - 1.0) / c2;
+    double b2 = 0.5 * b1 * u * u;
+    double uc = u / c, ic = 1.0 / c;
+    L[0][0] = 0.5 * (b2 + uc);
+    L[0][1] = -0.5 * (b1 * u + ic);
+    L[0][2] = 0.5 * b1;
+    L[1][0] = 1.0 - b2;
+    L[1][1] = b1 * u;
+    L[1][2] = -b1;
+    L[2][0] = 0.5 * (b2 - uc);
+    L[2][1] = -0.5 * (b1 * u - ic);
+    L[2][2] = 0.5 * b1;
     return 0;
 }
 

@@ -1,0 +1,830 @@
+// npw_api.cu -- host runtime of libnpweno: argument checks, workspace layout, device-side
+// time control kernels, the solve loops and the C ABI of include/npweno.h.
+#include <cuda_runtime.h>
+
+#include <time.h>
+
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "npw_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+npw_status fail(npw_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+npw_status fail(npw_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+npw_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(NPW_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define NPW_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int flux_m(int kind) { return kind == NPW_FLUX_EULER1D ? 3 : (kind == NPW_FLUX_EULER2D ? 4 : 1); }
+
+size_t elem_size(const npw_params* p) { return p->precision == NPW_FP32_MIXED ? sizeof(float) : sizeof(double); }
+
+npw_status check_params(const npw_params* p) {
+    if (!p) return fail(NPW_EINVAL, "params is NULL");
+    if (p->k != 3) return fail(NPW_EINVAL, "only k = 3 (ENO3 / WENO5) is supported, got k = %d", p->k);
+    if (p->scheme < NPW_ENO || p->scheme > NPW_RBF_WENO) return fail(NPW_EINVAL, "bad scheme %d", p->scheme);
+    if (p->rbf != NPW_RBF_MQ && p->rbf != NPW_RBF_GA) return fail(NPW_EINVAL, "bad rbf %d", p->rbf);
+    if (p->switch_variant < 0 || p->switch_variant > 1) return fail(NPW_EINVAL, "bad switch_variant");
+    if (p->precision != NPW_FP64 && p->precision != NPW_FP32_MIXED) return fail(NPW_EINVAL, "bad precision");
+    if (!(p->eps_weno > 0.0)) return fail(NPW_EINVAL, "eps_weno must be > 0");
+    if (!(p->gamma > 1.0)) return fail(NPW_EINVAL, "gamma must be > 1");
+    return NPW_OK;
+}
+
+npw::MethodParams method(const npw_params* p) {
+    npw::MethodParams mp{};
+    mp.scheme = p->scheme;
+    mp.rbf = p->rbf;
+    mp.monotone_switch = p->monotone_switch ? 1 : 0;
+    mp.switch_variant = p->switch_variant;
+    mp.characteristic = p->characteristic ? 1 : 0;
+    mp.eps_M = p->eps_M;
+    mp.eps_weno = p->eps_weno;
+    mp.gamma = p->gamma;
+    mp.adv_speed = p->adv_speed;
+    mp.adv_speed_y = p->adv_speed_y;
+    for (int k = 0; k < 4; ++k) mp.inflow[k] = p->inflow[k];
+    return mp;
+}
+
+npw_status check_kind_1d(int kind, int m, const npw_params* p) {
+    if (kind != NPW_FLUX_ADVECTION && kind != NPW_FLUX_BURGERS && kind != NPW_FLUX_EULER1D)
+        return fail(NPW_EINVAL, "flux kind %d is not a 1D flux", kind);
+    if (m != flux_m(kind)) return fail(NPW_EINVAL, "m = %d does not match flux kind %d", m, kind);
+    if (p->characteristic && kind != NPW_FLUX_EULER1D)
+        return fail(NPW_EINVAL, "characteristic reconstruction needs the 1D Euler flux");
+    return NPW_OK;
+}
+
+npw_status check_bc(int bc) {
+    if (bc < NPW_BC_PERIODIC || bc > NPW_BC_INFLOW) return fail(NPW_EINVAL, "bad boundary condition %d", bc);
+    return NPW_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Workspace layout of the 1D runtime: two stage buffers (u1, u2) of the arena size, the
+// instance table, the per-instance control words, the tile table and the poll words.
+// ---------------------------------------------------------------------------------------
+struct Layout1D {
+    size_t u1, u2, inst, ctl, tiles, poll, total;
+};
+
+Layout1D layout_1d(int64_t arena_elems, int count, int64_t ntiles, size_t esz) {
+    Layout1D L{};
+    size_t o = 0;
+    L.u1 = o;
+    o = align256(o + (size_t)arena_elems * esz);
+    L.u2 = o;
+    o = align256(o + (size_t)arena_elems * esz);
+    L.inst = o;
+    o = align256(o + sizeof(npw::InstDev) * (size_t)count);
+    L.ctl = o;
+    o = align256(o + sizeof(npw::Ctl) * (size_t)count);
+    L.tiles = o;
+    o = align256(o + sizeof(npw::Tile) * (size_t)ntiles);
+    L.poll = o;
+    o = align256(o + 4 * sizeof(long long));
+    L.total = o;
+    return L;
+}
+
+int64_t tiles_of(int64_t n) { return (n + npw::TILE_1D - 1) / npw::TILE_1D; }
+
+double wait_timeout_s() {
+    const char* e = getenv("NPW_WAIT_TIMEOUT_S");
+    double v = e ? atof(e) : 0.0;
+    return v > 0.0 ? v : 1800.0;
+}
+
+// Wait for the stream with a deadline (polling; never an unbounded block).
+npw_status bounded_sync(cudaStream_t s) {
+    cudaEvent_t ev;
+    NPW_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, s);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(ev);
+        return cuda_fail(e, "cudaEventRecord");
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    const double limit = wait_timeout_s();
+    while (true) {
+        e = cudaEventQuery(ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) {
+            cudaEventDestroy(ev);
+            return cuda_fail(e, "cudaEventQuery");
+        }
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > limit) {
+            cudaEventDestroy(ev);
+            return fail(NPW_ETIMEOUT, "stream did not complete within %.0f s", limit);
+        }
+        if (el > 1e-3) {
+            struct timespec ts = {0, 20000};
+            nanosleep(&ts, nullptr);
+        }
+    }
+    cudaEventDestroy(ev);
+    return NPW_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Profiling: launch counters and event-bracketed stage kernels
+// ---------------------------------------------------------------------------------------
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    int64_t launches = 0, stage_launches = 0, timed = 0;
+    double stage_ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending, pool;
+};
+Profiler& prof() {
+    static Profiler p;
+    return p;
+}
+void count_launch(int64_t k = 1) {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.launches += k;
+}
+// returns the event pair to bracket a stage launch (null events when profiling is off)
+std::pair<cudaEvent_t, cudaEvent_t> stage_begin(cudaStream_t s) {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.launches += 1;
+    p.stage_launches += 1;
+    if (!p.on) return {nullptr, nullptr};
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (!p.pool.empty()) {
+        ev = p.pool.back();
+        p.pool.pop_back();
+    } else if (cudaEventCreate(&ev.first) != cudaSuccess || cudaEventCreate(&ev.second) != cudaSuccess) {
+        return {nullptr, nullptr};
+    }
+    cudaEventRecord(ev.first, s);
+    return ev;
+}
+void stage_end(std::pair<cudaEvent_t, cudaEvent_t> ev, cudaStream_t s) {
+    if (!ev.first) return;
+    cudaEventRecord(ev.second, s);
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.pending.push_back(ev);
+}
+// after the stream has been waited for: sum the elapsed times of completed pairs
+void profile_collect() {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> still;
+    for (auto& ev : p.pending) {
+        if (cudaEventQuery(ev.second) == cudaSuccess) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) {
+                p.stage_ms += ms;
+                p.timed += 1;
+            }
+            p.pool.push_back(ev);
+        } else {
+            still.push_back(ev);
+        }
+    }
+    p.pending.swap(still);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Device-side time control helpers (precision independent)
+// ---------------------------------------------------------------------------------------
+namespace npw {
+
+// mode 0: reset; mode 1: start a solve (dt from alpha^0); mode 2: one step with fixed dt
+__global__ void ctl_start_kernel(Ctl* ctl, const InstDev* inst, int count, int mode, double dt_fixed) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    Ctl* c = ctl + i;
+    if (mode == 0) {
+        memset(c, 0, sizeof(Ctl));
+        return;
+    }
+    double a = __longlong_as_double((long long)c->alpha_next_bits);
+    c->alpha_next_bits = 0ull;
+    c->tiles_done = 0u;
+    if (!(a - a == 0.0)) {
+        c->status = NPW_ENONFINITE;
+        c->done = 1;
+        return;
+    }
+    c->alpha = a;
+    c->alpha_max = a;
+    if (mode == 2) {
+        c->dt = dt_fixed;
+        c->last = 0;
+        c->done = 0;
+        return;
+    }
+    const InstDev in = inst[i];
+    c->t = 0.0;
+    if (!(c->t < in.t_end)) {
+        c->done = 1;
+        return;
+    }
+    double rate = a / in.dx;
+    double dt = (rate > 0.0) ? in.cfl / rate : in.t_end - c->t;
+    int last = 0;
+    if (c->t + dt * (1.0 + 1e-10) >= in.t_end) {
+        dt = in.t_end - c->t;
+        last = 1;
+    }
+    c->dt = dt;
+    c->last = last;
+}
+
+__global__ void ctl_start_2d_kernel(Ctl* c, const Inst2D* inst, int mode, double dt_fixed) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (mode == 0) {
+        memset(c, 0, sizeof(Ctl));
+        return;
+    }
+    double ax = __longlong_as_double((long long)c->alpha_next_bits);
+    double ay = __longlong_as_double((long long)c->alpha_y_next_bits);
+    c->alpha_next_bits = 0ull;
+    c->alpha_y_next_bits = 0ull;
+    c->tiles_done = 0u;
+    if (!(ax - ax == 0.0) || !(ay - ay == 0.0)) {
+        c->status = NPW_ENONFINITE;
+        c->done = 1;
+        return;
+    }
+    c->alpha = ax;
+    c->alpha_y = ay;
+    c->alpha_max = ax > ay ? ax : ay;
+    if (mode == 2) {
+        c->dt = dt_fixed;
+        c->last = 0;
+        c->done = 0;
+        return;
+    }
+    const Inst2D in = *inst;
+    c->t = 0.0;
+    if (!(c->t < in.t_end)) {
+        c->done = 1;
+        return;
+    }
+    double rate = ax / in.dx + ay / in.dy;
+    double dt = (rate > 0.0) ? in.cfl / rate : in.t_end - c->t;
+    int last = 0;
+    if (c->t + dt * (1.0 + 1e-10) >= in.t_end) {
+        dt = in.t_end - c->t;
+        last = 1;
+    }
+    c->dt = dt;
+    c->last = last;
+}
+
+// poll[0] = active instances, poll[1] = largest remaining step estimate
+__global__ void count_active_kernel(const Ctl* ctl, const InstDev* inst, int count, const Inst2D* inst2d,
+                                    long long* poll) {
+    __shared__ long long s_act[256], s_rem[256];
+    long long act = 0, rem = 0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const Ctl& c = ctl[i];
+        if (!c.done) {
+            ++act;
+            double t_end = inst ? inst[i].t_end : inst2d->t_end;
+            double r = (c.dt > 0.0) ? (t_end - c.t) / c.dt : 1.0;
+            long long ri = (long long)(r < 1e9 ? r : 1e9) + 1;
+            rem = ri > rem ? ri : rem;
+        }
+    }
+    s_act[threadIdx.x] = act;
+    s_rem[threadIdx.x] = rem;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s_act[threadIdx.x] += s_act[threadIdx.x + o];
+            s_rem[threadIdx.x] = s_rem[threadIdx.x + o] > s_rem[threadIdx.x] ? s_rem[threadIdx.x + o] : s_rem[threadIdx.x];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        poll[0] = s_act[0];
+        poll[1] = s_rem[0];
+    }
+}
+
+}  // namespace npw
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// The 1D runtime shared by rk3_step, solve and batch_solve.
+// ---------------------------------------------------------------------------------------
+struct Run1D {
+    void* arena;
+    int count;
+    int m;
+    int kind;
+    npw::MethodParams mp;
+    bool fp32;
+    unsigned char* ws;
+    Layout1D L;
+    int64_t ntiles;
+    cudaStream_t s;
+};
+
+template <typename R>
+npw_status run_step_kernels(const Run1D& r, int advance) {
+    npw::Stage1DArgs a{};
+    a.inst = reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst);
+    a.ctl = reinterpret_cast<npw::Ctl*>(r.ws + r.L.ctl);
+    a.tiles = reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles);
+    a.ntiles = (int)r.ntiles;
+    a.advance = advance;
+    a.tile = npw::TILE_1D;
+    a.mp = r.mp;
+    void* u = r.arena;
+    void* u1 = r.ws + r.L.u1;
+    void* u2 = r.ws + r.L.u2;
+    // stage 1: u -> u1; stage 2: (u1, u) -> u2; stage 3: (u2, u) -> u (in place: each cell reads
+    // its own u^n before writing it, and the halo of stage 3 comes from u2)
+    const void* in_[3] = {u, u1, u2};
+    void* out_[3] = {u1, u2, u};
+    for (int st = 0; st < 3; ++st) {
+        a.uin = in_[st];
+        a.un = u;
+        a.uout = out_[st];
+        a.stage = st;
+        auto ev = stage_begin(r.s);
+        cudaError_t e = npw::launch_stage1d<R>(a, r.m, r.kind, r.s);
+        stage_end(ev, r.s);
+        if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
+    }
+    return NPW_OK;
+}
+
+npw_status step_kernels(const Run1D& r, int advance) {
+    return r.fp32 ? run_step_kernels<float>(r, advance) : run_step_kernels<double>(r, advance);
+}
+
+npw_status setup_1d(Run1D& r, const npw_instance* inst, int count, double dt_fixed, int mode) {
+    std::vector<npw::InstDev> hi(count);
+    std::vector<npw::Tile> ht;
+    ht.reserve((size_t)r.ntiles);
+    for (int i = 0; i < count; ++i) {
+        hi[i].off = inst[i].offset;
+        hi[i].n = inst[i].n;
+        hi[i].dx = inst[i].dx;
+        hi[i].t_end = inst[i].t_end;
+        hi[i].cfl = inst[i].cfl;
+        hi[i].bc = inst[i].bc;
+        hi[i].ntiles = (int32_t)tiles_of(inst[i].n);
+        for (int64_t t = 0; t < hi[i].ntiles; ++t) ht.push_back(npw::Tile{i, (int32_t)(t * npw::TILE_1D)});
+    }
+    // pageable source: each call returns once the data is staged
+    NPW_CUDA(cudaMemcpyAsync(r.ws + r.L.inst, hi.data(), sizeof(npw::InstDev) * count, cudaMemcpyHostToDevice, r.s));
+    NPW_CUDA(cudaMemcpyAsync(r.ws + r.L.tiles, ht.data(), sizeof(npw::Tile) * ht.size(), cudaMemcpyHostToDevice, r.s));
+    npw::Ctl* ctl = reinterpret_cast<npw::Ctl*>(r.ws + r.L.ctl);
+    const npw::InstDev* di = reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst);
+    const unsigned blocks = (unsigned)((count + 127) / 128);
+    npw::ctl_start_kernel<<<blocks, 128, 0, r.s>>>(ctl, di, count, 0, 0.0);
+    NPW_CUDA(cudaGetLastError());
+    cudaError_t e = r.fp32 ? npw::launch_alpha_init<float>(r.arena, di, ctl,
+                                                           reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles),
+                                                           (int)r.ntiles, npw::TILE_1D, r.m, r.kind, r.mp, r.s)
+                           : npw::launch_alpha_init<double>(r.arena, di, ctl,
+                                                            reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles),
+                                                            (int)r.ntiles, npw::TILE_1D, r.m, r.kind, r.mp, r.s);
+    if (e != cudaSuccess) return cuda_fail(e, "alpha kernel launch");
+    npw::ctl_start_kernel<<<blocks, 128, 0, r.s>>>(ctl, di, count, mode, dt_fixed);
+    NPW_CUDA(cudaGetLastError());
+    count_launch(3);
+    return NPW_OK;
+}
+
+npw_status poll(const Run1D& r, long long* act, long long* rem, const npw::Inst2D* inst2d = nullptr) {
+    long long* dpoll = reinterpret_cast<long long*>(r.ws + r.L.poll);
+    npw::count_active_kernel<<<1, 256, 0, r.s>>>(reinterpret_cast<const npw::Ctl*>(r.ws + r.L.ctl),
+                                                 inst2d ? nullptr : reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst),
+                                                 r.count, inst2d, dpoll);
+    NPW_CUDA(cudaGetLastError());
+    count_launch();
+    long long h[2] = {0, 0};
+    NPW_CUDA(cudaMemcpyAsync(h, dpoll, sizeof h, cudaMemcpyDeviceToHost, r.s));
+    npw_status st = bounded_sync(r.s);
+    if (st) return st;
+    profile_collect();
+    *act = h[0];
+    *rem = h[1];
+    return NPW_OK;
+}
+
+npw_status collect_stats(const Run1D& r, npw_solve_stats* out) {
+    std::vector<npw::Ctl> hc(r.count);
+    NPW_CUDA(cudaMemcpyAsync(hc.data(), r.ws + r.L.ctl, sizeof(npw::Ctl) * r.count, cudaMemcpyDeviceToHost, r.s));
+    npw_status st = bounded_sync(r.s);
+    if (st) return st;
+    profile_collect();
+    npw_status first = NPW_OK;
+    for (int i = 0; i < r.count; ++i) {
+        if (out) {
+            out[i].steps = hc[i].steps;
+            out[i].t = hc[i].t;
+            out[i].alpha_max = hc[i].alpha_max;
+            out[i].status = hc[i].status;
+        }
+        if (hc[i].status != NPW_OK && first == NPW_OK) first = (npw_status)hc[i].status;
+    }
+    if (first != NPW_OK) return fail(first, "an instance became non-finite");
+    return NPW_OK;
+}
+
+// Run steps until every instance is done: launch as many steps as the largest remaining
+// estimate (capped), then poll.
+npw_status run_to_end(Run1D& r, npw_solve_stats* out) {
+    long long act = 0, rem = 0;
+    npw_status st = poll(r, &act, &rem);
+    while (st == NPW_OK && act > 0) {
+        long long chunk = rem < 1 ? 1 : (rem > 256 ? 256 : rem);
+        for (long long k = 0; k < chunk && st == NPW_OK; ++k) st = step_kernels(r, 1);
+        if (st == NPW_OK) st = poll(r, &act, &rem);
+    }
+    if (st) return st;
+    return collect_stats(r, out);
+}
+
+}  // namespace
+
+// =======================================================================================
+// C ABI
+// =======================================================================================
+extern "C" {
+
+void npw_default_params(npw_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->k = 3;
+    p->scheme = NPW_RBF_WENO;
+    p->rbf = NPW_RBF_MQ;
+    p->monotone_switch = 1;
+    p->switch_variant = 0;
+    p->characteristic = 0;
+    p->precision = NPW_FP64;
+    p->eps_M = 1e-12;
+    p->eps_weno = 1e-6;
+    p->gamma = 1.4;
+    p->adv_speed = 1.0;
+    p->adv_speed_y = 1.0;
+}
+
+const char* npw_last_error(void) { return g_err.c_str(); }
+
+void npw_profile_enable(int32_t on) {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.on = on != 0;
+}
+
+void npw_profile_reset(void) {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.launches = p.stage_launches = p.timed = 0;
+    p.stage_ms = 0.0;
+    for (auto& ev : p.pending) p.pool.push_back(ev);
+    p.pending.clear();
+}
+
+void npw_profile_read(npw_profile* out) {
+    if (!out) return;
+    profile_collect();
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    out->kernel_launches = p.launches;
+    out->stage_launches = p.stage_launches;
+    out->stage_ms = p.stage_ms;
+    out->timed_launches = p.timed;
+}
+
+int32_t npw_version(void) { return 10000; }
+
+npw_status npweno_reconstruct(const void* vbar, int64_t n, int32_t m, int32_t bc, const npw_params* params,
+                              void* v_minus, void* v_plus, uint8_t* flags, void* stream) {
+    npw_status st = check_params(params);
+    if (st) return st;
+    if (!vbar || !v_minus || !v_plus) return fail(NPW_EINVAL, "null array pointer");
+    if (n < 6) return fail(NPW_EINVAL, "n = %lld < 6", (long long)n);
+    if (m < 1 || m > 4 || m == 2) return fail(NPW_EINVAL, "m = %d not supported", m);
+    if (params->characteristic && m != 3) return fail(NPW_EINVAL, "characteristic reconstruction needs m = 3");
+    if ((st = check_bc(bc))) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    npw::MethodParams mp = method(params);
+    cudaError_t e = params->precision == NPW_FP32_MIXED
+                        ? npw::launch_reconstruct<float>((const float*)vbar, n, m, bc, mp, (float*)v_minus,
+                                                         (float*)v_plus, flags, s)
+                        : npw::launch_reconstruct<double>((const double*)vbar, n, m, bc, mp, (double*)v_minus,
+                                                          (double*)v_plus, flags, s);
+    if (e != cudaSuccess) return cuda_fail(e, "reconstruct launch");
+    count_launch();
+    return NPW_OK;
+}
+
+npw_status npweno_flux(const void* v_minus, const void* v_plus, int64_t nfaces, int32_t m, int32_t flux_kind,
+                       double alpha, const npw_params* params, void* h, void* stream) {
+    npw_status st = check_params(params);
+    if (st) return st;
+    if (!v_minus || !v_plus || !h) return fail(NPW_EINVAL, "null array pointer");
+    if (nfaces < 1) return fail(NPW_EINVAL, "nfaces < 1");
+    if (flux_kind == NPW_FLUX_EULER2D || flux_kind < 0 || flux_kind > NPW_FLUX_EULER2D)
+        return fail(NPW_EINVAL, "flux kind %d not supported here", flux_kind);
+    if (m != flux_m(flux_kind)) return fail(NPW_EINVAL, "m = %d does not match flux kind", m);
+    if (!(alpha >= 0.0)) return fail(NPW_EINVAL, "alpha must be >= 0");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    npw::MethodParams mp = method(params);
+    cudaError_t e = params->precision == NPW_FP32_MIXED
+                        ? npw::launch_flux<float>((const float*)v_minus, (const float*)v_plus, nfaces, m, flux_kind,
+                                                  alpha, mp, (float*)h, s)
+                        : npw::launch_flux<double>((const double*)v_minus, (const double*)v_plus, nfaces, m,
+                                                   flux_kind, alpha, mp, (double*)h, s);
+    if (e != cudaSuccess) return cuda_fail(e, "flux launch");
+    count_launch();
+    return NPW_OK;
+}
+
+size_t npw_workspace_size(int64_t n, int32_t m, const npw_params* params) {
+    if (!params || n < 1 || m < 1) return 0;
+    return layout_1d(n * m, 1, tiles_of(n), elem_size(params)).total;
+}
+
+static npw_status single_run(void* u, int64_t n, int32_t m, double dx, double t_end, double cfl, int32_t flux_kind,
+                             int32_t bc, const npw_params* params, void* workspace, size_t workspace_bytes,
+                             cudaStream_t s, Run1D& r, npw_instance& in) {
+    npw_status st = check_params(params);
+    if (st) return st;
+    if (!u || !workspace) return fail(NPW_EINVAL, "null pointer");
+    if (n < 6) return fail(NPW_EINVAL, "n = %lld < 6", (long long)n);
+    if (n > (int64_t)1 << 30) return fail(NPW_EINVAL, "n too large");
+    if ((st = check_kind_1d(flux_kind, m, params))) return st;
+    if ((st = check_bc(bc))) return st;
+    if (!(dx > 0.0)) return fail(NPW_EINVAL, "dx must be > 0");
+    r.arena = u;
+    r.count = 1;
+    r.m = m;
+    r.kind = flux_kind;
+    r.mp = method(params);
+    r.fp32 = params->precision == NPW_FP32_MIXED;
+    r.ws = static_cast<unsigned char*>(workspace);
+    r.ntiles = tiles_of(n);
+    r.L = layout_1d(n * m, 1, r.ntiles, elem_size(params));
+    r.s = s;
+    if (workspace_bytes < r.L.total)
+        return fail(NPW_EINVAL, "workspace too small: %zu < %zu bytes", workspace_bytes, r.L.total);
+    in.offset = 0;
+    in.n = n;
+    in.dx = dx;
+    in.t_end = t_end;
+    in.cfl = cfl;
+    in.bc = bc;
+    return NPW_OK;
+}
+
+npw_status npweno_rk3_step(void* u, int64_t n, int32_t m, double dx, double dt, int32_t flux_kind, int32_t bc,
+                           const npw_params* params, void* workspace, size_t workspace_bytes, double* alpha_out,
+                           void* stream) {
+    Run1D r{};
+    npw_instance in{};
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    npw_status st = single_run(u, n, m, dx, 0.0, 0.0, flux_kind, bc, params, workspace, workspace_bytes, s, r, in);
+    if (st) return st;
+    if (!(dt >= 0.0)) return fail(NPW_EINVAL, "dt must be >= 0");
+    if ((st = setup_1d(r, &in, 1, dt, 2))) return st;
+    if ((st = step_kernels(r, 0))) return st;
+    if (alpha_out) {
+        npw::Ctl c;
+        NPW_CUDA(cudaMemcpyAsync(&c, r.ws + r.L.ctl, sizeof c, cudaMemcpyDeviceToHost, s));
+        if ((st = bounded_sync(s))) return st;
+        *alpha_out = c.alpha;
+        if (c.status) return fail((npw_status)c.status, "state is not finite");
+    }
+    return NPW_OK;
+}
+
+npw_status npweno_solve(void* u, int64_t n, int32_t m, double dx, double t_end, double cfl, int32_t flux_kind,
+                        int32_t bc, const npw_params* params, void* workspace, size_t workspace_bytes,
+                        npw_solve_stats* out, void* stream) {
+    Run1D r{};
+    npw_instance in{};
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    npw_status st = single_run(u, n, m, dx, t_end, cfl, flux_kind, bc, params, workspace, workspace_bytes, s, r, in);
+    if (st) return st;
+    if (!(cfl > 0.0)) return fail(NPW_EINVAL, "cfl must be > 0");
+    if ((st = setup_1d(r, &in, 1, 0.0, 1))) return st;
+    return run_to_end(r, out);
+}
+
+size_t npw_batch_workspace_size(const npw_instance* inst, int32_t count, int32_t m, const npw_params* params) {
+    if (!inst || count < 1 || !params || m < 1) return 0;
+    int64_t arena = 0, nt = 0;
+    for (int i = 0; i < count; ++i) {
+        int64_t end = inst[i].offset + inst[i].n * m;
+        arena = end > arena ? end : arena;
+        nt += tiles_of(inst[i].n);
+    }
+    return layout_1d(arena, count, nt, elem_size(params)).total;
+}
+
+npw_status npweno_batch_solve(void* arena, const npw_instance* inst, int32_t count, int32_t m, int32_t flux_kind,
+                              const npw_params* params, void* workspace, size_t workspace_bytes,
+                              npw_solve_stats* out, void* stream) {
+    npw_status st = check_params(params);
+    if (st) return st;
+    if (!arena || !inst || !workspace || count < 1) return fail(NPW_EINVAL, "null pointer or empty batch");
+    if ((st = check_kind_1d(flux_kind, m, params))) return st;
+    int64_t arena_elems = 0, nt = 0;
+    for (int i = 0; i < count; ++i) {
+        if (inst[i].n < 6 || inst[i].n > ((int64_t)1 << 30)) return fail(NPW_EINVAL, "instance %d: bad n", i);
+        if (!(inst[i].dx > 0.0) || !(inst[i].cfl > 0.0)) return fail(NPW_EINVAL, "instance %d: bad dx or cfl", i);
+        if (inst[i].offset < 0) return fail(NPW_EINVAL, "instance %d: negative offset", i);
+        if ((st = check_bc(inst[i].bc))) return st;
+        int64_t end = inst[i].offset + inst[i].n * m;
+        arena_elems = end > arena_elems ? end : arena_elems;
+        nt += tiles_of(inst[i].n);
+    }
+    if (nt > (int64_t)1 << 30) return fail(NPW_EINVAL, "too many tiles");
+    Run1D r{};
+    r.arena = arena;
+    r.count = count;
+    r.m = m;
+    r.kind = flux_kind;
+    r.mp = method(params);
+    r.fp32 = params->precision == NPW_FP32_MIXED;
+    r.ws = static_cast<unsigned char*>(workspace);
+    r.ntiles = nt;
+    r.L = layout_1d(arena_elems, count, nt, elem_size(params));
+    r.s = reinterpret_cast<cudaStream_t>(stream);
+    if (workspace_bytes < r.L.total)
+        return fail(NPW_EINVAL, "workspace too small: %zu < %zu bytes", workspace_bytes, r.L.total);
+    if ((st = setup_1d(r, inst, count, 0.0, 1))) return st;
+    return run_to_end(r, out);
+}
+
+// ---------------------------------------------------------------------------------------
+// 2D
+// ---------------------------------------------------------------------------------------
+size_t npw_workspace_size_2d(int64_t nx, int64_t ny, int32_t m, const npw_params* params) {
+    if (!params || nx < 1 || ny < 1 || m < 1) return 0;
+    size_t esz = elem_size(params);
+    size_t o = 0;
+    o = align256(o + (size_t)(nx * ny * m) * esz);
+    o = align256(o + (size_t)(nx * ny * m) * esz);
+    o = align256(o + sizeof(npw::Inst2D));
+    o = align256(o + sizeof(npw::Ctl));
+    o = align256(o + 4 * sizeof(long long));
+    return o;
+}
+
+static npw_status run_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx, double dy, double dt_fixed,
+                         double t_end, double cfl, int32_t flux_kind, int32_t bc, const npw_params* params,
+                         void* workspace, size_t workspace_bytes, npw_solve_stats* out, cudaStream_t s, int mode) {
+    npw_status st = check_params(params);
+    if (st) return st;
+    if (!u || !workspace) return fail(NPW_EINVAL, "null pointer");
+    if (nx < 6 || ny < 6) return fail(NPW_EINVAL, "nx, ny must be >= 6");
+    if (nx * ny > ((int64_t)1 << 31)) return fail(NPW_EINVAL, "grid too large");
+    if (flux_kind != NPW_FLUX_ADVECTION && flux_kind != NPW_FLUX_BURGERS && flux_kind != NPW_FLUX_EULER2D)
+        return fail(NPW_EINVAL, "flux kind %d is not a 2D flux", flux_kind);
+    if (m != flux_m(flux_kind)) return fail(NPW_EINVAL, "m does not match the flux kind");
+    if (params->characteristic) return fail(NPW_EINVAL, "2D runs are component-wise");
+    if ((st = check_bc(bc))) return st;
+    if (!(dx > 0.0) || !(dy > 0.0)) return fail(NPW_EINVAL, "dx, dy must be > 0");
+    const bool fp32 = params->precision == NPW_FP32_MIXED;
+    const size_t esz = elem_size(params);
+    if (workspace_bytes < npw_workspace_size_2d(nx, ny, m, params)) return fail(NPW_EINVAL, "workspace too small");
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    size_t o = 0;
+    void* u1 = ws + o;
+    o = align256(o + (size_t)(nx * ny * m) * esz);
+    void* u2 = ws + o;
+    o = align256(o + (size_t)(nx * ny * m) * esz);
+    npw::Inst2D* dinst = reinterpret_cast<npw::Inst2D*>(ws + o);
+    o = align256(o + sizeof(npw::Inst2D));
+    npw::Ctl* ctl = reinterpret_cast<npw::Ctl*>(ws + o);
+    o = align256(o + sizeof(npw::Ctl));
+    long long* dpoll = reinterpret_cast<long long*>(ws + o);
+
+    npw::Inst2D hi{};
+    hi.off = 0;
+    hi.nx = nx;
+    hi.ny = ny;
+    hi.dx = dx;
+    hi.dy = dy;
+    hi.t_end = t_end;
+    hi.cfl = cfl;
+    hi.bc = bc;
+    hi.tiles_x = (int32_t)((nx + npw::TX_2D - 1) / npw::TX_2D);
+    hi.tiles_y = (int32_t)((ny + npw::TY_2D - 1) / npw::TY_2D);
+    const int tiles = hi.tiles_x * hi.tiles_y;
+    NPW_CUDA(cudaMemcpyAsync(dinst, &hi, sizeof hi, cudaMemcpyHostToDevice, s));
+    npw::MethodParams mp = method(params);
+    npw::ctl_start_2d_kernel<<<1, 32, 0, s>>>(ctl, dinst, 0, 0.0);
+    NPW_CUDA(cudaGetLastError());
+    cudaError_t e = fp32 ? npw::launch_alpha_init_2d<float>(u, dinst, tiles, ctl, flux_kind, mp, s)
+                         : npw::launch_alpha_init_2d<double>(u, dinst, tiles, ctl, flux_kind, mp, s);
+    if (e != cudaSuccess) return cuda_fail(e, "alpha 2d launch");
+    npw::ctl_start_2d_kernel<<<1, 32, 0, s>>>(ctl, dinst, mode, dt_fixed);
+    NPW_CUDA(cudaGetLastError());
+    count_launch(3);
+
+    npw::Stage2DArgs a{};
+    a.inst = dinst;
+    a.ctl = ctl;
+    a.mp = mp;
+    a.advance = mode == 1;
+    const void* in_[3] = {u, u1, u2};
+    void* out_[3] = {u1, u2, u};
+    auto one_step = [&]() -> npw_status {
+        for (int stg = 0; stg < 3; ++stg) {
+            a.uin = in_[stg];
+            a.un = u;
+            a.uout = out_[stg];
+            a.stage = stg;
+            auto ev = stage_begin(s);
+            cudaError_t ee = fp32 ? npw::launch_stage2d<float>(a, tiles, flux_kind, s)
+                                  : npw::launch_stage2d<double>(a, tiles, flux_kind, s);
+            stage_end(ev, s);
+            if (ee != cudaSuccess) return cuda_fail(ee, "stage 2d launch");
+        }
+        return NPW_OK;
+    };
+    if (mode == 2) return one_step();
+    Run1D pr{};
+    pr.ws = ws;
+    pr.count = 1;
+    pr.s = s;
+    pr.L.ctl = (size_t)((unsigned char*)ctl - ws);
+    pr.L.poll = (size_t)((unsigned char*)dpoll - ws);
+    long long act = 0, rem = 0;
+    st = poll(pr, &act, &rem, dinst);
+    while (st == NPW_OK && act > 0) {
+        long long chunk = rem < 1 ? 1 : (rem > 256 ? 256 : rem);
+        for (long long k = 0; k < chunk && st == NPW_OK; ++k) st = one_step();
+        if (st == NPW_OK) st = poll(pr, &act, &rem, dinst);
+    }
+    if (st) return st;
+    npw::Ctl hc;
+    NPW_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, s));
+    if ((st = bounded_sync(s))) return st;
+    if (out) {
+        out->steps = hc.steps;
+        out->t = hc.t;
+        out->alpha_max = hc.alpha_max;
+        out->status = hc.status;
+    }
+    if (hc.status) return fail((npw_status)hc.status, "state is not finite");
+    return NPW_OK;
+}
+
+npw_status npweno_rk3_step_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx, double dy, double dt,
+                              int32_t flux_kind, int32_t bc, const npw_params* params, void* workspace,
+                              size_t workspace_bytes, void* stream) {
+    if (!(dt >= 0.0)) return fail(NPW_EINVAL, "dt must be >= 0");
+    return run_2d(u, nx, ny, m, dx, dy, dt, 0.0, 0.0, flux_kind, bc, params, workspace, workspace_bytes, nullptr,
+                  reinterpret_cast<cudaStream_t>(stream), 2);
+}
+
+npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx, double dy, double t_end,
+                           double cfl, int32_t flux_kind, int32_t bc, const npw_params* params, void* workspace,
+                           size_t workspace_bytes, npw_solve_stats* out, void* stream) {
+    if (!(cfl > 0.0)) return fail(NPW_EINVAL, "cfl must be > 0");
+    return run_2d(u, nx, ny, m, dx, dy, 0.0, t_end, cfl, flux_kind, bc, params, workspace, workspace_bytes, out,
+                  reinterpret_cast<cudaStream_t>(stream), 1);
+}
+
+}  // extern "C"

@@ -1,0 +1,381 @@
+// npw_device.cuh -- per-face arithmetic of the non-polynomial ENO3 / WENO5 method on the GPU.
+//
+// R is the state type (double or float); D is the type in which the shape parameter, the
+// monotone switch, the ENO choice and the smoothness indicators are evaluated (double).
+// In the double instantiation every expression is written in a fixed evaluation order and
+// the translation unit is compiled without multiply-add contraction, so that results are
+// reproducible bit for bit from the cell averages.
+//
+// Paper passages: Sec. 2 (stencils S_r(i), v^{(r)-}_{i+1/2} = sum_j c_rj vbar_{i-r+j}, eq.
+// weno_re with alpha_r = d_r / (eps + beta_r)^2), Sec. 3.5 Table k3 (coefficients and eta;
+// row r = -1 uses 11/6), Sec. 3.3 (Gaussian recipe; k = 3 rows derived from the flat limit of
+// the Gaussian interpolant of the primitive), Sec. 4 (eq. root_value, eq. adaptation),
+// Sec. 5.1 (Lax-Friedrichs flux), Sec. 5.2 Ex. 4 (Euler, ideal gas).
+#pragma once
+#include <cstdint>
+
+#include "npw_internal.h"
+
+namespace npw {
+
+// ---------------------------------------------------------------------------------------
+// Table k3.  row = r + 1 for r = -1..2; row r gives the value at face x_{i+1/2} from the
+// cells i-r, i-r+1, i-r+2.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T poly_coef(int row, int j) {
+    switch (row * 3 + j) {
+        case 0: return T(11.0 / 6.0);
+        case 1: return T(-7.0 / 6.0);
+        case 2: return T(1.0 / 3.0);
+        case 3: return T(1.0 / 3.0);
+        case 4: return T(5.0 / 6.0);
+        case 5: return T(-1.0 / 6.0);
+        case 6: return T(-1.0 / 6.0);
+        case 7: return T(5.0 / 6.0);
+        case 8: return T(1.0 / 3.0);
+        case 9: return T(1.0 / 3.0);
+        case 10: return T(-7.0 / 6.0);
+        default: return T(11.0 / 6.0);
+    }
+}
+
+// coefficient of eta: multiquadric (Table k3, right) or Gaussian (Sec. 3.3 recipe, k = 3)
+template <typename T>
+__device__ __forceinline__ T pert_coef(int rbf, int row, int j) {
+    if (rbf == NPW_RBF_GA_) {
+        switch (row * 3 + j) {
+            case 0: return T(-3.0);
+            case 1: return T(3.0);
+            case 2: return T(0.0);
+            case 3: return T(2.0 / 3.0);
+            case 4: return T(-1.0 / 3.0);
+            case 5: return T(-1.0 / 3.0);
+            case 6: return T(-1.0 / 3.0);
+            case 7: return T(-1.0 / 3.0);
+            case 8: return T(2.0 / 3.0);
+            case 9: return T(0.0);
+            case 10: return T(3.0);
+            default: return T(-3.0);
+        }
+    }
+    switch (row * 3 + j) {
+        case 0: return T(-9.0 / 2.0);
+        case 1: return T(6.0);
+        case 2: return T(-3.0 / 2.0);
+        case 3: return T(5.0 / 6.0);
+        case 4: return T(-2.0 / 3.0);
+        case 5: return T(-1.0 / 6.0);
+        case 6: return T(-1.0 / 6.0);
+        case 7: return T(-2.0 / 3.0);
+        case 8: return T(5.0 / 6.0);
+        case 9: return T(-3.0 / 2.0);
+        case 10: return T(6.0);
+        default: return T(-9.0 / 2.0);
+    }
+}
+
+// linear weights for v^-_{i+1/2} (d_r, r = cells to the left) and mirrored for v^+_{i-1/2}
+template <typename T>
+__device__ __forceinline__ T lin_weight(int side, int r) {
+    if (side == 0) return r == 0 ? T(3.0 / 10.0) : (r == 1 ? T(3.0 / 5.0) : T(1.0 / 10.0));
+    return r == 0 ? T(1.0 / 10.0) : (r == 1 ? T(3.0 / 5.0) : T(3.0 / 10.0));
+}
+
+// ---------------------------------------------------------------------------------------
+// Shape parameter (Table k3): eta = (w0 - 3 w1 + 3 w2 - w3) / (w0 - 15 w1 + 15 w2 - w3 + eps_M)
+// with w = cells i-1..i+2 of face i+1/2.
+// ---------------------------------------------------------------------------------------
+template <typename D>
+__device__ __forceinline__ D eta_num(D w0, D w1, D w2, D w3) {
+    return w0 - D(3.0) * w1 + D(3.0) * w2 - w3;
+}
+template <typename D>
+__device__ __forceinline__ D eta_den(D w0, D w1, D w2, D w3) {
+    return w0 - D(15.0) * w1 + D(15.0) * w2 - w3;
+}
+
+// ---------------------------------------------------------------------------------------
+// Monotone switch (Sec. 4).
+// Variant 0: the cubic p with averages w0..w3 over the cells of the eta stencil, in
+// s = (x - x_{i+1/2})/dx on -2 < s < 2; 12 p'(s) = A s^2 + B s + C with
+//   A = 6 ((w3 - w0) + 3 (w1 - w2)),  B = 6 ((w0 - w1) + (w3 - w2)),
+//   C = (w0 - w3) + 15 (w2 - w1).
+// p is non-monotone iff 12 p' takes both signs on the open interval: min < 0 < max over
+// 12p'(-2) = 4A - 2B + C, 12p'(2) = 4A + 2B + C and, when the vertex -B/(2A) is strictly
+// inside (|B| < 4|A|), 12p'(vertex) = C - B^2/(4A).
+// Variant 1: the k = 2 ratio of eq. root_value on cells (w0, w1, w2) and on (w1, w2, w3).
+// ---------------------------------------------------------------------------------------
+template <typename D>
+__device__ __forceinline__ bool k2_ratio_fires(D a, D b, D c) {
+    D num = D(-2.0) * a + D(3.0) * b - c;
+    D den = -a + D(2.0) * b - c;
+    if (den == D(0.0)) return false;
+    D ratio = num / den;
+    return ratio > D(0.0) && ratio < D(3.0);
+}
+
+template <typename D>
+__device__ __forceinline__ bool switch_fires(D w0, D w1, D w2, D w3, int variant) {
+    if (variant == 1) {
+        bool f1 = k2_ratio_fires(w0, w1, w2);
+        bool f2 = k2_ratio_fires(w1, w2, w3);
+        return f1 || f2;
+    }
+    D A = D(6.0) * ((w3 - w0) + D(3.0) * (w1 - w2));
+    D B = D(6.0) * ((w0 - w1) + (w3 - w2));
+    D C = (w0 - w3) + D(15.0) * (w2 - w1);
+    D vm = D(4.0) * A - D(2.0) * B + C;
+    D vp = D(4.0) * A + D(2.0) * B + C;
+    D mn = vm < vp ? vm : vp;
+    D mx = vm < vp ? vp : vm;
+    if (A != D(0.0) && fabs(B) < D(4.0) * fabs(A)) {
+        D vv = C - B * B / (D(4.0) * A);
+        mn = vv < mn ? vv : mn;
+        mx = vv > mx ? vv : mx;
+    }
+    return mn < D(0.0) && mx > D(0.0);
+}
+
+// ---------------------------------------------------------------------------------------
+// ENO stencil choice from Newton divided differences (Sec. 2, Sec. 3.1): c0..c4 = cells
+// i-2..i+2; the left extension is taken only when strictly smaller.  Returns r.
+// ---------------------------------------------------------------------------------------
+template <typename D>
+__device__ __forceinline__ int eno_choice(D c0, D c1, D c2, D c3, D c4) {
+    D dl = fabs(c2 - c1);
+    D dr = fabs(c3 - c2);
+    if (dl < dr) {
+        D ddl = fabs(c0 - D(2.0) * c1 + c2);
+        D ddr = fabs(c1 - D(2.0) * c2 + c3);
+        return (ddl < ddr) ? 2 : 1;
+    }
+    D ddl = fabs(c1 - D(2.0) * c2 + c3);
+    D ddr = fabs(c2 - D(2.0) * c3 + c4);
+    return (ddl < ddr) ? 1 : 0;
+}
+
+// Jiang-Shu smoothness indicators (cited in Sec. 2): beta[r] of stencil i-r..i-r+2.
+template <typename D>
+__device__ __forceinline__ void beta_k3(D c0, D c1, D c2, D c3, D c4, D beta[3]) {
+    D a, b;
+    a = c2 - D(2.0) * c3 + c4;
+    b = D(3.0) * c2 - D(4.0) * c3 + c4;
+    beta[0] = D(13.0 / 12.0) * a * a + D(0.25) * b * b;
+    a = c1 - D(2.0) * c2 + c3;
+    b = c1 - c3;
+    beta[1] = D(13.0 / 12.0) * a * a + D(0.25) * b * b;
+    a = c0 - D(2.0) * c1 + c2;
+    b = c0 - D(4.0) * c1 + D(3.0) * c2;
+    beta[2] = D(13.0 / 12.0) * a * a + D(0.25) * b * b;
+}
+
+// ---------------------------------------------------------------------------------------
+// Value of cell i at its right face (side 0: v^-_{i+1/2}, rows r) or left face (side 1:
+// v^+_{i-1/2}, rows r - 1).  c[0..4] = cells i-2..i+2; eta is the face's shape parameter
+// (already rounded to R).  forced_r >= 0 replays a stencil choice.
+// ---------------------------------------------------------------------------------------
+template <typename R, typename D>
+__device__ __forceinline__ R cell_face_value(const R* c, int side, R eta, const MethodParams& mp, int* r_out) {
+    R cand[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int row = (side == 0) ? r : r - 1;
+        R s = R(0.0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            R coef = poly_coef<R>(row + 1, j) + pert_coef<R>(mp.rbf, row + 1, j) * eta;
+            s += coef * c[2 - r + j];
+        }
+        cand[r] = s;
+    }
+    if (mp.scheme == NPW_ENO_ || mp.scheme == NPW_RBF_ENO_) {
+        int r = eno_choice<D>(D(c[0]), D(c[1]), D(c[2]), D(c[3]), D(c[4]));
+        *r_out = r;
+        return r == 0 ? cand[0] : (r == 1 ? cand[1] : cand[2]);
+    }
+    *r_out = 0;
+    D beta[3];
+    beta_k3<D>(D(c[0]), D(c[1]), D(c[2]), D(c[3]), D(c[4]), beta);
+    R alpha[3];
+    R asum = R(0.0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        R den = R(D(mp.eps_weno) + beta[r]);
+        alpha[r] = lin_weight<R>(side, r) / (den * den);
+        asum += alpha[r];
+    }
+    R v = R(0.0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) v += (alpha[r] / asum) * cand[r];
+    return v;
+}
+
+// One field at one face.  w[0..5] = cells i-2..i+3 around face i+1/2.  Returns the flag
+// byte (bit0 switch, bits 2-3 / 4-5 ENO r of the left / right cell).
+template <typename R, typename D>
+__device__ __forceinline__ uint32_t face_field(const R* w, const MethodParams& mp, R* vm, R* vp) {
+    uint32_t fl = 0;
+    R eta = R(0.0);
+    if (mp.scheme == NPW_RBF_ENO_ || mp.scheme == NPW_RBF_WENO_) {
+        const D w1 = D(w[1]), w2 = D(w[2]), w3 = D(w[3]), w4 = D(w[4]);
+        bool fires = mp.monotone_switch ? switch_fires<D>(w1, w2, w3, w4, mp.switch_variant) : false;
+        if (fires) {
+            fl |= 1u;
+        } else {
+            D den = eta_den<D>(w1, w2, w3, w4) + D(mp.eps_M);
+            eta = R(eta_num<D>(w1, w2, w3, w4) / den);
+        }
+    }
+    int rl = 0, rr = 0;
+    *vm = cell_face_value<R, D>(w, 0, eta, mp, &rl);
+    *vp = cell_face_value<R, D>(w + 1, 1, eta, mp, &rr);
+    fl |= (uint32_t(rl & 3) << 2) | (uint32_t(rr & 3) << 4);
+    return fl;
+}
+
+// ---------------------------------------------------------------------------------------
+// Physical fluxes and wave speeds (Sec. 5.2 examples).  dir 0 = x, 1 = y.
+// ---------------------------------------------------------------------------------------
+template <typename R, int KIND>
+__device__ __forceinline__ void phys_flux(const R* U, const MethodParams& mp, int dir, R* F) {
+    if (KIND == NPW_FLUX_ADVECTION_) {
+        F[0] = R(dir == 0 ? mp.adv_speed : mp.adv_speed_y) * U[0];
+    } else if (KIND == NPW_FLUX_BURGERS_) {
+        F[0] = R(0.5) * U[0] * U[0];
+    } else if (KIND == NPW_FLUX_EULER1D_) {
+        const R g = R(mp.gamma);
+        R rho = U[0], u = U[1] / rho, E = U[2];
+        R P = (g - R(1.0)) * (E - R(0.5) * rho * u * u);
+        F[0] = rho * u;
+        F[1] = rho * u * u + P;
+        F[2] = (E + P) * u;
+    } else {
+        const R g = R(mp.gamma);
+        R rho = U[0], u = U[1] / rho, v = U[2] / rho, E = U[3];
+        R P = (g - R(1.0)) * (E - R(0.5) * rho * (u * u + v * v));
+        R un = (dir == 0) ? u : v;
+        F[0] = rho * un;
+        F[1] = U[1] * un + ((dir == 0) ? P : R(0.0));
+        F[2] = U[2] * un + ((dir == 0) ? R(0.0) : P);
+        F[3] = (E + P) * un;
+    }
+}
+
+template <typename R, int KIND>
+__device__ __forceinline__ R wave_speed(const R* U, const MethodParams& mp, int dir) {
+    if (KIND == NPW_FLUX_ADVECTION_) return fabs(R(dir == 0 ? mp.adv_speed : mp.adv_speed_y));
+    if (KIND == NPW_FLUX_BURGERS_) return fabs(U[0]);
+    const R g = R(mp.gamma);
+    if (KIND == NPW_FLUX_EULER1D_) {
+        R rho = U[0], u = U[1] / rho;
+        R P = (g - R(1.0)) * (U[2] - R(0.5) * rho * u * u);
+        return fabs(u) + sqrt(g * P / rho);
+    }
+    R rho = U[0], u = U[1] / rho, v = U[2] / rho;
+    R P = (g - R(1.0)) * (U[3] - R(0.5) * rho * (u * u + v * v));
+    return fabs(dir == 0 ? u : v) + sqrt(g * P / rho);
+}
+
+template <int KIND>
+__host__ __device__ constexpr int kind_m() {
+    return KIND == NPW_FLUX_EULER1D_ ? 3 : (KIND == NPW_FLUX_EULER2D_ ? 4 : 1);
+}
+
+// Lax-Friedrichs flux of one face, all M fields: h = 0.5 (f(a) + f(b) - alpha (b - a)).
+template <typename R, int KIND, int M>
+__device__ __forceinline__ void lf_flux(const R* a, const R* b, R alpha, const MethodParams& mp, int dir, R* h) {
+    R fa[M], fb[M];
+    phys_flux<R, KIND>(a, mp, dir, fa);
+    phys_flux<R, KIND>(b, mp, dir, fb);
+#pragma unroll
+    for (int k = 0; k < M; ++k) h[k] = R(0.5) * (fa[k] + fb[k] - alpha * (b[k] - a[k]));
+}
+
+// ---------------------------------------------------------------------------------------
+// Characteristic variant (1D Euler): Roe average of the two cells at the face, right
+// eigenvectors R (columns) of dF/dU and their inverse in closed form,
+//   L = [ (b2 + u/c)/2, -(b1 u + 1/c)/2, b1/2 ;  1 - b2, b1 u, -b1 ;  (b2 - u/c)/2, -(b1 u - 1/c)/2, b1/2 ]
+// with b1 = (gamma - 1)/c^2, b2 = b1 u^2 / 2.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ bool euler_eig(const R* UL, const R* UR, R gamma, R Rm[3][3], R Lm[3][3]) {
+    R rl = UL[0], rr = UR[0];
+    R ul = UL[1] / rl, ur = UR[1] / rr;
+    R pl = (gamma - R(1.0)) * (UL[2] - R(0.5) * rl * ul * ul);
+    R pr = (gamma - R(1.0)) * (UR[2] - R(0.5) * rr * ur * ur);
+    R hl = (UL[2] + pl) / rl, hr = (UR[2] + pr) / rr;
+    R sl = sqrt(rl), sr = sqrt(rr);
+    R u = (sl * ul + sr * ur) / (sl + sr);
+    R h = (sl * hl + sr * hr) / (sl + sr);
+    R c2 = (gamma - R(1.0)) * (h - R(0.5) * u * u);
+    if (!(c2 > R(0.0))) return false;
+    R c = sqrt(c2);
+    Rm[0][0] = R(1.0);
+    Rm[0][1] = R(1.0);
+    Rm[0][2] = R(1.0);
+    Rm[1][0] = u - c;
+    Rm[1][1] = u;
+    Rm[1][2] = u + c;
+    Rm[2][0] = h - u * c;
+    Rm[2][1] = R(0.5) * u * u;
+    Rm[2][2] = h + u * c;
+    R b1 = (gamma - R(1.0)) / c2;
+    R b2 = R(0.5) * b1 * u * u;
+    R uc = u / c, ic = R(1.0) / c;
+    Lm[0][0] = R(0.5) * (b2 + uc);
+    Lm[0][1] = R(-0.5) * (b1 * u + ic);
+    Lm[0][2] = R(0.5) * b1;
+    Lm[1][0] = R(1.0) - b2;
+    Lm[1][1] = b1 * u;
+    Lm[1][2] = -b1;
+    Lm[2][0] = R(0.5) * (b2 - uc);
+    Lm[2][1] = R(-0.5) * (b1 * u - ic);
+    Lm[2][2] = R(0.5) * b1;
+    return true;
+}
+
+// All M fields at one face from the 6 x M stencil W[j*M + k] (cells i-2..i+3).  For the
+// characteristic variant the fields are projected by L, reconstructed, and mapped back by R.
+template <typename R, typename D, int KIND, int M, bool CHAR>
+__device__ __forceinline__ bool face_all(const R* S, const MethodParams& mp, R* vm, R* vp, uint32_t* flags) {
+    if (CHAR) {
+        R Rm[3][3], Lm[3][3];
+        if (!euler_eig<R>(S + 2 * M, S + 3 * M, R(mp.gamma), Rm, Lm)) return false;
+        R wm[3], wp[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R line[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                R s = R(0.0);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) s += Lm[a][k] * S[j * M + k];
+                line[j] = s;
+            }
+            flags[a] = face_field<R, D>(line, mp, &wm[a], &wp[a]);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            R sm = R(0.0), sp = R(0.0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                sm += Rm[k][a] * wm[a];
+                sp += Rm[k][a] * wp[a];
+            }
+            vm[k] = sm;
+            vp[k] = sp;
+        }
+        return true;
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        R line[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) line[j] = S[j * M + k];
+        flags[k] = face_field<R, D>(line, mp, &vm[k], &vp[k]);
+    }
+    return true;
+}
+
+}  // namespace npw

@@ -1,0 +1,136 @@
+// npw_internal.h -- types shared by the kernels and the host runtime of libnpweno.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "npweno.h"
+
+namespace npw {
+
+constexpr int NPW_ENO_ = NPW_ENO;
+constexpr int NPW_WENO_JS_ = NPW_WENO_JS;
+constexpr int NPW_RBF_ENO_ = NPW_RBF_ENO;
+constexpr int NPW_RBF_WENO_ = NPW_RBF_WENO;
+constexpr int NPW_RBF_MQ_ = NPW_RBF_MQ;
+constexpr int NPW_RBF_GA_ = NPW_RBF_GA;
+constexpr int NPW_FLUX_ADVECTION_ = NPW_FLUX_ADVECTION;
+constexpr int NPW_FLUX_BURGERS_ = NPW_FLUX_BURGERS;
+constexpr int NPW_FLUX_EULER1D_ = NPW_FLUX_EULER1D;
+constexpr int NPW_FLUX_EULER2D_ = NPW_FLUX_EULER2D;
+
+// Method parameters as the kernels see them (by value in the launch arguments).
+struct MethodParams {
+    int scheme;
+    int rbf;
+    int monotone_switch;
+    int switch_variant;
+    int characteristic;
+    int pad_;
+    double eps_M;
+    double eps_weno;
+    double gamma;
+    double adv_speed;
+    double adv_speed_y;
+    double inflow[4];
+};
+
+// One 1D problem (device copy of npw_instance plus its tile range).
+struct InstDev {
+    int64_t off;  // element offset of the [m][n] block in the arena
+    int64_t n;
+    double dx;
+    double t_end;
+    double cfl;
+    int32_t bc;
+    int32_t ntiles;
+};
+
+// Per-instance time control, owned by the device.  Written only by the last CTA of the
+// instance in stage 3 (or by the init kernels); read by every CTA of the next step.
+struct Ctl {
+    double t;
+    double dt;
+    double alpha;       // Lax-Friedrichs alpha of the current step (max |f'(u^n)|)
+    double alpha_max;   // largest alpha seen
+    unsigned long long alpha_next_bits;  // running max for the next step (bits of a double >= 0)
+    unsigned long long alpha_y_next_bits;
+    double alpha_y;
+    int64_t steps;
+    int32_t done;
+    int32_t status;
+    int32_t last;
+    uint32_t tiles_done;
+};
+
+// Work item: (instance, first cell of the tile).
+struct Tile {
+    int32_t inst;
+    int32_t start;
+};
+
+// 2D problem: one square/rectangle, tiles of TX x TY cells.
+struct Inst2D {
+    int64_t off;
+    int64_t nx, ny;
+    double dx, dy;
+    double t_end, cfl;
+    int32_t bc;
+    int32_t tiles_x, tiles_y;
+    int32_t pad_;
+};
+
+struct Stage1DArgs {
+    const void* uin;   // stage input u^(k)
+    const void* un;    // u^n (stages 2, 3)
+    void* uout;        // stage output
+    const InstDev* inst;
+    Ctl* ctl;
+    const Tile* tiles;
+    int32_t ntiles;
+    int32_t stage;     // 0, 1, 2
+    int32_t advance;   // stage 2 finalises the step (time control on the device)
+    int32_t tile;      // cells per tile
+    MethodParams mp;
+};
+
+struct Stage2DArgs {
+    const void* uin;
+    const void* un;
+    void* uout;
+    const Inst2D* inst;
+    Ctl* ctl;
+    int32_t stage;
+    int32_t advance;
+    MethodParams mp;
+};
+
+// ---- launchers (one definition per precision translation unit) ---------------------------
+template <typename R>
+cudaError_t launch_reconstruct(const R* u, int64_t n, int m, int bc, const MethodParams& mp, R* vm, R* vp,
+                               uint8_t* flags, cudaStream_t s);
+template <typename R>
+cudaError_t launch_flux(const R* vm, const R* vp, int64_t nf, int m, int kind, double alpha,
+                        const MethodParams& mp, R* h, cudaStream_t s);
+template <typename R>
+cudaError_t launch_alpha_init(const void* u, const InstDev* inst, Ctl* ctl, const Tile* tiles, int ntiles,
+                              int tile, int m, int kind, const MethodParams& mp, cudaStream_t s);
+template <typename R>
+cudaError_t launch_stage1d(const Stage1DArgs& a, int m, int kind, cudaStream_t s);
+template <typename R>
+cudaError_t launch_alpha_init_2d(const void* u, const Inst2D* inst, int tiles, Ctl* ctl, int kind,
+                                 const MethodParams& mp, cudaStream_t s);
+template <typename R>
+cudaError_t launch_stage2d(const Stage2DArgs& a, int tiles, int kind, cudaStream_t s);
+
+// precision-independent helpers (npw_api.cu)
+cudaError_t launch_ctl_start(Ctl* ctl, const InstDev* inst, int count, int mode, double dt, cudaStream_t s);
+cudaError_t launch_ctl_start_2d(Ctl* ctl, const Inst2D* inst, int mode, double dt, cudaStream_t s);
+cudaError_t launch_count_active(const Ctl* ctl, int count, int* active, cudaStream_t s);
+
+constexpr int TILE_1D = 1024;  // cells per CTA tile in the 1D stage kernel
+constexpr int THREADS_1D = 256;
+constexpr int TX_2D = 32;      // 2D tile
+constexpr int TY_2D = 8;
+
+}  // namespace npw

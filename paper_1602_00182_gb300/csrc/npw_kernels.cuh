@@ -1,0 +1,579 @@
+// npw_kernels.cuh -- CUDA kernels of libnpweno, templated on the state type.  Included by one
+// translation unit per precision (npw_fp64.cu, npw_fp32.cu), which instantiate the launchers.
+//
+// The hot kernel is stage1d_kernel: one CTA per (instance, tile) work item runs one whole
+// TVD-RK3 stage of its tile -- halo load with the boundary mapping, the per-face shape
+// parameter / switch / candidates / weights (Sec. 2-4), the Lax-Friedrichs flux (Sec. 5.1),
+// the flux difference of eq. PDE1 and the Shu-Osher stage combination -- and, in stage 3,
+// the block reduction of the next Lax-Friedrichs alpha and the per-instance time control.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "npw_device.cuh"
+#include "npw_internal.h"
+
+namespace npw {
+
+// value of cell k (any integer) of a line of n cells with stride `stride`; BC by index map
+template <typename R>
+__device__ __forceinline__ R line_get(const R* u, int64_t n, int64_t stride, int64_t k, int bc, double inflow) {
+    if (bc == NPW_BC_PERIODIC) {
+        int64_t kk = k % n;
+        if (kk < 0) kk += n;
+        return u[kk * stride];
+    }
+    if (k < 0) return (bc == NPW_BC_INFLOW) ? R(inflow) : u[0];
+    if (k >= n) return u[(n - 1) * stride];
+    return u[k * stride];
+}
+
+template <typename R>
+__device__ __forceinline__ bool finite_(R x) {
+    return x - x == R(0.0);
+}
+
+// max over the block of a non-negative speed; any non-finite input makes the result NaN
+__device__ __forceinline__ double block_max_nan(double v, bool bad, double* red, int* redbad) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    unsigned b = __ballot_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        red[warp] = v;
+        redbad[warp] = b != 0u;
+    }
+    __syncthreads();
+    double out = 0.0;
+    if (threadIdx.x == 0) {
+        int anybad = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            out = red[w] > out ? red[w] : out;
+            anybad |= redbad[w];
+        }
+        if (anybad) out = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    return out;  // valid in thread 0
+}
+
+// ---------------------------------------------------------------------------------------
+// time control, executed by one thread for one instance
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void next_dt(Ctl* c, double rate, double t_end, double cfl) {
+    double dt = (rate > 0.0) ? cfl / rate : t_end - c->t;
+    int last = 0;
+    if (c->t + dt * (1.0 + 1e-10) >= t_end) {
+        dt = t_end - c->t;
+        last = 1;
+    }
+    c->dt = dt;
+    c->last = last;
+}
+
+__device__ __forceinline__ bool take_alpha(Ctl* c, double* ax, double* ay, bool two_d) {
+    *ax = __longlong_as_double((long long)c->alpha_next_bits);
+    *ay = two_d ? __longlong_as_double((long long)c->alpha_y_next_bits) : 0.0;
+    c->alpha_next_bits = 0ull;
+    c->alpha_y_next_bits = 0ull;
+    bool ok = (*ax - *ax == 0.0) && (*ay - *ay == 0.0);
+    if (!ok) {
+        c->status = NPW_ENONFINITE;
+        c->done = 1;
+        return false;
+    }
+    c->alpha = *ax;
+    c->alpha_y = *ay;
+    double m = *ax > *ay ? *ax : *ay;
+    c->alpha_max = m > c->alpha_max ? m : c->alpha_max;
+    return true;
+}
+
+__device__ __forceinline__ void finalize_1d(Ctl* c, const InstDev& in) {
+    c->tiles_done = 0u;
+    c->steps += 1;
+    c->t = c->last ? in.t_end : c->t + c->dt;
+    double ax, ay;
+    if (!take_alpha(c, &ax, &ay, false)) return;
+    if (c->last) {
+        c->done = 1;
+        return;
+    }
+    next_dt(c, ax / in.dx, in.t_end, in.cfl);
+}
+
+__device__ __forceinline__ void finalize_2d(Ctl* c, const Inst2D& in) {
+    c->tiles_done = 0u;
+    c->steps += 1;
+    c->t = c->last ? in.t_end : c->t + c->dt;
+    double ax, ay;
+    if (!take_alpha(c, &ax, &ay, true)) return;
+    if (c->last) {
+        c->done = 1;
+        return;
+    }
+    next_dt(c, ax / in.dx + ay / in.dy, in.t_end, in.cfl);
+}
+
+// ---------------------------------------------------------------------------------------
+// npweno_reconstruct: one thread per face, all fields
+// ---------------------------------------------------------------------------------------
+template <typename R, typename D, int M, bool CHAR>
+__global__ void reconstruct_kernel(const R* __restrict__ u, int64_t n, int bc, MethodParams mp, R* __restrict__ vm,
+                                   R* __restrict__ vp, uint8_t* __restrict__ flags) {
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f > n) return;
+    R S[6 * M];
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+#pragma unroll
+        for (int k = 0; k < M; ++k) S[j * M + k] = line_get<R>(u + k * n, n, 1, f - 3 + j, bc, mp.inflow[k]);
+    R a[M], b[M];
+    uint32_t fl[M];
+    bool ok = face_all<R, D, NPW_FLUX_EULER1D_, M, CHAR>(S, mp, a, b, fl);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        R nan = R(__longlong_as_double(0x7ff8000000000000ll));
+        vm[k * (n + 1) + f] = ok ? a[k] : nan;
+        vp[k * (n + 1) + f] = ok ? b[k] : nan;
+        if (flags) flags[k * (n + 1) + f] = (uint8_t)fl[k];
+    }
+}
+
+// npweno_flux: one thread per face
+template <typename R, int KIND>
+__global__ void flux_kernel(const R* __restrict__ vm, const R* __restrict__ vp, int64_t nf, R alpha, MethodParams mp,
+                            R* __restrict__ h) {
+    constexpr int M = kind_m<KIND>();
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    R a[M], b[M], o[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        a[k] = vm[k * nf + f];
+        b[k] = vp[k * nf + f];
+    }
+    lf_flux<R, KIND, M>(a, b, alpha, mp, 0, o);
+#pragma unroll
+    for (int k = 0; k < M; ++k) h[k * nf + f] = o[k];
+}
+
+// alpha^0 = max |f'(u^0)| per instance: every tile adds its maximum by atomicMax on the
+// bits of the non-negative double (the bit order of non-negative doubles is their order).
+template <typename R, int KIND>
+__global__ void __launch_bounds__(THREADS_1D) alpha_init_kernel(const R* __restrict__ u, const InstDev* __restrict__ inst,
+                                                                 Ctl* ctl, const Tile* __restrict__ tiles, int tile,
+                                                                 MethodParams mp) {
+    constexpr int M = kind_m<KIND>();
+    __shared__ double red[32];
+    __shared__ int redbad[32];
+    const Tile td = tiles[blockIdx.x];
+    const InstDev in = inst[td.inst];
+    const int64_t n = in.n;
+    const int c0 = td.start;
+    const int cnt = (int)((n - c0) < tile ? (n - c0) : tile);
+    const R* base = u + in.off;
+    double vmax = 0.0;
+    bool bad = false;
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        R U[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            U[k] = base[k * n + c0 + q];
+            bad |= !finite_(U[k]);
+        }
+        double s = (double)wave_speed<R, KIND>(U, mp, 0);
+        bad |= !finite_(s);
+        vmax = s > vmax ? s : vmax;
+    }
+    double b = block_max_nan(vmax, bad, red, redbad);
+    if (threadIdx.x == 0) atomicMax(&ctl[td.inst].alpha_next_bits, (unsigned long long)__double_as_longlong(b));
+}
+
+// ---------------------------------------------------------------------------------------
+// The fused stage kernel (1D).  Shared memory: su[(tile + 6) * M] cell-major stage input
+// with 3 ghost cells per side, sh[(tile + 1) * M] face fluxes.
+// ---------------------------------------------------------------------------------------
+template <typename R, typename D, int KIND, bool CHAR>
+__global__ void __launch_bounds__(THREADS_1D) stage1d_kernel(Stage1DArgs a) {
+    constexpr int M = kind_m<KIND>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    __shared__ int redbad[32];
+    R* su = reinterpret_cast<R*>(smem_raw);
+    R* sh = su + (a.tile + 6) * M;
+
+    const Tile td = a.tiles[blockIdx.x];
+    const InstDev in = a.inst[td.inst];
+    Ctl* ctl = a.ctl + td.inst;
+    if (*(volatile int32_t*)&ctl->done) return;  // uniform over the CTA
+    const int64_t n = in.n;
+    const int c0 = td.start;
+    const int cnt = (int)((n - c0) < a.tile ? (n - c0) : a.tile);
+    const R* uin = reinterpret_cast<const R*>(a.uin) + in.off;
+    const int span = cnt + 6;
+
+    // halo load: cell c0 - 3 + j, field k; consecutive threads read consecutive cells
+    for (int idx = threadIdx.x; idx < span * M; idx += blockDim.x) {
+        const int k = idx / span;
+        const int j = idx - k * span;
+        su[j * M + k] = line_get<R>(uin + k * n, n, 1, (int64_t)c0 - 3 + j, in.bc, a.mp.inflow[k]);
+    }
+    const double dt = *(volatile double*)&ctl->dt;
+    const R alpha = R(*(volatile double*)&ctl->alpha);
+    __syncthreads();
+
+    // faces c0 - 1/2 .. c0 + cnt - 1/2 (local q = 0..cnt): stencil su[q .. q+5]
+    for (int q = threadIdx.x; q <= cnt; q += blockDim.x) {
+        R vm[M], vp[M], h[M];
+        uint32_t fl[M];
+        bool ok = face_all<R, D, KIND, M, CHAR>(su + q * M, a.mp, vm, vp, fl);
+        lf_flux<R, KIND, M>(vm, vp, alpha, a.mp, 0, h);
+#pragma unroll
+        for (int k = 0; k < M; ++k) sh[q * M + k] = ok ? h[k] : R(__longlong_as_double(0x7ff8000000000000ll));
+    }
+    __syncthreads();
+
+    // cells: eq. PDE1 and the Shu-Osher combination
+    R* uout = reinterpret_cast<R*>(a.uout) + in.off;
+    const R* un = reinterpret_cast<const R*>(a.un) + in.off;
+    const R dtR = R(dt);
+    const R dxR = R(in.dx);
+    double vmax = 0.0;
+    bool bad = false;
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        R U[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const R L = -(sh[(q + 1) * M + k] - sh[q * M + k]) / dxR;
+            const R uk = su[(q + 3) * M + k];
+            R o;
+            if (a.stage == 0) {
+                o = uk + dtR * L;
+            } else if (a.stage == 1) {
+                o = R(0.75) * un[k * n + c0 + q] + R(0.25) * (uk + dtR * L);
+            } else {
+                o = R(1.0 / 3.0) * un[k * n + c0 + q] + R(2.0 / 3.0) * (uk + dtR * L);
+            }
+            uout[k * n + c0 + q] = o;
+            U[k] = o;
+            bad |= !finite_(o);
+        }
+        if (a.stage == 2) {
+            double s = (double)wave_speed<R, KIND>(U, a.mp, 0);
+            bad |= !finite_(s);
+            vmax = s > vmax ? s : vmax;
+        }
+    }
+    if (a.stage == 2 && a.advance) {
+        double b = block_max_nan(vmax, bad, red, redbad);
+        if (threadIdx.x == 0) {
+            atomicMax(&ctl->alpha_next_bits, (unsigned long long)__double_as_longlong(b));
+            __threadfence();
+            unsigned prev = atomicAdd(&ctl->tiles_done, 1u);
+            if (prev == (unsigned)in.ntiles - 1u) {
+                __threadfence();
+                finalize_1d(ctl, in);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// 2D dimension-by-dimension stage kernel (component-wise).  Tile TX x TY cells; shared
+// memory holds the (TX + 6) x (TY + 6) input block, the x-face fluxes (TX + 1) x TY and
+// the y-face fluxes TX x (TY + 1).
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R grid_get(const R* u, const Inst2D& in, int64_t i, int64_t j, double inflow) {
+    // rows (j) and columns (i) each use the instance boundary condition
+    int64_t nx = in.nx, ny = in.ny;
+    if (in.bc == NPW_BC_PERIODIC) {
+        i %= nx;
+        if (i < 0) i += nx;
+        j %= ny;
+        if (j < 0) j += ny;
+    } else {
+        if (in.bc == NPW_BC_INFLOW && (i < 0 || j < 0)) return R(inflow);
+        i = i < 0 ? 0 : (i >= nx ? nx - 1 : i);
+        j = j < 0 ? 0 : (j >= ny ? ny - 1 : j);
+    }
+    return u[j * nx + i];
+}
+
+template <typename R, typename D, int KIND>
+__global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
+    constexpr int M = kind_m<KIND>();
+    constexpr int BX = TX_2D + 6, BY = TY_2D + 6;
+    __shared__ R su[BY * BX * M];
+    __shared__ R hx[TY_2D * (TX_2D + 1) * M];
+    __shared__ R hy[(TY_2D + 1) * TX_2D * M];
+    __shared__ double red[32];
+    __shared__ int redbad[32];
+    __shared__ double red2[32];
+    __shared__ int redbad2[32];
+    const Inst2D in = *a.inst;
+    Ctl* ctl = a.ctl;
+    if (*(volatile int32_t*)&ctl->done) return;
+    const int tx0 = (blockIdx.x % in.tiles_x) * TX_2D;
+    const int ty0 = (blockIdx.x / in.tiles_x) * TY_2D;
+    const int64_t nx = in.nx, ny = in.ny, cells = nx * ny;
+    const R* uin = reinterpret_cast<const R*>(a.uin) + in.off;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < BX * BY * M; idx += blockDim.x) {
+        const int k = idx / (BX * BY);
+        const int rem = idx - k * BX * BY;
+        const int by = rem / BX, bx = rem - by * BX;
+        const bool corner = (bx < 3 || bx >= TX_2D + 3) && (by < 3 || by >= TY_2D + 3);
+        su[(by * BX + bx) * M + k] =
+            corner ? R(0.0) : grid_get<R>(uin + k * cells, in, (int64_t)tx0 - 3 + bx, (int64_t)ty0 - 3 + by, a.mp.inflow[k]);
+    }
+    const double dt = *(volatile double*)&ctl->dt;
+    const R ax = R(*(volatile double*)&ctl->alpha);
+    const R ay = R(*(volatile double*)&ctl->alpha_y);
+    __syncthreads();
+    // x faces: (qx, qy), qx = 0..TX, qy = 0..TY-1, stencil su[qy+3][qx .. qx+5]
+    for (int f = tid; f < (TX_2D + 1) * TY_2D; f += blockDim.x) {
+        const int qy = f / (TX_2D + 1), qx = f - qy * (TX_2D + 1);
+        R S[6 * M], vm[M], vp[M], h[M];
+        uint32_t fl[M];
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+#pragma unroll
+            for (int k = 0; k < M; ++k) S[j * M + k] = su[((qy + 3) * BX + qx + j) * M + k];
+        face_all<R, D, KIND, M, false>(S, a.mp, vm, vp, fl);
+        lf_flux<R, KIND, M>(vm, vp, ax, a.mp, 0, h);
+#pragma unroll
+        for (int k = 0; k < M; ++k) hx[(qy * (TX_2D + 1) + qx) * M + k] = h[k];
+    }
+    // y faces: (qx, qy), qx = 0..TX-1, qy = 0..TY, stencil su[qy .. qy+5][qx+3]
+    for (int f = tid; f < TX_2D * (TY_2D + 1); f += blockDim.x) {
+        const int qy = f / TX_2D, qx = f - qy * TX_2D;
+        R S[6 * M], vm[M], vp[M], h[M];
+        uint32_t fl[M];
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+#pragma unroll
+            for (int k = 0; k < M; ++k) S[j * M + k] = su[((qy + j) * BX + qx + 3) * M + k];
+        face_all<R, D, KIND, M, false>(S, a.mp, vm, vp, fl);
+        lf_flux<R, KIND, M>(vm, vp, ay, a.mp, 1, h);
+#pragma unroll
+        for (int k = 0; k < M; ++k) hy[(qy * TX_2D + qx) * M + k] = h[k];
+    }
+    __syncthreads();
+    R* uout = reinterpret_cast<R*>(a.uout) + in.off;
+    const R* un = reinterpret_cast<const R*>(a.un) + in.off;
+    const R dtR = R(dt), dxR = R(in.dx), dyR = R(in.dy);
+    double vmx = 0.0, vmy = 0.0;
+    bool bad = false;
+    {
+        const int qy = tid / TX_2D, qx = tid - qy * TX_2D;
+        const int64_t gi = tx0 + qx, gj = ty0 + qy;
+        if (gi < nx && gj < ny) {
+            R U[M];
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                R L = -((hx[(qy * (TX_2D + 1) + qx + 1) * M + k] - hx[(qy * (TX_2D + 1) + qx) * M + k]) / dxR);
+                L = L - (hy[((qy + 1) * TX_2D + qx) * M + k] - hy[(qy * TX_2D + qx) * M + k]) / dyR;
+                const R uk = su[((qy + 3) * BX + qx + 3) * M + k];
+                const int64_t gidx = k * cells + gj * nx + gi;
+                R o;
+                if (a.stage == 0) {
+                    o = uk + dtR * L;
+                } else if (a.stage == 1) {
+                    o = R(0.75) * un[gidx] + R(0.25) * (uk + dtR * L);
+                } else {
+                    o = R(1.0 / 3.0) * un[gidx] + R(2.0 / 3.0) * (uk + dtR * L);
+                }
+                uout[gidx] = o;
+                U[k] = o;
+                bad |= !finite_(o);
+            }
+            if (a.stage == 2) {
+                double sx = (double)wave_speed<R, KIND>(U, a.mp, 0);
+                double sy = (double)wave_speed<R, KIND>(U, a.mp, 1);
+                bad |= !finite_(sx) || !finite_(sy);
+                vmx = sx;
+                vmy = sy;
+            }
+        }
+    }
+    if (a.stage == 2 && a.advance) {
+        double bx = block_max_nan(vmx, bad, red, redbad);
+        double by = block_max_nan(vmy, bad, red2, redbad2);
+        if (tid == 0) {
+            atomicMax(&ctl->alpha_next_bits, (unsigned long long)__double_as_longlong(bx));
+            atomicMax(&ctl->alpha_y_next_bits, (unsigned long long)__double_as_longlong(by));
+            __threadfence();
+            unsigned prev = atomicAdd(&ctl->tiles_done, 1u);
+            if (prev == (unsigned)(in.tiles_x * in.tiles_y) - 1u) {
+                __threadfence();
+                finalize_2d(ctl, in);
+            }
+        }
+    }
+}
+
+template <typename R, int KIND>
+__global__ void __launch_bounds__(TX_2D * TY_2D) alpha_init_2d_kernel(const R* __restrict__ u, const Inst2D* inst,
+                                                                       Ctl* ctl, MethodParams mp) {
+    constexpr int M = kind_m<KIND>();
+    __shared__ double red[32];
+    __shared__ int redbad[32];
+    __shared__ double red2[32];
+    __shared__ int redbad2[32];
+    const Inst2D in = *inst;
+    const int tx0 = (blockIdx.x % in.tiles_x) * TX_2D;
+    const int ty0 = (blockIdx.x / in.tiles_x) * TY_2D;
+    const int64_t cells = in.nx * in.ny;
+    const int qy = threadIdx.x / TX_2D, qx = threadIdx.x - qy * TX_2D;
+    const int64_t gi = tx0 + qx, gj = ty0 + qy;
+    double sx = 0.0, sy = 0.0;
+    bool bad = false;
+    if (gi < in.nx && gj < in.ny) {
+        R U[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            U[k] = u[in.off + k * cells + gj * in.nx + gi];
+            bad |= !finite_(U[k]);
+        }
+        sx = (double)wave_speed<R, KIND>(U, mp, 0);
+        sy = (double)wave_speed<R, KIND>(U, mp, 1);
+        bad |= !finite_(sx) || !finite_(sy);
+    }
+    double bx = block_max_nan(sx, bad, red, redbad);
+    double by = block_max_nan(sy, bad, red2, redbad2);
+    if (threadIdx.x == 0) {
+        atomicMax(&ctl->alpha_next_bits, (unsigned long long)__double_as_longlong(bx));
+        atomicMax(&ctl->alpha_y_next_bits, (unsigned long long)__double_as_longlong(by));
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+template <typename R, typename D>
+struct Launchers {
+    static cudaError_t reconstruct(const R* u, int64_t n, int m, int bc, const MethodParams& mp, R* vm, R* vp,
+                                   uint8_t* flags, cudaStream_t s) {
+        const int threads = 128;
+        const unsigned blocks = (unsigned)((n + 1 + threads - 1) / threads);
+        if (m == 1)
+            reconstruct_kernel<R, D, 1, false><<<blocks, threads, 0, s>>>(u, n, bc, mp, vm, vp, flags);
+        else if (m == 3 && mp.characteristic)
+            reconstruct_kernel<R, D, 3, true><<<blocks, threads, 0, s>>>(u, n, bc, mp, vm, vp, flags);
+        else if (m == 3)
+            reconstruct_kernel<R, D, 3, false><<<blocks, threads, 0, s>>>(u, n, bc, mp, vm, vp, flags);
+        else if (m == 4)
+            reconstruct_kernel<R, D, 4, false><<<blocks, threads, 0, s>>>(u, n, bc, mp, vm, vp, flags);
+        else
+            return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
+
+    static cudaError_t flux(const R* vm, const R* vp, int64_t nf, int kind, double alpha, const MethodParams& mp, R* h,
+                            cudaStream_t s) {
+        const int threads = 128;
+        const unsigned blocks = (unsigned)((nf + threads - 1) / threads);
+        switch (kind) {
+            case NPW_FLUX_ADVECTION:
+                flux_kernel<R, NPW_FLUX_ADVECTION_><<<blocks, threads, 0, s>>>(vm, vp, nf, R(alpha), mp, h);
+                break;
+            case NPW_FLUX_BURGERS:
+                flux_kernel<R, NPW_FLUX_BURGERS_><<<blocks, threads, 0, s>>>(vm, vp, nf, R(alpha), mp, h);
+                break;
+            case NPW_FLUX_EULER1D:
+                flux_kernel<R, NPW_FLUX_EULER1D_><<<blocks, threads, 0, s>>>(vm, vp, nf, R(alpha), mp, h);
+                break;
+            default:
+                return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+
+    static cudaError_t alpha_init(const void* u, const InstDev* inst, Ctl* ctl, const Tile* tiles, int ntiles, int tile,
+                                  int kind, const MethodParams& mp, cudaStream_t s) {
+        const R* uu = reinterpret_cast<const R*>(u);
+        switch (kind) {
+            case NPW_FLUX_ADVECTION:
+                alpha_init_kernel<R, NPW_FLUX_ADVECTION_><<<ntiles, THREADS_1D, 0, s>>>(uu, inst, ctl, tiles, tile, mp);
+                break;
+            case NPW_FLUX_BURGERS:
+                alpha_init_kernel<R, NPW_FLUX_BURGERS_><<<ntiles, THREADS_1D, 0, s>>>(uu, inst, ctl, tiles, tile, mp);
+                break;
+            case NPW_FLUX_EULER1D:
+                alpha_init_kernel<R, NPW_FLUX_EULER1D_><<<ntiles, THREADS_1D, 0, s>>>(uu, inst, ctl, tiles, tile, mp);
+                break;
+            default:
+                return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+
+    template <int KIND, bool CHAR>
+    static cudaError_t stage_k(const Stage1DArgs& a, cudaStream_t s) {
+        constexpr int M = kind_m<KIND>();
+        const size_t smem = (size_t)((a.tile + 6) + (a.tile + 1)) * M * sizeof(R);
+        auto kern = stage1d_kernel<R, D, KIND, CHAR>;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        kern<<<a.ntiles, THREADS_1D, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t stage1d(const Stage1DArgs& a, int kind, cudaStream_t s) {
+        switch (kind) {
+            case NPW_FLUX_ADVECTION: return stage_k<NPW_FLUX_ADVECTION_, false>(a, s);
+            case NPW_FLUX_BURGERS: return stage_k<NPW_FLUX_BURGERS_, false>(a, s);
+            case NPW_FLUX_EULER1D:
+                return a.mp.characteristic ? stage_k<NPW_FLUX_EULER1D_, true>(a, s)
+                                           : stage_k<NPW_FLUX_EULER1D_, false>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+
+    static cudaError_t alpha_init_2d(const void* u, const Inst2D* inst, int tiles, Ctl* ctl, int kind,
+                                     const MethodParams& mp, cudaStream_t s) {
+        const R* uu = reinterpret_cast<const R*>(u);
+        switch (kind) {
+            case NPW_FLUX_ADVECTION:
+                alpha_init_2d_kernel<R, NPW_FLUX_ADVECTION_><<<tiles, TX_2D * TY_2D, 0, s>>>(uu, inst, ctl, mp);
+                break;
+            case NPW_FLUX_BURGERS:
+                alpha_init_2d_kernel<R, NPW_FLUX_BURGERS_><<<tiles, TX_2D * TY_2D, 0, s>>>(uu, inst, ctl, mp);
+                break;
+            case NPW_FLUX_EULER2D:
+                alpha_init_2d_kernel<R, NPW_FLUX_EULER2D_><<<tiles, TX_2D * TY_2D, 0, s>>>(uu, inst, ctl, mp);
+                break;
+            default:
+                return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+
+    static cudaError_t stage2d(const Stage2DArgs& a, int tiles, int kind, cudaStream_t s) {
+        switch (kind) {
+            case NPW_FLUX_ADVECTION:
+                stage2d_kernel<R, D, NPW_FLUX_ADVECTION_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                break;
+            case NPW_FLUX_BURGERS:
+                stage2d_kernel<R, D, NPW_FLUX_BURGERS_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                break;
+            case NPW_FLUX_EULER2D:
+                stage2d_kernel<R, D, NPW_FLUX_EULER2D_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                break;
+            default:
+                return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace npw

@@ -1,0 +1,295 @@
+"""Thin Python binding of libnpweno (include/npweno.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module passes device pointers of
+torch tensors, sizes, the parameter struct and the current CUDA stream.  There is no CPU
+fallback: if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnpweno.so")
+
+# enums of npweno.h
+NPW_OK, NPW_EINVAL, NPW_ENOMEM, NPW_ECUDA, NPW_ETIMEOUT, NPW_ENONFINITE, NPW_EBUSY = 0, -1, -2, -3, -4, -5, -6
+NPW_FLUX_ADVECTION, NPW_FLUX_BURGERS, NPW_FLUX_EULER1D, NPW_FLUX_EULER2D = 0, 1, 2, 3
+NPW_BC_PERIODIC, NPW_BC_TRANSMISSIVE, NPW_BC_INFLOW = 0, 1, 2
+NPW_ENO, NPW_WENO_JS, NPW_RBF_ENO, NPW_RBF_WENO = 0, 1, 2, 3
+NPW_RBF_MQ, NPW_RBF_GA = 0, 1
+NPW_FP64, NPW_FP32_MIXED = 0, 1
+
+
+class npw_params(C.Structure):
+    _fields_ = [("k", C.c_int32), ("scheme", C.c_int32), ("rbf", C.c_int32), ("monotone_switch", C.c_int32),
+                ("switch_variant", C.c_int32), ("characteristic", C.c_int32), ("precision", C.c_int32),
+                ("pad_", C.c_int32), ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
+                ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4)]
+
+
+class npw_solve_stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("t", C.c_double), ("alpha_max", C.c_double), ("status", C.c_int32),
+                ("pad_", C.c_int32)]
+
+
+class npw_instance(C.Structure):
+    _fields_ = [("offset", C.c_int64), ("n", C.c_int64), ("dx", C.c_double), ("t_end", C.c_double),
+                ("cfl", C.c_double), ("bc", C.c_int32), ("pad_", C.c_int32)]
+
+
+class NpwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"npweno status {status}: {msg}")
+        self.status = status
+
+
+@dataclass
+class Params:
+    """Python mirror of npw_params (defaults = npw_default_params)."""
+    scheme: int = NPW_RBF_WENO
+    rbf: int = NPW_RBF_MQ
+    monotone_switch: int = 1
+    switch_variant: int = 0
+    characteristic: int = 0
+    precision: int = NPW_FP64
+    eps_M: float = 1e-12
+    eps_weno: float = 1e-6
+    gamma: float = 1.4
+    adv_speed: float = 1.0
+    adv_speed_y: float = 1.0
+    inflow: Sequence[float] = (0.0, 0.0, 0.0, 0.0)
+    k: int = 3
+
+    def c(self) -> npw_params:
+        p = npw_params()
+        for f in ("k", "scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "precision"):
+            setattr(p, f, int(getattr(self, f)))
+        for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y"):
+            setattr(p, f, float(getattr(self, f)))
+        for i in range(4):
+            p.inflow[i] = float(self.inflow[i]) if i < len(self.inflow) else 0.0
+        return p
+
+
+_lib = None
+
+
+def load():
+    """Load libnpweno.so (built by paper_1602_00182_gb300.build).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1602_00182_gb300.build` "
+                           "(there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, d, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_size_t
+    P = C.POINTER
+    lib.npw_default_params.argtypes = [P(npw_params)]
+    lib.npw_default_params.restype = None
+    lib.npw_last_error.restype = C.c_char_p
+    lib.npw_version.restype = i32
+    lib.npweno_reconstruct.argtypes = [vp, i64, i32, i32, P(npw_params), vp, vp, vp, vp]
+    lib.npweno_flux.argtypes = [vp, vp, i64, i32, i32, d, P(npw_params), vp, vp]
+    lib.npw_workspace_size.argtypes = [i64, i32, P(npw_params)]
+    lib.npw_workspace_size.restype = sz
+    lib.npweno_rk3_step.argtypes = [vp, i64, i32, d, d, i32, i32, P(npw_params), vp, sz, P(d), vp]
+    lib.npweno_solve.argtypes = [vp, i64, i32, d, d, d, i32, i32, P(npw_params), vp, sz, P(npw_solve_stats), vp]
+    lib.npw_batch_workspace_size.argtypes = [P(npw_instance), i32, i32, P(npw_params)]
+    lib.npw_batch_workspace_size.restype = sz
+    lib.npweno_batch_solve.argtypes = [vp, P(npw_instance), i32, i32, i32, P(npw_params), vp, sz,
+                                       P(npw_solve_stats), vp]
+    lib.npw_workspace_size_2d.argtypes = [i64, i64, i32, P(npw_params)]
+    lib.npw_workspace_size_2d.restype = sz
+    lib.npweno_rk3_step_2d.argtypes = [vp, i64, i64, i32, d, d, d, i32, i32, P(npw_params), vp, sz, vp]
+    lib.npweno_solve_2d.argtypes = [vp, i64, i64, i32, d, d, d, d, i32, i32, P(npw_params), vp, sz,
+                                    P(npw_solve_stats), vp]
+    for f in ("npweno_reconstruct", "npweno_flux", "npweno_rk3_step", "npweno_solve", "npweno_batch_solve",
+              "npweno_rk3_step_2d", "npweno_solve_2d"):
+        getattr(lib, f).restype = i32
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != NPW_OK:
+        raise NpwError(st, load().npw_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libnpweno needs a CUDA GPU (there is no CPU fallback)")
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dtype(params: Params):
+    torch = _torch()
+    return torch.float32 if params.precision == NPW_FP32_MIXED else torch.float64
+
+
+def _dev(t, params: Params, name: str):
+    torch = _torch()
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == _dtype(params)):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of dtype {_dtype(params)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def npw_default_params() -> Params:
+    return Params()
+
+
+def npw_version() -> int:
+    return load().npw_version()
+
+
+def npweno_reconstruct(vbar, bc: int, params: Params, with_flags: bool = True):
+    """Face values of vbar [m][n] (or [n]) -> (v_minus, v_plus, flags), each [m][n+1]."""
+    torch = _torch()
+    squeeze = vbar.dim() == 1
+    v = vbar[None] if squeeze else vbar
+    m, n = v.shape
+    vm = torch.empty((m, n + 1), dtype=v.dtype, device=v.device)
+    vp = torch.empty_like(vm)
+    fl = torch.empty((m, n + 1), dtype=torch.uint8, device=v.device) if with_flags else None
+    p = params.c()
+    _check(load().npweno_reconstruct(_dev(v, params, "vbar"), n, m, bc, C.byref(p), C.c_void_p(vm.data_ptr()),
+                                     C.c_void_p(vp.data_ptr()), C.c_void_p(fl.data_ptr()) if fl is not None else None,
+                                     _stream()))
+    if squeeze:
+        return vm[0], vp[0], (fl[0] if fl is not None else None)
+    return vm, vp, fl
+
+
+def npweno_flux(v_minus, v_plus, flux_kind: int, alpha: float, params: Params):
+    torch = _torch()
+    squeeze = v_minus.dim() == 1
+    a = v_minus[None] if squeeze else v_minus
+    b = v_plus[None] if squeeze else v_plus
+    m, nf = a.shape
+    h = torch.empty_like(a)
+    p = params.c()
+    _check(load().npweno_flux(_dev(a, params, "v_minus"), _dev(b, params, "v_plus"), nf, m, flux_kind, float(alpha),
+                              C.byref(p), C.c_void_p(h.data_ptr()), _stream()))
+    return h[0] if squeeze else h
+
+
+def npw_workspace_size(n: int, m: int, params: Params) -> int:
+    p = params.c()
+    return int(load().npw_workspace_size(n, m, C.byref(p)))
+
+
+def _workspace(nbytes: int, device, given=None):
+    torch = _torch()
+    if given is not None:
+        if given.numel() * given.element_size() < nbytes:
+            raise ValueError("workspace too small")
+        return given
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+
+
+def npweno_rk3_step(u, dx: float, dt: float, flux_kind: int, bc: int, params: Params, workspace=None,
+                    want_alpha: bool = False) -> Optional[float]:
+    """One TVD-RK3 step of u [m][n] (or [n]) in place; returns alpha if want_alpha."""
+    uu = u[None] if u.dim() == 1 else u
+    m, n = uu.shape
+    nbytes = npw_workspace_size(n, m, params)
+    ws = _workspace(nbytes, u.device, workspace)
+    p = params.c()
+    a = C.c_double(0.0)
+    _check(load().npweno_rk3_step(_dev(uu, params, "u"), n, m, float(dx), float(dt), flux_kind, bc, C.byref(p),
+                                  C.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size(),
+                                  C.byref(a) if want_alpha else None, _stream()))
+    return a.value if want_alpha else None
+
+
+def _stats(s: npw_solve_stats) -> dict:
+    return dict(steps=int(s.steps), t=float(s.t), alpha_max=float(s.alpha_max), status=int(s.status))
+
+
+def npweno_solve(u, dx: float, t_end: float, cfl: float, flux_kind: int, bc: int, params: Params, workspace=None):
+    """Advance u [m][n] (or [n]) in place to t_end; returns the statistics dict."""
+    uu = u[None] if u.dim() == 1 else u
+    m, n = uu.shape
+    nbytes = npw_workspace_size(n, m, params)
+    ws = _workspace(nbytes, u.device, workspace)
+    p = params.c()
+    st = npw_solve_stats()
+    _check(load().npweno_solve(_dev(uu, params, "u"), n, m, float(dx), float(t_end), float(cfl), flux_kind, bc,
+                               C.byref(p), C.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size(), C.byref(st),
+                               _stream()))
+    return _stats(st)
+
+
+def make_instances(ns: Sequence[int], dxs: Sequence[float], t_ends: Sequence[float], cfls: Sequence[float],
+                   bcs: Sequence[int], m: int = 1):
+    """Instance table for a packed arena: instance i occupies [off_i, off_i + m*n_i)."""
+    arr = (npw_instance * len(ns))()
+    off = 0
+    for i, n in enumerate(ns):
+        arr[i].offset = off
+        arr[i].n = int(n)
+        arr[i].dx = float(dxs[i])
+        arr[i].t_end = float(t_ends[i])
+        arr[i].cfl = float(cfls[i])
+        arr[i].bc = int(bcs[i])
+        off += m * int(n)
+    return arr, off
+
+
+def npw_batch_workspace_size(instances, m: int, params: Params) -> int:
+    p = params.c()
+    return int(load().npw_batch_workspace_size(instances, len(instances), m, C.byref(p)))
+
+
+def npweno_batch_solve(arena, instances, m: int, flux_kind: int, params: Params, workspace=None,
+                       raise_on_error: bool = True):
+    """Advance every instance of the packed arena (device) to its t_end; returns (status,
+    list of per-instance stats)."""
+    count = len(instances)
+    nbytes = npw_batch_workspace_size(instances, m, params)
+    ws = _workspace(nbytes, arena.device, workspace)
+    p = params.c()
+    out = (npw_solve_stats * count)()
+    st = load().npweno_batch_solve(_dev(arena, params, "arena"), instances, count, m, flux_kind, C.byref(p),
+                                   C.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size(), out, _stream())
+    if raise_on_error and st not in (NPW_OK, NPW_ENONFINITE):
+        _check(st)
+    return st, [_stats(out[i]) for i in range(count)]
+
+
+def npw_workspace_size_2d(nx: int, ny: int, m: int, params: Params) -> int:
+    p = params.c()
+    return int(load().npw_workspace_size_2d(nx, ny, m, C.byref(p)))
+
+
+def npweno_rk3_step_2d(u, dx: float, dy: float, dt: float, flux_kind: int, bc: int, params: Params,
+                       workspace=None):
+    uu = u[None] if u.dim() == 2 else u
+    m, ny, nx = uu.shape
+    ws = _workspace(npw_workspace_size_2d(nx, ny, m, params), u.device, workspace)
+    p = params.c()
+    _check(load().npweno_rk3_step_2d(_dev(uu, params, "u"), nx, ny, m, float(dx), float(dy), float(dt), flux_kind,
+                                     bc, C.byref(p), C.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size(),
+                                     _stream()))
+
+
+def npweno_solve_2d(u, dx: float, dy: float, t_end: float, cfl: float, flux_kind: int, bc: int, params: Params,
+                    workspace=None):
+    uu = u[None] if u.dim() == 2 else u
+    m, ny, nx = uu.shape
+    ws = _workspace(npw_workspace_size_2d(nx, ny, m, params), u.device, workspace)
+    p = params.c()
+    st = npw_solve_stats()
+    _check(load().npweno_solve_2d(_dev(uu, params, "u"), nx, ny, m, float(dx), float(dy), float(t_end), float(cfl),
+                                  flux_kind, bc, C.byref(p), C.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size(),
+                                  C.byref(st), _stream()))
+    return _stats(st)

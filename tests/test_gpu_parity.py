@@ -1,0 +1,292 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars (written here, derived in the design doc):
+  * NPW_FP64 vs oracle: relative L_inf <= 1e-12; ENO stencil choices and switch flags
+    identical except at faces the oracle marks as near ties (only the switch, evaluated in
+    closed form on the GPU and by a 4x4 solve in the oracle, can differ there).
+  * NPW_FP32_MIXED vs oracle: the per-config L1 / L_inf bounds stated in each test.
+Sizes span several 1024-cell tiles and a ragged last tile; edge cases: the minimum n = 6,
+tile boundaries, invalid arguments and non-finite states.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1602_00182_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+SCHEMES = [(O.ENO, 0), (O.WENO_JS, 1), (O.RBF_ENO, 2), (O.RBF_WENO, 3)]
+
+
+@pytest.fixture(scope="module")
+def npw():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1602_00182_gb300 import build as b
+    b.build()
+    import paper_1602_00182_gb300.npweno as m
+    m.load()
+    return m
+
+
+def _dev(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def _gparams(npw, o: "O.Params", precision=0):
+    return npw.Params(scheme=o.scheme, rbf=o.rbf, monotone_switch=o.monotone_switch, switch_variant=o.switch_variant,
+                      characteristic=o.characteristic, precision=precision, eps_M=o.eps_M, eps_weno=o.eps_weno,
+                      gamma=o.gamma, adv_speed=o.adv_speed, adv_speed_y=o.adv_speed_y, inflow=o.inflow)
+
+
+def _mixed_data(n, seed):
+    """Smooth waves, a jump, a flat stretch and a linear ramp (exercises every branch)."""
+    g = np.random.default_rng(seed)
+    x = np.linspace(0, 1, n, endpoint=False)
+    u = 1.0 + 0.3 * np.sin(2 * np.pi * 3 * x + g.uniform(0, 6)) + 0.1 * np.cos(2 * np.pi * 7 * x)
+    u[x > 0.6] += 0.5
+    u[(x > 0.2) & (x < 0.3)] = 1.1
+    u[(x > 0.75) & (x < 0.8)] = np.linspace(0, 1, ((x > 0.75) & (x < 0.8)).sum())
+    return u
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+TIES = O.FLAG_SWITCH_TIE | O.FLAG_ENO_TIE_L | O.FLAG_ENO_TIE_R
+
+
+# ------------------------------------------------------------------------------ reconstruct
+@pytest.mark.parametrize("scheme", [s for s, _ in SCHEMES])
+@pytest.mark.parametrize("rbf", [O.MQ, O.GA])
+@pytest.mark.parametrize("switch,variant", [(0, 0), (1, 0), (1, 1)])
+@pytest.mark.parametrize("bc", [O.PERIODIC, O.TRANSMISSIVE, O.INFLOW])
+def test_reconstruct_fp64(npw, scheme, rbf, switch, variant, bc):
+    op = O.Params(scheme=scheme, rbf=rbf, monotone_switch=switch, switch_variant=variant, inflow=(0.7, 0, 0, 0))
+    for n in (6, 37, 1025, 3001):
+        u = _mixed_data(n, n)
+        vm, vp, fl, _ = O.reconstruct(u, bc, op)
+        gvm, gvp, gfl = npw.npweno_reconstruct(_dev(u), bc, _gparams(npw, op))
+        gvm, gvp, gfl = gvm.cpu().numpy(), gvp.cpu().numpy(), gfl.cpu().numpy()
+        tie = (fl & TIES) != 0
+        ok = ~tie
+        assert np.array_equal(gfl[ok] & 0x3D, fl[ok] & 0x3D), n
+        scale = np.abs(u).max()
+        assert np.abs(gvm[ok] - vm[ok]).max() <= FP64_TOL * scale, n
+        assert np.abs(gvp[ok] - vp[ok]).max() <= FP64_TOL * scale, n
+
+
+@pytest.mark.parametrize("char", [0, 1])
+def test_reconstruct_euler_fp64(npw, char):
+    for inst in I.euler_batch(count=4, nmin=64, nmax=2500):
+        op = O.Params(characteristic=char)
+        vm, vp, fl, _ = O.reconstruct(inst.u0, O.TRANSMISSIVE, op)
+        gvm, gvp, gfl = npw.npweno_reconstruct(_dev(inst.u0), O.TRANSMISSIVE, _gparams(npw, op))
+        ok = (fl & TIES) == 0
+        tol = FP64_TOL
+        for a, b in ((gvm.cpu().numpy(), vm), (gvp.cpu().numpy(), vp)):
+            for k in range(3):
+                assert np.abs(a[k][ok[k]] - b[k][ok[k]]).max() <= tol * np.abs(b[k]).max()
+
+
+def test_flux_fp64(npw):
+    g = np.random.default_rng(1)
+    for kind, m in ((O.ADVECTION, 1), (O.BURGERS, 1), (O.EULER1D, 3)):
+        if m == 1:
+            a, b = g.normal(size=(1, 777)), g.normal(size=(1, 777))
+        else:
+            a = I.prim_to_cons(g.uniform(0.2, 1, 777), g.uniform(-1, 1, 777), g.uniform(0.2, 1, 777))
+            b = I.prim_to_cons(g.uniform(0.2, 1, 777), g.uniform(-1, 1, 777), g.uniform(0.2, 1, 777))
+        h = O.flux(a, b, kind, 1.7, O.Params())
+        gh = npw.npweno_flux(_dev(a), _dev(b), kind, 1.7, npw.Params()).cpu().numpy()
+        assert np.array_equal(gh, h), kind
+
+
+# ------------------------------------------------------------------------------ time stepping
+@pytest.mark.parametrize("scheme", [s for s, _ in SCHEMES])
+def test_rk3_step_fp64(npw, scheme):
+    for n in (6, 1023, 1024, 1025, 2500):
+        u = _mixed_data(n, 3 * n)
+        op = O.Params(scheme=scheme)
+        ref, a_ref = O.rk3_step(u, 1.0 / n, 0.3 / n, O.BURGERS, O.PERIODIC, op)
+        gu = _dev(u)
+        a = npw.npweno_rk3_step(gu, 1.0 / n, 0.3 / n, O.BURGERS, O.PERIODIC, _gparams(npw, op), want_alpha=True)
+        assert a == a_ref
+        assert _rel(gu.cpu().numpy(), ref) <= FP64_TOL, n
+
+
+@pytest.mark.parametrize("n", [25, 50, 100, 200, 400])
+@pytest.mark.parametrize("switch", [0, 1])
+def test_advection_solve_fp64(npw, n, switch):
+    """Linear advection of sin(pi x) on [-1, 1], periodic, RBF-WENO5 (MQ), LF, TVD-RK3 at
+    CFL 0.5 to T = 2 (400 steps at N = 200)."""
+    u0, dx = I.advection_sin(n)
+    op = O.Params(monotone_switch=switch)
+    ref, rst = O.solve(u0, dx, 2.0, 0.5, O.ADVECTION, O.PERIODIC, op)
+    gu = _dev(u0)
+    st = npw.npweno_solve(gu, dx, 2.0, 0.5, O.ADVECTION, O.PERIODIC, _gparams(npw, op))
+    assert st["steps"] == rst["steps"] and st["t"] == 2.0 and st["status"] == 0
+    assert _rel(gu.cpu().numpy(), ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("scheme", [s for s, _ in SCHEMES])
+def test_burgers_solve_fp64_through_shock(npw, scheme):
+    inst = I.burgers_batch(count=1, nmin=1500, nmax=1600)[0]
+    op = O.Params(scheme=scheme, rbf=O.GA)
+    ref, rst = O.solve(inst.u0[0], inst.dx, 0.6, 0.5, O.BURGERS, O.PERIODIC, op)
+    gu = _dev(inst.u0[0])
+    st = npw.npweno_solve(gu, inst.dx, 0.6, 0.5, O.BURGERS, O.PERIODIC, _gparams(npw, op))
+    assert st["steps"] == rst["steps"]
+    assert _rel(gu.cpu().numpy(), ref) <= 1e-11
+
+
+def test_batch_fp64_matches_oracle(npw):
+    """Uneven batch: each instance keeps its own dt and stops at its own t_end."""
+    inst = I.burgers_batch(count=12, nmin=64, nmax=2600)
+    tends = [0.1 + 0.05 * i for i in range(len(inst))]
+    table, total = npw.make_instances([it.n for it in inst], [it.dx for it in inst], tends, [0.5] * len(inst),
+                                      [O.PERIODIC] * len(inst))
+    arena = _dev(np.concatenate([it.u0[0] for it in inst]))
+    op = O.Params(rbf=O.GA)
+    status, stats = npw.npweno_batch_solve(arena, table, 1, O.BURGERS, _gparams(npw, op))
+    assert status == 0
+    a = arena.cpu().numpy()
+    off = 0
+    for it, te, s in zip(inst, tends, stats):
+        ref, rst = O.solve(it.u0[0], it.dx, te, 0.5, O.BURGERS, O.PERIODIC, op)
+        assert s["steps"] == rst["steps"] and s["t"] == te
+        assert _rel(a[off:off + it.n], ref) <= 1e-11
+        off += it.n
+
+
+@pytest.mark.parametrize("char", [0, 1])
+def test_euler_batch_fp64(npw, char):
+    inst = I.euler_batch(count=4, nmin=300, nmax=1200)
+    op = O.Params(characteristic=char)
+    table, total = npw.make_instances([it.n for it in inst], [it.dx for it in inst], [min(it.t_end, 0.05) for it in inst],
+                                      [0.5] * 4, [O.TRANSMISSIVE] * 4, m=3)
+    arena = _dev(np.concatenate([it.u0.ravel() for it in inst]))
+    status, stats = npw.npweno_batch_solve(arena, table, 3, O.EULER1D, _gparams(npw, op))
+    assert status == 0
+    a = arena.cpu().numpy()
+    off = 0
+    for it, s in zip(inst, stats):
+        ref, rst = O.solve(it.u0, it.dx, min(it.t_end, 0.05), 0.5, O.EULER1D, O.TRANSMISSIVE, op)
+        got = a[off:off + 3 * it.n].reshape(3, it.n)
+        assert s["steps"] == rst["steps"]
+        assert _rel(got, ref) <= 1e-11
+        off += 3 * it.n
+
+
+# ------------------------------------------------------------------------------ 2D
+@pytest.mark.parametrize("shape", [(32, 32), (40, 24), (70, 9)])
+def test_2d_euler_fp64(npw, shape):
+    nx, ny = shape
+    U, d = I.isentropic_vortex(max(nx, ny), 4.0, 5.0, 5.0)
+    U = np.ascontiguousarray(U[:, :ny, :nx])
+    op = O.Params()
+    gu = _dev(U)
+    ref1 = O.rk3_step_2d(U, d, d, 0.01, O.EULER2D, O.PERIODIC, op)
+    npw.npweno_rk3_step_2d(gu, d, d, 0.01, O.EULER2D, O.PERIODIC, _gparams(npw, op))
+    assert _rel(gu.cpu().numpy(), ref1) <= FP64_TOL
+
+
+def test_2d_solve_fp64(npw):
+    U, d = I.four_quadrant(48, np.random.default_rng(4))
+    op = O.Params()
+    ref, rst = O.solve_2d(U, d, d, 0.05, 0.5, O.EULER2D, O.PERIODIC, op)
+    gu = _dev(U)
+    st = npw.npweno_solve_2d(gu, d, d, 0.05, 0.5, O.EULER2D, O.PERIODIC, _gparams(npw, op))
+    assert st["steps"] == rst["steps"]
+    assert _rel(gu.cpu().numpy(), ref) <= 1e-11
+
+
+# ------------------------------------------------------------------------------ mixed precision
+def test_burgers_batch_mixed_precision_accuracy(npw):
+    """Config family of the benchmark (periodic Burgers on [0, 2 pi], Gaussian perturbation,
+    CFL 0.5) run past shock formation to T = 1.5 in NPW_FP32_MIXED, against the FP64 oracle
+    started from the same float-rounded data.  Bound from the arithmetic: each of the
+    3 S stage updates rounds the state to 2^-24 relative (|u| <= 2.5, S <= 1100 steps here),
+    so smooth regions drift by at most ~3 S 2^-24 |u| ~ 5e-4 (L_inf) and far less on average;
+    a shock displaced by a fraction of a cell adds jump x fraction to one cell.  Stated bars:
+    L1 <= 1e-4, L_inf <= 2e-2 per instance."""
+    inst = I.burgers_batch(count=16, nmin=64, nmax=1024)
+    table, total = npw.make_instances([it.n for it in inst], [it.dx for it in inst], [1.5] * 16, [0.5] * 16,
+                                      [O.PERIODIC] * 16)
+    arena = _dev(np.concatenate([it.u0[0] for it in inst]), torch.float32)
+    op = O.Params(rbf=O.GA)
+    status, stats = npw.npweno_batch_solve(arena, table, 1, O.BURGERS, _gparams(npw, op, precision=1))
+    assert status == 0
+    a = arena.cpu().numpy().astype(np.float64)
+    off = 0
+    worst_l1 = worst_linf = 0.0
+    for it in inst:
+        ref, _ = O.solve(it.u0[0].astype(np.float32).astype(np.float64), it.dx, 1.5, 0.5, O.BURGERS, O.PERIODIC, op)
+        e = np.abs(a[off:off + it.n] - ref)
+        worst_l1, worst_linf = max(worst_l1, e.mean()), max(worst_linf, e.max())
+        off += it.n
+    print(f"mixed precision Burgers T=1.5: worst L1 {worst_l1:.3e}, worst Linf {worst_linf:.3e}")
+    assert worst_l1 <= 1e-4 and worst_linf <= 2e-2
+
+
+def test_mixed_precision_single_stage(npw):
+    """One RK3 step from float-representable data: FP32 arithmetic bound ~ 1e-6 relative."""
+    u = _mixed_data(3000, 9).astype(np.float32).astype(np.float64)
+    op = O.Params()
+    ref, _ = O.rk3_step(u, 1.0 / 3000, 0.3 / 3000, O.BURGERS, O.PERIODIC, op)
+    gu = _dev(u, torch.float32)
+    npw.npweno_rk3_step(gu, 1.0 / 3000, 0.3 / 3000, O.BURGERS, O.PERIODIC, _gparams(npw, op, precision=1))
+    assert _rel(gu.cpu().numpy().astype(np.float64), ref) <= 2e-6
+
+
+# ------------------------------------------------------------------------------ properties / edges
+def test_conservation_fp64_periodic(npw):
+    inst = I.burgers_batch(count=1, nmin=3000, nmax=3100)[0]
+    gu = _dev(inst.u0[0])
+    s0 = gu.sum().item()
+    npw.npweno_solve(gu, inst.dx, 1.0, 0.5, O.BURGERS, O.PERIODIC, npw.Params(rbf=npw.NPW_RBF_GA))
+    assert abs(gu.sum().item() - s0) <= 1e-11 * abs(s0)
+
+
+def test_invalid_arguments(npw):
+    u = _dev(np.ones(5))
+    with pytest.raises(npw.NpwError) as e:
+        npw.npweno_reconstruct(u, 0, npw.Params())
+    assert e.value.status == npw.NPW_EINVAL
+    u = _dev(np.ones((2, 50)))
+    with pytest.raises(npw.NpwError):
+        npw.npweno_solve(u, 0.1, 1.0, 0.5, npw.NPW_FLUX_BURGERS, 0, npw.Params())
+    with pytest.raises(npw.NpwError):
+        npw.npweno_solve(_dev(np.ones(50)), -0.1, 1.0, 0.5, npw.NPW_FLUX_BURGERS, 0, npw.Params())
+    with pytest.raises(ValueError):  # dtype must match the precision
+        npw.npweno_solve(_dev(np.ones(50), torch.float32), 0.1, 1.0, 0.5, npw.NPW_FLUX_BURGERS, 0, npw.Params())
+
+
+def test_nonfinite_state_is_reported(npw):
+    u = np.ones(2000)
+    u[1234] = np.nan
+    with pytest.raises(npw.NpwError) as e:
+        npw.npweno_solve(_dev(u), 0.01, 1.0, 0.5, npw.NPW_FLUX_BURGERS, 0, npw.Params())
+    assert e.value.status == npw.NPW_ENONFINITE
+    # in a batch only the broken instance fails; the others finish
+    table, total = npw.make_instances([500, 700], [0.01, 0.01], [0.2, 0.2], [0.5, 0.5], [0, 0])
+    a = np.ones(1200)
+    a[100] = np.inf
+    arena = _dev(a)
+    st, stats = npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, npw.Params())
+    assert st == npw.NPW_ENONFINITE
+    assert stats[0]["status"] == npw.NPW_ENONFINITE and stats[1]["status"] == 0 and stats[1]["t"] == 0.2
+
+
+def test_zero_time_and_minimum_size(npw):
+    u0, dx = I.advection_sin(6)
+    gu = _dev(u0)
+    st = npw.npweno_solve(gu, dx, 0.0, 0.5, npw.NPW_FLUX_ADVECTION, 0, npw.Params())
+    assert st["steps"] == 0 and np.array_equal(gu.cpu().numpy(), u0)
+    ref, rst = O.solve(u0, dx, 0.7, 0.5, O.ADVECTION, O.PERIODIC, O.Params())
+    st = npw.npweno_solve(gu, dx, 0.7, 0.5, npw.NPW_FLUX_ADVECTION, 0, npw.Params())
+    assert st["steps"] == rst["steps"] and _rel(gu.cpu().numpy(), ref) <= FP64_TOL

@@ -1,0 +1,68 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and exports every function
+include/npweno.h declares (no compute calls: there is no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "npweno.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(npw[e]?\w*)\s*\(", txt, flags=re.M)
+    return sorted(set(n for n in names if not n.startswith("npw_status") and n not in ("npw_params",)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("npweno_reconstruct", "npweno_flux", "npweno_rk3_step", "npweno_solve",
+                     "npw_workspace_size", "npweno_batch_solve", "npweno_solve_2d", "npw_last_error"):
+        assert required in names
+
+
+def test_library_builds_loads_and_exports_every_symbol():
+    from paper_1602_00182_gb300 import build as b
+    path = b.build()
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), f"{name} declared in npweno.h but not exported"
+
+
+def test_default_params_and_errors_without_gpu():
+    from paper_1602_00182_gb300 import build as b
+    from paper_1602_00182_gb300 import npweno as npw
+    b.build()
+    lib = npw.load()
+    p = npw.npw_params()
+    lib.npw_default_params(ctypes.byref(p))
+    assert (p.k, p.scheme, p.rbf, p.monotone_switch, p.precision) == (3, npw.NPW_RBF_WENO, npw.NPW_RBF_MQ, 1, npw.NPW_FP64)
+    assert p.eps_weno == 1e-6 and p.gamma == 1.4 and p.eps_M == 1e-12
+    # argument validation happens before any CUDA call
+    bad = npw.Params(k=2).c()
+    st = lib.npweno_reconstruct(ctypes.c_void_p(16), 100, 1, 0, ctypes.byref(bad), ctypes.c_void_p(16),
+                                ctypes.c_void_p(16), None, None)
+    assert st == npw.NPW_EINVAL and b"k = 3" in lib.npw_last_error()
+    good = npw.Params().c()
+    st = lib.npweno_reconstruct(ctypes.c_void_p(16), 5, 1, 0, ctypes.byref(good), ctypes.c_void_p(16),
+                                ctypes.c_void_p(16), None, None)
+    assert st == npw.NPW_EINVAL
+    assert lib.npw_workspace_size(1000, 1, ctypes.byref(good)) > 2 * 1000 * 8
+    assert lib.npw_version() >= 10000
+
+
+def test_no_cpu_fallback_in_product_path():
+    """The binding refuses to run without a GPU rather than computing on the CPU, and the
+    package never imports the oracle."""
+    import torch
+    from paper_1602_00182_gb300 import npweno as npw
+    pkg = os.path.join(ROOT, "paper_1602_00182_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            assert "import oracle" not in open(os.path.join(pkg, f)).read()
+    if not torch.cuda.is_available():
+        with pytest.raises(RuntimeError):
+            npw.npweno_reconstruct(torch.zeros(10, dtype=torch.float64), 0, npw.Params())
