@@ -182,6 +182,31 @@ npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx
                            size_t workspace_bytes, npw_solve_stats* out, void* stream);
 
 /*
+ * npweno_rk3_step_noalloc -- the same TVD-RK3 step as npweno_rk3_step (identical kernels and
+ * results), for callers that cannot allocate device memory.  The paper has no counterpart:
+ * this is an interface for embedding.  Some callers own only device pointers to their state
+ * and cannot obtain more device memory where they call the solver -- a host framework that
+ * places every buffer itself and keeps the rest of the GPU in its own pool, or a job confined
+ * to a fixed share of GPU memory where a late allocation could fail.  This entry point takes no
+ * workspace: its scratch is one fixed 8 MiB array inside the library, placed on every GPU
+ * that loads the library and kept there until the process exits.
+ *   - Allocates no device memory (no cudaMalloc, cudaFree or allocating library call).
+ *   - Limit: npw_workspace_size(n, m, params) must not exceed npw_noalloc_scratch_bytes()
+ *     (8 MiB: n * m up to about 5.2e5 in NPW_FP64, 1.0e6 in NPW_FP32_MIXED); larger sizes
+ *     return NPW_EINVAL with an explanatory npw_last_error().
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ *     with that device current) and caches it; make that first call before any stream capture.
+ *   - Every call on a device uses the same array and the array keeps the last call's contents
+ *     (each call re-initialises what it reads), so calls that overlap on the GPU -- on
+ *     different streams or host threads at the same time -- race and must be serialised.
+ *   - u, n, m, dx, dt, flux_kind, bc, params and stream have the meaning of npweno_rk3_step.
+ */
+npw_status npweno_rk3_step_noalloc(void* u, int64_t n, int32_t m, double dx, double dt, int32_t flux_kind,
+                                   int32_t bc, const npw_params* params, void* stream);
+/* Size in bytes of the fixed scratch array used by npweno_rk3_step_noalloc. */
+size_t npw_noalloc_scratch_bytes(void);
+
+/*
  * Process-wide launch counters and stage-kernel timing (no counterpart in the paper; used to
  * put each kernel against its roofline).  When enabled, every launch of the fused stage
  * kernel is bracketed by two CUDA events recorded on the launching stream; the elapsed times

@@ -5,6 +5,7 @@ object next to this file:
   npw_fp64.cu  -- double-precision kernels, --fmad=false (each operation rounded as written)
   npw_fp32.cu  -- mixed-precision kernels
   npw_api.cu   -- host runtime and the C ABI
+  npw_noalloc.cu -- npweno_rk3_step_noalloc and its fixed device scratch array
 """
 from __future__ import annotations
 
@@ -26,6 +27,7 @@ UNITS = {
     "npw_fp64.cu": ["--fmad=false"],
     "npw_fp32.cu": [],
     "npw_api.cu": [],
+    "npw_noalloc.cu": [],
 }
 
 

@@ -483,6 +483,8 @@ npw_status run_to_end(Run1D& r, npw_solve_stats* out) {
 
 }  // namespace
 
+npw_status npw::set_error(npw_status st, const char* msg) { return fail(st, "%s", msg); }
+
 // =======================================================================================
 // C ABI
 // =======================================================================================

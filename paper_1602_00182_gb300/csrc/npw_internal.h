@@ -123,6 +123,9 @@ cudaError_t launch_alpha_init_2d(const void* u, const Inst2D* inst, int tiles, C
 template <typename R>
 cudaError_t launch_stage2d(const Stage2DArgs& a, int tiles, int kind, cudaStream_t s);
 
+// records msg as the calling thread's npw_last_error() text and returns st (npw_api.cu)
+npw_status set_error(npw_status st, const char* msg);
+
 // precision-independent helpers (npw_api.cu)
 cudaError_t launch_ctl_start(Ctl* ctl, const InstDev* inst, int count, int mode, double dt, cudaStream_t s);
 cudaError_t launch_ctl_start_2d(Ctl* ctl, const Inst2D* inst, int mode, double dt, cudaStream_t s);

@@ -107,8 +107,10 @@ def load():
     lib.npweno_rk3_step_2d.argtypes = [vp, i64, i64, i32, d, d, d, i32, i32, P(npw_params), vp, sz, vp]
     lib.npweno_solve_2d.argtypes = [vp, i64, i64, i32, d, d, d, d, i32, i32, P(npw_params), vp, sz,
                                     P(npw_solve_stats), vp]
+    lib.npweno_rk3_step_noalloc.argtypes = [vp, i64, i32, d, d, i32, i32, P(npw_params), vp]
+    lib.npw_noalloc_scratch_bytes.restype = sz
     for f in ("npweno_reconstruct", "npweno_flux", "npweno_rk3_step", "npweno_solve", "npweno_batch_solve",
-              "npweno_rk3_step_2d", "npweno_solve_2d"):
+              "npweno_rk3_step_2d", "npweno_solve_2d", "npweno_rk3_step_noalloc"):
         getattr(lib, f).restype = i32
     _lib = lib
     return lib
@@ -209,6 +211,17 @@ def npweno_rk3_step(u, dx: float, dt: float, flux_kind: int, bc: int, params: Pa
                                   C.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size(),
                                   C.byref(a) if want_alpha else None, _stream()))
     return a.value if want_alpha else None
+
+
+def npweno_rk3_step_noalloc(u, dx: float, dt: float, flux_kind: int, bc: int, params: Params):
+    """npweno_rk3_step without a workspace: the library's fixed scratch array is used (for
+    callers that cannot allocate device memory; see include/npweno.h for the size limit and
+    the rule that calls must not overlap on the GPU)."""
+    uu = u[None] if u.dim() == 1 else u
+    m, n = uu.shape
+    p = params.c()
+    _check(load().npweno_rk3_step_noalloc(_dev(uu, params, "u"), n, m, float(dx), float(dt), flux_kind, bc,
+                                          C.byref(p), _stream()))
 
 
 def _stats(s: npw_solve_stats) -> dict:
