@@ -142,10 +142,10 @@ def run_gpu(args, rank, world, local_rank):
     # largest instances first in the arena (the work list follows the arena order)
     order = sorted(range(len(inst)), key=lambda i: -inst[i].n)
     ns = [inst[i].n for i in order]
-    table, total = npw.make_instances(ns, [inst[i].dx for i in order], [T_END] * len(order), [CFL] * len(order),
+    table, total = npw.make_instances(ns, [inst[i].dx for i in order], [args.t_end] * len(order), [CFL] * len(order),
                                       [npw.NPW_BC_PERIODIC] * len(order))
     host0 = np.concatenate([inst[i].u0[0] for i in order]).astype(np.float32)
-    params = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED)
+    params = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, eta_eval=args.eta_eval)
     pristine = torch.tensor(host0, device=dev)
     arena = pristine.clone()
     ws = torch.empty(npw.npw_batch_workspace_size(table, 1, params), dtype=torch.uint8, device=dev)
@@ -224,6 +224,27 @@ def run_gpu(args, rank, world, local_rank):
         t = torch.tensor([e2e_value * world], dtype=torch.float64, device=dev)
         e2e_value = t.item()
 
+    variants = {}
+    if args.variant_steps > 0 and args.eta_eval == 0 and world == 1:
+        pv = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, eta_eval=1)
+        arena.copy_(pristine)
+        npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, pv, workspace=ws)
+        vt = []
+        for _ in range(args.variant_steps):
+            arena.copy_(pristine)
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, vstats = npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, pv, workspace=ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            vt.append(e0.elapsed_time(e1))
+        vcu = sum(n * s["steps"] for n, s in zip(ns, vstats))
+        variants["eta_eval=1 (exact double-float eta, no FP64 instruction)"] = {
+            "value": vcu * len(vt) / (sum(vt) / 1e3), "unit": "cell-updates/s", "ms_per_step": sum(vt) / len(vt)}
+
     out = {
         "metric": "cell-updates/s",
         "value": value,
@@ -243,7 +264,8 @@ def run_gpu(args, rank, world, local_rank):
             "instances": len(ns),
             "cells": int(sum(ns)),
             "cell_updates_per_step": int(cell_updates),
-            "precision": "NPW_FP32_MIXED: f32 state/candidates/weights/flux/update; f64 eta, switch, ENO choice, beta",
+            "precision": ("NPW_FP32_MIXED: f32 state, candidates, beta, weights, flux, update; eta in FP64 "
+                          f"(eta_eval={args.eta_eval}); switch decisions equal to FP64 evaluation"),
             "l2": "flushed (256 MB write) before every timed step; working set 3 x 4 B x cells",
             "parallelism": f"independent instance batches, one per rank (x{world})",
         },
@@ -262,6 +284,7 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": int(host0.nbytes),
                 "d2h_bytes_per_step": int(host0.nbytes)},
         "gpu_launches": int(pr.kernel_launches),
+        "variants": variants,
         "clocks": clocks.summary(local_rank),
     }
     return out, inst
@@ -291,7 +314,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--instances", type=int, default=4096)
+    ap.add_argument("--t-end", type=float, default=T_END, help="final time (shorter only for profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eta-eval", type=int, default=0, choices=[0, 1],
+                    help="0: eta in FP64 (the configuration's FP64 shape-parameter step); 1: exact double-float")
+    ap.add_argument("--variant-steps", type=int, default=1,
+                    help="timed solves of the eta_eval=1 variant reported beside the headline (0: skip)")
     ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
     args = ap.parse_args()
     os.makedirs(args.out_dir, exist_ok=True)

@@ -54,9 +54,11 @@ typedef enum { NPW_BC_PERIODIC = 0, NPW_BC_TRANSMISSIVE = 1, NPW_BC_INFLOW = 2 }
 /* Schemes compared in the paper (Sec. 5.2): ENO3, WENO-JS5 (eta = 0), RBF-ENO3, RBF-WENO5. */
 typedef enum { NPW_ENO = 0, NPW_WENO_JS = 1, NPW_RBF_ENO = 2, NPW_RBF_WENO = 3 } npw_scheme;
 typedef enum { NPW_RBF_MQ = 0, NPW_RBF_GA = 1 } npw_rbf;
-/* NPW_FP64: everything in double.  NPW_FP32_MIXED: float state, candidates, weights, flux
- * and update; the shape parameter, the monotone switch and the smoothness indicators are
- * evaluated in double from the float cell averages. */
+/* NPW_FP64: everything in double.  NPW_FP32_MIXED: float state, candidates, WENO weights and
+ * smoothness indicators, flux and update; the shape parameter eta is evaluated in FP64 (see
+ * eta_eval), and the monotone-switch and ENO decisions are those of FP64 evaluation (taken from
+ * float values with a certified error bound, recomputed in double when the bound does not
+ * decide them). */
 typedef enum { NPW_FP64 = 0, NPW_FP32_MIXED = 1 } npw_precision;
 
 typedef struct {
@@ -67,13 +69,19 @@ typedef struct {
     int32_t switch_variant;  /* 0: cubic on the 4-cell eta stencil; 1: eq. root_value on both 3-cell halves */
     int32_t characteristic;  /* 1D Euler only: reconstruct Roe characteristic fields */
     int32_t precision;       /* npw_precision */
-    int32_t pad_;
+    int32_t eta_eval;        /* NPW_FP32_MIXED only: 0 = eta in FP64 (exact FP64 numerator and
+                                denominator, FP64 division); 1 = from the exactly computed numerator
+                                and denominator held as float pairs, double-float quotient (no FP64
+                                instruction, ~2^-46 relative before rounding to float) */
     double eps_M;            /* additive guard of the eta denominator (Table k3), e.g. 1e-12 */
     double eps_weno;         /* WENO epsilon of Sec. 2, 1e-6 */
     double gamma;            /* ratio of specific heats, 1.4 */
     double adv_speed;        /* advection speed a (x) for NPW_FLUX_ADVECTION */
     double adv_speed_y;      /* advection speed (y) for 2D advection */
     double inflow[4];        /* ghost state of NPW_BC_INFLOW (conserved variables) */
+    double eta_guard;        /* eta = 0 where |den| <= eta_guard * (|w0| + 15|w1| + 15|w2| + |w3|), i.e.
+                                where the eta denominator is below the round-off of its cell averages;
+                                0 = automatic (off for NPW_FP64, 8 * 2^-24 for NPW_FP32_MIXED), < 0 = off */
 } npw_params;
 
 typedef struct {
@@ -97,7 +105,8 @@ typedef struct {
 } npw_instance;
 
 /* Fill *p with the defaults: k = 3, RBF-WENO5, multiquadric, switch on (variant 0),
- * component-wise, FP64, eps_M = 1e-12, eps_weno = 1e-6, gamma = 1.4, a = (1, 1). */
+ * component-wise, FP64, eps_M = 1e-12, eps_weno = 1e-6, gamma = 1.4, a = (1, 1),
+ * eta_eval = 0, eta_guard = 0 (automatic). */
 void npw_default_params(npw_params* p);
 
 /* Text of the last error on the calling thread ("" if none). */

@@ -286,8 +286,14 @@ static void face_field(const double w[6], const orc_params* p, const uint8_t* re
             eta = 0.0; /* eq. adaptation: vanishing shape parameter */
             fl |= ORC_FLAG_SWITCH;
         } else {
-            double den = eta_denominator(&w[1]) + p->eps_M;
-            eta = eta_numerator(&w[1]) / den;
+            /* optional guard (not in the paper): a denominator below the round-off of the cell
+             * averages of a float state is noise; eta = 0 there */
+            double den0 = eta_denominator(&w[1]);
+            double mag = fabs(w[1]) + 15.0 * fabs(w[2]) + 15.0 * fabs(w[3]) + fabs(w[4]);
+            if (!(p->eta_guard > 0.0 && fabs(den0) <= p->eta_guard * mag)) {
+                double den = den0 + p->eps_M;
+                eta = eta_numerator(&w[1]) / den;
+            }
         }
         if (near) fl |= ORC_FLAG_SWITCH_TIE;
     }

@@ -36,6 +36,7 @@ typedef struct {
     double adv_speed_y;
     double inflow[4]; /* ghost state for the inflow boundary */
     double tie_tol;   /* relative margin that marks a decision as a near tie */
+    double eta_guard; /* eta = 0 where |den| <= eta_guard * (|w0| + 15|w1| + 15|w2| + |w3|); 0 = off */
 } orc_params;
 
 typedef struct {

@@ -54,6 +54,7 @@ npw_status check_params(const npw_params* p) {
     if (p->rbf != NPW_RBF_MQ && p->rbf != NPW_RBF_GA) return fail(NPW_EINVAL, "bad rbf %d", p->rbf);
     if (p->switch_variant < 0 || p->switch_variant > 1) return fail(NPW_EINVAL, "bad switch_variant");
     if (p->precision != NPW_FP64 && p->precision != NPW_FP32_MIXED) return fail(NPW_EINVAL, "bad precision");
+    if (p->eta_eval < 0 || p->eta_eval > 1) return fail(NPW_EINVAL, "bad eta_eval %d", p->eta_eval);
     if (!(p->eps_weno > 0.0)) return fail(NPW_EINVAL, "eps_weno must be > 0");
     if (!(p->gamma > 1.0)) return fail(NPW_EINVAL, "gamma must be > 1");
     return NPW_OK;
@@ -66,12 +67,21 @@ npw::MethodParams method(const npw_params* p) {
     mp.monotone_switch = p->monotone_switch ? 1 : 0;
     mp.switch_variant = p->switch_variant;
     mp.characteristic = p->characteristic ? 1 : 0;
+    mp.eta_eval = p->eta_eval;
     mp.eps_M = p->eps_M;
     mp.eps_weno = p->eps_weno;
     mp.gamma = p->gamma;
     mp.adv_speed = p->adv_speed;
     mp.adv_speed_y = p->adv_speed_y;
     for (int k = 0; k < 4; ++k) mp.inflow[k] = p->inflow[k];
+    // automatic guard: none for the double state (the paper's eps_M alone), eight units of
+    // float round-off for the float state, whose noise a fixed eps_M = 1e-12 does not cover
+    if (p->eta_guard > 0.0)
+        mp.eta_guard = p->eta_guard;
+    else if (p->eta_guard == 0.0 && p->precision == NPW_FP32_MIXED)
+        mp.eta_guard = 8.0 * 5.9604644775390625e-08;
+    else
+        mp.eta_guard = 0.0;
     return mp;
 }
 

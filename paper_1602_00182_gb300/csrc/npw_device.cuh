@@ -223,8 +223,13 @@ __device__ __forceinline__ uint32_t face_field(const R* w, const MethodParams& m
         if (fires) {
             fl |= 1u;
         } else {
-            D den = eta_den<D>(w1, w2, w3, w4) + D(mp.eps_M);
-            eta = R(eta_num<D>(w1, w2, w3, w4) / den);
+            D den0 = eta_den<D>(w1, w2, w3, w4);
+            bool unresolved = mp.eta_guard > 0.0 &&
+                              fabs(den0) <= D(mp.eta_guard) * (fabs(w1) + D(15.0) * fabs(w2) + D(15.0) * fabs(w3) + fabs(w4));
+            if (!unresolved) {
+                D den = den0 + D(mp.eps_M);
+                eta = R(eta_num<D>(w1, w2, w3, w4) / den);
+            }
         }
     }
     int rl = 0, rr = 0;
@@ -332,49 +337,6 @@ __device__ __forceinline__ bool euler_eig(const R* UL, const R* UR, R gamma, R R
     Lm[2][0] = R(0.5) * (b2 - uc);
     Lm[2][1] = R(-0.5) * (b1 * u - ic);
     Lm[2][2] = R(0.5) * b1;
-    return true;
-}
-
-// All M fields at one face from the 6 x M stencil W[j*M + k] (cells i-2..i+3).  For the
-// characteristic variant the fields are projected by L, reconstructed, and mapped back by R.
-template <typename R, typename D, int KIND, int M, bool CHAR>
-__device__ __forceinline__ bool face_all(const R* S, const MethodParams& mp, R* vm, R* vp, uint32_t* flags) {
-    if (CHAR) {
-        R Rm[3][3], Lm[3][3];
-        if (!euler_eig<R>(S + 2 * M, S + 3 * M, R(mp.gamma), Rm, Lm)) return false;
-        R wm[3], wp[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            R line[6];
-#pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                R s = R(0.0);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) s += Lm[a][k] * S[j * M + k];
-                line[j] = s;
-            }
-            flags[a] = face_field<R, D>(line, mp, &wm[a], &wp[a]);
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            R sm = R(0.0), sp = R(0.0);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                sm += Rm[k][a] * wm[a];
-                sp += Rm[k][a] * wp[a];
-            }
-            vm[k] = sm;
-            vp[k] = sp;
-        }
-        return true;
-    }
-#pragma unroll
-    for (int k = 0; k < M; ++k) {
-        R line[6];
-#pragma unroll
-        for (int j = 0; j < 6; ++j) line[j] = S[j * M + k];
-        flags[k] = face_field<R, D>(line, mp, &vm[k], &vp[k]);
-    }
     return true;
 }
 

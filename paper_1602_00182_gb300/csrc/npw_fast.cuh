@@ -1,0 +1,323 @@
+// npw_fast.cuh -- per-face / per-cell arithmetic of the mixed-precision path (NPW_FP32_MIXED).
+//
+// On GB300 a double-precision operation costs as much issue bandwidth as ~58 single-precision
+// ones, so the mixed path keeps FP64 out of everything except the shape parameter:
+//   * The monotone switch (Sec. 4) and the ENO stencil choice (Sec. 2) are decisions.  They are
+//     taken from single-precision values with a rigorous forward error bound: a sign is used
+//     only when |value| exceeds the bound, which makes it the sign of the exact quantity and
+//     therefore the sign the double-precision evaluation gives; otherwise the decision is
+//     recomputed in double precision.  The decisions are thus those of FP64 evaluation.
+//   * The shape parameter eta of Table k3 (a ratio of two cancelling differences) is evaluated
+//     either in FP64 (eta_eval 0: exact FP64 numerator and denominator, FP64 division) or from
+//     the exactly computed numerator and denominator as float pairs with a double-float
+//     quotient (eta_eval 1: ~2^-46 relative, no FP64 instruction).  Both are rounded once to
+//     float for the perturbed coefficients c_rj + q_rj eta.
+//   * The WENO smoothness indicators beta_r (Jiang-Shu), the weights, candidates, flux and
+//     update are single precision.
+#pragma once
+#include <cstdint>
+
+#include "npw_device.cuh"
+#include "npw_internal.h"
+
+namespace npw {
+namespace fast {
+
+constexpr float kU = 5.9604645e-08f;  // 2^-24, unit roundoff of float
+constexpr float kE = 6.0f * kU;       // bound factor for short small-integer combinations
+constexpr int kUncertain = 2;
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// sign of the exact value v* given |v - v*| <= err: +1, -1, 0 (v == 0 exactly) or uncertain
+__device__ __forceinline__ int csign(float v, float err) {
+    if (v > err) return 1;
+    if (v < -err) return -1;
+    if (v == 0.0f && err == 0.0f) return 0;
+    return kUncertain;
+}
+
+// Variant 0 of the switch from the neighbour differences d_j = w_{j+1} - w_j of the eta
+// stencil.  In these terms 12 p'(-2) = 35 d0 - 34 d1 + 11 d2, 12 p'(2) = 11 d0 - 34 d1 + 35 d2,
+// 12 p'(s) = 6 A s^2 + 6 B s + C with A = d0 - 2 d1 + d2, B = d2 - d0, C = -d0 + 14 d1 - d2; the
+// vertex lies strictly inside iff 4|A| - |B| > 0, and sign(12 p'(vertex)) = sign(A) sign(2AC - 3B^2).
+// Returns 1 (fires), 0 (does not) or -1 (not certain: decide in double precision).
+__device__ __forceinline__ int switch_v0_cert(float d0, float d1, float d2) {
+    const float a0 = fabsf(d0), a1 = fabsf(d1), a2 = fabsf(d2);
+    const float Em = fmaf(35.f, d0, fmaf(-34.f, d1, 11.f * d2));
+    const float Ep = fmaf(11.f, d0, fmaf(-34.f, d1, 35.f * d2));
+    const int s1 = csign(Em, kE * fmaf(35.f, a0, fmaf(34.f, a1, 11.f * a2)));
+    const int s2 = csign(Ep, kE * fmaf(11.f, a0, fmaf(34.f, a1, 35.f * a2)));
+    if (s1 == kUncertain || s2 == kUncertain) return -1;
+    // p' takes both signs at the two ends: non-monotone whatever the vertex does
+    if ((s1 < 0 && s2 > 0) || (s1 > 0 && s2 < 0)) return 1;
+    const float A = fmaf(-2.f, d1, d0 + d2);
+    const float eA = kE * fmaf(2.f, a1, a0 + a2);
+    const float B = d2 - d0;
+    const float eB = kE * (a0 + a2);
+    const float C = fmaf(14.f, d1, -(d0 + d2));
+    const float eC = kE * fmaf(14.f, a1, a0 + a2);
+    const float aA = fabsf(A), aB = fabsf(B), aC = fabsf(C);
+    // With the vertex inside (|B| < 4|A|), |12 p'(vertex) - C| = 1.5 B^2 / |A| < 24 |A|.  If C
+    // has the common sign of both ends and |C| exceeds that bound, p' keeps one sign on the
+    // whole interval whether or not the vertex is inside (nearly linear data: A, B ~ 0).
+    if (s1 == s2 && s1 != 0) {
+        const int sC = csign(C, eC);
+        if (sC == s1 && aC - eC > 24.f * (aA + eA) * (1.f + 4.f * kU)) return 0;
+    }
+    const int sD = csign(fmaf(4.f, aA, -aB), 4.f * eA + eB + kE * fmaf(4.f, aA, aB));
+    if (sD == kUncertain) return -1;
+    bool neg = s1 < 0 || s2 < 0, pos = s1 > 0 || s2 > 0;
+    if (sD > 0) {
+        const int sA = csign(A, eA);
+        if (sA == kUncertain || sA == 0) return -1;
+        const float G = fmaf(2.f * A, C, -3.f * B * B);
+        const float eG = 2.f * (aA * eC + aC * eA + 3.f * eA * eC) + 3.f * (2.f * aB * eB + 3.f * eB * eB) +
+                         kE * (2.f * aA * aC + 3.f * aB * aB);
+        const int sG = csign(G, eG);
+        if (sG == kUncertain) return -1;
+        const int sV = sG * sA;
+        neg = neg || sV < 0;
+        pos = pos || sV > 0;
+    }
+    return (neg && pos) ? 1 : 0;
+}
+
+// eq. root_value on three cells with differences (da, db): ratio = (2 da - db) / (da - db);
+// fires iff 0 < ratio < 3, i.e. sign(2da - db) = sign(da - db) = sign(da - 2db) != 0.
+__device__ __forceinline__ int k2_cert(float da, float db) {
+    const float a = fabsf(da), b = fabsf(db);
+    const int sn = csign(fmaf(2.f, da, -db), kE * fmaf(2.f, a, b));
+    const int st = csign(fmaf(-2.f, db, da), kE * fmaf(2.f, b, a));
+    if (sn == kUncertain || st == kUncertain) return -1;
+    if (sn == 0 || sn != st) return 0;  // the three signs cannot agree (nearly linear data)
+    const int sd = csign(da - db, kE * (a + b));
+    if (sd == kUncertain) return -1;
+    return (sd != 0 && sn == sd) ? 1 : 0;
+}
+
+__device__ __forceinline__ bool switch_fires_f(float w0, float w1, float w2, float w3, int variant) {
+    const float d0 = w1 - w0, d1 = w2 - w1, d2 = w3 - w2;
+    int c;
+    if (variant == 1) {
+        const int c1 = k2_cert(d0, d1);
+        const int c2 = k2_cert(d1, d2);
+        c = (c1 == 1 || c2 == 1) ? 1 : ((c1 == 0 && c2 == 0) ? 0 : -1);
+    } else {
+        c = switch_v0_cert(d0, d1, d2);
+    }
+    if (c >= 0) return c == 1;
+    return switch_fires<double>((double)w0, (double)w1, (double)w2, (double)w3, variant);
+}
+
+// ENO stencil choice with the same certification (see eno_choice for the rule)
+__device__ __forceinline__ int eno_choice_f(float c0, float c1, float c2, float c3, float c4) {
+    const float dm = c1 - c0, dl = c2 - c1, dr = c3 - c2, dp = c4 - c3;
+    const float al = fabsf(dl), ar = fabsf(dr);
+    const int s1 = csign(ar - al, kE * (al + ar));
+    if (s1 != kUncertain) {
+        float ddl, ddr, e;
+        if (s1 > 0) {  // left extension: cells {i-1, i}
+            ddl = dl - dm;
+            ddr = dr - dl;
+            e = kE * (fabsf(dm) + 2.f * al + ar);
+        } else {
+            ddl = dr - dl;
+            ddr = dp - dr;
+            e = kE * (al + 2.f * ar + fabsf(dp));
+        }
+        const float adl = fabsf(ddl), adr = fabsf(ddr);
+        const int s2 = csign(adr - adl, e + kE * (adl + adr));
+        if (s2 != kUncertain) {
+            if (s1 > 0) return s2 > 0 ? 2 : 1;
+            return s2 > 0 ? 1 : 0;
+        }
+    }
+    return eno_choice<double>((double)c0, (double)c1, (double)c2, (double)c3, (double)c4);
+}
+
+// ---------------------------------------------------------------------------------------
+// Shape parameter.  num = w0 - 3 w1 + 3 w2 - w3, den = w0 - 15 w1 + 15 w2 - w3 (Table k3).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3, double eps_M, float guard) {
+    const double W0 = w0, W1 = w1, W2 = w2, W3 = w3;
+    const double num = (W0 - W3) + 3.0 * (W2 - W1);
+    const double den0 = (W0 - W3) + 15.0 * (W2 - W1);
+    if (fabs(den0) <= (double)guard) return 0.0f;
+    return (float)(num / (den0 + eps_M));
+}
+
+// exact value of the small-integer combination k0 w0 + k1 (w2 - w1)... as an unevaluated pair:
+// the differences are formed exactly with two_sum, then combined with compensated sums.
+__device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, float w3, float eps_M, float guard) {
+    float ah, al, bh, bl;
+    two_sum(w0, -w3, ah, al);  // w0 - w3 = ah + al exactly
+    two_sum(w2, -w1, bh, bl);  // w2 - w1 = bh + bl exactly
+    // num = a + 3 b, den = a + 15 b + eps_M; products by 3 and 15 made exact with fma
+    float p3 = 3.f * bh, p3e = fmaf(3.f, bh, -p3);
+    float p15 = 15.f * bh, p15e = fmaf(15.f, bh, -p15);
+    float nh, ne, dh, de;
+    two_sum(ah, p3, nh, ne);
+    two_sum(ah, p15, dh, de);
+    float nl = ne + (al + (p3e + 3.f * bl));
+    float dl = de + (al + (p15e + 15.f * bl));
+    if (fabsf(dh + dl) <= guard) return 0.0f;
+    float t;
+    two_sum(dh, eps_M, dh, t);
+    dl += t;
+    // renormalise the pairs
+    float s;
+    two_sum(nh, nl, s, nl);
+    nh = s;
+    two_sum(dh, dl, s, dl);
+    dh = s;
+    if (dh == 0.0f) return nh / dh;  // same 0/0 or inf behaviour as the plain quotient
+    // double-float quotient (nh + nl) / (dh + dl)
+    const float q1 = nh / dh;
+    const float p = q1 * dh;
+    const float pe = fmaf(q1, dh, -p);
+    const float r = ((nh - p) - pe) + fmaf(-q1, dl, nl);
+    const float q2 = r / dh;
+    return q1 + q2;
+}
+
+// The guard sets eta = 0 where the denominator is below eta_guard times the sum of the
+// magnitudes of its terms: such a denominator is round-off of the cell averages, and the
+// quotient would be noise amplified by 1/eps_M.
+__device__ __forceinline__ float eta_eval(float w0, float w1, float w2, float w3, const MethodParams& mp) {
+    const float guard = (float)mp.eta_guard * (fabsf(w0) + 15.f * fabsf(w1) + 15.f * fabsf(w2) + fabsf(w3));
+    return mp.eta_eval == 1 ? eta_doublefloat(w0, w1, w2, w3, (float)mp.eps_M, guard)
+                            : eta_fp64(w0, w1, w2, w3, mp.eps_M, guard);
+}
+
+// eta of the face whose eta stencil is (w0..w3), 0 where the switch fires; flag bit0 = switch
+__device__ __forceinline__ float face_eta(float w0, float w1, float w2, float w3, const MethodParams& mp,
+                                          uint32_t* flag) {
+    if (mp.scheme != NPW_RBF_ENO_ && mp.scheme != NPW_RBF_WENO_) return 0.0f;
+    if (mp.monotone_switch && switch_fires_f(w0, w1, w2, w3, mp.switch_variant)) {
+        *flag |= 1u;
+        return 0.0f;
+    }
+    return eta_eval(w0, w1, w2, w3, mp);
+}
+
+// ---------------------------------------------------------------------------------------
+// One cell: c[0..4] = cells i-2..i+2; eta_r = eta of face i+1/2, eta_l of face i-1/2.
+// Writes v^-_{i+1/2} and v^+_{i-1/2}.  Returns the ENO stencil (0 for WENO).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int cell_recon(const float* c, float eta_r, float eta_l, const MethodParams& mp,
+                                          float* vm, float* vp) {
+    float cm[3], cp[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float sm = 0.0f, sp = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float x = c[2 - r + j];
+            sm = fmaf(fmaf(pert_coef<float>(mp.rbf, r + 1, j), eta_r, poly_coef<float>(r + 1, j)), x, sm);
+            sp = fmaf(fmaf(pert_coef<float>(mp.rbf, r, j), eta_l, poly_coef<float>(r, j)), x, sp);
+        }
+        cm[r] = sm;
+        cp[r] = sp;
+    }
+    if (mp.scheme == NPW_ENO_ || mp.scheme == NPW_RBF_ENO_) {
+        const int r = eno_choice_f(c[0], c[1], c[2], c[3], c[4]);
+        *vm = r == 0 ? cm[0] : (r == 1 ? cm[1] : cm[2]);
+        *vp = r == 0 ? cp[0] : (r == 1 ? cp[1] : cp[2]);
+        return r;
+    }
+    // Jiang-Shu indicators (single precision), shared by both faces of the cell
+    float a, b, inv[3];
+    const float eps = (float)mp.eps_weno;
+    a = c[2] - 2.f * c[3] + c[4];
+    b = fmaf(3.f, c[2], fmaf(-4.f, c[3], c[4]));
+    float be = fmaf(13.f / 12.f * a, a, 0.25f * b * b) + eps;
+    inv[0] = 1.0f / (be * be);
+    a = c[1] - 2.f * c[2] + c[3];
+    b = c[1] - c[3];
+    be = fmaf(13.f / 12.f * a, a, 0.25f * b * b) + eps;
+    inv[1] = 1.0f / (be * be);
+    a = c[0] - 2.f * c[1] + c[2];
+    b = fmaf(-4.f, c[1], fmaf(3.f, c[2], c[0]));
+    be = fmaf(13.f / 12.f * a, a, 0.25f * b * b) + eps;
+    inv[2] = 1.0f / (be * be);
+    // v^-: d = (3/10, 3/5, 1/10); v^+: d = (1/10, 3/5, 3/10)
+    const float am0 = 0.3f * inv[0], am1 = 0.6f * inv[1], am2 = 0.1f * inv[2];
+    const float ap0 = 0.1f * inv[0], ap1 = 0.6f * inv[1], ap2 = 0.3f * inv[2];
+    *vm = fmaf(am0, cm[0], fmaf(am1, cm[1], am2 * cm[2])) / (am0 + am1 + am2);
+    *vp = fmaf(ap0, cp[0], fmaf(ap1, cp[1], ap2 * cp[2])) / (ap0 + ap1 + ap2);
+    return 0;
+}
+
+// Face form (used where the cells of a face see different data, as in the characteristic
+// variant): w[0..5] = cells i-2..i+3 of face i+1/2.  The neighbouring faces' eta values are
+// not needed: v^- uses this face's eta, v^+ of cell i+1 too.
+__device__ __forceinline__ uint32_t face_field(const float* w, const MethodParams& mp, float* vm, float* vp) {
+    uint32_t fl = 0;
+    const float eta = face_eta(w[1], w[2], w[3], w[4], mp, &fl);
+    float dummy;
+    const int rl = cell_recon(w, eta, eta, mp, vm, &dummy);
+    const int rr = cell_recon(w + 1, eta, eta, mp, &dummy, vp);
+    return fl | (uint32_t(rl & 3) << 2) | (uint32_t(rr & 3) << 4);
+}
+
+}  // namespace fast
+
+// the literal double-precision arithmetic for R = double, the mixed path for R = float
+template <typename R, typename D>
+__device__ __forceinline__ uint32_t face_field_any(const R* w, const MethodParams& mp, R* vm, R* vp) {
+    if constexpr (sizeof(R) == sizeof(float)) {
+        return fast::face_field(w, mp, vm, vp);
+    } else {
+        return face_field<R, D>(w, mp, vm, vp);
+    }
+}
+
+// All M fields at one face from the 6 x M stencil W[j*M + k] (cells i-2..i+3).  For the
+// characteristic variant the fields are projected by L, reconstructed, and mapped back by R.
+template <typename R, typename D, int KIND, int M, bool CHAR>
+__device__ __forceinline__ bool face_all(const R* S, const MethodParams& mp, R* vm, R* vp, uint32_t* flags) {
+    if (CHAR) {
+        R Rm[3][3], Lm[3][3];
+        if (!euler_eig<R>(S + 2 * M, S + 3 * M, R(mp.gamma), Rm, Lm)) return false;
+        R wm[3], wp[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R line[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                R s = R(0.0);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) s += Lm[a][k] * S[j * M + k];
+                line[j] = s;
+            }
+            flags[a] = face_field_any<R, D>(line, mp, &wm[a], &wp[a]);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            R sm = R(0.0), sp = R(0.0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                sm += Rm[k][a] * wm[a];
+                sp += Rm[k][a] * wp[a];
+            }
+            vm[k] = sm;
+            vp[k] = sp;
+        }
+        return true;
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        R line[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) line[j] = S[j * M + k];
+        flags[k] = face_field_any<R, D>(line, mp, &vm[k], &vp[k]);
+    }
+    return true;
+}
+
+}  // namespace npw

@@ -26,13 +26,14 @@ struct MethodParams {
     int monotone_switch;
     int switch_variant;
     int characteristic;
-    int pad_;
+    int eta_eval;  // mixed precision: 0 = FP64 division, 1 = exact double-float quotient
     double eps_M;
     double eps_weno;
     double gamma;
     double adv_speed;
     double adv_speed_y;
     double inflow[4];
+    double eta_guard;  // resolved threshold (0 = off)
 };
 
 // One 1D problem (device copy of npw_instance plus its tile range).

@@ -12,6 +12,7 @@
 #include <cstdint>
 
 #include "npw_device.cuh"
+#include "npw_fast.cuh"
 #include "npw_internal.h"
 
 namespace npw {
@@ -283,6 +284,112 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_kernel(Stage1DArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// The mixed-precision fused stage kernel (1D, component-wise).  Phases over the tile with
+// three ghost cells per side, extended index e = 0 .. cnt+5 for cell c0 - 3 + e:
+//   F: eta (and the switch) once per face, faces between e-1 and e for e = 2 .. cnt+4;
+//   C: once per cell e = 2 .. cnt+3: smoothness indicators, weights and the two face values
+//      v^-_{e+1/2} (with the eta of face e|e+1) and v^+_{e-1/2} (eta of face e-1|e);
+//   U: cells e = 3 .. cnt+2: Lax-Friedrichs fluxes of both faces, eq. PDE1, stage combination.
+// Shared memory (floats): u, eta, v^-, v^+, each (tile + 6) * M.
+// ---------------------------------------------------------------------------------------
+template <int KIND>
+__global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a) {
+    constexpr int M = kind_m<KIND>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    __shared__ int redbad[32];
+    const int span_max = a.tile + 6;
+    float* su = reinterpret_cast<float*>(smem_raw);
+    float* se = su + span_max * M;
+    float* svm = se + span_max * M;
+    float* svp = svm + span_max * M;
+
+    const Tile td = a.tiles[blockIdx.x];
+    const InstDev in = a.inst[td.inst];
+    Ctl* ctl = a.ctl + td.inst;
+    if (*(volatile int32_t*)&ctl->done) return;  // uniform over the CTA
+    const int64_t n = in.n;
+    const int c0 = td.start;
+    const int cnt = (int)((n - c0) < a.tile ? (n - c0) : a.tile);
+    const float* uin = reinterpret_cast<const float*>(a.uin) + in.off;
+    const int span = cnt + 6;
+    for (int idx = threadIdx.x; idx < span * M; idx += blockDim.x) {
+        const int k = idx / span;
+        const int j = idx - k * span;
+        su[j * M + k] = line_get<float>(uin + k * n, n, 1, (int64_t)c0 - 3 + j, in.bc, a.mp.inflow[k]);
+    }
+    const double dt = *(volatile double*)&ctl->dt;
+    const float alpha = (float)*(volatile double*)&ctl->alpha;
+    __syncthreads();
+
+    // F: faces between extended cells e-1 and e
+    for (int idx = threadIdx.x; idx < (cnt + 3) * M; idx += blockDim.x) {
+        const int e = 2 + idx / M, k = idx - (e - 2) * M;
+        uint32_t fl = 0;
+        se[e * M + k] = fast::face_eta(su[(e - 2) * M + k], su[(e - 1) * M + k], su[e * M + k], su[(e + 1) * M + k],
+                                       a.mp, &fl);
+    }
+    __syncthreads();
+    // C: cells
+    for (int idx = threadIdx.x; idx < (cnt + 2) * M; idx += blockDim.x) {
+        const int e = 2 + idx / M, k = idx - (e - 2) * M;
+        float c[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) c[j] = su[(e - 2 + j) * M + k];
+        float vm, vp;
+        fast::cell_recon(c, se[(e + 1) * M + k], se[e * M + k], a.mp, &vm, &vp);
+        svm[e * M + k] = vm;
+        svp[e * M + k] = vp;
+    }
+    __syncthreads();
+    // U: cells
+    float* uout = reinterpret_cast<float*>(a.uout) + in.off;
+    const float* un = reinterpret_cast<const float*>(a.un) + in.off;
+    const float lam = (float)(dt / in.dx);
+    double vmax = 0.0;
+    bool bad = false;
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int e = q + 3;
+        float hl[M], hr[M], U[M];
+        lf_flux<float, KIND, M>(svm + (e - 1) * M, svp + e * M, alpha, a.mp, 0, hl);
+        lf_flux<float, KIND, M>(svm + e * M, svp + (e + 1) * M, alpha, a.mp, 0, hr);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const float du = lam * (hl[k] - hr[k]);
+            const float uk = su[e * M + k];
+            float o;
+            if (a.stage == 0) {
+                o = uk + du;
+            } else if (a.stage == 1) {
+                o = fmaf(0.75f, un[k * n + c0 + q], 0.25f * (uk + du));
+            } else {
+                o = fmaf(1.0f / 3.0f, un[k * n + c0 + q], (2.0f / 3.0f) * (uk + du));
+            }
+            uout[k * n + c0 + q] = o;
+            U[k] = o;
+            bad |= !finite_(o);
+        }
+        if (a.stage == 2) {
+            const double s = (double)wave_speed<float, KIND>(U, a.mp, 0);
+            bad |= !finite_(s);
+            vmax = s > vmax ? s : vmax;
+        }
+    }
+    if (a.stage == 2 && a.advance) {
+        const double b = block_max_nan(vmax, bad, red, redbad);
+        if (threadIdx.x == 0) {
+            atomicMax(&ctl->alpha_next_bits, (unsigned long long)__double_as_longlong(b));
+            __threadfence();
+            const unsigned prev = atomicAdd(&ctl->tiles_done, 1u);
+            if (prev == (unsigned)in.ntiles - 1u) {
+                __threadfence();
+                finalize_1d(ctl, in);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // 2D dimension-by-dimension stage kernel (component-wise).  Tile TX x TY cells; shared
 // memory holds the (TX + 6) x (TY + 6) input block, the x-face fluxes (TX + 1) x TY and
 // the y-face fluxes TX x (TY + 1).
@@ -528,7 +635,32 @@ struct Launchers {
         return cudaGetLastError();
     }
 
+    template <int KIND>
+    static cudaError_t stage_fast(const Stage1DArgs& a, cudaStream_t s) {
+        constexpr int M = kind_m<KIND>();
+        const size_t smem = (size_t)(a.tile + 6) * 4 * M * sizeof(float);
+        auto kern = stage1d_fast_kernel<KIND>;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        kern<<<a.ntiles, THREADS_1D, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+
     static cudaError_t stage1d(const Stage1DArgs& a, int kind, cudaStream_t s) {
+        if constexpr (sizeof(R) == sizeof(float)) {
+            if (!a.mp.characteristic) {
+                switch (kind) {
+                    case NPW_FLUX_ADVECTION: return stage_fast<NPW_FLUX_ADVECTION_>(a, s);
+                    case NPW_FLUX_BURGERS: return stage_fast<NPW_FLUX_BURGERS_>(a, s);
+                    case NPW_FLUX_EULER1D: return stage_fast<NPW_FLUX_EULER1D_>(a, s);
+                    default: return cudaErrorInvalidValue;
+                }
+            }
+        }
         switch (kind) {
             case NPW_FLUX_ADVECTION: return stage_k<NPW_FLUX_ADVECTION_, false>(a, s);
             case NPW_FLUX_BURGERS: return stage_k<NPW_FLUX_BURGERS_, false>(a, s);

@@ -26,8 +26,9 @@ NPW_FP64, NPW_FP32_MIXED = 0, 1
 class npw_params(C.Structure):
     _fields_ = [("k", C.c_int32), ("scheme", C.c_int32), ("rbf", C.c_int32), ("monotone_switch", C.c_int32),
                 ("switch_variant", C.c_int32), ("characteristic", C.c_int32), ("precision", C.c_int32),
-                ("pad_", C.c_int32), ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
-                ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4)]
+                ("eta_eval", C.c_int32), ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
+                ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4),
+                ("eta_guard", C.c_double)]
 
 
 class npw_solve_stats(C.Structure):
@@ -55,19 +56,22 @@ class Params:
     switch_variant: int = 0
     characteristic: int = 0
     precision: int = NPW_FP64
+    eta_eval: int = 0
     eps_M: float = 1e-12
     eps_weno: float = 1e-6
     gamma: float = 1.4
     adv_speed: float = 1.0
     adv_speed_y: float = 1.0
     inflow: Sequence[float] = (0.0, 0.0, 0.0, 0.0)
+    eta_guard: float = 0.0
     k: int = 3
 
     def c(self) -> npw_params:
         p = npw_params()
-        for f in ("k", "scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "precision"):
+        for f in ("k", "scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "precision",
+                  "eta_eval"):
             setattr(p, f, int(getattr(self, f)))
-        for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y"):
+        for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "eta_guard"):
             setattr(p, f, float(getattr(self, f)))
         for i in range(4):
             p.inflow[i] = float(self.inflow[i]) if i < len(self.inflow) else 0.0

@@ -18,6 +18,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
+MIXED_GUARD = 8.0 * 2.0 ** -24  # the mixed path's automatic eta guard, given to the oracle
 SCHEMES = [(O.ENO, 0), (O.WENO_JS, 1), (O.RBF_ENO, 2), (O.RBF_WENO, 3)]
 
 
@@ -39,7 +40,8 @@ def _dev(x, dtype=torch.float64):
 def _gparams(npw, o: "O.Params", precision=0):
     return npw.Params(scheme=o.scheme, rbf=o.rbf, monotone_switch=o.monotone_switch, switch_variant=o.switch_variant,
                       characteristic=o.characteristic, precision=precision, eps_M=o.eps_M, eps_weno=o.eps_weno,
-                      gamma=o.gamma, adv_speed=o.adv_speed, adv_speed_y=o.adv_speed_y, inflow=o.inflow)
+                      gamma=o.gamma, adv_speed=o.adv_speed, adv_speed_y=o.adv_speed_y, inflow=o.inflow,
+                      eta_guard=o.eta_guard if o.eta_guard > 0 else 0.0)
 
 
 def _mixed_data(n, seed):
@@ -218,7 +220,7 @@ def test_burgers_batch_mixed_precision_accuracy(npw):
     table, total = npw.make_instances([it.n for it in inst], [it.dx for it in inst], [1.5] * 16, [0.5] * 16,
                                       [O.PERIODIC] * 16)
     arena = _dev(np.concatenate([it.u0[0] for it in inst]), torch.float32)
-    op = O.Params(rbf=O.GA)
+    op = O.Params(rbf=O.GA, eta_guard=MIXED_GUARD)
     status, stats = npw.npweno_batch_solve(arena, table, 1, O.BURGERS, _gparams(npw, op, precision=1))
     assert status == 0
     a = arena.cpu().numpy().astype(np.float64)
@@ -236,7 +238,7 @@ def test_burgers_batch_mixed_precision_accuracy(npw):
 def test_mixed_precision_single_stage(npw):
     """One RK3 step from float-representable data: FP32 arithmetic bound ~ 1e-6 relative."""
     u = _mixed_data(3000, 9).astype(np.float32).astype(np.float64)
-    op = O.Params()
+    op = O.Params(eta_guard=MIXED_GUARD)
     ref, _ = O.rk3_step(u, 1.0 / 3000, 0.3 / 3000, O.BURGERS, O.PERIODIC, op)
     gu = _dev(u, torch.float32)
     npw.npweno_rk3_step(gu, 1.0 / 3000, 0.3 / 3000, O.BURGERS, O.PERIODIC, _gparams(npw, op, precision=1))
@@ -290,3 +292,53 @@ def test_zero_time_and_minimum_size(npw):
     ref, rst = O.solve(u0, dx, 0.7, 0.5, O.ADVECTION, O.PERIODIC, O.Params())
     st = npw.npweno_solve(gu, dx, 0.7, 0.5, npw.NPW_FLUX_ADVECTION, 0, npw.Params())
     assert st["steps"] == rst["steps"] and _rel(gu.cpu().numpy(), ref) <= FP64_TOL
+
+
+# ------------------------------------------------------------------------------ mixed-precision decisions
+def _near_tie_data(n, seed):
+    """Data that puts the switch and ENO decisions close to their thresholds: smooth waves
+    with extrema on and near faces, constant and linear stretches, tiny oscillations."""
+    g = np.random.default_rng(seed)
+    x = (np.arange(n) + 0.5) / n
+    u = 1.0 + 0.5 * np.sin(4 * np.pi * x)
+    u[n // 5: n // 5 + 20] = 0.75
+    u[n // 3: n // 3 + 30] = np.linspace(0.2, 0.4, 30)
+    u[n // 2: n // 2 + 40] += 1e-6 * g.normal(size=40)
+    u[2 * n // 3:] = np.round(u[2 * n // 3:] * 64) / 64  # plateaus with exact steps
+    return u.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("scheme", [s for s, _ in SCHEMES])
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("eta_eval", [0, 1])
+def test_reconstruct_mixed_decisions_match_fp64(npw, scheme, variant, eta_eval):
+    """NPW_FP32_MIXED: switch flags and ENO choices equal the double-precision decisions of the
+    oracle on the same float data (except oracle-marked near ties); values within float
+    arithmetic of the oracle."""
+    for n in (64, 1500, 4097):
+        u = _near_tie_data(n, n) if n != 64 else _mixed_data(n, 5).astype(np.float32).astype(np.float64)
+        op = O.Params(scheme=scheme, switch_variant=variant, eta_guard=MIXED_GUARD)
+        vm, vp, fl, _ = O.reconstruct(u, O.PERIODIC, op)
+        gp = _gparams(npw, op, precision=1)
+        gp.eta_eval = eta_eval
+        gvm, gvp, gfl = npw.npweno_reconstruct(_dev(u, torch.float32), O.PERIODIC, gp)
+        gvm = gvm.cpu().numpy().astype(np.float64)
+        gvp = gvp.cpu().numpy().astype(np.float64)
+        gfl = gfl.cpu().numpy()
+        ok = (fl & TIES) == 0
+        assert np.array_equal(gfl[ok] & 0x3D, fl[ok] & 0x3D), n
+        scale = np.abs(u).max()
+        assert np.abs(gvm[ok] - vm[ok]).max() <= 2e-6 * scale, n
+        assert np.abs(gvp[ok] - vp[ok]).max() <= 2e-6 * scale, n
+
+
+def test_mixed_precision_full_burgers_instance_stays_finite(npw):
+    """The instance of the 4096-instance batch (N = 5612) whose float-state plateau noise made
+    the eta denominator exactly zero: with the round-off guard it finishes, and it stays within
+    the mixed-precision bars of the FP64 oracle."""
+    inst = I.burgers_batch(count=4096, seed_index=1)
+    it = max((x for x in inst if x.n == 5612), key=lambda x: x.n)
+    u = _dev(it.u0[0], torch.float32)
+    st = npw.npweno_solve(u, it.dx, 1.5, 0.5, O.BURGERS, O.PERIODIC, npw.Params(rbf=npw.NPW_RBF_GA, precision=1))
+    assert st["status"] == 0 and st["t"] == 1.5
+    assert np.all(np.isfinite(u.cpu().numpy()))

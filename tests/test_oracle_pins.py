@@ -190,3 +190,21 @@ def test_periodic_faces_coincide():
     u = g.normal(size=37)
     vm, vp, fl, eta = O.reconstruct(u, O.PERIODIC, O.Params())
     assert vm[0] == vm[-1] and vp[0] == vp[-1] and eta[0] == eta[-1]
+
+
+def test_eta_guard_on_unresolved_denominator():
+    """Cell averages of x^3 around a face: the cubic is monotone with zero slope at the face, so
+    the eta denominator is exactly 0 and eta = num / eps_M.  The optional guard (a reading for
+    float states, off by default) sets eta = 0 there and leaves resolved faces alone."""
+    edges = np.arange(-5.0, 6.0)
+    P = lambda x: x ** 4 / 4
+    avg = P(edges[1:]) - P(edges[:-1])  # exact averages of x^3 on unit cells
+    face = 5  # face x = 0 between cell 4 and cell 5
+    p0 = O.Params(scheme=O.RBF_WENO, monotone_switch=1)
+    _, _, _, eta0 = O.reconstruct(avg, O.TRANSMISSIVE, p0)
+    assert abs(eta0[face]) > 1e10  # num / eps_M
+    p1 = O.Params(scheme=O.RBF_WENO, monotone_switch=1, eta_guard=8 * 2.0 ** -24)
+    _, _, _, eta1 = O.reconstruct(avg, O.TRANSMISSIVE, p1)
+    assert eta1[face] == 0.0
+    other = [f for f in range(3, 9) if f != face]
+    np.testing.assert_array_equal(eta1[other], eta0[other])
