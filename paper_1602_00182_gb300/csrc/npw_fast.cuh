@@ -23,6 +23,26 @@
 namespace npw {
 namespace fast {
 
+// float copies of the method parameters, converted once per thread
+struct FParams {
+    float eps_weno, eps_M_f, eta_guard;
+    double eps_M;
+    int scheme, rbf, monotone_switch, switch_variant, eta_eval;
+};
+__device__ __forceinline__ FParams fparams(const MethodParams& mp) {
+    FParams f;
+    f.eps_weno = (float)mp.eps_weno;
+    f.eps_M_f = (float)mp.eps_M;
+    f.eta_guard = (float)mp.eta_guard;
+    f.eps_M = mp.eps_M;
+    f.scheme = mp.scheme;
+    f.rbf = mp.rbf;
+    f.monotone_switch = mp.monotone_switch;
+    f.switch_variant = mp.switch_variant;
+    f.eta_eval = mp.eta_eval;
+    return f;
+}
+
 constexpr float kU = 5.9604645e-08f;  // 2^-24, unit roundoff of float
 constexpr float kE = 6.0f * kU;       // bound factor for short small-integer combinations
 constexpr int kUncertain = 2;
@@ -143,12 +163,27 @@ __device__ __forceinline__ int eno_choice_f(float c0, float c1, float c2, float 
 // ---------------------------------------------------------------------------------------
 // Shape parameter.  num = w0 - 3 w1 + 3 w2 - w3, den = w0 - 15 w1 + 15 w2 - w3 (Table k3).
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3, double eps_M, float guard) {
+// FP64 evaluation.  The numerator and denominator are exact in double (small-integer
+// combinations of floats).  The quotient is formed with a float reciprocal seed refined by
+// Newton steps in double: r = r0 (2 - den r0) twice gives |r - 1/den| < 2^-50 / |den|, then
+// q = num r and one residual correction q += (num - q den) r, so |q - num/den| is within a
+// few units of the last place of double before the result is rounded to float.
+__device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3, const FParams& fp, float guard) {
     const double W0 = w0, W1 = w1, W2 = w2, W3 = w3;
-    const double num = (W0 - W3) + 3.0 * (W2 - W1);
-    const double den0 = (W0 - W3) + 15.0 * (W2 - W1);
-    if (fabs(den0) <= (double)guard) return 0.0f;
-    return (float)(num / (den0 + eps_M));
+    const double a = W0 - W3, b = W2 - W1;
+    const double num = fma(3.0, b, a);
+    const double den0 = fma(15.0, b, a);
+    const float den0f = (float)den0;
+    if (fabsf(den0f) <= guard) return 0.0f;
+    const double den = den0 + fp.eps_M;
+    const float denf = (float)den;
+    if (!(fabsf(denf) > 1e-30f && fabsf(denf) < 1e30f)) return (float)(num / den);  // outside the seed's range
+    double r = (double)(1.0f / denf);
+    r = fma(r, fma(-den, r, 1.0), r);
+    r = fma(r, fma(-den, r, 1.0), r);
+    double q = num * r;
+    q = fma(fma(-q, den, num), r, q);
+    return (float)q;
 }
 
 // exact value of the small-integer combination k0 w0 + k1 (w2 - w1)... as an unevaluated pair:
@@ -188,28 +223,27 @@ __device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, f
 // The guard sets eta = 0 where the denominator is below eta_guard times the sum of the
 // magnitudes of its terms: such a denominator is round-off of the cell averages, and the
 // quotient would be noise amplified by 1/eps_M.
-__device__ __forceinline__ float eta_eval(float w0, float w1, float w2, float w3, const MethodParams& mp) {
-    const float guard = (float)mp.eta_guard * (fabsf(w0) + 15.f * fabsf(w1) + 15.f * fabsf(w2) + fabsf(w3));
-    return mp.eta_eval == 1 ? eta_doublefloat(w0, w1, w2, w3, (float)mp.eps_M, guard)
-                            : eta_fp64(w0, w1, w2, w3, mp.eps_M, guard);
+__device__ __forceinline__ float eta_eval(float w0, float w1, float w2, float w3, const FParams& fp) {
+    const float guard = fp.eta_guard * (fabsf(w0) + 15.f * fabsf(w1) + 15.f * fabsf(w2) + fabsf(w3));
+    return fp.eta_eval == 1 ? eta_doublefloat(w0, w1, w2, w3, fp.eps_M_f, guard) : eta_fp64(w0, w1, w2, w3, fp, guard);
 }
 
 // eta of the face whose eta stencil is (w0..w3), 0 where the switch fires; flag bit0 = switch
-__device__ __forceinline__ float face_eta(float w0, float w1, float w2, float w3, const MethodParams& mp,
+__device__ __forceinline__ float face_eta(float w0, float w1, float w2, float w3, const FParams& fp,
                                           uint32_t* flag) {
-    if (mp.scheme != NPW_RBF_ENO_ && mp.scheme != NPW_RBF_WENO_) return 0.0f;
-    if (mp.monotone_switch && switch_fires_f(w0, w1, w2, w3, mp.switch_variant)) {
+    if (fp.scheme != NPW_RBF_ENO_ && fp.scheme != NPW_RBF_WENO_) return 0.0f;
+    if (fp.monotone_switch && switch_fires_f(w0, w1, w2, w3, fp.switch_variant)) {
         *flag |= 1u;
         return 0.0f;
     }
-    return eta_eval(w0, w1, w2, w3, mp);
+    return eta_eval(w0, w1, w2, w3, fp);
 }
 
 // ---------------------------------------------------------------------------------------
 // One cell: c[0..4] = cells i-2..i+2; eta_r = eta of face i+1/2, eta_l of face i-1/2.
 // Writes v^-_{i+1/2} and v^+_{i-1/2}.  Returns the ENO stencil (0 for WENO).
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ int cell_recon(const float* c, float eta_r, float eta_l, const MethodParams& mp,
+__device__ __forceinline__ int cell_recon(const float* c, float eta_r, float eta_l, const FParams& mp,
                                           float* vm, float* vp) {
     float cm[3], cp[3];
 #pragma unroll
@@ -232,7 +266,7 @@ __device__ __forceinline__ int cell_recon(const float* c, float eta_r, float eta
     }
     // Jiang-Shu indicators (single precision), shared by both faces of the cell
     float a, b, inv[3];
-    const float eps = (float)mp.eps_weno;
+    const float eps = mp.eps_weno;
     a = c[2] - 2.f * c[3] + c[4];
     b = fmaf(3.f, c[2], fmaf(-4.f, c[3], c[4]));
     float be = fmaf(13.f / 12.f * a, a, 0.25f * b * b) + eps;
@@ -256,8 +290,9 @@ __device__ __forceinline__ int cell_recon(const float* c, float eta_r, float eta
 // Face form (used where the cells of a face see different data, as in the characteristic
 // variant): w[0..5] = cells i-2..i+3 of face i+1/2.  The neighbouring faces' eta values are
 // not needed: v^- uses this face's eta, v^+ of cell i+1 too.
-__device__ __forceinline__ uint32_t face_field(const float* w, const MethodParams& mp, float* vm, float* vp) {
+__device__ __forceinline__ uint32_t face_field(const float* w, const MethodParams& mp0, float* vm, float* vp) {
     uint32_t fl = 0;
+    const FParams mp = fparams(mp0);
     const float eta = face_eta(w[1], w[2], w[3], w[4], mp, &fl);
     float dummy;
     const int rl = cell_recon(w, eta, eta, mp, vm, &dummy);

@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
     }
     const double dt = *(volatile double*)&ctl->dt;
     const float alpha = (float)*(volatile double*)&ctl->alpha;
+    const fast::FParams fp = fast::fparams(a.mp);
     __syncthreads();
 
     // F: faces between extended cells e-1 and e
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
         const int e = 2 + idx / M, k = idx - (e - 2) * M;
         uint32_t fl = 0;
         se[e * M + k] = fast::face_eta(su[(e - 2) * M + k], su[(e - 1) * M + k], su[e * M + k], su[(e + 1) * M + k],
-                                       a.mp, &fl);
+                                       fp, &fl);
     }
     __syncthreads();
     // C: cells
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
 #pragma unroll
         for (int j = 0; j < 5; ++j) c[j] = su[(e - 2 + j) * M + k];
         float vm, vp;
-        fast::cell_recon(c, se[(e + 1) * M + k], se[e * M + k], a.mp, &vm, &vp);
+        fast::cell_recon(c, se[(e + 1) * M + k], se[e * M + k], fp, &vm, &vp);
         svm[e * M + k] = vm;
         svp[e * M + k] = vp;
     }
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
     float* uout = reinterpret_cast<float*>(a.uout) + in.off;
     const float* un = reinterpret_cast<const float*>(a.un) + in.off;
     const float lam = (float)(dt / in.dx);
-    double vmax = 0.0;
+    float vmaxf = 0.0f;
     bool bad = false;
     for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
         const int e = q + 3;
@@ -370,13 +371,13 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
             bad |= !finite_(o);
         }
         if (a.stage == 2) {
-            const double s = (double)wave_speed<float, KIND>(U, a.mp, 0);
+            const float s = wave_speed<float, KIND>(U, a.mp, 0);
             bad |= !finite_(s);
-            vmax = s > vmax ? s : vmax;
+            vmaxf = s > vmaxf ? s : vmaxf;
         }
     }
     if (a.stage == 2 && a.advance) {
-        const double b = block_max_nan(vmax, bad, red, redbad);
+        const double b = block_max_nan((double)vmaxf, bad, red, redbad);
         if (threadIdx.x == 0) {
             atomicMax(&ctl->alpha_next_bits, (unsigned long long)__double_as_longlong(b));
             __threadfence();
