@@ -82,6 +82,10 @@ typedef struct {
     double eta_guard;        /* eta = 0 where |den| <= eta_guard * (|w0| + 15|w1| + 15|w2| + |w3|), i.e.
                                 where the eta denominator is below the round-off of its cell averages;
                                 0 = automatic (off for NPW_FP64, 8 * 2^-24 for NPW_FP32_MIXED), < 0 = off */
+    int32_t batch_mode;      /* npweno_batch_solve, NPW_FP32_MIXED: 0 = instances whose state fits in one
+                                CTA's shared memory run whole in one CTA (resident), the rest through the
+                                per-stage kernels; 1 = every instance through the per-stage kernels */
+    int32_t pad_;
 } npw_params;
 
 typedef struct {
@@ -165,7 +169,12 @@ npw_status npweno_solve(void* u, int64_t n, int32_t m, double dx, double t_end, 
 /*
  * Many independent 1D problems in one arena (device), advanced together by the same fused
  * stage kernels over a work list of (instance, tile) pairs; each instance keeps its own t,
- * dt and alpha on the device and drops out of the work when it reaches its t_end.
+ * dt and alpha on the device and drops out of the work when it reaches its t_end.  In
+ * NPW_FP32_MIXED (batch_mode 0, component-wise) an instance whose state fits in one CTA's
+ * shared memory (n up to about 10000 for m = 1, 3400 for m = 3) is instead solved whole by one
+ * CTA: all its RK3 steps run in shared memory and only the initial and final states cross HBM;
+ * those CTAs run on library-owned side streams concurrently with the per-stage work and the
+ * call returns when both are done.
  * inst (host, count entries) describes the instances; out (host, count entries, may be
  * NULL) receives per-instance statistics.  The returned status is NPW_OK when every
  * instance finished; otherwise the first failing instance's status.

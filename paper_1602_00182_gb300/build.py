@@ -3,7 +3,9 @@
 Three translation units are compiled in parallel with nvcc and linked into one shared
 object next to this file:
   npw_fp64.cu  -- double-precision kernels, --fmad=false (each operation rounded as written)
-  npw_fp32.cu  -- mixed-precision kernels
+  npw_fp32.cu  -- mixed-precision kernels, also --fmad=false: every fused multiply-add is an
+                  explicit fmaf, so the per-stage and the resident kernels (and any batch mix)
+                  produce the same bits from the same data
   npw_api.cu   -- host runtime and the C ABI
   npw_noalloc.cu -- npweno_rk3_step_noalloc and its fixed device scratch array
 """
@@ -25,7 +27,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}
           "--expt-relaxed-constexpr", "-diag-suppress", "128"]
 UNITS = {
     "npw_fp64.cu": ["--fmad=false"],
-    "npw_fp32.cu": [],
+    "npw_fp32.cu": ["--fmad=false"],
     "npw_api.cu": [],
     "npw_noalloc.cu": [],
 }

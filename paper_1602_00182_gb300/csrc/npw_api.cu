@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <string>
 #include <mutex>
 #include <utility>
@@ -55,6 +56,7 @@ npw_status check_params(const npw_params* p) {
     if (p->switch_variant < 0 || p->switch_variant > 1) return fail(NPW_EINVAL, "bad switch_variant");
     if (p->precision != NPW_FP64 && p->precision != NPW_FP32_MIXED) return fail(NPW_EINVAL, "bad precision");
     if (p->eta_eval < 0 || p->eta_eval > 1) return fail(NPW_EINVAL, "bad eta_eval %d", p->eta_eval);
+    if (p->batch_mode < 0 || p->batch_mode > 1) return fail(NPW_EINVAL, "bad batch_mode %d", p->batch_mode);
     if (!(p->eps_weno > 0.0)) return fail(NPW_EINVAL, "eps_weno must be > 0");
     if (!(p->gamma > 1.0)) return fail(NPW_EINVAL, "gamma must be > 1");
     return NPW_OK;
@@ -104,12 +106,14 @@ npw_status check_bc(int bc) {
 // instance table, the per-instance control words, the tile table and the poll words.
 // ---------------------------------------------------------------------------------------
 struct Layout1D {
-    size_t u1, u2, inst, ctl, tiles, poll, total;
+    size_t u1, u2, inst, ctl, tiles, poll, list, total;
 };
 
 Layout1D layout_1d(int64_t arena_elems, int count, int64_t ntiles, size_t esz) {
     Layout1D L{};
     size_t o = 0;
+    L.list = o;
+    o = align256(o + sizeof(int32_t) * (size_t)count);
     L.u1 = o;
     o = align256(o + (size_t)arena_elems * esz);
     L.u2 = o;
@@ -263,7 +267,7 @@ __global__ void ctl_start_kernel(Ctl* ctl, const InstDev* inst, int count, int m
     }
     const InstDev in = inst[i];
     c->t = 0.0;
-    if (!(c->t < in.t_end)) {
+    if (!(c->t < in.t_end) || in.ntiles == 0) {  // finished, or solved by the resident kernel
         c->done = 1;
         return;
     }
@@ -369,10 +373,26 @@ struct Run1D {
     Layout1D L;
     int64_t ntiles;
     cudaStream_t s;
+    std::vector<char> resident;  // per instance: solved by the resident kernel
+    std::vector<cudaEvent_t> joins;  // side-stream work the caller's stream waits for at the end
 };
+
+// instances the resident kernel can take: float state, component-wise, fits in shared memory
+bool resident_ok(const npw_params* p, int m, int64_t n) {
+    return p->precision == NPW_FP32_MIXED && !p->characteristic && p->batch_mode == 0 &&
+           npw::resident_smem_bytes(n, m) <= npw::RESIDENT_SMEM_MAX;
+}
+
+int64_t tiles_for(const Run1D& r, const npw_instance* inst, int count) {
+    int64_t nt = 0;
+    for (int i = 0; i < count; ++i)
+        if (r.resident.empty() || !r.resident[i]) nt += tiles_of(inst[i].n);
+    return nt;
+}
 
 template <typename R>
 npw_status run_step_kernels(const Run1D& r, int advance) {
+    if (r.ntiles == 0) return NPW_OK;
     npw::Stage1DArgs a{};
     a.inst = reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst);
     a.ctl = reinterpret_cast<npw::Ctl*>(r.ws + r.L.ctl);
@@ -416,18 +436,21 @@ npw_status setup_1d(Run1D& r, const npw_instance* inst, int count, double dt_fix
         hi[i].t_end = inst[i].t_end;
         hi[i].cfl = inst[i].cfl;
         hi[i].bc = inst[i].bc;
-        hi[i].ntiles = (int32_t)tiles_of(inst[i].n);
+        const bool res = !r.resident.empty() && r.resident[i];
+        hi[i].ntiles = res ? 0 : (int32_t)tiles_of(inst[i].n);
         for (int64_t t = 0; t < hi[i].ntiles; ++t) ht.push_back(npw::Tile{i, (int32_t)(t * npw::TILE_1D)});
     }
     // pageable source: each call returns once the data is staged
     NPW_CUDA(cudaMemcpyAsync(r.ws + r.L.inst, hi.data(), sizeof(npw::InstDev) * count, cudaMemcpyHostToDevice, r.s));
-    NPW_CUDA(cudaMemcpyAsync(r.ws + r.L.tiles, ht.data(), sizeof(npw::Tile) * ht.size(), cudaMemcpyHostToDevice, r.s));
+    if (!ht.empty())
+        NPW_CUDA(cudaMemcpyAsync(r.ws + r.L.tiles, ht.data(), sizeof(npw::Tile) * ht.size(), cudaMemcpyHostToDevice, r.s));
     npw::Ctl* ctl = reinterpret_cast<npw::Ctl*>(r.ws + r.L.ctl);
     const npw::InstDev* di = reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst);
     const unsigned blocks = (unsigned)((count + 127) / 128);
     npw::ctl_start_kernel<<<blocks, 128, 0, r.s>>>(ctl, di, count, 0, 0.0);
     NPW_CUDA(cudaGetLastError());
-    cudaError_t e = r.fp32 ? npw::launch_alpha_init<float>(r.arena, di, ctl,
+    cudaError_t e = r.ntiles == 0 ? cudaSuccess
+                  : r.fp32 ? npw::launch_alpha_init<float>(r.arena, di, ctl,
                                                            reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles),
                                                            (int)r.ntiles, npw::TILE_1D, r.m, r.kind, r.mp, r.s)
                            : npw::launch_alpha_init<double>(r.arena, di, ctl,
@@ -477,6 +500,87 @@ npw_status collect_stats(const Run1D& r, npw_solve_stats* out) {
     return NPW_OK;
 }
 
+// Library-owned side streams (created once per device) for the resident launches.
+struct SideStreams {
+    cudaStream_t st[4];
+    cudaEvent_t fork, join[4];
+    bool ok = false;
+};
+std::mutex g_side_mu;
+SideStreams g_side[64];
+
+npw_status side_streams(SideStreams** out) {
+    int dev = 0;
+    NPW_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(NPW_ECUDA, "device index out of range");
+    std::lock_guard<std::mutex> g(g_side_mu);
+    SideStreams& s = g_side[dev];
+    if (!s.ok) {
+        for (int k = 0; k < 4; ++k) {
+            NPW_CUDA(cudaStreamCreateWithFlags(&s.st[k], cudaStreamNonBlocking));
+            NPW_CUDA(cudaEventCreateWithFlags(&s.join[k], cudaEventDisableTiming));
+        }
+        NPW_CUDA(cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming));
+        s.ok = true;
+    }
+    *out = &s;
+    return NPW_OK;
+}
+
+// Launch the resident instances in four size classes (largest first within a class), each on
+// its own side stream after the set-up on the caller's stream; returns the number of streams
+// the caller's stream must join.
+npw_status launch_resident(Run1D& r, const npw_instance* inst, SideStreams* ss, int* joined) {
+    *joined = 0;
+    std::vector<int32_t> cls[4];
+    for (int i = 0; i < r.count; ++i) {
+        if (!r.resident[i]) continue;
+        const int64_t n = inst[i].n;
+        const int c = n > 4096 ? 0 : (n > 2048 ? 1 : (n > 1024 ? 2 : 3));
+        cls[c].push_back(i);
+    }
+    static const int threads[4] = {1024, 512, 256, 128};
+    std::vector<int32_t> all;
+    size_t offs[5] = {0, 0, 0, 0, 0};
+    for (int c = 0; c < 4; ++c) {
+        auto& v = cls[c];
+        // longest runs first: work ~ n * (t_end / dt) ~ n^2 t_end / (cfl L)
+        std::sort(v.begin(), v.end(), [&](int a, int b) {
+            const double wa = (double)inst[a].n * inst[a].t_end / (inst[a].cfl * inst[a].dx);
+            const double wb = (double)inst[b].n * inst[b].t_end / (inst[b].cfl * inst[b].dx);
+            return wa > wb;
+        });
+        offs[c] = all.size();
+        all.insert(all.end(), v.begin(), v.end());
+    }
+    offs[4] = all.size();
+    if (all.empty()) return NPW_OK;
+    int32_t* dlist = reinterpret_cast<int32_t*>(r.ws + r.L.list);
+    NPW_CUDA(cudaMemcpyAsync(dlist, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, r.s));
+    NPW_CUDA(cudaEventRecord(ss->fork, r.s));
+    for (int c = 0; c < 4; ++c) {
+        const int cnt = (int)(offs[c + 1] - offs[c]);
+        if (cnt == 0) continue;
+        int64_t max_n = 0;
+        for (size_t k = offs[c]; k < offs[c + 1]; ++k) max_n = inst[all[k]].n > max_n ? inst[all[k]].n : max_n;
+        NPW_CUDA(cudaStreamWaitEvent(ss->st[c], ss->fork, 0));
+        npw::ResidentArgs a{};
+        a.arena = r.arena;
+        a.inst = reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst);
+        a.ctl = reinterpret_cast<npw::Ctl*>(r.ws + r.L.ctl);
+        a.list = dlist + offs[c];
+        a.count = cnt;
+        a.mp = r.mp;
+        cudaError_t e = npw::launch_resident_f32(a, r.m, r.kind, max_n, threads[c], ss->st[c]);
+        if (e != cudaSuccess) return cuda_fail(e, "resident kernel launch");
+        count_launch();
+        NPW_CUDA(cudaEventRecord(ss->join[c], ss->st[c]));
+        r.joins.push_back(ss->join[c]);
+        ++*joined;
+    }
+    return NPW_OK;
+}
+
 // Run steps until every instance is done: launch as many steps as the largest remaining
 // estimate (capped), then poll.
 npw_status run_to_end(Run1D& r, npw_solve_stats* out) {
@@ -486,6 +590,10 @@ npw_status run_to_end(Run1D& r, npw_solve_stats* out) {
         long long chunk = rem < 1 ? 1 : (rem > 256 ? 256 : rem);
         for (long long k = 0; k < chunk && st == NPW_OK; ++k) st = step_kernels(r, 1);
         if (st == NPW_OK) st = poll(r, &act, &rem);
+    }
+    for (cudaEvent_t ev : r.joins) {  // resident kernels on the side streams
+        cudaError_t e = cudaStreamWaitEvent(r.s, ev, 0);
+        if (e != cudaSuccess && st == NPW_OK) st = cuda_fail(e, "cudaStreamWaitEvent");
     }
     if (st) return st;
     return collect_stats(r, out);
@@ -698,12 +806,24 @@ npw_status npweno_batch_solve(void* arena, const npw_instance* inst, int32_t cou
     r.mp = method(params);
     r.fp32 = params->precision == NPW_FP32_MIXED;
     r.ws = static_cast<unsigned char*>(workspace);
-    r.ntiles = nt;
     r.L = layout_1d(arena_elems, count, nt, elem_size(params));
     r.s = reinterpret_cast<cudaStream_t>(stream);
     if (workspace_bytes < r.L.total)
         return fail(NPW_EINVAL, "workspace too small: %zu < %zu bytes", workspace_bytes, r.L.total);
+    r.resident.assign(count, 0);
+    bool any_res = false;
+    for (int i = 0; i < count; ++i) {
+        r.resident[i] = resident_ok(params, m, inst[i].n) ? 1 : 0;
+        any_res |= r.resident[i] != 0;
+    }
+    r.ntiles = tiles_for(r, inst, count);
     if ((st = setup_1d(r, inst, count, 0.0, 1))) return st;
+    if (any_res) {
+        SideStreams* ss = nullptr;
+        int joined = 0;
+        if ((st = side_streams(&ss))) return st;
+        if ((st = launch_resident(r, inst, ss, &joined))) return st;
+    }
     return run_to_end(r, out);
 }
 

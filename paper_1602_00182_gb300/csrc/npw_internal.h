@@ -95,6 +95,17 @@ struct Stage1DArgs {
     MethodParams mp;
 };
 
+// Whole-solve kernel for instances that fit in one CTA's shared memory: every RK3 step of
+// the instance runs inside the CTA, the state never leaves shared memory until t_end.
+struct ResidentArgs {
+    void* arena;             // state of all instances ([m][n] at inst.off), in/out
+    const InstDev* inst;
+    Ctl* ctl;
+    const int32_t* list;     // instance indices handled by this launch, one per CTA
+    int32_t count;
+    MethodParams mp;
+};
+
 struct Stage2DArgs {
     const void* uin;
     const void* un;
@@ -123,6 +134,9 @@ cudaError_t launch_alpha_init_2d(const void* u, const Inst2D* inst, int tiles, C
                                  const MethodParams& mp, cudaStream_t s);
 template <typename R>
 cudaError_t launch_stage2d(const Stage2DArgs& a, int tiles, int kind, cudaStream_t s);
+// resident whole-solve launch (float state only); max_n = largest n in the list
+cudaError_t launch_resident_f32(const ResidentArgs& a, int m, int kind, int64_t max_n, int threads, cudaStream_t s);
+size_t resident_smem_bytes(int64_t n, int m);
 
 // records msg as the calling thread's npw_last_error() text and returns st (npw_api.cu)
 npw_status set_error(npw_status st, const char* msg);
@@ -133,6 +147,7 @@ cudaError_t launch_ctl_start_2d(Ctl* ctl, const Inst2D* inst, int mode, double d
 cudaError_t launch_count_active(const Ctl* ctl, int count, int* active, cudaStream_t s);
 
 constexpr int TILE_1D = 1024;  // cells per CTA tile in the 1D stage kernel
+constexpr size_t RESIDENT_SMEM_MAX = 200 * 1024;  // shared memory a resident CTA may use
 constexpr int THREADS_1D = 256;
 constexpr int TX_2D = 32;      // 2D tile
 constexpr int TY_2D = 8;

@@ -356,8 +356,8 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
         lf_flux<float, KIND, M>(svm + e * M, svp + (e + 1) * M, alpha, a.mp, 0, hr);
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-            const float du = lam * (hl[k] - hr[k]);
             const float uk = su[e * M + k];
+            const float du = lam * (hl[k] - hr[k]);
             float o;
             if (a.stage == 0) {
                 o = uk + du;
@@ -387,6 +387,199 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
                 finalize_1d(ctl, in);
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Resident whole-solve kernel (float state, component-wise).  One CTA owns one instance for
+// its whole run: u^n and the stage value u^(k) live in shared memory, each RK3 stage is the
+// same three phases as stage1d_fast_kernel (eta per face, reconstruction per cell, fluxes and
+// update per cell) over the whole line with the boundary condition applied by index maps, and
+// thread 0 advances t, alpha and dt between steps.  Shared memory per field: u^n [n],
+// u^(k) [n], eta [n+1] (face f between cells f-1 and f), v^- and v^+ [n+2] (cells -1..n).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int res_map(int i, int n, int bc) {
+    if (bc == NPW_BC_PERIODIC) return i < 0 ? i + n : (i >= n ? i - n : i);
+    return i < 0 ? (bc == NPW_BC_INFLOW ? -1 : 0) : (i >= n ? n - 1 : i);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) {
+    constexpr int M = kind_m<KIND>();
+    extern __shared__ __align__(16) float smf[];
+    __shared__ double red[32];
+    __shared__ int redbad[32];
+    __shared__ double s_dt;
+    __shared__ int s_done;
+    const int inst_idx = a.list[blockIdx.x];
+    const InstDev in = a.inst[inst_idx];
+    Ctl* ctl = a.ctl + inst_idx;
+    const int n = (int)in.n;
+    float* un = smf;               // [M][n]
+    float* uk = un + M * n;        // [M][n]
+    float* se = uk + M * n;        // [M][n+1]
+    float* svm = se + M * (n + 1); // [M][n+2], index i+1 for cell i
+    float* svp = svm + M * (n + 2);
+    const fast::FParams fp = fast::fparams(a.mp);
+    float* g = reinterpret_cast<float*>(a.arena) + in.off;
+    for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) un[idx] = g[idx];
+    float inflow[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) inflow[k] = (float)a.mp.inflow[k];
+    __syncthreads();
+
+    // alpha^0 and the first dt
+    float vmaxf = 0.0f;
+    bool bad = false;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        float U[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            U[k] = un[k * n + i];
+            bad |= !finite_(U[k]);
+        }
+        const float sp = wave_speed<float, KIND>(U, a.mp, 0);
+        bad |= !finite_(sp);
+        vmaxf = sp > vmaxf ? sp : vmaxf;
+    }
+    // thread-0 state of the time loop
+    double t = 0.0, dt = 0.0, alpha = 0.0, alpha_max = 0.0;
+    int64_t steps = 0;
+    int last = 0, status = 0;
+    {
+        const double b = block_max_nan((double)vmaxf, bad, red, redbad);
+        if (threadIdx.x == 0) {
+            if (!(b - b == 0.0)) {
+                status = NPW_ENONFINITE;
+                s_done = 1;
+            } else {
+                alpha = alpha_max = b;
+                s_done = !(t < in.t_end);
+                const double rate = b / in.dx;
+                dt = (rate > 0.0) ? in.cfl / rate : in.t_end - t;
+                if (t + dt * (1.0 + 1e-10) >= in.t_end) {
+                    dt = in.t_end - t;
+                    last = 1;
+                }
+            }
+            s_dt = dt;
+        }
+        __syncthreads();
+    }
+
+    while (!s_done) {
+        const float lam = (float)(s_dt / in.dx);
+        __shared__ float s_alpha;  // alpha lives in thread 0's registers; broadcast it
+        if (threadIdx.x == 0) s_alpha = (float)alpha;
+        __syncthreads();
+        const float alphaf = s_alpha;
+        vmaxf = 0.0f;
+        bad = false;
+#pragma unroll 1
+        for (int stage = 0; stage < 3; ++stage) {
+            const float* X = stage == 0 ? un : uk;
+            // F: eta of faces f = 0..n (cells f-2..f+1)
+            for (int idx = threadIdx.x; idx < (n + 1) * M; idx += blockDim.x) {
+                const int k = idx / (n + 1), f = idx - k * (n + 1);
+                float w[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = res_map(f - 2 + j, n, in.bc);
+                    w[j] = c < 0 ? inflow[k] : X[k * n + c];
+                }
+                uint32_t fl = 0;
+                se[k * (n + 1) + f] = fast::face_eta(w[0], w[1], w[2], w[3], fp, &fl);
+            }
+            __syncthreads();
+            // C: cells i = -1..n (v^- needed for -1..n-1, v^+ for 0..n)
+            for (int idx = threadIdx.x; idx < (n + 2) * M; idx += blockDim.x) {
+                const int k = idx / (n + 2), i = idx - k * (n + 2) - 1;
+                float c[5];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) {
+                    const int cc = res_map(i - 2 + j, n, in.bc);
+                    c[j] = cc < 0 ? inflow[k] : X[k * n + cc];
+                }
+                const float er = i + 1 <= n ? se[k * (n + 1) + i + 1] : 0.0f;
+                const float el = i >= 0 ? se[k * (n + 1) + i] : 0.0f;
+                float vm, vp;
+                fast::cell_recon(c, er, el, fp, &vm, &vp);
+                svm[k * (n + 2) + i + 1] = vm;
+                svp[k * (n + 2) + i + 1] = vp;
+            }
+            __syncthreads();
+            // U: cells 0..n-1; stage 3 writes u^{n+1} over u^n
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                float A[M], B[M], C[M], D[M], hl[M], hr[M], U[M];
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    A[k] = svm[k * (n + 2) + i];      // v^- of cell i-1 (face i)
+                    B[k] = svp[k * (n + 2) + i + 1];  // v^+ of cell i   (face i)
+                    C[k] = svm[k * (n + 2) + i + 1];  // v^- of cell i   (face i+1)
+                    D[k] = svp[k * (n + 2) + i + 2];  // v^+ of cell i+1 (face i+1)
+                }
+                lf_flux<float, KIND, M>(A, B, alphaf, a.mp, 0, hl);
+                lf_flux<float, KIND, M>(C, D, alphaf, a.mp, 0, hr);
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const float du = lam * (hl[k] - hr[k]);
+                    const float x = X[k * n + i];
+                    float o;
+                    if (stage == 0) {
+                        o = x + du;
+                        uk[k * n + i] = o;
+                    } else if (stage == 1) {
+                        o = fmaf(0.75f, un[k * n + i], 0.25f * (x + du));
+                        uk[k * n + i] = o;
+                    } else {
+                        o = fmaf(1.0f / 3.0f, un[k * n + i], (2.0f / 3.0f) * (x + du));
+                        un[k * n + i] = o;
+                    }
+                    U[k] = o;
+                    bad |= !finite_(o);
+                }
+                if (stage == 2) {
+                    const float sp = wave_speed<float, KIND>(U, a.mp, 0);
+                    bad |= !finite_(sp);
+                    vmaxf = sp > vmaxf ? sp : vmaxf;
+                }
+            }
+            __syncthreads();
+        }
+        const double b = block_max_nan((double)vmaxf, bad, red, redbad);
+        if (threadIdx.x == 0) {
+            steps += 1;
+            t = last ? in.t_end : t + dt;
+            if (!(b - b == 0.0)) {
+                status = NPW_ENONFINITE;
+                s_done = 1;
+            } else {
+                alpha = b;
+                alpha_max = b > alpha_max ? b : alpha_max;
+                if (last) {
+                    s_done = 1;
+                } else {
+                    const double rate = b / in.dx;
+                    dt = (rate > 0.0) ? in.cfl / rate : in.t_end - t;
+                    if (t + dt * (1.0 + 1e-10) >= in.t_end) {
+                        dt = in.t_end - t;
+                        last = 1;
+                    }
+                    s_dt = dt;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) g[idx] = un[idx];
+    if (threadIdx.x == 0) {
+        ctl->t = t;
+        ctl->dt = dt;
+        ctl->alpha = alpha;
+        ctl->alpha_max = alpha_max;
+        ctl->steps = steps;
+        ctl->status = status;
+        ctl->done = 1;
     }
 }
 

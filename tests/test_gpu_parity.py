@@ -342,3 +342,62 @@ def test_mixed_precision_full_burgers_instance_stays_finite(npw):
     st = npw.npweno_solve(u, it.dx, 1.5, 0.5, O.BURGERS, O.PERIODIC, npw.Params(rbf=npw.NPW_RBF_GA, precision=1))
     assert st["status"] == 0 and st["t"] == 1.5
     assert np.all(np.isfinite(u.cpu().numpy()))
+
+
+# ------------------------------------------------------------------------------ resident whole-solve kernel
+@pytest.mark.parametrize("family", ["burgers", "euler", "inflow"])
+def test_resident_matches_per_stage_kernels(npw, family):
+    """Instances that fit in shared memory are solved whole by one CTA (batch_mode 0); the
+    per-stage kernels (batch_mode 1) run the same arithmetic, so both give identical bits."""
+    if family == "burgers":
+        inst = I.burgers_batch(count=24, nmin=64, nmax=9000)
+        m, kind, bc = 1, O.BURGERS, O.PERIODIC
+        tends = [0.4] * len(inst)
+        u0s = [it.u0.ravel() for it in inst]
+        ns, dxs = [it.n for it in inst], [it.dx for it in inst]
+        inflow = (0.0, 0, 0, 0)
+    elif family == "euler":
+        inst = I.euler_batch(count=6, nmin=300, nmax=3300)
+        m, kind, bc = 3, O.EULER1D, O.TRANSMISSIVE
+        tends = [min(it.t_end, 0.05) for it in inst]
+        u0s = [it.u0.ravel() for it in inst]
+        ns, dxs = [it.n for it in inst], [it.dx for it in inst]
+        inflow = (0.0, 0, 0, 0)
+    else:
+        ns = [200, 1500, 5000]
+        dxs = [2.0 / n for n in ns]
+        u0s = [np.where(np.linspace(-1, 1, n, endpoint=False) <= 0, 1.0, -1.0) for n in ns]
+        m, kind, bc = 1, O.ADVECTION, O.INFLOW
+        tends = [0.5] * 3
+        inflow = (1.0, 0, 0, 0)
+    table, total = npw.make_instances(ns, dxs, tends, [0.5] * len(ns), [bc] * len(ns), m=m)
+    outs = []
+    for mode in (0, 1):
+        arena = _dev(np.concatenate(u0s), torch.float32)
+        p = npw.Params(rbf=npw.NPW_RBF_GA, precision=1, batch_mode=mode, inflow=inflow)
+        st, stats = npw.npweno_batch_solve(arena, table, m, kind, p)
+        assert st == 0
+        outs.append((arena.cpu().numpy(), stats))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for a, b in zip(outs[0][1], outs[1][1]):
+        assert a["steps"] == b["steps"] and a["t"] == b["t"] and a["alpha_max"] == b["alpha_max"]
+
+
+def test_per_stage_mixed_burgers_accuracy(npw):
+    """The per-stage mixed kernels (batch_mode 1) against the oracle on a multi-tile batch."""
+    inst = I.burgers_batch(count=6, nmin=1000, nmax=5000)
+    table, total = npw.make_instances([it.n for it in inst], [it.dx for it in inst], [0.5] * 6, [0.5] * 6,
+                                      [O.PERIODIC] * 6)
+    arena = _dev(np.concatenate([it.u0[0] for it in inst]), torch.float32)
+    op = O.Params(rbf=O.GA, eta_guard=MIXED_GUARD)
+    p = _gparams(npw, op, precision=1)
+    p.batch_mode = 1
+    status, stats = npw.npweno_batch_solve(arena, table, 1, O.BURGERS, p)
+    assert status == 0
+    a = arena.cpu().numpy().astype(np.float64)
+    off = 0
+    for it in inst:
+        ref, _ = O.solve(it.u0[0].astype(np.float32).astype(np.float64), it.dx, 0.5, 0.5, O.BURGERS, O.PERIODIC, op)
+        e = np.abs(a[off:off + it.n] - ref)
+        assert e.mean() <= 1e-4 and e.max() <= 2e-2
+        off += it.n
