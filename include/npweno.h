@@ -236,6 +236,9 @@ typedef struct {
     int64_t stage_launches;  /* launches of the fused stage kernel (1D and 2D) */
     double stage_ms;         /* summed device time of the timed stage launches (enabled only) */
     int64_t timed_launches;  /* stage launches that were timed */
+    int64_t resident_launches[4]; /* resident whole-solve launches per size class (n > 4096,
+                                     > 2048, > 1024, <= 1024) */
+    double resident_ms[4];   /* their summed device time (enabled only; the classes overlap) */
 } npw_profile;
 void npw_profile_enable(int32_t on);
 void npw_profile_reset(void);

@@ -178,7 +178,11 @@ struct Profiler {
     bool on = false;
     int64_t launches = 0, stage_launches = 0, timed = 0;
     double stage_ms = 0.0;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending, pool;
+    int64_t res_launches[4] = {0, 0, 0, 0};
+    double res_ms[4] = {0.0, 0.0, 0.0, 0.0};
+    // pending event pairs with the slot they add to: -1 = stage kernel, 0..3 = resident class
+    std::vector<std::pair<std::pair<cudaEvent_t, cudaEvent_t>, int>> pending;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
 };
 Profiler& prof() {
     static Profiler p;
@@ -190,11 +194,14 @@ void count_launch(int64_t k = 1) {
     p.launches += k;
 }
 // returns the event pair to bracket a stage launch (null events when profiling is off)
-std::pair<cudaEvent_t, cudaEvent_t> stage_begin(cudaStream_t s) {
+std::pair<cudaEvent_t, cudaEvent_t> stage_begin(cudaStream_t s, int slot = -1) {
     Profiler& p = prof();
     std::lock_guard<std::mutex> g(p.mu);
     p.launches += 1;
-    p.stage_launches += 1;
+    if (slot < 0)
+        p.stage_launches += 1;
+    else
+        p.res_launches[slot] += 1;
     if (!p.on) return {nullptr, nullptr};
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (!p.pool.empty()) {
@@ -206,28 +213,33 @@ std::pair<cudaEvent_t, cudaEvent_t> stage_begin(cudaStream_t s) {
     cudaEventRecord(ev.first, s);
     return ev;
 }
-void stage_end(std::pair<cudaEvent_t, cudaEvent_t> ev, cudaStream_t s) {
+void stage_end(std::pair<cudaEvent_t, cudaEvent_t> ev, cudaStream_t s, int slot = -1) {
     if (!ev.first) return;
     cudaEventRecord(ev.second, s);
     Profiler& p = prof();
     std::lock_guard<std::mutex> g(p.mu);
-    p.pending.push_back(ev);
+    p.pending.push_back({ev, slot});
 }
 // after the stream has been waited for: sum the elapsed times of completed pairs
 void profile_collect() {
     Profiler& p = prof();
     std::lock_guard<std::mutex> g(p.mu);
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> still;
-    for (auto& ev : p.pending) {
+    std::vector<std::pair<std::pair<cudaEvent_t, cudaEvent_t>, int>> still;
+    for (auto& item : p.pending) {
+        auto& ev = item.first;
         if (cudaEventQuery(ev.second) == cudaSuccess) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) {
-                p.stage_ms += ms;
-                p.timed += 1;
+                if (item.second < 0) {
+                    p.stage_ms += ms;
+                    p.timed += 1;
+                } else {
+                    p.res_ms[item.second] += ms;
+                }
             }
             p.pool.push_back(ev);
         } else {
-            still.push_back(ev);
+            still.push_back(item);
         }
     }
     p.pending.swap(still);
@@ -571,9 +583,10 @@ npw_status launch_resident(Run1D& r, const npw_instance* inst, SideStreams* ss, 
         a.list = dlist + offs[c];
         a.count = cnt;
         a.mp = r.mp;
+        auto ev = stage_begin(ss->st[c], c);
         cudaError_t e = npw::launch_resident_f32(a, r.m, r.kind, max_n, threads[c], ss->st[c]);
+        stage_end(ev, ss->st[c], c);
         if (e != cudaSuccess) return cuda_fail(e, "resident kernel launch");
-        count_launch();
         NPW_CUDA(cudaEventRecord(ss->join[c], ss->st[c]));
         r.joins.push_back(ss->join[c]);
         ++*joined;
@@ -638,7 +651,11 @@ void npw_profile_reset(void) {
     std::lock_guard<std::mutex> g(p.mu);
     p.launches = p.stage_launches = p.timed = 0;
     p.stage_ms = 0.0;
-    for (auto& ev : p.pending) p.pool.push_back(ev);
+    for (int c = 0; c < 4; ++c) {
+        p.res_launches[c] = 0;
+        p.res_ms[c] = 0.0;
+    }
+    for (auto& item : p.pending) p.pool.push_back(item.first);
     p.pending.clear();
 }
 
@@ -651,6 +668,10 @@ void npw_profile_read(npw_profile* out) {
     out->stage_launches = p.stage_launches;
     out->stage_ms = p.stage_ms;
     out->timed_launches = p.timed;
+    for (int c = 0; c < 4; ++c) {
+        out->resident_launches[c] = p.res_launches[c];
+        out->resident_ms[c] = p.res_ms[c];
+    }
 }
 
 int32_t npw_version(void) { return 10000; }

@@ -163,23 +163,56 @@ __device__ __forceinline__ int eno_choice_f(float c0, float c1, float c2, float 
 // ---------------------------------------------------------------------------------------
 // Shape parameter.  num = w0 - 3 w1 + 3 w2 - w3, den = w0 - 15 w1 + 15 w2 - w3 (Table k3).
 // ---------------------------------------------------------------------------------------
-// FP64 evaluation.  The numerator and denominator are exact in double (small-integer
-// combinations of floats).  The quotient is formed with a float reciprocal seed refined by
-// Newton steps in double: r = r0 (2 - den r0) twice gives |r - 1/den| < 2^-50 / |den|, then
-// q = num r and one residual correction q += (num - q den) r, so |q - num/den| is within a
-// few units of the last place of double before the result is rounded to float.
+// Exact IEEE 754 format changes done with integer operations, so that they do not occupy
+// the FP64 pipe (on GB300 a float<->double conversion costs an FP64-pipe slot).
+// widen: binary32 -> binary64 is exact: same sign, exponent rebiased by 1023 - 127 = 896,
+// mantissa shifted left by 52 - 23 = 29 bits.  Zeros are handled here; subnormal, infinite
+// and NaN inputs take the hardware conversion.
+__device__ __forceinline__ double widen(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    if ((b << 1) == 0u) return __longlong_as_double((long long)((uint64_t)(b >> 31) << 63));
+    if (e == 0u || e == 255u) return (double)x;
+    const uint64_t bits = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+// narrow_trunc: binary64 -> binary32 by truncating the mantissa (relative error < 2^-23);
+// returns 0 when the value is outside the normal float range (the caller then takes the
+// plain division).  Used only for the seed of the reciprocal and for the guard test.
+__device__ __forceinline__ float narrow_trunc(double d) {
+    const uint64_t b = (uint64_t)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7FFu) - 1023 + 127;
+    if (e <= 0 || e >= 255) return 0.0f;
+    const uint32_t r = (uint32_t)((b >> 32) & 0x80000000u) | ((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu);
+    return __uint_as_float(r);
+}
+
+// FP64 evaluation.  The differences a = w0 - w3 and b = w2 - w1 are formed exactly as float
+// pairs (two_sum) and summed exactly in double; numerator a + 3b and denominator a + 15b are
+// exact double multiply-adds.  The quotient follows the Newton-Raphson reciprocal iteration
+// with a residual correction (Markstein's scheme for division): from a float seed r0 ~ 1/den
+// (relative error < 2^-21), one Newton step r1 = r0 + r0 (1 - den r0) in double leaves
+// |r1 den - 1| < 2^-42; then q = num r1 and one correction q += (num - q den) r1 brings the
+// quotient within a few units of the last place of double, far below the rounding to float
+// that follows.  FP64-pipe instructions: 2 adds, 2 multiply-adds, 1 add of eps_M, 2 for the
+// Newton step, 1 multiply and 2 multiply-adds for the correction, 1 conversion of the result.
 __device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3, const FParams& fp, float guard) {
-    const double W0 = w0, W1 = w1, W2 = w2, W3 = w3;
-    const double a = W0 - W3, b = W2 - W1;
+    float ah, al, bh, bl;
+    two_sum(w0, -w3, ah, al);
+    two_sum(w2, -w1, bh, bl);
+    const double a = widen(ah) + widen(al);
+    const double b = widen(bh) + widen(bl);
     const double num = fma(3.0, b, a);
     const double den0 = fma(15.0, b, a);
-    const float den0f = (float)den0;
-    if (fabsf(den0f) <= guard) return 0.0f;
+    const float den0f = narrow_trunc(den0);
+    if (guard > 0.0f && fabsf(den0f) <= guard * (1.0f + 2.0f * kU)) {
+        // near or below the guard (or outside the float range): decide exactly in double
+        if (fabs(den0) <= (double)guard) return 0.0f;
+    }
     const double den = den0 + fp.eps_M;
-    const float denf = (float)den;
-    if (!(fabsf(denf) > 1e-30f && fabsf(denf) < 1e30f)) return (float)(num / den);  // outside the seed's range
-    double r = (double)(1.0f / denf);
-    r = fma(r, fma(-den, r, 1.0), r);
+    const float denf = narrow_trunc(den);
+    if (!(fabsf(denf) > 1e-30f && fabsf(denf) < 1e30f)) return (float)(num / den);
+    double r = widen(1.0f / denf);
     r = fma(r, fma(-den, r, 1.0), r);
     double q = num * r;
     q = fma(fma(-q, den, num), r, q);
@@ -200,7 +233,7 @@ __device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, f
     two_sum(ah, p15, dh, de);
     float nl = ne + (al + (p3e + 3.f * bl));
     float dl = de + (al + (p15e + 15.f * bl));
-    if (fabsf(dh + dl) <= guard) return 0.0f;
+    if (guard > 0.0f && fabsf(dh + dl) <= guard) return 0.0f;
     float t;
     two_sum(dh, eps_M, dh, t);
     dl += t;

@@ -6,7 +6,7 @@
 #include "npw_instantiate.inc"
 
 namespace npw {
-size_t resident_smem_bytes(int64_t n, int m) { return (size_t)m * (size_t)(5 * n + 5) * sizeof(float); }
+size_t resident_smem_bytes(int64_t n, int m) { return (size_t)m * (size_t)(6 * n + 5) * sizeof(float); }
 
 template <int KIND>
 static cudaError_t launch_res(const ResidentArgs& a, int64_t max_n, int threads, cudaStream_t s) {

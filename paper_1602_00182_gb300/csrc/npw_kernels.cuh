@@ -392,11 +392,17 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
 
 // ---------------------------------------------------------------------------------------
 // Resident whole-solve kernel (float state, component-wise).  One CTA owns one instance for
-// its whole run: u^n and the stage value u^(k) live in shared memory, each RK3 stage is the
-// same three phases as stage1d_fast_kernel (eta per face, reconstruction per cell, fluxes and
-// update per cell) over the whole line with the boundary condition applied by index maps, and
-// thread 0 advances t, alpha and dt between steps.  Shared memory per field: u^n [n],
-// u^(k) [n], eta [n+1] (face f between cells f-1 and f), v^- and v^+ [n+2] (cells -1..n).
+// its whole run: u^n and the two stage values live in shared memory, and thread 0 advances
+// t, alpha and dt between steps.  Each warp owns a contiguous range of cells [lo, hi) and
+// runs the three phases of a stage on it without waiting for the other warps: eta of the
+// faces lo..hi (the two boundary faces are also computed by the neighbouring warps, from the
+// same data, so the copies agree bit for bit), the reconstruction of cells lo-1..hi, then
+// fluxes and the update of its own cells.  Warps therefore drift apart within a stage and the
+// FP64 work of the shape parameter overlaps the FP32 work of other warps; the only CTA-wide
+// barrier is between stages (the next stage reads the neighbours' halo).  Stage values are
+// double-buffered (u^n -> uA -> uB -> u^{n+1}) so no warp overwrites a value another still reads.
+// Shared memory per field: u^n, uA, uB [n]; eta [n+1] (face f between cells f-1 and f);
+// v^-, v^+ [n+2] (cells -1..n at index i+1).
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ int res_map(int i, int n, int bc) {
     if (bc == NPW_BC_PERIODIC) return i < 0 ? i + n : (i >= n ? i - n : i);
@@ -410,22 +416,27 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
     __shared__ double red[32];
     __shared__ int redbad[32];
     __shared__ double s_dt;
+    __shared__ float s_alpha;
     __shared__ int s_done;
     const int inst_idx = a.list[blockIdx.x];
     const InstDev in = a.inst[inst_idx];
     Ctl* ctl = a.ctl + inst_idx;
     const int n = (int)in.n;
-    float* un = smf;               // [M][n]
-    float* uk = un + M * n;        // [M][n]
-    float* se = uk + M * n;        // [M][n+1]
-    float* svm = se + M * (n + 1); // [M][n+2], index i+1 for cell i
-    float* svp = svm + M * (n + 2);
+    float* un = smf;                // [M][n]
+    float* uA = un + M * n;         // [M][n]
+    float* uB = uA + M * n;         // [M][n]
+    float* se = uB + M * n;         // [M][n+1]
+    float* svm = se + M * (n + 1);  // [M][n+2]
+    float* svp = svm + M * (n + 2); // [M][n+2]
     const fast::FParams fp = fast::fparams(a.mp);
     float* g = reinterpret_cast<float*>(a.arena) + in.off;
     for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) un[idx] = g[idx];
     float inflow[M];
 #pragma unroll
     for (int k = 0; k < M; ++k) inflow[k] = (float)a.mp.inflow[k];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int per = (n + nwarps - 1) / nwarps;
+    const int lo = min(n, warp * per), hi = min(n, lo + per);
     __syncthreads();
 
     // alpha^0 and the first dt
@@ -442,8 +453,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
         bad |= !finite_(sp);
         vmaxf = sp > vmaxf ? sp : vmaxf;
     }
-    // thread-0 state of the time loop
-    double t = 0.0, dt = 0.0, alpha = 0.0, alpha_max = 0.0;
+    double t = 0.0, dt = 0.0, alpha = 0.0, alpha_max = 0.0;  // thread 0's copies
     int64_t steps = 0;
     int last = 0, status = 0;
     {
@@ -463,85 +473,90 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
                 }
             }
             s_dt = dt;
+            s_alpha = (float)alpha;
         }
         __syncthreads();
     }
 
     while (!s_done) {
         const float lam = (float)(s_dt / in.dx);
-        __shared__ float s_alpha;  // alpha lives in thread 0's registers; broadcast it
-        if (threadIdx.x == 0) s_alpha = (float)alpha;
-        __syncthreads();
         const float alphaf = s_alpha;
         vmaxf = 0.0f;
         bad = false;
 #pragma unroll 1
         for (int stage = 0; stage < 3; ++stage) {
-            const float* X = stage == 0 ? un : uk;
-            // F: eta of faces f = 0..n (cells f-2..f+1)
-            for (int idx = threadIdx.x; idx < (n + 1) * M; idx += blockDim.x) {
-                const int k = idx / (n + 1), f = idx - k * (n + 1);
-                float w[4];
+            const float* X = stage == 0 ? un : (stage == 1 ? uA : uB);
+            float* Y = stage == 0 ? uA : (stage == 1 ? uB : un);
+            if (lo < hi) {
+                // F: eta of faces lo..hi (cells f-2..f+1)
+                for (int f = lo + lane; f <= hi; f += 32) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = res_map(f - 2 + j, n, in.bc);
-                    w[j] = c < 0 ? inflow[k] : X[k * n + c];
-                }
-                uint32_t fl = 0;
-                se[k * (n + 1) + f] = fast::face_eta(w[0], w[1], w[2], w[3], fp, &fl);
-            }
-            __syncthreads();
-            // C: cells i = -1..n (v^- needed for -1..n-1, v^+ for 0..n)
-            for (int idx = threadIdx.x; idx < (n + 2) * M; idx += blockDim.x) {
-                const int k = idx / (n + 2), i = idx - k * (n + 2) - 1;
-                float c[5];
+                    for (int k = 0; k < M; ++k) {
+                        float w[4];
 #pragma unroll
-                for (int j = 0; j < 5; ++j) {
-                    const int cc = res_map(i - 2 + j, n, in.bc);
-                    c[j] = cc < 0 ? inflow[k] : X[k * n + cc];
-                }
-                const float er = i + 1 <= n ? se[k * (n + 1) + i + 1] : 0.0f;
-                const float el = i >= 0 ? se[k * (n + 1) + i] : 0.0f;
-                float vm, vp;
-                fast::cell_recon(c, er, el, fp, &vm, &vp);
-                svm[k * (n + 2) + i + 1] = vm;
-                svp[k * (n + 2) + i + 1] = vp;
-            }
-            __syncthreads();
-            // U: cells 0..n-1; stage 3 writes u^{n+1} over u^n
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                float A[M], B[M], C[M], D[M], hl[M], hr[M], U[M];
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    A[k] = svm[k * (n + 2) + i];      // v^- of cell i-1 (face i)
-                    B[k] = svp[k * (n + 2) + i + 1];  // v^+ of cell i   (face i)
-                    C[k] = svm[k * (n + 2) + i + 1];  // v^- of cell i   (face i+1)
-                    D[k] = svp[k * (n + 2) + i + 2];  // v^+ of cell i+1 (face i+1)
-                }
-                lf_flux<float, KIND, M>(A, B, alphaf, a.mp, 0, hl);
-                lf_flux<float, KIND, M>(C, D, alphaf, a.mp, 0, hr);
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    const float du = lam * (hl[k] - hr[k]);
-                    const float x = X[k * n + i];
-                    float o;
-                    if (stage == 0) {
-                        o = x + du;
-                        uk[k * n + i] = o;
-                    } else if (stage == 1) {
-                        o = fmaf(0.75f, un[k * n + i], 0.25f * (x + du));
-                        uk[k * n + i] = o;
-                    } else {
-                        o = fmaf(1.0f / 3.0f, un[k * n + i], (2.0f / 3.0f) * (x + du));
-                        un[k * n + i] = o;
+                        for (int j = 0; j < 4; ++j) {
+                            const int c = res_map(f - 2 + j, n, in.bc);
+                            w[j] = c < 0 ? inflow[k] : X[k * n + c];
+                        }
+                        uint32_t fl = 0;
+                        se[k * (n + 1) + f] = fast::face_eta(w[0], w[1], w[2], w[3], fp, &fl);
                     }
-                    U[k] = o;
-                    bad |= !finite_(o);
                 }
-                if (stage == 2) {
-                    const float sp = wave_speed<float, KIND>(U, a.mp, 0);
-                    bad |= !finite_(sp);
-                    vmaxf = sp > vmaxf ? sp : vmaxf;
+                __syncwarp();
+                // C: cells lo-1..hi (v^- uses the eta of face i+1, v^+ that of face i)
+                for (int i = lo - 1 + lane; i <= hi; i += 32) {
+#pragma unroll
+                    for (int k = 0; k < M; ++k) {
+                        float c[5];
+#pragma unroll
+                        for (int j = 0; j < 5; ++j) {
+                            const int cc = res_map(i - 2 + j, n, in.bc);
+                            c[j] = cc < 0 ? inflow[k] : X[k * n + cc];
+                        }
+                        const float er = (i + 1 <= hi) ? se[k * (n + 1) + i + 1] : 0.0f;
+                        const float el = (i >= lo) ? se[k * (n + 1) + i] : 0.0f;
+                        float vm, vp;
+                        fast::cell_recon(c, er, el, fp, &vm, &vp);
+                        // cell lo-1 contributes only v^- (face lo), cell hi only v^+ (face hi); their
+                        // other side belongs to the neighbouring warp and is not written here
+                        if (i < hi) svm[k * (n + 2) + i + 1] = vm;
+                        if (i >= lo) svp[k * (n + 2) + i + 1] = vp;
+                    }
+                }
+                __syncwarp();
+                // U: own cells lo..hi-1
+                for (int i = lo + lane; i < hi; i += 32) {
+                    float A[M], B[M], C[M], D[M], hl[M], hr[M], U[M];
+#pragma unroll
+                    for (int k = 0; k < M; ++k) {
+                        A[k] = svm[k * (n + 2) + i];      // v^- of cell i-1 (face i)
+                        B[k] = svp[k * (n + 2) + i + 1];  // v^+ of cell i   (face i)
+                        C[k] = svm[k * (n + 2) + i + 1];  // v^- of cell i   (face i+1)
+                        D[k] = svp[k * (n + 2) + i + 2];  // v^+ of cell i+1 (face i+1)
+                    }
+                    lf_flux<float, KIND, M>(A, B, alphaf, a.mp, 0, hl);
+                    lf_flux<float, KIND, M>(C, D, alphaf, a.mp, 0, hr);
+#pragma unroll
+                    for (int k = 0; k < M; ++k) {
+                        const float du = lam * (hl[k] - hr[k]);
+                        const float x = X[k * n + i];
+                        float o;
+                        if (stage == 0) {
+                            o = x + du;
+                        } else if (stage == 1) {
+                            o = fmaf(0.75f, un[k * n + i], 0.25f * (x + du));
+                        } else {
+                            o = fmaf(1.0f / 3.0f, un[k * n + i], (2.0f / 3.0f) * (x + du));
+                        }
+                        Y[k * n + i] = o;
+                        U[k] = o;
+                        bad |= !finite_(o);
+                    }
+                    if (stage == 2) {
+                        const float sp = wave_speed<float, KIND>(U, a.mp, 0);
+                        bad |= !finite_(sp);
+                        vmaxf = sp > vmaxf ? sp : vmaxf;
+                    }
                 }
             }
             __syncthreads();
@@ -566,6 +581,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
                         last = 1;
                     }
                     s_dt = dt;
+                    s_alpha = (float)alpha;
                 }
             }
         }
