@@ -326,6 +326,87 @@ def _ncu_traffic():
         return None
 
 
+# ------------------------------------------------------------------------------- serving
+def serving_requests(count: int, rate: float, seed: int = 5):
+    """Poisson arrivals of mixed 1D requests: periodic Burgers (the batch family, T scaled by
+    U(0.1, 1)) and transmissive Euler Riemann / Shu-Osher data (n up to 8192)."""
+    g = np.random.Generator(np.random.PCG64(I.SEED_BASE + 50 + seed))
+    burg = I.burgers_batch(count=count, seed_index=60 + seed)
+    eul = I.euler_batch(count=count, nmin=256, nmax=8192, seed_index=70 + seed)
+    reqs, t = [], 0.0
+    for k in range(count):
+        t += g.exponential(1.0 / rate)
+        if g.uniform() < 0.5:
+            it = burg[k]
+            reqs.append(dict(arrival=t, kind=1, bc=0, m=1, n=it.n, dx=it.dx, t_end=1.5 * g.uniform(0.1, 1.0),
+                             u0=it.u0.ravel()))
+        else:
+            it = eul[k]
+            reqs.append(dict(arrival=t, kind=2, bc=1, m=3, n=it.n, dx=it.dx, t_end=it.t_end * g.uniform(0.1, 1.0),
+                             u0=it.u0.ravel()))
+    return reqs
+
+
+def run_serving(npw, reqs, max_steps: int = 32):
+    """Continuous batching: requests are submitted at their arrival times and stepped together."""
+    import torch
+    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, batch_mode=1)
+    srv = npw.Server(heap_cells=64 * 1024 * 1024, max_slots=512, params=p)
+    t0 = time.perf_counter()
+    k, done = 0, {}
+    while len(done) < len(reqs):
+        now = time.perf_counter() - t0
+        while k < len(reqs) and reqs[k]["arrival"] <= now:
+            r = reqs[k]
+            srv.submit(r["u0"], r["kind"], r["bc"], r["dx"], r["t_end"], 0.5, tag=k)
+            k += 1
+        act, q = srv.step(max_steps)
+        for res in srv.poll():
+            done[res["tag"]] = res
+        if act == 0 and q == 0 and k < len(reqs):
+            time.sleep(max(0.0, reqs[k]["arrival"] - (time.perf_counter() - t0)))
+    srv.close()
+    lat = np.array([done[i]["done_s"] - reqs[i]["arrival"] for i in range(len(reqs))])
+    cells = sum(reqs[i]["n"] * done[i]["steps"] for i in range(len(reqs)))
+    span = max(done[i]["done_s"] for i in done) - reqs[0]["arrival"]
+    ok = all(done[i]["status"] == 0 for i in done)
+    return lat, cells / span, ok
+
+
+def run_fifo_fp64(npw, reqs):
+    """The comparator: one request at a time, first in first out, plain FP64 per-instance solve."""
+    import torch
+    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP64)
+    t0 = time.perf_counter()
+    lat, cells = [], 0
+    for r in reqs:
+        now = time.perf_counter() - t0
+        if now < r["arrival"]:
+            time.sleep(r["arrival"] - now)
+        u = torch.tensor(r["u0"], dtype=torch.float64, device="cuda")
+        st = npw.npweno_solve(u.view(r["m"], r["n"]), r["dx"], r["t_end"], 0.5, r["kind"], r["bc"], p)
+        u.cpu()
+        lat.append(time.perf_counter() - t0 - r["arrival"])
+        cells += r["n"] * st["steps"]
+    span = time.perf_counter() - t0 - reqs[0]["arrival"]
+    return np.array(lat), cells / span
+
+
+def serving_block(npw, count: int, rate: float):
+    reqs = serving_requests(count, rate)
+    lat, thr, ok = run_serving(npw, reqs)
+    flat, fthr = run_fifo_fp64(npw, reqs)
+    q = lambda a, x: float(np.percentile(a, x) * 1e3)
+    return {
+        "requests": count, "rate_per_s": rate,
+        "mix": "1/2 periodic Burgers (N 64..8192, T 0.15..1.5), 1/2 transmissive Euler (N 256..8192)",
+        "server": {"p50_ms": q(lat, 50), "p99_ms": q(lat, 99), "cell_updates_per_s": thr, "all_ok": ok,
+                   "mode": "continuous batching, NPW_FP32_MIXED, per-stage kernels, 32-step rounds"},
+        "fp64_fifo": {"p50_ms": q(flat, 50), "p99_ms": q(flat, 99), "cell_updates_per_s": fthr,
+                      "mode": "one request at a time, npweno_solve NPW_FP64"},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,6 +418,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eta-eval", type=int, default=0, choices=[0, 1],
                     help="0: eta in FP64 (the configuration's FP64 shape-parameter step); 1: exact double-float")
+    ap.add_argument("--serve-requests", type=int, default=60, help="requests of the serving run (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrival rate of the serving run (1/s)")
     ap.add_argument("--variant-steps", type=int, default=1,
                     help="timed solves of the eta_eval=1 variant reported beside the headline (0: skip)")
     ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
@@ -376,6 +459,9 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     out, inst = run_gpu(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        import paper_1602_00182_gb300.npweno as npw
+        out["serving"] = serving_block(npw, args.serve_requests, args.serve_rate)
     if rank == 0:
         if not args.no_cpu_baseline:
             v, wall, desc = cpu_sample(inst, cores)

@@ -200,6 +200,60 @@ npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx
                            size_t workspace_bytes, npw_solve_stats* out, void* stream);
 
 /*
+ * Request server: continuous batching of 1D solves (no counterpart in the paper; the serving
+ * loop around the method).  The server sub-allocates a caller-provided device arena: per
+ * request it needs 3 * m * n elements (state and two stage buffers) of the server's precision.
+ * Requests are queued by npw_server_submit (non-blocking) and admitted first-in first-out
+ * whenever a slot and arena space are free; every npw_server_step advances all admitted
+ * requests together -- each with its own dt, alpha and t_end -- by up to max_steps RK3 steps
+ * through the fused per-stage kernels (one launch set per flux kind), then copies finished
+ * states to their host buffers and frees their space.  Each request's arithmetic depends only
+ * on its own data, so its result is the same bits alone or in any mix.
+ *   device_arena / arena_bytes: caller-owned device memory, at least
+ *       npw_server_arena_bytes(heap_cells, max_slots, params) for a heap of heap_cells elements.
+ *   params: method and precision of every request (precision decides the element type).
+ *   stream: cudaStream_t (void*) for all server work.
+ * Host buffers of a request (u0_host read at admission, out_host written at completion, both
+ * [m][n] of the server's element type) must stay valid until its result has been polled.
+ * Timestamps are seconds since npw_server_create.  Not thread-safe: one thread drives a server.
+ */
+typedef struct npw_server npw_server;
+typedef struct {
+    int32_t flux_kind;     /* NPW_FLUX_ADVECTION, NPW_FLUX_BURGERS or NPW_FLUX_EULER1D */
+    int32_t bc;            /* npw_bc */
+    int64_t n;             /* cells (m = 1, or 3 for Euler) */
+    double dx;
+    double t_end;
+    double cfl;
+    const void* u0_host;   /* initial cell averages, host */
+    void* out_host;        /* final state, host */
+    uint64_t tag;          /* returned with the result */
+} npw_request;
+typedef struct {
+    uint64_t id;           /* as returned by npw_server_submit */
+    uint64_t tag;
+    int32_t status;        /* npw_status of this request */
+    int32_t pad_;
+    int64_t steps;
+    double t;
+    double submit_s;       /* when submitted */
+    double admit_s;        /* when its state reached the device */
+    double done_s;         /* when its final state reached out_host */
+} npw_result;
+size_t npw_server_arena_bytes(int64_t heap_cells, int32_t max_slots, const npw_params* params);
+npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max_slots, const npw_params* params,
+                             void* stream, npw_server** out);
+/* Queue a request.  NPW_EINVAL for a malformed request or one larger than the whole heap;
+ * NPW_EBUSY when max_slots requests are already waiting. */
+npw_status npw_server_submit(npw_server* s, const npw_request* req, uint64_t* id);
+/* One round: admit, advance every admitted request by up to max_steps steps, retire finished
+ * ones.  *active / *queued (may be NULL) receive the counts after the round. */
+npw_status npw_server_step(npw_server* s, int32_t max_steps, int32_t* active, int32_t* queued);
+/* Completed results, oldest first; *nout <= max. */
+npw_status npw_server_poll(npw_server* s, npw_result* out, int32_t max, int32_t* nout);
+void npw_server_destroy(npw_server* s);
+
+/*
  * npweno_rk3_step_noalloc -- the same TVD-RK3 step as npweno_rk3_step (identical kernels and
  * results), for callers that cannot allocate device memory.  The paper has no counterpart:
  * this is an interface for embedding.  Some callers own only device pointers to their state

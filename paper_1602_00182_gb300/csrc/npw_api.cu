@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <deque>
 #include <string>
 #include <mutex>
 #include <utility>
@@ -365,6 +366,44 @@ __global__ void count_active_kernel(const Ctl* ctl, const InstDev* inst, int cou
         poll[0] = s_act[0];
         poll[1] = s_rem[0];
     }
+}
+
+// Server slots: mode 0 zeroes the control words of the listed slots; mode 1 starts them
+// (alpha^0 from the running max bits, first dt).
+__global__ void ctl_slots_kernel(Ctl* ctl, const InstDev* inst, const int32_t* list, int count, int mode) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int i = list[k];
+    Ctl* c = ctl + i;
+    if (mode == 0) {
+        memset(c, 0, sizeof(Ctl));
+        return;
+    }
+    const double a = __longlong_as_double((long long)c->alpha_next_bits);
+    c->alpha_next_bits = 0ull;
+    c->tiles_done = 0u;
+    if (!(a - a == 0.0)) {
+        c->status = NPW_ENONFINITE;
+        c->done = 1;
+        return;
+    }
+    c->alpha = a;
+    c->alpha_max = a;
+    const InstDev in = inst[i];
+    c->t = 0.0;
+    if (!(c->t < in.t_end)) {
+        c->done = 1;
+        return;
+    }
+    const double rate = a / in.dx;
+    double dt = (rate > 0.0) ? in.cfl / rate : in.t_end - c->t;
+    int last = 0;
+    if (c->t + dt * (1.0 + 1e-10) >= in.t_end) {
+        dt = in.t_end - c->t;
+        last = 1;
+    }
+    c->dt = dt;
+    c->last = last;
 }
 
 }  // namespace npw
@@ -978,6 +1017,371 @@ npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx
     if (!(cfl > 0.0)) return fail(NPW_EINVAL, "cfl must be > 0");
     return run_2d(u, nx, ny, m, dx, dy, 0.0, t_end, cfl, flux_kind, bc, params, workspace, workspace_bytes, out,
                   reinterpret_cast<cudaStream_t>(stream), 1);
+}
+
+}  // extern "C"
+
+// =======================================================================================
+// Request server (continuous batching over the per-stage kernels)
+// =======================================================================================
+namespace {
+
+struct ServerLayout {
+    size_t inst, ctl, tiles, newtiles, list, poll, heap_u, heap_u1, heap_u2, total;
+    int64_t max_tiles;
+};
+
+ServerLayout server_layout(int64_t heap_cells, int max_slots, size_t esz) {
+    ServerLayout L{};
+    L.max_tiles = heap_cells / npw::TILE_1D + max_slots;
+    size_t o = 0;
+    L.inst = o;
+    o = align256(o + sizeof(npw::InstDev) * (size_t)max_slots);
+    L.ctl = o;
+    o = align256(o + sizeof(npw::Ctl) * (size_t)max_slots);
+    L.tiles = o;
+    o = align256(o + sizeof(npw::Tile) * (size_t)L.max_tiles);
+    L.newtiles = o;
+    o = align256(o + sizeof(npw::Tile) * (size_t)L.max_tiles);
+    L.list = o;
+    o = align256(o + sizeof(int32_t) * (size_t)max_slots);
+    L.poll = o;
+    o = align256(o + 256);
+    L.heap_u = o;
+    o = align256(o + (size_t)heap_cells * esz);
+    L.heap_u1 = o;
+    o = align256(o + (size_t)heap_cells * esz);
+    L.heap_u2 = o;
+    o = align256(o + (size_t)heap_cells * esz);
+    L.total = o;
+    return L;
+}
+
+double now_s(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+struct npw_server {
+    npw_params params;
+    npw::MethodParams mp;
+    bool fp32 = false;
+    size_t esz = 8;
+    int max_slots = 0;
+    cudaStream_t s = nullptr;
+    unsigned char* arena = nullptr;
+    int64_t heap_cells = 0;
+    ServerLayout L{};
+    std::chrono::steady_clock::time_point t0;
+    struct Slot {
+        bool used = false;
+        bool fresh = false;
+        uint64_t id = 0;
+        npw_request req{};
+        int m = 1;
+        int64_t off = 0;
+        double submit_s = 0.0, admit_s = 0.0;
+    };
+    std::vector<Slot> slots;
+    struct Pending {
+        uint64_t id;
+        npw_request req;
+        double submit_s;
+    };
+    std::deque<Pending> queue;
+    std::vector<std::pair<int64_t, int64_t>> free_ranges;  // [begin, end), sorted, disjoint
+    std::deque<npw_result> results;
+    std::vector<npw::Ctl> host_ctl;
+    uint64_t next_id = 1;
+    long long remaining_hint = 0;  // largest remaining step estimate after the last round
+
+    bool heap_alloc(int64_t len, int64_t* off) {
+        for (size_t k = 0; k < free_ranges.size(); ++k) {
+            auto& r = free_ranges[k];
+            if (r.second - r.first >= len) {
+                *off = r.first;
+                r.first += len;
+                if (r.first == r.second) free_ranges.erase(free_ranges.begin() + (long)k);
+                return true;
+            }
+        }
+        return false;
+    }
+    void heap_free(int64_t off, int64_t len) {
+        free_ranges.push_back({off, off + len});
+        std::sort(free_ranges.begin(), free_ranges.end());
+        std::vector<std::pair<int64_t, int64_t>> merged;
+        for (auto& r : free_ranges) {
+            if (!merged.empty() && merged.back().second == r.first)
+                merged.back().second = r.second;
+            else
+                merged.push_back(r);
+        }
+        free_ranges.swap(merged);
+    }
+};
+
+namespace {
+
+template <typename R>
+npw_status server_launch_steps(npw_server* sv, const std::vector<int>& kind_tiles, const std::vector<size_t>& kind_off,
+                               int steps) {
+    npw::Stage1DArgs a{};
+    a.inst = reinterpret_cast<const npw::InstDev*>(sv->arena + sv->L.inst);
+    a.ctl = reinterpret_cast<npw::Ctl*>(sv->arena + sv->L.ctl);
+    a.advance = 1;
+    a.tile = npw::TILE_1D;
+    a.mp = sv->mp;
+    void* u = sv->arena + sv->L.heap_u;
+    void* u1 = sv->arena + sv->L.heap_u1;
+    void* u2 = sv->arena + sv->L.heap_u2;
+    const void* in_[3] = {u, u1, u2};
+    void* out_[3] = {u1, u2, u};
+    for (int step = 0; step < steps; ++step) {
+        for (int kind = 0; kind < 3; ++kind) {
+            if (kind_tiles[kind] == 0) continue;
+            a.tiles = reinterpret_cast<const npw::Tile*>(sv->arena + sv->L.tiles) + kind_off[kind];
+            a.ntiles = kind_tiles[kind];
+            for (int st = 0; st < 3; ++st) {
+                a.uin = in_[st];
+                a.un = u;
+                a.uout = out_[st];
+                a.stage = st;
+                auto ev = stage_begin(sv->s);
+                cudaError_t e = npw::launch_stage1d<R>(a, kind == NPW_FLUX_EULER1D ? 3 : 1, kind, sv->s);
+                stage_end(ev, sv->s);
+                if (e != cudaSuccess) return cuda_fail(e, "server stage launch");
+            }
+        }
+    }
+    return NPW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t npw_server_arena_bytes(int64_t heap_cells, int32_t max_slots, const npw_params* params) {
+    if (!params || heap_cells < 1 || max_slots < 1) return 0;
+    return server_layout(heap_cells, max_slots, elem_size(params)).total;
+}
+
+npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max_slots, const npw_params* params,
+                             void* stream, npw_server** out) {
+    npw_status st = check_params(params);
+    if (st) return st;
+    if (!device_arena || !out || max_slots < 1 || max_slots > (1 << 20)) return fail(NPW_EINVAL, "bad server arguments");
+    if (params->characteristic) return fail(NPW_EINVAL, "the server runs component-wise reconstruction");
+    const size_t esz = elem_size(params);
+    // largest heap that fits the arena
+    int64_t lo = 0, hi = (int64_t)(arena_bytes / (3 * esz)) + 1;
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (server_layout(mid, max_slots, esz).total <= arena_bytes)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    if (lo < 6) return fail(NPW_EINVAL, "arena too small for a server with %d slots", max_slots);
+    npw_server* sv = new (std::nothrow) npw_server();
+    if (!sv) return fail(NPW_ENOMEM, "host allocation of the server failed");
+    sv->params = *params;
+    sv->mp = method(params);
+    sv->fp32 = params->precision == NPW_FP32_MIXED;
+    sv->esz = esz;
+    sv->max_slots = max_slots;
+    sv->s = reinterpret_cast<cudaStream_t>(stream);
+    sv->arena = static_cast<unsigned char*>(device_arena);
+    sv->heap_cells = lo;
+    sv->L = server_layout(lo, max_slots, esz);
+    sv->slots.resize(max_slots);
+    sv->host_ctl.resize(max_slots);
+    sv->free_ranges.push_back({0, lo});
+    sv->t0 = std::chrono::steady_clock::now();
+    *out = sv;
+    return NPW_OK;
+}
+
+void npw_server_destroy(npw_server* s) { delete s; }
+
+npw_status npw_server_submit(npw_server* sv, const npw_request* req, uint64_t* id) {
+    if (!sv || !req) return fail(NPW_EINVAL, "null server or request");
+    if (req->flux_kind != NPW_FLUX_ADVECTION && req->flux_kind != NPW_FLUX_BURGERS && req->flux_kind != NPW_FLUX_EULER1D)
+        return fail(NPW_EINVAL, "request flux kind %d is not a 1D flux", req->flux_kind);
+    npw_status st = check_bc(req->bc);
+    if (st) return st;
+    if (req->n < 6 || req->n > ((int64_t)1 << 30) || !(req->dx > 0.0) || !(req->cfl > 0.0) || !req->u0_host ||
+        !req->out_host)
+        return fail(NPW_EINVAL, "malformed request");
+    const int m = flux_m(req->flux_kind);
+    if (req->n * m > sv->heap_cells) return fail(NPW_EINVAL, "request larger than the server heap");
+    if ((int)sv->queue.size() >= sv->max_slots) return fail(NPW_EBUSY, "request queue full");
+    npw_server::Pending p{sv->next_id++, *req, now_s(sv->t0)};
+    sv->queue.push_back(p);
+    if (id) *id = p.id;
+    return NPW_OK;
+}
+
+npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, int32_t* queued) {
+    if (!sv || max_steps < 1) return fail(NPW_EINVAL, "bad server step arguments");
+    npw_status st = NPW_OK;
+    // 1. admit, first in first out
+    std::vector<int32_t> fresh;
+    while (!sv->queue.empty()) {
+        const npw_server::Pending& p = sv->queue.front();
+        const int m = flux_m(p.req.flux_kind);
+        int slot = -1;
+        for (int k = 0; k < sv->max_slots; ++k)
+            if (!sv->slots[k].used) {
+                slot = k;
+                break;
+            }
+        int64_t off = 0;
+        if (slot < 0 || !sv->heap_alloc(p.req.n * m, &off)) break;
+        NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.heap_u + (size_t)off * sv->esz, p.req.u0_host,
+                                 (size_t)(p.req.n * m) * sv->esz, cudaMemcpyHostToDevice, sv->s));
+        npw_server::Slot& sl = sv->slots[slot];
+        sl.used = true;
+        sl.fresh = true;
+        sl.id = p.id;
+        sl.req = p.req;
+        sl.m = m;
+        sl.off = off;
+        sl.submit_s = p.submit_s;
+        sl.admit_s = now_s(sv->t0);
+        fresh.push_back(slot);
+        sv->queue.pop_front();
+    }
+    // 2. instance and tile tables of the admitted requests (grouped by flux kind)
+    std::vector<npw::InstDev> hi(sv->max_slots);
+    std::vector<npw::Tile> tiles, newtiles;
+    std::vector<int> kind_tiles(3, 0);
+    std::vector<size_t> kind_off(3, 0);
+    int n_active = 0;
+    for (int kind = 0; kind < 3; ++kind) {
+        kind_off[kind] = tiles.size();
+        for (int k = 0; k < sv->max_slots; ++k) {
+            const npw_server::Slot& sl = sv->slots[k];
+            if (!sl.used || sl.req.flux_kind != kind) continue;
+            npw::InstDev& d = hi[k];
+            d.off = sl.off;
+            d.n = sl.req.n;
+            d.dx = sl.req.dx;
+            d.t_end = sl.req.t_end;
+            d.cfl = sl.req.cfl;
+            d.bc = sl.req.bc;
+            d.ntiles = (int32_t)tiles_of(sl.req.n);
+            for (int64_t t = 0; t < d.ntiles; ++t) {
+                tiles.push_back(npw::Tile{k, (int32_t)(t * npw::TILE_1D)});
+                if (sl.fresh) newtiles.push_back(npw::Tile{k, (int32_t)(t * npw::TILE_1D)});
+            }
+            ++n_active;
+        }
+        kind_tiles[kind] = (int)(tiles.size() - kind_off[kind]);
+    }
+    if (n_active == 0) {
+        if (active) *active = 0;
+        if (queued) *queued = (int32_t)sv->queue.size();
+        return NPW_OK;
+    }
+    NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.inst, hi.data(), sizeof(npw::InstDev) * hi.size(),
+                             cudaMemcpyHostToDevice, sv->s));
+    NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.tiles, tiles.data(), sizeof(npw::Tile) * tiles.size(),
+                             cudaMemcpyHostToDevice, sv->s));
+    npw::Ctl* ctl = reinterpret_cast<npw::Ctl*>(sv->arena + sv->L.ctl);
+    const npw::InstDev* dinst = reinterpret_cast<const npw::InstDev*>(sv->arena + sv->L.inst);
+    // 3. start the admitted requests: reset, alpha^0 over their tiles, first dt
+    if (!fresh.empty()) {
+        int32_t* dlist = reinterpret_cast<int32_t*>(sv->arena + sv->L.list);
+        NPW_CUDA(cudaMemcpyAsync(dlist, fresh.data(), sizeof(int32_t) * fresh.size(), cudaMemcpyHostToDevice, sv->s));
+        NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.newtiles, newtiles.data(), sizeof(npw::Tile) * newtiles.size(),
+                                 cudaMemcpyHostToDevice, sv->s));
+        const unsigned blocks = (unsigned)((fresh.size() + 127) / 128);
+        npw::ctl_slots_kernel<<<blocks, 128, 0, sv->s>>>(ctl, dinst, dlist, (int)fresh.size(), 0);
+        NPW_CUDA(cudaGetLastError());
+        // alpha^0 per fresh request, one launch per flux kind over its fresh tiles
+        size_t b = 0;
+        while (b < newtiles.size()) {
+            const int kind = sv->slots[newtiles[b].inst].req.flux_kind;
+            size_t e = b;
+            while (e < newtiles.size() && sv->slots[newtiles[e].inst].req.flux_kind == kind) ++e;
+            const npw::Tile* tl = reinterpret_cast<const npw::Tile*>(sv->arena + sv->L.newtiles) + b;
+            cudaError_t ce = sv->fp32 ? npw::launch_alpha_init<float>(sv->arena + sv->L.heap_u, dinst, ctl, tl, (int)(e - b),
+                                                                       npw::TILE_1D, flux_m(kind), kind, sv->mp, sv->s)
+                                      : npw::launch_alpha_init<double>(sv->arena + sv->L.heap_u, dinst, ctl, tl, (int)(e - b),
+                                                                        npw::TILE_1D, flux_m(kind), kind, sv->mp, sv->s);
+            if (ce != cudaSuccess) return cuda_fail(ce, "server alpha launch");
+            count_launch();
+            b = e;
+        }
+        npw::ctl_slots_kernel<<<blocks, 128, 0, sv->s>>>(ctl, dinst, dlist, (int)fresh.size(), 1);
+        NPW_CUDA(cudaGetLastError());
+        count_launch(2);
+        for (int k : fresh) sv->slots[k].fresh = false;
+    }
+    // 4. advance everything admitted
+    int steps = max_steps;
+    if (fresh.empty() && sv->remaining_hint > 0 && sv->remaining_hint < steps) steps = (int)sv->remaining_hint;
+    st = sv->fp32 ? server_launch_steps<float>(sv, kind_tiles, kind_off, steps)
+                  : server_launch_steps<double>(sv, kind_tiles, kind_off, steps);
+    if (st) return st;
+    // 5. read the control words, retire finished requests
+    NPW_CUDA(cudaMemcpyAsync(sv->host_ctl.data(), ctl, sizeof(npw::Ctl) * sv->max_slots, cudaMemcpyDeviceToHost, sv->s));
+    if ((st = bounded_sync(sv->s))) return st;
+    profile_collect();
+    std::vector<int> finished;
+    long long rem = 0;
+    for (int k = 0; k < sv->max_slots; ++k) {
+        const npw_server::Slot& sl = sv->slots[k];
+        if (!sl.used) continue;
+        const npw::Ctl& c = sv->host_ctl[k];
+        if (c.done) {
+            finished.push_back(k);
+        } else {
+            const double r = c.dt > 0.0 ? (sl.req.t_end - c.t) / c.dt : 1.0;
+            const long long ri = (long long)(r < 1e9 ? r : 1e9) + 1;
+            rem = ri > rem ? ri : rem;
+        }
+    }
+    sv->remaining_hint = rem;
+    for (int k : finished) {
+        const npw_server::Slot& sl = sv->slots[k];
+        NPW_CUDA(cudaMemcpyAsync(sl.req.out_host, sv->arena + sv->L.heap_u + (size_t)sl.off * sv->esz,
+                                 (size_t)(sl.req.n * sl.m) * sv->esz, cudaMemcpyDeviceToHost, sv->s));
+    }
+    if (!finished.empty() && (st = bounded_sync(sv->s))) return st;
+    const double tdone = now_s(sv->t0);
+    for (int k : finished) {
+        npw_server::Slot& sl = sv->slots[k];
+        const npw::Ctl& c = sv->host_ctl[k];
+        npw_result r{};
+        r.id = sl.id;
+        r.tag = sl.req.tag;
+        r.status = c.status;
+        r.steps = c.steps;
+        r.t = c.t;
+        r.submit_s = sl.submit_s;
+        r.admit_s = sl.admit_s;
+        r.done_s = tdone;
+        sv->results.push_back(r);
+        sv->heap_free(sl.off, sl.req.n * sl.m);
+        sl.used = false;
+    }
+    if (active) *active = n_active - (int32_t)finished.size();
+    if (queued) *queued = (int32_t)sv->queue.size();
+    return NPW_OK;
+}
+
+npw_status npw_server_poll(npw_server* sv, npw_result* out, int32_t max, int32_t* nout) {
+    if (!sv || (!out && max > 0) || !nout) return fail(NPW_EINVAL, "bad poll arguments");
+    int32_t k = 0;
+    while (k < max && !sv->results.empty()) {
+        out[k++] = sv->results.front();
+        sv->results.pop_front();
+    }
+    *nout = k;
+    return NPW_OK;
 }
 
 }  // extern "C"

@@ -311,3 +311,98 @@ def npweno_solve_2d(u, dx: float, dy: float, t_end: float, cfl: float, flux_kind
                                   flux_kind, bc, C.byref(p), C.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size(),
                                   C.byref(st), _stream()))
     return _stats(st)
+
+
+# ---------------------------------------------------------------------------------------
+# request server
+# ---------------------------------------------------------------------------------------
+class npw_request(C.Structure):
+    _fields_ = [("flux_kind", C.c_int32), ("bc", C.c_int32), ("n", C.c_int64), ("dx", C.c_double),
+                ("t_end", C.c_double), ("cfl", C.c_double), ("u0_host", C.c_void_p), ("out_host", C.c_void_p),
+                ("tag", C.c_uint64)]
+
+
+class npw_result(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("tag", C.c_uint64), ("status", C.c_int32), ("pad_", C.c_int32),
+                ("steps", C.c_int64), ("t", C.c_double), ("submit_s", C.c_double), ("admit_s", C.c_double),
+                ("done_s", C.c_double)]
+
+
+def _server_protos(lib):
+    if getattr(lib, "_server_protos", False):
+        return
+    P, vp, i32, i64, sz = C.POINTER, C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+    lib.npw_server_arena_bytes.argtypes = [i64, i32, P(npw_params)]
+    lib.npw_server_arena_bytes.restype = sz
+    lib.npw_server_create.argtypes = [vp, sz, i32, P(npw_params), vp, P(vp)]
+    lib.npw_server_create.restype = i32
+    lib.npw_server_submit.argtypes = [vp, P(npw_request), P(C.c_uint64)]
+    lib.npw_server_submit.restype = i32
+    lib.npw_server_step.argtypes = [vp, i32, P(i32), P(i32)]
+    lib.npw_server_step.restype = i32
+    lib.npw_server_poll.argtypes = [vp, P(npw_result), i32, P(i32)]
+    lib.npw_server_poll.restype = i32
+    lib.npw_server_destroy.argtypes = [vp]
+    lib.npw_server_destroy.restype = None
+    lib._server_protos = True
+
+
+class Server:
+    """npw_server_*: continuous batching of 1D solves on one device arena (allocated here with
+    torch, owned by this object).  Host arrays of each request are kept alive until polled."""
+
+    def __init__(self, heap_cells: int, max_slots: int, params: Params, device=None):
+        torch = _torch()
+        lib = load()
+        _server_protos(lib)
+        self.params = params
+        self._p = params.c()
+        nbytes = int(lib.npw_server_arena_bytes(heap_cells, max_slots, C.byref(self._p)))
+        self.arena = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+        self.stream = torch.cuda.current_stream(self.arena.device)
+        h = C.c_void_p()
+        _check(lib.npw_server_create(C.c_void_p(self.arena.data_ptr()), nbytes, max_slots, C.byref(self._p),
+                                     C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+        self._keep = {}
+        self._np_dtype = "float32" if params.precision == NPW_FP32_MIXED else "float64"
+
+    def submit(self, u0, flux_kind: int, bc: int, dx: float, t_end: float, cfl: float, tag: int = 0) -> int:
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(u0, dtype=self._np_dtype))
+        m = 3 if flux_kind == NPW_FLUX_EULER1D else 1
+        n = a.size // m
+        out = np.empty_like(a)
+        r = npw_request(flux_kind, bc, n, dx, t_end, cfl, a.ctypes.data, out.ctypes.data, tag)
+        rid = C.c_uint64(0)
+        _check(load().npw_server_submit(self._h, C.byref(r), C.byref(rid)))
+        self._keep[rid.value] = (a, out)
+        return rid.value
+
+    def step(self, max_steps: int = 32):
+        act, q = C.c_int32(0), C.c_int32(0)
+        _check(load().npw_server_step(self._h, max_steps, C.byref(act), C.byref(q)))
+        return act.value, q.value
+
+    def poll(self, max_results: int = 1024):
+        buf = (npw_result * max_results)()
+        nout = C.c_int32(0)
+        _check(load().npw_server_poll(self._h, buf, max_results, C.byref(nout)))
+        out = []
+        for k in range(nout.value):
+            r = buf[k]
+            a, res = self._keep.pop(r.id)
+            out.append(dict(id=r.id, tag=r.tag, status=r.status, steps=r.steps, t=r.t, submit_s=r.submit_s,
+                            admit_s=r.admit_s, done_s=r.done_s, u=res))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().npw_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,139 @@
+"""The request server: continuous batching of 1D solves over one device arena.
+
+Each request's result must be the same bits alone and in any mix (its arithmetic depends
+only on its own data and its own time step), equal to the batch solve of the same
+instance, and the server must admit requests only as arena space frees up."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1602_00182_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def npw():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1602_00182_gb300 import build as b
+    b.build()
+    import paper_1602_00182_gb300.npweno as m
+    m.load()
+    return m
+
+
+def _drain(srv, max_steps=16, limit=100000):
+    res = []
+    for _ in range(limit):
+        act, q = srv.step(max_steps)
+        res += srv.poll()
+        if act == 0 and q == 0:
+            break
+    return res
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_alone_equals_mixed_and_batch(npw, precision):
+    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=precision, batch_mode=1)
+    target = I.burgers_batch(count=1, nmin=2500, nmax=2600, seed_index=7)[0]
+    others = I.burgers_batch(count=8, nmin=64, nmax=5000, seed_index=8)
+    # alone
+    srv = npw.Server(heap_cells=200000, max_slots=16, params=p)
+    srv.submit(target.u0[0], npw.NPW_FLUX_BURGERS, 0, target.dx, 0.4, 0.5, tag=1)
+    alone = _drain(srv)[0]
+    srv.close()
+    # in a mix: others start first, the target arrives while they run, more arrive later
+    srv = npw.Server(heap_cells=200000, max_slots=16, params=p)
+    for it in others[:5]:
+        srv.submit(it.u0[0], npw.NPW_FLUX_BURGERS, 0, it.dx, 0.3, 0.5, tag=0)
+    got = []
+    for _ in range(3):
+        srv.step(8)
+        got += srv.poll()
+    srv.submit(target.u0[0], npw.NPW_FLUX_BURGERS, 0, target.dx, 0.4, 0.5, tag=1)
+    srv.step(5)
+    got += srv.poll()
+    for it in others[5:]:
+        srv.submit(it.u0[0], npw.NPW_FLUX_BURGERS, 0, it.dx, 0.2, 0.5, tag=0)
+    got += _drain(srv, max_steps=7)
+    mixed = [r for r in got if r["tag"] == 1][0]
+    assert alone["status"] == 0 and mixed["status"] == 0
+    assert alone["steps"] == mixed["steps"]
+    assert np.array_equal(alone["u"], mixed["u"])
+    # the same instance through the batch solve
+    table, _ = npw.make_instances([target.n], [target.dx], [0.4], [0.5], [0])
+    dt = torch.float32 if precision == 1 else torch.float64
+    arena = torch.tensor(target.u0[0], dtype=dt, device="cuda")
+    st, stats = npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, p)
+    assert st == 0 and stats[0]["steps"] == alone["steps"]
+    assert np.array_equal(arena.cpu().numpy(), alone["u"])
+    assert len([r for r in got if r["status"] == 0]) == 9
+
+
+def test_fp64_server_matches_oracle(npw):
+    p = npw.Params(precision=0)
+    srv = npw.Server(heap_cells=50000, max_slots=8, params=p)
+    insts = I.burgers_batch(count=4, nmin=100, nmax=900, seed_index=9)
+    for k, it in enumerate(insts):
+        srv.submit(it.u0[0], npw.NPW_FLUX_BURGERS, 0, it.dx, 0.2, 0.5, tag=k)
+    res = sorted(_drain(srv), key=lambda r: r["tag"])
+    for it, r in zip(insts, res):
+        ref, rst = O.solve(it.u0[0], it.dx, 0.2, 0.5, O.BURGERS, O.PERIODIC, O.Params())
+        assert r["steps"] == rst["steps"]
+        assert np.abs(r["u"] - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_admission_by_memory_and_mixed_kinds(npw):
+    """The heap holds about two requests at a time; eight (Burgers and Euler) all finish, each
+    identical to its own batch solve."""
+    p = npw.Params(rbf=npw.NPW_RBF_MQ, precision=1, batch_mode=1)
+    burg = I.burgers_batch(count=4, nmin=1900, nmax=2000, seed_index=10)
+    eul = I.euler_batch(count=4, nmin=600, nmax=650, seed_index=11)
+    srv = npw.Server(heap_cells=4100, max_slots=8, params=p)
+    for k, it in enumerate(burg):
+        srv.submit(it.u0[0], npw.NPW_FLUX_BURGERS, 0, it.dx, 0.1, 0.5, tag=k)
+    for k, it in enumerate(eul):
+        srv.submit(it.u0.ravel(), npw.NPW_FLUX_EULER1D, 1, it.dx, min(it.t_end, 0.02), 0.5, tag=10 + k)
+    got, max_active = [], 0
+    for _ in range(100000):
+        act, q = srv.step(6)
+        max_active = max(max_active, act)
+        got += srv.poll()
+        if act == 0 and q == 0:
+            break
+    assert len(got) == 8 and all(r["status"] == 0 for r in got)
+    assert max_active <= 2
+    for r in got:
+        if r["tag"] < 10:
+            it, m, kind, bc, te = burg[r["tag"]], 1, npw.NPW_FLUX_BURGERS, 0, 0.1
+        else:
+            it, m, kind, bc, te = eul[r["tag"] - 10], 3, npw.NPW_FLUX_EULER1D, 1, min(eul[r["tag"] - 10].t_end, 0.02)
+        table, _ = npw.make_instances([it.n], [it.dx], [te], [0.5], [bc], m=m)
+        arena = torch.tensor(it.u0.ravel(), dtype=torch.float32, device="cuda")
+        st, stats = npw.npweno_batch_solve(arena, table, m, kind, p)
+        assert np.array_equal(arena.cpu().numpy(), r["u"])
+
+
+def test_failed_request_does_not_disturb_others(npw):
+    p = npw.Params(precision=1, batch_mode=1)
+    srv = npw.Server(heap_cells=20000, max_slots=4, params=p)
+    good = I.burgers_batch(count=2, nmin=500, nmax=900, seed_index=12)
+    bad = good[0].u0[0].copy()
+    bad[10] = np.nan
+    srv.submit(good[0].u0[0], npw.NPW_FLUX_BURGERS, 0, good[0].dx, 0.2, 0.5, tag=0)
+    srv.submit(bad, npw.NPW_FLUX_BURGERS, 0, good[0].dx, 0.2, 0.5, tag=1)
+    srv.submit(good[1].u0[0], npw.NPW_FLUX_BURGERS, 0, good[1].dx, 0.2, 0.5, tag=2)
+    res = {r["tag"]: r for r in _drain(srv)}
+    assert res[1]["status"] == npw.NPW_ENONFINITE
+    assert res[0]["status"] == 0 and res[2]["status"] == 0 and res[2]["t"] == 0.2
+    with pytest.raises(npw.NpwError) as e:
+        srv.submit(np.ones(5), npw.NPW_FLUX_BURGERS, 0, 0.1, 0.2, 0.5)
+    assert e.value.status == npw.NPW_EINVAL
+    for _ in range(4):
+        srv.submit(good[0].u0[0], npw.NPW_FLUX_BURGERS, 0, good[0].dx, 0.2, 0.5)
+    with pytest.raises(npw.NpwError) as e:
+        srv.submit(good[0].u0[0], npw.NPW_FLUX_BURGERS, 0, good[0].dx, 0.2, 0.5)
+    assert e.value.status == npw.NPW_EBUSY
+    _drain(srv)
