@@ -86,6 +86,9 @@ typedef struct {
                                 CTA's shared memory run whole in one CTA (resident), the rest through the
                                 per-stage kernels; 1 = every instance through the per-stage kernels */
     int32_t pad_;
+    double eta_max;          /* eta = 0 where |eta| > eta_max: the perturbation argument (Sec. 3) needs a small
+                                eta, and a monotone stencil with zero slope at the face makes the Table k3
+                                denominator vanish (eta ~ num / eps_M); 0 = automatic (1.0), < 0 = off */
 } npw_params;
 
 typedef struct {
@@ -110,7 +113,7 @@ typedef struct {
 
 /* Fill *p with the defaults: k = 3, RBF-WENO5, multiquadric, switch on (variant 0),
  * component-wise, FP64, eps_M = 1e-12, eps_weno = 1e-6, gamma = 1.4, a = (1, 1),
- * eta_eval = 0, eta_guard = 0 (automatic). */
+ * eta_eval = 0, eta_guard = 0 (automatic), eta_max = 0 (automatic: 1). */
 void npw_default_params(npw_params* p);
 
 /* Text of the last error on the calling thread ("" if none). */

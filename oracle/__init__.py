@@ -41,7 +41,7 @@ class _Params(C.Structure):
         ("characteristic", C.c_int), ("pad_", C.c_int),
         ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
         ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4),
-        ("tie_tol", C.c_double), ("eta_guard", C.c_double),
+        ("tie_tol", C.c_double), ("eta_guard", C.c_double), ("eta_max", C.c_double),
     ]
 
 
@@ -66,12 +66,13 @@ class Params:
     inflow: tuple = (0.0, 0.0, 0.0, 0.0)
     tie_tol: float = 1e-10
     eta_guard: float = 0.0
+    eta_max: float = 1.0
 
     def _c(self) -> _Params:
         p = _Params()
         for f in ("scheme", "rbf", "monotone_switch", "switch_variant", "characteristic"):
             setattr(p, f, int(getattr(self, f)))
-        for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "tie_tol", "eta_guard"):
+        for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "tie_tol", "eta_guard", "eta_max"):
             setattr(p, f, float(getattr(self, f)))
         for k in range(4):
             p.inflow[k] = float(self.inflow[k]) if k < len(self.inflow) else 0.0

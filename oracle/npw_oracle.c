@@ -293,6 +293,9 @@ static void face_field(const double w[6], const orc_params* p, const uint8_t* re
             if (!(p->eta_guard > 0.0 && fabs(den0) <= p->eta_guard * mag)) {
                 double den = den0 + p->eps_M;
                 eta = eta_numerator(&w[1]) / den;
+                /* optional bound (not in the paper): the perturbation argument of Sec. 3 needs a
+                 * small eta; a monotone stencil with zero slope at the face sends eta to num/eps_M */
+                if (p->eta_max > 0.0 && fabs(eta) > p->eta_max) eta = 0.0;
             }
         }
         if (near) fl |= ORC_FLAG_SWITCH_TIE;

@@ -37,6 +37,7 @@ typedef struct {
     double inflow[4]; /* ghost state for the inflow boundary */
     double tie_tol;   /* relative margin that marks a decision as a near tie */
     double eta_guard; /* eta = 0 where |den| <= eta_guard * (|w0| + 15|w1| + 15|w2| + |w3|); 0 = off */
+    double eta_max;   /* eta = 0 where |eta| > eta_max; 0 = off */
 } orc_params;
 
 typedef struct {

@@ -85,6 +85,7 @@ npw::MethodParams method(const npw_params* p) {
         mp.eta_guard = 8.0 * 5.9604644775390625e-08;
     else
         mp.eta_guard = 0.0;
+    mp.eta_max = p->eta_max > 0.0 ? p->eta_max : (p->eta_max == 0.0 ? 1.0 : 0.0);
     return mp;
 }
 
@@ -107,7 +108,7 @@ npw_status check_bc(int bc) {
 // instance table, the per-instance control words, the tile table and the poll words.
 // ---------------------------------------------------------------------------------------
 struct Layout1D {
-    size_t u1, u2, inst, ctl, tiles, poll, list, total;
+    size_t u1, u2, inst, ctl, tiles, poll, list, sbuf, cbuf, total;
 };
 
 Layout1D layout_1d(int64_t arena_elems, int count, int64_t ntiles, size_t esz) {
@@ -119,6 +120,11 @@ Layout1D layout_1d(int64_t arena_elems, int count, int64_t ntiles, size_t esz) {
     o = align256(o + (size_t)arena_elems * esz);
     L.u2 = o;
     o = align256(o + (size_t)arena_elems * esz);
+    // compensated float path: next state s and carry c (float, arena-shaped)
+    L.sbuf = o;
+    o = align256(o + (esz == sizeof(float) ? (size_t)arena_elems * sizeof(float) : 0));
+    L.cbuf = o;
+    o = align256(o + (esz == sizeof(float) ? (size_t)arena_elems * sizeof(float) : 0));
     L.inst = o;
     o = align256(o + sizeof(npw::InstDev) * (size_t)count);
     L.ctl = o;
@@ -424,6 +430,7 @@ struct Run1D {
     Layout1D L;
     int64_t ntiles;
     cudaStream_t s;
+    bool comp = false;           // compensated float per-stage kernels (float, component-wise)
     std::vector<char> resident;  // per instance: solved by the resident kernel
     std::vector<cudaEvent_t> joins;  // side-stream work the caller's stream waits for at the end
 };
@@ -455,8 +462,14 @@ npw_status run_step_kernels(const Run1D& r, int advance) {
     void* u = r.arena;
     void* u1 = r.ws + r.L.u1;
     void* u2 = r.ws + r.L.u2;
+    a.u = reinterpret_cast<float*>(u);
+    a.d1 = reinterpret_cast<float*>(u1);
+    a.d2 = reinterpret_cast<float*>(u2);
+    a.s = reinterpret_cast<float*>(r.ws + r.L.sbuf);
+    a.c = reinterpret_cast<float*>(r.ws + r.L.cbuf);
     // stage 1: u -> u1; stage 2: (u1, u) -> u2; stage 3: (u2, u) -> u (in place: each cell reads
-    // its own u^n before writing it, and the halo of stage 3 comes from u2)
+    // its own u^n before writing it, and the halo of stage 3 comes from u2).  The compensated
+    // float kernels use u, d1, d2, s and c instead (see stage1d_fast_kernel).
     const void* in_[3] = {u, u1, u2};
     void* out_[3] = {u1, u2, u};
     for (int st = 0; st < 3; ++st) {
@@ -511,6 +524,12 @@ npw_status setup_1d(Run1D& r, const npw_instance* inst, int count, double dt_fix
     npw::ctl_start_kernel<<<blocks, 128, 0, r.s>>>(ctl, di, count, mode, dt_fixed);
     NPW_CUDA(cudaGetLastError());
     count_launch(3);
+    if (r.comp && r.ntiles > 0) {
+        NPW_CUDA(npw::launch_comp_begin(reinterpret_cast<const float*>(r.arena), reinterpret_cast<float*>(r.ws + r.L.sbuf),
+                                        reinterpret_cast<float*>(r.ws + r.L.cbuf), di,
+                                        reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles), (int)r.ntiles, r.m, r.s));
+        count_launch();
+    }
     return NPW_OK;
 }
 
@@ -617,6 +636,7 @@ npw_status launch_resident(Run1D& r, const npw_instance* inst, SideStreams* ss, 
         NPW_CUDA(cudaStreamWaitEvent(ss->st[c], ss->fork, 0));
         npw::ResidentArgs a{};
         a.arena = r.arena;
+        a.carry = reinterpret_cast<float*>(r.ws + r.L.cbuf);
         a.inst = reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst);
         a.ctl = reinterpret_cast<npw::Ctl*>(r.ws + r.L.ctl);
         a.list = dlist + offs[c];
@@ -633,6 +653,16 @@ npw_status launch_resident(Run1D& r, const npw_instance* inst, SideStreams* ss, 
     return NPW_OK;
 }
 
+// compensated float path: the final states are in s; copy them back into the arena
+npw_status comp_end(const Run1D& r) {
+    if (!r.comp || r.ntiles == 0) return NPW_OK;
+    NPW_CUDA(npw::launch_comp_end(reinterpret_cast<float*>(r.arena), reinterpret_cast<const float*>(r.ws + r.L.sbuf),
+                                  reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst),
+                                  reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles), (int)r.ntiles, r.m, r.s));
+    count_launch();
+    return NPW_OK;
+}
+
 // Run steps until every instance is done: launch as many steps as the largest remaining
 // estimate (capped), then poll.
 npw_status run_to_end(Run1D& r, npw_solve_stats* out) {
@@ -643,6 +673,7 @@ npw_status run_to_end(Run1D& r, npw_solve_stats* out) {
         for (long long k = 0; k < chunk && st == NPW_OK; ++k) st = step_kernels(r, 1);
         if (st == NPW_OK) st = poll(r, &act, &rem);
     }
+    if (st == NPW_OK) st = comp_end(r);
     for (cudaEvent_t ev : r.joins) {  // resident kernels on the side streams
         cudaError_t e = cudaStreamWaitEvent(r.s, ev, 0);
         if (e != cudaSuccess && st == NPW_OK) st = cuda_fail(e, "cudaStreamWaitEvent");
@@ -784,6 +815,7 @@ static npw_status single_run(void* u, int64_t n, int32_t m, double dx, double t_
     r.ntiles = tiles_of(n);
     r.L = layout_1d(n * m, 1, r.ntiles, elem_size(params));
     r.s = s;
+    r.comp = r.fp32 && !params->characteristic;
     if (workspace_bytes < r.L.total)
         return fail(NPW_EINVAL, "workspace too small: %zu < %zu bytes", workspace_bytes, r.L.total);
     in.offset = 0;
@@ -806,6 +838,7 @@ npw_status npweno_rk3_step(void* u, int64_t n, int32_t m, double dx, double dt, 
     if (!(dt >= 0.0)) return fail(NPW_EINVAL, "dt must be >= 0");
     if ((st = setup_1d(r, &in, 1, dt, 2))) return st;
     if ((st = step_kernels(r, 0))) return st;
+    if ((st = comp_end(r))) return st;
     if (alpha_out) {
         npw::Ctl c;
         NPW_CUDA(cudaMemcpyAsync(&c, r.ws + r.L.ctl, sizeof c, cudaMemcpyDeviceToHost, s));
@@ -870,6 +903,7 @@ npw_status npweno_batch_solve(void* arena, const npw_instance* inst, int32_t cou
     r.s = reinterpret_cast<cudaStream_t>(stream);
     if (workspace_bytes < r.L.total)
         return fail(NPW_EINVAL, "workspace too small: %zu < %zu bytes", workspace_bytes, r.L.total);
+    r.comp = r.fp32 && !params->characteristic;
     r.resident.assign(count, 0);
     bool any_res = false;
     for (int i = 0; i < count; ++i) {
@@ -1027,7 +1061,7 @@ npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx
 namespace {
 
 struct ServerLayout {
-    size_t inst, ctl, tiles, newtiles, list, poll, heap_u, heap_u1, heap_u2, total;
+    size_t inst, ctl, tiles, newtiles, list, poll, heap_u, heap_u1, heap_u2, heap_s, heap_c, total;
     int64_t max_tiles;
 };
 
@@ -1053,6 +1087,12 @@ ServerLayout server_layout(int64_t heap_cells, int max_slots, size_t esz) {
     o = align256(o + (size_t)heap_cells * esz);
     L.heap_u2 = o;
     o = align256(o + (size_t)heap_cells * esz);
+    // compensated float path: next state and carry
+    const size_t extra = esz == sizeof(float) ? (size_t)heap_cells * sizeof(float) : 0;
+    L.heap_s = o;
+    o = align256(o + extra);
+    L.heap_c = o;
+    o = align256(o + extra);
     L.total = o;
     return L;
 }
@@ -1136,6 +1176,11 @@ npw_status server_launch_steps(npw_server* sv, const std::vector<int>& kind_tile
     void* u = sv->arena + sv->L.heap_u;
     void* u1 = sv->arena + sv->L.heap_u1;
     void* u2 = sv->arena + sv->L.heap_u2;
+    a.u = reinterpret_cast<float*>(u);
+    a.d1 = reinterpret_cast<float*>(u1);
+    a.d2 = reinterpret_cast<float*>(u2);
+    a.s = reinterpret_cast<float*>(sv->arena + sv->L.heap_s);
+    a.c = reinterpret_cast<float*>(sv->arena + sv->L.heap_c);
     const void* in_[3] = {u, u1, u2};
     void* out_[3] = {u1, u2, u};
     for (int step = 0; step < steps; ++step) {
@@ -1318,6 +1363,20 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
         npw::ctl_slots_kernel<<<blocks, 128, 0, sv->s>>>(ctl, dinst, dlist, (int)fresh.size(), 1);
         NPW_CUDA(cudaGetLastError());
         count_launch(2);
+        if (sv->fp32) {  // compensated float kernels: s = u, c = 0 for the admitted requests
+            for (size_t b2 = 0; b2 < newtiles.size();) {
+                const int kind = sv->slots[newtiles[b2].inst].req.flux_kind;
+                size_t e2 = b2;
+                while (e2 < newtiles.size() && sv->slots[newtiles[e2].inst].req.flux_kind == kind) ++e2;
+                NPW_CUDA(npw::launch_comp_begin(reinterpret_cast<const float*>(sv->arena + sv->L.heap_u),
+                                                reinterpret_cast<float*>(sv->arena + sv->L.heap_s),
+                                                reinterpret_cast<float*>(sv->arena + sv->L.heap_c), dinst,
+                                                reinterpret_cast<const npw::Tile*>(sv->arena + sv->L.newtiles) + b2,
+                                                (int)(e2 - b2), flux_m(kind), sv->s));
+                count_launch();
+                b2 = e2;
+            }
+        }
         for (int k : fresh) sv->slots[k].fresh = false;
     }
     // 4. advance everything admitted
@@ -1345,9 +1404,10 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
         }
     }
     sv->remaining_hint = rem;
-    for (int k : finished) {
+    for (int k : finished) {  // the compensated float kernels leave the final state in s
         const npw_server::Slot& sl = sv->slots[k];
-        NPW_CUDA(cudaMemcpyAsync(sl.req.out_host, sv->arena + sv->L.heap_u + (size_t)sl.off * sv->esz,
+        const size_t region = sv->fp32 ? sv->L.heap_s : sv->L.heap_u;
+        NPW_CUDA(cudaMemcpyAsync(sl.req.out_host, sv->arena + region + (size_t)sl.off * sv->esz,
                                  (size_t)(sl.req.n * sl.m) * sv->esz, cudaMemcpyDeviceToHost, sv->s));
     }
     if (!finished.empty() && (st = bounded_sync(sv->s))) return st;

@@ -228,7 +228,8 @@ __device__ __forceinline__ uint32_t face_field(const R* w, const MethodParams& m
                               fabs(den0) <= D(mp.eta_guard) * (fabs(w1) + D(15.0) * fabs(w2) + D(15.0) * fabs(w3) + fabs(w4));
             if (!unresolved) {
                 D den = den0 + D(mp.eps_M);
-                eta = R(eta_num<D>(w1, w2, w3, w4) / den);
+                D e = eta_num<D>(w1, w2, w3, w4) / den;
+                if (!(mp.eta_max > 0.0 && fabs(e) > D(mp.eta_max))) eta = R(e);
             }
         }
     }

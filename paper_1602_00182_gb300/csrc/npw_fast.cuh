@@ -25,7 +25,7 @@ namespace fast {
 
 // float copies of the method parameters, converted once per thread
 struct FParams {
-    float eps_weno, eps_M_f, eta_guard;
+    float eps_weno, eps_M_f, eta_guard, eta_max;
     double eps_M;
     int scheme, rbf, monotone_switch, switch_variant, eta_eval;
 };
@@ -34,6 +34,7 @@ __device__ __forceinline__ FParams fparams(const MethodParams& mp) {
     f.eps_weno = (float)mp.eps_weno;
     f.eps_M_f = (float)mp.eps_M;
     f.eta_guard = (float)mp.eta_guard;
+    f.eta_max = (float)mp.eta_max;
     f.eps_M = mp.eps_M;
     f.scheme = mp.scheme;
     f.rbf = mp.rbf;
@@ -269,7 +270,8 @@ __device__ __forceinline__ float face_eta(float w0, float w1, float w2, float w3
         *flag |= 1u;
         return 0.0f;
     }
-    return eta_eval(w0, w1, w2, w3, fp);
+    const float e = eta_eval(w0, w1, w2, w3, fp);
+    return (fp.eta_max > 0.0f && fabsf(e) > fp.eta_max) ? 0.0f : e;
 }
 
 // ---------------------------------------------------------------------------------------

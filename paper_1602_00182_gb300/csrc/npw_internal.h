@@ -34,6 +34,7 @@ struct MethodParams {
     double adv_speed_y;
     double inflow[4];
     double eta_guard;  // resolved threshold (0 = off)
+    double eta_max;    // resolved bound on |eta| (0 = off)
 };
 
 // One 1D problem (device copy of npw_instance plus its tile range).
@@ -85,6 +86,13 @@ struct Stage1DArgs {
     const void* uin;   // stage input u^(k)
     const void* un;    // u^n (stages 2, 3)
     void* uout;        // stage output
+    // compensated float path (stage1d_fast_kernel): u^n in `u` (arena), increments d1 and d2,
+    // the next state s (written by stage 3, copied into u by the next stage 1) and the carry c
+    float* u;
+    float* d1;
+    float* d2;
+    float* s;
+    float* c;
     const InstDev* inst;
     Ctl* ctl;
     const Tile* tiles;
@@ -99,6 +107,7 @@ struct Stage1DArgs {
 // the instance runs inside the CTA, the state never leaves shared memory until t_end.
 struct ResidentArgs {
     void* arena;             // state of all instances ([m][n] at inst.off), in/out
+    float* carry;            // per-cell compensation of the step update (arena-shaped scratch)
     const InstDev* inst;
     Ctl* ctl;
     const int32_t* list;     // instance indices handled by this launch, one per CTA
@@ -145,6 +154,11 @@ npw_status set_error(npw_status st, const char* msg);
 cudaError_t launch_ctl_start(Ctl* ctl, const InstDev* inst, int count, int mode, double dt, cudaStream_t s);
 cudaError_t launch_ctl_start_2d(Ctl* ctl, const Inst2D* inst, int mode, double dt, cudaStream_t s);
 cudaError_t launch_count_active(const Ctl* ctl, int count, int* active, cudaStream_t s);
+// compensated float path: before the first step s = u and c = 0; after the last, u = s
+cudaError_t launch_comp_begin(const float* u, float* s, float* c, const InstDev* inst, const Tile* tiles, int ntiles,
+                              int m, cudaStream_t st);
+cudaError_t launch_comp_end(float* u, const float* s, const InstDev* inst, const Tile* tiles, int ntiles, int m,
+                            cudaStream_t st);
 
 constexpr int TILE_1D = 1024;  // cells per CTA tile in the 1D stage kernel
 constexpr size_t RESIDENT_SMEM_MAX = 200 * 1024;  // shared memory a resident CTA may use

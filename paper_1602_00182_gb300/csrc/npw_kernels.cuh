@@ -30,9 +30,35 @@ __device__ __forceinline__ R line_get(const R* u, int64_t n, int64_t stride, int
     return u[k * stride];
 }
 
+// index of cell k (any integer) of a line of n cells under the boundary condition; -1 means
+// "the inflow ghost state"
+__device__ __forceinline__ int64_t line_idx(int64_t n, int64_t k, int bc) {
+    if (bc == NPW_BC_PERIODIC) {
+        int64_t kk = k % n;
+        return kk < 0 ? kk + n : kk;
+    }
+    if (k < 0) return bc == NPW_BC_INFLOW ? -1 : 0;
+    return k >= n ? n - 1 : k;
+}
+
 template <typename R>
 __device__ __forceinline__ bool finite_(R x) {
     return x - x == R(0.0);
+}
+
+// Weights of the last Shu-Osher stage, u^{n+1} = w1 u^n + w2 (u2 + dt L(u2)).  They must sum to
+// one exactly, or every step scales the conserved sum: in float, RN(1/3) + RN(2/3) = 1 + 3e-8,
+// so the float kernels take w2 = RN(2/3) and w1 = 1 - w2 (exact).  Double keeps 1/3 and 2/3
+// (their rounded sum differs from one by 1e-17, below the FP64 path's other rounding).
+constexpr float kTwoThirdsF = 2.0f / 3.0f;
+constexpr float kThirdF = 1.0f - kTwoThirdsF;
+template <typename R>
+__device__ __forceinline__ R stage3_w1() {
+    return sizeof(R) == sizeof(float) ? R(kThirdF) : R(1.0 / 3.0);
+}
+template <typename R>
+__device__ __forceinline__ R stage3_w2() {
+    return sizeof(R) == sizeof(float) ? R(kTwoThirdsF) : R(2.0 / 3.0);
 }
 
 // max over the block of a non-negative speed; any non-finite input makes the result NaN
@@ -257,7 +283,7 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_kernel(Stage1DArgs a) {
             } else if (a.stage == 1) {
                 o = R(0.75) * un[k * n + c0 + q] + R(0.25) * (uk + dtR * L);
             } else {
-                o = R(1.0 / 3.0) * un[k * n + c0 + q] + R(2.0 / 3.0) * (uk + dtR * L);
+                o = stage3_w1<R>() * un[k * n + c0 + q] + stage3_w2<R>() * (uk + dtR * L);
             }
             uout[k * n + c0 + q] = o;
             U[k] = o;
@@ -289,8 +315,16 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_kernel(Stage1DArgs a) {
 //   F: eta (and the switch) once per face, faces between e-1 and e for e = 2 .. cnt+4;
 //   C: once per cell e = 2 .. cnt+3: smoothness indicators, weights and the two face values
 //      v^-_{e+1/2} (with the eta of face e|e+1) and v^+_{e-1/2} (eta of face e-1|e);
-//   U: cells e = 3 .. cnt+2: Lax-Friedrichs fluxes of both faces, eq. PDE1, stage combination.
-// Shared memory (floats): u, eta, v^-, v^+, each (tile + 6) * M.
+//   U: cells e = 3 .. cnt+2: Lax-Friedrichs fluxes of both faces, eq. PDE1, stage update.
+// The stages are kept in increment form so that the float state conserves its sum: with
+// du = dt L(u^(k)) (per cell, telescoping over the faces),
+//   stage 1: d1 = du0                         (u1 = u^n + d1)
+//   stage 2: d2 = (d1 + du1) / 4              (u2 = 3/4 u^n + 1/4 (u1 + du1) = u^n + d2)
+//   stage 3: u^{n+1} = u^n + 2/3 (d2 + du2)   (= 1/3 u^n + 2/3 (u2 + du2))
+// and the last addition is compensated with a per-cell carry (Kahan): increments smaller than
+// half an ulp of u are kept in the carry instead of being rounded away.  Stage 3 writes the new
+// state to s (neighbouring tiles still read u^n); the next step's stage 1 reads s and commits it
+// to u.  Shared memory (floats): u^(k), eta, v^-, v^+, each (tile + 6) * M.
 // ---------------------------------------------------------------------------------------
 template <int KIND>
 __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a) {
@@ -311,12 +345,25 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
     const int64_t n = in.n;
     const int c0 = td.start;
     const int cnt = (int)((n - c0) < a.tile ? (n - c0) : a.tile);
-    const float* uin = reinterpret_cast<const float*>(a.uin) + in.off;
+    const int stage = a.stage;
+    float* u = a.u + in.off;
+    float* d1 = a.d1 + in.off;
+    float* d2 = a.d2 + in.off;
+    float* sn = a.s + in.off;
+    float* cr = a.c + in.off;
     const int span = cnt + 6;
     for (int idx = threadIdx.x; idx < span * M; idx += blockDim.x) {
         const int k = idx / span;
         const int j = idx - k * span;
-        su[j * M + k] = line_get<float>(uin + k * n, n, 1, (int64_t)c0 - 3 + j, in.bc, a.mp.inflow[k]);
+        const int64_t g = line_idx(n, (int64_t)c0 - 3 + j, in.bc);
+        float x;
+        if (g < 0)
+            x = (float)a.mp.inflow[k];
+        else if (stage == 0)
+            x = sn[k * n + g];
+        else
+            x = u[k * n + g] + (stage == 1 ? d1[k * n + g] : d2[k * n + g]);
+        su[j * M + k] = x;
     }
     const double dt = *(volatile double*)&ctl->dt;
     const float alpha = (float)*(volatile double*)&ctl->alpha;
@@ -344,39 +391,44 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
     }
     __syncthreads();
     // U: cells
-    float* uout = reinterpret_cast<float*>(a.uout) + in.off;
-    const float* un = reinterpret_cast<const float*>(a.un) + in.off;
     const float lam = (float)(dt / in.dx);
     float vmaxf = 0.0f;
     bool bad = false;
     for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
         const int e = q + 3;
+        const int64_t gi = c0 + q;
         float hl[M], hr[M], U[M];
         lf_flux<float, KIND, M>(svm + (e - 1) * M, svp + e * M, alpha, a.mp, 0, hl);
         lf_flux<float, KIND, M>(svm + e * M, svp + (e + 1) * M, alpha, a.mp, 0, hr);
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-            const float uk = su[e * M + k];
             const float du = lam * (hl[k] - hr[k]);
-            float o;
-            if (a.stage == 0) {
-                o = uk + du;
-            } else if (a.stage == 1) {
-                o = fmaf(0.75f, un[k * n + c0 + q], 0.25f * (uk + du));
+            const int64_t ix = k * n + gi;
+            if (stage == 0) {
+                u[ix] = su[e * M + k];  // commit u^n (the state s of the previous step)
+                d1[ix] = du;
+                bad |= !finite_(du);
+            } else if (stage == 1) {
+                const float v = 0.25f * (d1[ix] + du);
+                d2[ix] = v;
+                bad |= !finite_(v);
             } else {
-                o = fmaf(1.0f / 3.0f, un[k * n + c0 + q], (2.0f / 3.0f) * (uk + du));
+                const float base = u[ix];
+                const float y = kTwoThirdsF * (d2[ix] + du) + cr[ix];
+                const float t = base + y;
+                cr[ix] = y - (t - base);
+                sn[ix] = t;
+                U[k] = t;
+                bad |= !finite_(t);
             }
-            uout[k * n + c0 + q] = o;
-            U[k] = o;
-            bad |= !finite_(o);
         }
-        if (a.stage == 2) {
-            const float s = wave_speed<float, KIND>(U, a.mp, 0);
-            bad |= !finite_(s);
-            vmaxf = s > vmaxf ? s : vmaxf;
+        if (stage == 2) {
+            const float sp = wave_speed<float, KIND>(U, a.mp, 0);
+            bad |= !finite_(sp);
+            vmaxf = sp > vmaxf ? sp : vmaxf;
         }
     }
-    if (a.stage == 2 && a.advance) {
+    if (stage == 2 && a.advance) {
         const double b = block_max_nan((double)vmaxf, bad, red, redbad);
         if (threadIdx.x == 0) {
             atomicMax(&ctl->alpha_next_bits, (unsigned long long)__double_as_longlong(b));
@@ -387,6 +439,22 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
                 finalize_1d(ctl, in);
             }
         }
+    }
+}
+
+// s = u and c = 0 over the tiles (before the first step); u = s (after the last)
+static __global__ void comp_copy_kernel(float* dst, const float* src, float* zero, const InstDev* __restrict__ inst,
+                                 const Tile* __restrict__ tiles, int tile, int m) {
+    const Tile td = tiles[blockIdx.x];
+    const InstDev in = inst[td.inst];
+    const int64_t n = in.n;
+    const int c0 = td.start;
+    const int cnt = (int)((n - c0) < tile ? (n - c0) : tile);
+    for (int idx = threadIdx.x; idx < cnt * m; idx += blockDim.x) {
+        const int k = idx / cnt, q = idx - k * cnt;
+        const int64_t ix = in.off + k * n + c0 + q;
+        dst[ix] = src[ix];
+        if (zero) zero[ix] = 0.0f;
     }
 }
 
@@ -422,15 +490,19 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
     const InstDev in = a.inst[inst_idx];
     Ctl* ctl = a.ctl + inst_idx;
     const int n = (int)in.n;
-    float* un = smf;                // [M][n]
-    float* uA = un + M * n;         // [M][n]
-    float* uB = uA + M * n;         // [M][n]
+    float* un = smf;                // [M][n] u^n
+    float* uA = un + M * n;         // [M][n] d1, then the new state
+    float* uB = uA + M * n;         // [M][n] d2
     float* se = uB + M * n;         // [M][n+1]
     float* svm = se + M * (n + 1);  // [M][n+2]
     float* svp = svm + M * (n + 2); // [M][n+2]
     const fast::FParams fp = fast::fparams(a.mp);
     float* g = reinterpret_cast<float*>(a.arena) + in.off;
-    for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) un[idx] = g[idx];
+    float* cr = a.carry + in.off;
+    for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) {
+        un[idx] = g[idx];
+        cr[idx] = 0.0f;
+    }
     float inflow[M];
 #pragma unroll
     for (int k = 0; k < M; ++k) inflow[k] = (float)a.mp.inflow[k];
@@ -485,8 +557,10 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
         bad = false;
 #pragma unroll 1
         for (int stage = 0; stage < 3; ++stage) {
-            const float* X = stage == 0 ? un : (stage == 1 ? uA : uB);
-            float* Y = stage == 0 ? uA : (stage == 1 ? uB : un);
+            // stage input u^(k) = u^n + d_k, formed on the fly (increment form, see
+            // stage1d_fast_kernel); stage 3 writes the new state into uA
+            const float* D = stage == 1 ? uA : uB;
+#define NPW_X(idx) (stage == 0 ? un[(idx)] : un[(idx)] + D[(idx)])
             if (lo < hi) {
                 // F: eta of faces lo..hi (cells f-2..f+1)
                 for (int f = lo + lane; f <= hi; f += 32) {
@@ -496,7 +570,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const int c = res_map(f - 2 + j, n, in.bc);
-                            w[j] = c < 0 ? inflow[k] : X[k * n + c];
+                            w[j] = c < 0 ? inflow[k] : NPW_X(k * n + c);
                         }
                         uint32_t fl = 0;
                         se[k * (n + 1) + f] = fast::face_eta(w[0], w[1], w[2], w[3], fp, &fl);
@@ -511,7 +585,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
 #pragma unroll
                         for (int j = 0; j < 5; ++j) {
                             const int cc = res_map(i - 2 + j, n, in.bc);
-                            c[j] = cc < 0 ? inflow[k] : X[k * n + cc];
+                            c[j] = cc < 0 ? inflow[k] : NPW_X(k * n + cc);
                         }
                         const float er = (i + 1 <= hi) ? se[k * (n + 1) + i + 1] : 0.0f;
                         const float el = (i >= lo) ? se[k * (n + 1) + i] : 0.0f;
@@ -539,18 +613,23 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
 #pragma unroll
                     for (int k = 0; k < M; ++k) {
                         const float du = lam * (hl[k] - hr[k]);
-                        const float x = X[k * n + i];
-                        float o;
+                        const int ix = k * n + i;
                         if (stage == 0) {
-                            o = x + du;
+                            uA[ix] = du;
+                            U[k] = du;
                         } else if (stage == 1) {
-                            o = fmaf(0.75f, un[k * n + i], 0.25f * (x + du));
+                            const float v = 0.25f * (uA[ix] + du);
+                            uB[ix] = v;
+                            U[k] = v;
                         } else {
-                            o = fmaf(1.0f / 3.0f, un[k * n + i], (2.0f / 3.0f) * (x + du));
+                            const float base = un[ix];
+                            const float y = kTwoThirdsF * (uB[ix] + du) + cr[ix];
+                            const float t = base + y;
+                            cr[ix] = y - (t - base);
+                            uA[ix] = t;
+                            U[k] = t;
                         }
-                        Y[k * n + i] = o;
-                        U[k] = o;
-                        bad |= !finite_(o);
+                        bad |= !finite_(U[k]);
                     }
                     if (stage == 2) {
                         const float sp = wave_speed<float, KIND>(U, a.mp, 0);
@@ -560,6 +639,12 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
                 }
             }
             __syncthreads();
+#undef NPW_X
+        }
+        {  // the new state (in uA) becomes u^n
+            float* tmp = un;
+            un = uA;
+            uA = tmp;
         }
         const double b = block_max_nan((double)vmaxf, bad, red, redbad);
         if (threadIdx.x == 0) {
@@ -703,7 +788,7 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
                 } else if (a.stage == 1) {
                     o = R(0.75) * un[gidx] + R(0.25) * (uk + dtR * L);
                 } else {
-                    o = R(1.0 / 3.0) * un[gidx] + R(2.0 / 3.0) * (uk + dtR * L);
+                    o = stage3_w1<R>() * un[gidx] + stage3_w2<R>() * (uk + dtR * L);
                 }
                 uout[gidx] = o;
                 U[k] = o;

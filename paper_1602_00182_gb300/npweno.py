@@ -28,7 +28,8 @@ class npw_params(C.Structure):
                 ("switch_variant", C.c_int32), ("characteristic", C.c_int32), ("precision", C.c_int32),
                 ("eta_eval", C.c_int32), ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
                 ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4),
-                ("eta_guard", C.c_double), ("batch_mode", C.c_int32), ("pad_", C.c_int32)]
+                ("eta_guard", C.c_double), ("batch_mode", C.c_int32), ("pad_", C.c_int32),
+                ("eta_max", C.c_double)]
 
 
 class npw_solve_stats(C.Structure):
@@ -65,6 +66,7 @@ class Params:
     inflow: Sequence[float] = (0.0, 0.0, 0.0, 0.0)
     eta_guard: float = 0.0
     batch_mode: int = 0
+    eta_max: float = 0.0
     k: int = 3
 
     def c(self) -> npw_params:
@@ -72,7 +74,7 @@ class Params:
         for f in ("k", "scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "precision",
                   "eta_eval", "batch_mode"):
             setattr(p, f, int(getattr(self, f)))
-        for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "eta_guard"):
+        for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "eta_guard", "eta_max"):
             setattr(p, f, float(getattr(self, f)))
         for i in range(4):
             p.inflow[i] = float(self.inflow[i]) if i < len(self.inflow) else 0.0

@@ -1,0 +1,121 @@
+"""Parity at the workloads' full sizes, in the launch configuration the benchmark uses.
+
+The oracle cannot run the full workloads, so full-size runs are checked by properties that hold
+at any size (every instance finishes at its t_end, stays finite, conserves its periodic sum within
+the float-state bound) and, on sampled instances, against the oracle started from the same
+float-rounded data, within the mixed-precision bars of test_gpu_parity."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1602_00182_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+MIXED_GUARD = 8.0 * 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def npw():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1602_00182_gb300 import build as b
+    b.build()
+    import paper_1602_00182_gb300.npweno as m
+    m.load()
+    return m
+
+
+def test_burgers_batch_full_size(npw):
+    """4096 periodic Burgers instances, N log-uniform in [64, 8192], to T = 1.5 (the benchmark's
+    workload and launch configuration: resident whole-solve kernels, eta in FP64)."""
+    inst = I.burgers_batch(count=4096, seed_index=1)
+    order = sorted(range(len(inst)), key=lambda i: -inst[i].n)
+    ns = [inst[i].n for i in order]
+    table, total = npw.make_instances(ns, [inst[i].dx for i in order], [1.5] * len(ns), [0.5] * len(ns),
+                                      [0] * len(ns))
+    host0 = np.concatenate([inst[i].u0[0] for i in order]).astype(np.float32)
+    arena = torch.tensor(host0, device="cuda")
+    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED)
+    st, stats = npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, p)
+    assert st == 0
+    a = arena.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(a))
+    offs = np.concatenate([[0], np.cumsum(ns)])
+    for k, s in enumerate(stats):
+        assert s["status"] == 0 and s["t"] == 1.5
+        # periodic sum: conserved up to the float rounding of the updates (3 per step)
+        seg0 = host0[offs[k]:offs[k + 1]].astype(np.float64)
+        seg = a[offs[k]:offs[k + 1]]
+        drift = abs(seg.sum() - seg0.sum())
+        assert drift <= 4.0 * 2.0 ** -24 * np.abs(seg0).max() * np.sqrt(3.0 * s["steps"] * ns[k]) + 1e-3, k
+    # sampled instances against the oracle (one per decade of N, small enough for the CPU)
+    op = O.Params(rbf=O.GA, eta_guard=MIXED_GUARD)
+    for k in [len(ns) - 1, len(ns) - 200, len(ns) - 900, len(ns) - 1500]:
+        u0 = host0[offs[k]:offs[k + 1]].astype(np.float64)
+        dx = inst[order[k]].dx
+        ref, rst = O.solve(u0, dx, 1.5, 0.5, O.BURGERS, O.PERIODIC, op)
+        e = np.abs(a[offs[k]:offs[k + 1]] - ref)
+        assert e.mean() <= 1e-4 and e.max() <= 2e-2, (k, ns[k], e.mean(), e.max())
+
+
+@pytest.mark.parametrize("char", [0, 1])
+def test_euler_batch_full_size(npw, char):
+    """512 transmissive Euler instances, N log-uniform in [256, 65536] (Riemann and
+    Shu-Osher-type data), component- and characteristic-wise, advanced to 2% of their end time
+    (the full run is ~1e11 cell-updates): every instance finishes, density and pressure stay
+    positive, and sampled instances match the oracle."""
+    inst = I.euler_batch(count=512, seed_index=2)
+    ns = [it.n for it in inst]
+    tends = [0.02 * it.t_end for it in inst]
+    table, total = npw.make_instances(ns, [it.dx for it in inst], tends, [0.5] * len(ns), [1] * len(ns), m=3)
+    host0 = np.concatenate([it.u0.ravel() for it in inst]).astype(np.float32)
+    arena = torch.tensor(host0, device="cuda")
+    p = npw.Params(precision=npw.NPW_FP32_MIXED, characteristic=char)
+    st, stats = npw.npweno_batch_solve(arena, table, 3, npw.NPW_FLUX_EULER1D, p)
+    assert st == 0
+    a = arena.cpu().numpy().astype(np.float64)
+    off = 0
+    sampled = 0
+    op = O.Params(characteristic=char, eta_guard=MIXED_GUARD)
+    for k, it in enumerate(inst):
+        U = a[off:off + 3 * it.n].reshape(3, it.n)
+        assert stats[k]["status"] == 0 and stats[k]["t"] == tends[k]
+        rho = U[0]
+        P = 0.4 * (U[2] - 0.5 * U[1] ** 2 / rho)
+        assert rho.min() > 0 and P.min() > 0
+        if it.n <= 1200 and sampled < 3:
+            u0 = host0[off:off + 3 * it.n].astype(np.float64).reshape(3, it.n)
+            ref, _ = O.solve(u0, it.dx, tends[k], 0.5, O.EULER1D, O.TRANSMISSIVE, op)
+            e = np.abs(U - ref) / np.abs(ref).max(axis=1, keepdims=True)
+            assert e.mean() <= 1e-4 and e.max() <= 2e-2, (k, it.n, e.mean(), e.max())
+            sampled += 1
+        off += 3 * it.n
+    assert sampled == 3
+
+
+@pytest.mark.parametrize("n", [256, 2048])
+def test_2d_euler_full_size_step(npw, n):
+    """2D Euler, dimension by dimension, on the largest square (2048^2) and the smallest: one RK3
+    step of four-quadrant data from the GPU against the oracle's step of the same float data,
+    and ten steps of the isentropic vortex staying finite and conserved."""
+    U, d = I.four_quadrant(n, np.random.default_rng(n))
+    U32 = U.astype(np.float32)
+    gu = torch.tensor(U32, device="cuda")
+    p = npw.Params(precision=npw.NPW_FP32_MIXED)
+    npw.npweno_rk3_step_2d(gu, d, d, 0.2 * d, npw.NPW_FLUX_EULER2D, 0, p)
+    ref = O.rk3_step_2d(U32.astype(np.float64), d, d, 0.2 * d, O.EULER2D, O.PERIODIC,
+                        O.Params(eta_guard=MIXED_GUARD))
+    got = gu.cpu().numpy().astype(np.float64)
+    rel = np.abs(got - ref).max() / np.abs(ref).max()
+    assert rel <= 2e-6, rel
+    if n > 256:
+        return
+    V, d = I.isentropic_vortex(n, 4.0, 5.0, 5.0, npts=2)
+    gv = torch.tensor(V.astype(np.float32), device="cuda")
+    s0 = gv.double().sum(dim=(1, 2)).cpu().numpy()
+    st = npw.npweno_solve_2d(gv, d, d, 10 * 0.25 * d, 0.5, npw.NPW_FLUX_EULER2D, 0, p)
+    assert st["status"] == 0
+    s1 = gv.double().sum(dim=(1, 2)).cpu().numpy()
+    assert np.all(np.isfinite(gv.cpu().numpy()))
+    assert np.all(np.abs(s1 - s0) <= 1e-5 * np.abs(s0))

@@ -16,6 +16,7 @@ import pytest
 from fractions import Fraction as F
 
 import oracle as O
+from paper_1602_00182_gb300 import inputs as I
 from tests import bruteforce as B
 
 
@@ -172,8 +173,9 @@ def test_bruteforce_tiny_grid(scheme, rbf, switch):
         n = 8
         vals = [F(int(x), 16) for x in g.integers(-32, 33, size=n)]
         vmx, vpx = B.reconstruct_periodic(vals, scheme, rbf=rbf, monotone_switch=switch)
+        # random data can give |eta| > 1: compare the paper's formula without the eta bound
         p = O.Params(scheme=O.SCHEMES[scheme], rbf=O.MQ if rbf == "mq" else O.GA, monotone_switch=int(switch),
-                     tie_tol=1e-9)
+                     tie_tol=1e-9, eta_max=0.0)
         vm, vp, fl, eta = O.reconstruct(np.array([float(x) for x in vals]), O.PERIODIC, p)
         ties = (fl & (O.FLAG_SWITCH_TIE | O.FLAG_ENO_TIE_L | O.FLAG_ENO_TIE_R)) != 0
         for f in range(n + 1):
@@ -200,11 +202,30 @@ def test_eta_guard_on_unresolved_denominator():
     P = lambda x: x ** 4 / 4
     avg = P(edges[1:]) - P(edges[:-1])  # exact averages of x^3 on unit cells
     face = 5  # face x = 0 between cell 4 and cell 5
-    p0 = O.Params(scheme=O.RBF_WENO, monotone_switch=1)
+    p0 = O.Params(scheme=O.RBF_WENO, monotone_switch=1, eta_max=0.0)
     _, _, _, eta0 = O.reconstruct(avg, O.TRANSMISSIVE, p0)
     assert abs(eta0[face]) > 1e10  # num / eps_M
-    p1 = O.Params(scheme=O.RBF_WENO, monotone_switch=1, eta_guard=8 * 2.0 ** -24)
+    p1 = O.Params(scheme=O.RBF_WENO, monotone_switch=1, eta_guard=8 * 2.0 ** -24, eta_max=0.0)
     _, _, _, eta1 = O.reconstruct(avg, O.TRANSMISSIVE, p1)
     assert eta1[face] == 0.0
     other = [f for f in range(3, 9) if f != face]
     np.testing.assert_array_equal(eta1[other], eta0[other])
+
+
+def test_eta_bound_on_monotone_zero_slope_stencil():
+    """A monotone stencil with nearly zero slope at the face, (-1, -1/15 - 1e-3, 1/15 + 1e-3, 1):
+    12 p'(s) = 9.56 s^2 + 0.03 > 0 (the switch does not fire) while the Table k3 denominator is
+    only 0.03, so eta = -53 (at (-1, -1/15, 1/15, 1) it would be num / eps_M ~ 1e12).  The bound
+    eta_max (a reading, default 1) returns the polynomial reconstruction there; the smooth data
+    of the paper's tests have |eta| < 0.05 and are untouched."""
+    w = np.array([3.0, 3.0, -1.0, -1.0 / 15.0 - 1e-3, 1.0 / 15.0 + 1e-3, 1.0, 1.0, 1.0])
+    fires, near = O.switch_k3(w[2:6], tol=1e-9)
+    assert not fires and not near
+    _, _, _, eta_off = O.reconstruct(w, O.TRANSMISSIVE, O.Params(eta_max=0.0))
+    _, _, _, eta_on = O.reconstruct(w, O.TRANSMISSIVE, O.Params())
+    face = 4  # between cells 3 and 4: stencil cells 2..5
+    assert eta_off[face] == pytest.approx(-1.594 / 0.03, rel=1e-6) and eta_on[face] == 0.0
+    u, dx = I.advection_sin(40)
+    _, _, _, e1 = O.reconstruct(u, O.PERIODIC, O.Params())
+    _, _, _, e0 = O.reconstruct(u, O.PERIODIC, O.Params(eta_max=0.0))
+    np.testing.assert_array_equal(e1, e0)
