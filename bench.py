@@ -407,6 +407,148 @@ def serving_block(npw, count: int, rate: float):
     }
 
 
+# ------------------------------------------------------------------------------- other workloads
+def _timed(fn, steps, flush, world):
+    import torch
+    times = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times
+
+
+def run_euler1d(args, rank, world, local_rank):
+    """Batched 1D Euler (512 instances, N log-uniform in [256, 65536], transmissive, Riemann and
+    Shu-Osher-type data) through the per-stage kernels (batch_mode 1), to t_frac of each end time."""
+    import torch
+    import paper_1602_00182_gb300.npweno as npw
+    from paper_1602_00182_gb300 import build as b
+    b.build()
+    lib = npw.load()
+    torch.cuda.set_device(local_rank)
+    inst = I.euler_batch(count=512, seed_index=2 + 1000 * rank)
+    ns = [it.n for it in inst]
+    tends = [args.t_frac * it.t_end for it in inst]
+    table, total = npw.make_instances(ns, [it.dx for it in inst], tends, [CFL] * len(ns), [1] * len(ns), m=3)
+    host0 = np.concatenate([it.u0.ravel() for it in inst]).astype(np.float32)
+    pristine = torch.tensor(host0, device="cuda")
+    arena = pristine.clone()
+    p = npw.Params(precision=npw.NPW_FP32_MIXED, characteristic=args.characteristic, batch_mode=1)
+    ws = torch.empty(npw.npw_batch_workspace_size(table, 3, p), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    holder = {}
+
+    def one():
+        arena.copy_(pristine)
+        st, stats = npw.npweno_batch_solve(arena, table, 3, npw.NPW_FLUX_EULER1D, p, workspace=ws)
+        if st != 0:
+            raise RuntimeError(f"batch solve failed: {st}")
+        holder["stats"] = stats
+
+    for _ in range(args.warmup):
+        one()
+    pr = npw_profile()
+    lib.npw_profile_reset()
+    lib.npw_profile_enable(1)
+    times = _timed(one, args.steps, flush, world)
+    lib.npw_profile_read(ctypes.byref(pr))
+    lib.npw_profile_enable(0)
+    stats = holder["stats"]
+    cu = sum(n * s["steps"] for n, s in zip(ns, stats))
+    faces = sum((n + 1) * 3 * 3 * s["steps"] for n, s in zip(ns, stats)) * args.steps
+    st_s = pr.stage_ms / 1e3
+    fp64 = FP64_OPS_PER_ETA * faces / st_s / 1e9 if (st_s > 0 and not args.characteristic) else None
+    alg_bytes = cu * args.steps * 3 * 44  # per field: 12 + 12 + 20 B over the three compensated stages
+    return {
+        "metric": "cell-updates/s", "value": cu * args.steps / (sum(times) / 1e3), "unit": "cell-updates/s",
+        "ms_per_step": sum(times) / len(times),
+        "config": {"workload": ("batched 1D Euler (m=3, gamma=1.4), transmissive: 512 instances, N log-uniform "
+                                f"[256,65536], Riemann + Shu-Osher-type data, {'characteristic' if args.characteristic else 'component'}-wise, "
+                                f"RBF-WENO5 MQ + switch, LF, TVD-RK3 CFL 0.5 to {args.t_frac} x each end time"),
+                   "instances": 512, "cells": int(sum(ns)), "cell_updates_per_step": int(cu),
+                   "path": "per-stage fused kernels (batch_mode 1), 1024-cell tiles", "l2": "flushed before every timed step"},
+        "roofline": {"bound": "alu", "achieved": fp64, "peak": FP64_PIPE_PEAK / 1e9, "unit": "G FP64-pipe instr/s",
+                     "frac": (fp64 / (FP64_PIPE_PEAK / 1e9)) if fp64 else None, "traffic": None,
+                     "kernel": "stage1d_fast_kernel<EULER1D>",
+                     "hbm_view": {"achieved_gbs": alg_bytes / st_s / 1e9 if st_s > 0 else None,
+                                  "peak_gbs": _peaks()[0], "bytes_per_cell_update": 132},
+                     "stage_launches": int(pr.stage_launches), "stage_ms": pr.stage_ms},
+        "gpu_launches": int(pr.kernel_launches),
+    }
+
+
+def run_euler2d(args, rank, world, local_rank):
+    """2D Euler, dimension by dimension, on periodic squares: 4 x 2048^2 (2^24 cells), isentropic
+    vortices and four-quadrant data, ~100 RK3 steps at CFL 0.5 each."""
+    import torch
+    import paper_1602_00182_gb300.npweno as npw
+    from paper_1602_00182_gb300 import build as b
+    b.build()
+    lib = npw.load()
+    torch.cuda.set_device(local_rank)
+    n = args.n2d
+    count = max(1, (1 << 24) // (n * n))
+    doms = I.euler2d_batch(n, count, seed_index=3 + 1000 * rank)
+    p = npw.Params(precision=npw.NPW_FP32_MIXED)
+    pristine = [torch.tensor(U.astype(np.float32), device="cuda") for U, d in doms]
+    work = [x.clone() for x in pristine]
+    ws = torch.empty(npw.npw_workspace_size_2d(n, n, 4, p), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tends = []
+    for U, d in doms:
+        rho, mx, my, E = U
+        u, v = mx / rho, my / rho
+        c = np.sqrt(1.4 * 0.4 * (E - 0.5 * rho * (u * u + v * v)) / rho)
+        rate = (np.abs(u) + c).max() / d + (np.abs(v) + c).max() / d
+        tends.append(args.steps2d * CFL / rate)
+    holder = {}
+
+    def one():
+        tot = 0
+        for k, (U, d) in enumerate(doms):
+            work[k].copy_(pristine[k])
+            st = npw.npweno_solve_2d(work[k], d, d, tends[k], CFL, npw.NPW_FLUX_EULER2D, 0, p, workspace=ws)
+            tot += n * n * st["steps"]
+        holder["cu"] = tot
+
+    for _ in range(args.warmup):
+        one()
+    pr = npw_profile()
+    lib.npw_profile_reset()
+    lib.npw_profile_enable(1)
+    times = _timed(one, args.steps, flush, world)
+    lib.npw_profile_read(ctypes.byref(pr))
+    lib.npw_profile_enable(0)
+    cu = holder["cu"]
+    st_s = pr.stage_ms / 1e3
+    fp64 = FP64_OPS_PER_ETA * cu * args.steps * 3 * 4 * 2 / st_s / 1e9 if st_s > 0 else None
+    return {
+        "metric": "cell-updates/s", "value": cu * args.steps / (sum(times) / 1e3), "unit": "cell-updates/s",
+        "ms_per_step": sum(times) / len(times),
+        "config": {"workload": (f"2D Euler dimension by dimension, periodic {n}^2 x {count} (isentropic vortex + "
+                                "four-quadrant), RBF-WENO5 MQ + switch, one midpoint point per face, ~"
+                                f"{args.steps2d} RK3 steps at CFL 0.5"),
+                   "domains": count, "cells": n * n * count, "cell_updates_per_step": int(cu),
+                   "l2": "flushed before every timed step"},
+        "roofline": {"bound": "alu", "achieved": fp64, "peak": FP64_PIPE_PEAK / 1e9, "unit": "G FP64-pipe instr/s",
+                     "frac": (fp64 / (FP64_PIPE_PEAK / 1e9)) if fp64 else None, "traffic": None,
+                     "kernel": "stage2d_kernel<float,double,EULER2D>",
+                     "hbm_view": {"achieved_gbs": cu * args.steps * 128 / st_s / 1e9 if st_s > 0 else None,
+                                  "peak_gbs": _peaks()[0], "bytes_per_cell_update": 128},
+                     "stage_launches": int(pr.stage_launches), "stage_ms": pr.stage_ms},
+        "gpu_launches": int(pr.kernel_launches),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,6 +557,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--t-end", type=float, default=T_END, help="final time (shorter only for profiling runs)")
+    ap.add_argument("--workload", default="burgers", choices=["burgers", "euler1d", "euler2d"],
+                    help="burgers: the headline batch; euler1d / euler2d: the other families (separate lines)")
+    ap.add_argument("--t-frac", type=float, default=0.1, help="euler1d: fraction of each instance's end time")
+    ap.add_argument("--characteristic", type=int, default=0, help="euler1d: characteristic-wise reconstruction")
+    ap.add_argument("--n2d", type=int, default=2048, help="euler2d: square size")
+    ap.add_argument("--steps2d", type=int, default=100, help="euler2d: RK3 steps per solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eta-eval", type=int, default=0, choices=[0, 1],
                     help="0: eta in FP64 (the configuration's FP64 shape-parameter step); 1: exact double-float")
@@ -458,6 +606,17 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.workload != "burgers":
+        fn = run_euler1d if args.workload == "euler1d" else run_euler2d
+        out = fn(args, rank, world, local_rank)
+        out.update({"n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)", "impl": "ours"})
+        if rank == 0:
+            print(json.dumps(out))
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
     out, inst = run_gpu(args, rank, world, local_rank)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         import paper_1602_00182_gb300.npweno as npw

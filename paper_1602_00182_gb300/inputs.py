@@ -226,7 +226,7 @@ def euler2d_batch(n: int, count: int, seed_index: int = 3):
     out = []
     for i in range(count):
         if i % 2 == 0:
-            U, d = isentropic_vortex(n, g.uniform(3.0, 5.0), g.uniform(0.0, 10.0), g.uniform(0.0, 10.0))
+            U, d = isentropic_vortex(n, g.uniform(3.0, 5.0), g.uniform(0.0, 10.0), g.uniform(0.0, 10.0), npts=2)
         else:
             U, d = four_quadrant(n, g)
         out.append((U, d))
