@@ -4,9 +4,13 @@
 Workload (one "step" = one whole solve of the batch): 4096 periodic Burgers instances on
 [0, 2 pi], N log-uniform in [64, 8192] (seeded), u0 = 1 + four Fourier modes + up to two
 jumps, Gaussian perturbation with the monotone switch, Lax-Friedrichs flux, TVD-RK3 at
-CFL 0.5, run past shock formation to T = 1.5; float state, shape parameter / switch /
-smoothness indicators in double.  Each instance keeps its own dt; the batch runs through
-the fused per-stage kernels of libnpweno over a work list of (instance, tile) pairs.
+CFL 0.5, run past shock formation to T = 1.5.  Float state, candidates, weights and flux;
+the shape parameter eta in double; switch and ENO decisions certified equal to their double
+evaluation.  Each instance keeps its own dt; every instance fits in shared memory, so the
+batch runs in the resident whole-solve kernel (four size classes on side streams).
+
+`--workload euler1d` (512 transmissive Euler instances, per-stage kernels) and
+`--workload euler2d` (2D Euler on 2048^2 squares) print their own lines.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead, on
 a bounded sample of the same workload.
@@ -138,7 +142,7 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
 
-    inst = I.burgers_batch(count=args.instances, seed_index=1 + 1000 * rank)
+    inst = I.burgers_batch(count=args.instances, seed_index=rank_seed(1, rank))
     # largest instances first in the arena (the work list follows the arena order)
     order = sorted(range(len(inst)), key=lambda i: -inst[i].n)
     ns = [inst[i].n for i in order]
@@ -185,16 +189,7 @@ def run_gpu(args, rank, world, local_rank):
             times.append(e0.elapsed_time(e1))
     lib.npw_profile_read(ctypes.byref(pr))
     lib.npw_profile_enable(0)
-    total_ms = sum(times)
-    tmax = total_ms
-    cu_all = cell_updates * args.steps
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tmax = t.item()
-        c = torch.tensor([float(cu_all)], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(c, op=torch.distributed.ReduceOp.SUM)
-        cu_all = c.item()
+    tmax, cu_all = job_totals(sum(times), cell_updates * args.steps, world, dev)
     value = cu_all / (tmax / 1e3)
 
     # Roofline of the dominant kernel.  Every instance of this workload fits in shared memory,
@@ -224,10 +219,8 @@ def run_gpu(args, rank, world, local_rank):
         pinned_out.copy_(arena, non_blocking=True)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-    e2e_value = cell_updates * args.steps / sum(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_value * world], dtype=torch.float64, device=dev)
-        e2e_value = t.item()
+    e2e_ms, e2e_units = job_totals(1e3 * sum(e2e_times), cell_updates * args.steps, world, dev)
+    e2e_value = e2e_units / (e2e_ms / 1e3)
 
     variants = {}
     if args.variant_steps > 0 and args.eta_eval == 0 and world == 1:
@@ -407,6 +400,26 @@ def serving_block(npw, count: int, rate: float):
     }
 
 
+# ------------------------------------------------------------------------------- ranks
+def rank_seed(base: int, rank: int) -> int:
+    """Seed index of a rank's batch: every rank solves its own seeded batch of the same family
+    and size (weak scaling; the instances are independent, so no data crosses ranks)."""
+    return base + 1000 * rank
+
+
+def job_totals(total_ms: float, units: float, world: int, device):
+    """Whole-job figures: the slowest rank's time and the units all ranks processed (the only
+    two collectives of the benchmark; none on the data path)."""
+    if world <= 1:
+        return total_ms, units
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    c = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(c, op=torch.distributed.ReduceOp.SUM)
+    return t.item(), c.item()
+
+
 # ------------------------------------------------------------------------------- other workloads
 def _timed(fn, steps, flush, world):
     import torch
@@ -435,7 +448,7 @@ def run_euler1d(args, rank, world, local_rank):
     b.build()
     lib = npw.load()
     torch.cuda.set_device(local_rank)
-    inst = I.euler_batch(count=512, seed_index=2 + 1000 * rank)
+    inst = I.euler_batch(count=512, seed_index=rank_seed(2, rank))
     ns = [it.n for it in inst]
     tends = [args.t_frac * it.t_end for it in inst]
     table, total = npw.make_instances(ns, [it.dx for it in inst], tends, [CFL] * len(ns), [1] * len(ns), m=3)
@@ -468,9 +481,10 @@ def run_euler1d(args, rank, world, local_rank):
     st_s = pr.stage_ms / 1e3
     fp64 = FP64_OPS_PER_ETA * faces / st_s / 1e9 if (st_s > 0 and not args.characteristic) else None
     alg_bytes = cu * args.steps * 3 * 44  # per field: 12 + 12 + 20 B over the three compensated stages
+    tmax, cu_all = job_totals(sum(times), cu * args.steps, world, torch.device("cuda", local_rank))
     return {
-        "metric": "cell-updates/s", "value": cu * args.steps / (sum(times) / 1e3), "unit": "cell-updates/s",
-        "ms_per_step": sum(times) / len(times),
+        "metric": "cell-updates/s", "value": cu_all / (tmax / 1e3), "unit": "cell-updates/s",
+        "ms_per_step": tmax / len(times),
         "config": {"workload": ("batched 1D Euler (m=3, gamma=1.4), transmissive: 512 instances, N log-uniform "
                                 f"[256,65536], Riemann + Shu-Osher-type data, {'characteristic' if args.characteristic else 'component'}-wise, "
                                 f"RBF-WENO5 MQ + switch, LF, TVD-RK3 CFL 0.5 to {args.t_frac} x each end time"),
@@ -497,7 +511,7 @@ def run_euler2d(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     n = args.n2d
     count = max(1, (1 << 24) // (n * n))
-    doms = I.euler2d_batch(n, count, seed_index=3 + 1000 * rank)
+    doms = I.euler2d_batch(n, count, seed_index=rank_seed(3, rank))
     p = npw.Params(precision=npw.NPW_FP32_MIXED)
     pristine = [torch.tensor(U.astype(np.float32), device="cuda") for U, d in doms]
     work = [x.clone() for x in pristine]
@@ -531,9 +545,10 @@ def run_euler2d(args, rank, world, local_rank):
     cu = holder["cu"]
     st_s = pr.stage_ms / 1e3
     fp64 = FP64_OPS_PER_ETA * cu * args.steps * 3 * 4 * 2 / st_s / 1e9 if st_s > 0 else None
+    tmax, cu_all = job_totals(sum(times), cu * args.steps, world, torch.device("cuda", local_rank))
     return {
-        "metric": "cell-updates/s", "value": cu * args.steps / (sum(times) / 1e3), "unit": "cell-updates/s",
-        "ms_per_step": sum(times) / len(times),
+        "metric": "cell-updates/s", "value": cu_all / (tmax / 1e3), "unit": "cell-updates/s",
+        "ms_per_step": tmax / len(times),
         "config": {"workload": (f"2D Euler dimension by dimension, periodic {n}^2 x {count} (isentropic vortex + "
                                 "four-quadrant), RBF-WENO5 MQ + switch, one midpoint point per face, ~"
                                 f"{args.steps2d} RK3 steps at CFL 0.5"),

@@ -205,7 +205,8 @@ npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx
 /*
  * Request server: continuous batching of 1D solves (no counterpart in the paper; the serving
  * loop around the method).  The server sub-allocates a caller-provided device arena: per
- * request it needs 3 * m * n elements (state and two stage buffers) of the server's precision.
+ * request it needs 3 * m * n elements (state and two stage buffers) of the server's precision,
+ * plus 2 * m * n floats (next state and compensation carry) in mixed precision.
  * Requests are queued by npw_server_submit (non-blocking) and admitted first-in first-out
  * whenever a slot and arena space are free; every npw_server_step advances all admitted
  * requests together -- each with its own dt, alpha and t_end -- by up to max_steps RK3 steps
