@@ -280,6 +280,7 @@ def run_gpu(args, rank, world, local_rank):
             "peak_source": ("derived: 2 FP64-pipe instr/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s FP64); "
                             "probe of DFMA chains: 1.19 TFLOP/s"),
             "hbm_bytes_per_cell_update": "8 per solve (state read once, written once)",
+            "kernel_source_sha256": kernel_source_hash(),
         },
         "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": int(host0.nbytes),
                 "d2h_bytes_per_step": int(host0.nbytes)},
@@ -297,23 +298,36 @@ class npw_profile(ctypes.Structure):
 
 
 # FP64-pipe instructions of one shape-parameter evaluation in the mixed path (eta_fp64 in
-# csrc/npw_fast.cuh): 2 adds forming the exact differences, 2 multiply-adds (numerator,
-# denominator), 1 add of eps_M, 2 multiply-adds of one Newton step, 1 multiply and 2
-# multiply-adds of the residual correction, 1 conversion of the result (the float<->double
+# csrc/npw_fast.cuh): 2 adds taking the numerator and denominator pairs to double, 2 multiply-
+# adds of the Newton step, 1 multiply, 1 conversion of the result (the float<->double
 # widenings of the inputs and of the seed are integer operations).
-FP64_OPS_PER_ETA = 11
+FP64_OPS_PER_ETA = 6
 # FP64 pipe peak: 1.25 TFLOP/s nominal FP64 = 0.625e12 FMA/s over 152 SMs at 2.07 GHz, i.e.
 # 2 FP64-pipe instructions per clock per SM (a probe of independent DFMA chains measured 1.19 TFLOP/s)
 FP64_PIPE_PEAK = 2.0 * 152 * 2.07e9
 
 
+def kernel_source_hash() -> str:
+    """sha256 over the device sources of the mixed-precision kernels (ncu figures are valid only
+    for the sources they were taken from)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1602_00182_gb300", "csrc")
+    for f in ("npw_internal.h", "npw_device.cuh", "npw_fast.cuh", "npw_kernels.cuh", "npw_fp32.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _ncu_traffic():
-    """DRAM bytes per stage launch from the committed ncu summary, when it matches the
-    current kernel (null otherwise)."""
+    """DRAM bytes per launch of the dominant launch from the committed ncu summary, when it was
+    taken from the current kernel sources (null otherwise)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as fh:
             d = json.load(fh)
+        if d.get("kernel_source_sha256") != kernel_source_hash():
+            return None
         return d.get("solve1d_resident_burgers_classA_dram_bytes_per_launch")
     except Exception:
         return None

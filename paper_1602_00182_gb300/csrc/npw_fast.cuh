@@ -26,6 +26,7 @@ namespace fast {
 // float copies of the method parameters, converted once per thread
 struct FParams {
     float eps_weno, eps_M_f, eta_guard, eta_max;
+    float eps_hi, eps_lo;  // eps_M = eps_hi + eps_lo to ~2^-48
     double eps_M;
     int scheme, rbf, monotone_switch, switch_variant, eta_eval;
 };
@@ -35,6 +36,8 @@ __device__ __forceinline__ FParams fparams(const MethodParams& mp) {
     f.eps_M_f = (float)mp.eps_M;
     f.eta_guard = (float)mp.eta_guard;
     f.eta_max = (float)mp.eta_max;
+    f.eps_hi = (float)mp.eps_M;
+    f.eps_lo = (float)(mp.eps_M - (double)f.eps_hi);
     f.eps_M = mp.eps_M;
     f.scheme = mp.scheme;
     f.rbf = mp.rbf;
@@ -177,63 +180,59 @@ __device__ __forceinline__ double widen(float x) {
     const uint64_t bits = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
     return __longlong_as_double((long long)bits);
 }
-// narrow_trunc: binary64 -> binary32 by truncating the mantissa (relative error < 2^-23);
-// returns 0 when the value is outside the normal float range (the caller then takes the
-// plain division).  Used only for the seed of the reciprocal and for the guard test.
-__device__ __forceinline__ float narrow_trunc(double d) {
-    const uint64_t b = (uint64_t)__double_as_longlong(d);
-    const int e = (int)((b >> 52) & 0x7FFu) - 1023 + 127;
-    if (e <= 0 || e >= 255) return 0.0f;
-    const uint32_t r = (uint32_t)((b >> 32) & 0x80000000u) | ((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu);
-    return __uint_as_float(r);
-}
-
-// FP64 evaluation.  The differences a = w0 - w3 and b = w2 - w1 are formed exactly as float
-// pairs (two_sum) and summed exactly in double; numerator a + 3b and denominator a + 15b are
-// exact double multiply-adds.  The quotient follows the Newton-Raphson reciprocal iteration
-// with a residual correction (Markstein's scheme for division): from a float seed r0 ~ 1/den
-// (relative error < 2^-21), one Newton step r1 = r0 + r0 (1 - den r0) in double leaves
-// |r1 den - 1| < 2^-42; then q = num r1 and one correction q += (num - q den) r1 brings the
-// quotient within a few units of the last place of double, far below the rounding to float
-// that follows.  FP64-pipe instructions: 2 adds, 2 multiply-adds, 1 add of eps_M, 2 for the
-// Newton step, 1 multiply and 2 multiply-adds for the correction, 1 conversion of the result.
-__device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3, const FParams& fp, float guard) {
-    float ah, al, bh, bl;
-    two_sum(w0, -w3, ah, al);
-    two_sum(w2, -w1, bh, bl);
-    const double a = widen(ah) + widen(al);
-    const double b = widen(bh) + widen(bl);
-    const double num = fma(3.0, b, a);
-    const double den0 = fma(15.0, b, a);
-    const float den0f = narrow_trunc(den0);
-    if (guard > 0.0f && fabsf(den0f) <= guard * (1.0f + 2.0f * kU)) {
-        // near or below the guard (or outside the float range): decide exactly in double
-        if (fabs(den0) <= (double)guard) return 0.0f;
-    }
-    const double den = den0 + fp.eps_M;
-    const float denf = narrow_trunc(den);
-    if (!(fabsf(denf) > 1e-30f && fabsf(denf) < 1e30f)) return (float)(num / den);
-    double r = widen(1.0f / denf);
-    r = fma(r, fma(-den, r, 1.0), r);
-    double q = num * r;
-    q = fma(fma(-q, den, num), r, q);
-    return (float)q;
-}
-
-// exact value of the small-integer combination k0 w0 + k1 (w2 - w1)... as an unevaluated pair:
-// the differences are formed exactly with two_sum, then combined with compensated sums.
-__device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, float w3, float eps_M, float guard) {
+// Numerator a + 3b and denominator a + 15b (a = w0 - w3, b = w2 - w1) as unevaluated float
+// pairs.  The differences are exact two_sum pairs, the products 3 bh and 15 bh are split
+// exactly by fma and the leading terms are added with two_sum; the remaining small terms
+// (each within 2^-23 of a leading term) are summed in float, so each pair is within ~2^-47 of
+// its largest term.
+__device__ __forceinline__ void eta_pairs(float w0, float w1, float w2, float w3, float& nh, float& nl, float& dh,
+                                          float& dl) {
     float ah, al, bh, bl;
     two_sum(w0, -w3, ah, al);  // w0 - w3 = ah + al exactly
     two_sum(w2, -w1, bh, bl);  // w2 - w1 = bh + bl exactly
-    // num = a + 3 b, den = a + 15 b + eps_M; products by 3 and 15 made exact with fma
-    float p3 = 3.f * bh, p3e = fmaf(3.f, bh, -p3);
-    float p15 = 15.f * bh, p15e = fmaf(15.f, bh, -p15);
-    float nh, ne, dh, de;
+    const float p3 = 3.f * bh, p3e = fmaf(3.f, bh, -p3);
+    const float p15 = 15.f * bh, p15e = fmaf(15.f, bh, -p15);
+    float ne, de;
     two_sum(ah, p3, nh, ne);
     two_sum(ah, p15, dh, de);
-    float nl = ne + (al + (p3e + 3.f * bl));
-    float dl = de + (al + (p15e + 15.f * bl));
+    nl = ne + (al + (p3e + 3.f * bl));
+    dl = de + (al + (p15e + 15.f * bl));
+}
+
+// FP64 evaluation of the quotient.  Numerator and denominator come from the float pairs of
+// eta_pairs, widened exactly and added in double; eps_M is added to the denominator pair as
+// the pair eps_hi + eps_lo.  The quotient is the Newton-Raphson reciprocal iteration in
+// double: from the float seed r0 = 1 / fl(den) (relative error < 2^-23), one step
+// r1 = r0 + r0 (1 - den r0) leaves |r1 den - 1| < 2^-45, and q = num r1 is within ~2^-45 of
+// the quotient, far below the rounding to float that follows (it can differ from the
+// correctly rounded float only when the quotient lies within 2^-45 of a rounding boundary).
+// FP64-pipe instructions: 2 adds (numerator and denominator to double), 2 multiply-adds (the
+// Newton step), 1 multiply, 1 conversion of the result.
+__device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3, const FParams& fp, float guard) {
+    float nh, nl, dh, dl;
+    eta_pairs(w0, w1, w2, w3, nh, nl, dh, dl);
+    if (guard > 0.0f && fabsf(dh + dl) <= guard * (1.0f + 2.0f * kU)) {
+        // near or below the guard: decide in double
+        if (fabs(widen(dh) + widen(dl)) <= (double)guard) return 0.0f;
+    }
+    float s, t;
+    two_sum(dh, fp.eps_hi, s, t);
+    dl = dl + (t + fp.eps_lo);
+    dh = s;
+    const double num = widen(nh) + widen(nl);
+    const double den = widen(dh) + widen(dl);
+    const float denf = dh + dl;
+    if (!(fabsf(denf) > 1e-30f && fabsf(denf) < 1e30f)) return (float)(num / den);
+    double r = widen(1.0f / denf);
+    r = fma(r, fma(-den, r, 1.0), r);
+    return (float)(num * r);
+}
+
+// Double-float evaluation (no FP64 instruction): the pairs of eta_pairs, eps_M added by
+// two_sum, renormalised, and the double-float quotient (one correction of the float quotient).
+__device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, float w3, float eps_M, float guard) {
+    float nh, nl, dh, dl;
+    eta_pairs(w0, w1, w2, w3, nh, nl, dh, dl);
     if (guard > 0.0f && fabsf(dh + dl) <= guard) return 0.0f;
     float t;
     two_sum(dh, eps_M, dh, t);
@@ -299,26 +298,30 @@ __device__ __forceinline__ int cell_recon(const float* c, float eta_r, float eta
         *vp = r == 0 ? cp[0] : (r == 1 ? cp[1] : cp[2]);
         return r;
     }
-    // Jiang-Shu indicators (single precision), shared by both faces of the cell
+    // Jiang-Shu indicators (single precision), shared by both faces of the cell.  The weights
+    // use the fast float division (within 2 ulp for divisors in [2^-126, 2^126]): beta + eps is
+    // at least eps_weno and is clamped at 1e18 (differences of the cell averages near 1e9, far
+    // beyond any workload), so every divisor below stays inside that range.
+    constexpr float kBeMax = 1e18f;
     float a, b, inv[3];
     const float eps = mp.eps_weno;
     a = c[2] - 2.f * c[3] + c[4];
     b = fmaf(3.f, c[2], fmaf(-4.f, c[3], c[4]));
-    float be = fmaf(13.f / 12.f * a, a, 0.25f * b * b) + eps;
-    inv[0] = 1.0f / (be * be);
+    float be = fminf(fmaf(13.f / 12.f * a, a, 0.25f * b * b) + eps, kBeMax);
+    inv[0] = __fdividef(1.0f, be * be);
     a = c[1] - 2.f * c[2] + c[3];
     b = c[1] - c[3];
-    be = fmaf(13.f / 12.f * a, a, 0.25f * b * b) + eps;
-    inv[1] = 1.0f / (be * be);
+    be = fminf(fmaf(13.f / 12.f * a, a, 0.25f * b * b) + eps, kBeMax);
+    inv[1] = __fdividef(1.0f, be * be);
     a = c[0] - 2.f * c[1] + c[2];
     b = fmaf(-4.f, c[1], fmaf(3.f, c[2], c[0]));
-    be = fmaf(13.f / 12.f * a, a, 0.25f * b * b) + eps;
-    inv[2] = 1.0f / (be * be);
+    be = fminf(fmaf(13.f / 12.f * a, a, 0.25f * b * b) + eps, kBeMax);
+    inv[2] = __fdividef(1.0f, be * be);
     // v^-: d = (3/10, 3/5, 1/10); v^+: d = (1/10, 3/5, 3/10)
     const float am0 = 0.3f * inv[0], am1 = 0.6f * inv[1], am2 = 0.1f * inv[2];
     const float ap0 = 0.1f * inv[0], ap1 = 0.6f * inv[1], ap2 = 0.3f * inv[2];
-    *vm = fmaf(am0, cm[0], fmaf(am1, cm[1], am2 * cm[2])) / (am0 + am1 + am2);
-    *vp = fmaf(ap0, cp[0], fmaf(ap1, cp[1], ap2 * cp[2])) / (ap0 + ap1 + ap2);
+    *vm = __fdividef(fmaf(am0, cm[0], fmaf(am1, cm[1], am2 * cm[2])), am0 + am1 + am2);
+    *vp = __fdividef(fmaf(ap0, cp[0], fmaf(ap1, cp[1], ap2 * cp[2])), ap0 + ap1 + ap2);
     return 0;
 }
 

@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
         const float alphaf = s_alpha;
         vmaxf = 0.0f;
         bad = false;
-#pragma unroll 1
+#pragma unroll
         for (int stage = 0; stage < 3; ++stage) {
             // stage input u^(k) = u^n + d_k, formed on the fly (increment form, see
             // stage1d_fast_kernel); stage 3 writes the new state into uA
