@@ -31,6 +31,7 @@ MQ, GA = 0, 1
 PERIODIC, TRANSMISSIVE, INFLOW = 0, 1, 2
 ADVECTION, BURGERS, EULER1D, EULER2D = 0, 1, 2, 3
 FLAG_SWITCH, FLAG_SWITCH_TIE, FLAG_ENO_TIE_L, FLAG_ENO_TIE_R = 0x01, 0x02, 0x40, 0x80
+FLAG_SWITCH_R_K2 = 0x08  # k = 2: switch of the right cell of the face (bit 0: left cell)
 
 SCHEMES = {"eno": ENO, "weno_js": WENO_JS, "rbf_eno": RBF_ENO, "rbf_weno": RBF_WENO}
 
@@ -38,7 +39,7 @@ SCHEMES = {"eno": ENO, "weno_js": WENO_JS, "rbf_eno": RBF_ENO, "rbf_weno": RBF_W
 class _Params(C.Structure):
     _fields_ = [
         ("scheme", C.c_int), ("rbf", C.c_int), ("monotone_switch", C.c_int), ("switch_variant", C.c_int),
-        ("characteristic", C.c_int), ("pad_", C.c_int),
+        ("characteristic", C.c_int), ("k", C.c_int),
         ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
         ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4),
         ("tie_tol", C.c_double), ("eta_guard", C.c_double), ("eta_max", C.c_double),
@@ -58,6 +59,7 @@ class Params:
     monotone_switch: int = 1
     switch_variant: int = 0
     characteristic: int = 0
+    k: int = 3
     eps_M: float = 1e-12
     eps_weno: float = 1e-6
     gamma: float = 1.4
@@ -70,7 +72,7 @@ class Params:
 
     def _c(self) -> _Params:
         p = _Params()
-        for f in ("scheme", "rbf", "monotone_switch", "switch_variant", "characteristic"):
+        for f in ("scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "k"):
             setattr(p, f, int(getattr(self, f)))
         for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "tie_tol", "eta_guard", "eta_max"):
             setattr(p, f, float(getattr(self, f)))
@@ -102,6 +104,11 @@ def lib():
         _lib.orc_table_coef.restype = d
         _lib.orc_table_coef.argtypes = [i, i, i, d]
         _lib.orc_switch_k3.argtypes = [P(d), i, d, P(i)]
+        _lib.orc_table_coef_k2.restype = d
+        _lib.orc_table_coef_k2.argtypes = [i, i, i, d]
+        _lib.orc_switch_k2.argtypes = [P(d), d, P(i)]
+        _lib.orc_eta_k2.restype = d
+        _lib.orc_eta_k2.argtypes = [P(d), i, P(_Params)]
         _lib.orc_eno_choice.argtypes = [P(d), d, P(i)]
         _lib.orc_beta_k3.argtypes = [P(d), P(d)]
         _lib.orc_euler_eigvec.argtypes = [P(d), P(d), d, P(d), P(d)]
@@ -143,6 +150,27 @@ def _check(st: int, what: str):
 def table_coef(rbf: int, r: int, j: int, eta: float) -> float:
     """c_rj(eta) of Table k3 (poly row + eta * perturbation row)."""
     return lib().orc_table_coef(rbf, r, j, eta)
+
+
+def table_coef_k2(rbf: int, r: int, j: int, eta: float) -> float:
+    """c_rj(eta) of Table k2 (poly row + eta * perturbation row), r = -1, 0, 1; j = 0, 1."""
+    return lib().orc_table_coef_k2(rbf, r, j, eta)
+
+
+def switch_k2(c3, tol: float = 0.0):
+    """k = 2 switch of a cell from its stencil (cells i-1, i, i+1): (fires, near tie)."""
+    c = _f64(c3)
+    near = C.c_int(0)
+    fires = lib().orc_switch_k2(_dp(c), tol, C.byref(near))
+    return bool(fires), bool(near.value)
+
+
+def eta_k2(c3, side: int, params: "Params") -> float:
+    """k = 2 shape parameter of a cell (cells i-1, i, i+1): side 0 for v^-_{i+1/2}, 1 for
+    v^+_{i-1/2}."""
+    c = _f64(c3)
+    p = params._c()
+    return lib().orc_eta_k2(_dp(c), side, C.byref(p))
 
 
 def switch_k3(w4, variant: int = 0, tol: float = 0.0):

@@ -18,6 +18,10 @@
  *   Sec. 3.5 Table k3 (polynomial rows and MQ perturbed rows, eta = eps^2 dx^2).  The
  *            r = -1 row prints 6/11 where the row sum, the Taylor expansion and the flat
  *            limit of the RBF interpolant all require 11/6; 11/6 is used.
+ *   Sec. 3.2-3.5 Table k2 (k = 2: polynomial rows, MQ perturbed rows, eta of eq.
+ *            i+1/2_eps_approx; Gaussian eta of eq. i+1/2_eps_approx1 and its r = 0 row of eq.
+ *            i+1/2_approx1; the Gaussian r = -1, 1 rows are not printed and are derived by
+ *            the flat limit of the Gaussian interpolant, as for k = 3).
  *   Sec. 3.3 Gaussian RBF recipe; its k = 3 rows are not printed and are derived from the
  *            same recipe (flat limit of the pure Gaussian interpolant of the primitive,
  *            anchored V(x_{i+1/2}) = 0, first order in eta).
@@ -65,6 +69,39 @@ static const double PERT_GA[4][3] = {
  * (deferred by the paper to Shu's lecture notes).  v^+_{i-1/2} uses them mirrored. */
 static const double D_MINUS[3] = {3.0 / 10.0, 3.0 / 5.0, 1.0 / 10.0};
 static const double D_PLUS[3] = {1.0 / 10.0, 3.0 / 5.0, 3.0 / 10.0};
+
+/* ------------------------------------------------------------------------------------ */
+/* k = 2 tables, Sec. 3.5 Table k2.  Row r (r = -1, 0, 1 at index r+1) gives the value at */
+/* face x_{i+1/2} from the cells i-r, i-r+1.                                              */
+/* ------------------------------------------------------------------------------------ */
+static const double POLY2[3][2] = {
+    {3.0 / 2.0, -1.0 / 2.0}, /* r = -1 */
+    {1.0 / 2.0, 1.0 / 2.0},  /* r = 0 */
+    {-1.0 / 2.0, 3.0 / 2.0}, /* r = 1 */
+};
+/* Multiquadric: coefficient of eta in Table k2 (right). */
+static const double PERT2_MQ[3][2] = {
+    {-3.0 / 2.0, 1.0 / 2.0},
+    {1.0 / 4.0, 1.0 / 4.0},
+    {1.0 / 2.0, -3.0 / 2.0},
+};
+/* Gaussian: r = 0 is eq. i+1/2_approx1 (1/2 + eta/2 on both cells); r = -1 and r = 1 are not
+ * printed and follow from the flat limit of the pure Gaussian interpolant of the primitive. */
+static const double PERT2_GA[3][2] = {
+    {-2.0, 0.0},
+    {1.0 / 2.0, 1.0 / 2.0},
+    {0.0, -2.0},
+};
+/* WENO3 linear weights for v^-_{i+1/2}, r = 0 (cells i, i+1) and r = 1 (cells i-1, i);
+ * v^+_{i-1/2} uses them mirrored. */
+static const double D2_MINUS[2] = {2.0 / 3.0, 1.0 / 3.0};
+static const double D2_PLUS[2] = {1.0 / 3.0, 2.0 / 3.0};
+
+double orc_table_coef_k2(int rbf, int r, int j, double eta) {
+    if (r < -1 || r > 1 || j < 0 || j > 1) return NAN;
+    const double(*q)[2] = (rbf == ORC_RBF_GA) ? PERT2_GA : PERT2_MQ;
+    return POLY2[r + 1][j] + q[r + 1][j] * eta;
+}
 
 double orc_table_coef(int rbf, int r, int j, double eta) {
     if (r < -1 || r > 2 || j < 0 || j > 2) return NAN;
@@ -271,8 +308,15 @@ static double cell_face_value(const double c[5], int side, double eta, const orc
 /* One face, one field.  w[0..5] = cells i-2..i+3 around face i+1/2 (left cell i = w[2]). */
 /* Writes v^- (from cell i), v^+ (from cell i+1), the flag byte and eta.                  */
 /* ------------------------------------------------------------------------------------ */
+static void face_field_k2(const double w[6], const orc_params* p, const uint8_t* replay, double* vm, double* vp,
+                          uint8_t* flag, double* eta_out);
+
 static void face_field(const double w[6], const orc_params* p, const uint8_t* replay, double* vm, double* vp,
                        uint8_t* flag, double* eta_out) {
+    if (p->k == 2) {
+        face_field_k2(w, p, replay, vm, vp, flag, eta_out);
+        return;
+    }
     uint8_t fl = 0;
     double eta = 0.0;
     int rbf_scheme = (p->scheme == ORC_RBF_ENO || p->scheme == ORC_RBF_WENO);
@@ -313,6 +357,114 @@ static void face_field(const double w[6], const orc_params* p, const uint8_t* re
     if (nr) fl |= ORC_FLAG_ENO_TIE_R;
     *flag = fl;
     if (eta_out) *eta_out = eta;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* k = 2.  A cell i has the 3-cell stencil c[0..2] = cells i-1, i, i+1.                   */
+/*                                                                                        */
+/* Switch (Sec. 4, eq. root_value, eq. adaptation, as printed for k = 2): the vertex of   */
+/* the quadratic p on the stencil lies at x_p / dx = (-2c0 + 3c1 - c2) / (-c0 + 2c1 - c2)  */
+/* from x_{i-3/2}; eta = 0 for both faces of the cell when 0 < x_p / dx < 3.              */
+/* ------------------------------------------------------------------------------------ */
+int orc_switch_k2(const double c[3], double tol, int* near_tie) {
+    int near = 0;
+    int fires = k2_ratio_fires(c[0], c[1], c[2], tol, &near);
+    if (near_tie) *near_tie = near;
+    return fires;
+}
+
+/* Shape parameter of cell i, Table k2 / eq. i+1/2_eps_approx (MQ) and eq. i+1/2_eps_approx1
+ * (Gaussian, half the MQ value; eps_M added as for MQ).  side 0: eta of v^-_{i+1/2}, which
+ * estimates v and v'' at x_{i+1/2} from the cells i-1, i, i+1; side 1: eta of v^+_{i-1/2},
+ * the mirror image (the same cells read from the right).  Applies the optional guard and
+ * bound of the k = 3 path, with the magnitudes of the denominator's terms. */
+double orc_eta_k2(const double c[3], int side, const orc_params* p) {
+    double a = (side == 0) ? c[0] : c[2]; /* far cell behind the face's cell */
+    double b = c[1];
+    double d = (side == 0) ? c[2] : c[0]; /* cell across the face */
+    double num = -a + 2.0 * b - d;
+    double den0 = -a + 5.0 * b + 2.0 * d;
+    double mag = fabs(a) + 5.0 * fabs(b) + 2.0 * fabs(d);
+    if (p->eta_guard > 0.0 && fabs(den0) <= p->eta_guard * mag) return 0.0;
+    double eta = ((p->rbf == ORC_RBF_GA) ? 1.0 : 2.0) * num / (den0 + p->eps_M);
+    if (p->eta_max > 0.0 && fabs(eta) > p->eta_max) eta = 0.0;
+    return eta;
+}
+
+/* Value of cell i at its right face (side 0: v^-_{i+1/2}, rows r) or left face (side 1:   */
+/* v^+_{i-1/2}, rows r - 1), k = 2.  c[0..2] = cells i-1, i, i+1; stencil r uses cells     */
+/* i-r, i-r+1.                                                                             */
+static double cell_face_value_k2(const double c[3], int side, double eta, const orc_params* p, int forced_r,
+                                 int* r_out, int* near_out) {
+    const double(*q)[2] = (p->rbf == ORC_RBF_GA) ? PERT2_GA : PERT2_MQ;
+    double cand[2];
+    for (int r = 0; r < 2; ++r) {
+        int row = (side == 0) ? r : r - 1;
+        double s = 0.0;
+        for (int j = 0; j < 2; ++j) s += (POLY2[row + 1][j] + q[row + 1][j] * eta) * c[1 - r + j];
+        cand[r] = s;
+    }
+    *near_out = 0;
+    *r_out = 0;
+    double dl = fabs(c[1] - c[0]), dr = fabs(c[2] - c[1]);
+    if (p->scheme == ORC_ENO || p->scheme == ORC_RBF_ENO) {
+        /* ENO, Sec. 2: add the left interface point only when its divided difference is
+         * strictly smaller */
+        if (fabs(dl - dr) <= p->tie_tol * fmax(dl, dr)) *near_out = 1;
+        int r = (dl < dr) ? 1 : 0;
+        if (forced_r >= 0) r = forced_r;
+        *r_out = r;
+        return cand[r];
+    }
+    /* WENO3 (Jiang-Shu): beta_0 = (c2 - c1)^2, beta_1 = (c1 - c0)^2 */
+    double beta[2] = {(c[2] - c[1]) * (c[2] - c[1]), (c[1] - c[0]) * (c[1] - c[0])};
+    const double* dw = (side == 0) ? D2_MINUS : D2_PLUS;
+    double alpha[2], asum = 0.0;
+    for (int r = 0; r < 2; ++r) {
+        double den = p->eps_weno + beta[r];
+        alpha[r] = dw[r] / (den * den);
+        asum += alpha[r];
+    }
+    double v = 0.0;
+    for (int r = 0; r < 2; ++r) v += (alpha[r] / asum) * cand[r];
+    return v;
+}
+
+/* One face, one field, k = 2.  w[0..5] = cells i-2..i+3 around face i+1/2: v^- comes from
+ * cell i (stencil w[1..3]) with that cell's side-0 eta, v^+ from cell i+1 (stencil w[2..4])
+ * with its side-1 eta.  eta_out receives the eta of v^-. */
+static void face_field_k2(const double w[6], const orc_params* p, const uint8_t* replay, double* vm, double* vp,
+                          uint8_t* flag, double* eta_out) {
+    uint8_t fl = 0;
+    double eta_l = 0.0, eta_r = 0.0;
+    if (p->scheme == ORC_RBF_ENO || p->scheme == ORC_RBF_WENO) {
+        int near_l = 0, near_r = 0, fires_l = 0, fires_r = 0;
+        if (p->monotone_switch) {
+            fires_l = orc_switch_k2(&w[1], p->tie_tol, &near_l);
+            fires_r = orc_switch_k2(&w[2], p->tie_tol, &near_r);
+            if (replay) {
+                fires_l = (*replay & ORC_FLAG_SWITCH) ? 1 : 0;
+                fires_r = (*replay & ORC_FLAG_SWITCH_R_K2) ? 1 : 0;
+            }
+        }
+        if (fires_l) fl |= ORC_FLAG_SWITCH;
+        else eta_l = orc_eta_k2(&w[1], 0, p);
+        if (fires_r) fl |= ORC_FLAG_SWITCH_R_K2;
+        else eta_r = orc_eta_k2(&w[2], 1, p);
+        if (near_l || near_r) fl |= ORC_FLAG_SWITCH_TIE;
+    }
+    int rl = 0, rr = 0, nl = 0, nr = 0, fl_r = -1, fr_r = -1;
+    if (replay && (p->scheme == ORC_ENO || p->scheme == ORC_RBF_ENO)) {
+        fl_r = (*replay >> 2) & 1;
+        fr_r = (*replay >> 4) & 1;
+    }
+    *vm = cell_face_value_k2(&w[1], 0, eta_l, p, fl_r, &rl, &nl);
+    *vp = cell_face_value_k2(&w[2], 1, eta_r, p, fr_r, &rr, &nr);
+    fl |= (uint8_t)((rl & 1) << 2) | (uint8_t)((rr & 1) << 4);
+    if (nl) fl |= ORC_FLAG_ENO_TIE_L;
+    if (nr) fl |= ORC_FLAG_ENO_TIE_R;
+    *flag = fl;
+    if (eta_out) *eta_out = eta_l;
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -432,6 +584,7 @@ static int recon_line(const double* u, long n, int m, long stride, long m_stride
 static int check_params(long n, int m, const orc_params* p) {
     if (!p || n < 6 || m < 1 || m > 4) return ORC_EINVAL;
     if (p->scheme < 0 || p->scheme > 3 || p->rbf < 0 || p->rbf > 1) return ORC_EINVAL;
+    if (p->k != 0 && p->k != 2 && p->k != 3) return ORC_EINVAL;
     if (p->characteristic && m != 3) return ORC_EINVAL;
     return ORC_OK;
 }

@@ -21,6 +21,10 @@ enum { ORC_FLUX_ADVECTION = 0, ORC_FLUX_BURGERS = 1, ORC_FLUX_EULER1D = 2, ORC_F
 /* bits 2-3: ENO stencil r of the left cell (for v^-); bits 4-5: of the right cell (v^+) */
 #define ORC_FLAG_ENO_TIE_L 0x40
 #define ORC_FLAG_ENO_TIE_R 0x80
+/* k = 2: the switch belongs to a cell (its 3-cell stencil), so a face has two: bit 0 is the
+ * switch of the left cell (v^-), bit 3 that of the right cell (v^+); bit 2 / bit 4 hold the
+ * ENO stencil r (0 or 1) of the left / right cell; bit 1 marks a near tie of either switch. */
+#define ORC_FLAG_SWITCH_R_K2 0x08
 
 typedef struct {
     int scheme;          /* ORC_ENO .. ORC_RBF_WENO */
@@ -28,7 +32,7 @@ typedef struct {
     int monotone_switch; /* 0/1 */
     int switch_variant;  /* 0: cubic on the 4-cell eta stencil; 1: k=2 ratio test on both 3-cell halves */
     int characteristic;  /* 1D Euler: reconstruct characteristic fields */
-    int pad_;
+    int k;               /* order parameter of the ENO stencils: 2 or 3 (0 means 3) */
     double eps_M;     /* additive guard of the eta denominator */
     double eps_weno;  /* WENO epsilon (1e-6) */
     double gamma;     /* ratio of specific heats */
@@ -50,6 +54,9 @@ typedef struct {
 
 double orc_table_coef(int rbf, int r, int j, double eta);
 int orc_switch_k3(const double w[4], int variant, double tol, int* near_tie);
+int orc_switch_k2(const double c[3], double tol, int* near_tie);
+double orc_eta_k2(const double c[3], int side, const orc_params* p);
+double orc_table_coef_k2(int rbf, int r, int j, double eta);
 int orc_eno_choice(const double c[5], double tol, int* near_tie);
 void orc_beta_k3(const double c[5], double beta[3]);
 int orc_euler_eigvec(const double UL[3], const double UR[3], double gamma, double R[3][3], double L[3][3]);

@@ -276,3 +276,160 @@ def reconstruct_periodic(vals, scheme, rbf="mq", monotone_switch=False, eps_M=F(
         vm.append(value(f - 1, 0, eta))
         vp.append(value(f, 1, eta))
     return vm, vp
+
+
+# ---------------------------------------------------------------------------------------
+# k = 2 (two-cell stencils), from the same definitions
+# ---------------------------------------------------------------------------------------
+
+
+def poly_row_k2(r, side):
+    """Coefficients of the 2-cell candidate of cell 0 with r cells to its left (r = 0, 1), at
+    its right face (side 0, x = 1) or left face (side 1, x = 0)."""
+    out = []
+    for j in range(2):
+        v = {c: F(0) for c in range(-r, -r + 2)}
+        v[-r + j] = F(1)
+        out.append(peval(cell_poly(v, -r, 2), F(1) if side == 0 else F(0)))
+    return out
+
+
+def linear_weights_k2(side):
+    """d_r (r = 0, 1) with d_0 * candidate_0 + d_1 * candidate_1 == 3-cell candidate."""
+    rows = [poly_row_k2(r, side) for r in range(2)]
+    three = []
+    for j in range(3):
+        v = {c: F(0) for c in range(-1, 2)}
+        v[-1 + j] = F(1)
+        three.append(peval(cell_poly(v, -1, 3), F(1) if side == 0 else F(0)))
+    # cell 1 appears only in r = 0 (its j = 1), cell -1 only in r = 1 (its j = 0)
+    d0 = three[2] / rows[0][1]
+    d1 = three[0] / rows[1][0]
+    assert d0 * rows[0][0] + d1 * rows[1][1] == three[1]
+    return [d0, d1]
+
+
+def beta_k2(v, i, r):
+    """Indicator of the linear p on cells i-r, i-r+1 over cell i (dx = 1): int (p')^2."""
+    d1 = pder(cell_poly(v, i - r, 2))
+    return pint(pmul(d1, d1), i, i + 1)
+
+
+def eno_r_k2(v, i):
+    """One Newton divided-difference step from the interfaces of cell i."""
+    def V(x):
+        return sum((F(v[c]) for c in range(i - 2, x)), F(0))
+    left = [i - 1, i, i + 1]
+    right = [i, i + 1, i + 2]
+    dl = abs(divided_difference([F(x) for x in left], [V(x) for x in left]))
+    dr = abs(divided_difference([F(x) for x in right], [V(x) for x in right]))
+    return 1 if dl < dr else 0
+
+
+def switch_fires_k2(c3):
+    """p = V' of the cubic primitive interpolant on cells [0,1], [1,2], [2,3] (averages c3):
+    True when the vertex of the quadratic p lies strictly inside (0, 3)."""
+    v = {c: F(c3[c]) for c in range(3)}
+    p = cell_poly(v, 0, 3) + [F(0)] * 3
+    b, a = p[1], p[2]
+    if a == 0:
+        return False
+    xp = -b / (2 * a)
+    return 0 < xp < 3
+
+
+def eta_k2_from_derivation(c3, side, kind):
+    """eps^2 dx^2 that cancels the dx^2 error term (Sec. 3.2 / 3.3): with v and v'' at the face
+    taken from the cubic interpolant of the primitive through the four interfaces of cells
+    i-1, i, i+1, the MQ condition is eta/2 v + v''/6 = 0 and the Gaussian one eta v + v''/6 = 0.
+    side 0: face x_{i+1/2}; side 1: x_{i-1/2}.  Cells at [0,1], [1,2], [2,3]."""
+    v = {c: F(c3[c]) for c in range(3)}
+    p = cell_poly(v, 0, 3)
+    x = F(2) if side == 0 else F(1)
+    val = peval(p, x)
+    dd = peval(pder(pder(p)), x)
+    return -dd / (3 * val) if kind == "mq" else -dd / (6 * val)
+
+
+_Q2_CACHE = {}
+
+
+def rbf_rows_k2(kind):
+    """k = 2 perturbation rows q[r] (r = -1, 0, 1) from the flat limit of the pure RBF
+    interpolant of the primitive through the 3 interfaces of the 2-cell stencil."""
+    if kind in _Q2_CACHE:
+        return _Q2_CACHE[kind]
+    import mpmath as mp
+    mp.mp.dps = 260
+
+    def coeffs(r, eta):
+        xs = [mp.mpf(-r - 1 + j) for j in range(3)]
+
+        def phi(dd):
+            return mp.sqrt(1 + eta * dd * dd) if kind == "mq" else mp.exp(-eta * dd * dd)
+
+        def dphi(dd):
+            return eta * dd / mp.sqrt(1 + eta * dd * dd) if kind == "mq" else -2 * eta * dd * mp.exp(-eta * dd * dd)
+
+        out = []
+        for c in range(2):
+            def V(x):
+                a, b = -r - 1 + c, -r + c
+                lo, hi = (0, x) if x >= 0 else (x, 0)
+                ov = max(0, min(b, hi) - max(a, lo))
+                return ov * (1 if x >= 0 else -1)
+            A = mp.matrix(3, 3)
+            for a in range(3):
+                for b in range(3):
+                    A[a, b] = phi(xs[a] - xs[b])
+            lam = mp.lu_solve(A, mp.matrix([V(x) for x in xs]))
+            out.append(sum(lam[j] * dphi(0 - xs[j]) for j in range(3)))
+        return out
+
+    h = mp.mpf("1e-40")
+    rows = {}
+    for r in (-1, 0, 1):
+        c1, c2 = coeffs(r, h), coeffs(r, 2 * h)
+        rows[r] = [F(str(mp.nstr((b - a) / h, 30))).limit_denominator(1000) for a, b in zip(c1, c2)]
+    _Q2_CACHE[kind] = rows
+    return rows
+
+
+def reconstruct_periodic_k2(vals, scheme, rbf="mq", monotone_switch=False, eps_weno=F(1, 10 ** 6)):
+    """(vm, vp) at faces f = 0..n for the k = 2 schemes.  The shape parameter of a cell comes
+    from the derivation above (no eps_M), zero where the switch fires."""
+    n = len(vals)
+    v = {c: F(vals[c % n]) for c in range(-6, n + 6)}
+    q = rbf_rows_k2(rbf) if scheme.startswith("rbf") else None
+    dm, dp_ = linear_weights_k2(0), linear_weights_k2(1)
+
+    def cell_eta(i, side):
+        if q is None:
+            return F(0)
+        c3 = [v[i - 1], v[i], v[i + 1]]
+        if monotone_switch and switch_fires_k2(c3):
+            return F(0)
+        return eta_k2_from_derivation(c3, side, rbf)
+
+    def cand(i, r, side, eta):
+        row = poly_row_k2(r, side)
+        s = F(0)
+        for j in range(2):
+            coef = row[j]
+            if q is not None:
+                coef += q[r - side][j] * eta
+            s += coef * v[i - r + j]
+        return s
+
+    def value(i, side):
+        eta = cell_eta(i, side)
+        if scheme in ("eno", "rbf_eno"):
+            return cand(i, eno_r_k2(v, i), side, eta)
+        d = dm if side == 0 else dp_
+        al = [d[r] / (eps_weno + beta_k2(v, i, r)) ** 2 for r in range(2)]
+        tot = sum(al)
+        return sum(al[r] / tot * cand(i, r, side, eta) for r in range(2))
+
+    vm = [value(f - 1, 0) for f in range(n + 1)]
+    vp = [value(f, 1) for f in range(n + 1)]
+    return vm, vp

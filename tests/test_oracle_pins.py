@@ -229,3 +229,139 @@ def test_eta_bound_on_monotone_zero_slope_stencil():
     _, _, _, e1 = O.reconstruct(u, O.PERIODIC, O.Params())
     _, _, _, e0 = O.reconstruct(u, O.PERIODIC, O.Params(eta_max=0.0))
     np.testing.assert_array_equal(e1, e0)
+
+
+# --------------------------------------------------------------------------------------- k = 2
+# Table k2 and its shape parameter (Sec. 3.2-3.5), the k = 2 switch as printed (Sec. 4), ENO2
+# and WENO3.  Same pins as for k = 3: rows from the definition, flat limit, eta from its
+# derivation, Taylor order, exactness, and the whole-grid brute force.
+@pytest.mark.parametrize("rbf", [O.MQ, O.GA])
+def test_k2_poly_rows_are_primitive_interpolation(rbf):
+    # row r (face i+1/2 from cells i-r, i-r+1): r = 0, 1 are cell i's right-face candidates,
+    # r = -1 is cell i+1's left-face candidate with its own stencil r = 0
+    expect = {0: B.poly_row_k2(0, 0), 1: B.poly_row_k2(1, 0), -1: B.poly_row_k2(0, 1)}
+    for r, row in expect.items():
+        for j in range(2):
+            assert O.table_coef_k2(rbf, r, j, 0.0) == float(row[j]), (r, j)
+
+
+def test_k2_linear_weights_are_the_three_cell_candidate():
+    assert B.linear_weights_k2(0) == [F(2, 3), F(1, 3)]
+    assert B.linear_weights_k2(1) == [F(1, 3), F(2, 3)]
+
+
+@pytest.mark.parametrize("kind,rbf", [("mq", O.MQ), ("ga", O.GA)])
+def test_k2_perturbation_rows_are_rbf_flat_limit(kind, rbf):
+    """MQ: Table k2 (right) as printed; Gaussian: eq. i+1/2_approx1 for r = 0 and the flat
+    limit for r = -1, 1."""
+    pytest.importorskip("mpmath")
+    rows = B.rbf_rows_k2(kind)
+    for r in (-1, 0, 1):
+        for j in range(2):
+            q = O.table_coef_k2(rbf, r, j, 1.0) - O.table_coef_k2(rbf, r, j, 0.0)
+            assert q == pytest.approx(float(rows[r][j]), abs=1e-12), (kind, r, j)
+
+
+@pytest.mark.parametrize("rbf,kind", [(O.MQ, "mq"), (O.GA, "ga")])
+def test_k2_eta_is_the_error_cancelling_shape_parameter(rbf, kind):
+    """eta of eq. i+1/2_eps_approx / i+1/2_eps_approx1 equals -v''/(3v) (MQ) or -v''/(6v)
+    (Gaussian) with v, v'' at the face from the cubic interpolant of the primitive (the paper's
+    derivation, done here in exact rationals), for both faces of the cell."""
+    g = np.random.default_rng(21)
+    p = O.Params(k=2, rbf=rbf, eps_M=0.0, eta_max=0.0)
+    checked = 0
+    for _ in range(200):
+        c3 = [F(int(x), 8) for x in g.integers(-40, 41, size=3)]
+        for side in (0, 1):
+            try:
+                ex = B.eta_k2_from_derivation(c3, side, kind)
+            except ZeroDivisionError:
+                continue
+            got = O.eta_k2([float(x) for x in c3], side, p)
+            assert got == pytest.approx(float(ex), rel=1e-13, abs=1e-13), (c3, side)
+            checked += 1
+    assert checked > 300
+
+
+def test_k2_switch_is_the_vertex_test():
+    """eq. root_value / eq. adaptation: fires exactly when the vertex of p lies strictly inside
+    the stencil (exact rational location), and never on linear data."""
+    g = np.random.default_rng(22)
+    checked = 0
+    for _ in range(400):
+        c3 = [F(int(x), 4) for x in g.integers(-20, 21, size=3)]
+        fires, near = O.switch_k2([float(x) for x in c3], tol=1e-12)
+        if near:
+            continue
+        assert fires == B.switch_fires_k2(c3), c3
+        checked += 1
+    assert checked > 300
+    assert not O.switch_k2([1.0, 2.0, 3.0])[0]
+    assert O.switch_k2([0.0, 1.0, 0.0])[0]
+
+
+@pytest.mark.parametrize("rbf", [O.MQ, O.GA])
+@pytest.mark.parametrize("r", [0, 1])
+def test_k2_perturbed_rows_are_third_order(rbf, r):
+    """RBF-ENO2 with the stencil forced to r: v^- and v^+ converge at order 3 with the table's
+    eta (one above ENO2, Sec. 3.2); ENO2 at order 2."""
+    def errs(scheme):
+        out_m, out_p = [], []
+        for n in (80, 160, 320):
+            edges = np.linspace(0.0, 2.0, n + 1)
+            avg = _smooth_avgs(edges)
+            replay = np.full(n + 1, (r << 2) | (r << 4), dtype=np.uint8)
+            vm, vp, _, _ = O.reconstruct(avg, O.TRANSMISSIVE,
+                                         O.Params(k=2, scheme=scheme, rbf=rbf, monotone_switch=0), replay=replay)
+            ex = np.sin(edges + 0.3) + 2.0
+            inner = slice(4, n - 3)
+            out_m.append(np.abs(vm[inner] - ex[inner]).max())
+            out_p.append(np.abs(vp[inner] - ex[inner]).max())
+        return np.array(out_m), np.array(out_p)
+
+    for e in errs(O.RBF_ENO):
+        orders = np.log2(e[:-1] / e[1:])
+        assert np.all(orders > 2.8), orders
+    for e in errs(O.ENO):
+        orders = np.log2(e[:-1] / e[1:])
+        assert np.all(np.abs(orders - 2.0) < 0.2), orders
+
+
+@pytest.mark.parametrize("scheme", [O.ENO, O.WENO_JS, O.RBF_ENO, O.RBF_WENO])
+@pytest.mark.parametrize("rbf", [O.MQ, O.GA])
+def test_k2_linear_data_reconstructed_exactly(scheme, rbf):
+    n = 24
+    edges = np.linspace(-1.0, 2.0, n + 1)
+    avg = 0.5 * (edges[:-1] + edges[1:]) * 3.0 - 1.0  # averages of 3x - 1
+    vm, vp, fl, eta = O.reconstruct(avg, O.TRANSMISSIVE, O.Params(k=2, scheme=scheme, rbf=rbf))
+    ex = 3.0 * edges - 1.0
+    inner = slice(3, n - 2)
+    np.testing.assert_allclose(vm[inner], ex[inner], atol=1e-12)
+    np.testing.assert_allclose(vp[inner], ex[inner], atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", ["eno", "weno_js", "rbf_eno", "rbf_weno"])
+@pytest.mark.parametrize("rbf", ["mq", "ga"])
+@pytest.mark.parametrize("switch", [False, True])
+def test_k2_bruteforce_tiny_grid(scheme, rbf, switch):
+    pytest.importorskip("mpmath")
+    g = np.random.default_rng([2, len(scheme), ord(scheme[0]), ord(rbf[0]), int(switch)])
+    checked = 0
+    for trial in range(6):
+        n = 8
+        vals = [F(int(x), 16) for x in g.integers(-32, 33, size=n)]
+        try:
+            vmx, vpx = B.reconstruct_periodic_k2(vals, scheme, rbf=rbf, monotone_switch=switch)
+        except ZeroDivisionError:
+            continue
+        p = O.Params(k=2, scheme=O.SCHEMES[scheme], rbf=O.MQ if rbf == "mq" else O.GA,
+                     monotone_switch=int(switch), tie_tol=1e-9, eps_M=0.0, eta_max=0.0)
+        vm, vp, fl, eta = O.reconstruct(np.array([float(x) for x in vals]), O.PERIODIC, p)
+        ties = (fl & (O.FLAG_SWITCH_TIE | O.FLAG_ENO_TIE_L | O.FLAG_ENO_TIE_R)) != 0
+        for f in range(n + 1):
+            if ties[f]:
+                continue
+            assert vm[f] == pytest.approx(float(vmx[f]), rel=1e-11, abs=1e-11), (trial, f)
+            assert vp[f] == pytest.approx(float(vpx[f]), rel=1e-11, abs=1e-11), (trial, f)
+            checked += 1
+    assert checked > 20

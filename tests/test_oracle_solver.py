@@ -68,6 +68,41 @@ def test_design_order_odd_grids(method, order):
         assert errs[-1] < 0.5 * _golden_err_weno_js(ns[-1])
 
 
+@pytest.mark.parametrize("method", list(METHODS))
+def test_advection_matches_paper_table_k2(method):
+    """Sec. 5.2 Example 1, table0 (k = 2, T = 0.5, dt = 0.1 dx, switch off): ENO2, RBF-ENO2
+    and RBF-WENO3 L1 and Linf errors within 25% of the printed values at N = 20..320.  WENO-JS
+    (k = 2) follows the printed row (within 3x) up to N = 40 only: the standard WENO3-JS weights (eps = 1e-6)
+    lose an order at the extrema of sin(pi x), which the printed row does not show (a reading
+    of the unstated WENO3 details)."""
+    gold = _golden("table_advection_k2.txt")[method]
+    ns = (20, 40) if method == "WENO-JS" else (20, 40, 80, 160, 320)
+    tol = 3.0 if method == "WENO-JS" else 1.25
+    for n in ns:
+        u, dx = I.advection_sin(n)
+        uT, st = O.solve(u, dx, 0.5, 0.1, O.ADVECTION, O.PERIODIC,
+                         O.Params(k=2, scheme=METHODS[method], monotone_switch=0))
+        ex, _ = I.advection_sin(n, shift=0.5)
+        l1, linf = np.mean(np.abs(uT - ex)), np.abs(uT - ex).max()
+        assert gold[n][0] / tol < l1 < gold[n][0] * tol, (method, n, l1, gold[n][0])
+        assert gold[n][1] / tol < linf < gold[n][1] * tol, (method, n, linf, gold[n][1])
+
+
+@pytest.mark.parametrize("method,order", [("ENO", 2.0), ("RBF-ENO", 3.0), ("RBF-WENO", 3.0)])
+def test_design_order_odd_grids_k2(method, order):
+    """k = 2 design orders on odd N: ENO2 2, RBF-ENO2 3 (one above ENO2, Sec. 3.2), RBF-WENO3 3."""
+    errs = []
+    ns = (41, 81, 161, 321)
+    for n in ns:
+        u, dx = I.advection_sin(n)
+        uT, _ = O.solve(u, dx, 0.5, 0.1, O.ADVECTION, O.PERIODIC,
+                        O.Params(k=2, scheme=METHODS[method], monotone_switch=0))
+        ex, _ = I.advection_sin(n, shift=0.5)
+        errs.append(np.mean(np.abs(uT - ex)))
+    orders = [np.log(errs[i] / errs[i + 1]) / np.log(ns[i + 1] / ns[i]) for i in range(3)]
+    assert abs(orders[-1] - order) < 0.2, orders
+
+
 def _golden_err_weno_js(n):
     u, dx = I.advection_sin(n)
     uT, _ = O.solve(u, dx, 0.5, _small_dt_cfl(dx), O.ADVECTION, O.PERIODIC, O.Params(scheme=O.WENO_JS))
