@@ -62,7 +62,10 @@ typedef enum { NPW_RBF_MQ = 0, NPW_RBF_GA = 1 } npw_rbf;
 typedef enum { NPW_FP64 = 0, NPW_FP32_MIXED = 1 } npw_precision;
 
 typedef struct {
-    int32_t k;               /* reconstruction order parameter; only 3 is supported */
+    int32_t k;               /* 3: ENO3 / WENO5 (Table k3); 2: ENO2 / WENO3 (Table k2, Sec. 3.2-3.5: one
+                                shape parameter per face value, from the cell's 3-cell stencil,
+                                and the switch of eq. root_value per cell; switch_variant unused).
+                                k = 2 runs the face-based stage kernels in both precisions */
     int32_t scheme;          /* npw_scheme */
     int32_t rbf;             /* npw_rbf: perturbation rows of Table k3 (MQ) or Sec. 3.3 (GA) */
     int32_t monotone_switch; /* 1: eta = 0 where the stencil polynomial is non-monotone */
@@ -123,12 +126,14 @@ const char* npw_last_error(void);
 int32_t npw_version(void);
 
 /*
- * Reconstruction only (paper Sec. 2 and 3.5, eq. weno_re, Table k3, Sec. 4 eq. adaptation):
- * for each of the n+1 faces, the left/right states v^-, v^+ of every field.
+ * Reconstruction only (paper Sec. 2 and 3.5, eq. weno_re, Table k3 / Table k2, Sec. 4 eq.
+ * adaptation): for each of the n+1 faces, the left/right states v^-, v^+ of every field.
  *   vbar    [m][n] cell averages (device)
  *   v_minus [m][n+1] out: v^-_f from cell f-1;  v_plus [m][n+1] out: v^+_f from cell f
- *   flags   [m][n+1] out, may be NULL: bit0 = monotone switch fired (eta set to 0),
+ *   flags   [m][n+1] out, may be NULL.  k = 3: bit0 = monotone switch fired (eta set to 0),
  *           bits 2-3 = ENO stencil r of cell f-1, bits 4-5 = ENO stencil r of cell f.
+ *           k = 2: bit0 / bit3 = switch fired for cell f-1 / cell f, bit2 / bit4 = ENO
+ *           stencil r (0 or 1) of cell f-1 / cell f.
  * m = 1, or m = 3 with params->characteristic for the 1D Euler characteristic fields.
  * Returns NPW_EINVAL for n < 6, m outside 1..4, characteristic with m != 3, null pointers.
  */

@@ -51,7 +51,7 @@ size_t elem_size(const npw_params* p) { return p->precision == NPW_FP32_MIXED ? 
 
 npw_status check_params(const npw_params* p) {
     if (!p) return fail(NPW_EINVAL, "params is NULL");
-    if (p->k != 3) return fail(NPW_EINVAL, "only k = 3 (ENO3 / WENO5) is supported, got k = %d", p->k);
+    if (p->k != 2 && p->k != 3) return fail(NPW_EINVAL, "k must be 2 (ENO2 / WENO3) or 3 (ENO3 / WENO5), got %d", p->k);
     if (p->scheme < NPW_ENO || p->scheme > NPW_RBF_WENO) return fail(NPW_EINVAL, "bad scheme %d", p->scheme);
     if (p->rbf != NPW_RBF_MQ && p->rbf != NPW_RBF_GA) return fail(NPW_EINVAL, "bad rbf %d", p->rbf);
     if (p->switch_variant < 0 || p->switch_variant > 1) return fail(NPW_EINVAL, "bad switch_variant");
@@ -71,6 +71,7 @@ npw::MethodParams method(const npw_params* p) {
     mp.switch_variant = p->switch_variant;
     mp.characteristic = p->characteristic ? 1 : 0;
     mp.eta_eval = p->eta_eval;
+    mp.k = p->k;
     mp.eps_M = p->eps_M;
     mp.eps_weno = p->eps_weno;
     mp.gamma = p->gamma;
@@ -435,10 +436,15 @@ struct Run1D {
     std::vector<cudaEvent_t> joins;  // side-stream work the caller's stream waits for at the end
 };
 
-// instances the resident kernel can take: float state, component-wise, fits in shared memory
+// the compensated float kernels (stage1d_fast_kernel, the resident kernel) cover float,
+// component-wise, k = 3; every other case runs the face-based stage kernel
+bool compensated(const npw_params* p) {
+    return p->precision == NPW_FP32_MIXED && !p->characteristic && p->k == 3;
+}
+
+// instances the resident kernel can take: compensated float path, fits in shared memory
 bool resident_ok(const npw_params* p, int m, int64_t n) {
-    return p->precision == NPW_FP32_MIXED && !p->characteristic && p->batch_mode == 0 &&
-           npw::resident_smem_bytes(n, m) <= npw::RESIDENT_SMEM_MAX;
+    return compensated(p) && p->batch_mode == 0 && npw::resident_smem_bytes(n, m) <= npw::RESIDENT_SMEM_MAX;
 }
 
 int64_t tiles_for(const Run1D& r, const npw_instance* inst, int count) {
@@ -815,7 +821,7 @@ static npw_status single_run(void* u, int64_t n, int32_t m, double dx, double t_
     r.ntiles = tiles_of(n);
     r.L = layout_1d(n * m, 1, r.ntiles, elem_size(params));
     r.s = s;
-    r.comp = r.fp32 && !params->characteristic;
+    r.comp = compensated(params);
     if (workspace_bytes < r.L.total)
         return fail(NPW_EINVAL, "workspace too small: %zu < %zu bytes", workspace_bytes, r.L.total);
     in.offset = 0;
@@ -903,7 +909,7 @@ npw_status npweno_batch_solve(void* arena, const npw_instance* inst, int32_t cou
     r.s = reinterpret_cast<cudaStream_t>(stream);
     if (workspace_bytes < r.L.total)
         return fail(NPW_EINVAL, "workspace too small: %zu < %zu bytes", workspace_bytes, r.L.total);
-    r.comp = r.fp32 && !params->characteristic;
+    r.comp = compensated(params);
     r.resident.assign(count, 0);
     bool any_res = false;
     for (int i = 0; i < count; ++i) {
@@ -1107,6 +1113,7 @@ struct npw_server {
     npw_params params;
     npw::MethodParams mp;
     bool fp32 = false;
+    bool comp = false;  // compensated float kernels (state ends in the s region)
     size_t esz = 8;
     int max_slots = 0;
     cudaStream_t s = nullptr;
@@ -1234,6 +1241,7 @@ npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max
     sv->params = *params;
     sv->mp = method(params);
     sv->fp32 = params->precision == NPW_FP32_MIXED;
+    sv->comp = compensated(params);
     sv->esz = esz;
     sv->max_slots = max_slots;
     sv->s = reinterpret_cast<cudaStream_t>(stream);
@@ -1363,7 +1371,7 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
         npw::ctl_slots_kernel<<<blocks, 128, 0, sv->s>>>(ctl, dinst, dlist, (int)fresh.size(), 1);
         NPW_CUDA(cudaGetLastError());
         count_launch(2);
-        if (sv->fp32) {  // compensated float kernels: s = u, c = 0 for the admitted requests
+        if (sv->comp) {  // compensated float kernels: s = u, c = 0 for the admitted requests
             for (size_t b2 = 0; b2 < newtiles.size();) {
                 const int kind = sv->slots[newtiles[b2].inst].req.flux_kind;
                 size_t e2 = b2;
@@ -1406,7 +1414,7 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
     sv->remaining_hint = rem;
     for (int k : finished) {  // the compensated float kernels leave the final state in s
         const npw_server::Slot& sl = sv->slots[k];
-        const size_t region = sv->fp32 ? sv->L.heap_s : sv->L.heap_u;
+        const size_t region = sv->comp ? sv->L.heap_s : sv->L.heap_u;
         NPW_CUDA(cudaMemcpyAsync(sl.req.out_host, sv->arena + region + (size_t)sl.off * sv->esz,
                                  (size_t)(sl.req.n * sl.m) * sv->esz, cudaMemcpyDeviceToHost, sv->s));
     }

@@ -10,7 +10,10 @@
 // weno_re with alpha_r = d_r / (eps + beta_r)^2), Sec. 3.5 Table k3 (coefficients and eta;
 // row r = -1 uses 11/6), Sec. 3.3 (Gaussian recipe; k = 3 rows derived from the flat limit of
 // the Gaussian interpolant of the primitive), Sec. 4 (eq. root_value, eq. adaptation),
-// Sec. 5.1 (Lax-Friedrichs flux), Sec. 5.2 Ex. 4 (Euler, ideal gas).
+// Sec. 5.1 (Lax-Friedrichs flux), Sec. 5.2 Ex. 4 (Euler, ideal gas).  k = 2: Sec. 3.2-3.5
+// Table k2 with the shape parameter of eq. i+1/2_eps_approx (MQ) / i+1/2_eps_approx1
+// (Gaussian), the Gaussian rows r = -1, 1 from the flat limit, and the switch of eq.
+// root_value / eq. adaptation on the cell's three-cell stencil.
 #pragma once
 #include <cstdint>
 
@@ -211,10 +214,134 @@ __device__ __forceinline__ R cell_face_value(const R* c, int side, R eta, const 
     return v;
 }
 
+// ---------------------------------------------------------------------------------------
+// k = 2.  Table k2: row = r + 1 for r = -1, 0, 1; row r gives the value at x_{i+1/2} from the
+// cells i-r, i-r+1.  A cell i has the stencil c[0..2] = cells i-1, i, i+1; its two face
+// values use their own shape parameters (side 0: v^-_{i+1/2}; side 1: v^+_{i-1/2}, the mirror).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T poly2_coef(int row, int j) {
+    switch (row * 2 + j) {
+        case 0: return T(3.0 / 2.0);
+        case 1: return T(-1.0 / 2.0);
+        case 2: return T(1.0 / 2.0);
+        case 3: return T(1.0 / 2.0);
+        case 4: return T(-1.0 / 2.0);
+        default: return T(3.0 / 2.0);
+    }
+}
+
+// coefficient of eta: multiquadric (Table k2, right) or Gaussian (r = 0: eq. i+1/2_approx1;
+// r = -1, 1: flat limit of the Gaussian interpolant)
+template <typename T>
+__device__ __forceinline__ T pert2_coef(int rbf, int row, int j) {
+    if (rbf == NPW_RBF_GA_) {
+        switch (row * 2 + j) {
+            case 0: return T(-2.0);
+            case 1: return T(0.0);
+            case 2: return T(1.0 / 2.0);
+            case 3: return T(1.0 / 2.0);
+            case 4: return T(0.0);
+            default: return T(-2.0);
+        }
+    }
+    switch (row * 2 + j) {
+        case 0: return T(-3.0 / 2.0);
+        case 1: return T(1.0 / 2.0);
+        case 2: return T(1.0 / 4.0);
+        case 3: return T(1.0 / 4.0);
+        case 4: return T(1.0 / 2.0);
+        default: return T(-3.0 / 2.0);
+    }
+}
+
+// WENO3 linear weights: v^-_{i+1/2} d = (2/3, 1/3) for r = 0 (cells i, i+1), r = 1 (i-1, i);
+// v^+_{i-1/2} mirrored
+template <typename T>
+__device__ __forceinline__ T lin_weight2(int side, int r) {
+    if (side == 0) return r == 0 ? T(2.0 / 3.0) : T(1.0 / 3.0);
+    return r == 0 ? T(1.0 / 3.0) : T(2.0 / 3.0);
+}
+
+// shape parameter of a cell, side 0 / 1 (MQ: 2 num / (den + eps_M); Gaussian: half), with the
+// optional guard and bound of the k = 3 path (magnitudes of the denominator's terms)
+template <typename D>
+__device__ __forceinline__ D eta_k2(const D* c, int side, const MethodParams& mp) {
+    const D a = side == 0 ? c[0] : c[2];
+    const D b = c[1];
+    const D d = side == 0 ? c[2] : c[0];
+    const D num = -a + D(2.0) * b - d;
+    const D den0 = -a + D(5.0) * b + D(2.0) * d;
+    const D mag = fabs(a) + D(5.0) * fabs(b) + D(2.0) * fabs(d);
+    if (mp.eta_guard > 0.0 && fabs(den0) <= D(mp.eta_guard) * mag) return D(0.0);
+    const D e = (mp.rbf == NPW_RBF_GA_ ? D(1.0) : D(2.0)) * num / (den0 + D(mp.eps_M));
+    if (mp.eta_max > 0.0 && fabs(e) > D(mp.eta_max)) return D(0.0);
+    return e;
+}
+
+// value of cell i at its right (side 0) or left (side 1) face, k = 2; c[0..2] = cells i-1..i+1
+template <typename R, typename D>
+__device__ __forceinline__ R cell_face_value_k2(const R* c, int side, R eta, const MethodParams& mp, int* r_out) {
+    R cand[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int row = (side == 0) ? r : r - 1;
+        R s = R(0.0);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) s += (poly2_coef<R>(row + 1, j) + pert2_coef<R>(mp.rbf, row + 1, j) * eta) * c[1 - r + j];
+        cand[r] = s;
+    }
+    if (mp.scheme == NPW_ENO_ || mp.scheme == NPW_RBF_ENO_) {
+        const int r = fabs(D(c[1]) - D(c[0])) < fabs(D(c[2]) - D(c[1])) ? 1 : 0;
+        *r_out = r;
+        return cand[r];
+    }
+    *r_out = 0;
+    const D b0 = (D(c[2]) - D(c[1])) * (D(c[2]) - D(c[1]));
+    const D b1 = (D(c[1]) - D(c[0])) * (D(c[1]) - D(c[0]));
+    const R den0 = R(D(mp.eps_weno) + b0), den1 = R(D(mp.eps_weno) + b1);
+    const R a0 = lin_weight2<R>(side, 0) / (den0 * den0);
+    const R a1 = lin_weight2<R>(side, 1) / (den1 * den1);
+    R asum = R(0.0);
+    asum += a0;
+    asum += a1;
+    R v = R(0.0);
+    v += (a0 / asum) * cand[0];
+    v += (a1 / asum) * cand[1];
+    return v;
+}
+
+// One field at one face, k = 2.  w[0..5] = cells i-2..i+3 around face i+1/2; v^- from cell i
+// (stencil w[1..3]), v^+ from cell i+1 (stencil w[2..4]).  Flag bits: 0 switch of cell i,
+// 3 switch of cell i+1, 2 / 4 ENO r of cell i / i+1.
+template <typename R, typename D>
+__device__ __forceinline__ uint32_t face_field_k2(const R* w, const MethodParams& mp, R* vm, R* vp) {
+    uint32_t fl = 0;
+    R el = R(0.0), er = R(0.0);
+    if (mp.scheme == NPW_RBF_ENO_ || mp.scheme == NPW_RBF_WENO_) {
+        const D cl[3] = {D(w[1]), D(w[2]), D(w[3])};
+        const D cr[3] = {D(w[2]), D(w[3]), D(w[4])};
+        if (mp.monotone_switch && k2_ratio_fires<D>(cl[0], cl[1], cl[2]))
+            fl |= 1u;
+        else
+            el = R(eta_k2<D>(cl, 0, mp));
+        if (mp.monotone_switch && k2_ratio_fires<D>(cr[0], cr[1], cr[2]))
+            fl |= 8u;
+        else
+            er = R(eta_k2<D>(cr, 1, mp));
+    }
+    int rl = 0, rr = 0;
+    *vm = cell_face_value_k2<R, D>(w + 1, 0, el, mp, &rl);
+    *vp = cell_face_value_k2<R, D>(w + 2, 1, er, mp, &rr);
+    fl |= (uint32_t(rl & 1) << 2) | (uint32_t(rr & 1) << 4);
+    return fl;
+}
+
 // One field at one face.  w[0..5] = cells i-2..i+3 around face i+1/2.  Returns the flag
 // byte (bit0 switch, bits 2-3 / 4-5 ENO r of the left / right cell).
 template <typename R, typename D>
 __device__ __forceinline__ uint32_t face_field(const R* w, const MethodParams& mp, R* vm, R* vp) {
+    if (mp.k == 2) return face_field_k2<R, D>(w, mp, vm, vp);
     uint32_t fl = 0;
     R eta = R(0.0);
     if (mp.scheme == NPW_RBF_ENO_ || mp.scheme == NPW_RBF_WENO_) {

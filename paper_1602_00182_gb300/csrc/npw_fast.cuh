@@ -26,7 +26,6 @@ namespace fast {
 // float copies of the method parameters, converted once per thread
 struct FParams {
     float eps_weno, eps_M_f, eta_guard, eta_max;
-    float eps_hi, eps_lo;  // eps_M = eps_hi + eps_lo to ~2^-48
     double eps_M;
     int scheme, rbf, monotone_switch, switch_variant, eta_eval;
 };
@@ -36,8 +35,6 @@ __device__ __forceinline__ FParams fparams(const MethodParams& mp) {
     f.eps_M_f = (float)mp.eps_M;
     f.eta_guard = (float)mp.eta_guard;
     f.eta_max = (float)mp.eta_max;
-    f.eps_hi = (float)mp.eps_M;
-    f.eps_lo = (float)(mp.eps_M - (double)f.eps_hi);
     f.eps_M = mp.eps_M;
     f.scheme = mp.scheme;
     f.rbf = mp.rbf;
@@ -200,14 +197,14 @@ __device__ __forceinline__ void eta_pairs(float w0, float w1, float w2, float w3
 }
 
 // FP64 evaluation of the quotient.  Numerator and denominator come from the float pairs of
-// eta_pairs, widened exactly and added in double; eps_M is added to the denominator pair as
-// the pair eps_hi + eps_lo.  The quotient is the Newton-Raphson reciprocal iteration in
-// double: from the float seed r0 = 1 / fl(den) (relative error < 2^-23), one step
-// r1 = r0 + r0 (1 - den r0) leaves |r1 den - 1| < 2^-45, and q = num r1 is within ~2^-45 of
-// the quotient, far below the rounding to float that follows (it can differ from the
-// correctly rounded float only when the quotient lies within 2^-45 of a rounding boundary).
-// FP64-pipe instructions: 2 adds (numerator and denominator to double), 2 multiply-adds (the
-// Newton step), 1 multiply, 1 conversion of the result.
+// eta_pairs, widened exactly and added in double, and eps_M is added in double.  The
+// quotient is the Newton-Raphson reciprocal iteration in double: from the float seed
+// r0 = 1 / fl(den) (relative error < 2^-23), one step r1 = r0 + r0 (1 - den r0) leaves
+// |r1 den - 1| < 2^-45, and q = num r1 is within ~2^-45 of the quotient, far below the
+// rounding to float that follows (it can differ from the correctly rounded float only when
+// the quotient lies within 2^-45 of a rounding boundary).  FP64-pipe instructions: 3 adds
+// (numerator, denominator, eps_M), 2 multiply-adds (the Newton step), 1 multiply and 2
+// conversions (the seed's argument and the result).
 __device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3, const FParams& fp, float guard) {
     float nh, nl, dh, dl;
     eta_pairs(w0, w1, w2, w3, nh, nl, dh, dl);
@@ -215,13 +212,9 @@ __device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3
         // near or below the guard: decide in double
         if (fabs(widen(dh) + widen(dl)) <= (double)guard) return 0.0f;
     }
-    float s, t;
-    two_sum(dh, fp.eps_hi, s, t);
-    dl = dl + (t + fp.eps_lo);
-    dh = s;
     const double num = widen(nh) + widen(nl);
-    const double den = widen(dh) + widen(dl);
-    const float denf = dh + dl;
+    const double den = (widen(dh) + widen(dl)) + fp.eps_M;
+    const float denf = (float)den;
     if (!(fabsf(denf) > 1e-30f && fabsf(denf) < 1e30f)) return (float)(num / den);
     double r = widen(1.0f / denf);
     r = fma(r, fma(-den, r, 1.0), r);
@@ -328,7 +321,76 @@ __device__ __forceinline__ int cell_recon(const float* c, float eta_r, float eta
 // Face form (used where the cells of a face see different data, as in the characteristic
 // variant): w[0..5] = cells i-2..i+3 of face i+1/2.  The neighbouring faces' eta values are
 // not needed: v^- uses this face's eta, v^+ of cell i+1 too.
+// ---------------------------------------------------------------------------------------
+// k = 2 in mixed precision.  The switch (eq. root_value on the cell's stencil) and the ENO2
+// choice are certified from float differences with an FP64 fallback, as for k = 3; the shape
+// parameter of each face value is evaluated in FP64 from the float cell averages (the
+// literal formula of Table k2, identical to the FP64 path on the same data); candidates and
+// WENO3 weights are float.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ bool switch_k2_f(float c0, float c1, float c2) {
+    const int c = k2_cert(c1 - c0, c2 - c1);
+    if (c >= 0) return c == 1;
+    return k2_ratio_fires<double>((double)c0, (double)c1, (double)c2);
+}
+
+__device__ __forceinline__ int eno2_choice_f(float c0, float c1, float c2) {
+    const float al = fabsf(c1 - c0), ar = fabsf(c2 - c1);
+    const int s = csign(ar - al, kE * (al + ar));
+    if (s != kUncertain) return s > 0 ? 1 : 0;
+    return fabs((double)c1 - (double)c0) < fabs((double)c2 - (double)c1) ? 1 : 0;
+}
+
+// value of cell i (c[0..2] = cells i-1..i+1) at its right (side 0) or left (side 1) face
+__device__ __forceinline__ float cell_value_k2_f(const float* c, int side, float eta, const FParams& fp, int* r_out) {
+    float cand[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int row = (side == 0) ? r : r - 1;
+        const float k0 = fmaf(pert2_coef<float>(fp.rbf, row + 1, 0), eta, poly2_coef<float>(row + 1, 0));
+        const float k1 = fmaf(pert2_coef<float>(fp.rbf, row + 1, 1), eta, poly2_coef<float>(row + 1, 1));
+        cand[r] = fmaf(k0, c[1 - r], k1 * c[2 - r]);
+    }
+    if (fp.scheme == NPW_ENO_ || fp.scheme == NPW_RBF_ENO_) {
+        const int r = eno2_choice_f(c[0], c[1], c[2]);
+        *r_out = r;
+        return r == 0 ? cand[0] : cand[1];
+    }
+    *r_out = 0;
+    constexpr float kBeMax = 1e18f;  // keeps the fast division in range (see cell_recon)
+    const float g0 = c[2] - c[1], g1 = c[1] - c[0];
+    const float be0 = fminf(fmaf(g0, g0, fp.eps_weno), kBeMax), be1 = fminf(fmaf(g1, g1, fp.eps_weno), kBeMax);
+    const float a0 = __fdividef(side == 0 ? 2.f / 3.f : 1.f / 3.f, be0 * be0);
+    const float a1 = __fdividef(side == 0 ? 1.f / 3.f : 2.f / 3.f, be1 * be1);
+    return __fdividef(fmaf(a0, cand[0], a1 * cand[1]), a0 + a1);
+}
+
+__device__ __forceinline__ uint32_t face_field_k2(const float* w, const MethodParams& mp0, float* vm, float* vp) {
+    const FParams fp = fparams(mp0);
+    uint32_t fl = 0;
+    float el = 0.0f, er = 0.0f;
+    if (fp.scheme == NPW_RBF_ENO_ || fp.scheme == NPW_RBF_WENO_) {
+        if (fp.monotone_switch && switch_k2_f(w[1], w[2], w[3])) {
+            fl |= 1u;
+        } else {
+            const double c[3] = {widen(w[1]), widen(w[2]), widen(w[3])};
+            el = (float)eta_k2<double>(c, 0, mp0);
+        }
+        if (fp.monotone_switch && switch_k2_f(w[2], w[3], w[4])) {
+            fl |= 8u;
+        } else {
+            const double c[3] = {widen(w[2]), widen(w[3]), widen(w[4])};
+            er = (float)eta_k2<double>(c, 1, mp0);
+        }
+    }
+    int rl = 0, rr = 0;
+    *vm = cell_value_k2_f(w + 1, 0, el, fp, &rl);
+    *vp = cell_value_k2_f(w + 2, 1, er, fp, &rr);
+    return fl | (uint32_t(rl & 1) << 2) | (uint32_t(rr & 1) << 4);
+}
+
 __device__ __forceinline__ uint32_t face_field(const float* w, const MethodParams& mp0, float* vm, float* vp) {
+    if (mp0.k == 2) return face_field_k2(w, mp0, vm, vp);
     uint32_t fl = 0;
     const FParams mp = fparams(mp0);
     const float eta = face_eta(w[1], w[2], w[3], w[4], mp, &fl);

@@ -27,6 +27,7 @@ struct MethodParams {
     int switch_variant;
     int characteristic;
     int eta_eval;  // mixed precision: 0 = FP64 division, 1 = exact double-float quotient
+    int k;         // 2 (ENO2 / WENO3) or 3 (ENO3 / WENO5)
     double eps_M;
     double eps_weno;
     double gamma;

@@ -947,7 +947,7 @@ struct Launchers {
 
     static cudaError_t stage1d(const Stage1DArgs& a, int kind, cudaStream_t s) {
         if constexpr (sizeof(R) == sizeof(float)) {
-            if (!a.mp.characteristic) {
+            if (!a.mp.characteristic && a.mp.k == 3) {
                 switch (kind) {
                     case NPW_FLUX_ADVECTION: return stage_fast<NPW_FLUX_ADVECTION_>(a, s);
                     case NPW_FLUX_BURGERS: return stage_fast<NPW_FLUX_BURGERS_>(a, s);

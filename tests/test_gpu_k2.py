@@ -1,0 +1,217 @@
+"""Parity of the k = 2 schemes (Table k2: ENO2, WENO3, RBF-ENO2, RBF-WENO3; one shape parameter
+per face value and the per-cell switch of eq. root_value) on the GPU with the FP64 oracle.
+
+Bars as for k = 3: NPW_FP64 relative L_inf <= 1e-12 with switch and ENO flags identical away
+from near ties; NPW_FP32_MIXED decisions identical to the oracle's on the same float data and
+values within float arithmetic (one stage 2e-6 relative, full runs L1 <= 1e-4 and
+L_inf <= 2e-2).  Flag bits for k = 2: 0 / 3 switch of the left / right cell of the face,
+2 / 4 their ENO stencil.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1602_00182_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_GUARD = 8.0 * 2.0 ** -24
+TIES = O.FLAG_SWITCH_TIE | O.FLAG_ENO_TIE_L | O.FLAG_ENO_TIE_R
+DECISIONS = 0x01 | 0x04 | 0x08 | 0x10
+
+
+@pytest.fixture(scope="module")
+def npw():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1602_00182_gb300 import build as b
+    b.build()
+    import paper_1602_00182_gb300.npweno as m
+    m.load()
+    return m
+
+
+def _dev(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def _gp(npw, o, precision=0):
+    return npw.Params(k=2, scheme=o.scheme, rbf=o.rbf, monotone_switch=o.monotone_switch,
+                      characteristic=o.characteristic, precision=precision, eps_M=o.eps_M, eps_weno=o.eps_weno,
+                      gamma=o.gamma, adv_speed=o.adv_speed, inflow=o.inflow,
+                      eta_guard=o.eta_guard if o.eta_guard > 0 else 0.0, eta_max=o.eta_max if o.eta_max > 0 else -1.0)
+
+
+def _data(n, seed):
+    g = np.random.default_rng(seed)
+    x = np.linspace(0, 1, n, endpoint=False)
+    u = 1.0 + 0.3 * np.sin(2 * np.pi * 3 * x + g.uniform(0, 6)) + 0.1 * np.cos(2 * np.pi * 7 * x)
+    u[x > 0.6] += 0.5
+    u[(x > 0.2) & (x < 0.3)] = 1.1
+    u[(x > 0.75) & (x < 0.8)] = np.linspace(0, 1, ((x > 0.75) & (x < 0.8)).sum())
+    return u
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("scheme", [O.ENO, O.WENO_JS, O.RBF_ENO, O.RBF_WENO])
+@pytest.mark.parametrize("rbf", [O.MQ, O.GA])
+@pytest.mark.parametrize("switch", [0, 1])
+@pytest.mark.parametrize("bc", [O.PERIODIC, O.TRANSMISSIVE, O.INFLOW])
+def test_k2_reconstruct_fp64(npw, scheme, rbf, switch, bc):
+    op = O.Params(k=2, scheme=scheme, rbf=rbf, monotone_switch=switch, inflow=(0.7, 0, 0, 0))
+    for n in (6, 37, 1025, 3001):
+        u = _data(n, n)
+        vm, vp, fl, _ = O.reconstruct(u, bc, op)
+        gvm, gvp, gfl = npw.npweno_reconstruct(_dev(u), bc, _gp(npw, op))
+        gvm, gvp, gfl = gvm.cpu().numpy(), gvp.cpu().numpy(), gfl.cpu().numpy()
+        ok = (fl & TIES) == 0
+        assert np.array_equal(gfl[ok] & DECISIONS, fl[ok] & DECISIONS), n
+        scale = np.abs(u).max()
+        assert np.abs(gvm[ok] - vm[ok]).max() <= FP64_TOL * scale, n
+        assert np.abs(gvp[ok] - vp[ok]).max() <= FP64_TOL * scale, n
+
+
+@pytest.mark.parametrize("char", [0, 1])
+def test_k2_reconstruct_euler_fp64(npw, char):
+    for inst in I.euler_batch(count=4, nmin=64, nmax=2500):
+        op = O.Params(k=2, characteristic=char)
+        vm, vp, fl, _ = O.reconstruct(inst.u0, O.TRANSMISSIVE, op)
+        gvm, gvp, gfl = npw.npweno_reconstruct(_dev(inst.u0), O.TRANSMISSIVE, _gp(npw, op))
+        ok = (fl & TIES) == 0
+        for a, b in ((gvm.cpu().numpy(), vm), (gvp.cpu().numpy(), vp)):
+            for k in range(3):
+                assert np.abs(a[k][ok[k]] - b[k][ok[k]]).max() <= FP64_TOL * np.abs(b[k]).max()
+
+
+@pytest.mark.parametrize("scheme", [O.ENO, O.WENO_JS, O.RBF_ENO, O.RBF_WENO])
+def test_k2_rk3_step_fp64(npw, scheme):
+    for n in (6, 1023, 1025, 2500):
+        u = _data(n, 3 * n)
+        op = O.Params(k=2, scheme=scheme)
+        ref, a_ref = O.rk3_step(u, 1.0 / n, 0.3 / n, O.BURGERS, O.PERIODIC, op)
+        gu = _dev(u)
+        a = npw.npweno_rk3_step(gu, 1.0 / n, 0.3 / n, O.BURGERS, O.PERIODIC, _gp(npw, op), want_alpha=True)
+        assert a == a_ref
+        assert _rel(gu.cpu().numpy(), ref) <= FP64_TOL, n
+
+
+@pytest.mark.parametrize("n", [25, 50, 100, 200, 400])
+@pytest.mark.parametrize("scheme", [O.RBF_ENO, O.RBF_WENO])
+def test_k2_advection_solve_fp64(npw, n, scheme):
+    """sin(pi x) advected to T = 2 at CFL 0.5 with RBF-ENO2 / RBF-WENO3 (MQ), switch on."""
+    u0, dx = I.advection_sin(n)
+    op = O.Params(k=2, scheme=scheme)
+    ref, rst = O.solve(u0, dx, 2.0, 0.5, O.ADVECTION, O.PERIODIC, op)
+    gu = _dev(u0)
+    st = npw.npweno_solve(gu, dx, 2.0, 0.5, O.ADVECTION, O.PERIODIC, _gp(npw, op))
+    assert st["steps"] == rst["steps"] and st["t"] == 2.0 and st["status"] == 0
+    assert _rel(gu.cpu().numpy(), ref) <= FP64_TOL
+
+
+def test_k2_burgers_through_shock_fp64(npw):
+    u0 = -np.sin(np.pi * np.linspace(-1, 1, 201)[:-1])
+    op = O.Params(k=2, scheme=O.RBF_ENO, rbf=O.GA)
+    ref, rst = O.solve(u0, 0.01, 0.6, 0.5, O.BURGERS, O.PERIODIC, op)
+    gu = _dev(u0)
+    st = npw.npweno_solve(gu, 0.01, 0.6, 0.5, O.BURGERS, O.PERIODIC, _gp(npw, op))
+    assert st["steps"] == rst["steps"]
+    assert _rel(gu.cpu().numpy(), ref) <= 1e-11
+
+
+@pytest.mark.parametrize("scheme", [O.ENO, O.WENO_JS, O.RBF_ENO, O.RBF_WENO])
+def test_k2_mixed_decisions_match_fp64(npw, scheme):
+    """NPW_FP32_MIXED, k = 2: switch and ENO flags equal the oracle's double-precision
+    decisions on the same float data; values within float arithmetic."""
+    for n in (64, 1500, 4097):
+        u = _data(n, n).astype(np.float32).astype(np.float64)
+        u[n // 2: n // 2 + 40] = np.round(u[n // 2: n // 2 + 40] * 64) / 64  # plateaus and exact steps
+        op = O.Params(k=2, scheme=scheme, eta_guard=MIXED_GUARD)
+        vm, vp, fl, _ = O.reconstruct(u, O.PERIODIC, op)
+        gvm, gvp, gfl = npw.npweno_reconstruct(_dev(u, torch.float32), O.PERIODIC, _gp(npw, op, precision=1))
+        gvm = gvm.cpu().numpy().astype(np.float64)
+        gvp = gvp.cpu().numpy().astype(np.float64)
+        gfl = gfl.cpu().numpy()
+        ok = (fl & TIES) == 0
+        assert np.array_equal(gfl[ok] & DECISIONS, fl[ok] & DECISIONS), n
+        scale = np.abs(u).max()
+        assert np.abs(gvm[ok] - vm[ok]).max() <= 2e-6 * scale, n
+        assert np.abs(gvp[ok] - vp[ok]).max() <= 2e-6 * scale, n
+
+
+def test_k2_mixed_burgers_batch(npw):
+    """Mixed-precision batch of periodic Burgers instances (ragged sizes) to T = 0.5 with
+    RBF-WENO3 (Gaussian) against the oracle from the same float data."""
+    inst = I.burgers_batch(count=12, nmin=64, nmax=1500, t_end=0.5, seed_index=31)
+    ns = [it.n for it in inst]
+    table, total = npw.make_instances(ns, [it.dx for it in inst], [0.5] * len(ns), [0.5] * len(ns), [0] * len(ns))
+    host0 = np.concatenate([it.u0[0] for it in inst]).astype(np.float32)
+    arena = _dev(host0, torch.float32)
+    p = npw.Params(k=2, rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED)
+    st, stats = npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, p)
+    assert st == 0
+    a = arena.cpu().numpy().astype(np.float64)
+    off = 0
+    op = O.Params(k=2, rbf=O.GA, eta_guard=MIXED_GUARD)
+    for k, it in enumerate(inst):
+        u0 = host0[off:off + it.n].astype(np.float64)
+        ref, rst = O.solve(u0, it.dx, 0.5, 0.5, O.BURGERS, O.PERIODIC, op)
+        assert stats[k]["status"] == 0 and stats[k]["t"] == 0.5
+        e = np.abs(a[off:off + it.n] - ref)
+        assert e.mean() <= 1e-4 and e.max() <= 2e-2, (k, it.n, e.mean(), e.max())
+        off += it.n
+
+
+@pytest.mark.parametrize("precision,switch", [(0, 1), (1, 0), (1, 1)])
+def test_k2_2d_euler_step(npw, precision, switch):
+    """One RK3 step of the isentropic vortex, 2D dimension by dimension, k = 2.  FP64: the
+    oracle's bits (1e-12).  Mixed without the switch: float rounding (2e-6 relative).  Mixed
+    with the switch: the decisions of stages 2 and 3 are taken on the float stage values, which
+    differ from the oracle's double stage values by rounding, so a switch at a near tie may go
+    the other way there (measured: the maximum error grows from 9e-7 to 3e-5 on this data while
+    the mean stays at rounding level): mean error <= 1e-6 and max <= 3e-5 relative."""
+    U, d = I.isentropic_vortex(64, 4.0, 5.0, 5.0, npts=2)
+    if precision:
+        U = U.astype(np.float32).astype(np.float64)
+    op = O.Params(k=2, monotone_switch=switch, eta_guard=MIXED_GUARD if precision else 0.0)
+    ref = O.rk3_step_2d(U, d, d, 0.2 * d, O.EULER2D, O.PERIODIC, op)
+    gu = _dev(U, torch.float32 if precision else torch.float64)
+    npw.npweno_rk3_step_2d(gu, d, d, 0.2 * d, O.EULER2D, O.PERIODIC, _gp(npw, op, precision=precision))
+    got = gu.cpu().numpy().astype(np.float64)
+    if not precision:
+        assert _rel(got, ref) <= FP64_TOL
+    elif not switch:
+        assert _rel(got, ref) <= 2e-6
+    else:
+        scale = np.abs(ref).max()
+        e = np.abs(got - ref)
+        assert e.mean() <= 1e-6 * scale and e.max() <= 3e-5 * scale, (e.mean() / scale, e.max() / scale)
+
+
+def test_k2_server_matches_batch_solve(npw):
+    """The request server runs k = 2 requests (face-based float kernels, uncompensated); each
+    result equals the batch solve of the same instance."""
+    p = npw.Params(k=2, precision=1, batch_mode=1)
+    srv = npw.Server(heap_cells=20000, max_slots=4, params=p)
+    reqs = I.burgers_batch(count=3, nmin=300, nmax=900, seed_index=33)
+    for j, it in enumerate(reqs):
+        srv.submit(it.u0[0], npw.NPW_FLUX_BURGERS, 0, it.dx, 0.3, 0.5, tag=j)
+    got = {}
+    for _ in range(1000):
+        act, q = srv.step(16)
+        for r in srv.poll():
+            got[r["tag"]] = r
+        if act == 0 and q == 0:
+            break
+    srv.close()
+    assert len(got) == 3
+    for j, it in enumerate(reqs):
+        table, _ = npw.make_instances([it.n], [it.dx], [0.3], [0.5], [0])
+        arena = _dev(it.u0[0], torch.float32)
+        st, stats = npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, p)
+        assert st == 0 and got[j]["status"] == 0 and got[j]["steps"] == stats[0]["steps"]
+        assert np.array_equal(got[j]["u"], arena.cpu().numpy())
