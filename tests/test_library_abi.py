@@ -42,10 +42,10 @@ def test_default_params_and_errors_without_gpu():
     assert (p.k, p.scheme, p.rbf, p.monotone_switch, p.precision) == (3, npw.NPW_RBF_WENO, npw.NPW_RBF_MQ, 1, npw.NPW_FP64)
     assert p.eps_weno == 1e-6 and p.gamma == 1.4 and p.eps_M == 1e-12
     # argument validation happens before any CUDA call
-    bad = npw.Params(k=2).c()
+    bad = npw.Params(k=4).c()
     st = lib.npweno_reconstruct(ctypes.c_void_p(16), 100, 1, 0, ctypes.byref(bad), ctypes.c_void_p(16),
                                 ctypes.c_void_p(16), None, None)
-    assert st == npw.NPW_EINVAL and b"k = 3" in lib.npw_last_error()
+    assert st == npw.NPW_EINVAL and b"k must be 2" in lib.npw_last_error()
     good = npw.Params().c()
     st = lib.npweno_reconstruct(ctypes.c_void_p(16), 5, 1, 0, ctypes.byref(good), ctypes.c_void_p(16),
                                 ctypes.c_void_p(16), None, None)
