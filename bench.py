@@ -380,38 +380,57 @@ def run_serving(npw, reqs, max_steps: int = 32):
     return lat, cells / span, ok
 
 
-def run_fifo_fp64(npw, reqs):
-    """The comparator: one request at a time, first in first out, plain FP64 per-instance solve."""
+def fifo_service_times(npw, reqs):
+    """The comparator's service time of every request: the plain FP64 per-instance solve, one
+    request at a time (host copy in, solve, host copy out)."""
     import torch
     p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP64)
-    t0 = time.perf_counter()
-    lat, cells = [], 0
+    svc, cells = [], []
     for r in reqs:
-        now = time.perf_counter() - t0
-        if now < r["arrival"]:
-            time.sleep(r["arrival"] - now)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         u = torch.tensor(r["u0"], dtype=torch.float64, device="cuda")
         st = npw.npweno_solve(u.view(r["m"], r["n"]), r["dx"], r["t_end"], 0.5, r["kind"], r["bc"], p)
         u.cpu()
-        lat.append(time.perf_counter() - t0 - r["arrival"])
-        cells += r["n"] * st["steps"]
-    span = time.perf_counter() - t0 - reqs[0]["arrival"]
-    return np.array(lat), cells / span
+        svc.append(time.perf_counter() - t0)
+        cells.append(r["n"] * st["steps"])
+    return np.array(svc), np.array(cells)
 
 
-def serving_block(npw, count: int, rate: float):
-    reqs = serving_requests(count, rate)
-    lat, thr, ok = run_serving(npw, reqs)
-    flat, fthr = run_fifo_fp64(npw, reqs)
+def fifo_latencies(svc, arrivals):
+    """Latencies of a first-in first-out server that runs one request at a time: request i
+    starts at max(its arrival, the end of request i-1) and takes its service time."""
+    lat, end = [], 0.0
+    for s, a in zip(svc, arrivals):
+        end = max(end, a) + s
+        lat.append(end - a)
+    return np.array(lat), end
+
+
+def serving_block(npw, count: int, rates):
+    """The request stream at each arrival rate (the same requests; only the arrival times
+    scale): the continuous-batching server measured live, and the FP64 first-in first-out
+    comparator from its measured per-request service times (it runs one request at a time, so
+    its latencies follow from the arrival times and the service times)."""
     q = lambda a, x: float(np.percentile(a, x) * 1e3)
-    return {
-        "requests": count, "rate_per_s": rate,
-        "mix": "1/2 periodic Burgers (N 64..8192, T 0.15..1.5), 1/2 transmissive Euler (N 256..8192)",
-        "server": {"p50_ms": q(lat, 50), "p99_ms": q(lat, 99), "cell_updates_per_s": thr, "all_ok": ok,
-                   "mode": "continuous batching, NPW_FP32_MIXED, per-stage kernels, 32-step rounds"},
-        "fp64_fifo": {"p50_ms": q(flat, 50), "p99_ms": q(flat, 99), "cell_updates_per_s": fthr,
-                      "mode": "one request at a time, npweno_solve NPW_FP64"},
-    }
+    base = serving_requests(count, rates[0])
+    svc, fcells = fifo_service_times(npw, base)
+    out = {"requests": count,
+           "mix": "1/2 periodic Burgers (N 64..8192, T 0.15..1.5), 1/2 transmissive Euler (N 256..8192)",
+           "server_mode": "continuous batching, NPW_FP32_MIXED, per-stage kernels, 32-step rounds",
+           "fp64_fifo_mode": "one request at a time, npweno_solve NPW_FP64; latencies from measured service times",
+           "rates": []}
+    for rate in rates:
+        reqs = serving_requests(count, rate)
+        lat, thr, ok = run_serving(npw, reqs)
+        flat, fend = fifo_latencies(svc, [r["arrival"] for r in reqs])
+        out["rates"].append({
+            "rate_per_s": rate,
+            "server": {"p50_ms": q(lat, 50), "p99_ms": q(lat, 99), "cell_updates_per_s": thr, "all_ok": ok},
+            "fp64_fifo": {"p50_ms": q(flat, 50), "p99_ms": q(flat, 99),
+                          "cell_updates_per_s": float(fcells.sum() / (fend - reqs[0]["arrival"]))},
+        })
+    return out
 
 
 # ------------------------------------------------------------------------------- ranks
@@ -470,6 +489,7 @@ def run_euler1d(args, rank, world, local_rank):
     pristine = torch.tensor(host0, device="cuda")
     arena = pristine.clone()
     p = npw.Params(precision=npw.NPW_FP32_MIXED, characteristic=args.characteristic, batch_mode=1)
+    tile = npw.npw_autotune_1d(npw.NPW_FLUX_EULER1D, 3, p)  # later runs with tile_1d = 0 use it
     ws = torch.empty(npw.npw_batch_workspace_size(table, 3, p), dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     holder = {}
@@ -503,7 +523,8 @@ def run_euler1d(args, rank, world, local_rank):
                                 f"[256,65536], Riemann + Shu-Osher-type data, {'characteristic' if args.characteristic else 'component'}-wise, "
                                 f"RBF-WENO5 MQ + switch, LF, TVD-RK3 CFL 0.5 to {args.t_frac} x each end time"),
                    "instances": 512, "cells": int(sum(ns)), "cell_updates_per_step": int(cu),
-                   "path": "per-stage fused kernels (batch_mode 1), 1024-cell tiles", "l2": "flushed before every timed step"},
+                   "path": f"per-stage fused kernels (batch_mode 1), {tile}-cell tiles (autotuned), steps replayed "
+                           "as CUDA graphs", "l2": "flushed before every timed step"},
         "roofline": {"bound": "alu", "achieved": fp64, "peak": FP64_PIPE_PEAK / 1e9, "unit": "G FP64-pipe instr/s",
                      "frac": (fp64 / (FP64_PIPE_PEAK / 1e9)) if fp64 else None, "traffic": None,
                      "kernel": "stage1d_fast_kernel<EULER1D>",
@@ -570,7 +591,7 @@ def run_euler2d(args, rank, world, local_rank):
                    "l2": "flushed before every timed step"},
         "roofline": {"bound": "alu", "achieved": fp64, "peak": FP64_PIPE_PEAK / 1e9, "unit": "G FP64-pipe instr/s",
                      "frac": (fp64 / (FP64_PIPE_PEAK / 1e9)) if fp64 else None, "traffic": None,
-                     "kernel": "stage2d_kernel<float,double,EULER2D>",
+                     "kernel": "stage2d_fast_kernel<EULER2D>",
                      "hbm_view": {"achieved_gbs": cu * args.steps * 128 / st_s / 1e9 if st_s > 0 else None,
                                   "peak_gbs": _peaks()[0], "bytes_per_cell_update": 128},
                      "stage_launches": int(pr.stage_launches), "stage_ms": pr.stage_ms},
@@ -596,7 +617,7 @@ def main():
     ap.add_argument("--eta-eval", type=int, default=0, choices=[0, 1],
                     help="0: eta in FP64 (the configuration's FP64 shape-parameter step); 1: exact double-float")
     ap.add_argument("--serve-requests", type=int, default=60, help="requests of the serving run (0: skip)")
-    ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrival rate of the serving run (1/s)")
+    ap.add_argument("--serve-rates", default="10,100,1000", help="Poisson arrival rates of the serving runs (1/s)")
     ap.add_argument("--variant-steps", type=int, default=1,
                     help="timed solves of the eta_eval=1 variant reported beside the headline (0: skip)")
     ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
@@ -649,7 +670,7 @@ def main():
     out, inst = run_gpu(args, rank, world, local_rank)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         import paper_1602_00182_gb300.npweno as npw
-        out["serving"] = serving_block(npw, args.serve_requests, args.serve_rate)
+        out["serving"] = serving_block(npw, args.serve_requests, [float(x) for x in args.serve_rates.split(",")])
     if rank == 0:
         if not args.no_cpu_baseline:
             v, wall, desc = cpu_sample(inst, cores)

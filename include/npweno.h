@@ -88,7 +88,10 @@ typedef struct {
     int32_t batch_mode;      /* npweno_batch_solve, NPW_FP32_MIXED: 0 = instances whose state fits in one
                                 CTA's shared memory run whole in one CTA (resident), the rest through the
                                 per-stage kernels; 1 = every instance through the per-stage kernels */
-    int32_t pad_;
+    int32_t tile_1d;         /* cells per CTA of the 1D per-stage kernels: 256, 512, 1024 or 2048; 0 = the
+                                value npw_autotune_1d chose for this flux kind, m, k, precision and
+                                characteristic flag on this device, else 1024.  Results do not depend on
+                                it (each face gets the same arithmetic in any tiling) */
     double eta_max;          /* eta = 0 where |eta| > eta_max: the perturbation argument (Sec. 3) needs a small
                                 eta, and a monotone stencil with zero slope at the face makes the Table k3
                                 denominator vanish (eta ~ num / eps_M); 0 = automatic (1.0), < 0 = off */
@@ -261,6 +264,22 @@ npw_status npw_server_step(npw_server* s, int32_t max_steps, int32_t* active, in
 /* Completed results, oldest first; *nout <= max. */
 npw_status npw_server_poll(npw_server* s, npw_result* out, int32_t max, int32_t* nout);
 void npw_server_destroy(npw_server* s);
+
+/*
+ * Tile autotuner for the 1D per-stage kernels (the batching pattern's autotuned tile shape).
+ * Times TVD-RK3 steps of a 2^21-cell periodic instance of smooth synthetic data (a quiet
+ * Euler state for m = 3) with each tile size 256, 512, 1024, 2048 cells per CTA, keeps the
+ * fastest in a process-wide table keyed by device, flux kind, m, k, precision and
+ * characteristic flag, and returns it.  Later runs with params->tile_1d = 0 use it.
+ *   scratch: caller-owned device memory of at least npw_autotune_scratch_bytes(m, params)
+ *            bytes (its contents are overwritten).
+ *   stream:  cudaStream_t (void*); the call synchronises with it (bounded wait).
+ * Returns NPW_EINVAL for bad arguments or a small scratch, NPW_ECUDA / NPW_ETIMEOUT on device
+ * errors (the table is then unchanged).
+ */
+size_t npw_autotune_scratch_bytes(int32_t m, const npw_params* params);
+npw_status npw_autotune_1d(int32_t flux_kind, int32_t m, const npw_params* params, void* scratch,
+                           size_t scratch_bytes, void* stream, int32_t* best_tile);
 
 /*
  * npweno_rk3_step_noalloc -- the same TVD-RK3 step as npweno_rk3_step (identical kernels and

@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <deque>
 #include <string>
+#include <array>
+#include <map>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -58,6 +60,8 @@ npw_status check_params(const npw_params* p) {
     if (p->precision != NPW_FP64 && p->precision != NPW_FP32_MIXED) return fail(NPW_EINVAL, "bad precision");
     if (p->eta_eval < 0 || p->eta_eval > 1) return fail(NPW_EINVAL, "bad eta_eval %d", p->eta_eval);
     if (p->batch_mode < 0 || p->batch_mode > 1) return fail(NPW_EINVAL, "bad batch_mode %d", p->batch_mode);
+    if (p->tile_1d != 0 && p->tile_1d != 256 && p->tile_1d != 512 && p->tile_1d != 1024 && p->tile_1d != 2048)
+        return fail(NPW_EINVAL, "tile_1d must be 0, 256, 512, 1024 or 2048, got %d", p->tile_1d);
     if (!(p->eps_weno > 0.0)) return fail(NPW_EINVAL, "eps_weno must be > 0");
     if (!(p->gamma > 1.0)) return fail(NPW_EINVAL, "gamma must be > 1");
     return NPW_OK;
@@ -138,7 +142,8 @@ Layout1D layout_1d(int64_t arena_elems, int count, int64_t ntiles, size_t esz) {
     return L;
 }
 
-int64_t tiles_of(int64_t n) { return (n + npw::TILE_1D - 1) / npw::TILE_1D; }
+// tiles of an instance; the default (the smallest tile a run may use) sizes the tile tables
+int64_t tiles_of(int64_t n, int tile = npw::TILE_1D_MIN) { return (n + tile - 1) / tile; }
 
 double wait_timeout_s() {
     const char* e = getenv("NPW_WAIT_TIMEOUT_S");
@@ -201,15 +206,21 @@ void count_launch(int64_t k = 1) {
     std::lock_guard<std::mutex> g(p.mu);
     p.launches += k;
 }
-// returns the event pair to bracket a stage launch (null events when profiling is off)
-std::pair<cudaEvent_t, cudaEvent_t> stage_begin(cudaStream_t s, int slot = -1) {
+// set while a step sequence is captured into a CUDA graph: launches are counted, and timed,
+// when the graph is replayed instead
+thread_local bool t_capturing = false;
+
+// returns the event pair to bracket a stage launch, or a replay of nlaunch captured stage
+// launches (null events when profiling is off)
+std::pair<cudaEvent_t, cudaEvent_t> stage_begin(cudaStream_t s, int slot = -1, int64_t nlaunch = 1) {
+    if (t_capturing) return {nullptr, nullptr};
     Profiler& p = prof();
     std::lock_guard<std::mutex> g(p.mu);
-    p.launches += 1;
+    p.launches += nlaunch;
     if (slot < 0)
-        p.stage_launches += 1;
+        p.stage_launches += nlaunch;
     else
-        p.res_launches[slot] += 1;
+        p.res_launches[slot] += nlaunch;
     if (!p.on) return {nullptr, nullptr};
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (!p.pool.empty()) {
@@ -431,10 +442,31 @@ struct Run1D {
     Layout1D L;
     int64_t ntiles;
     cudaStream_t s;
+    int tile = npw::TILE_1D;     // cells per CTA of the per-stage kernels
     bool comp = false;           // compensated float per-stage kernels (float, component-wise)
     std::vector<char> resident;  // per instance: solved by the resident kernel
     std::vector<cudaEvent_t> joins;  // side-stream work the caller's stream waits for at the end
 };
+
+// ---------------------------------------------------------------------------------------
+// Tile sizes chosen by npw_autotune_1d, per device and (flux kind, m, k, precision,
+// characteristic).  A run with params->tile_1d = 0 takes the chosen size, else the default.
+// ---------------------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::array<int, 6>, int> g_tune;
+
+std::array<int, 6> tune_key(const npw_params* p, int kind, int m) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    return {dev, kind, m, p->k, p->precision, p->characteristic ? 1 : 0};
+}
+
+int resolve_tile(const npw_params* p, int kind, int m) {
+    if (p->tile_1d > 0) return p->tile_1d;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(tune_key(p, kind, m));
+    return it == g_tune.end() ? npw::TILE_1D : it->second;
+}
 
 // the compensated float kernels (stage1d_fast_kernel, the resident kernel) cover float,
 // component-wise, k = 3; every other case runs the face-based stage kernel
@@ -450,7 +482,7 @@ bool resident_ok(const npw_params* p, int m, int64_t n) {
 int64_t tiles_for(const Run1D& r, const npw_instance* inst, int count) {
     int64_t nt = 0;
     for (int i = 0; i < count; ++i)
-        if (r.resident.empty() || !r.resident[i]) nt += tiles_of(inst[i].n);
+        if (r.resident.empty() || !r.resident[i]) nt += tiles_of(inst[i].n, r.tile);
     return nt;
 }
 
@@ -463,7 +495,7 @@ npw_status run_step_kernels(const Run1D& r, int advance) {
     a.tiles = reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles);
     a.ntiles = (int)r.ntiles;
     a.advance = advance;
-    a.tile = npw::TILE_1D;
+    a.tile = r.tile;
     a.mp = r.mp;
     void* u = r.arena;
     void* u1 = r.ws + r.L.u1;
@@ -507,8 +539,8 @@ npw_status setup_1d(Run1D& r, const npw_instance* inst, int count, double dt_fix
         hi[i].cfl = inst[i].cfl;
         hi[i].bc = inst[i].bc;
         const bool res = !r.resident.empty() && r.resident[i];
-        hi[i].ntiles = res ? 0 : (int32_t)tiles_of(inst[i].n);
-        for (int64_t t = 0; t < hi[i].ntiles; ++t) ht.push_back(npw::Tile{i, (int32_t)(t * npw::TILE_1D)});
+        hi[i].ntiles = res ? 0 : (int32_t)tiles_of(inst[i].n, r.tile);
+        for (int64_t t = 0; t < hi[i].ntiles; ++t) ht.push_back(npw::Tile{i, (int32_t)(t * r.tile)});
     }
     // pageable source: each call returns once the data is staged
     NPW_CUDA(cudaMemcpyAsync(r.ws + r.L.inst, hi.data(), sizeof(npw::InstDev) * count, cudaMemcpyHostToDevice, r.s));
@@ -522,10 +554,10 @@ npw_status setup_1d(Run1D& r, const npw_instance* inst, int count, double dt_fix
     cudaError_t e = r.ntiles == 0 ? cudaSuccess
                   : r.fp32 ? npw::launch_alpha_init<float>(r.arena, di, ctl,
                                                            reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles),
-                                                           (int)r.ntiles, npw::TILE_1D, r.m, r.kind, r.mp, r.s)
+                                                           (int)r.ntiles, r.tile, r.m, r.kind, r.mp, r.s)
                            : npw::launch_alpha_init<double>(r.arena, di, ctl,
                                                             reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles),
-                                                            (int)r.ntiles, npw::TILE_1D, r.m, r.kind, r.mp, r.s);
+                                                            (int)r.ntiles, r.tile, r.m, r.kind, r.mp, r.s);
     if (e != cudaSuccess) return cuda_fail(e, "alpha kernel launch");
     npw::ctl_start_kernel<<<blocks, 128, 0, r.s>>>(ctl, di, count, mode, dt_fixed);
     NPW_CUDA(cudaGetLastError());
@@ -533,7 +565,8 @@ npw_status setup_1d(Run1D& r, const npw_instance* inst, int count, double dt_fix
     if (r.comp && r.ntiles > 0) {
         NPW_CUDA(npw::launch_comp_begin(reinterpret_cast<const float*>(r.arena), reinterpret_cast<float*>(r.ws + r.L.sbuf),
                                         reinterpret_cast<float*>(r.ws + r.L.cbuf), di,
-                                        reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles), (int)r.ntiles, r.m, r.s));
+                                        reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles), (int)r.ntiles, r.tile,
+                                        r.m, r.s));
         count_launch();
     }
     return NPW_OK;
@@ -664,19 +697,85 @@ npw_status comp_end(const Run1D& r) {
     if (!r.comp || r.ntiles == 0) return NPW_OK;
     NPW_CUDA(npw::launch_comp_end(reinterpret_cast<float*>(r.arena), reinterpret_cast<const float*>(r.ws + r.L.sbuf),
                                   reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst),
-                                  reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles), (int)r.ntiles, r.m, r.s));
+                                  reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles), (int)r.ntiles, r.tile, r.m,
+                                  r.s));
     count_launch();
     return NPW_OK;
 }
 
 // Run steps until every instance is done: launch as many steps as the largest remaining
 // estimate (capped), then poll.
+// ---------------------------------------------------------------------------------------
+// CUDA graph of GRAPH_STEPS whole steps (3 stage launches each) for the per-stage path.  The
+// stage kernels read t, dt, alpha and the done flag of every instance from its control word,
+// so one captured launch sequence serves every replay, and steps past an instance's end time
+// are no-ops for it (its CTAs return at once).  Capture uses a private stream; the graph is
+// launched on the caller's stream.
+// ---------------------------------------------------------------------------------------
+constexpr int GRAPH_STEPS = 8;
+
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    StepGraph() = default;
+    StepGraph(const StepGraph&) = delete;
+    StepGraph& operator=(const StepGraph&) = delete;
+    ~StepGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+npw_status capture_steps(const Run1D& r, StepGraph& g) {
+    cudaStream_t cs = nullptr;
+    NPW_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    Run1D rc = r;
+    rc.s = cs;
+    cudaGraph_t graph = nullptr;
+    npw_status st = NPW_OK;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        t_capturing = true;
+        for (int k = 0; k < GRAPH_STEPS && st == NPW_OK; ++k) st = step_kernels(rc, 1);
+        t_capturing = false;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e2 != cudaSuccess) e = e2;
+    }
+    if (st == NPW_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (st) return st;
+    if (e != cudaSuccess) {
+        g.exec = nullptr;
+        return cuda_fail(e, "capture of the step graph");
+    }
+    return NPW_OK;
+}
+
+npw_status replay_steps(const Run1D& r, const StepGraph& g, long long graphs) {
+    for (long long k = 0; k < graphs; ++k) {
+        auto ev = stage_begin(r.s, -1, 3 * GRAPH_STEPS);
+        const cudaError_t e = cudaGraphLaunch(g.exec, r.s);
+        stage_end(ev, r.s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    }
+    return NPW_OK;
+}
+
 npw_status run_to_end(Run1D& r, npw_solve_stats* out) {
     long long act = 0, rem = 0;
     npw_status st = poll(r, &act, &rem);
+    StepGraph graph;
+    bool direct_done = false;
     while (st == NPW_OK && act > 0) {
         long long chunk = rem < 1 ? 1 : (rem > 256 ? 256 : rem);
+        // long chunks replay the captured graph (after one direct step has set up the kernels'
+        // attributes); the remainder, and short runs, launch directly
+        if (chunk > GRAPH_STEPS && direct_done) {
+            if (!graph.exec && (st = capture_steps(r, graph))) break;
+            if ((st = replay_steps(r, graph, chunk / GRAPH_STEPS))) break;
+            chunk %= GRAPH_STEPS;
+        }
         for (long long k = 0; k < chunk && st == NPW_OK; ++k) st = step_kernels(r, 1);
+        direct_done = true;
         if (st == NPW_OK) st = poll(r, &act, &rem);
     }
     if (st == NPW_OK) st = comp_end(r);
@@ -818,8 +917,9 @@ static npw_status single_run(void* u, int64_t n, int32_t m, double dx, double t_
     r.mp = method(params);
     r.fp32 = params->precision == NPW_FP32_MIXED;
     r.ws = static_cast<unsigned char*>(workspace);
-    r.ntiles = tiles_of(n);
-    r.L = layout_1d(n * m, 1, r.ntiles, elem_size(params));
+    r.tile = resolve_tile(params, flux_kind, m);
+    r.ntiles = tiles_of(n, r.tile);
+    r.L = layout_1d(n * m, 1, tiles_of(n), elem_size(params));
     r.s = s;
     r.comp = compensated(params);
     if (workspace_bytes < r.L.total)
@@ -910,6 +1010,7 @@ npw_status npweno_batch_solve(void* arena, const npw_instance* inst, int32_t cou
     if (workspace_bytes < r.L.total)
         return fail(NPW_EINVAL, "workspace too small: %zu < %zu bytes", workspace_bytes, r.L.total);
     r.comp = compensated(params);
+    r.tile = resolve_tile(params, flux_kind, m);
     r.resident.assign(count, 0);
     bool any_res = false;
     for (int i = 0; i < count; ++i) {
@@ -925,6 +1026,79 @@ npw_status npweno_batch_solve(void* arena, const npw_instance* inst, int32_t cou
         if ((st = launch_resident(r, inst, ss, &joined))) return st;
     }
     return run_to_end(r, out);
+}
+
+// ---------------------------------------------------------------------------------------
+// Tile autotuner
+// ---------------------------------------------------------------------------------------
+static const int64_t kTuneCells = (int64_t)1 << 21;
+
+size_t npw_autotune_scratch_bytes(int32_t m, const npw_params* params) {
+    if (!params || m < 1 || m > 3) return 0;
+    return align256((size_t)(kTuneCells * m) * elem_size(params)) + npw_workspace_size(kTuneCells, m, params);
+}
+
+npw_status npw_autotune_1d(int32_t flux_kind, int32_t m, const npw_params* params, void* scratch,
+                           size_t scratch_bytes, void* stream, int32_t* best_tile) {
+    npw_status st = check_params(params);
+    if (st) return st;
+    if (!scratch || !best_tile) return fail(NPW_EINVAL, "null pointer");
+    if ((st = check_kind_1d(flux_kind, m, params))) return st;
+    const size_t need = npw_autotune_scratch_bytes(m, params);
+    if (scratch_bytes < need) return fail(NPW_EINVAL, "autotune scratch too small: %zu < %zu bytes", scratch_bytes, need);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* base = static_cast<unsigned char*>(scratch);
+    const size_t arena_b = align256((size_t)(kTuneCells * m) * elem_size(params));
+    void* u = base;
+    void* ws = base + arena_b;
+    const size_t ws_b = scratch_bytes - arena_b;
+    const bool fp32 = params->precision == NPW_FP32_MIXED;
+    const double dx = 1.0 / (double)kTuneCells, dt = 0.1 * dx;
+    static const int kTiles[4] = {256, 512, 1024, 2048};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NPW_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(NPW_ECUDA, "cudaEventCreate");
+    }
+    int best = 0;
+    float best_ms = 0.0f;
+    for (int c = 0; c < 4 && st == NPW_OK; ++c) {
+        npw_params q = *params;
+        q.tile_1d = kTiles[c];
+        cudaError_t e = fp32 ? npw::launch_tune_init<float>(static_cast<float*>(u), kTuneCells, m, s)
+                             : npw::launch_tune_init<double>(static_cast<double*>(u), kTuneCells, m, s);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "autotune init");
+            break;
+        }
+        for (int w = 0; w < 2 && st == NPW_OK; ++w)
+            st = npweno_rk3_step(u, kTuneCells, m, dx, dt, flux_kind, NPW_BC_PERIODIC, &q, ws, ws_b, nullptr, stream);
+        if (st) break;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < 4 && st == NPW_OK; ++k)
+            st = npweno_rk3_step(u, kTuneCells, m, dx, dt, flux_kind, NPW_BC_PERIODIC, &q, ws, ws_b, nullptr, stream);
+        cudaEventRecord(e1, s);
+        if (st || (st = bounded_sync(s))) break;
+        float ms = 0.0f;
+        if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+            st = cuda_fail(e, "cudaEventElapsedTime");
+            break;
+        }
+        if (best == 0 || ms < best_ms) {
+            best = kTiles[c];
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune[tune_key(params, flux_kind, m)] = best;
+    }
+    *best_tile = best;
+    return NPW_OK;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1324,7 +1498,7 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
             d.t_end = sl.req.t_end;
             d.cfl = sl.req.cfl;
             d.bc = sl.req.bc;
-            d.ntiles = (int32_t)tiles_of(sl.req.n);
+            d.ntiles = (int32_t)tiles_of(sl.req.n, npw::TILE_1D);
             for (int64_t t = 0; t < d.ntiles; ++t) {
                 tiles.push_back(npw::Tile{k, (int32_t)(t * npw::TILE_1D)});
                 if (sl.fresh) newtiles.push_back(npw::Tile{k, (int32_t)(t * npw::TILE_1D)});
@@ -1380,7 +1554,7 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
                                                 reinterpret_cast<float*>(sv->arena + sv->L.heap_s),
                                                 reinterpret_cast<float*>(sv->arena + sv->L.heap_c), dinst,
                                                 reinterpret_cast<const npw::Tile*>(sv->arena + sv->L.newtiles) + b2,
-                                                (int)(e2 - b2), flux_m(kind), sv->s));
+                                                (int)(e2 - b2), npw::TILE_1D, flux_m(kind), sv->s));
                 count_launch();
                 b2 = e2;
             }

@@ -37,15 +37,15 @@ cudaError_t launch_resident_f32(const ResidentArgs& a, int m, int kind, int64_t 
 
 namespace npw {
 cudaError_t launch_comp_begin(const float* u, float* s, float* c, const InstDev* inst, const Tile* tiles, int ntiles,
-                              int m, cudaStream_t st) {
+                              int tile, int m, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
-    comp_copy_kernel<<<ntiles, THREADS_1D, 0, st>>>(s, u, c, inst, tiles, TILE_1D, m);
+    comp_copy_kernel<<<ntiles, THREADS_1D, 0, st>>>(s, u, c, inst, tiles, tile, m);
     return cudaGetLastError();
 }
-cudaError_t launch_comp_end(float* u, const float* s, const InstDev* inst, const Tile* tiles, int ntiles, int m,
-                            cudaStream_t st) {
+cudaError_t launch_comp_end(float* u, const float* s, const InstDev* inst, const Tile* tiles, int ntiles, int tile,
+                            int m, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
-    comp_copy_kernel<<<ntiles, THREADS_1D, 0, st>>>(u, s, nullptr, inst, tiles, TILE_1D, m);
+    comp_copy_kernel<<<ntiles, THREADS_1D, 0, st>>>(u, s, nullptr, inst, tiles, tile, m);
     return cudaGetLastError();
 }
 }  // namespace npw

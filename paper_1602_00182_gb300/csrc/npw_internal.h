@@ -157,11 +157,15 @@ cudaError_t launch_ctl_start_2d(Ctl* ctl, const Inst2D* inst, int mode, double d
 cudaError_t launch_count_active(const Ctl* ctl, int count, int* active, cudaStream_t s);
 // compensated float path: before the first step s = u and c = 0; after the last, u = s
 cudaError_t launch_comp_begin(const float* u, float* s, float* c, const InstDev* inst, const Tile* tiles, int ntiles,
-                              int m, cudaStream_t st);
-cudaError_t launch_comp_end(float* u, const float* s, const InstDev* inst, const Tile* tiles, int ntiles, int m,
-                            cudaStream_t st);
+                              int tile, int m, cudaStream_t st);
+cudaError_t launch_comp_end(float* u, const float* s, const InstDev* inst, const Tile* tiles, int ntiles, int tile,
+                            int m, cudaStream_t st);
+// fills [m][n] with smooth data for the tile autotuner (m = 3: a quiet Euler state)
+template <typename R>
+cudaError_t launch_tune_init(R* u, int64_t n, int m, cudaStream_t st);
 
-constexpr int TILE_1D = 1024;  // cells per CTA tile in the 1D stage kernel
+constexpr int TILE_1D = 1024;     // default cells per CTA tile in the 1D stage kernels
+constexpr int TILE_1D_MIN = 256;  // smallest tile a run may choose (sizes the tile tables)
 constexpr size_t RESIDENT_SMEM_MAX = 200 * 1024;  // shared memory a resident CTA may use
 constexpr int THREADS_1D = 256;
 constexpr int TX_2D = 32;      // 2D tile

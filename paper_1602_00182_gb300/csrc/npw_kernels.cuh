@@ -706,6 +706,180 @@ __device__ __forceinline__ R grid_get(const R* u, const Inst2D& in, int64_t i, i
     return u[j * nx + i];
 }
 
+// ---------------------------------------------------------------------------------------
+// 2D stage kernel of the mixed path (float state, component-wise, k = 3) in phases, each a
+// balanced loop over independent work items:
+//   E  eta of every (face, field) of both directions (FP64 quotient, switch)
+//   C  reconstruction of every (cell, field) of both directions: v^- at its right / upper face
+//      and v^+ at its left / lower face, one set of smoothness indicators for both
+//   F  Lax-Friedrichs flux of every face (all fields)
+//   U  flux difference and Shu-Osher stage combination of every cell
+// Every face value gets the arithmetic of fast::face_field, so the result is the same as the
+// face-by-face kernel's; the phases avoid reconstructing a cell once per face and the uneven
+// per-thread face counts of that kernel.
+// ---------------------------------------------------------------------------------------
+template <int KIND>
+__global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs a) {
+    constexpr int M = kind_m<KIND>();
+    constexpr int BX = TX_2D + 6, BY = TY_2D + 6;
+    constexpr int NFX = (TX_2D + 1) * TY_2D;  // x faces: (qx, qy), qx = 0..TX between cells qx-1, qx
+    constexpr int NFY = TX_2D * (TY_2D + 1);  // y faces: (qx, qy), qy = 0..TY
+    __shared__ float su[BY * BX * M];
+    __shared__ float ef[(NFX + NFY) * M];    // eta per (face, field); then the fluxes
+    __shared__ float vmf[(NFX + NFY) * M];   // v^- per (face, field)
+    __shared__ float vpf[(NFX + NFY) * M];   // v^+ per (face, field)
+    __shared__ double red[32];
+    __shared__ int redbad[32];
+    __shared__ double red2[32];
+    __shared__ int redbad2[32];
+    const Inst2D in = *a.inst;
+    Ctl* ctl = a.ctl;
+    if (*(volatile int32_t*)&ctl->done) return;
+    const int tx0 = (blockIdx.x % in.tiles_x) * TX_2D;
+    const int ty0 = (blockIdx.x / in.tiles_x) * TY_2D;
+    const int64_t nx = in.nx, ny = in.ny, cells = nx * ny;
+    const float* uin = reinterpret_cast<const float*>(a.uin) + in.off;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const fast::FParams fp = fast::fparams(a.mp);
+    for (int idx = tid; idx < BX * BY * M; idx += nthr) {
+        const int k = idx / (BX * BY);
+        const int rem = idx - k * BX * BY;
+        const int by = rem / BX, bx = rem - by * BX;
+        const bool corner = (bx < 3 || bx >= TX_2D + 3) && (by < 3 || by >= TY_2D + 3);
+        su[(by * BX + bx) * M + k] = corner ? 0.0f
+                                            : grid_get<float>(uin + k * cells, in, (int64_t)tx0 - 3 + bx,
+                                                              (int64_t)ty0 - 3 + by, a.mp.inflow[k]);
+    }
+    const double dt = *(volatile double*)&ctl->dt;
+    const float ax = (float)(*(volatile double*)&ctl->alpha);
+    const float ay = (float)(*(volatile double*)&ctl->alpha_y);
+    __syncthreads();
+#define NPW_SU(bx, by, k) su[((by) * BX + (bx)) * M + (k)]
+    // E: item = (face, field); x face (qx, qy) has the eta stencil su[qy+3][qx+1 .. qx+4],
+    // y face (qx, qy) su[qy+1 .. qy+4][qx+3]
+    for (int it = tid; it < (NFX + NFY) * M; it += nthr) {
+        const int k = it % M, f = it / M;
+        float w0, w1, w2, w3;
+        if (f < NFX) {
+            const int qy = f / (TX_2D + 1), qx = f - qy * (TX_2D + 1);
+            w0 = NPW_SU(qx + 1, qy + 3, k);
+            w1 = NPW_SU(qx + 2, qy + 3, k);
+            w2 = NPW_SU(qx + 3, qy + 3, k);
+            w3 = NPW_SU(qx + 4, qy + 3, k);
+        } else {
+            const int g = f - NFX;
+            const int qy = g / TX_2D, qx = g - qy * TX_2D;
+            w0 = NPW_SU(qx + 3, qy + 1, k);
+            w1 = NPW_SU(qx + 3, qy + 2, k);
+            w2 = NPW_SU(qx + 3, qy + 3, k);
+            w3 = NPW_SU(qx + 3, qy + 4, k);
+        }
+        uint32_t fl = 0;
+        ef[it] = fast::face_eta(w0, w1, w2, w3, fp, &fl);
+    }
+    __syncthreads();
+    // C: item = (cell, field); x: cells cx = -1..TX of each row (TX + 2 per row), y: cells
+    // cy = -1..TY of each column.  Cell -1 only gives v^- at face 0, cell TX (TY) only v^+ at the
+    // last face.
+    constexpr int NCX = (TX_2D + 2) * TY_2D, NCY = TX_2D * (TY_2D + 2);
+    for (int it = tid; it < (NCX + NCY) * M; it += nthr) {
+        const int k = it % M, c = it / M;
+        float cc[5];
+        int fl_idx, fr_idx;  // faces left / right of the cell (-1 when outside the tile)
+        if (c < NCX) {
+            const int qy = c / (TX_2D + 2), cx = c - qy * (TX_2D + 2) - 1;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) cc[j] = NPW_SU(cx + 1 + j, qy + 3, k);
+            fl_idx = cx >= 0 ? qy * (TX_2D + 1) + cx : -1;
+            fr_idx = cx < TX_2D ? qy * (TX_2D + 1) + cx + 1 : -1;
+        } else {
+            const int g = c - NCX;
+            const int qx = g / (TY_2D + 2), cy = g - qx * (TY_2D + 2) - 1;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) cc[j] = NPW_SU(qx + 3, cy + 1 + j, k);
+            fl_idx = cy >= 0 ? NFX + cy * TX_2D + qx : -1;
+            fr_idx = cy < TY_2D ? NFX + (cy + 1) * TX_2D + qx : -1;
+        }
+        const float er = fr_idx >= 0 ? ef[fr_idx * M + k] : 0.0f;
+        const float el = fl_idx >= 0 ? ef[fl_idx * M + k] : 0.0f;
+        float vm, vp;
+        fast::cell_recon(cc, er, el, fp, &vm, &vp);
+        if (fr_idx >= 0) vmf[fr_idx * M + k] = vm;
+        if (fl_idx >= 0) vpf[fl_idx * M + k] = vp;
+    }
+    __syncthreads();
+    // F: item = face (all fields); the fluxes overwrite the eta array
+    for (int f = tid; f < NFX + NFY; f += nthr) {
+        float vm[M], vp[M], h[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            vm[k] = vmf[f * M + k];
+            vp[k] = vpf[f * M + k];
+        }
+        if (f < NFX)
+            lf_flux<float, KIND, M>(vm, vp, ax, a.mp, 0, h);
+        else
+            lf_flux<float, KIND, M>(vm, vp, ay, a.mp, 1, h);
+#pragma unroll
+        for (int k = 0; k < M; ++k) ef[f * M + k] = h[k];
+    }
+    __syncthreads();
+#undef NPW_SU
+    // U: one cell per thread (the same arithmetic as stage2d_kernel)
+    float* uout = reinterpret_cast<float*>(a.uout) + in.off;
+    const float* un = reinterpret_cast<const float*>(a.un) + in.off;
+    const float dtR = (float)dt, dxR = (float)in.dx, dyR = (float)in.dy;
+    double vmx = 0.0, vmy = 0.0;
+    bool bad = false;
+    for (int cidx = tid; cidx < TX_2D * TY_2D; cidx += nthr) {
+        const int qy = cidx / TX_2D, qx = cidx - qy * TX_2D;
+        const int64_t gi = tx0 + qx, gj = ty0 + qy;
+        if (gi >= nx || gj >= ny) continue;
+        float U[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const float* hx = ef;
+            const float* hy = ef + NFX * M;
+            float L = -((hx[(qy * (TX_2D + 1) + qx + 1) * M + k] - hx[(qy * (TX_2D + 1) + qx) * M + k]) / dxR);
+            L = L - (hy[((qy + 1) * TX_2D + qx) * M + k] - hy[(qy * TX_2D + qx) * M + k]) / dyR;
+            const float uk = su[((qy + 3) * BX + qx + 3) * M + k];
+            const int64_t gidx = k * cells + gj * nx + gi;
+            float o;
+            if (a.stage == 0) {
+                o = uk + dtR * L;
+            } else if (a.stage == 1) {
+                o = 0.75f * un[gidx] + 0.25f * (uk + dtR * L);
+            } else {
+                o = stage3_w1<float>() * un[gidx] + stage3_w2<float>() * (uk + dtR * L);
+            }
+            uout[gidx] = o;
+            U[k] = o;
+            bad |= !finite_(o);
+        }
+        if (a.stage == 2) {
+            const double sx = (double)wave_speed<float, KIND>(U, a.mp, 0);
+            const double sy = (double)wave_speed<float, KIND>(U, a.mp, 1);
+            bad |= !finite_(sx) || !finite_(sy);
+            vmx = sx > vmx ? sx : vmx;
+            vmy = sy > vmy ? sy : vmy;
+        }
+    }
+    if (a.stage == 2 && a.advance) {
+        const double bx = block_max_nan(vmx, bad, red, redbad);
+        const double by = block_max_nan(vmy, bad, red2, redbad2);
+        if (tid == 0) {
+            atomicMax(&ctl->alpha_next_bits, (unsigned long long)__double_as_longlong(bx));
+            atomicMax(&ctl->alpha_y_next_bits, (unsigned long long)__double_as_longlong(by));
+            __threadfence();
+            const unsigned prev = atomicAdd(&ctl->tiles_done, 1u);
+            if (prev == (unsigned)(in.tiles_x * in.tiles_y) - 1u) {
+                __threadfence();
+                finalize_2d(ctl, in);
+            }
+        }
+    }
+}
+
 template <typename R, typename D, int KIND>
 __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
     constexpr int M = kind_m<KIND>();
@@ -857,6 +1031,22 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) alpha_init_2d_kernel(const R* _
 // ---------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------
+// smooth data for the tile autotuner: m = 1: 1 + 0.5 sin(16 pi x); m = 3: a quiet Euler state
+// (rho = 1 + 0.2 sin(16 pi x), u = 0, p = 1, gamma = 1.4)
+template <typename R>
+__global__ void tune_init_kernel(R* u, int64_t n, int m) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = ((double)i + 0.5) / (double)n;
+    const double s = sin(16.0 * 3.141592653589793 * x);
+    if (m == 1) {
+        u[i] = R(1.0 + 0.5 * s);
+    } else {
+        u[i] = R(1.0 + 0.2 * s);
+        for (int k = 1; k < m; ++k) u[k * n + i] = R(k == m - 1 ? 2.5 : 0.0);
+    }
+}
+
 template <typename R, typename D>
 struct Launchers {
     static cudaError_t reconstruct(const R* u, int64_t n, int m, int bc, const MethodParams& mp, R* vm, R* vp,
@@ -986,6 +1176,24 @@ struct Launchers {
     }
 
     static cudaError_t stage2d(const Stage2DArgs& a, int tiles, int kind, cudaStream_t s) {
+        if constexpr (sizeof(R) == sizeof(float)) {
+            if (a.mp.k == 3) {
+                switch (kind) {
+                    case NPW_FLUX_ADVECTION:
+                        stage2d_fast_kernel<NPW_FLUX_ADVECTION_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                        break;
+                    case NPW_FLUX_BURGERS:
+                        stage2d_fast_kernel<NPW_FLUX_BURGERS_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                        break;
+                    case NPW_FLUX_EULER2D:
+                        stage2d_fast_kernel<NPW_FLUX_EULER2D_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                        break;
+                    default:
+                        return cudaErrorInvalidValue;
+                }
+                return cudaGetLastError();
+            }
+        }
         switch (kind) {
             case NPW_FLUX_ADVECTION:
                 stage2d_kernel<R, D, NPW_FLUX_ADVECTION_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);

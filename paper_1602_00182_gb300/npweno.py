@@ -28,7 +28,7 @@ class npw_params(C.Structure):
                 ("switch_variant", C.c_int32), ("characteristic", C.c_int32), ("precision", C.c_int32),
                 ("eta_eval", C.c_int32), ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
                 ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4),
-                ("eta_guard", C.c_double), ("batch_mode", C.c_int32), ("pad_", C.c_int32),
+                ("eta_guard", C.c_double), ("batch_mode", C.c_int32), ("tile_1d", C.c_int32),
                 ("eta_max", C.c_double)]
 
 
@@ -68,11 +68,12 @@ class Params:
     batch_mode: int = 0
     eta_max: float = 0.0
     k: int = 3
+    tile_1d: int = 0
 
     def c(self) -> npw_params:
         p = npw_params()
         for f in ("k", "scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "precision",
-                  "eta_eval", "batch_mode"):
+                  "eta_eval", "batch_mode", "tile_1d"):
             setattr(p, f, int(getattr(self, f)))
         for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "eta_guard", "eta_max"):
             setattr(p, f, float(getattr(self, f)))
@@ -116,8 +117,11 @@ def load():
                                     P(npw_solve_stats), vp]
     lib.npweno_rk3_step_noalloc.argtypes = [vp, i64, i32, d, d, i32, i32, P(npw_params), vp]
     lib.npw_noalloc_scratch_bytes.restype = sz
+    lib.npw_autotune_scratch_bytes.argtypes = [i32, P(npw_params)]
+    lib.npw_autotune_scratch_bytes.restype = sz
+    lib.npw_autotune_1d.argtypes = [i32, i32, P(npw_params), vp, sz, vp, P(i32)]
     for f in ("npweno_reconstruct", "npweno_flux", "npweno_rk3_step", "npweno_solve", "npweno_batch_solve",
-              "npweno_rk3_step_2d", "npweno_solve_2d", "npweno_rk3_step_noalloc"):
+              "npweno_rk3_step_2d", "npweno_solve_2d", "npweno_rk3_step_noalloc", "npw_autotune_1d"):
         getattr(lib, f).restype = i32
     _lib = lib
     return lib
@@ -268,6 +272,23 @@ def make_instances(ns: Sequence[int], dxs: Sequence[float], t_ends: Sequence[flo
 def npw_batch_workspace_size(instances, m: int, params: Params) -> int:
     p = params.c()
     return int(load().npw_batch_workspace_size(instances, len(instances), m, C.byref(p)))
+
+
+def npw_autotune_1d(flux_kind: int, m: int, params: Params, device=None) -> int:
+    """Time the 1D per-stage kernels with each tile size on a synthetic 2^21-cell instance
+    (scratch allocated here) and return the fastest; later runs with tile_1d = 0 use it."""
+    import torch
+    p = params.c()
+    lib = load()
+    nbytes = lib.npw_autotune_scratch_bytes(m, C.byref(p))
+    if nbytes == 0:
+        raise NpwError(NPW_EINVAL, "npw_autotune_scratch_bytes: bad arguments")
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    best = C.c_int32(0)
+    _check(lib.npw_autotune_1d(flux_kind, m, C.byref(p), C.c_void_p(scratch.data_ptr()), nbytes, _stream(),
+                               C.byref(best)))
+    return best.value
 
 
 def npweno_batch_solve(arena, instances, m: int, flux_kind: int, params: Params, workspace=None,

@@ -422,3 +422,37 @@ def test_mixed_precision_conserves_with_compensation(npw, mode):
         s1 = a[off:off + it.n].sum()
         assert abs(s1 - s0) <= 2e-7 * abs(s0) + 2.0 ** -24 * np.sqrt(it.n) * 4, (it.n, s["steps"], s1 - s0)
         off += it.n
+
+
+@pytest.mark.parametrize("switch", [0, 1])
+@pytest.mark.parametrize("kind", [O.ADVECTION, O.BURGERS, O.EULER2D])
+def test_2d_mixed_step_matches_oracle(npw, switch, kind):
+    """NPW_FP32_MIXED 2D (the phased tile kernel: eta per face, one reconstruction per cell and
+    direction): one RK3 step against the oracle from the same float data on a ragged grid (tiles
+    cut at both edges).  Without the switch the bar is float rounding (2e-6 relative); with it,
+    decisions of stages 2 and 3 taken on float stage values may differ at near ties (mean 1e-6,
+    max 3e-5 relative)."""
+    nx, ny = 70, 45
+    if kind == O.EULER2D:
+        nx = ny = 70  # the whole periodic vortex (a cropped one would have a jump at the wrap)
+        U, d = I.isentropic_vortex(nx, 4.0, 5.0, 5.0, npts=2)
+    else:
+        g = np.random.default_rng(kind)
+        x = (np.arange(nx) + 0.5) / nx
+        y = (np.arange(ny) + 0.5) / ny
+        U = (1.0 + 0.5 * np.sin(2 * np.pi * x)[None, :] * np.cos(2 * np.pi * y)[:, None])[None]
+        U[0, ny // 3:, nx // 2:] += 0.3 * g.uniform()
+        d = 1.0 / nx
+    U = U.astype(np.float32).astype(np.float64)
+    op = O.Params(monotone_switch=switch, eta_guard=MIXED_GUARD, adv_speed=1.0, adv_speed_y=0.5)
+    dt = 0.2 * d
+    ref = O.rk3_step_2d(U, d, d, dt, kind, O.PERIODIC, op)
+    gu = _dev(U, torch.float32)
+    npw.npweno_rk3_step_2d(gu, d, d, dt, kind, O.PERIODIC, _gparams(npw, op, precision=1))
+    got = gu.cpu().numpy().astype(np.float64)
+    scale = np.abs(ref).max()
+    e = np.abs(got - ref)
+    if not switch:
+        assert e.max() <= 2e-6 * scale, e.max() / scale
+    else:
+        assert e.mean() <= 1e-6 * scale and e.max() <= 3e-5 * scale, (e.mean() / scale, e.max() / scale)

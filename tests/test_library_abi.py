@@ -46,6 +46,11 @@ def test_default_params_and_errors_without_gpu():
     st = lib.npweno_reconstruct(ctypes.c_void_p(16), 100, 1, 0, ctypes.byref(bad), ctypes.c_void_p(16),
                                 ctypes.c_void_p(16), None, None)
     assert st == npw.NPW_EINVAL and b"k must be 2" in lib.npw_last_error()
+    badtile = npw.Params(tile_1d=300).c()
+    st = lib.npweno_reconstruct(ctypes.c_void_p(16), 100, 1, 0, ctypes.byref(badtile), ctypes.c_void_p(16),
+                                ctypes.c_void_p(16), None, None)
+    assert st == npw.NPW_EINVAL and b"tile_1d" in lib.npw_last_error()
+    assert lib.npw_autotune_scratch_bytes(1, ctypes.byref(npw.Params(precision=1).c())) > (1 << 21) * 4
     good = npw.Params().c()
     st = lib.npweno_reconstruct(ctypes.c_void_p(16), 5, 1, 0, ctypes.byref(good), ctypes.c_void_p(16),
                                 ctypes.c_void_p(16), None, None)
