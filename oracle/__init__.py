@@ -39,7 +39,7 @@ SCHEMES = {"eno": ENO, "weno_js": WENO_JS, "rbf_eno": RBF_ENO, "rbf_weno": RBF_W
 class _Params(C.Structure):
     _fields_ = [
         ("scheme", C.c_int), ("rbf", C.c_int), ("monotone_switch", C.c_int), ("switch_variant", C.c_int),
-        ("characteristic", C.c_int), ("k", C.c_int),
+        ("characteristic", C.c_int), ("k", C.c_int), ("cross_2d", C.c_int), ("pad2_", C.c_int),
         ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
         ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4),
         ("tie_tol", C.c_double), ("eta_guard", C.c_double), ("eta_max", C.c_double),
@@ -60,6 +60,7 @@ class Params:
     switch_variant: int = 0
     characteristic: int = 0
     k: int = 3
+    cross_2d: int = 0
     eps_M: float = 1e-12
     eps_weno: float = 1e-6
     gamma: float = 1.4
@@ -72,7 +73,7 @@ class Params:
 
     def _c(self) -> _Params:
         p = _Params()
-        for f in ("scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "k"):
+        for f in ("scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "k", "cross_2d"):
             setattr(p, f, int(getattr(self, f)))
         for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "tie_tol", "eta_guard", "eta_max"):
             setattr(p, f, float(getattr(self, f)))
@@ -109,6 +110,9 @@ def lib():
         _lib.orc_switch_k2.argtypes = [P(d), d, P(i)]
         _lib.orc_eta_k2.restype = d
         _lib.orc_eta_k2.argtypes = [P(d), i, P(_Params)]
+        _lib.orc_eta_k2_cross.restype = d
+        _lib.orc_eta_k2_cross.argtypes = [P(d), i, i, d, P(_Params)]
+        _lib.orc_reconstruct_2d.argtypes = [P(d), l, l, i, i, P(_Params), P(d), P(d), P(d), P(d)]
         _lib.orc_eno_choice.argtypes = [P(d), d, P(i)]
         _lib.orc_beta_k3.argtypes = [P(d), P(d)]
         _lib.orc_euler_eigvec.argtypes = [P(d), P(d), d, P(d), P(d)]
@@ -171,6 +175,33 @@ def eta_k2(c3, side: int, params: "Params") -> float:
     c = _f64(c3)
     p = params._c()
     return lib().orc_eta_k2(_dp(c), side, C.byref(p))
+
+
+def eta_k2_cross(c3, side: int, central: bool, trans: float, params: "Params") -> float:
+    """k = 2 shape parameter on the 5-cell cross (Sec. 6): c3 = cells along the face normal,
+    trans = transverse second difference of the cell, central: the stencil of the two cells at
+    the face."""
+    c = _f64(c3)
+    p = params._c()
+    return lib().orc_eta_k2_cross(_dp(c), side, int(central), float(trans), C.byref(p))
+
+
+def reconstruct_2d(u, bc: int, params: "Params"):
+    """Face values of u [m][ny][nx] (or [ny][nx]): (vmx, vpx) [m][ny][nx+1] at the x faces and
+    (vmy, vpy) [m][ny+1][nx] at the y faces."""
+    u = _f64(u)
+    squeeze = u.ndim == 2
+    if squeeze:
+        u = u[None]
+    m, ny, nx = u.shape
+    vmx, vpx = np.zeros((m, ny, nx + 1)), np.zeros((m, ny, nx + 1))
+    vmy, vpy = np.zeros((m, ny + 1, nx)), np.zeros((m, ny + 1, nx))
+    p = params._c()
+    _check(lib().orc_reconstruct_2d(_dp(u), nx, ny, m, bc, C.byref(p), _dp(vmx), _dp(vpx), _dp(vmy), _dp(vpy)),
+           "reconstruct_2d")
+    if squeeze:
+        return vmx[0], vpx[0], vmy[0], vpy[0]
+    return vmx, vpx, vmy, vpy
 
 
 def switch_k3(w4, variant: int = 0, tol: float = 0.0):

@@ -31,6 +31,9 @@
  *   Sec. 5.1 semi-discrete update (eq. PDE1), Lax-Friedrichs flux with a constant alpha,
  *            TVD Runge-Kutta 3.
  *   Sec. 5.2 Example 4: Euler equations, gamma = 1.4.
+ *   Sec. 6   2D perturbed reconstruction for k = 2 at a face midpoint (eq. rbf_recon_2d,
+ *            eq. i+1/2_eps_2d, eq. i+1/2_eps_approx_2d): the shape parameter also cancels the
+ *            transverse term v_yy dy^2 / 24 of the cell averages, using the 5-cell cross.
  *   Sec. 7   2D finite volume form (eq. 2DIntegral) with one midpoint quadrature point
  *            per cell boundary, applied dimension by dimension.
  */
@@ -309,12 +312,14 @@ static double cell_face_value(const double c[5], int side, double eta, const orc
 /* Writes v^- (from cell i), v^+ (from cell i+1), the flag byte and eta.                  */
 /* ------------------------------------------------------------------------------------ */
 static void face_field_k2(const double w[6], const orc_params* p, const uint8_t* replay, double* vm, double* vp,
-                          uint8_t* flag, double* eta_out);
+                          uint8_t* flag, double* eta_out, double tl, double tr);
 
+/* tl, tr: transverse second differences of the two cells of the face (used by k = 2 with the
+ * 5-cell cross of Sec. 6; 0 on a line) */
 static void face_field(const double w[6], const orc_params* p, const uint8_t* replay, double* vm, double* vp,
-                       uint8_t* flag, double* eta_out) {
+                       uint8_t* flag, double* eta_out, double tl, double tr) {
     if (p->k == 2) {
-        face_field_k2(w, p, replay, vm, vp, flag, eta_out);
+        face_field_k2(w, p, replay, vm, vp, flag, eta_out, tl, tr);
         return;
     }
     uint8_t fl = 0;
@@ -378,11 +383,20 @@ int orc_switch_k2(const double c[3], double tol, int* near_tie) {
  * estimates v and v'' at x_{i+1/2} from the cells i-1, i, i+1; side 1: eta of v^+_{i-1/2},
  * the mirror image (the same cells read from the right).  Applies the optional guard and
  * bound of the k = 3 path, with the magnitudes of the denominator's terms. */
-double orc_eta_k2(const double c[3], int side, const orc_params* p) {
+/* Sec. 6 (k = 2, 2D): at a face midpoint the polynomial row of the stencil has the error
+ * e v_xx dx^2 + v_yy dy^2 / 24 (e = 1/6 for the stencil of the two cells at the face, -1/3 for
+ * the extrapolating one) and the perturbation adds (sum of its q) eta v.  With the second
+ * differences a2 (along the face normal) and trans (across it) for v_xx dx^2 and v_yy dy^2, and
+ * the face value v from the cells far, centre, across (eq. i+1/2_eps_approx), the cancelling
+ * eta is F (-a2 + t trans) / (-far + 5 centre + 2 across + eps_M): F = 2 (MQ), 1 (Gaussian),
+ * t = -1/4 for the central stencil and 1/8 for the extrapolating one.  With trans = 0 this is
+ * the line formula of Table k2.  (The printed denominator of eq. i+1/2_eps_approx_2d lists the
+ * coefficients -2, 1, -5, a permutation of the 1, -5, -2 that the derivation gives.) */
+double orc_eta_k2_cross(const double c[3], int side, int central, double trans, const orc_params* p) {
     double a = (side == 0) ? c[0] : c[2]; /* far cell behind the face's cell */
     double b = c[1];
     double d = (side == 0) ? c[2] : c[0]; /* cell across the face */
-    double num = -a + 2.0 * b - d;
+    double num = -a + 2.0 * b - d + (central ? -0.25 : 0.125) * trans;
     double den0 = -a + 5.0 * b + 2.0 * d;
     double mag = fabs(a) + 5.0 * fabs(b) + 2.0 * fabs(d);
     if (p->eta_guard > 0.0 && fabs(den0) <= p->eta_guard * mag) return 0.0;
@@ -391,15 +405,20 @@ double orc_eta_k2(const double c[3], int side, const orc_params* p) {
     return eta;
 }
 
+double orc_eta_k2(const double c[3], int side, const orc_params* p) { return orc_eta_k2_cross(c, side, 1, 0.0, p); }
+
 /* Value of cell i at its right face (side 0: v^-_{i+1/2}, rows r) or left face (side 1:   */
 /* v^+_{i-1/2}, rows r - 1), k = 2.  c[0..2] = cells i-1, i, i+1; stencil r uses cells     */
 /* i-r, i-r+1.                                                                             */
-static double cell_face_value_k2(const double c[3], int side, double eta, const orc_params* p, int forced_r,
-                                 int* r_out, int* near_out) {
+/* eta_c: shape parameter of the stencil of the two cells at the face (row 0), eta_x: of the   */
+/* extrapolating stencil (rows -1, 1); equal except on the 5-cell cross of Sec. 6.              */
+static double cell_face_value_k2(const double c[3], int side, double eta_c, double eta_x, const orc_params* p,
+                                 int forced_r, int* r_out, int* near_out) {
     const double(*q)[2] = (p->rbf == ORC_RBF_GA) ? PERT2_GA : PERT2_MQ;
     double cand[2];
     for (int r = 0; r < 2; ++r) {
         int row = (side == 0) ? r : r - 1;
+        double eta = (row == 0) ? eta_c : eta_x;
         double s = 0.0;
         for (int j = 0; j < 2; ++j) s += (POLY2[row + 1][j] + q[row + 1][j] * eta) * c[1 - r + j];
         cand[r] = s;
@@ -434,9 +453,9 @@ static double cell_face_value_k2(const double c[3], int side, double eta, const 
  * cell i (stencil w[1..3]) with that cell's side-0 eta, v^+ from cell i+1 (stencil w[2..4])
  * with its side-1 eta.  eta_out receives the eta of v^-. */
 static void face_field_k2(const double w[6], const orc_params* p, const uint8_t* replay, double* vm, double* vp,
-                          uint8_t* flag, double* eta_out) {
+                          uint8_t* flag, double* eta_out, double tl, double tr) {
     uint8_t fl = 0;
-    double eta_l = 0.0, eta_r = 0.0;
+    double eta_l = 0.0, eta_r = 0.0, eta_lx = 0.0, eta_rx = 0.0;
     if (p->scheme == ORC_RBF_ENO || p->scheme == ORC_RBF_WENO) {
         int near_l = 0, near_r = 0, fires_l = 0, fires_r = 0;
         if (p->monotone_switch) {
@@ -447,10 +466,18 @@ static void face_field_k2(const double w[6], const orc_params* p, const uint8_t*
                 fires_r = (*replay & ORC_FLAG_SWITCH_R_K2) ? 1 : 0;
             }
         }
-        if (fires_l) fl |= ORC_FLAG_SWITCH;
-        else eta_l = orc_eta_k2(&w[1], 0, p);
-        if (fires_r) fl |= ORC_FLAG_SWITCH_R_K2;
-        else eta_r = orc_eta_k2(&w[2], 1, p);
+        if (fires_l) {
+            fl |= ORC_FLAG_SWITCH;
+        } else {
+            eta_l = orc_eta_k2_cross(&w[1], 0, 1, tl, p);
+            eta_lx = orc_eta_k2_cross(&w[1], 0, 0, tl, p);
+        }
+        if (fires_r) {
+            fl |= ORC_FLAG_SWITCH_R_K2;
+        } else {
+            eta_r = orc_eta_k2_cross(&w[2], 1, 1, tr, p);
+            eta_rx = orc_eta_k2_cross(&w[2], 1, 0, tr, p);
+        }
         if (near_l || near_r) fl |= ORC_FLAG_SWITCH_TIE;
     }
     int rl = 0, rr = 0, nl = 0, nr = 0, fl_r = -1, fr_r = -1;
@@ -458,8 +485,8 @@ static void face_field_k2(const double w[6], const orc_params* p, const uint8_t*
         fl_r = (*replay >> 2) & 1;
         fr_r = (*replay >> 4) & 1;
     }
-    *vm = cell_face_value_k2(&w[1], 0, eta_l, p, fl_r, &rl, &nl);
-    *vp = cell_face_value_k2(&w[2], 1, eta_r, p, fr_r, &rr, &nr);
+    *vm = cell_face_value_k2(&w[1], 0, eta_l, eta_lx, p, fl_r, &rl, &nl);
+    *vp = cell_face_value_k2(&w[2], 1, eta_r, eta_rx, p, fr_r, &rr, &nr);
     fl |= (uint8_t)((rl & 1) << 2) | (uint8_t)((rr & 1) << 4);
     if (nl) fl |= ORC_FLAG_ENO_TIE_L;
     if (nr) fl |= ORC_FLAG_ENO_TIE_R;
@@ -530,8 +557,10 @@ int orc_euler_eigvec(const double UL[3], const double UR[3], double gamma, doubl
 /* field k of cell i.  Face f (f = 0..n) separates cell f-1 and cell f.  Outputs          */
 /* vm/vp/flags/eta are [m][n+1].                                                           */
 /* ------------------------------------------------------------------------------------ */
+/* trans: [m][n] transverse second differences of the cells of the line (NULL: none). */
 static int recon_line(const double* u, long n, int m, long stride, long m_stride, int bc, const orc_params* p,
-                      double* vm, double* vp, uint8_t* flags, double* eta, const uint8_t* replay, long out_stride) {
+                      double* vm, double* vp, uint8_t* flags, double* eta, const uint8_t* replay, long out_stride,
+                      const double* trans) {
     for (long f = 0; f <= n; ++f) {
         if (p->characteristic && m == 3) {
             double U[6][3], W[6][3], R[3][3], L[3][3];
@@ -552,7 +581,7 @@ static int recon_line(const double* u, long n, int m, long stride, long m_stride
                 uint8_t fl;
                 double et;
                 const uint8_t* rp = replay ? &replay[a * out_stride + f] : NULL;
-                face_field(line, p, rp, &wm[a], &wp[a], &fl, &et);
+                face_field(line, p, rp, &wm[a], &wp[a], &fl, &et, 0.0, 0.0);
                 if (flags) flags[a * out_stride + f] = fl;
                 if (eta) eta[a * out_stride + f] = et;
             }
@@ -572,7 +601,12 @@ static int recon_line(const double* u, long n, int m, long stride, long m_stride
                 uint8_t fl;
                 double et;
                 const uint8_t* rp = replay ? &replay[k * out_stride + f] : NULL;
-                face_field(line, p, rp, &vm[k * out_stride + f], &vp[k * out_stride + f], &fl, &et);
+                double tl = 0.0, tr = 0.0;
+                if (trans) {
+                    tl = line_get(trans + k * n, n, 1, f - 1, bc, 0.0);
+                    tr = line_get(trans + k * n, n, 1, f, bc, 0.0);
+                }
+                face_field(line, p, rp, &vm[k * out_stride + f], &vp[k * out_stride + f], &fl, &et, tl, tr);
                 if (flags) flags[k * out_stride + f] = fl;
                 if (eta) eta[k * out_stride + f] = et;
             }
@@ -593,7 +627,7 @@ int orc_reconstruct(const double* u, long n, int m, int bc, const orc_params* p,
                     uint8_t* flags, double* eta, const uint8_t* replay) {
     int st = check_params(n, m, p);
     if (st) return st;
-    return recon_line(u, n, m, 1, n, bc, p, vm, vp, flags, eta, replay, n + 1);
+    return recon_line(u, n, m, 1, n, bc, p, vm, vp, flags, eta, replay, n + 1, NULL);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -694,7 +728,7 @@ static int rhs_1d(const double* u, long n, int m, double dx, int kind, int bc, d
     double* vp = malloc(sizeof(double) * m * nf);
     double* h = malloc(sizeof(double) * m * nf);
     int st = (vm && vp && h) ? ORC_OK : ORC_ENOMEM;
-    if (!st) st = recon_line(u, n, m, 1, n, bc, p, vm, vp, NULL, NULL, NULL, nf);
+    if (!st) st = recon_line(u, n, m, 1, n, bc, p, vm, vp, NULL, NULL, NULL, nf, NULL);
     if (!st) st = orc_flux(vm, vp, nf, m, kind, 0, alpha, p, h);
     if (!st)
         for (int k = 0; k < m; ++k)
@@ -705,8 +739,72 @@ static int rhs_1d(const double* u, long n, int m, double dx, int kind, int bc, d
     return st;
 }
 
+/* Transverse second differences of the cells of one grid line (Sec. 6, k = 2 on the cross):  */
+/* dir 0: row j, out[k*nx + i] = u(i, j-1) - 2 u(i, j) + u(i, j+1); dir 1: column i,             */
+/* out[k*ny + j] = u(i-1, j) - 2 u(i, j) + u(i+1, j).  Neighbours follow the boundary condition. */
+static void transverse_line(const double* u, long nx, long ny, int m, int bc, const orc_params* p, int dir, long line,
+                            double* out) {
+    long cells = nx * ny;
+    for (int k = 0; k < m; ++k) {
+        const double* uk = u + k * cells;
+        if (dir == 0) {
+            for (long i = 0; i < nx; ++i) {
+                double dn = line_get(uk + i, ny, nx, line - 1, bc, p->inflow[k]);
+                double up = line_get(uk + i, ny, nx, line + 1, bc, p->inflow[k]);
+                out[k * nx + i] = dn - 2.0 * uk[line * nx + i] + up;
+            }
+        } else {
+            for (long j = 0; j < ny; ++j) {
+                double lf = line_get(uk + j * nx, nx, 1, line - 1, bc, p->inflow[k]);
+                double rt = line_get(uk + j * nx, nx, 1, line + 1, bc, p->inflow[k]);
+                out[k * ny + j] = lf - 2.0 * uk[j * nx + line] + rt;
+            }
+        }
+    }
+}
+
+static int use_cross(const orc_params* p) {
+    return p->cross_2d && p->k == 2 && (p->scheme == ORC_RBF_ENO || p->scheme == ORC_RBF_WENO);
+}
+
+/* Face values of the 2D grid: x faces vmx/vpx [m][ny][nx+1] (face i of row j between cells
+ * i-1 and i), y faces vmy/vpy [m][ny+1][nx] (face j of column i between rows j-1 and j). */
+int orc_reconstruct_2d(const double* u, long nx, long ny, int m, int bc, const orc_params* p, double* vmx, double* vpx,
+                       double* vmy, double* vpy) {
+    int st = check_params(nx, m, p);
+    if (st || ny < 6 || p->characteristic) return ORC_EINVAL;
+    long cells = nx * ny, nmax = (nx > ny) ? nx : ny;
+    double* vm = malloc(sizeof(double) * m * (nmax + 1));
+    double* vp = malloc(sizeof(double) * m * (nmax + 1));
+    double* tr = malloc(sizeof(double) * m * nmax);
+    st = (vm && vp && tr) ? ORC_OK : ORC_ENOMEM;
+    for (long j = 0; j < ny && !st; ++j) {
+        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, p, 0, j, tr);
+        st = recon_line(u + j * nx, nx, m, 1, cells, bc, p, vm, vp, NULL, NULL, NULL, nx + 1, use_cross(p) ? tr : NULL);
+        for (int k = 0; k < m && !st; ++k)
+            for (long i = 0; i <= nx; ++i) {
+                vmx[(k * ny + j) * (nx + 1) + i] = vm[k * (nx + 1) + i];
+                vpx[(k * ny + j) * (nx + 1) + i] = vp[k * (nx + 1) + i];
+            }
+    }
+    for (long i = 0; i < nx && !st; ++i) {
+        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, p, 1, i, tr);
+        st = recon_line(u + i, ny, m, nx, cells, bc, p, vm, vp, NULL, NULL, NULL, ny + 1, use_cross(p) ? tr : NULL);
+        for (int k = 0; k < m && !st; ++k)
+            for (long j = 0; j <= ny; ++j) {
+                vmy[(k * (ny + 1) + j) * nx + i] = vm[k * (ny + 1) + j];
+                vpy[(k * (ny + 1) + j) * nx + i] = vp[k * (ny + 1) + j];
+            }
+    }
+    free(vm);
+    free(vp);
+    free(tr);
+    return st;
+}
+
 /* 2D: eq. 2DIntegral with one midpoint point per face, the x and y sweeps each a 1D       */
-/* reconstruction along a grid line.  u is [m][ny][nx].                                    */
+/* reconstruction along a grid line (k = 2 with cross_2d: the shape parameter of Sec. 6).   */
+/* u is [m][ny][nx].                                                                         */
 static int rhs_2d(const double* u, long nx, long ny, int m, double dx, double dy, int kind, int bc, double ax,
                   double ay, const orc_params* p, double* L) {
     long cells = nx * ny;
@@ -714,18 +812,21 @@ static int rhs_2d(const double* u, long nx, long ny, int m, double dx, double dy
     double* vm = malloc(sizeof(double) * m * (nmax + 1));
     double* vp = malloc(sizeof(double) * m * (nmax + 1));
     double* h = malloc(sizeof(double) * m * (nmax + 1));
-    int st = (vm && vp && h) ? ORC_OK : ORC_ENOMEM;
+    double* tr = malloc(sizeof(double) * m * nmax);
+    int st = (vm && vp && h && tr) ? ORC_OK : ORC_ENOMEM;
     for (long i = 0; i < m * cells && !st; ++i) L[i] = 0.0;
     /* x sweeps: row j */
     for (long j = 0; j < ny && !st; ++j) {
-        st = recon_line(u + j * nx, nx, m, 1, cells, bc, p, vm, vp, NULL, NULL, NULL, nx + 1);
+        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, p, 0, j, tr);
+        st = recon_line(u + j * nx, nx, m, 1, cells, bc, p, vm, vp, NULL, NULL, NULL, nx + 1, use_cross(p) ? tr : NULL);
         if (!st) st = orc_flux(vm, vp, nx + 1, m, kind, 0, ax, p, h);
         for (int k = 0; k < m && !st; ++k)
             for (long i = 0; i < nx; ++i) L[k * cells + j * nx + i] -= (h[k * (nx + 1) + i + 1] - h[k * (nx + 1) + i]) / dx;
     }
     /* y sweeps: column i */
     for (long i = 0; i < nx && !st; ++i) {
-        st = recon_line(u + i, ny, m, nx, cells, bc, p, vm, vp, NULL, NULL, NULL, ny + 1);
+        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, p, 1, i, tr);
+        st = recon_line(u + i, ny, m, nx, cells, bc, p, vm, vp, NULL, NULL, NULL, ny + 1, use_cross(p) ? tr : NULL);
         if (!st) st = orc_flux(vm, vp, ny + 1, m, kind, 1, ay, p, h);
         for (int k = 0; k < m && !st; ++k)
             for (long j = 0; j < ny; ++j) L[k * cells + j * nx + i] -= (h[k * (ny + 1) + j + 1] - h[k * (ny + 1) + j]) / dy;
@@ -733,6 +834,7 @@ static int rhs_2d(const double* u, long nx, long ny, int m, double dx, double dy
     free(vm);
     free(vp);
     free(h);
+    free(tr);
     return st;
 }
 

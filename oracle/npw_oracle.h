@@ -33,6 +33,8 @@ typedef struct {
     int switch_variant;  /* 0: cubic on the 4-cell eta stencil; 1: k=2 ratio test on both 3-cell halves */
     int characteristic;  /* 1D Euler: reconstruct characteristic fields */
     int k;               /* order parameter of the ENO stencils: 2 or 3 (0 means 3) */
+    int cross_2d;        /* 2D, k = 2: shape parameter of Sec. 6 on the 5-cell cross (1) or of the line (0) */
+    int pad2_;
     double eps_M;     /* additive guard of the eta denominator */
     double eps_weno;  /* WENO epsilon (1e-6) */
     double gamma;     /* ratio of specific heats */
@@ -56,6 +58,9 @@ double orc_table_coef(int rbf, int r, int j, double eta);
 int orc_switch_k3(const double w[4], int variant, double tol, int* near_tie);
 int orc_switch_k2(const double c[3], double tol, int* near_tie);
 double orc_eta_k2(const double c[3], int side, const orc_params* p);
+double orc_eta_k2_cross(const double c[3], int side, int central, double trans, const orc_params* p);
+int orc_reconstruct_2d(const double* u, long nx, long ny, int m, int bc, const orc_params* p, double* vmx, double* vpx,
+                       double* vmy, double* vpy);
 double orc_table_coef_k2(int rbf, int r, int j, double eta);
 int orc_eno_choice(const double c[5], double tol, int* near_tie);
 void orc_beta_k3(const double c[5], double beta[3]);

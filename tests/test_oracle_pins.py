@@ -365,3 +365,56 @@ def test_k2_bruteforce_tiny_grid(scheme, rbf, switch):
             assert vp[f] == pytest.approx(float(vpx[f]), rel=1e-11, abs=1e-11), (trial, f)
             checked += 1
     assert checked > 20
+
+
+# --------------------------------------------------------------------------------------- 2D cross
+def _avg_sin2d(n, shift=0.0):
+    """Exact cell averages of sin(2 pi (x + y - shift)) on n x n cells of [0, 1]^2."""
+    e = np.linspace(0.0, 1.0, n + 1)
+
+    def F(x, y):  # d2F/dxdy = sin(2 pi (x + y - shift))
+        return -np.sin(2 * np.pi * (x + y - shift)) / (4 * np.pi ** 2)
+    X0, X1 = e[:-1][None, :], e[1:][None, :]
+    Y0, Y1 = e[:-1][:, None], e[1:][:, None]
+    return (F(X1, Y1) - F(X0, Y1) - F(X1, Y0) + F(X0, Y0)) * n * n, e
+
+
+@pytest.mark.parametrize("scheme", [O.RBF_ENO, O.RBF_WENO])
+@pytest.mark.parametrize("rbf", [O.MQ, O.GA])
+def test_cross_2d_face_values_are_third_order(scheme, rbf):
+    """Sec. 6: with the shape parameter on the 5-cell cross, the k = 2 face values at the x-face
+    midpoints of sin(2 pi (x + y)) converge at order 3 (the paper's reconstruction test); the
+    line form, whose eta ignores the transverse term v_yy dy^2 / 24 of the cell averages, stays
+    at order 2, as does ENO2.  A wrong transverse coefficient or a wrong denominator drops the
+    cross form to order 2."""
+    def errs(cross, sch):
+        out = []
+        for n in (40, 80, 160, 320):
+            U, e = _avg_sin2d(n)
+            vmx, vpx, vmy, vpy = O.reconstruct_2d(U, O.PERIODIC,
+                                                 O.Params(k=2, scheme=sch, rbf=rbf, monotone_switch=0, cross_2d=cross))
+            c = (e[:-1] + e[1:]) / 2
+            ex_x = np.sin(2 * np.pi * (e[None, :] + c[:, None]))
+            ex_y = np.sin(2 * np.pi * (c[None, :] + e[:, None]))
+            out.append(max(np.abs(vmx - ex_x).max(), np.abs(vpx - ex_x).max(),
+                           np.abs(vmy - ex_y).max(), np.abs(vpy - ex_y).max()))
+        return np.log2(np.array(out[:-1]) / np.array(out[1:]))
+    assert np.all(errs(1, scheme) > 2.9)
+    assert np.all(np.abs(errs(0, scheme) - 2.0) < 0.3)
+    assert np.all(np.abs(errs(1, O.ENO) - 2.0) < 0.1)
+
+
+def test_cross_2d_reduces_to_line_without_transverse_variation():
+    """On data constant along y the transverse second differences of the x faces vanish, and the
+    cross form of Sec. 6 gives exactly the line values of Table k2 there.  (Its y faces do
+    change: a cell average differs from the value at a y-face midpoint by the x curvature.)"""
+    g = np.random.default_rng(23)
+    row = g.uniform(0.5, 1.5, size=37)
+    U = np.tile(row, (12, 1))
+    for sch in (O.RBF_ENO, O.RBF_WENO):
+        a = O.reconstruct_2d(U, O.PERIODIC, O.Params(k=2, scheme=sch, cross_2d=1))
+        b = O.reconstruct_2d(U, O.PERIODIC, O.Params(k=2, scheme=sch, cross_2d=0))
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert not np.array_equal(a[2], b[2])
+        vm, vp, _, _ = O.reconstruct(row, O.PERIODIC, O.Params(k=2, scheme=sch))
+        assert np.array_equal(a[0][5], vm) and np.array_equal(a[1][5], vp)
