@@ -223,8 +223,8 @@ def run_gpu(args, rank, world, local_rank):
     e2e_value = e2e_units / (e2e_ms / 1e3)
 
     variants = {}
-    if args.variant_steps > 0 and args.eta_eval == 0 and world == 1:
-        pv = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, eta_eval=1)
+
+    def time_variant(pv, label):
         arena.copy_(pristine)
         npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, pv, workspace=ws)
         vt = []
@@ -240,8 +240,14 @@ def run_gpu(args, rank, world, local_rank):
             torch.cuda.synchronize()
             vt.append(e0.elapsed_time(e1))
         vcu = sum(n * s["steps"] for n, s in zip(ns, vstats))
-        variants["eta_eval=1 (exact double-float eta, no FP64 instruction)"] = {
-            "value": vcu * len(vt) / (sum(vt) / 1e3), "unit": "cell-updates/s", "ms_per_step": sum(vt) / len(vt)}
+        variants[label] = {"value": vcu * len(vt) / (sum(vt) / 1e3), "unit": "cell-updates/s",
+                           "ms_per_step": sum(vt) / len(vt)}
+
+    if args.variant_steps > 0 and args.eta_eval == 0 and world == 1:
+        time_variant(npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, eta_eval=1),
+                     "eta_eval=1 (exact double-float eta, no FP64 instruction)")
+        time_variant(npw.Params(k=2, rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED),
+                     "k=2 RBF-WENO3 Gaussian + switch (Table k2; face-based per-stage kernels, eta in FP64)")
 
     out = {
         "metric": "cell-updates/s",
@@ -547,7 +553,7 @@ def run_euler2d(args, rank, world, local_rank):
     n = args.n2d
     count = max(1, (1 << 24) // (n * n))
     doms = I.euler2d_batch(n, count, seed_index=rank_seed(3, rank))
-    p = npw.Params(precision=npw.NPW_FP32_MIXED)
+    p = npw.Params(precision=npw.NPW_FP32_MIXED, k=args.k, cross_2d=args.cross_2d)
     pristine = [torch.tensor(U.astype(np.float32), device="cuda") for U, d in doms]
     work = [x.clone() for x in pristine]
     ws = torch.empty(npw.npw_workspace_size_2d(n, n, 4, p), dtype=torch.uint8, device="cuda")
@@ -579,19 +585,22 @@ def run_euler2d(args, rank, world, local_rank):
     lib.npw_profile_enable(0)
     cu = holder["cu"]
     st_s = pr.stage_ms / 1e3
-    fp64 = FP64_OPS_PER_ETA * cu * args.steps * 3 * 4 * 2 / st_s / 1e9 if st_s > 0 else None
+    # FP64-pipe view for k = 3 only (k = 2 evaluates two literal FP64 quotients per face)
+    fp64 = FP64_OPS_PER_ETA * cu * args.steps * 3 * 4 * 2 / st_s / 1e9 if (st_s > 0 and args.k == 3) else None
     tmax, cu_all = job_totals(sum(times), cu * args.steps, world, torch.device("cuda", local_rank))
     return {
         "metric": "cell-updates/s", "value": cu_all / (tmax / 1e3), "unit": "cell-updates/s",
         "ms_per_step": tmax / len(times),
         "config": {"workload": (f"2D Euler dimension by dimension, periodic {n}^2 x {count} (isentropic vortex + "
-                                "four-quadrant), RBF-WENO5 MQ + switch, one midpoint point per face, ~"
-                                f"{args.steps2d} RK3 steps at CFL 0.5"),
+                                "four-quadrant), "
+                                + ("RBF-WENO5 MQ" if args.k == 3 else
+                                   "RBF-WENO3 MQ" + (" with the Sec. 6 cross shape parameter" if args.cross_2d else ""))
+                                + f" + switch, one midpoint point per face, ~{args.steps2d} RK3 steps at CFL 0.5"),
                    "domains": count, "cells": n * n * count, "cell_updates_per_step": int(cu),
                    "l2": "flushed before every timed step"},
         "roofline": {"bound": "alu", "achieved": fp64, "peak": FP64_PIPE_PEAK / 1e9, "unit": "G FP64-pipe instr/s",
                      "frac": (fp64 / (FP64_PIPE_PEAK / 1e9)) if fp64 else None, "traffic": None,
-                     "kernel": "stage2d_fast_kernel<EULER2D>",
+                     "kernel": "stage2d_fast_kernel<EULER2D>" if args.k == 3 else "stage2d_kernel<float,double,EULER2D>",
                      "hbm_view": {"achieved_gbs": cu * args.steps * 128 / st_s / 1e9 if st_s > 0 else None,
                                   "peak_gbs": _peaks()[0], "bytes_per_cell_update": 128},
                      "stage_launches": int(pr.stage_launches), "stage_ms": pr.stage_ms},
@@ -613,6 +622,9 @@ def main():
     ap.add_argument("--characteristic", type=int, default=0, help="euler1d: characteristic-wise reconstruction")
     ap.add_argument("--n2d", type=int, default=2048, help="euler2d: square size")
     ap.add_argument("--steps2d", type=int, default=100, help="euler2d: RK3 steps per solve")
+    ap.add_argument("--k", type=int, default=3, choices=[2, 3], help="euler2d: ENO order parameter (Table k3 / k2)")
+    ap.add_argument("--cross-2d", type=int, default=0, choices=[0, 1],
+                    help="euler2d with --k 2: shape parameter on the 5-cell cross (Sec. 6)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eta-eval", type=int, default=0, choices=[0, 1],
                     help="0: eta in FP64 (the configuration's FP64 shape-parameter step); 1: exact double-float")

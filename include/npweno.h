@@ -95,6 +95,10 @@ typedef struct {
     double eta_max;          /* eta = 0 where |eta| > eta_max: the perturbation argument (Sec. 3) needs a small
                                 eta, and a monotone stencil with zero slope at the face makes the Table k3
                                 denominator vanish (eta ~ num / eps_M); 0 = automatic (1.0), < 0 = off */
+    int32_t cross_2d;        /* 2D runs with k = 2 and an RBF scheme: 1 = the shape parameter of Sec. 6 on the
+                                5-cell cross, which also cancels the transverse curvature of the cell averages
+                                at the face midpoint (third-order face values); 0 = the line form of Table k2 */
+    int32_t pad2_;
 } npw_params;
 
 typedef struct {

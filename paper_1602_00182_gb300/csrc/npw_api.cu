@@ -60,6 +60,7 @@ npw_status check_params(const npw_params* p) {
     if (p->precision != NPW_FP64 && p->precision != NPW_FP32_MIXED) return fail(NPW_EINVAL, "bad precision");
     if (p->eta_eval < 0 || p->eta_eval > 1) return fail(NPW_EINVAL, "bad eta_eval %d", p->eta_eval);
     if (p->batch_mode < 0 || p->batch_mode > 1) return fail(NPW_EINVAL, "bad batch_mode %d", p->batch_mode);
+    if (p->cross_2d < 0 || p->cross_2d > 1) return fail(NPW_EINVAL, "bad cross_2d %d", p->cross_2d);
     if (p->tile_1d != 0 && p->tile_1d != 256 && p->tile_1d != 512 && p->tile_1d != 1024 && p->tile_1d != 2048)
         return fail(NPW_EINVAL, "tile_1d must be 0, 256, 512, 1024 or 2048, got %d", p->tile_1d);
     if (!(p->eps_weno > 0.0)) return fail(NPW_EINVAL, "eps_weno must be > 0");
@@ -76,6 +77,7 @@ npw::MethodParams method(const npw_params* p) {
     mp.characteristic = p->characteristic ? 1 : 0;
     mp.eta_eval = p->eta_eval;
     mp.k = p->k;
+    mp.cross_2d = p->cross_2d ? 1 : 0;
     mp.eps_M = p->eps_M;
     mp.eps_weno = p->eps_weno;
     mp.gamma = p->gamma;
@@ -849,7 +851,7 @@ void npw_profile_read(npw_profile* out) {
     }
 }
 
-int32_t npw_version(void) { return 10000; }
+int32_t npw_version(void) { return 10100; }
 
 npw_status npweno_reconstruct(const void* vbar, int64_t n, int32_t m, int32_t bc, const npw_params* params,
                               void* v_minus, void* v_plus, uint8_t* flags, void* stream) {

@@ -264,13 +264,17 @@ __device__ __forceinline__ T lin_weight2(int side, int r) {
 }
 
 // shape parameter of a cell, side 0 / 1 (MQ: 2 num / (den + eps_M); Gaussian: half), with the
-// optional guard and bound of the k = 3 path (magnitudes of the denominator's terms)
+// optional guard and bound of the k = 3 path (magnitudes of the denominator's terms).  On the
+// 5-cell cross of Sec. 6 (2D) the numerator also carries the transverse second difference
+// trans of the cell, with weight -1/4 for the stencil of the two cells at the face (central)
+// and 1/8 for the extrapolating one: the terms that cancel the transverse curvature of the
+// cell averages at the face midpoint.
 template <typename D>
-__device__ __forceinline__ D eta_k2(const D* c, int side, const MethodParams& mp) {
+__device__ __forceinline__ D eta_k2_cross(const D* c, int side, bool central, D trans, const MethodParams& mp) {
     const D a = side == 0 ? c[0] : c[2];
     const D b = c[1];
     const D d = side == 0 ? c[2] : c[0];
-    const D num = -a + D(2.0) * b - d;
+    const D num = -a + D(2.0) * b - d + (central ? D(-0.25) : D(0.125)) * trans;
     const D den0 = -a + D(5.0) * b + D(2.0) * d;
     const D mag = fabs(a) + D(5.0) * fabs(b) + D(2.0) * fabs(d);
     if (mp.eta_guard > 0.0 && fabs(den0) <= D(mp.eta_guard) * mag) return D(0.0);
@@ -279,13 +283,16 @@ __device__ __forceinline__ D eta_k2(const D* c, int side, const MethodParams& mp
     return e;
 }
 
-// value of cell i at its right (side 0) or left (side 1) face, k = 2; c[0..2] = cells i-1..i+1
+// value of cell i at its right (side 0) or left (side 1) face, k = 2; c[0..2] = cells i-1..i+1;
+// eta_c: shape parameter of the central row (row 0), eta_x: of the extrapolating rows
 template <typename R, typename D>
-__device__ __forceinline__ R cell_face_value_k2(const R* c, int side, R eta, const MethodParams& mp, int* r_out) {
+__device__ __forceinline__ R cell_face_value_k2(const R* c, int side, R eta_c, R eta_x, const MethodParams& mp,
+                                               int* r_out) {
     R cand[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int row = (side == 0) ? r : r - 1;
+        const R eta = row == 0 ? eta_c : eta_x;
         R s = R(0.0);
 #pragma unroll
         for (int j = 0; j < 2; ++j) s += (poly2_coef<R>(row + 1, j) + pert2_coef<R>(mp.rbf, row + 1, j) * eta) * c[1 - r + j];
@@ -312,27 +319,32 @@ __device__ __forceinline__ R cell_face_value_k2(const R* c, int side, R eta, con
 }
 
 // One field at one face, k = 2.  w[0..5] = cells i-2..i+3 around face i+1/2; v^- from cell i
-// (stencil w[1..3]), v^+ from cell i+1 (stencil w[2..4]).  Flag bits: 0 switch of cell i,
-// 3 switch of cell i+1, 2 / 4 ENO r of cell i / i+1.
+// (stencil w[1..3]), v^+ from cell i+1 (stencil w[2..4]); tl, tr: transverse second
+// differences of cells i and i+1 (0 on a line).  Flag bits: 0 switch of cell i, 3 switch of
+// cell i+1, 2 / 4 ENO r of cell i / i+1.
 template <typename R, typename D>
-__device__ __forceinline__ uint32_t face_field_k2(const R* w, const MethodParams& mp, R* vm, R* vp) {
+__device__ __forceinline__ uint32_t face_field_k2(const R* w, const MethodParams& mp, R* vm, R* vp, R tl, R tr) {
     uint32_t fl = 0;
-    R el = R(0.0), er = R(0.0);
+    R el = R(0.0), er = R(0.0), elx = R(0.0), erx = R(0.0);
     if (mp.scheme == NPW_RBF_ENO_ || mp.scheme == NPW_RBF_WENO_) {
         const D cl[3] = {D(w[1]), D(w[2]), D(w[3])};
         const D cr[3] = {D(w[2]), D(w[3]), D(w[4])};
-        if (mp.monotone_switch && k2_ratio_fires<D>(cl[0], cl[1], cl[2]))
+        if (mp.monotone_switch && k2_ratio_fires<D>(cl[0], cl[1], cl[2])) {
             fl |= 1u;
-        else
-            el = R(eta_k2<D>(cl, 0, mp));
-        if (mp.monotone_switch && k2_ratio_fires<D>(cr[0], cr[1], cr[2]))
+        } else {
+            el = R(eta_k2_cross<D>(cl, 0, true, D(tl), mp));
+            elx = tl == R(0.0) ? el : R(eta_k2_cross<D>(cl, 0, false, D(tl), mp));
+        }
+        if (mp.monotone_switch && k2_ratio_fires<D>(cr[0], cr[1], cr[2])) {
             fl |= 8u;
-        else
-            er = R(eta_k2<D>(cr, 1, mp));
+        } else {
+            er = R(eta_k2_cross<D>(cr, 1, true, D(tr), mp));
+            erx = tr == R(0.0) ? er : R(eta_k2_cross<D>(cr, 1, false, D(tr), mp));
+        }
     }
     int rl = 0, rr = 0;
-    *vm = cell_face_value_k2<R, D>(w + 1, 0, el, mp, &rl);
-    *vp = cell_face_value_k2<R, D>(w + 2, 1, er, mp, &rr);
+    *vm = cell_face_value_k2<R, D>(w + 1, 0, el, elx, mp, &rl);
+    *vp = cell_face_value_k2<R, D>(w + 2, 1, er, erx, mp, &rr);
     fl |= (uint32_t(rl & 1) << 2) | (uint32_t(rr & 1) << 4);
     return fl;
 }
@@ -340,8 +352,9 @@ __device__ __forceinline__ uint32_t face_field_k2(const R* w, const MethodParams
 // One field at one face.  w[0..5] = cells i-2..i+3 around face i+1/2.  Returns the flag
 // byte (bit0 switch, bits 2-3 / 4-5 ENO r of the left / right cell).
 template <typename R, typename D>
-__device__ __forceinline__ uint32_t face_field(const R* w, const MethodParams& mp, R* vm, R* vp) {
-    if (mp.k == 2) return face_field_k2<R, D>(w, mp, vm, vp);
+__device__ __forceinline__ uint32_t face_field(const R* w, const MethodParams& mp, R* vm, R* vp, R tl = R(0.0),
+                                               R tr = R(0.0)) {
+    if (mp.k == 2) return face_field_k2<R, D>(w, mp, vm, vp, tl, tr);
     uint32_t fl = 0;
     R eta = R(0.0);
     if (mp.scheme == NPW_RBF_ENO_ || mp.scheme == NPW_RBF_WENO_) {

@@ -341,12 +341,15 @@ __device__ __forceinline__ int eno2_choice_f(float c0, float c1, float c2) {
     return fabs((double)c1 - (double)c0) < fabs((double)c2 - (double)c1) ? 1 : 0;
 }
 
-// value of cell i (c[0..2] = cells i-1..i+1) at its right (side 0) or left (side 1) face
-__device__ __forceinline__ float cell_value_k2_f(const float* c, int side, float eta, const FParams& fp, int* r_out) {
+// value of cell i (c[0..2] = cells i-1..i+1) at its right (side 0) or left (side 1) face;
+// eta_c for the central row, eta_x for the extrapolating ones
+__device__ __forceinline__ float cell_value_k2_f(const float* c, int side, float eta_c, float eta_x, const FParams& fp,
+                                                 int* r_out) {
     float cand[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int row = (side == 0) ? r : r - 1;
+        const float eta = row == 0 ? eta_c : eta_x;
         const float k0 = fmaf(pert2_coef<float>(fp.rbf, row + 1, 0), eta, poly2_coef<float>(row + 1, 0));
         const float k1 = fmaf(pert2_coef<float>(fp.rbf, row + 1, 1), eta, poly2_coef<float>(row + 1, 1));
         cand[r] = fmaf(k0, c[1 - r], k1 * c[2 - r]);
@@ -365,32 +368,66 @@ __device__ __forceinline__ float cell_value_k2_f(const float* c, int side, float
     return __fdividef(fmaf(a0, cand[0], a1 * cand[1]), a0 + a1);
 }
 
-__device__ __forceinline__ uint32_t face_field_k2(const float* w, const MethodParams& mp0, float* vm, float* vp) {
+// Both shape parameters of one face value of a k = 2 cell (the central row's and the
+// extrapolating rows'), in FP64 from the float cell averages c[0..2] = cells i-1..i+1: the
+// numerators and the denominator of Table k2 (with the transverse term of the 5-cell cross,
+// Sec. 6) formed in double, the guard of R12 as in the FP64 path, and the quotient by one
+// reciprocal shared by both: a float seed of 1 / fl(den), one Newton step in double (relative
+// error ~2^-45 before the rounding to float), and the products.  The bound eta_max is applied
+// to the rounded values.
+__device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double trans, const MethodParams& mp, float* ec,
+                                            float* ex) {
+    const double a = widen(side == 0 ? cf[0] : cf[2]);
+    const double b = widen(cf[1]);
+    const double d = widen(side == 0 ? cf[2] : cf[0]);
+    const double base = (-a + 2.0 * b) - d;
+    const double den0 = (-a + 5.0 * b) + 2.0 * d;
+    *ec = *ex = 0.0f;
+    if (mp.eta_guard > 0.0 && fabs(den0) <= mp.eta_guard * ((fabs(a) + 5.0 * fabs(b)) + 2.0 * fabs(d))) return;
+    const double den = den0 + mp.eps_M;
+    const double F = mp.rbf == NPW_RBF_GA_ ? 1.0 : 2.0;
+    const float denf = (float)den;
+    double rF;
+    if (fabsf(denf) > 1e-30f && fabsf(denf) < 1e30f) {
+        double r = widen(1.0f / denf);
+        r = fma(r, fma(-den, r, 1.0), r);
+        rF = F * r;
+    } else {
+        rF = F / den;
+    }
+    const float vc = (float)(fma(-0.25, trans, base) * rF);
+    const float vx = trans == 0.0 ? vc : (float)(fma(0.125, trans, base) * rF);
+    const float bound = (float)mp.eta_max;
+    *ec = (bound > 0.0f && fabsf(vc) > bound) ? 0.0f : vc;
+    *ex = (bound > 0.0f && fabsf(vx) > bound) ? 0.0f : vx;
+}
+
+// tl, tr: transverse second differences of the two cells (the 5-cell cross of Sec. 6; 0 on a
+// line), taken in double from the float cell averages like the rest of the shape parameter
+__device__ __forceinline__ uint32_t face_field_k2(const float* w, const MethodParams& mp0, float* vm, float* vp,
+                                                  double tl, double tr) {
     const FParams fp = fparams(mp0);
     uint32_t fl = 0;
-    float el = 0.0f, er = 0.0f;
+    float el = 0.0f, er = 0.0f, elx = 0.0f, erx = 0.0f;
     if (fp.scheme == NPW_RBF_ENO_ || fp.scheme == NPW_RBF_WENO_) {
-        if (fp.monotone_switch && switch_k2_f(w[1], w[2], w[3])) {
+        if (fp.monotone_switch && switch_k2_f(w[1], w[2], w[3]))
             fl |= 1u;
-        } else {
-            const double c[3] = {widen(w[1]), widen(w[2]), widen(w[3])};
-            el = (float)eta_k2<double>(c, 0, mp0);
-        }
-        if (fp.monotone_switch && switch_k2_f(w[2], w[3], w[4])) {
+        else
+            eta_k2_pair(w + 1, 0, tl, mp0, &el, &elx);
+        if (fp.monotone_switch && switch_k2_f(w[2], w[3], w[4]))
             fl |= 8u;
-        } else {
-            const double c[3] = {widen(w[2]), widen(w[3]), widen(w[4])};
-            er = (float)eta_k2<double>(c, 1, mp0);
-        }
+        else
+            eta_k2_pair(w + 2, 1, tr, mp0, &er, &erx);
     }
     int rl = 0, rr = 0;
-    *vm = cell_value_k2_f(w + 1, 0, el, fp, &rl);
-    *vp = cell_value_k2_f(w + 2, 1, er, fp, &rr);
+    *vm = cell_value_k2_f(w + 1, 0, el, elx, fp, &rl);
+    *vp = cell_value_k2_f(w + 2, 1, er, erx, fp, &rr);
     return fl | (uint32_t(rl & 1) << 2) | (uint32_t(rr & 1) << 4);
 }
 
-__device__ __forceinline__ uint32_t face_field(const float* w, const MethodParams& mp0, float* vm, float* vp) {
-    if (mp0.k == 2) return face_field_k2(w, mp0, vm, vp);
+__device__ __forceinline__ uint32_t face_field(const float* w, const MethodParams& mp0, float* vm, float* vp,
+                                               double tl = 0.0, double tr = 0.0) {
+    if (mp0.k == 2) return face_field_k2(w, mp0, vm, vp, tl, tr);
     uint32_t fl = 0;
     const FParams mp = fparams(mp0);
     const float eta = face_eta(w[1], w[2], w[3], w[4], mp, &fl);
@@ -404,18 +441,22 @@ __device__ __forceinline__ uint32_t face_field(const float* w, const MethodParam
 
 // the literal double-precision arithmetic for R = double, the mixed path for R = float
 template <typename R, typename D>
-__device__ __forceinline__ uint32_t face_field_any(const R* w, const MethodParams& mp, R* vm, R* vp) {
+__device__ __forceinline__ uint32_t face_field_any(const R* w, const MethodParams& mp, R* vm, R* vp, D tl = D(0.0),
+                                                   D tr = D(0.0)) {
     if constexpr (sizeof(R) == sizeof(float)) {
-        return fast::face_field(w, mp, vm, vp);
+        return fast::face_field(w, mp, vm, vp, tl, tr);
     } else {
-        return face_field<R, D>(w, mp, vm, vp);
+        return face_field<R, D>(w, mp, vm, vp, R(tl), R(tr));
     }
 }
 
 // All M fields at one face from the 6 x M stencil W[j*M + k] (cells i-2..i+3).  For the
 // characteristic variant the fields are projected by L, reconstructed, and mapped back by R.
+// T (optional, component-wise): transverse second differences [2][M] of the face's left and
+// right cells, for the k = 2 shape parameter on the 5-cell cross (Sec. 6).
 template <typename R, typename D, int KIND, int M, bool CHAR>
-__device__ __forceinline__ bool face_all(const R* S, const MethodParams& mp, R* vm, R* vp, uint32_t* flags) {
+__device__ __forceinline__ bool face_all(const R* S, const MethodParams& mp, R* vm, R* vp, uint32_t* flags,
+                                         const D* T = nullptr) {
     if (CHAR) {
         R Rm[3][3], Lm[3][3];
         if (!euler_eig<R>(S + 2 * M, S + 3 * M, R(mp.gamma), Rm, Lm)) return false;
@@ -450,7 +491,8 @@ __device__ __forceinline__ bool face_all(const R* S, const MethodParams& mp, R* 
         R line[6];
 #pragma unroll
         for (int j = 0; j < 6; ++j) line[j] = S[j * M + k];
-        flags[k] = face_field_any<R, D>(line, mp, &vm[k], &vp[k]);
+        flags[k] = T ? face_field_any<R, D>(line, mp, &vm[k], &vp[k], T[k], T[M + k])
+                     : face_field_any<R, D>(line, mp, &vm[k], &vp[k]);
     }
     return true;
 }

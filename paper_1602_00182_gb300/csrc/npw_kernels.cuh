@@ -899,13 +899,19 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
     const int64_t nx = in.nx, ny = in.ny, cells = nx * ny;
     const R* uin = reinterpret_cast<const R*>(a.uin) + in.off;
     const int tid = threadIdx.x;
+    const bool cross = a.mp.k == 2 && a.mp.cross_2d &&
+                       (a.mp.scheme == NPW_RBF_ENO_ || a.mp.scheme == NPW_RBF_WENO_);
     for (int idx = tid; idx < BX * BY * M; idx += blockDim.x) {
         const int k = idx / (BX * BY);
         const int rem = idx - k * BX * BY;
         const int by = rem / BX, bx = rem - by * BX;
+        // the corners are read only by the 5-cell cross of k = 2 (transverse differences of the
+        // halo cells next to the tile)
         const bool corner = (bx < 3 || bx >= TX_2D + 3) && (by < 3 || by >= TY_2D + 3);
         su[(by * BX + bx) * M + k] =
-            corner ? R(0.0) : grid_get<R>(uin + k * cells, in, (int64_t)tx0 - 3 + bx, (int64_t)ty0 - 3 + by, a.mp.inflow[k]);
+            (corner && !cross) ? R(0.0)
+                               : grid_get<R>(uin + k * cells, in, (int64_t)tx0 - 3 + bx, (int64_t)ty0 - 3 + by,
+                                             a.mp.inflow[k]);
     }
     const double dt = *(volatile double*)&ctl->dt;
     const R ax = R(*(volatile double*)&ctl->alpha);
@@ -920,7 +926,21 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
         for (int j = 0; j < 6; ++j)
 #pragma unroll
             for (int k = 0; k < M; ++k) S[j * M + k] = su[((qy + 3) * BX + qx + j) * M + k];
-        face_all<R, D, KIND, M, false>(S, a.mp, vm, vp, fl);
+        if (cross) {
+            // transverse (y) second differences of the cells qx-1 and qx of row qy
+            D T[2 * M];
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const int bx = qx + 2 + c;
+                    T[c * M + k] = (D(su[((qy + 2) * BX + bx) * M + k]) - D(2.0) * D(su[((qy + 3) * BX + bx) * M + k])) +
+                                   D(su[((qy + 4) * BX + bx) * M + k]);
+                }
+            face_all<R, D, KIND, M, false>(S, a.mp, vm, vp, fl, T);
+        } else {
+            face_all<R, D, KIND, M, false>(S, a.mp, vm, vp, fl);
+        }
         lf_flux<R, KIND, M>(vm, vp, ax, a.mp, 0, h);
 #pragma unroll
         for (int k = 0; k < M; ++k) hx[(qy * (TX_2D + 1) + qx) * M + k] = h[k];
@@ -934,7 +954,21 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
         for (int j = 0; j < 6; ++j)
 #pragma unroll
             for (int k = 0; k < M; ++k) S[j * M + k] = su[((qy + j) * BX + qx + 3) * M + k];
-        face_all<R, D, KIND, M, false>(S, a.mp, vm, vp, fl);
+        if (cross) {
+            // transverse (x) second differences of the cells qy-1 and qy of column qx
+            D T[2 * M];
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const int by = qy + 2 + c;
+                    T[c * M + k] = (D(su[(by * BX + qx + 2) * M + k]) - D(2.0) * D(su[(by * BX + qx + 3) * M + k])) +
+                                   D(su[(by * BX + qx + 4) * M + k]);
+                }
+            face_all<R, D, KIND, M, false>(S, a.mp, vm, vp, fl, T);
+        } else {
+            face_all<R, D, KIND, M, false>(S, a.mp, vm, vp, fl);
+        }
         lf_flux<R, KIND, M>(vm, vp, ay, a.mp, 1, h);
 #pragma unroll
         for (int k = 0; k < M; ++k) hy[(qy * TX_2D + qx) * M + k] = h[k];

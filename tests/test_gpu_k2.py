@@ -215,3 +215,64 @@ def test_k2_server_matches_batch_solve(npw):
         st, stats = npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, p)
         assert st == 0 and got[j]["status"] == 0 and got[j]["steps"] == stats[0]["steps"]
         assert np.array_equal(got[j]["u"], arena.cpu().numpy())
+
+
+def _cross_params(npw, op, precision):
+    p = _gp(npw, op, precision=precision)
+    p.cross_2d = 1
+    return p
+
+
+@pytest.mark.parametrize("shape", [(40, 24), (70, 45)])
+@pytest.mark.parametrize("bc", [O.PERIODIC, O.TRANSMISSIVE, O.INFLOW])
+@pytest.mark.parametrize("scheme", [O.RBF_ENO, O.RBF_WENO])
+def test_k2_cross_2d_step_fp64(npw, shape, bc, scheme):
+    """Sec. 6 shape parameter on the 5-cell cross (k = 2, 2D), FP64: one RK3 step of Burgers on
+    a ragged grid equals the oracle to 1e-12, for every boundary condition."""
+    nx, ny = shape
+    g = np.random.default_rng(nx * ny + bc)
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    U = 1.0 + 0.4 * np.sin(2 * np.pi * (x[None, :] + 0.7 * y[:, None])) + 0.1 * np.cos(6 * np.pi * y)[:, None]
+    U[ny // 2:, nx // 3:] += 0.3 * g.uniform()
+    d = 1.0 / nx
+    op = O.Params(k=2, scheme=scheme, cross_2d=1, inflow=(1.2, 0, 0, 0))
+    ref = O.rk3_step_2d(U, d, d, 0.2 * d, O.BURGERS, bc, op)
+    gu = _dev(U)
+    npw.npweno_rk3_step_2d(gu, d, d, 0.2 * d, O.BURGERS, bc, _cross_params(npw, op, 0))
+    assert _rel(gu.cpu().numpy(), ref) <= FP64_TOL
+    # the line form differs from the cross form on this data
+    line = O.rk3_step_2d(U, d, d, 0.2 * d, O.BURGERS, bc, O.Params(k=2, scheme=scheme, inflow=(1.2, 0, 0, 0)))
+    assert _rel(line, ref) > 1e-8
+
+
+def test_k2_cross_2d_euler_fp64_and_mixed(npw):
+    U, d = I.isentropic_vortex(48, 4.0, 5.0, 5.0, npts=2)
+    op = O.Params(k=2, cross_2d=1)
+    ref = O.rk3_step_2d(U, d, d, 0.2 * d, O.EULER2D, O.PERIODIC, op)
+    gu = _dev(U)
+    npw.npweno_rk3_step_2d(gu, d, d, 0.2 * d, O.EULER2D, O.PERIODIC, _cross_params(npw, op, 0))
+    assert _rel(gu.cpu().numpy(), ref) <= FP64_TOL
+    # mixed precision without the switch: float rounding of one step
+    U32 = U.astype(np.float32).astype(np.float64)
+    opm = O.Params(k=2, cross_2d=1, monotone_switch=0, eta_guard=MIXED_GUARD)
+    refm = O.rk3_step_2d(U32, d, d, 0.2 * d, O.EULER2D, O.PERIODIC, opm)
+    gm = _dev(U32, torch.float32)
+    npw.npweno_rk3_step_2d(gm, d, d, 0.2 * d, O.EULER2D, O.PERIODIC, _cross_params(npw, opm, 1))
+    assert _rel(gm.cpu().numpy().astype(np.float64), refm) <= 2e-6
+
+
+def test_k2_cross_2d_solve_fp64(npw):
+    """Advection of sin(2 pi (x + y)) for 40 steps with the cross form, FP64, against the oracle."""
+    n = 32
+    e = np.linspace(0.0, 1.0, n + 1)
+    F = lambda x, y: -np.sin(2 * np.pi * (x + y)) / (4 * np.pi ** 2)  # noqa: E731
+    U = (F(e[1:][None, :], e[1:][:, None]) - F(e[:-1][None, :], e[1:][:, None]) - F(e[1:][None, :], e[:-1][:, None]) +
+         F(e[:-1][None, :], e[:-1][:, None])) * n * n
+    d = 1.0 / n
+    op = O.Params(k=2, scheme=O.RBF_ENO, monotone_switch=0, cross_2d=1)
+    ref, rst = O.solve_2d(U, d, d, 40 * 0.1 * d, 0.2, O.ADVECTION, O.PERIODIC, op)
+    gu = _dev(U)
+    st = npw.npweno_solve_2d(gu, d, d, 40 * 0.1 * d, 0.2, O.ADVECTION, O.PERIODIC, _cross_params(npw, op, 0))
+    assert st["status"] == 0 and st["steps"] == rst["steps"]
+    assert _rel(gu.cpu().numpy(), ref) <= 1e-11
