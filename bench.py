@@ -247,7 +247,7 @@ def run_gpu(args, rank, world, local_rank):
         time_variant(npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, eta_eval=1),
                      "eta_eval=1 (exact double-float eta, no FP64 instruction)")
         time_variant(npw.Params(k=2, rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED),
-                     "k=2 RBF-WENO3 Gaussian + switch (Table k2; face-based per-stage kernels, eta in FP64)")
+                     "k=2 RBF-WENO3 Gaussian + switch (Table k2; resident kernels, eta in FP64)")
 
     out = {
         "metric": "cell-updates/s",
@@ -600,7 +600,7 @@ def run_euler2d(args, rank, world, local_rank):
                    "l2": "flushed before every timed step"},
         "roofline": {"bound": "alu", "achieved": fp64, "peak": FP64_PIPE_PEAK / 1e9, "unit": "G FP64-pipe instr/s",
                      "frac": (fp64 / (FP64_PIPE_PEAK / 1e9)) if fp64 else None, "traffic": None,
-                     "kernel": "stage2d_fast_kernel<EULER2D>" if args.k == 3 else "stage2d_kernel<float,double,EULER2D>",
+                     "kernel": f"stage2d_fast_kernel<EULER2D, k={args.k}>",
                      "hbm_view": {"achieved_gbs": cu * args.steps * 128 / st_s / 1e9 if st_s > 0 else None,
                                   "peak_gbs": _peaks()[0], "bytes_per_cell_update": 128},
                      "stage_launches": int(pr.stage_launches), "stage_ms": pr.stage_ms},

@@ -471,9 +471,9 @@ int resolve_tile(const npw_params* p, int kind, int m) {
 }
 
 // the compensated float kernels (stage1d_fast_kernel, the resident kernel) cover float,
-// component-wise, k = 3; every other case runs the face-based stage kernel
+// component-wise (k = 3 and k = 2); FP64 and characteristic runs take the face-based stage kernel
 bool compensated(const npw_params* p) {
-    return p->precision == NPW_FP32_MIXED && !p->characteristic && p->k == 3;
+    return p->precision == NPW_FP32_MIXED && !p->characteristic;
 }
 
 // instances the resident kernel can take: compensated float path, fits in shared memory

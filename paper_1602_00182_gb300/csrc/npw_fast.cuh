@@ -402,6 +402,22 @@ __device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double tr
     *ex = (bound > 0.0f && fabsf(vx) > bound) ? 0.0f : vx;
 }
 
+// Both face values of one k = 2 cell (c3 = cells i-1..i+1, trans its transverse second
+// difference or 0): v^- at its right face and v^+ at its left face, with the arithmetic that
+// face_field_k2 gives them face by face.
+__device__ __forceinline__ void cell_recon_k2(const float* c3, double trans, const MethodParams& mp0, const FParams& fp,
+                                              float* vm, float* vp) {
+    float e0c = 0.0f, e0x = 0.0f, e1c = 0.0f, e1x = 0.0f;
+    if ((fp.scheme == NPW_RBF_ENO_ || fp.scheme == NPW_RBF_WENO_) &&
+        !(fp.monotone_switch && switch_k2_f(c3[0], c3[1], c3[2]))) {
+        eta_k2_pair(c3, 0, trans, mp0, &e0c, &e0x);
+        eta_k2_pair(c3, 1, trans, mp0, &e1c, &e1x);
+    }
+    int r;
+    *vm = cell_value_k2_f(c3, 0, e0c, e0x, fp, &r);
+    *vp = cell_value_k2_f(c3, 1, e1c, e1x, fp, &r);
+}
+
 // tl, tr: transverse second differences of the two cells (the 5-cell cross of Sec. 6; 0 on a
 // line), taken in double from the float cell averages like the rest of the shape parameter
 __device__ __forceinline__ uint32_t face_field_k2(const float* w, const MethodParams& mp0, float* vm, float* vp,

@@ -8,11 +8,11 @@
 namespace npw {
 size_t resident_smem_bytes(int64_t n, int m) { return (size_t)m * (size_t)(6 * n + 5) * sizeof(float); }
 
-template <int KIND>
+template <int KIND, int K>
 static cudaError_t launch_res(const ResidentArgs& a, int64_t max_n, int threads, cudaStream_t s) {
     constexpr int M = kind_m<KIND>();
     const size_t smem = resident_smem_bytes(max_n, M);
-    auto kern = solve1d_resident_kernel<KIND>;
+    auto kern = solve1d_resident_kernel<KIND, K>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RESIDENT_SMEM_MAX);
@@ -27,9 +27,15 @@ cudaError_t launch_resident_f32(const ResidentArgs& a, int m, int kind, int64_t 
     (void)m;
     if (resident_smem_bytes(max_n, kind == NPW_FLUX_EULER1D ? 3 : 1) > RESIDENT_SMEM_MAX) return cudaErrorInvalidValue;
     switch (kind) {
-        case NPW_FLUX_ADVECTION: return launch_res<NPW_FLUX_ADVECTION_>(a, max_n, threads, s);
-        case NPW_FLUX_BURGERS: return launch_res<NPW_FLUX_BURGERS_>(a, max_n, threads, s);
-        case NPW_FLUX_EULER1D: return launch_res<NPW_FLUX_EULER1D_>(a, max_n, threads, s);
+        case NPW_FLUX_ADVECTION:
+            return a.mp.k == 2 ? launch_res<NPW_FLUX_ADVECTION_, 2>(a, max_n, threads, s)
+                               : launch_res<NPW_FLUX_ADVECTION_, 3>(a, max_n, threads, s);
+        case NPW_FLUX_BURGERS:
+            return a.mp.k == 2 ? launch_res<NPW_FLUX_BURGERS_, 2>(a, max_n, threads, s)
+                               : launch_res<NPW_FLUX_BURGERS_, 3>(a, max_n, threads, s);
+        case NPW_FLUX_EULER1D:
+            return a.mp.k == 2 ? launch_res<NPW_FLUX_EULER1D_, 2>(a, max_n, threads, s)
+                               : launch_res<NPW_FLUX_EULER1D_, 3>(a, max_n, threads, s);
         default: return cudaErrorInvalidValue;
     }
 }

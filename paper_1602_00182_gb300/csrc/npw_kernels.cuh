@@ -324,9 +324,11 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_kernel(Stage1DArgs a) {
 // and the last addition is compensated with a per-cell carry (Kahan): increments smaller than
 // half an ulp of u are kept in the carry instead of being rounded away.  Stage 3 writes the new
 // state to s (neighbouring tiles still read u^n); the next step's stage 1 reads s and commits it
-// to u.  Shared memory (floats): u^(k), eta, v^-, v^+, each (tile + 6) * M.
+// to u.  Shared memory (floats): u^(k), eta, v^-, v^+, each (tile + 6) * M.  K = 2: the shape
+// parameters belong to the cell (Table k2) and are formed in the reconstruction phase; the eta
+// phase is skipped.
 // ---------------------------------------------------------------------------------------
-template <int KIND>
+template <int KIND, int K>
 __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a) {
     constexpr int M = kind_m<KIND>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -371,13 +373,15 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
     __syncthreads();
 
     // F: faces between extended cells e-1 and e
-    for (int idx = threadIdx.x; idx < (cnt + 3) * M; idx += blockDim.x) {
-        const int e = 2 + idx / M, k = idx - (e - 2) * M;
-        uint32_t fl = 0;
-        se[e * M + k] = fast::face_eta(su[(e - 2) * M + k], su[(e - 1) * M + k], su[e * M + k], su[(e + 1) * M + k],
-                                       fp, &fl);
+    if constexpr (K == 3) {
+        for (int idx = threadIdx.x; idx < (cnt + 3) * M; idx += blockDim.x) {
+            const int e = 2 + idx / M, k = idx - (e - 2) * M;
+            uint32_t fl = 0;
+            se[e * M + k] = fast::face_eta(su[(e - 2) * M + k], su[(e - 1) * M + k], su[e * M + k],
+                                           su[(e + 1) * M + k], fp, &fl);
+        }
+        __syncthreads();
     }
-    __syncthreads();
     // C: cells
     for (int idx = threadIdx.x; idx < (cnt + 2) * M; idx += blockDim.x) {
         const int e = 2 + idx / M, k = idx - (e - 2) * M;
@@ -385,7 +389,10 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
 #pragma unroll
         for (int j = 0; j < 5; ++j) c[j] = su[(e - 2 + j) * M + k];
         float vm, vp;
-        fast::cell_recon(c, se[(e + 1) * M + k], se[e * M + k], fp, &vm, &vp);
+        if constexpr (K == 3)
+            fast::cell_recon(c, se[(e + 1) * M + k], se[e * M + k], fp, &vm, &vp);
+        else
+            fast::cell_recon_k2(c + 1, 0.0, a.mp, fp, &vm, &vp);
         svm[e * M + k] = vm;
         svp[e * M + k] = vp;
     }
@@ -477,7 +484,7 @@ __device__ __forceinline__ int res_map(int i, int n, int bc) {
     return i < 0 ? (bc == NPW_BC_INFLOW ? -1 : 0) : (i >= n ? n - 1 : i);
 }
 
-template <int KIND>
+template <int KIND, int K>
 __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) {
     constexpr int M = kind_m<KIND>();
     extern __shared__ __align__(16) float smf[];
@@ -562,8 +569,9 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
             const float* D = stage == 1 ? uA : uB;
 #define NPW_X(idx) (stage == 0 ? un[(idx)] : un[(idx)] + D[(idx)])
             if (lo < hi) {
-                // F: eta of faces lo..hi (cells f-2..f+1)
-                for (int f = lo + lane; f <= hi; f += 32) {
+                // F: eta of faces lo..hi (cells f-2..f+1); k = 2 forms its shape parameters per
+                // cell in C instead
+                for (int f = lo + lane; K == 3 && f <= hi; f += 32) {
 #pragma unroll
                     for (int k = 0; k < M; ++k) {
                         float w[4];
@@ -587,10 +595,14 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
                             const int cc = res_map(i - 2 + j, n, in.bc);
                             c[j] = cc < 0 ? inflow[k] : NPW_X(k * n + cc);
                         }
-                        const float er = (i + 1 <= hi) ? se[k * (n + 1) + i + 1] : 0.0f;
-                        const float el = (i >= lo) ? se[k * (n + 1) + i] : 0.0f;
                         float vm, vp;
-                        fast::cell_recon(c, er, el, fp, &vm, &vp);
+                        if constexpr (K == 3) {
+                            const float er = (i + 1 <= hi) ? se[k * (n + 1) + i + 1] : 0.0f;
+                            const float el = (i >= lo) ? se[k * (n + 1) + i] : 0.0f;
+                            fast::cell_recon(c, er, el, fp, &vm, &vp);
+                        } else {
+                            fast::cell_recon_k2(c + 1, 0.0, a.mp, fp, &vm, &vp);
+                        }
                         // cell lo-1 contributes only v^- (face lo), cell hi only v^+ (face hi); their
                         // other side belongs to the neighbouring warp and is not written here
                         if (i < hi) svm[k * (n + 2) + i + 1] = vm;
@@ -707,18 +719,19 @@ __device__ __forceinline__ R grid_get(const R* u, const Inst2D& in, int64_t i, i
 }
 
 // ---------------------------------------------------------------------------------------
-// 2D stage kernel of the mixed path (float state, component-wise, k = 3) in phases, each a
-// balanced loop over independent work items:
-//   E  eta of every (face, field) of both directions (FP64 quotient, switch)
+// 2D stage kernel of the mixed path (float state, component-wise) in phases, each a balanced
+// loop over independent work items:
+//   E  (k = 3) eta of every (face, field) of both directions (FP64 quotient, switch)
 //   C  reconstruction of every (cell, field) of both directions: v^- at its right / upper face
-//      and v^+ at its left / lower face, one set of smoothness indicators for both
+//      and v^+ at its left / lower face, one set of smoothness indicators for both (k = 2: the
+//      cell's own switch and shape parameters, with the transverse term of the 5-cell cross)
 //   F  Lax-Friedrichs flux of every face (all fields)
 //   U  flux difference and Shu-Osher stage combination of every cell
 // Every face value gets the arithmetic of fast::face_field, so the result is the same as the
 // face-by-face kernel's; the phases avoid reconstructing a cell once per face and the uneven
 // per-thread face counts of that kernel.
 // ---------------------------------------------------------------------------------------
-template <int KIND>
+template <int KIND, int K>
 __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs a) {
     constexpr int M = kind_m<KIND>();
     constexpr int BX = TX_2D + 6, BY = TY_2D + 6;
@@ -741,14 +754,17 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
     const float* uin = reinterpret_cast<const float*>(a.uin) + in.off;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const fast::FParams fp = fast::fparams(a.mp);
+    const bool cross = K == 2 && a.mp.cross_2d && (a.mp.scheme == NPW_RBF_ENO_ || a.mp.scheme == NPW_RBF_WENO_);
     for (int idx = tid; idx < BX * BY * M; idx += nthr) {
         const int k = idx / (BX * BY);
         const int rem = idx - k * BX * BY;
         const int by = rem / BX, bx = rem - by * BX;
+        // the corners are read only by the 5-cell cross (transverse differences of halo cells)
         const bool corner = (bx < 3 || bx >= TX_2D + 3) && (by < 3 || by >= TY_2D + 3);
-        su[(by * BX + bx) * M + k] = corner ? 0.0f
-                                            : grid_get<float>(uin + k * cells, in, (int64_t)tx0 - 3 + bx,
-                                                              (int64_t)ty0 - 3 + by, a.mp.inflow[k]);
+        su[(by * BX + bx) * M + k] = (corner && !cross)
+                                         ? 0.0f
+                                         : grid_get<float>(uin + k * cells, in, (int64_t)tx0 - 3 + bx,
+                                                           (int64_t)ty0 - 3 + by, a.mp.inflow[k]);
     }
     const double dt = *(volatile double*)&ctl->dt;
     const float ax = (float)(*(volatile double*)&ctl->alpha);
@@ -757,7 +773,7 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
 #define NPW_SU(bx, by, k) su[((by) * BX + (bx)) * M + (k)]
     // E: item = (face, field); x face (qx, qy) has the eta stencil su[qy+3][qx+1 .. qx+4],
     // y face (qx, qy) su[qy+1 .. qy+4][qx+3]
-    for (int it = tid; it < (NFX + NFY) * M; it += nthr) {
+    for (int it = tid; K == 3 && it < (NFX + NFY) * M; it += nthr) {
         const int k = it % M, f = it / M;
         float w0, w1, w2, w3;
         if (f < NFX) {
@@ -785,6 +801,7 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
     for (int it = tid; it < (NCX + NCY) * M; it += nthr) {
         const int k = it % M, c = it / M;
         float cc[5];
+        double trans = 0.0;  // k = 2 cross: transverse second difference of the cell
         int fl_idx, fr_idx;  // faces left / right of the cell (-1 when outside the tile)
         if (c < NCX) {
             const int qy = c / (TX_2D + 2), cx = c - qy * (TX_2D + 2) - 1;
@@ -792,6 +809,9 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
             for (int j = 0; j < 5; ++j) cc[j] = NPW_SU(cx + 1 + j, qy + 3, k);
             fl_idx = cx >= 0 ? qy * (TX_2D + 1) + cx : -1;
             fr_idx = cx < TX_2D ? qy * (TX_2D + 1) + cx + 1 : -1;
+            if (cross)
+                trans = ((double)NPW_SU(cx + 3, qy + 2, k) - 2.0 * (double)NPW_SU(cx + 3, qy + 3, k)) +
+                        (double)NPW_SU(cx + 3, qy + 4, k);
         } else {
             const int g = c - NCX;
             const int qx = g / (TY_2D + 2), cy = g - qx * (TY_2D + 2) - 1;
@@ -799,11 +819,18 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
             for (int j = 0; j < 5; ++j) cc[j] = NPW_SU(qx + 3, cy + 1 + j, k);
             fl_idx = cy >= 0 ? NFX + cy * TX_2D + qx : -1;
             fr_idx = cy < TY_2D ? NFX + (cy + 1) * TX_2D + qx : -1;
+            if (cross)
+                trans = ((double)NPW_SU(qx + 2, cy + 3, k) - 2.0 * (double)NPW_SU(qx + 3, cy + 3, k)) +
+                        (double)NPW_SU(qx + 4, cy + 3, k);
         }
-        const float er = fr_idx >= 0 ? ef[fr_idx * M + k] : 0.0f;
-        const float el = fl_idx >= 0 ? ef[fl_idx * M + k] : 0.0f;
         float vm, vp;
-        fast::cell_recon(cc, er, el, fp, &vm, &vp);
+        if constexpr (K == 3) {
+            const float er = fr_idx >= 0 ? ef[fr_idx * M + k] : 0.0f;
+            const float el = fl_idx >= 0 ? ef[fl_idx * M + k] : 0.0f;
+            fast::cell_recon(cc, er, el, fp, &vm, &vp);
+        } else {
+            fast::cell_recon_k2(cc + 1, trans, a.mp, fp, &vm, &vp);
+        }
         if (fr_idx >= 0) vmf[fr_idx * M + k] = vm;
         if (fl_idx >= 0) vpf[fl_idx * M + k] = vp;
     }
@@ -1154,11 +1181,11 @@ struct Launchers {
         return cudaGetLastError();
     }
 
-    template <int KIND>
+    template <int KIND, int K>
     static cudaError_t stage_fast(const Stage1DArgs& a, cudaStream_t s) {
         constexpr int M = kind_m<KIND>();
         const size_t smem = (size_t)(a.tile + 6) * 4 * M * sizeof(float);
-        auto kern = stage1d_fast_kernel<KIND>;
+        auto kern = stage1d_fast_kernel<KIND, K>;
         static bool attr_set = false;
         if (!attr_set) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
@@ -1171,11 +1198,15 @@ struct Launchers {
 
     static cudaError_t stage1d(const Stage1DArgs& a, int kind, cudaStream_t s) {
         if constexpr (sizeof(R) == sizeof(float)) {
-            if (!a.mp.characteristic && a.mp.k == 3) {
+            if (!a.mp.characteristic) {
+                const bool k2 = a.mp.k == 2;
                 switch (kind) {
-                    case NPW_FLUX_ADVECTION: return stage_fast<NPW_FLUX_ADVECTION_>(a, s);
-                    case NPW_FLUX_BURGERS: return stage_fast<NPW_FLUX_BURGERS_>(a, s);
-                    case NPW_FLUX_EULER1D: return stage_fast<NPW_FLUX_EULER1D_>(a, s);
+                    case NPW_FLUX_ADVECTION:
+                        return k2 ? stage_fast<NPW_FLUX_ADVECTION_, 2>(a, s) : stage_fast<NPW_FLUX_ADVECTION_, 3>(a, s);
+                    case NPW_FLUX_BURGERS:
+                        return k2 ? stage_fast<NPW_FLUX_BURGERS_, 2>(a, s) : stage_fast<NPW_FLUX_BURGERS_, 3>(a, s);
+                    case NPW_FLUX_EULER1D:
+                        return k2 ? stage_fast<NPW_FLUX_EULER1D_, 2>(a, s) : stage_fast<NPW_FLUX_EULER1D_, 3>(a, s);
                     default: return cudaErrorInvalidValue;
                 }
             }
@@ -1211,22 +1242,30 @@ struct Launchers {
 
     static cudaError_t stage2d(const Stage2DArgs& a, int tiles, int kind, cudaStream_t s) {
         if constexpr (sizeof(R) == sizeof(float)) {
-            if (a.mp.k == 3) {
-                switch (kind) {
-                    case NPW_FLUX_ADVECTION:
-                        stage2d_fast_kernel<NPW_FLUX_ADVECTION_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
-                        break;
-                    case NPW_FLUX_BURGERS:
-                        stage2d_fast_kernel<NPW_FLUX_BURGERS_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
-                        break;
-                    case NPW_FLUX_EULER2D:
-                        stage2d_fast_kernel<NPW_FLUX_EULER2D_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
-                        break;
-                    default:
-                        return cudaErrorInvalidValue;
-                }
-                return cudaGetLastError();
+            // the mixed path: the phased kernel, k = 3 or k = 2
+            switch (kind * 4 + a.mp.k) {
+                case NPW_FLUX_ADVECTION * 4 + 3:
+                    stage2d_fast_kernel<NPW_FLUX_ADVECTION_, 3><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                    break;
+                case NPW_FLUX_BURGERS * 4 + 3:
+                    stage2d_fast_kernel<NPW_FLUX_BURGERS_, 3><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                    break;
+                case NPW_FLUX_EULER2D * 4 + 3:
+                    stage2d_fast_kernel<NPW_FLUX_EULER2D_, 3><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                    break;
+                case NPW_FLUX_ADVECTION * 4 + 2:
+                    stage2d_fast_kernel<NPW_FLUX_ADVECTION_, 2><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                    break;
+                case NPW_FLUX_BURGERS * 4 + 2:
+                    stage2d_fast_kernel<NPW_FLUX_BURGERS_, 2><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                    break;
+                case NPW_FLUX_EULER2D * 4 + 2:
+                    stage2d_fast_kernel<NPW_FLUX_EULER2D_, 2><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                    break;
+                default:
+                    return cudaErrorInvalidValue;
             }
+            return cudaGetLastError();
         }
         switch (kind) {
             case NPW_FLUX_ADVECTION:

@@ -346,9 +346,11 @@ def test_mixed_precision_full_burgers_instance_stays_finite(npw):
 
 # ------------------------------------------------------------------------------ resident whole-solve kernel
 @pytest.mark.parametrize("family", ["burgers", "euler", "inflow"])
-def test_resident_matches_per_stage_kernels(npw, family):
+@pytest.mark.parametrize("k", [3, 2])
+def test_resident_matches_per_stage_kernels(npw, family, k):
     """Instances that fit in shared memory are solved whole by one CTA (batch_mode 0); the
-    per-stage kernels (batch_mode 1) run the same arithmetic, so both give identical bits."""
+    per-stage kernels (batch_mode 1) run the same arithmetic, so both give identical bits
+    (k = 3 and k = 2)."""
     if family == "burgers":
         inst = I.burgers_batch(count=24, nmin=64, nmax=9000)
         m, kind, bc = 1, O.BURGERS, O.PERIODIC
@@ -374,7 +376,7 @@ def test_resident_matches_per_stage_kernels(npw, family):
     outs = []
     for mode in (0, 1):
         arena = _dev(np.concatenate(u0s), torch.float32)
-        p = npw.Params(rbf=npw.NPW_RBF_GA, precision=1, batch_mode=mode, inflow=inflow)
+        p = npw.Params(k=k, rbf=npw.NPW_RBF_GA, precision=1, batch_mode=mode, inflow=inflow)
         st, stats = npw.npweno_batch_solve(arena, table, m, kind, p)
         assert st == 0
         outs.append((arena.cpu().numpy(), stats))
