@@ -93,6 +93,14 @@ npw::MethodParams method(const npw_params* p) {
     else
         mp.eta_guard = 0.0;
     mp.eta_max = p->eta_max > 0.0 ? p->eta_max : (p->eta_max == 0.0 ? 1.0 : 0.0);
+    mp.eps_weno_f = (float)mp.eps_weno;
+    mp.eps_M_f = (float)mp.eps_M;
+    mp.eta_guard_f = (float)mp.eta_guard;
+    mp.eta_max_f = (float)mp.eta_max;
+    mp.gamma_f = (float)mp.gamma;
+    mp.adv_speed_f = (float)mp.adv_speed;
+    mp.adv_speed_y_f = (float)mp.adv_speed_y;
+    for (int k = 0; k < 4; ++k) mp.inflow_f[k] = (float)mp.inflow[k];
     return mp;
 }
 

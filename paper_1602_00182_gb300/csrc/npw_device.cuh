@@ -386,18 +386,18 @@ __device__ __forceinline__ uint32_t face_field(const R* w, const MethodParams& m
 template <typename R, int KIND>
 __device__ __forceinline__ void phys_flux(const R* U, const MethodParams& mp, int dir, R* F) {
     if (KIND == NPW_FLUX_ADVECTION_) {
-        F[0] = R(dir == 0 ? mp.adv_speed : mp.adv_speed_y) * U[0];
+        F[0] = (dir == 0 ? mp_val<R>(mp.adv_speed, mp.adv_speed_f) : mp_val<R>(mp.adv_speed_y, mp.adv_speed_y_f)) * U[0];
     } else if (KIND == NPW_FLUX_BURGERS_) {
         F[0] = R(0.5) * U[0] * U[0];
     } else if (KIND == NPW_FLUX_EULER1D_) {
-        const R g = R(mp.gamma);
+        const R g = mp_val<R>(mp.gamma, mp.gamma_f);
         R rho = U[0], u = U[1] / rho, E = U[2];
         R P = (g - R(1.0)) * (E - R(0.5) * rho * u * u);
         F[0] = rho * u;
         F[1] = rho * u * u + P;
         F[2] = (E + P) * u;
     } else {
-        const R g = R(mp.gamma);
+        const R g = mp_val<R>(mp.gamma, mp.gamma_f);
         R rho = U[0], u = U[1] / rho, v = U[2] / rho, E = U[3];
         R P = (g - R(1.0)) * (E - R(0.5) * rho * (u * u + v * v));
         R un = (dir == 0) ? u : v;
@@ -410,9 +410,10 @@ __device__ __forceinline__ void phys_flux(const R* U, const MethodParams& mp, in
 
 template <typename R, int KIND>
 __device__ __forceinline__ R wave_speed(const R* U, const MethodParams& mp, int dir) {
-    if (KIND == NPW_FLUX_ADVECTION_) return fabs(R(dir == 0 ? mp.adv_speed : mp.adv_speed_y));
+    if (KIND == NPW_FLUX_ADVECTION_)
+        return fabs(dir == 0 ? mp_val<R>(mp.adv_speed, mp.adv_speed_f) : mp_val<R>(mp.adv_speed_y, mp.adv_speed_y_f));
     if (KIND == NPW_FLUX_BURGERS_) return fabs(U[0]);
-    const R g = R(mp.gamma);
+    const R g = mp_val<R>(mp.gamma, mp.gamma_f);
     if (KIND == NPW_FLUX_EULER1D_) {
         R rho = U[0], u = U[1] / rho;
         R P = (g - R(1.0)) * (U[2] - R(0.5) * rho * u * u);

@@ -8,7 +8,7 @@
 //     therefore the sign the double-precision evaluation gives; otherwise the decision is
 //     recomputed in double precision.  The decisions are thus those of FP64 evaluation.
 //   * The shape parameter eta of Table k3 (a ratio of two cancelling differences) is evaluated
-//     either in FP64 (eta_eval 0: exact FP64 numerator and denominator, FP64 division) or from
+//     either in FP64 (eta_eval 0: exact FP64 numerator and denominator, FP64 Newton quotient) or from
 //     the exactly computed numerator and denominator as float pairs with a double-float
 //     quotient (eta_eval 1: ~2^-46 relative, no FP64 instruction).  Both are rounded once to
 //     float for the perturbed coefficients c_rj + q_rj eta.
@@ -23,7 +23,7 @@
 namespace npw {
 namespace fast {
 
-// float copies of the method parameters, converted once per thread
+// float copies of the method parameters (rounded on the host)
 struct FParams {
     float eps_weno, eps_M_f, eta_guard, eta_max;
     double eps_M;
@@ -31,10 +31,10 @@ struct FParams {
 };
 __device__ __forceinline__ FParams fparams(const MethodParams& mp) {
     FParams f;
-    f.eps_weno = (float)mp.eps_weno;
-    f.eps_M_f = (float)mp.eps_M;
-    f.eta_guard = (float)mp.eta_guard;
-    f.eta_max = (float)mp.eta_max;
+    f.eps_weno = mp.eps_weno_f;
+    f.eps_M_f = mp.eps_M_f;
+    f.eta_guard = mp.eta_guard_f;
+    f.eta_max = mp.eta_max_f;
     f.eps_M = mp.eps_M;
     f.scheme = mp.scheme;
     f.rbf = mp.rbf;
@@ -164,19 +164,61 @@ __device__ __forceinline__ int eno_choice_f(float c0, float c1, float c2, float 
 // ---------------------------------------------------------------------------------------
 // Shape parameter.  num = w0 - 3 w1 + 3 w2 - w3, den = w0 - 15 w1 + 15 w2 - w3 (Table k3).
 // ---------------------------------------------------------------------------------------
-// Exact IEEE 754 format changes done with integer operations, so that they do not occupy
-// the FP64 pipe (on GB300 a float<->double conversion costs an FP64-pipe slot).
-// widen: binary32 -> binary64 is exact: same sign, exponent rebiased by 1023 - 127 = 896,
-// mantissa shifted left by 52 - 23 = 29 bits.  Zeros are handled here; subnormal, infinite
-// and NaN inputs take the hardware conversion.
+// IEEE 754 format changes done with integer operations only, without a branch that could
+// hold a hardware conversion, so that none of them occupies the FP64 pipe (on GB300 a
+// float<->double conversion takes FP64-pipe slots like an FP64 add).
+//
+// widen: binary32 -> binary64, exact.  A normal number keeps sign and fraction (shifted left
+// by 52 - 23 = 29 bits) and its exponent is rebiased by 1023 - 127 = 896.  A subnormal f 2^-149
+// is normalised with a leading-zero count (its leading one at bit p = 31 - clz(f) gives the
+// exponent p - 149, biased 905 - clz(f)); zero stays a signed zero (clz = 32 shifts f out);
+// infinities and NaNs keep exponent 2047 and their fraction.
 __device__ __forceinline__ double widen(float x) {
     const uint32_t b = __float_as_uint(x);
     const uint32_t e = (b >> 23) & 0xFFu;
-    if ((b << 1) == 0u) return __longlong_as_double((long long)((uint64_t)(b >> 31) << 63));
-    if (e == 0u || e == 255u) return (double)x;
-    const uint64_t bits = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)bits);
+    uint32_t f = b & 0x7FFFFFu, E;
+    if (e == 0u) {
+        const int lz = __clz(f);
+        E = f != 0u ? (uint32_t)(905 - lz) : 0u;
+        f = (f << ((lz - 8) & 31)) & 0x7FFFFFu;
+    } else {
+        E = e == 255u ? 2047u : e + 896u;
+    }
+    return __hiloint2double((int)((b & 0x80000000u) | (E << 20) | (f >> 3)), (int)(f << 29));
 }
+
+// narrow: a finite binary64 value to the nearest binary32 (ties away from zero: the fraction
+// is rounded by adding half a unit of bit 29 and truncating; a carry out of the fraction
+// raises the exponent, which is the correct result).  Magnitudes below the float normal range
+// (2^-126) give a signed zero and magnitudes beyond it a signed infinity.  Callers pass
+// finite values only.
+__device__ __forceinline__ float narrow(double v) {
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const uint64_t m = (b & 0x7FFFFFFFFFFFFFFFull) + (1ull << 28);
+    const uint32_t E = (uint32_t)(m >> 52);
+    // bits 29..60 of m: the 23 fraction bits and the low 9 exponent bits; subtracting 896 from
+    // the exponent field modulo 2^9 leaves E - 896, exact for E in [897, 1150]
+    uint32_t f = (uint32_t)(m >> 29) - (896u << 23);
+    f = E < 897u ? 0u : (E > 1150u ? 0x7F800000u : f);
+    return __uint_as_float(f | ((uint32_t)(b >> 32) & 0x80000000u));
+}
+
+// seed_f: a binary64 value whose magnitude lies in [2^-99, 2^99) truncated to binary32
+// (relative error below 2^-23), for a reciprocal seed; false outside that range (zero,
+// subnormal, huge, infinite or NaN), where the caller divides in double instead.
+__device__ __forceinline__ bool seed_f(double v, float* out) {
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const uint32_t E = (uint32_t)(b >> 52) & 0x7FFu;
+    *out = __uint_as_float(((uint32_t)(b >> 29) - (896u << 23)) | ((uint32_t)(b >> 32) & 0x80000000u));
+    return E - 924u < 198u;
+}
+
+// The rare branches below are kept out of line: a call is executed only when taken, while an
+// inlined short branch may be turned into predicated instructions that take issue slots of
+// the FP64 pipe on every evaluation.
+static __device__ __noinline__ float div_rn_f(double num, double den) { return (float)(num / den); }
+static __device__ __noinline__ double div_d(double num, double den) { return num / den; }
+
 // Numerator a + 3b and denominator a + 15b (a = w0 - w3, b = w2 - w1) as unevaluated float
 // pairs.  The differences are exact two_sum pairs, the products 3 bh and 15 bh are split
 // exactly by fma and the leading terms are added with two_sum; the remaining small terms
@@ -198,27 +240,26 @@ __device__ __forceinline__ void eta_pairs(float w0, float w1, float w2, float w3
 
 // FP64 evaluation of the quotient.  Numerator and denominator come from the float pairs of
 // eta_pairs, widened exactly and added in double, and eps_M is added in double.  The
-// quotient is the Newton-Raphson reciprocal iteration in double: from the float seed
-// r0 = 1 / fl(den) (relative error < 2^-23), one step r1 = r0 + r0 (1 - den r0) leaves
-// |r1 den - 1| < 2^-45, and q = num r1 is within ~2^-45 of the quotient, far below the
-// rounding to float that follows (it can differ from the correctly rounded float only when
-// the quotient lies within 2^-45 of a rounding boundary).  FP64-pipe instructions: 3 adds
-// (numerator, denominator, eps_M), 2 multiply-adds (the Newton step), 1 multiply and 2
-// conversions (the seed's argument and the result).
+// quotient is the Newton-Raphson reciprocal iteration in double: the seed r0 is the fast float
+// reciprocal of den truncated to float (|1 - den r0| < 2^-21); with e = 1 - den r0 (one
+// multiply-add) and q0 = num r0, the quotient num r0 (1 + e) = (num / den)(1 - e^2) is within
+// 2^-42 of num / den before the rounding to float.  FP64-pipe instructions: 3 adds (numerator,
+// denominator, eps_M), 1 multiply and 2 multiply-adds; the format changes are integer work.
 __device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3, const FParams& fp, float guard) {
     float nh, nl, dh, dl;
     eta_pairs(w0, w1, w2, w3, nh, nl, dh, dl);
     if (guard > 0.0f && fabsf(dh + dl) <= guard * (1.0f + 2.0f * kU)) {
         // near or below the guard: decide in double
-        if (fabs(widen(dh) + widen(dl)) <= (double)guard) return 0.0f;
+        if (fabs(widen(dh) + widen(dl)) <= widen(guard)) return 0.0f;
     }
     const double num = widen(nh) + widen(nl);
     const double den = (widen(dh) + widen(dl)) + fp.eps_M;
-    const float denf = (float)den;
-    if (!(fabsf(denf) > 1e-30f && fabsf(denf) < 1e30f)) return (float)(num / den);
-    double r = widen(1.0f / denf);
-    r = fma(r, fma(-den, r, 1.0), r);
-    return (float)(num * r);
+    float denf;
+    if (!seed_f(den, &denf)) return div_rn_f(num, den);
+    const double r0 = widen(__fdividef(1.0f, denf));
+    const double q0 = num * r0;
+    const double e = fma(-den, r0, 1.0);
+    return narrow(fma(q0, e, q0));
 }
 
 // Double-float evaluation (no FP64 instruction): the pairs of eta_pairs, eps_M added by
@@ -371,33 +412,55 @@ __device__ __forceinline__ float cell_value_k2_f(const float* c, int side, float
 // Both shape parameters of one face value of a k = 2 cell (the central row's and the
 // extrapolating rows'), in FP64 from the float cell averages c[0..2] = cells i-1..i+1: the
 // numerators and the denominator of Table k2 (with the transverse term of the 5-cell cross,
-// Sec. 6) formed in double, the guard of R12 as in the FP64 path, and the quotient by one
-// reciprocal shared by both: a float seed of 1 / fl(den), one Newton step in double (relative
-// error ~2^-45 before the rounding to float), and the products.  The bound eta_max is applied
-// to the rounded values.
-__device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double trans, const MethodParams& mp, float* ec,
-                                            float* ex) {
-    const double a = widen(side == 0 ? cf[0] : cf[2]);
-    const double b = widen(cf[1]);
-    const double d = widen(side == 0 ? cf[2] : cf[0]);
-    const double base = (-a + 2.0 * b) - d;
-    const double den0 = (-a + 5.0 * b) + 2.0 * d;
+// Sec. 6) formed in double, the guard of R12 with the decision of the FP64 path, and the
+// quotients by one reciprocal shared by both.
+//   * The guard compares |den0| with eta_guard (|a| + 5|b| + 2|d|).  It is first taken in float
+//     with a bound on the rounding of both sides (each below 3u of the magnitude sum, and the
+//     double evaluation within 2^-52 of it): only a float margin smaller than that bound sends
+//     the test to double, so the outcome is the FP64 path's.
+//   * With r0 the fast float reciprocal of den truncated to float (|1 - den r0| < 2^-21) and
+//     e = 1 - den r0, each quotient is q0 (1 + e) with q0 = num r0, within 2^-42 of num / den.
+//   * The factor 2 of the multiquadric row is applied to the rounded float value (exact).
+// FP64-pipe instructions per face value: 4 for the numerator and the denominator, 1 for eps_M,
+// 1 for e and 2 per quotient (6 more on the cross: its two numerators).
+__device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double trans, const MethodParams& mp,
+                                            const FParams& fp, float* ec, float* ex) {
+    const float af = side == 0 ? cf[0] : cf[2], bf = cf[1], df = side == 0 ? cf[2] : cf[0];
     *ec = *ex = 0.0f;
-    if (mp.eta_guard > 0.0 && fabs(den0) <= mp.eta_guard * ((fabs(a) + 5.0 * fabs(b)) + 2.0 * fabs(d))) return;
-    const double den = den0 + mp.eps_M;
-    const double F = mp.rbf == NPW_RBF_GA_ ? 1.0 : 2.0;
-    const float denf = (float)den;
-    double rF;
-    if (fabsf(denf) > 1e-30f && fabsf(denf) < 1e30f) {
-        double r = widen(1.0f / denf);
-        r = fma(r, fma(-den, r, 1.0), r);
-        rF = F * r;
-    } else {
-        rF = F / den;
+    const double a = widen(af), b = widen(bf), d = widen(df);
+    const double den0 = (-a + 5.0 * b) + 2.0 * d;
+    if (fp.eta_guard > 0.0f) {
+        const float magf = (fabsf(af) + 5.0f * fabsf(bf)) + 2.0f * fabsf(df);
+        const float den0f = fmaf(2.0f, df, fmaf(5.0f, bf, -af));
+        const float gm = fp.eta_guard * magf;
+        if (!(fabsf(den0f) > gm + kE * magf * (1.0f + fp.eta_guard))) {
+            if (fabs(den0) <= mp.eta_guard * ((fabs(a) + 5.0 * fabs(b)) + 2.0 * fabs(d))) return;
+        }
     }
-    const float vc = (float)(fma(-0.25, trans, base) * rF);
-    const float vx = trans == 0.0 ? vc : (float)(fma(0.125, trans, base) * rF);
-    const float bound = (float)mp.eta_max;
+    const double base = (-a + 2.0 * b) - d;
+    const double den = den0 + mp.eps_M;
+    float denf, vc, vx;
+    if (seed_f(den, &denf)) {
+        const double r0 = widen(__fdividef(1.0f, denf));
+        const double e = fma(-den, r0, 1.0);
+        const double nc = fma(-0.25, trans, base);
+        const double qc = nc * r0;
+        vc = narrow(fma(qc, e, qc));
+        if (trans == 0.0) {
+            vx = vc;
+        } else {
+            const double qx = fma(0.125, trans, base) * r0;
+            vx = narrow(fma(qx, e, qx));
+        }
+    } else {
+        vc = div_rn_f(fma(-0.25, trans, base), den);
+        vx = trans == 0.0 ? vc : div_rn_f(fma(0.125, trans, base), den);
+    }
+    if (mp.rbf != NPW_RBF_GA_) {
+        vc *= 2.0f;
+        vx *= 2.0f;
+    }
+    const float bound = fp.eta_max;
     *ec = (bound > 0.0f && fabsf(vc) > bound) ? 0.0f : vc;
     *ex = (bound > 0.0f && fabsf(vx) > bound) ? 0.0f : vx;
 }
@@ -410,8 +473,8 @@ __device__ __forceinline__ void cell_recon_k2(const float* c3, double trans, con
     float e0c = 0.0f, e0x = 0.0f, e1c = 0.0f, e1x = 0.0f;
     if ((fp.scheme == NPW_RBF_ENO_ || fp.scheme == NPW_RBF_WENO_) &&
         !(fp.monotone_switch && switch_k2_f(c3[0], c3[1], c3[2]))) {
-        eta_k2_pair(c3, 0, trans, mp0, &e0c, &e0x);
-        eta_k2_pair(c3, 1, trans, mp0, &e1c, &e1x);
+        eta_k2_pair(c3, 0, trans, mp0, fp, &e0c, &e0x);
+        eta_k2_pair(c3, 1, trans, mp0, fp, &e1c, &e1x);
     }
     int r;
     *vm = cell_value_k2_f(c3, 0, e0c, e0x, fp, &r);
@@ -429,11 +492,11 @@ __device__ __forceinline__ uint32_t face_field_k2(const float* w, const MethodPa
         if (fp.monotone_switch && switch_k2_f(w[1], w[2], w[3]))
             fl |= 1u;
         else
-            eta_k2_pair(w + 1, 0, tl, mp0, &el, &elx);
+            eta_k2_pair(w + 1, 0, tl, mp0, fp, &el, &elx);
         if (fp.monotone_switch && switch_k2_f(w[2], w[3], w[4]))
             fl |= 8u;
         else
-            eta_k2_pair(w + 2, 1, tr, mp0, &er, &erx);
+            eta_k2_pair(w + 2, 1, tr, mp0, fp, &er, &erx);
     }
     int rl = 0, rr = 0;
     *vm = cell_value_k2_f(w + 1, 0, el, elx, fp, &rl);
@@ -475,7 +538,7 @@ __device__ __forceinline__ bool face_all(const R* S, const MethodParams& mp, R* 
                                          const D* T = nullptr) {
     if (CHAR) {
         R Rm[3][3], Lm[3][3];
-        if (!euler_eig<R>(S + 2 * M, S + 3 * M, R(mp.gamma), Rm, Lm)) return false;
+        if (!euler_eig<R>(S + 2 * M, S + 3 * M, mp_val<R>(mp.gamma, mp.gamma_f), Rm, Lm)) return false;
         R wm[3], wp[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {

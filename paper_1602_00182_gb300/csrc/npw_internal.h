@@ -37,7 +37,21 @@ struct MethodParams {
     double inflow[4];
     double eta_guard;  // resolved threshold (0 = off)
     double eta_max;    // resolved bound on |eta| (0 = off)
+    // the same values rounded once to float on the host, for the float state (a conversion
+    // in the kernels would take FP64-pipe slots)
+    float eps_weno_f, eps_M_f, eta_guard_f, eta_max_f;
+    float gamma_f, adv_speed_f, adv_speed_y_f;
+    float inflow_f[4];
 };
+
+// a method parameter in the arithmetic type R: the double value, or its float copy
+template <typename R>
+__host__ __device__ __forceinline__ R mp_val(double d, float f) {
+    if constexpr (sizeof(R) == sizeof(float))
+        return f;
+    else
+        return R(d);
+}
 
 // One 1D problem (device copy of npw_instance plus its tile range).
 struct InstDev {

@@ -87,6 +87,34 @@ __device__ __forceinline__ double block_max_nan(double v, bool bad, double* red,
     return out;  // valid in thread 0
 }
 
+// The same maximum over float values (exact, so equal to the maximum of their widened
+// values), taken with float comparisons; one conversion of the result in thread 0.
+__device__ __forceinline__ double block_max_nan_f(float v, bool bad, float* red, int* redbad) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        red[warp] = v;
+        redbad[warp] = b != 0u;
+    }
+    __syncthreads();
+    double out = 0.0;
+    if (threadIdx.x == 0) {
+        float m = 0.0f;
+        int anybad = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            m = red[w] > m ? red[w] : m;
+            anybad |= redbad[w];
+        }
+        out = anybad ? __longlong_as_double(0x7ff8000000000000ll) : (double)m;
+    }
+    return out;  // valid in thread 0
+}
+
 // ---------------------------------------------------------------------------------------
 // time control, executed by one thread for one instance
 // ---------------------------------------------------------------------------------------
@@ -332,8 +360,9 @@ template <int KIND, int K>
 __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a) {
     constexpr int M = kind_m<KIND>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
+    __shared__ float red[32];
     __shared__ int redbad[32];
+    __shared__ float s_lam;
     const int span_max = a.tile + 6;
     float* su = reinterpret_cast<float*>(smem_raw);
     float* se = su + span_max * M;
@@ -360,14 +389,14 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
         const int64_t g = line_idx(n, (int64_t)c0 - 3 + j, in.bc);
         float x;
         if (g < 0)
-            x = (float)a.mp.inflow[k];
+            x = a.mp.inflow_f[k];
         else if (stage == 0)
             x = sn[k * n + g];
         else
             x = u[k * n + g] + (stage == 1 ? d1[k * n + g] : d2[k * n + g]);
         su[j * M + k] = x;
     }
-    const double dt = *(volatile double*)&ctl->dt;
+    if (threadIdx.x == 0) s_lam = (float)(*(volatile double*)&ctl->dt / in.dx);
     const float alpha = (float)*(volatile double*)&ctl->alpha;
     const fast::FParams fp = fast::fparams(a.mp);
     __syncthreads();
@@ -398,7 +427,7 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
     }
     __syncthreads();
     // U: cells
-    const float lam = (float)(dt / in.dx);
+    const float lam = s_lam;
     float vmaxf = 0.0f;
     bool bad = false;
     for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
@@ -436,7 +465,7 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
         }
     }
     if (stage == 2 && a.advance) {
-        const double b = block_max_nan((double)vmaxf, bad, red, redbad);
+        const double b = block_max_nan_f(vmaxf, bad, red, redbad);
         if (threadIdx.x == 0) {
             atomicMax(&ctl->alpha_next_bits, (unsigned long long)__double_as_longlong(b));
             __threadfence();
@@ -488,10 +517,9 @@ template <int KIND, int K>
 __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) {
     constexpr int M = kind_m<KIND>();
     extern __shared__ __align__(16) float smf[];
-    __shared__ double red[32];
+    __shared__ float red[32];
     __shared__ int redbad[32];
-    __shared__ double s_dt;
-    __shared__ float s_alpha;
+    __shared__ float s_alpha, s_lam;
     __shared__ int s_done;
     const int inst_idx = a.list[blockIdx.x];
     const InstDev in = a.inst[inst_idx];
@@ -512,7 +540,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
     }
     float inflow[M];
 #pragma unroll
-    for (int k = 0; k < M; ++k) inflow[k] = (float)a.mp.inflow[k];
+    for (int k = 0; k < M; ++k) inflow[k] = a.mp.inflow_f[k];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int per = (n + nwarps - 1) / nwarps;
     const int lo = min(n, warp * per), hi = min(n, lo + per);
@@ -536,7 +564,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
     int64_t steps = 0;
     int last = 0, status = 0;
     {
-        const double b = block_max_nan((double)vmaxf, bad, red, redbad);
+        const double b = block_max_nan_f(vmaxf, bad, red, redbad);
         if (threadIdx.x == 0) {
             if (!(b - b == 0.0)) {
                 status = NPW_ENONFINITE;
@@ -551,14 +579,14 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
                     last = 1;
                 }
             }
-            s_dt = dt;
+            s_lam = (float)(dt / in.dx);
             s_alpha = (float)alpha;
         }
         __syncthreads();
     }
 
     while (!s_done) {
-        const float lam = (float)(s_dt / in.dx);
+        const float lam = s_lam;
         const float alphaf = s_alpha;
         vmaxf = 0.0f;
         bad = false;
@@ -658,7 +686,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
             un = uA;
             uA = tmp;
         }
-        const double b = block_max_nan((double)vmaxf, bad, red, redbad);
+        const double b = block_max_nan_f(vmaxf, bad, red, redbad);
         if (threadIdx.x == 0) {
             steps += 1;
             t = last ? in.t_end : t + dt;
@@ -677,7 +705,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
                         dt = in.t_end - t;
                         last = 1;
                     }
-                    s_dt = dt;
+                    s_lam = (float)(dt / in.dx);
                     s_alpha = (float)alpha;
                 }
             }
@@ -810,8 +838,8 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
             fl_idx = cx >= 0 ? qy * (TX_2D + 1) + cx : -1;
             fr_idx = cx < TX_2D ? qy * (TX_2D + 1) + cx + 1 : -1;
             if (cross)
-                trans = ((double)NPW_SU(cx + 3, qy + 2, k) - 2.0 * (double)NPW_SU(cx + 3, qy + 3, k)) +
-                        (double)NPW_SU(cx + 3, qy + 4, k);
+                trans = (fast::widen(NPW_SU(cx + 3, qy + 2, k)) - 2.0 * fast::widen(NPW_SU(cx + 3, qy + 3, k))) +
+                        fast::widen(NPW_SU(cx + 3, qy + 4, k));
         } else {
             const int g = c - NCX;
             const int qx = g / (TY_2D + 2), cy = g - qx * (TY_2D + 2) - 1;
@@ -820,8 +848,8 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
             fl_idx = cy >= 0 ? NFX + cy * TX_2D + qx : -1;
             fr_idx = cy < TY_2D ? NFX + (cy + 1) * TX_2D + qx : -1;
             if (cross)
-                trans = ((double)NPW_SU(qx + 2, cy + 3, k) - 2.0 * (double)NPW_SU(qx + 3, cy + 3, k)) +
-                        (double)NPW_SU(qx + 4, cy + 3, k);
+                trans = (fast::widen(NPW_SU(qx + 2, cy + 3, k)) - 2.0 * fast::widen(NPW_SU(qx + 3, cy + 3, k))) +
+                        fast::widen(NPW_SU(qx + 4, cy + 3, k));
         }
         float vm, vp;
         if constexpr (K == 3) {
