@@ -304,10 +304,10 @@ class npw_profile(ctypes.Structure):
 
 
 # FP64-pipe instructions of one shape-parameter evaluation in the mixed path (eta_fp64 in
-# csrc/npw_fast.cuh): 3 adds (numerator and denominator pairs to double, eps_M), 1 multiply
-# and 2 multiply-adds (the Newton-corrected quotient); the format changes between float and
-# double (the pairs, the seed, the result) are integer operations.
-FP64_OPS_PER_ETA = 6
+# csrc/npw_fast.cuh): 2 adds (the numerator pair and the denominator pair, which carries
+# eps_M, to double), 1 multiply and 2 multiply-adds (the Newton-corrected quotient); the
+# format changes between float and double (the pairs, the seed, the result) are integer work.
+FP64_OPS_PER_ETA = 5
 # FP64 pipe peak: 1.25 TFLOP/s nominal FP64 = 0.625e12 FMA/s over 152 SMs at 2.07 GHz, i.e.
 # 2 FP64-pipe instructions per clock per SM (a probe of independent DFMA chains measured 1.19 TFLOP/s)
 FP64_PIPE_PEAK = 2.0 * 152 * 2.07e9

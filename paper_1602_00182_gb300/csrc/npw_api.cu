@@ -95,6 +95,7 @@ npw::MethodParams method(const npw_params* p) {
     mp.eta_max = p->eta_max > 0.0 ? p->eta_max : (p->eta_max == 0.0 ? 1.0 : 0.0);
     mp.eps_weno_f = (float)mp.eps_weno;
     mp.eps_M_f = (float)mp.eps_M;
+    mp.eps_M_lo_f = (float)(mp.eps_M - (double)mp.eps_M_f);
     mp.eta_guard_f = (float)mp.eta_guard;
     mp.eta_max_f = (float)mp.eta_max;
     mp.gamma_f = (float)mp.gamma;

@@ -25,7 +25,7 @@ namespace fast {
 
 // float copies of the method parameters (rounded on the host)
 struct FParams {
-    float eps_weno, eps_M_f, eta_guard, eta_max;
+    float eps_weno, eps_M_f, eps_M_lo, eta_guard, eta_max;
     double eps_M;
     int scheme, rbf, monotone_switch, switch_variant, eta_eval;
 };
@@ -33,6 +33,7 @@ __device__ __forceinline__ FParams fparams(const MethodParams& mp) {
     FParams f;
     f.eps_weno = mp.eps_weno_f;
     f.eps_M_f = mp.eps_M_f;
+    f.eps_M_lo = mp.eps_M_lo_f;
     f.eta_guard = mp.eta_guard_f;
     f.eta_max = mp.eta_max_f;
     f.eps_M = mp.eps_M;
@@ -187,6 +188,26 @@ __device__ __forceinline__ double widen(float x) {
     return __hiloint2double((int)((b & 0x80000000u) | (E << 20) | (f >> 3)), (int)(f << 29));
 }
 
+// Zero or a normal number (neither subnormal, infinite nor NaN).
+__device__ __forceinline__ bool zero_or_normal(float x) {
+    const uint32_t t = __float_as_uint(x) & 0x7FFFFFFFu;
+    return (t == 0u) | (t - 0x00800000u < 0x7F000000u);
+}
+
+// widen for a zero or normal x (the common case): the exponent field is rebiased in place.
+__device__ __forceinline__ double widen_nz(float x) {
+    const uint32_t b = __float_as_uint(x), t = b & 0x7FFFFFFFu;
+    const uint32_t hi = t != 0u ? (t >> 3) + (896u << 20) : 0u;
+    return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(b << 29));
+}
+template <bool NZ>
+__device__ __forceinline__ double widen_as(float x) {
+    if constexpr (NZ)
+        return widen_nz(x);
+    else
+        return widen(x);
+}
+
 // narrow: a finite binary64 value to the nearest binary32 (ties away from zero: the fraction
 // is rounded by adding half a unit of bit 29 and truncating; a carry out of the fraction
 // raises the exponent, which is the correct result).  Magnitudes below the float normal range
@@ -211,6 +232,11 @@ __device__ __forceinline__ bool seed_f(double v, float* out) {
     const uint32_t E = (uint32_t)(b >> 52) & 0x7FFu;
     *out = __uint_as_float(((uint32_t)(b >> 29) - (896u << 23)) | ((uint32_t)(b >> 32) & 0x80000000u));
     return E - 924u < 198u;
+}
+
+// |e| < 2^-20 (a biased exponent below 1023 - 20), read from the bits of e
+__device__ __forceinline__ bool below_2m20(double e) {
+    return ((uint32_t)((uint64_t)__double_as_longlong(e) >> 52) & 0x7FFu) < 1003u;
 }
 
 // The rare branches below are kept out of line: a call is executed only when taken, while an
@@ -239,12 +265,30 @@ __device__ __forceinline__ void eta_pairs(float w0, float w1, float w2, float w3
 }
 
 // FP64 evaluation of the quotient.  Numerator and denominator come from the float pairs of
-// eta_pairs, widened exactly and added in double, and eps_M is added in double.  The
+// eta_pairs, with eps_M (as its float pair, within 2^-48 of the double value) folded into the
+// denominator pair by two_sum; each pair is widened exactly and summed by one FP64 add.  The
 // quotient is the Newton-Raphson reciprocal iteration in double: the seed r0 is the fast float
 // reciprocal of den truncated to float (|1 - den r0| < 2^-21); with e = 1 - den r0 (one
 // multiply-add) and q0 = num r0, the quotient num r0 (1 + e) = (num / den)(1 - e^2) is within
-// 2^-42 of num / den before the rounding to float.  FP64-pipe instructions: 3 adds (numerator,
-// denominator, eps_M), 1 multiply and 2 multiply-adds; the format changes are integer work.
+// 2^-42 of num / den before the rounding to float.  FP64-pipe instructions: 2 adds (numerator,
+// denominator), 1 multiply and 2 multiply-adds; the format changes are integer work.
+// NZ: the four pair components are zero or normal (the cheaper widening applies); the other
+// case, possible only for cell averages below 2^-100 in magnitude or not finite, takes the
+// same arithmetic out of line.
+template <bool NZ>
+__device__ __forceinline__ float eta_quot(float nh, float nl, float eh, float el) {
+    const double num = widen_as<NZ>(nh) + widen_as<NZ>(nl);
+    const double den = widen_as<NZ>(eh) + widen_as<NZ>(el);
+    float denf;
+    if (!seed_f(den, &denf)) return div_rn_f(num, den);
+    const double r0 = widen_nz(__fdividef(1.0f, denf));  // |r0| in (2^-99, 2^99]: normal
+    const double q0 = num * r0;
+    const double e = fma(-den, r0, 1.0);
+    return narrow(fma(q0, e, q0));
+}
+static __device__ __noinline__ float eta_quot_any(float nh, float nl, float eh, float el) {
+    return eta_quot<false>(nh, nl, eh, el);
+}
 __device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3, const FParams& fp, float guard) {
     float nh, nl, dh, dl;
     eta_pairs(w0, w1, w2, w3, nh, nl, dh, dl);
@@ -252,14 +296,12 @@ __device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3
         // near or below the guard: decide in double
         if (fabs(widen(dh) + widen(dl)) <= widen(guard)) return 0.0f;
     }
-    const double num = widen(nh) + widen(nl);
-    const double den = (widen(dh) + widen(dl)) + fp.eps_M;
-    float denf;
-    if (!seed_f(den, &denf)) return div_rn_f(num, den);
-    const double r0 = widen(__fdividef(1.0f, denf));
-    const double q0 = num * r0;
-    const double e = fma(-den, r0, 1.0);
-    return narrow(fma(q0, e, q0));
+    float eh, et;
+    two_sum(dh, fp.eps_M_f, eh, et);
+    const float el = dl + (et + fp.eps_M_lo);
+    if (!(zero_or_normal(nh) & zero_or_normal(nl) & zero_or_normal(eh) & zero_or_normal(el)))
+        return eta_quot_any(nh, nl, eh, el);
+    return eta_quot<true>(nh, nl, eh, el);
 }
 
 // Double-float evaluation (no FP64 instruction): the pairs of eta_pairs, eps_M added by
@@ -423,11 +465,11 @@ __device__ __forceinline__ float cell_value_k2_f(const float* c, int side, float
 //   * The factor 2 of the multiquadric row is applied to the rounded float value (exact).
 // FP64-pipe instructions per face value: 4 for the numerator and the denominator, 1 for eps_M,
 // 1 for e and 2 per quotient (6 more on the cross: its two numerators).
-__device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double trans, const MethodParams& mp,
+template <bool NZ>
+__device__ __forceinline__ void eta_k2_eval(float af, float bf, float df, double trans, const MethodParams& mp,
                                             const FParams& fp, float* ec, float* ex) {
-    const float af = side == 0 ? cf[0] : cf[2], bf = cf[1], df = side == 0 ? cf[2] : cf[0];
     *ec = *ex = 0.0f;
-    const double a = widen(af), b = widen(bf), d = widen(df);
+    const double a = widen_as<NZ>(af), b = widen_as<NZ>(bf), d = widen_as<NZ>(df);
     const double den0 = (-a + 5.0 * b) + 2.0 * d;
     if (fp.eta_guard > 0.0f) {
         const float magf = (fabsf(af) + 5.0f * fabsf(bf)) + 2.0f * fabsf(df);
@@ -439,9 +481,11 @@ __device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double tr
     }
     const double base = (-a + 2.0 * b) - d;
     const double den = den0 + mp.eps_M;
+    // seed from den truncated to float: the float denominator den0f may have cancelled where
+    // the cell averages change sign, den has not
     float denf, vc, vx;
     if (seed_f(den, &denf)) {
-        const double r0 = widen(__fdividef(1.0f, denf));
+        const double r0 = widen_nz(__fdividef(1.0f, denf));
         const double e = fma(-den, r0, 1.0);
         const double nc = fma(-0.25, trans, base);
         const double qc = nc * r0;
@@ -463,6 +507,19 @@ __device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double tr
     const float bound = fp.eta_max;
     *ec = (bound > 0.0f && fabsf(vc) > bound) ? 0.0f : vc;
     *ex = (bound > 0.0f && fabsf(vx) > bound) ? 0.0f : vx;
+}
+static __device__ __noinline__ void eta_k2_eval_any(float af, float bf, float df, double trans, const MethodParams& mp,
+                                                    const FParams& fp, float* ec, float* ex) {
+    eta_k2_eval<false>(af, bf, df, trans, mp, fp, ec, ex);
+}
+// NZ fast path when the three cell averages are zero or normal (see eta_quot)
+__device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double trans, const MethodParams& mp,
+                                            const FParams& fp, float* ec, float* ex) {
+    const float af = side == 0 ? cf[0] : cf[2], bf = cf[1], df = side == 0 ? cf[2] : cf[0];
+    if (zero_or_normal(af) & zero_or_normal(bf) & zero_or_normal(df))
+        eta_k2_eval<true>(af, bf, df, trans, mp, fp, ec, ex);
+    else
+        eta_k2_eval_any(af, bf, df, trans, mp, fp, ec, ex);
 }
 
 // Both face values of one k = 2 cell (c3 = cells i-1..i+1, trans its transverse second

@@ -6,7 +6,10 @@
 #include "npw_instantiate.inc"
 
 namespace npw {
-size_t resident_smem_bytes(int64_t n, int m) { return (size_t)m * (size_t)(6 * n + 5) * sizeof(float); }
+// per field: u^n, d1, d2 with their ghost cells, eta (n + 1), v^- and v^+ (n + 2 each)
+size_t resident_smem_bytes(int64_t n, int m) {
+    return (size_t)m * (size_t)(6 * n + 5 + 6 * RES_GHOST) * sizeof(float);
+}
 
 template <int KIND, int K>
 static cudaError_t launch_res(const ResidentArgs& a, int64_t max_n, int threads, cudaStream_t s) {

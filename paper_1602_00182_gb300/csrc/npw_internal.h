@@ -39,7 +39,7 @@ struct MethodParams {
     double eta_max;    // resolved bound on |eta| (0 = off)
     // the same values rounded once to float on the host, for the float state (a conversion
     // in the kernels would take FP64-pipe slots)
-    float eps_weno_f, eps_M_f, eta_guard_f, eta_max_f;
+    float eps_weno_f, eps_M_f, eps_M_lo_f, eta_guard_f, eta_max_f;  // eps_M ~ eps_M_f + eps_M_lo_f
     float gamma_f, adv_speed_f, adv_speed_y_f;
     float inflow_f[4];
 };
@@ -181,6 +181,7 @@ cudaError_t launch_tune_init(R* u, int64_t n, int m, cudaStream_t st);
 
 constexpr int TILE_1D = 1024;     // default cells per CTA tile in the 1D stage kernels
 constexpr int TILE_1D_MIN = 256;  // smallest tile a run may choose (sizes the tile tables)
+constexpr int RES_GHOST = 3;       // ghost cells on each side of the resident kernel's state arrays
 constexpr size_t RESIDENT_SMEM_MAX = 200 * 1024;  // shared memory a resident CTA may use
 constexpr int THREADS_1D = 256;
 constexpr int TX_2D = 32;      // 2D tile

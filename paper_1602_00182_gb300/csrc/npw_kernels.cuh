@@ -513,6 +513,29 @@ __device__ __forceinline__ int res_map(int i, int n, int bc) {
     return i < 0 ? (bc == NPW_BC_INFLOW ? -1 : 0) : (i >= n ? n - 1 : i);
 }
 
+// Store v as cell i of a ghosted array p (p[-3..-1] and p[n..n+2] are the ghost cells, n >= 6)
+// and refresh the ghost cells that copy it: periodic ghosts are cells n-3..n-1 (left) and
+// 0..2 (right); outflow ghosts repeat cells 0 and n-1; the inflow boundary (left) holds
+// inflow_ghost (the inflow value in a state, -0 in an increment, so that u^n + d reproduces
+// the inflow value bit for bit).
+__device__ __forceinline__ void res_store(float* p, int i, int n, int bc, float v, float inflow_ghost) {
+    p[i] = v;
+    if (i >= RES_GHOST && i < n - RES_GHOST) return;
+    if (bc == NPW_BC_PERIODIC) {
+        p[i < RES_GHOST ? i + n : i - n] = v;
+    } else {
+        if (i == 0) {
+            const float gl = bc == NPW_BC_INFLOW ? inflow_ghost : v;
+#pragma unroll
+            for (int j = 1; j <= RES_GHOST; ++j) p[-j] = gl;
+        }
+        if (i == n - 1) {
+#pragma unroll
+            for (int j = 0; j < RES_GHOST; ++j) p[n + j] = v;
+        }
+    }
+}
+
 template <int KIND, int K>
 __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) {
     constexpr int M = kind_m<KIND>();
@@ -525,17 +548,22 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
     const InstDev in = a.inst[inst_idx];
     Ctl* ctl = a.ctl + inst_idx;
     const int n = (int)in.n;
-    float* un = smf;                // [M][n] u^n
-    float* uA = un + M * n;         // [M][n] d1, then the new state
-    float* uB = uA + M * n;         // [M][n] d2
-    float* se = uB + M * n;         // [M][n+1]
+    // u^n, d1 and d2 carry RES_GHOST ghost cells on each side (field k, cell i at k NS + 3 + i),
+    // so that the stencils read them without a boundary map: the boundary cells write the
+    // ghost copies when they are updated (res_store).
+    const int NS = n + 2 * RES_GHOST;
+    float* un = smf;                // [M][NS] u^n
+    float* uA = un + M * NS;        // [M][NS] d1, then the new state
+    float* uB = uA + M * NS;        // [M][NS] d2
+    float* se = uB + M * NS;        // [M][n+1]
     float* svm = se + M * (n + 1);  // [M][n+2]
     float* svp = svm + M * (n + 2); // [M][n+2]
     const fast::FParams fp = fast::fparams(a.mp);
     float* g = reinterpret_cast<float*>(a.arena) + in.off;
     float* cr = a.carry + in.off;
     for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) {
-        un[idx] = g[idx];
+        const int k = idx / n;
+        un[idx + k * 2 * RES_GHOST + RES_GHOST] = g[idx];
         cr[idx] = 0.0f;
     }
     float inflow[M];
@@ -545,6 +573,15 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
     const int per = (n + nwarps - 1) / nwarps;
     const int lo = min(n, warp * per), hi = min(n, lo + per);
     __syncthreads();
+    // ghost cells of u^n
+    if (threadIdx.x < 2 * RES_GHOST * M) {
+        const int k = threadIdx.x / (2 * RES_GHOST), q = threadIdx.x - k * 2 * RES_GHOST;
+        const int gi = q < RES_GHOST ? q - RES_GHOST : n + q - RES_GHOST;
+        const int c = res_map(gi, n, in.bc);
+        const float v = c < 0 ? inflow[k] : un[k * NS + RES_GHOST + c];
+        un[k * NS + RES_GHOST + gi] = v;
+    }
+    __syncthreads();
 
     // alpha^0 and the first dt
     float vmaxf = 0.0f;
@@ -553,7 +590,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
         float U[M];
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-            U[k] = un[k * n + i];
+            U[k] = un[k * NS + RES_GHOST + i];
             bad |= !finite_(U[k]);
         }
         const float sp = wave_speed<float, KIND>(U, a.mp, 0);
@@ -604,10 +641,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
                     for (int k = 0; k < M; ++k) {
                         float w[4];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int c = res_map(f - 2 + j, n, in.bc);
-                            w[j] = c < 0 ? inflow[k] : NPW_X(k * n + c);
-                        }
+                        for (int j = 0; j < 4; ++j) w[j] = NPW_X(k * NS + RES_GHOST + f - 2 + j);
                         uint32_t fl = 0;
                         se[k * (n + 1) + f] = fast::face_eta(w[0], w[1], w[2], w[3], fp, &fl);
                     }
@@ -619,10 +653,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
                     for (int k = 0; k < M; ++k) {
                         float c[5];
 #pragma unroll
-                        for (int j = 0; j < 5; ++j) {
-                            const int cc = res_map(i - 2 + j, n, in.bc);
-                            c[j] = cc < 0 ? inflow[k] : NPW_X(k * n + cc);
-                        }
+                        for (int j = 0; j < 5; ++j) c[j] = NPW_X(k * NS + RES_GHOST + i - 2 + j);
                         float vm, vp;
                         if constexpr (K == 3) {
                             const float er = (i + 1 <= hi) ? se[k * (n + 1) + i + 1] : 0.0f;
@@ -653,20 +684,21 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
 #pragma unroll
                     for (int k = 0; k < M; ++k) {
                         const float du = lam * (hl[k] - hr[k]);
-                        const int ix = k * n + i;
+                        const int ix = k * NS + RES_GHOST + i;
                         if (stage == 0) {
-                            uA[ix] = du;
+                            res_store(uA + k * NS + RES_GHOST, i, n, in.bc, du, -0.0f);
                             U[k] = du;
                         } else if (stage == 1) {
                             const float v = 0.25f * (uA[ix] + du);
-                            uB[ix] = v;
+                            res_store(uB + k * NS + RES_GHOST, i, n, in.bc, v, -0.0f);
                             U[k] = v;
                         } else {
+                            const int gx = k * n + i;
                             const float base = un[ix];
-                            const float y = kTwoThirdsF * (uB[ix] + du) + cr[ix];
+                            const float y = kTwoThirdsF * (uB[ix] + du) + cr[gx];
                             const float t = base + y;
-                            cr[ix] = y - (t - base);
-                            uA[ix] = t;
+                            cr[gx] = y - (t - base);
+                            res_store(uA + k * NS + RES_GHOST, i, n, in.bc, t, inflow[k]);
                             U[k] = t;
                         }
                         bad |= !finite_(U[k]);
@@ -712,7 +744,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
         }
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) g[idx] = un[idx];
+    for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) g[idx] = un[idx + (idx / n) * 2 * RES_GHOST + RES_GHOST];
     if (threadIdx.x == 0) {
         ctl->t = t;
         ctl->dt = dt;
