@@ -452,42 +452,34 @@ __device__ __forceinline__ float cell_value_k2_f(const float* c, int side, float
 }
 
 // Both shape parameters of one face value of a k = 2 cell (the central row's and the
-// extrapolating rows'), in FP64 from the float cell averages c[0..2] = cells i-1..i+1: the
-// numerators and the denominator of Table k2 (with the transverse term of the 5-cell cross,
-// Sec. 6) formed in double, the guard of R12 with the decision of the FP64 path, and the
-// quotients by one reciprocal shared by both.
-//   * The guard compares |den0| with eta_guard (|a| + 5|b| + 2|d|).  It is first taken in float
-//     with a bound on the rounding of both sides (each below 3u of the magnitude sum, and the
-//     double evaluation within 2^-52 of it): only a float margin smaller than that bound sends
-//     the test to double, so the outcome is the FP64 path's.
-//   * With r0 the fast float reciprocal of den truncated to float (|1 - den r0| < 2^-21) and
-//     e = 1 - den r0, each quotient is q0 (1 + e) with q0 = num r0, within 2^-42 of num / den.
+// extrapolating rows'), in FP64 from the float cell averages c[0..2] = cells i-1..i+1, with
+// a, b, d the cells beside, at and across from the face (Table k2; the transverse term of the
+// 5-cell cross of Sec. 6 enters the numerators).
+//   * The guard of R12 compares |den0| with eta_guard (|a| + 5|b| + 2|d|).  It is first taken
+//     in float with a bound on the rounding of both sides (each below 3u of the magnitude sum,
+//     and the double evaluation within 2^-52 of it): only a float margin smaller than that
+//     bound sends the test to double, where it is the FP64 path's expression, so the outcome
+//     is the FP64 path's.
+//   * The numerator (b - a) + (b - d) and the denominator 4b + 2d + (b - a) + eps_M are formed
+//     as float pairs (exact two_sum differences, the leading terms added by two_sum, eps_M as
+//     its float pair), each within ~2^-46 of its largest term, and widened to double by one
+//     FP64 add each.
+//   * One reciprocal serves both quotients: r0, the fast float reciprocal of den truncated to
+//     float (|1 - den r0| < 2^-21), and e = 1 - den r0; each quotient is q0 (1 + e) with
+//     q0 = num r0, within 2^-42 of num / den.
 //   * The factor 2 of the multiquadric row is applied to the rounded float value (exact).
-// FP64-pipe instructions per face value: 4 for the numerator and the denominator, 1 for eps_M,
-// 1 for e and 2 per quotient (6 more on the cross: its two numerators).
+// FP64-pipe instructions per face value: 2 for the pairs, 1 for e and 2 per quotient (on the
+// cross, 2 more for the two numerators).
 template <bool NZ>
-__device__ __forceinline__ void eta_k2_eval(float af, float bf, float df, double trans, const MethodParams& mp,
-                                            const FParams& fp, float* ec, float* ex) {
-    *ec = *ex = 0.0f;
-    const double a = widen_as<NZ>(af), b = widen_as<NZ>(bf), d = widen_as<NZ>(df);
-    const double den0 = (-a + 5.0 * b) + 2.0 * d;
-    if (fp.eta_guard > 0.0f) {
-        const float magf = (fabsf(af) + 5.0f * fabsf(bf)) + 2.0f * fabsf(df);
-        const float den0f = fmaf(2.0f, df, fmaf(5.0f, bf, -af));
-        const float gm = fp.eta_guard * magf;
-        if (!(fabsf(den0f) > gm + kE * magf * (1.0f + fp.eta_guard))) {
-            if (fabs(den0) <= mp.eta_guard * ((fabs(a) + 5.0 * fabs(b)) + 2.0 * fabs(d))) return;
-        }
-    }
-    const double base = (-a + 2.0 * b) - d;
-    const double den = den0 + mp.eps_M;
-    // seed from den truncated to float: the float denominator den0f may have cancelled where
-    // the cell averages change sign, den has not
+__device__ __forceinline__ void eta_k2_quot(float bh, float bl, float dh, float dl, double trans, const FParams& fp,
+                                            float* ec, float* ex) {
+    const double base = widen_as<NZ>(bh) + widen_as<NZ>(bl);
+    const double den = widen_as<NZ>(dh) + widen_as<NZ>(dl);
     float denf, vc, vx;
     if (seed_f(den, &denf)) {
         const double r0 = widen_nz(__fdividef(1.0f, denf));
         const double e = fma(-den, r0, 1.0);
-        const double nc = fma(-0.25, trans, base);
+        const double nc = trans == 0.0 ? base : fma(-0.25, trans, base);
         const double qc = nc * r0;
         vc = narrow(fma(qc, e, qc));
         if (trans == 0.0) {
@@ -500,7 +492,7 @@ __device__ __forceinline__ void eta_k2_eval(float af, float bf, float df, double
         vc = div_rn_f(fma(-0.25, trans, base), den);
         vx = trans == 0.0 ? vc : div_rn_f(fma(0.125, trans, base), den);
     }
-    if (mp.rbf != NPW_RBF_GA_) {
+    if (fp.rbf != NPW_RBF_GA_) {
         vc *= 2.0f;
         vx *= 2.0f;
     }
@@ -508,18 +500,36 @@ __device__ __forceinline__ void eta_k2_eval(float af, float bf, float df, double
     *ec = (bound > 0.0f && fabsf(vc) > bound) ? 0.0f : vc;
     *ex = (bound > 0.0f && fabsf(vx) > bound) ? 0.0f : vx;
 }
-static __device__ __noinline__ void eta_k2_eval_any(float af, float bf, float df, double trans, const MethodParams& mp,
+static __device__ __noinline__ void eta_k2_quot_any(float bh, float bl, float dh, float dl, double trans,
                                                     const FParams& fp, float* ec, float* ex) {
-    eta_k2_eval<false>(af, bf, df, trans, mp, fp, ec, ex);
+    eta_k2_quot<false>(bh, bl, dh, dl, trans, fp, ec, ex);
 }
-// NZ fast path when the three cell averages are zero or normal (see eta_quot)
 __device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double trans, const MethodParams& mp,
                                             const FParams& fp, float* ec, float* ex) {
     const float af = side == 0 ? cf[0] : cf[2], bf = cf[1], df = side == 0 ? cf[2] : cf[0];
-    if (zero_or_normal(af) & zero_or_normal(bf) & zero_or_normal(df))
-        eta_k2_eval<true>(af, bf, df, trans, mp, fp, ec, ex);
+    *ec = *ex = 0.0f;
+    if (fp.eta_guard > 0.0f) {
+        const float magf = (fabsf(af) + 5.0f * fabsf(bf)) + 2.0f * fabsf(df);
+        const float den0f = fmaf(2.0f, df, fmaf(5.0f, bf, -af));
+        const float gm = fp.eta_guard * magf;
+        if (!(fabsf(den0f) > gm + kE * magf * (1.0f + fp.eta_guard))) {
+            const double a = widen(af), b = widen(bf), d = widen(df);
+            if (fabs((-a + 5.0 * b) + 2.0 * d) <= mp.eta_guard * ((fabs(a) + 5.0 * fabs(b)) + 2.0 * fabs(d))) return;
+        }
+    }
+    float p, pe, q, qe, bh, be, s1, e1, s2, e2, dh, dt;
+    two_sum(bf, -af, p, pe);  // b - a
+    two_sum(bf, -df, q, qe);  // b - d
+    two_sum(p, q, bh, be);
+    const float bl = be + (pe + qe);
+    two_sum(4.0f * bf, 2.0f * df, s1, e1);
+    two_sum(s1, p, s2, e2);
+    two_sum(s2, fp.eps_M_f, dh, dt);
+    const float dl = ((e1 + e2) + pe) + (dt + fp.eps_M_lo);
+    if (zero_or_normal(bh) & zero_or_normal(bl) & zero_or_normal(dh) & zero_or_normal(dl))
+        eta_k2_quot<true>(bh, bl, dh, dl, trans, fp, ec, ex);
     else
-        eta_k2_eval_any(af, bf, df, trans, mp, fp, ec, ex);
+        eta_k2_quot_any(bh, bl, dh, dl, trans, fp, ec, ex);
 }
 
 // Both face values of one k = 2 cell (c3 = cells i-1..i+1, trans its transverse second
