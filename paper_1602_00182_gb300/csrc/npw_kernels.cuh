@@ -41,6 +41,14 @@ __device__ __forceinline__ int64_t line_idx(int64_t n, int64_t k, int bc) {
     return k >= n ? n - 1 : k;
 }
 
+// line_idx for a tile halo: k in [-3, n + 2] with n >= 6, so one comparison per side replaces
+// the 64-bit remainder
+__device__ __forceinline__ int64_t halo_idx(int64_t n, int64_t k, int bc) {
+    if (bc == NPW_BC_PERIODIC) return k < 0 ? k + n : (k >= n ? k - n : k);
+    if (k < 0) return bc == NPW_BC_INFLOW ? -1 : 0;
+    return k >= n ? n - 1 : k;
+}
+
 template <typename R>
 __device__ __forceinline__ bool finite_(R x) {
     return x - x == R(0.0);
@@ -383,18 +391,19 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
     float* sn = a.s + in.off;
     float* cr = a.c + in.off;
     const int span = cnt + 6;
-    for (int idx = threadIdx.x; idx < span * M; idx += blockDim.x) {
-        const int k = idx / span;
-        const int j = idx - k * span;
-        const int64_t g = line_idx(n, (int64_t)c0 - 3 + j, in.bc);
-        float x;
-        if (g < 0)
-            x = a.mp.inflow_f[k];
-        else if (stage == 0)
-            x = sn[k * n + g];
-        else
-            x = u[k * n + g] + (stage == 1 ? d1[k * n + g] : d2[k * n + g]);
-        su[j * M + k] = x;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        for (int j = threadIdx.x; j < span; j += blockDim.x) {
+            const int64_t g = halo_idx(n, (int64_t)c0 - 3 + j, in.bc);
+            float x;
+            if (g < 0)
+                x = a.mp.inflow_f[k];
+            else if (stage == 0)
+                x = sn[k * n + g];
+            else
+                x = u[k * n + g] + (stage == 1 ? d1[k * n + g] : d2[k * n + g]);
+            su[j * M + k] = x;
+        }
     }
     if (threadIdx.x == 0) s_lam = (float)(*(volatile double*)&ctl->dt / in.dx);
     const float alpha = (float)*(volatile double*)&ctl->alpha;
@@ -778,6 +787,21 @@ __device__ __forceinline__ R grid_get(const R* u, const Inst2D& in, int64_t i, i
     return u[j * nx + i];
 }
 
+// grid_get for a tile halo: i in [-3, nx + 2] and j in [-3, ny + 2] (nx, ny >= 6), so one
+// comparison per side replaces the general map of grid_get (and its 64-bit remainders)
+__device__ __forceinline__ float halo_get(const float* u, const Inst2D& in, int i, int j, float inflow) {
+    const int nx = (int)in.nx, ny = (int)in.ny;
+    if (in.bc == NPW_BC_PERIODIC) {
+        i = i < 0 ? i + nx : (i >= nx ? i - nx : i);
+        j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
+    } else {
+        if (in.bc == NPW_BC_INFLOW && (i < 0 || j < 0)) return inflow;
+        i = i < 0 ? 0 : (i >= nx ? nx - 1 : i);
+        j = j < 0 ? 0 : (j >= ny ? ny - 1 : j);
+    }
+    return u[(int64_t)j * in.nx + i];
+}
+
 // ---------------------------------------------------------------------------------------
 // 2D stage kernel of the mixed path (float state, component-wise) in phases, each a balanced
 // loop over independent work items:
@@ -801,10 +825,11 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
     __shared__ float ef[(NFX + NFY) * M];    // eta per (face, field); then the fluxes
     __shared__ float vmf[(NFX + NFY) * M];   // v^- per (face, field)
     __shared__ float vpf[(NFX + NFY) * M];   // v^+ per (face, field)
-    __shared__ double red[32];
+    __shared__ float red[32];
     __shared__ int redbad[32];
-    __shared__ double red2[32];
+    __shared__ float red2[32];
     __shared__ int redbad2[32];
+    __shared__ float s_par[5];               // alpha_x, alpha_y, dt, dx, dy in float
     const Inst2D in = *a.inst;
     Ctl* ctl = a.ctl;
     if (*(volatile int32_t*)&ctl->done) return;
@@ -821,15 +846,18 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
         const int by = rem / BX, bx = rem - by * BX;
         // the corners are read only by the 5-cell cross (transverse differences of halo cells)
         const bool corner = (bx < 3 || bx >= TX_2D + 3) && (by < 3 || by >= TY_2D + 3);
-        su[(by * BX + bx) * M + k] = (corner && !cross)
-                                         ? 0.0f
-                                         : grid_get<float>(uin + k * cells, in, (int64_t)tx0 - 3 + bx,
-                                                           (int64_t)ty0 - 3 + by, a.mp.inflow[k]);
+        su[(by * BX + bx) * M + k] =
+            (corner && !cross) ? 0.0f : halo_get(uin + k * cells, in, tx0 - 3 + bx, ty0 - 3 + by, a.mp.inflow_f[k]);
     }
-    const double dt = *(volatile double*)&ctl->dt;
-    const float ax = (float)(*(volatile double*)&ctl->alpha);
-    const float ay = (float)(*(volatile double*)&ctl->alpha_y);
+    if (tid == 0) {
+        s_par[0] = (float)(*(volatile double*)&ctl->alpha);
+        s_par[1] = (float)(*(volatile double*)&ctl->alpha_y);
+        s_par[2] = (float)(*(volatile double*)&ctl->dt);
+        s_par[3] = (float)in.dx;
+        s_par[4] = (float)in.dy;
+    }
     __syncthreads();
+    const float ax = s_par[0], ay = s_par[1];
 #define NPW_SU(bx, by, k) su[((by) * BX + (bx)) * M + (k)]
     // E: item = (face, field); x face (qx, qy) has the eta stencil su[qy+3][qx+1 .. qx+4],
     // y face (qx, qy) su[qy+1 .. qy+4][qx+3]
@@ -915,8 +943,8 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
     // U: one cell per thread (the same arithmetic as stage2d_kernel)
     float* uout = reinterpret_cast<float*>(a.uout) + in.off;
     const float* un = reinterpret_cast<const float*>(a.un) + in.off;
-    const float dtR = (float)dt, dxR = (float)in.dx, dyR = (float)in.dy;
-    double vmx = 0.0, vmy = 0.0;
+    const float dtR = s_par[2], dxR = s_par[3], dyR = s_par[4];
+    float vmx = 0.0f, vmy = 0.0f;
     bool bad = false;
     for (int cidx = tid; cidx < TX_2D * TY_2D; cidx += nthr) {
         const int qy = cidx / TX_2D, qx = cidx - qy * TX_2D;
@@ -944,16 +972,16 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
             bad |= !finite_(o);
         }
         if (a.stage == 2) {
-            const double sx = (double)wave_speed<float, KIND>(U, a.mp, 0);
-            const double sy = (double)wave_speed<float, KIND>(U, a.mp, 1);
+            const float sx = wave_speed<float, KIND>(U, a.mp, 0);
+            const float sy = wave_speed<float, KIND>(U, a.mp, 1);
             bad |= !finite_(sx) || !finite_(sy);
             vmx = sx > vmx ? sx : vmx;
             vmy = sy > vmy ? sy : vmy;
         }
     }
     if (a.stage == 2 && a.advance) {
-        const double bx = block_max_nan(vmx, bad, red, redbad);
-        const double by = block_max_nan(vmy, bad, red2, redbad2);
+        const double bx = block_max_nan_f(vmx, bad, red, redbad);
+        const double by = block_max_nan_f(vmy, bad, red2, redbad2);
         if (tid == 0) {
             atomicMax(&ctl->alpha_next_bits, (unsigned long long)__double_as_longlong(bx));
             atomicMax(&ctl->alpha_y_next_bits, (unsigned long long)__double_as_longlong(by));
