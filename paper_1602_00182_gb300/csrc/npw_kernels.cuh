@@ -564,9 +564,8 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
     float* un = smf;                // [M][NS] u^n
     float* uA = un + M * NS;        // [M][NS] d1, then the new state
     float* uB = uA + M * NS;        // [M][NS] d2
-    float* se = uB + M * NS;        // [M][n+1]
-    float* svm = se + M * (n + 1);  // [M][n+2]
-    float* svp = svm + M * (n + 2); // [M][n+2]
+    float* svm = uB + M * NS;       // [M][n+2] v^- of face i at i
+    float* svp = svm + M * (n + 2); // [M][n+2] v^+ of face i at i + 1
     const fast::FParams fp = fast::fparams(a.mp);
     float* g = reinterpret_cast<float*>(a.arena) + in.off;
     float* cr = a.carry + in.off;
@@ -643,38 +642,55 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
             const float* D = stage == 1 ? uA : uB;
 #define NPW_X(idx) (stage == 0 ? un[(idx)] : un[(idx)] + D[(idx)])
             if (lo < hi) {
-                // F: eta of faces lo..hi (cells f-2..f+1); k = 2 forms its shape parameters per
-                // cell in C instead
-                for (int f = lo + lane; K == 3 && f <= hi; f += 32) {
+                // F and C: eta of faces lo..hi (cells f-2..f+1) and the reconstruction of cells
+                // lo-1..hi (v^- with the eta of face i+1, v^+ with that of face i).  Cell lo-1
+                // contributes only v^- (face lo), cell hi only v^+ (face hi); their other side
+                // belongs to the neighbouring warp and is not written here.
+                if constexpr (K == 3) {
+                    // one pass: lane l of the chunk at base takes face f = base + l and cell
+                    // f - 1, which reads the eta of face f - 1 from lane l - 1 (lane 0: from lane
+                    // 31 of the previous chunk); the five cells f-3..f+1 serve both
+                    float carry[M];
 #pragma unroll
-                    for (int k = 0; k < M; ++k) {
-                        float w[4];
+                    for (int k = 0; k < M; ++k) carry[k] = 0.0f;
+                    for (int base = lo; base <= hi + 1; base += 32) {
+                        const int f = base + lane, i = f - 1;
+                        const bool face_ok = f <= hi, cell_ok = i <= hi;
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) w[j] = NPW_X(k * NS + RES_GHOST + f - 2 + j);
-                        uint32_t fl = 0;
-                        se[k * (n + 1) + f] = fast::face_eta(w[0], w[1], w[2], w[3], fp, &fl);
-                    }
-                }
-                __syncwarp();
-                // C: cells lo-1..hi (v^- uses the eta of face i+1, v^+ that of face i)
-                for (int i = lo - 1 + lane; i <= hi; i += 32) {
+                        for (int k = 0; k < M; ++k) {
+                            float c[5], eta = 0.0f;
+                            if (cell_ok) {
 #pragma unroll
-                    for (int k = 0; k < M; ++k) {
-                        float c[5];
-#pragma unroll
-                        for (int j = 0; j < 5; ++j) c[j] = NPW_X(k * NS + RES_GHOST + i - 2 + j);
-                        float vm, vp;
-                        if constexpr (K == 3) {
-                            const float er = (i + 1 <= hi) ? se[k * (n + 1) + i + 1] : 0.0f;
-                            const float el = (i >= lo) ? se[k * (n + 1) + i] : 0.0f;
-                            fast::cell_recon(c, er, el, fp, &vm, &vp);
-                        } else {
-                            fast::cell_recon_k2(c + 1, 0.0, a.mp, fp, &vm, &vp);
+                                for (int j = 0; j < 5; ++j) c[j] = NPW_X(k * NS + RES_GHOST + i - 2 + j);
+                                if (face_ok) {
+                                    uint32_t fl = 0;
+                                    eta = fast::face_eta(c[1], c[2], c[3], c[4], fp, &fl);
+                                }
+                            }
+                            float eprev = __shfl_up_sync(0xffffffffu, eta, 1);
+                            if (lane == 0) eprev = carry[k];
+                            carry[k] = __shfl_sync(0xffffffffu, eta, 31);
+                            if (cell_ok) {
+                                float vm, vp;
+                                fast::cell_recon(c, eta, i >= lo ? eprev : 0.0f, fp, &vm, &vp);
+                                if (i < hi) svm[k * (n + 2) + i + 1] = vm;
+                                if (i >= lo) svp[k * (n + 2) + i + 1] = vp;
+                            }
                         }
-                        // cell lo-1 contributes only v^- (face lo), cell hi only v^+ (face hi); their
-                        // other side belongs to the neighbouring warp and is not written here
-                        if (i < hi) svm[k * (n + 2) + i + 1] = vm;
-                        if (i >= lo) svp[k * (n + 2) + i + 1] = vp;
+                    }
+                } else {
+                    // k = 2: the shape parameters belong to the cell
+                    for (int i = lo - 1 + lane; i <= hi; i += 32) {
+#pragma unroll
+                        for (int k = 0; k < M; ++k) {
+                            float c[5];
+#pragma unroll
+                            for (int j = 0; j < 5; ++j) c[j] = NPW_X(k * NS + RES_GHOST + i - 2 + j);
+                            float vm, vp;
+                            fast::cell_recon_k2(c + 1, 0.0, a.mp, fp, &vm, &vp);
+                            if (i < hi) svm[k * (n + 2) + i + 1] = vm;
+                            if (i >= lo) svp[k * (n + 2) + i + 1] = vp;
+                        }
                     }
                 }
                 __syncwarp();
