@@ -6,9 +6,9 @@
 #include "npw_instantiate.inc"
 
 namespace npw {
-// per field: u^n, d1, d2 with their ghost cells, v^- and v^+ (n + 2 each)
+// per field: u^n, d1 and d2 with their ghost cells
 size_t resident_smem_bytes(int64_t n, int m) {
-    return (size_t)m * (size_t)(5 * n + 4 + 6 * RES_GHOST) * sizeof(float);
+    return (size_t)m * (size_t)(3 * (n + 2 * RES_GHOST)) * sizeof(float);
 }
 
 template <int KIND, int K>

@@ -564,8 +564,6 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
     float* un = smf;                // [M][NS] u^n
     float* uA = un + M * NS;        // [M][NS] d1, then the new state
     float* uB = uA + M * NS;        // [M][NS] d2
-    float* svm = uB + M * NS;       // [M][n+2] v^- of face i at i
-    float* svp = svm + M * (n + 2); // [M][n+2] v^+ of face i at i + 1
     const fast::FParams fp = fast::fparams(a.mp);
     float* g = reinterpret_cast<float*>(a.arena) + in.off;
     float* cr = a.carry + in.off;
@@ -642,96 +640,90 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
             const float* D = stage == 1 ? uA : uB;
 #define NPW_X(idx) (stage == 0 ? un[(idx)] : un[(idx)] + D[(idx)])
             if (lo < hi) {
-                // F and C: eta of faces lo..hi (cells f-2..f+1) and the reconstruction of cells
-                // lo-1..hi (v^- with the eta of face i+1, v^+ with that of face i).  Cell lo-1
-                // contributes only v^- (face lo), cell hi only v^+ (face hi); their other side
-                // belongs to the neighbouring warp and is not written here.
-                if constexpr (K == 3) {
-                    // one pass: lane l of the chunk at base takes face f = base + l and cell
-                    // f - 1, which reads the eta of face f - 1 from lane l - 1 (lane 0: from lane
-                    // 31 of the previous chunk); the five cells f-3..f+1 serve both
-                    float carry[M];
+                // One pass over the warp's range: lane l of the chunk at base takes
+                //   face f = base + l: its eta (k = 3, cells f-2..f+1);
+                //   cell f - 1: its reconstruction (cells f-3..f+1), v^+ at face f - 1 with the eta
+                //     of face f - 1 (lane l - 1) and v^- at face f with the eta of face f;
+                //   face f - 1: the Lax-Friedrichs flux from v^- of cell f - 2 (lane l - 1) and
+                //     v^+ of cell f - 1;
+                //   cell f - 2: the update from the fluxes of faces f - 2 (lane l - 1) and f - 1.
+                // Lane 0 takes the lane l - 1 values from lane 31 of the previous chunk.  Faces
+                // lo..hi, cells lo-1..hi and the updates of the own cells lo..hi-1 are covered by
+                // f = lo..hi+1; the boundary faces are computed by both neighbouring warps.
+                float c_eta[M], c_vm[M], c_h[M];
 #pragma unroll
-                    for (int k = 0; k < M; ++k) carry[k] = 0.0f;
-                    for (int base = lo; base <= hi + 1; base += 32) {
-                        const int f = base + lane, i = f - 1;
-                        const bool face_ok = f <= hi, cell_ok = i <= hi;
+                for (int k = 0; k < M; ++k) c_eta[k] = c_vm[k] = c_h[k] = 0.0f;
+                for (int base = lo; base <= hi + 1; base += 32) {
+                    const int f = base + lane, i = f - 1, j = f - 2;
+                    const bool face_ok = f <= hi, cell_ok = i <= hi;
+                    float vm[M], vp[M];
 #pragma unroll
-                        for (int k = 0; k < M; ++k) {
-                            float c[5], eta = 0.0f;
-                            if (cell_ok) {
+                    for (int k = 0; k < M; ++k) {
+                        float c[5], eta = 0.0f;
+                        vm[k] = vp[k] = 0.0f;
+                        if (cell_ok) {
 #pragma unroll
-                                for (int j = 0; j < 5; ++j) c[j] = NPW_X(k * NS + RES_GHOST + i - 2 + j);
-                                if (face_ok) {
-                                    uint32_t fl = 0;
-                                    eta = fast::face_eta(c[1], c[2], c[3], c[4], fp, &fl);
-                                }
+                            for (int q = 0; q < 5; ++q) c[q] = NPW_X(k * NS + RES_GHOST + i - 2 + q);
+                            if (K == 3 && face_ok) {
+                                uint32_t fl = 0;
+                                eta = fast::face_eta(c[1], c[2], c[3], c[4], fp, &fl);
                             }
+                        }
+                        if constexpr (K == 3) {
                             float eprev = __shfl_up_sync(0xffffffffu, eta, 1);
-                            if (lane == 0) eprev = carry[k];
-                            carry[k] = __shfl_sync(0xffffffffu, eta, 31);
-                            if (cell_ok) {
-                                float vm, vp;
-                                fast::cell_recon(c, eta, i >= lo ? eprev : 0.0f, fp, &vm, &vp);
-                                if (i < hi) svm[k * (n + 2) + i + 1] = vm;
-                                if (i >= lo) svp[k * (n + 2) + i + 1] = vp;
-                            }
+                            if (lane == 0) eprev = c_eta[k];
+                            c_eta[k] = __shfl_sync(0xffffffffu, eta, 31);
+                            if (cell_ok) fast::cell_recon(c, eta, i >= lo ? eprev : 0.0f, fp, &vm[k], &vp[k]);
+                        } else {
+                            if (cell_ok) fast::cell_recon_k2(c + 1, 0.0, a.mp, fp, &vm[k], &vp[k]);
                         }
                     }
-                } else {
-                    // k = 2: the shape parameters belong to the cell
-                    for (int i = lo - 1 + lane; i <= hi; i += 32) {
+                    // flux of face f - 1
+                    float A[M], h[M], hl[M];
+#pragma unroll
+                    for (int k = 0; k < M; ++k) {
+                        A[k] = __shfl_up_sync(0xffffffffu, vm[k], 1);
+                        if (lane == 0) A[k] = c_vm[k];
+                        c_vm[k] = __shfl_sync(0xffffffffu, vm[k], 31);
+                        h[k] = 0.0f;
+                    }
+                    if (i >= lo && i <= hi) lf_flux<float, KIND, M>(A, vp, alphaf, a.mp, 0, h);
+#pragma unroll
+                    for (int k = 0; k < M; ++k) {
+                        hl[k] = __shfl_up_sync(0xffffffffu, h[k], 1);
+                        if (lane == 0) hl[k] = c_h[k];
+                        c_h[k] = __shfl_sync(0xffffffffu, h[k], 31);
+                    }
+                    // update of cell j = f - 2 (own cells lo..hi-1)
+                    if (j >= lo && j < hi) {
+                        float U[M];
 #pragma unroll
                         for (int k = 0; k < M; ++k) {
-                            float c[5];
-#pragma unroll
-                            for (int j = 0; j < 5; ++j) c[j] = NPW_X(k * NS + RES_GHOST + i - 2 + j);
-                            float vm, vp;
-                            fast::cell_recon_k2(c + 1, 0.0, a.mp, fp, &vm, &vp);
-                            if (i < hi) svm[k * (n + 2) + i + 1] = vm;
-                            if (i >= lo) svp[k * (n + 2) + i + 1] = vp;
+                            const float du = lam * (hl[k] - h[k]);
+                            const int ix = k * NS + RES_GHOST + j;
+                            if (stage == 0) {
+                                res_store(uA + k * NS + RES_GHOST, j, n, in.bc, du, -0.0f);
+                                U[k] = du;
+                            } else if (stage == 1) {
+                                const float v = 0.25f * (uA[ix] + du);
+                                res_store(uB + k * NS + RES_GHOST, j, n, in.bc, v, -0.0f);
+                                U[k] = v;
+                            } else {
+                                const int gx = k * n + j;
+                                const float base_u = un[ix];
+                                const float y = kTwoThirdsF * (uB[ix] + du) + cr[gx];
+                                const float t = base_u + y;
+                                cr[gx] = y - (t - base_u);
+                                res_store(uA + k * NS + RES_GHOST, j, n, in.bc, t, inflow[k]);
+                                U[k] = t;
+                            }
+                            bad |= !finite_(U[k]);
                         }
-                    }
-                }
-                __syncwarp();
-                // U: own cells lo..hi-1
-                for (int i = lo + lane; i < hi; i += 32) {
-                    float A[M], B[M], C[M], D[M], hl[M], hr[M], U[M];
-#pragma unroll
-                    for (int k = 0; k < M; ++k) {
-                        A[k] = svm[k * (n + 2) + i];      // v^- of cell i-1 (face i)
-                        B[k] = svp[k * (n + 2) + i + 1];  // v^+ of cell i   (face i)
-                        C[k] = svm[k * (n + 2) + i + 1];  // v^- of cell i   (face i+1)
-                        D[k] = svp[k * (n + 2) + i + 2];  // v^+ of cell i+1 (face i+1)
-                    }
-                    lf_flux<float, KIND, M>(A, B, alphaf, a.mp, 0, hl);
-                    lf_flux<float, KIND, M>(C, D, alphaf, a.mp, 0, hr);
-#pragma unroll
-                    for (int k = 0; k < M; ++k) {
-                        const float du = lam * (hl[k] - hr[k]);
-                        const int ix = k * NS + RES_GHOST + i;
-                        if (stage == 0) {
-                            res_store(uA + k * NS + RES_GHOST, i, n, in.bc, du, -0.0f);
-                            U[k] = du;
-                        } else if (stage == 1) {
-                            const float v = 0.25f * (uA[ix] + du);
-                            res_store(uB + k * NS + RES_GHOST, i, n, in.bc, v, -0.0f);
-                            U[k] = v;
-                        } else {
-                            const int gx = k * n + i;
-                            const float base = un[ix];
-                            const float y = kTwoThirdsF * (uB[ix] + du) + cr[gx];
-                            const float t = base + y;
-                            cr[gx] = y - (t - base);
-                            res_store(uA + k * NS + RES_GHOST, i, n, in.bc, t, inflow[k]);
-                            U[k] = t;
+                        if (stage == 2) {
+                            const float sp = wave_speed<float, KIND>(U, a.mp, 0);
+                            bad |= !finite_(sp);
+                            vmaxf = sp > vmaxf ? sp : vmaxf;
                         }
-                        bad |= !finite_(U[k]);
-                    }
-                    if (stage == 2) {
-                        const float sp = wave_speed<float, KIND>(U, a.mp, 0);
-                        bad |= !finite_(sp);
-                        vmaxf = sp > vmaxf ? sp : vmaxf;
                     }
                 }
             }
