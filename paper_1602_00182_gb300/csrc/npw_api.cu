@@ -659,7 +659,9 @@ npw_status launch_resident(Run1D& r, const npw_instance* inst, SideStreams* ss, 
         const int c = n > 4096 ? 0 : (n > 2048 ? 1 : (n > 1024 ? 2 : 3));
         cls[c].push_back(i);
     }
-    static const int threads[4] = {1024, 512, 256, 128};
+    // two 512-thread CTAs per SM for the largest class (64 registers per thread fill the register
+    // file either way) measured 10% faster than one 1024-thread CTA
+    static const int threads[4] = {512, 512, 256, 128};
     std::vector<int32_t> all;
     size_t offs[5] = {0, 0, 0, 0, 0};
     for (int c = 0; c < 4; ++c) {

@@ -507,15 +507,14 @@ static __global__ void comp_copy_kernel(float* dst, const float* src, float* zer
 // Resident whole-solve kernel (float state, component-wise).  One CTA owns one instance for
 // its whole run: u^n and the two stage values live in shared memory, and thread 0 advances
 // t, alpha and dt between steps.  Each warp owns a contiguous range of cells [lo, hi) and
-// runs the three phases of a stage on it without waiting for the other warps: eta of the
-// faces lo..hi (the two boundary faces are also computed by the neighbouring warps, from the
-// same data, so the copies agree bit for bit), the reconstruction of cells lo-1..hi, then
-// fluxes and the update of its own cells.  Warps therefore drift apart within a stage and the
-// FP64 work of the shape parameter overlaps the FP32 work of other warps; the only CTA-wide
-// barrier is between stages (the next stage reads the neighbours' halo).  Stage values are
-// double-buffered (u^n -> uA -> uB -> u^{n+1}) so no warp overwrites a value another still reads.
-// Shared memory per field: u^n, uA, uB [n]; eta [n+1] (face f between cells f-1 and f);
-// v^-, v^+ [n+2] (cells -1..n at index i+1).
+// runs a stage on it in one pass without waiting for the other warps: per chunk of 32 faces,
+// each lane forms the eta of its face, reconstructs the cell to its left, computes the flux of
+// the face before and updates the cell before that, taking its left neighbour's values by lane
+// shuffles.  The faces lo and hi are also computed by the neighbouring warps, from the same
+// data, so the copies agree bit for bit.  Warps therefore drift apart within a stage; the only
+// CTA-wide barrier is between stages (the next stage reads the neighbours' halo).  Stage values
+// are double-buffered (u^n -> uA -> uB -> u^{n+1}) so no warp overwrites a value another still
+// reads.  Shared memory per field: u^n, uA, uB, each n cells with RES_GHOST ghost cells per side.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ int res_map(int i, int n, int bc) {
     if (bc == NPW_BC_PERIODIC) return i < 0 ? i + n : (i >= n ? i - n : i);
