@@ -346,6 +346,72 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_kernel(Stage1DArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// One warp's pass over the cells [lo, hi) of a line, for one RK stage of the resident kernel
+// (the per-stage kernel runs the same arithmetic in phases over its tile): lane l of the chunk
+// at base takes
+//   face f = base + l: its eta (k = 3, cells f-2..f+1);
+//   cell f - 1: its reconstruction (cells f-3..f+1), v^+ at face f - 1 with the eta of face
+//     f - 1 (lane l - 1) and v^- at face f with the eta of face f;
+//   face f - 1: the Lax-Friedrichs flux from v^- of cell f - 2 (lane l - 1) and v^+ of cell f - 1;
+//   cell f - 2: the update, upd(j, flux of face j, flux of face j + 1).
+// Lane 0 takes the lane l - 1 values from lane 31 of the previous chunk.  Faces lo..hi, cells
+// lo-1..hi and the updates of cells lo..hi-1 are covered by f = lo..hi+1; faces lo and hi are
+// also computed by the warps on either side, from the same data, so the copies agree bit for
+// bit.  X(k, i) is the stage input of field k at cell i, for i in lo-3..hi+2.
+// ---------------------------------------------------------------------------------------
+template <int KIND, int K, int M, typename LoadX, typename Upd>
+__device__ __forceinline__ void warp_line_pass(int lo, int hi, int lane, const fast::FParams& fp,
+                                               const MethodParams& mp, float alpha, LoadX X, Upd upd) {
+    float c_eta[M], c_vm[M], c_h[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) c_eta[k] = c_vm[k] = c_h[k] = 0.0f;
+    for (int base = lo; base <= hi + 1; base += 32) {
+        const int f = base + lane, i = f - 1, j = f - 2;
+        const bool face_ok = f <= hi, cell_ok = i <= hi;
+        float vm[M], vp[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            float c[5], eta = 0.0f;
+            vm[k] = vp[k] = 0.0f;
+            if (cell_ok) {
+#pragma unroll
+                for (int q = 0; q < 5; ++q) c[q] = X(k, i - 2 + q);
+                if (K == 3 && face_ok) {
+                    uint32_t fl = 0;
+                    eta = fast::face_eta(c[1], c[2], c[3], c[4], fp, &fl);
+                }
+            }
+            if constexpr (K == 3) {
+                float eprev = __shfl_up_sync(0xffffffffu, eta, 1);
+                if (lane == 0) eprev = c_eta[k];
+                c_eta[k] = __shfl_sync(0xffffffffu, eta, 31);
+                if (cell_ok) fast::cell_recon(c, eta, i >= lo ? eprev : 0.0f, fp, &vm[k], &vp[k]);
+            } else {
+                if (cell_ok) fast::cell_recon_k2(c + 1, 0.0, mp, fp, &vm[k], &vp[k]);
+            }
+        }
+        // flux of face f - 1
+        float A[M], h[M], hl[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            A[k] = __shfl_up_sync(0xffffffffu, vm[k], 1);
+            if (lane == 0) A[k] = c_vm[k];
+            c_vm[k] = __shfl_sync(0xffffffffu, vm[k], 31);
+            h[k] = 0.0f;
+        }
+        if (i >= lo && i <= hi) lf_flux<float, KIND, M>(A, vp, alpha, mp, 0, h);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            hl[k] = __shfl_up_sync(0xffffffffu, h[k], 1);
+            if (lane == 0) hl[k] = c_h[k];
+            c_h[k] = __shfl_sync(0xffffffffu, h[k], 31);
+        }
+        // update of cell j = f - 2 (cells lo..hi-1)
+        if (j >= lo && j < hi) upd(j, hl, h);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // The mixed-precision fused stage kernel (1D, component-wise).  Phases over the tile with
 // three ghost cells per side, extended index e = 0 .. cnt+5 for cell c0 - 3 + e:
 //   F: eta (and the switch) once per face, faces between e-1 and e for e = 2 .. cnt+4;
@@ -639,92 +705,38 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
             const float* D = stage == 1 ? uA : uB;
 #define NPW_X(idx) (stage == 0 ? un[(idx)] : un[(idx)] + D[(idx)])
             if (lo < hi) {
-                // One pass over the warp's range: lane l of the chunk at base takes
-                //   face f = base + l: its eta (k = 3, cells f-2..f+1);
-                //   cell f - 1: its reconstruction (cells f-3..f+1), v^+ at face f - 1 with the eta
-                //     of face f - 1 (lane l - 1) and v^- at face f with the eta of face f;
-                //   face f - 1: the Lax-Friedrichs flux from v^- of cell f - 2 (lane l - 1) and
-                //     v^+ of cell f - 1;
-                //   cell f - 2: the update from the fluxes of faces f - 2 (lane l - 1) and f - 1.
-                // Lane 0 takes the lane l - 1 values from lane 31 of the previous chunk.  Faces
-                // lo..hi, cells lo-1..hi and the updates of the own cells lo..hi-1 are covered by
-                // f = lo..hi+1; the boundary faces are computed by both neighbouring warps.
-                float c_eta[M], c_vm[M], c_h[M];
-#pragma unroll
-                for (int k = 0; k < M; ++k) c_eta[k] = c_vm[k] = c_h[k] = 0.0f;
-                for (int base = lo; base <= hi + 1; base += 32) {
-                    const int f = base + lane, i = f - 1, j = f - 2;
-                    const bool face_ok = f <= hi, cell_ok = i <= hi;
-                    float vm[M], vp[M];
+                auto X = [&](int k, int i) { return NPW_X(k * NS + RES_GHOST + i); };
+                auto upd = [&](int j, const float* hl, const float* hr) {
+                    float U[M];
 #pragma unroll
                     for (int k = 0; k < M; ++k) {
-                        float c[5], eta = 0.0f;
-                        vm[k] = vp[k] = 0.0f;
-                        if (cell_ok) {
-#pragma unroll
-                            for (int q = 0; q < 5; ++q) c[q] = NPW_X(k * NS + RES_GHOST + i - 2 + q);
-                            if (K == 3 && face_ok) {
-                                uint32_t fl = 0;
-                                eta = fast::face_eta(c[1], c[2], c[3], c[4], fp, &fl);
-                            }
-                        }
-                        if constexpr (K == 3) {
-                            float eprev = __shfl_up_sync(0xffffffffu, eta, 1);
-                            if (lane == 0) eprev = c_eta[k];
-                            c_eta[k] = __shfl_sync(0xffffffffu, eta, 31);
-                            if (cell_ok) fast::cell_recon(c, eta, i >= lo ? eprev : 0.0f, fp, &vm[k], &vp[k]);
+                        const float du = lam * (hl[k] - hr[k]);
+                        const int ix = k * NS + RES_GHOST + j;
+                        if (stage == 0) {
+                            res_store(uA + k * NS + RES_GHOST, j, n, in.bc, du, -0.0f);
+                            U[k] = du;
+                        } else if (stage == 1) {
+                            const float v = 0.25f * (uA[ix] + du);
+                            res_store(uB + k * NS + RES_GHOST, j, n, in.bc, v, -0.0f);
+                            U[k] = v;
                         } else {
-                            if (cell_ok) fast::cell_recon_k2(c + 1, 0.0, a.mp, fp, &vm[k], &vp[k]);
+                            const int gx = k * n + j;
+                            const float base_u = un[ix];
+                            const float y = kTwoThirdsF * (uB[ix] + du) + cr[gx];
+                            const float t = base_u + y;
+                            cr[gx] = y - (t - base_u);
+                            res_store(uA + k * NS + RES_GHOST, j, n, in.bc, t, inflow[k]);
+                            U[k] = t;
                         }
+                        bad |= !finite_(U[k]);
                     }
-                    // flux of face f - 1
-                    float A[M], h[M], hl[M];
-#pragma unroll
-                    for (int k = 0; k < M; ++k) {
-                        A[k] = __shfl_up_sync(0xffffffffu, vm[k], 1);
-                        if (lane == 0) A[k] = c_vm[k];
-                        c_vm[k] = __shfl_sync(0xffffffffu, vm[k], 31);
-                        h[k] = 0.0f;
+                    if (stage == 2) {
+                        const float sp = wave_speed<float, KIND>(U, a.mp, 0);
+                        bad |= !finite_(sp);
+                        vmaxf = sp > vmaxf ? sp : vmaxf;
                     }
-                    if (i >= lo && i <= hi) lf_flux<float, KIND, M>(A, vp, alphaf, a.mp, 0, h);
-#pragma unroll
-                    for (int k = 0; k < M; ++k) {
-                        hl[k] = __shfl_up_sync(0xffffffffu, h[k], 1);
-                        if (lane == 0) hl[k] = c_h[k];
-                        c_h[k] = __shfl_sync(0xffffffffu, h[k], 31);
-                    }
-                    // update of cell j = f - 2 (own cells lo..hi-1)
-                    if (j >= lo && j < hi) {
-                        float U[M];
-#pragma unroll
-                        for (int k = 0; k < M; ++k) {
-                            const float du = lam * (hl[k] - h[k]);
-                            const int ix = k * NS + RES_GHOST + j;
-                            if (stage == 0) {
-                                res_store(uA + k * NS + RES_GHOST, j, n, in.bc, du, -0.0f);
-                                U[k] = du;
-                            } else if (stage == 1) {
-                                const float v = 0.25f * (uA[ix] + du);
-                                res_store(uB + k * NS + RES_GHOST, j, n, in.bc, v, -0.0f);
-                                U[k] = v;
-                            } else {
-                                const int gx = k * n + j;
-                                const float base_u = un[ix];
-                                const float y = kTwoThirdsF * (uB[ix] + du) + cr[gx];
-                                const float t = base_u + y;
-                                cr[gx] = y - (t - base_u);
-                                res_store(uA + k * NS + RES_GHOST, j, n, in.bc, t, inflow[k]);
-                                U[k] = t;
-                            }
-                            bad |= !finite_(U[k]);
-                        }
-                        if (stage == 2) {
-                            const float sp = wave_speed<float, KIND>(U, a.mp, 0);
-                            bad |= !finite_(sp);
-                            vmaxf = sp > vmaxf ? sp : vmaxf;
-                        }
-                    }
-                }
+                };
+                warp_line_pass<KIND, K, M>(lo, hi, lane, fp, a.mp, alphaf, X, upd);
             }
             __syncthreads();
 #undef NPW_X
