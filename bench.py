@@ -280,7 +280,7 @@ def run_gpu(args, rank, world, local_rank):
             "unit": "G FP64-pipe instr/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": traffic,
-            "kernel": "solve1d_resident_kernel<BURGERS>, size class n > 4096 (1024 threads, 1 CTA/SM)",
+            "kernel": "solve1d_resident_kernel<BURGERS>, size class n > 4096 (512 threads, 2 CTAs/SM)",
             "resident_launches": [int(x) for x in pr.resident_launches],
             "resident_ms": [float(x) for x in pr.resident_ms],
             "peak_source": ("derived: 2 FP64-pipe instr/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s FP64); "
@@ -512,7 +512,9 @@ def run_euler1d(args, rank, world, local_rank):
     pr = npw_profile()
     lib.npw_profile_reset()
     lib.npw_profile_enable(1)
-    times = _timed(one, args.steps, flush, world)
+    clocks = Clocks(os.path.join(args.out_dir, f"clocks_rank{rank}.csv"))
+    with clocks:
+        times = _timed(one, args.steps, flush, world)
     lib.npw_profile_read(ctypes.byref(pr))
     lib.npw_profile_enable(0)
     stats = holder["stats"]
@@ -538,6 +540,7 @@ def run_euler1d(args, rank, world, local_rank):
                                   "peak_gbs": _peaks()[0], "bytes_per_cell_update": 132},
                      "stage_launches": int(pr.stage_launches), "stage_ms": pr.stage_ms},
         "gpu_launches": int(pr.kernel_launches),
+        "clocks": clocks.summary(local_rank),
     }
 
 
@@ -580,7 +583,9 @@ def run_euler2d(args, rank, world, local_rank):
     pr = npw_profile()
     lib.npw_profile_reset()
     lib.npw_profile_enable(1)
-    times = _timed(one, args.steps, flush, world)
+    clocks = Clocks(os.path.join(args.out_dir, f"clocks_rank{rank}.csv"))
+    with clocks:
+        times = _timed(one, args.steps, flush, world)
     lib.npw_profile_read(ctypes.byref(pr))
     lib.npw_profile_enable(0)
     cu = holder["cu"]
@@ -605,6 +610,7 @@ def run_euler2d(args, rank, world, local_rank):
                                   "peak_gbs": _peaks()[0], "bytes_per_cell_update": 128},
                      "stage_launches": int(pr.stage_launches), "stage_ms": pr.stage_ms},
         "gpu_launches": int(pr.kernel_launches),
+        "clocks": clocks.summary(local_rank),
     }
 
 
