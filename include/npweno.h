@@ -311,6 +311,29 @@ npw_status npweno_rk3_step_noalloc(void* u, int64_t n, int32_t m, double dx, dou
 size_t npw_noalloc_scratch_bytes(void);
 
 /*
+ * npw_format_check -- self-check of the integer float<->double format changes that the
+ * mixed-precision shape parameter uses instead of hardware conversions (no counterpart in the
+ * paper).  For i < count it writes, from the device arrays f_in[count] (float) and
+ * d_in[count] (double):
+ *   widen_out[i]   the exact widening of f_in[i] by integer operations (every float class);
+ *   widen_nz_out[i] the fast widening, meaningful where f_in[i] is zero or normal;
+ *   narrow_out[i]  d_in[i] rounded to float by integer operations (round to nearest, ties away
+ *                  from zero; below 2^-126 in magnitude: signed zero; beyond the float range:
+ *                  signed infinity; d_in finite);
+ *   seed_out[i]    d_in[i] truncated to float for a reciprocal seed;
+ *   flags_out[i]   bit 0: f_in[i] is zero or normal; bit 1: d_in[i] is in the seed range
+ *                  [2^-99, 2^99) in magnitude;
+ *   hw_widen_out[i], hw_narrow_out[i]  the hardware conversions (double)f_in[i] and
+ *                  (float)d_in[i], for comparison.
+ * All pointers are device pointers of the stated lengths, owned by the caller; stream is a
+ * cudaStream_t (NULL: the legacy default stream).  Returns NPW_EINVAL for count < 0 or a null
+ * pointer with count > 0, NPW_ECUDA on a launch error; it does not synchronise.
+ */
+npw_status npw_format_check(const float* f_in, const double* d_in, int64_t count, double* widen_out,
+                            double* widen_nz_out, float* narrow_out, float* seed_out, int32_t* flags_out,
+                            double* hw_widen_out, float* hw_narrow_out, void* stream);
+
+/*
  * Process-wide launch counters and stage-kernel timing (no counterpart in the paper; used to
  * put each kernel against its roofline).  When enabled, every launch of the fused stage
  * kernel is bracketed by two CUDA events recorded on the launching stream; the elapsed times

@@ -1,6 +1,6 @@
 """Build libnpweno.so (the CUDA library behind include/npweno.h) in-tree for sm_103a.
 
-Three translation units are compiled in parallel with nvcc and linked into one shared
+Five translation units are compiled in parallel with nvcc and linked into one shared
 object next to this file:
   npw_fp64.cu  -- double-precision kernels, --fmad=false (each operation rounded as written)
   npw_fp32.cu  -- mixed-precision kernels, also --fmad=false: every fused multiply-add is an
@@ -8,6 +8,7 @@ object next to this file:
                   produce the same bits from the same data
   npw_api.cu   -- host runtime and the C ABI
   npw_noalloc.cu -- npweno_rk3_step_noalloc and its fixed device scratch array
+  npw_format.cu  -- npw_format_check, the self-check of the integer float<->double format changes
 """
 from __future__ import annotations
 
@@ -30,6 +31,7 @@ UNITS = {
     "npw_fp32.cu": ["--fmad=false"],
     "npw_api.cu": [],
     "npw_noalloc.cu": [],
+    "npw_format.cu": ["--fmad=false"],
 }
 
 

@@ -121,8 +121,10 @@ def load():
     lib.npw_autotune_scratch_bytes.argtypes = [i32, P(npw_params)]
     lib.npw_autotune_scratch_bytes.restype = sz
     lib.npw_autotune_1d.argtypes = [i32, i32, P(npw_params), vp, sz, vp, P(i32)]
+    lib.npw_format_check.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     for f in ("npweno_reconstruct", "npweno_flux", "npweno_rk3_step", "npweno_solve", "npweno_batch_solve",
-              "npweno_rk3_step_2d", "npweno_solve_2d", "npweno_rk3_step_noalloc", "npw_autotune_1d"):
+              "npweno_rk3_step_2d", "npweno_solve_2d", "npweno_rk3_step_noalloc", "npw_autotune_1d",
+              "npw_format_check"):
         getattr(lib, f).restype = i32
     _lib = lib
     return lib
@@ -234,6 +236,30 @@ def npweno_rk3_step_noalloc(u, dx: float, dt: float, flux_kind: int, bc: int, pa
     p = params.c()
     _check(load().npweno_rk3_step_noalloc(_dev(uu, params, "u"), n, m, float(dx), float(dt), flux_kind, bc,
                                           C.byref(p), _stream()))
+
+
+def npw_format_check(f_in, d_in):
+    """Run the library's integer float<->double format changes on the device tensors f_in
+    (float32) and d_in (float64, same length) next to the hardware conversions; returns a dict
+    of device tensors (see include/npweno.h)."""
+    import torch
+    if f_in.dtype != torch.float32 or d_in.dtype != torch.float64 or f_in.numel() != d_in.numel():
+        raise ValueError("f_in must be float32 and d_in float64 of the same length")
+    if not (f_in.is_cuda and d_in.is_cuda and f_in.is_contiguous() and d_in.is_contiguous()):
+        raise ValueError("f_in and d_in must be contiguous CUDA tensors")
+    cnt = f_in.numel()
+    out = dict(widen=torch.empty(cnt, dtype=torch.float64, device=f_in.device),
+               widen_nz=torch.empty(cnt, dtype=torch.float64, device=f_in.device),
+               narrow=torch.empty(cnt, dtype=torch.float32, device=f_in.device),
+               seed=torch.empty(cnt, dtype=torch.float32, device=f_in.device),
+               flags=torch.empty(cnt, dtype=torch.int32, device=f_in.device),
+               hw_widen=torch.empty(cnt, dtype=torch.float64, device=f_in.device),
+               hw_narrow=torch.empty(cnt, dtype=torch.float32, device=f_in.device))
+    ptr = lambda t: C.c_void_p(t.data_ptr())
+    _check(load().npw_format_check(ptr(f_in), ptr(d_in), cnt, ptr(out["widen"]), ptr(out["widen_nz"]),
+                                   ptr(out["narrow"]), ptr(out["seed"]), ptr(out["flags"]), ptr(out["hw_widen"]),
+                                   ptr(out["hw_narrow"]), _stream()))
+    return out
 
 
 def _stats(s: npw_solve_stats) -> dict:
