@@ -24,7 +24,7 @@
  *     calls poll a 4-byte completion word between launches and return when done).
  *   - Errors are returned as npw_status and never abort; npw_last_error() gives the text
  *     of the most recent failure on the calling thread.
- *   - n >= 6 cells (3 ghost cells per side feed the WENO5 stencil); dx > 0; k must be 3.
+ *   - n >= 6 cells (3 ghost cells per side feed the WENO5 stencil); dx > 0; k is 2 or 3.
  */
 #ifndef NPWENO_H
 #define NPWENO_H
@@ -49,7 +49,8 @@ typedef enum {
  * 1D Euler (Ex. 4, m = 3), 2D Euler (Sec. 7 form, m = 4). */
 typedef enum { NPW_FLUX_ADVECTION = 0, NPW_FLUX_BURGERS = 1, NPW_FLUX_EULER1D = 2, NPW_FLUX_EULER2D = 3 } npw_flux_kind;
 /* Boundary conditions: periodic (Ex. 1, 3), transmissive = zero-gradient ghost cells
- * (Ex. 4), inflow = constant left ghost state params->inflow (Ex. 2), right transmissive. */
+ * (Ex. 4), inflow = constant left ghost state params->inflow (Ex. 2), right transmissive.
+ * 2D: bc applies to x and, unless params->bc_y >= 0, to y (inflow: bottom side, top transmissive). */
 typedef enum { NPW_BC_PERIODIC = 0, NPW_BC_TRANSMISSIVE = 1, NPW_BC_INFLOW = 2 } npw_bc;
 /* Schemes compared in the paper (Sec. 5.2): ENO3, WENO-JS5 (eta = 0), RBF-ENO3, RBF-WENO5. */
 typedef enum { NPW_ENO = 0, NPW_WENO_JS = 1, NPW_RBF_ENO = 2, NPW_RBF_WENO = 3 } npw_scheme;
@@ -64,16 +65,16 @@ typedef enum { NPW_FP64 = 0, NPW_FP32_MIXED = 1 } npw_precision;
 typedef struct {
     int32_t k;               /* 3: ENO3 / WENO5 (Table k3); 2: ENO2 / WENO3 (Table k2, Sec. 3.2-3.5: one
                                 shape parameter per face value, from the cell's 3-cell stencil,
-                                and the switch of eq. root_value per cell; switch_variant unused).
-                                k = 2 runs the face-based stage kernels in both precisions */
+                                and the switch of eq. root_value per cell; switch_variant unused) */
     int32_t scheme;          /* npw_scheme */
     int32_t rbf;             /* npw_rbf: perturbation rows of Table k3 (MQ) or Sec. 3.3 (GA) */
     int32_t monotone_switch; /* 1: eta = 0 where the stencil polynomial is non-monotone */
     int32_t switch_variant;  /* 0: cubic on the 4-cell eta stencil; 1: eq. root_value on both 3-cell halves */
     int32_t characteristic;  /* 1D Euler only: reconstruct Roe characteristic fields */
     int32_t precision;       /* npw_precision */
-    int32_t eta_eval;        /* NPW_FP32_MIXED only: 0 = eta in FP64 (exact FP64 numerator and
-                                denominator, FP64 division); 1 = from the exactly computed numerator
+    int32_t eta_eval;        /* NPW_FP32_MIXED only: 0 = eta in FP64 (numerator and denominator formed
+                                exactly as float pairs and summed in FP64, Newton-Raphson quotient in
+                                FP64, within 2^-42 before rounding to float); 1 = from the same numerator
                                 and denominator held as float pairs, double-float quotient (no FP64
                                 instruction, ~2^-46 relative before rounding to float) */
     double eps_M;            /* additive guard of the eta denominator (Table k3), e.g. 1e-12 */
@@ -98,7 +99,10 @@ typedef struct {
     int32_t cross_2d;        /* 2D runs with k = 2 and an RBF scheme: 1 = the shape parameter of Sec. 6 on the
                                 5-cell cross, which also cancels the transverse curvature of the cell averages
                                 at the face midpoint (third-order face values); 0 = the line form of Table k2 */
-    int32_t pad2_;
+    int32_t bc_y;            /* 2D entry points: boundary condition of the y direction (rows), NPW_BC_*; < 0
+                                (npw_default_params: -1) = the bc argument, which then applies to both
+                                directions and otherwise to x only.  An inflow side (left for x, bottom
+                                for y) holds params.inflow; 1D entry points ignore it */
 } npw_params;
 
 typedef struct {

@@ -39,7 +39,7 @@ SCHEMES = {"eno": ENO, "weno_js": WENO_JS, "rbf_eno": RBF_ENO, "rbf_weno": RBF_W
 class _Params(C.Structure):
     _fields_ = [
         ("scheme", C.c_int), ("rbf", C.c_int), ("monotone_switch", C.c_int), ("switch_variant", C.c_int),
-        ("characteristic", C.c_int), ("k", C.c_int), ("cross_2d", C.c_int), ("pad2_", C.c_int),
+        ("characteristic", C.c_int), ("k", C.c_int), ("cross_2d", C.c_int), ("bc_y", C.c_int),
         ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
         ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4),
         ("tie_tol", C.c_double), ("eta_guard", C.c_double), ("eta_max", C.c_double),
@@ -61,6 +61,7 @@ class Params:
     characteristic: int = 0
     k: int = 3
     cross_2d: int = 0
+    bc_y: int = -1  # 2D: boundary of the y direction (-1: the same as the bc argument)
     eps_M: float = 1e-12
     eps_weno: float = 1e-6
     gamma: float = 1.4
@@ -73,7 +74,7 @@ class Params:
 
     def _c(self) -> _Params:
         p = _Params()
-        for f in ("scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "k", "cross_2d"):
+        for f in ("scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "k", "cross_2d", "bc_y"):
             setattr(p, f, int(getattr(self, f)))
         for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "tie_tol", "eta_guard", "eta_max"):
             setattr(p, f, float(getattr(self, f)))

@@ -620,6 +620,7 @@ static int check_params(long n, int m, const orc_params* p) {
     if (p->scheme < 0 || p->scheme > 3 || p->rbf < 0 || p->rbf > 1) return ORC_EINVAL;
     if (p->k != 0 && p->k != 2 && p->k != 3) return ORC_EINVAL;
     if (p->characteristic && m != 3) return ORC_EINVAL;
+    if (p->bc_y > 2) return ORC_EINVAL;
     return ORC_OK;
 }
 
@@ -741,16 +742,17 @@ static int rhs_1d(const double* u, long n, int m, double dx, int kind, int bc, d
 
 /* Transverse second differences of the cells of one grid line (Sec. 6, k = 2 on the cross):  */
 /* dir 0: row j, out[k*nx + i] = u(i, j-1) - 2 u(i, j) + u(i, j+1); dir 1: column i,             */
-/* out[k*ny + j] = u(i-1, j) - 2 u(i, j) + u(i+1, j).  Neighbours follow the boundary condition. */
-static void transverse_line(const double* u, long nx, long ny, int m, int bc, const orc_params* p, int dir, long line,
-                            double* out) {
+/* out[k*ny + j] = u(i-1, j) - 2 u(i, j) + u(i+1, j).  Neighbours follow the boundary condition  */
+/* of their direction (bc along x, bc_y along y).                                                */
+static void transverse_line(const double* u, long nx, long ny, int m, int bc, int bc_y, const orc_params* p, int dir,
+                            long line, double* out) {
     long cells = nx * ny;
     for (int k = 0; k < m; ++k) {
         const double* uk = u + k * cells;
         if (dir == 0) {
             for (long i = 0; i < nx; ++i) {
-                double dn = line_get(uk + i, ny, nx, line - 1, bc, p->inflow[k]);
-                double up = line_get(uk + i, ny, nx, line + 1, bc, p->inflow[k]);
+                double dn = line_get(uk + i, ny, nx, line - 1, bc_y, p->inflow[k]);
+                double up = line_get(uk + i, ny, nx, line + 1, bc_y, p->inflow[k]);
                 out[k * nx + i] = dn - 2.0 * uk[line * nx + i] + up;
             }
         } else {
@@ -774,12 +776,13 @@ int orc_reconstruct_2d(const double* u, long nx, long ny, int m, int bc, const o
     int st = check_params(nx, m, p);
     if (st || ny < 6 || p->characteristic) return ORC_EINVAL;
     long cells = nx * ny, nmax = (nx > ny) ? nx : ny;
+    const int bcy = p->bc_y < 0 ? bc : p->bc_y; /* boundary of the y sweeps */
     double* vm = malloc(sizeof(double) * m * (nmax + 1));
     double* vp = malloc(sizeof(double) * m * (nmax + 1));
     double* tr = malloc(sizeof(double) * m * nmax);
     st = (vm && vp && tr) ? ORC_OK : ORC_ENOMEM;
     for (long j = 0; j < ny && !st; ++j) {
-        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, p, 0, j, tr);
+        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, bcy, p, 0, j, tr);
         st = recon_line(u + j * nx, nx, m, 1, cells, bc, p, vm, vp, NULL, NULL, NULL, nx + 1, use_cross(p) ? tr : NULL);
         for (int k = 0; k < m && !st; ++k)
             for (long i = 0; i <= nx; ++i) {
@@ -788,8 +791,8 @@ int orc_reconstruct_2d(const double* u, long nx, long ny, int m, int bc, const o
             }
     }
     for (long i = 0; i < nx && !st; ++i) {
-        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, p, 1, i, tr);
-        st = recon_line(u + i, ny, m, nx, cells, bc, p, vm, vp, NULL, NULL, NULL, ny + 1, use_cross(p) ? tr : NULL);
+        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, bcy, p, 1, i, tr);
+        st = recon_line(u + i, ny, m, nx, cells, bcy, p, vm, vp, NULL, NULL, NULL, ny + 1, use_cross(p) ? tr : NULL);
         for (int k = 0; k < m && !st; ++k)
             for (long j = 0; j <= ny; ++j) {
                 vmy[(k * (ny + 1) + j) * nx + i] = vm[k * (ny + 1) + j];
@@ -809,6 +812,7 @@ static int rhs_2d(const double* u, long nx, long ny, int m, double dx, double dy
                   double ay, const orc_params* p, double* L) {
     long cells = nx * ny;
     long nmax = (nx > ny) ? nx : ny;
+    const int bcy = p->bc_y < 0 ? bc : p->bc_y; /* boundary of the y sweeps */
     double* vm = malloc(sizeof(double) * m * (nmax + 1));
     double* vp = malloc(sizeof(double) * m * (nmax + 1));
     double* h = malloc(sizeof(double) * m * (nmax + 1));
@@ -817,7 +821,7 @@ static int rhs_2d(const double* u, long nx, long ny, int m, double dx, double dy
     for (long i = 0; i < m * cells && !st; ++i) L[i] = 0.0;
     /* x sweeps: row j */
     for (long j = 0; j < ny && !st; ++j) {
-        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, p, 0, j, tr);
+        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, bcy, p, 0, j, tr);
         st = recon_line(u + j * nx, nx, m, 1, cells, bc, p, vm, vp, NULL, NULL, NULL, nx + 1, use_cross(p) ? tr : NULL);
         if (!st) st = orc_flux(vm, vp, nx + 1, m, kind, 0, ax, p, h);
         for (int k = 0; k < m && !st; ++k)
@@ -825,8 +829,8 @@ static int rhs_2d(const double* u, long nx, long ny, int m, double dx, double dy
     }
     /* y sweeps: column i */
     for (long i = 0; i < nx && !st; ++i) {
-        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, p, 1, i, tr);
-        st = recon_line(u + i, ny, m, nx, cells, bc, p, vm, vp, NULL, NULL, NULL, ny + 1, use_cross(p) ? tr : NULL);
+        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, bcy, p, 1, i, tr);
+        st = recon_line(u + i, ny, m, nx, cells, bcy, p, vm, vp, NULL, NULL, NULL, ny + 1, use_cross(p) ? tr : NULL);
         if (!st) st = orc_flux(vm, vp, ny + 1, m, kind, 1, ay, p, h);
         for (int k = 0; k < m && !st; ++k)
             for (long j = 0; j < ny; ++j) L[k * cells + j * nx + i] -= (h[k * (ny + 1) + j + 1] - h[k * (ny + 1) + j]) / dy;

@@ -34,7 +34,7 @@ typedef struct {
     int characteristic;  /* 1D Euler: reconstruct characteristic fields */
     int k;               /* order parameter of the ENO stencils: 2 or 3 (0 means 3) */
     int cross_2d;        /* 2D, k = 2: shape parameter of Sec. 6 on the 5-cell cross (1) or of the line (0) */
-    int pad2_;
+    int bc_y;            /* 2D: boundary condition of the y direction (columns); < 0: the bc argument */
     double eps_M;     /* additive guard of the eta denominator */
     double eps_weno;  /* WENO epsilon (1e-6) */
     double gamma;     /* ratio of specific heats */

@@ -824,6 +824,7 @@ void npw_default_params(npw_params* p) {
     p->gamma = 1.4;
     p->adv_speed = 1.0;
     p->adv_speed_y = 1.0;
+    p->bc_y = -1;
 }
 
 const char* npw_last_error(void) { return g_err.c_str(); }
@@ -1142,6 +1143,7 @@ static npw_status run_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx, 
     if (m != flux_m(flux_kind)) return fail(NPW_EINVAL, "m does not match the flux kind");
     if (params->characteristic) return fail(NPW_EINVAL, "2D runs are component-wise");
     if ((st = check_bc(bc))) return st;
+    if (params->bc_y >= 0 && (st = check_bc(params->bc_y))) return st;
     if (!(dx > 0.0) || !(dy > 0.0)) return fail(NPW_EINVAL, "dx, dy must be > 0");
     const bool fp32 = params->precision == NPW_FP32_MIXED;
     const size_t esz = elem_size(params);
@@ -1167,6 +1169,7 @@ static npw_status run_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx, 
     hi.t_end = t_end;
     hi.cfl = cfl;
     hi.bc = bc;
+    hi.bc_y = params->bc_y < 0 ? bc : params->bc_y;
     hi.tiles_x = (int32_t)((nx + npw::TX_2D - 1) / npw::TX_2D);
     hi.tiles_y = (int32_t)((ny + npw::TY_2D - 1) / npw::TY_2D);
     const int tiles = hi.tiles_x * hi.tiles_y;

@@ -93,9 +93,9 @@ struct Inst2D {
     int64_t nx, ny;
     double dx, dy;
     double t_end, cfl;
-    int32_t bc;
+    int32_t bc;      // boundary of the x direction (columns)
     int32_t tiles_x, tiles_y;
-    int32_t pad_;
+    int32_t bc_y;    // boundary of the y direction (rows)
 };
 
 struct Stage1DArgs {

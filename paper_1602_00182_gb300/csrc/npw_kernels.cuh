@@ -791,16 +791,21 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
 // ---------------------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ R grid_get(const R* u, const Inst2D& in, int64_t i, int64_t j, double inflow) {
-    // rows (j) and columns (i) each use the instance boundary condition
-    int64_t nx = in.nx, ny = in.ny;
+    // columns (i) follow the instance boundary condition bc, rows (j) bc_y; an inflow side
+    // (left for bc, bottom for bc_y) gives the inflow state, whatever the other index
+    const int64_t nx = in.nx, ny = in.ny;
+    if (in.bc_y == NPW_BC_INFLOW && j < 0) return R(inflow);
+    if (in.bc == NPW_BC_INFLOW && i < 0) return R(inflow);
     if (in.bc == NPW_BC_PERIODIC) {
         i %= nx;
         if (i < 0) i += nx;
+    } else {
+        i = i < 0 ? 0 : (i >= nx ? nx - 1 : i);
+    }
+    if (in.bc_y == NPW_BC_PERIODIC) {
         j %= ny;
         if (j < 0) j += ny;
     } else {
-        if (in.bc == NPW_BC_INFLOW && (i < 0 || j < 0)) return R(inflow);
-        i = i < 0 ? 0 : (i >= nx ? nx - 1 : i);
         j = j < 0 ? 0 : (j >= ny ? ny - 1 : j);
     }
     return u[j * nx + i];
@@ -810,14 +815,16 @@ __device__ __forceinline__ R grid_get(const R* u, const Inst2D& in, int64_t i, i
 // comparison per side replaces the general map of grid_get (and its 64-bit remainders)
 __device__ __forceinline__ float halo_get(const float* u, const Inst2D& in, int i, int j, float inflow) {
     const int nx = (int)in.nx, ny = (int)in.ny;
-    if (in.bc == NPW_BC_PERIODIC) {
+    if (in.bc_y == NPW_BC_INFLOW && j < 0) return inflow;
+    if (in.bc == NPW_BC_INFLOW && i < 0) return inflow;
+    if (in.bc == NPW_BC_PERIODIC)
         i = i < 0 ? i + nx : (i >= nx ? i - nx : i);
-        j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
-    } else {
-        if (in.bc == NPW_BC_INFLOW && (i < 0 || j < 0)) return inflow;
+    else
         i = i < 0 ? 0 : (i >= nx ? nx - 1 : i);
+    if (in.bc_y == NPW_BC_PERIODIC)
+        j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
+    else
         j = j < 0 ? 0 : (j >= ny ? ny - 1 : j);
-    }
     return u[(int64_t)j * in.nx + i];
 }
 

@@ -29,7 +29,7 @@ class npw_params(C.Structure):
                 ("eta_eval", C.c_int32), ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
                 ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4),
                 ("eta_guard", C.c_double), ("batch_mode", C.c_int32), ("tile_1d", C.c_int32),
-                ("eta_max", C.c_double), ("cross_2d", C.c_int32), ("pad2_", C.c_int32)]
+                ("eta_max", C.c_double), ("cross_2d", C.c_int32), ("bc_y", C.c_int32)]
 
 
 class npw_solve_stats(C.Structure):
@@ -70,11 +70,12 @@ class Params:
     k: int = 3
     tile_1d: int = 0
     cross_2d: int = 0
+    bc_y: int = -1  # 2D: boundary of the y direction (-1: the bc argument)
 
     def c(self) -> npw_params:
         p = npw_params()
         for f in ("k", "scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "precision",
-                  "eta_eval", "batch_mode", "tile_1d", "cross_2d"):
+                  "eta_eval", "batch_mode", "tile_1d", "cross_2d", "bc_y"):
             setattr(p, f, int(getattr(self, f)))
         for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "eta_guard", "eta_max"):
             setattr(p, f, float(getattr(self, f)))

@@ -303,6 +303,39 @@ def test_inflow_discontinuous_advection_is_non_oscillatory():
         assert np.sum(np.abs(np.diff(uT))) <= 2.0 + 1e-9
 
 
+def _example2(n=200):
+    edges = np.linspace(-1, 1, n + 1)
+    dx = 2.0 / n
+    u0 = np.where(edges[1:] <= 0, 1.0, -1.0)
+    exact = np.where(edges[1:] <= 0.5, 1.0, -1.0)  # T = 0.5: the jump sits on the edge x = 0.5
+    return u0, dx, exact
+
+
+def _example2_solve(k, scheme, u0, dx):
+    uT, _ = O.solve(u0, dx, 0.5, 0.1, O.ADVECTION, O.INFLOW, O.Params(k=k, scheme=scheme, inflow=(1.0, 0, 0, 0)))
+    return uT
+
+
+def test_example2_k2_eno_and_rbf_eno_are_non_oscillatory():
+    """Sec. 5.2 Example 2 with k = 2 (switch on): ENO2 and RBF-ENO2 stay within [-1, 1] with no
+    new variation, as the paper states for both."""
+    u0, dx, _ = _example2()
+    for sch in (O.ENO, O.RBF_ENO):
+        uT = _example2_solve(2, sch, u0, dx)
+        assert uT.max() <= 1.0 + 1e-12 and uT.min() >= -1.0 - 1e-12
+        assert np.sum(np.abs(np.diff(uT))) <= 2.0 + 1e-9
+
+
+def test_example2_rbf_eno_is_sharper():
+    """Sec. 5.2 Example 2: for k = 2 the RBF-ENO solution is better than the ENO and WENO-JS
+    solutions, and for k = 3 RBF-ENO is better than ENO (L1 distance to the exact profile)."""
+    u0, dx, exact = _example2()
+    l1 = {(k, s): np.abs(_example2_solve(k, s, u0, dx) - exact).sum() * dx
+          for k in (2, 3) for s in (O.ENO, O.WENO_JS, O.RBF_ENO)}
+    assert l1[(2, O.RBF_ENO)] < min(l1[(2, O.ENO)], l1[(2, O.WENO_JS)])
+    assert l1[(3, O.RBF_ENO)] < l1[(3, O.ENO)]
+
+
 # ------------------------------------------------------------------------------- 2D
 def test_2d_reduces_to_1d_on_x_invariant_data():
     """The dimension-by-dimension form (eq. 2DIntegral, midpoint point per face) on data that
@@ -316,6 +349,54 @@ def test_2d_reduces_to_1d_on_x_invariant_data():
     p2 = O.Params(adv_speed_y=0.0)
     r2, _ = O.solve_2d(u2, dx, dx, 0.3, 0.4, O.ADVECTION, O.PERIODIC, p2, max_steps=5)
     np.testing.assert_allclose(r2, np.repeat(r1[None, :], 8, axis=0), rtol=0, atol=1e-15)
+
+
+def _example2_2d(n=100):
+    """Sec. 7 Example 2 on [0, 1]^2: v = 1 for y <= 0.5, -1 above; v(x, 0, t) = 1 (bottom inflow),
+    periodic in x, transmissive at the top (the outflow side of v_t + v_x + v_y = 0)."""
+    edges = np.linspace(0, 1, n + 1)
+    col = np.where(edges[1:] <= 0.5, 1.0, -1.0)
+    return np.repeat(col[:, None], n, axis=1), 1.0 / n, edges
+
+
+def test_2d_bc_y_defaults_to_bc():
+    u, d, _ = _example2_2d(24)
+    a, _ = O.solve_2d(u, d, d, 0.1, 0.1, O.ADVECTION, O.INFLOW, O.Params(k=2, scheme=O.RBF_ENO, inflow=(1.0, 0, 0, 0)))
+    b, _ = O.solve_2d(u, d, d, 0.1, 0.1, O.ADVECTION, O.INFLOW,
+                      O.Params(k=2, scheme=O.RBF_ENO, inflow=(1.0, 0, 0, 0), bc_y=O.INFLOW))
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("k,scheme,cross", [(2, O.ENO, 0), (2, O.RBF_ENO, 0), (2, O.RBF_ENO, 1), (3, O.RBF_WENO, 0)])
+def test_2d_example2_reduces_to_1d_inflow_along_y(k, scheme, cross):
+    """With data constant along x, periodic in x and the inflow boundary in y, every column of
+    the 2D solve is the 1D inflow solve along y (the x sweeps difference equal fluxes; with
+    dx = dy the 2D CFL step is the 1D step at half the CFL number).  On the cross, the
+    transverse differences vanish and the line form results."""
+    u, d, _ = _example2_2d(40)
+    p2 = O.Params(k=k, scheme=scheme, cross_2d=cross, inflow=(1.0, 0, 0, 0), bc_y=O.INFLOW)
+    r2, s2 = O.solve_2d(u, d, d, 0.3, 0.2, O.ADVECTION, O.PERIODIC, p2)
+    r1, s1 = O.solve(u[:, 0], d, 0.3, 0.1, O.ADVECTION, O.INFLOW, O.Params(k=k, scheme=scheme, inflow=(1.0, 0, 0, 0)))
+    assert s1["steps"] == s2["steps"]
+    np.testing.assert_allclose(r2, np.repeat(r1[:, None], 40, axis=1), rtol=0, atol=1e-14)
+
+
+def test_2d_example2_eno_and_rbf_eno_non_oscillatory_and_rbf_eno_sharper():
+    """Sec. 7 Example 2 (k = 2, N = 100): the ENO and RBF-ENO profiles along y stay within [-1, 1]
+    with no new variation at every sampled time, and the RBF-ENO profile is the sharper one."""
+    u, d, edges = _example2_2d(100)
+    l1 = {}
+    for sch in (O.ENO, O.RBF_ENO):
+        for t in (0.1, 0.25, 0.4):
+            r, _ = O.solve_2d(u, d, d, t, 0.1, O.ADVECTION, O.PERIODIC,
+                              O.Params(k=2, scheme=sch, inflow=(1.0, 0, 0, 0), bc_y=O.INFLOW))
+            col = r[:, 50]
+            assert col.max() <= 1.0 + 1e-12 and col.min() >= -1.0 - 1e-12
+            assert np.sum(np.abs(np.diff(col))) <= 2.0 + 1e-9
+            if t == 0.25:
+                exact = np.where(edges[1:] <= 0.75 + 1e-12, 1.0, -1.0)
+                l1[sch] = np.abs(col - exact).sum() * d
+    assert l1[O.RBF_ENO] < l1[O.ENO]
 
 
 def test_2d_vortex_second_order_and_conservation():
