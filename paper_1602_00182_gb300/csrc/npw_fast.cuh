@@ -234,16 +234,11 @@ __device__ __forceinline__ bool seed_f(double v, float* out) {
     return E - 924u < 198u;
 }
 
-// |e| < 2^-20 (a biased exponent below 1023 - 20), read from the bits of e
-__device__ __forceinline__ bool below_2m20(double e) {
-    return ((uint32_t)((uint64_t)__double_as_longlong(e) >> 52) & 0x7FFu) < 1003u;
-}
 
 // The rare branches below are kept out of line: a call is executed only when taken, while an
 // inlined short branch may be turned into predicated instructions that take issue slots of
 // the FP64 pipe on every evaluation.
 static __device__ __noinline__ float div_rn_f(double num, double den) { return (float)(num / den); }
-static __device__ __noinline__ double div_d(double num, double den) { return num / den; }
 
 // Numerator a + 3b and denominator a + 15b (a = w0 - w3, b = w2 - w1) as unevaluated float
 // pairs.  The differences are exact two_sum pairs, the products 3 bh and 15 bh are split

@@ -30,19 +30,8 @@ __device__ __forceinline__ R line_get(const R* u, int64_t n, int64_t stride, int
     return u[k * stride];
 }
 
-// index of cell k (any integer) of a line of n cells under the boundary condition; -1 means
-// "the inflow ghost state"
-__device__ __forceinline__ int64_t line_idx(int64_t n, int64_t k, int bc) {
-    if (bc == NPW_BC_PERIODIC) {
-        int64_t kk = k % n;
-        return kk < 0 ? kk + n : kk;
-    }
-    if (k < 0) return bc == NPW_BC_INFLOW ? -1 : 0;
-    return k >= n ? n - 1 : k;
-}
-
-// line_idx for a tile halo: k in [-3, n + 2] with n >= 6, so one comparison per side replaces
-// the 64-bit remainder
+// Index of cell k of a line of n cells for a tile halo (k in [-3, n + 2], n >= 6), or -1 for
+// the inflow state: periodic images, repeated end cells, inflow on the left
 __device__ __forceinline__ int64_t halo_idx(int64_t n, int64_t k, int bc) {
     if (bc == NPW_BC_PERIODIC) return k < 0 ? k + n : (k >= n ? k - n : k);
     if (k < 0) return bc == NPW_BC_INFLOW ? -1 : 0;
