@@ -340,24 +340,40 @@ def _ncu_traffic():
 
 
 # ------------------------------------------------------------------------------- serving
+_SERVING_CACHE = {}
+
+
 def serving_requests(count: int, rate: float, seed: int = 5):
-    """Poisson arrivals of mixed 1D requests: periodic Burgers (the batch family, T scaled by
-    U(0.1, 1)) and transmissive Euler Riemann / Shu-Osher data (n up to 8192)."""
-    g = np.random.Generator(np.random.PCG64(I.SEED_BASE + 50 + seed))
-    burg = I.burgers_batch(count=count, seed_index=60 + seed)
-    eul = I.euler_batch(count=count, nmin=256, nmax=8192, seed_index=70 + seed)
-    reqs, t = [], 0.0
-    for k in range(count):
-        t += g.exponential(1.0 / rate)
-        if g.uniform() < 0.5:
-            it = burg[k]
-            reqs.append(dict(arrival=t, kind=1, bc=0, m=1, n=it.n, dx=it.dx, t_end=1.5 * g.uniform(0.1, 1.0),
-                             u0=it.u0.ravel()))
-        else:
-            it = eul[k]
-            reqs.append(dict(arrival=t, kind=2, bc=1, m=3, n=it.n, dx=it.dx, t_end=it.t_end * g.uniform(0.1, 1.0),
-                             u0=it.u0.ravel()))
-    return reqs
+    """Poisson arrivals of mixed requests: periodic Burgers (the batch family, T scaled by
+    U(0.1, 1)), transmissive 1D Euler Riemann / Shu-Osher data (n up to 8192) and periodic 2D
+    Euler squares (isentropic vortex or four-quadrant data, 128^2 to 1024^2).  The payloads are
+    drawn once per (count, seed); the rate only scales the arrival times."""
+    key = (count, seed)
+    if key not in _SERVING_CACHE:
+        g = np.random.Generator(np.random.PCG64(I.SEED_BASE + 50 + seed))
+        burg = I.burgers_batch(count=count, seed_index=60 + seed)
+        eul = I.euler_batch(count=count, nmin=256, nmax=8192, seed_index=70 + seed)
+        gaps, items = [], []
+        for k in range(count):
+            gaps.append(g.exponential(1.0))
+            u = g.uniform()
+            if u < 0.4:
+                it = burg[k]
+                items.append(dict(kind=1, bc=0, m=1, n=it.n, ny=0, dx=it.dx, t_end=1.5 * g.uniform(0.1, 1.0),
+                                  u0=it.u0.ravel()))
+            elif u < 0.8:
+                it = eul[k]
+                items.append(dict(kind=2, bc=1, m=3, n=it.n, ny=0, dx=it.dx, t_end=it.t_end * g.uniform(0.1, 1.0),
+                                  u0=it.u0.ravel()))
+            else:
+                n2 = int(g.choice([128, 256, 512, 1024], p=[0.4, 0.3, 0.2, 0.1]))
+                U, d = I.euler2d_batch(n2, 2, seed_index=1000 + 100 * seed + k)[k % 2]
+                t2 = (0.1 if k % 2 == 0 else 0.02) * g.uniform(0.1, 1.0)  # ~10-80 steps
+                items.append(dict(kind=3, bc=0, m=4, n=n2, ny=n2, dx=d, t_end=t2, u0=U))
+        _SERVING_CACHE[key] = (np.array(gaps), items)
+    gaps, items = _SERVING_CACHE[key]
+    arrivals = np.cumsum(gaps) / rate
+    return [dict(arrival=float(t), **it) for t, it in zip(arrivals, items)]
 
 
 def run_serving(npw, reqs, max_steps: int = 32):
@@ -371,7 +387,8 @@ def run_serving(npw, reqs, max_steps: int = 32):
         now = time.perf_counter() - t0
         while k < len(reqs) and reqs[k]["arrival"] <= now:
             r = reqs[k]
-            srv.submit(r["u0"], r["kind"], r["bc"], r["dx"], r["t_end"], 0.5, tag=k)
+            srv.submit(r["u0"], r["kind"], r["bc"], r["dx"], r["t_end"], 0.5, tag=k,
+                       dy=r["dx"] if r["ny"] else 0.0)
             k += 1
         act, q = srv.step(max_steps)
         for res in srv.poll():
@@ -380,7 +397,7 @@ def run_serving(npw, reqs, max_steps: int = 32):
             time.sleep(max(0.0, reqs[k]["arrival"] - (time.perf_counter() - t0)))
     srv.close()
     lat = np.array([done[i]["done_s"] - reqs[i]["arrival"] for i in range(len(reqs))])
-    cells = sum(reqs[i]["n"] * done[i]["steps"] for i in range(len(reqs)))
+    cells = sum(reqs[i]["n"] * max(reqs[i]["ny"], 1) * done[i]["steps"] for i in range(len(reqs)))
     span = max(done[i]["done_s"] for i in done) - reqs[0]["arrival"]
     ok = all(done[i]["status"] == 0 for i in done)
     return lat, cells / span, ok
@@ -396,10 +413,13 @@ def fifo_service_times(npw, reqs):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         u = torch.tensor(r["u0"], dtype=torch.float64, device="cuda")
-        st = npw.npweno_solve(u.view(r["m"], r["n"]), r["dx"], r["t_end"], 0.5, r["kind"], r["bc"], p)
+        if r["ny"]:
+            st = npw.npweno_solve_2d(u, r["dx"], r["dx"], r["t_end"], 0.5, r["kind"], r["bc"], p)
+        else:
+            st = npw.npweno_solve(u.view(r["m"], r["n"]), r["dx"], r["t_end"], 0.5, r["kind"], r["bc"], p)
         u.cpu()
         svc.append(time.perf_counter() - t0)
-        cells.append(r["n"] * st["steps"])
+        cells.append(r["n"] * max(r["ny"], 1) * st["steps"])
     return np.array(svc), np.array(cells)
 
 
@@ -422,9 +442,11 @@ def serving_block(npw, count: int, rates):
     base = serving_requests(count, rates[0])
     svc, fcells = fifo_service_times(npw, base)
     out = {"requests": count,
-           "mix": "1/2 periodic Burgers (N 64..8192, T 0.15..1.5), 1/2 transmissive Euler (N 256..8192)",
+           "mix": "0.4 periodic Burgers (N 64..8192, T 0.15..1.5), 0.4 transmissive 1D Euler (N 256..8192), "
+                  "0.2 periodic 2D Euler squares (128^2..1024^2, vortex or four-quadrant)",
            "server_mode": "continuous batching, NPW_FP32_MIXED, per-stage kernels, 32-step rounds",
-           "fp64_fifo_mode": "one request at a time, npweno_solve NPW_FP64; latencies from measured service times",
+           "fp64_fifo_mode": "one request at a time, npweno_solve / npweno_solve_2d NPW_FP64; latencies from "
+                             "measured service times",
            "rates": []}
     for rate in rates:
         reqs = serving_requests(count, rate)

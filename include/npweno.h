@@ -226,8 +226,9 @@ npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx
  * Requests are queued by npw_server_submit (non-blocking) and admitted first-in first-out
  * whenever a slot and arena space are free; every npw_server_step advances all admitted
  * requests together -- each with its own dt, alpha and t_end -- by up to max_steps RK3 steps
- * through the fused per-stage kernels (one launch set per flux kind), then copies finished
- * states to their host buffers and frees their space.  Each request's arithmetic depends only
+ * through the fused per-stage kernels (one launch set per 1D flux kind over all 1D requests,
+ * one per 2D request), then copies finished states to their host buffers and frees their
+ * space.  A request occupies m * n (2D: m * n * ny) heap cells.  Each request's arithmetic depends only
  * on its own data, so its result is the same bits alone or in any mix.
  *   device_arena / arena_bytes: caller-owned device memory, at least
  *       npw_server_arena_bytes(heap_cells, max_slots, params) for a heap of heap_cells elements.
@@ -239,15 +240,20 @@ npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx
  */
 typedef struct npw_server npw_server;
 typedef struct {
-    int32_t flux_kind;     /* NPW_FLUX_ADVECTION, NPW_FLUX_BURGERS or NPW_FLUX_EULER1D */
-    int32_t bc;            /* npw_bc */
-    int64_t n;             /* cells (m = 1, or 3 for Euler) */
+    int32_t flux_kind;     /* 1D (ny == 0): NPW_FLUX_ADVECTION, NPW_FLUX_BURGERS or NPW_FLUX_EULER1D;
+                              2D (ny > 0): NPW_FLUX_ADVECTION, NPW_FLUX_BURGERS or NPW_FLUX_EULER2D */
+    int32_t bc;            /* npw_bc (2D: of the x direction) */
+    int64_t n;             /* cells (2D: nx); m = 1, 3 for 1D Euler, 4 for 2D Euler */
     double dx;
     double t_end;
     double cfl;
-    const void* u0_host;   /* initial cell averages, host */
-    void* out_host;        /* final state, host */
+    const void* u0_host;   /* initial cell averages, host: [m][n] (2D: [m][ny][nx]) */
+    void* out_host;        /* final state, host, same layout */
     uint64_t tag;          /* returned with the result */
+    int64_t ny;            /* 0: a 1D request; >= 6: a 2D request of n x ny cells (dimension by dimension) */
+    double dy;             /* 2D: cell size in y */
+    int32_t bc_y;          /* 2D: npw_bc of the y direction; < 0: bc */
+    int32_t reserved_;
 } npw_request;
 typedef struct {
     uint64_t id;           /* as returned by npw_server_submit */

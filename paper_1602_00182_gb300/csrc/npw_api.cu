@@ -1257,7 +1257,7 @@ npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx
 namespace {
 
 struct ServerLayout {
-    size_t inst, ctl, tiles, newtiles, list, poll, heap_u, heap_u1, heap_u2, heap_s, heap_c, total;
+    size_t inst, inst2d, ctl, tiles, newtiles, list, poll, heap_u, heap_u1, heap_u2, heap_s, heap_c, total;
     int64_t max_tiles;
 };
 
@@ -1267,6 +1267,8 @@ ServerLayout server_layout(int64_t heap_cells, int max_slots, size_t esz) {
     size_t o = 0;
     L.inst = o;
     o = align256(o + sizeof(npw::InstDev) * (size_t)max_slots);
+    L.inst2d = o;  // per slot, used by 2D requests
+    o = align256(o + sizeof(npw::Inst2D) * (size_t)max_slots);
     L.ctl = o;
     o = align256(o + sizeof(npw::Ctl) * (size_t)max_slots);
     L.tiles = o;
@@ -1317,6 +1319,8 @@ struct npw_server {
         uint64_t id = 0;
         npw_request req{};
         int m = 1;
+        bool is2d = false;
+        int64_t cells = 0;  // heap cells: m n (2D: m n ny)
         int64_t off = 0;
         double submit_s = 0.0, admit_s = 0.0;
     };
@@ -1332,6 +1336,12 @@ struct npw_server {
     std::vector<npw::Ctl> host_ctl;
     uint64_t next_id = 1;
     long long remaining_hint = 0;  // largest remaining step estimate after the last round
+
+    // CTAs of a 2D request's stage launch (tiles of TX_2D x TY_2D cells)
+    int tiles2d(int k) const {
+        const npw_request& r = slots[k].req;
+        return (int)(((r.n + npw::TX_2D - 1) / npw::TX_2D) * ((r.ny + npw::TY_2D - 1) / npw::TY_2D));
+    }
 
     bool heap_alloc(int64_t len, int64_t* off) {
         for (size_t k = 0; k < free_ranges.size(); ++k) {
@@ -1363,7 +1373,7 @@ namespace {
 
 template <typename R>
 npw_status server_launch_steps(npw_server* sv, const std::vector<int>& kind_tiles, const std::vector<size_t>& kind_off,
-                               int steps) {
+                               const std::vector<int>& slots2d, int steps) {
     npw::Stage1DArgs a{};
     a.inst = reinterpret_cast<const npw::InstDev*>(sv->arena + sv->L.inst);
     a.ctl = reinterpret_cast<npw::Ctl*>(sv->arena + sv->L.ctl);
@@ -1380,7 +1390,29 @@ npw_status server_launch_steps(npw_server* sv, const std::vector<int>& kind_tile
     a.c = reinterpret_cast<float*>(sv->arena + sv->L.heap_c);
     const void* in_[3] = {u, u1, u2};
     void* out_[3] = {u1, u2, u};
+    // 2D requests: the Shu-Osher stages of npweno_solve_2d on their own instance and control
+    // words (u -> u1 -> u2 -> u at the request's heap offset)
+    npw::Stage2DArgs b{};
+    b.mp = sv->mp;
+    b.advance = 1;
+    const npw::Inst2D* inst2d = reinterpret_cast<const npw::Inst2D*>(sv->arena + sv->L.inst2d);
+    npw::Ctl* ctl = reinterpret_cast<npw::Ctl*>(sv->arena + sv->L.ctl);
     for (int step = 0; step < steps; ++step) {
+        for (int k : slots2d) {
+            const int tiles = sv->tiles2d(k);
+            b.inst = inst2d + k;
+            b.ctl = ctl + k;
+            for (int st = 0; st < 3; ++st) {
+                b.uin = in_[st];
+                b.un = u;
+                b.uout = out_[st];
+                b.stage = st;
+                auto ev = stage_begin(sv->s);
+                cudaError_t e = npw::launch_stage2d<R>(b, tiles, sv->slots[k].req.flux_kind, sv->s);
+                stage_end(ev, sv->s);
+                if (e != cudaSuccess) return cuda_fail(e, "server stage 2d launch");
+            }
+        }
         for (int kind = 0; kind < 3; ++kind) {
             if (kind_tiles[kind] == 0) continue;
             a.tiles = reinterpret_cast<const npw::Tile*>(sv->arena + sv->L.tiles) + kind_off[kind];
@@ -1450,15 +1482,27 @@ void npw_server_destroy(npw_server* s) { delete s; }
 
 npw_status npw_server_submit(npw_server* sv, const npw_request* req, uint64_t* id) {
     if (!sv || !req) return fail(NPW_EINVAL, "null server or request");
-    if (req->flux_kind != NPW_FLUX_ADVECTION && req->flux_kind != NPW_FLUX_BURGERS && req->flux_kind != NPW_FLUX_EULER1D)
+    const bool is2d = req->ny != 0;
+    if (!is2d && req->flux_kind != NPW_FLUX_ADVECTION && req->flux_kind != NPW_FLUX_BURGERS &&
+        req->flux_kind != NPW_FLUX_EULER1D)
         return fail(NPW_EINVAL, "request flux kind %d is not a 1D flux", req->flux_kind);
+    if (is2d && req->flux_kind != NPW_FLUX_ADVECTION && req->flux_kind != NPW_FLUX_BURGERS &&
+        req->flux_kind != NPW_FLUX_EULER2D)
+        return fail(NPW_EINVAL, "request flux kind %d is not a 2D flux", req->flux_kind);
     npw_status st = check_bc(req->bc);
     if (st) return st;
     if (req->n < 6 || req->n > ((int64_t)1 << 30) || !(req->dx > 0.0) || !(req->cfl > 0.0) || !req->u0_host ||
         !req->out_host)
         return fail(NPW_EINVAL, "malformed request");
+    if (is2d) {
+        if (req->ny < 6 || req->ny > ((int64_t)1 << 30) || !(req->dy > 0.0))
+            return fail(NPW_EINVAL, "malformed 2D request (ny >= 6, dy > 0)");
+        if (req->bc_y >= 0 && (st = check_bc(req->bc_y))) return st;
+        if (sv->params.characteristic) return fail(NPW_EINVAL, "2D requests are component-wise");
+    }
     const int m = flux_m(req->flux_kind);
-    if (req->n * m > sv->heap_cells) return fail(NPW_EINVAL, "request larger than the server heap");
+    const int64_t cells = req->n * m * (is2d ? req->ny : 1);
+    if (cells > sv->heap_cells) return fail(NPW_EINVAL, "request larger than the server heap");
     if ((int)sv->queue.size() >= sv->max_slots) return fail(NPW_EBUSY, "request queue full");
     npw_server::Pending p{sv->next_id++, *req, now_s(sv->t0)};
     sv->queue.push_back(p);
@@ -1474,6 +1518,8 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
     while (!sv->queue.empty()) {
         const npw_server::Pending& p = sv->queue.front();
         const int m = flux_m(p.req.flux_kind);
+        const bool is2d = p.req.ny != 0;
+        const int64_t cells = p.req.n * m * (is2d ? p.req.ny : 1);
         int slot = -1;
         for (int k = 0; k < sv->max_slots; ++k)
             if (!sv->slots[k].used) {
@@ -1481,15 +1527,17 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
                 break;
             }
         int64_t off = 0;
-        if (slot < 0 || !sv->heap_alloc(p.req.n * m, &off)) break;
+        if (slot < 0 || !sv->heap_alloc(cells, &off)) break;
         NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.heap_u + (size_t)off * sv->esz, p.req.u0_host,
-                                 (size_t)(p.req.n * m) * sv->esz, cudaMemcpyHostToDevice, sv->s));
+                                 (size_t)cells * sv->esz, cudaMemcpyHostToDevice, sv->s));
         npw_server::Slot& sl = sv->slots[slot];
         sl.used = true;
         sl.fresh = true;
         sl.id = p.id;
         sl.req = p.req;
         sl.m = m;
+        sl.is2d = is2d;
+        sl.cells = cells;
         sl.off = off;
         sl.submit_s = p.submit_s;
         sl.admit_s = now_s(sv->t0);
@@ -1506,7 +1554,7 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
         kind_off[kind] = tiles.size();
         for (int k = 0; k < sv->max_slots; ++k) {
             const npw_server::Slot& sl = sv->slots[k];
-            if (!sl.used || sl.req.flux_kind != kind) continue;
+            if (!sl.used || sl.is2d || sl.req.flux_kind != kind) continue;
             npw::InstDev& d = hi[k];
             d.off = sl.off;
             d.n = sl.req.n;
@@ -1523,6 +1571,13 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
         }
         kind_tiles[kind] = (int)(tiles.size() - kind_off[kind]);
     }
+    std::vector<int> slots2d, fresh1d, fresh2d;
+    for (int k = 0; k < sv->max_slots; ++k)
+        if (sv->slots[k].used && sv->slots[k].is2d) {
+            slots2d.push_back(k);
+            ++n_active;
+        }
+    for (int k : fresh) (sv->slots[k].is2d ? fresh2d : fresh1d).push_back(k);
     if (n_active == 0) {
         if (active) *active = 0;
         if (queued) *queued = (int32_t)sv->queue.size();
@@ -1530,12 +1585,41 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
     }
     NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.inst, hi.data(), sizeof(npw::InstDev) * hi.size(),
                              cudaMemcpyHostToDevice, sv->s));
-    NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.tiles, tiles.data(), sizeof(npw::Tile) * tiles.size(),
-                             cudaMemcpyHostToDevice, sv->s));
+    if (!tiles.empty())
+        NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.tiles, tiles.data(), sizeof(npw::Tile) * tiles.size(),
+                                 cudaMemcpyHostToDevice, sv->s));
     npw::Ctl* ctl = reinterpret_cast<npw::Ctl*>(sv->arena + sv->L.ctl);
     const npw::InstDev* dinst = reinterpret_cast<const npw::InstDev*>(sv->arena + sv->L.inst);
     // 3. start the admitted requests: reset, alpha^0 over their tiles, first dt
-    if (!fresh.empty()) {
+    for (int k : fresh2d) {  // 2D: the start sequence of npweno_solve_2d on the request's own words
+        const npw_server::Slot& sl = sv->slots[k];
+        npw::Inst2D h2{};
+        h2.off = sl.off;
+        h2.nx = sl.req.n;
+        h2.ny = sl.req.ny;
+        h2.dx = sl.req.dx;
+        h2.dy = sl.req.dy;
+        h2.t_end = sl.req.t_end;
+        h2.cfl = sl.req.cfl;
+        h2.bc = sl.req.bc;
+        h2.bc_y = sl.req.bc_y < 0 ? sl.req.bc : sl.req.bc_y;
+        h2.tiles_x = (int32_t)((sl.req.n + npw::TX_2D - 1) / npw::TX_2D);
+        h2.tiles_y = (int32_t)((sl.req.ny + npw::TY_2D - 1) / npw::TY_2D);
+        npw::Inst2D* d2 = reinterpret_cast<npw::Inst2D*>(sv->arena + sv->L.inst2d) + k;
+        NPW_CUDA(cudaMemcpyAsync(d2, &h2, sizeof h2, cudaMemcpyHostToDevice, sv->s));
+        npw::ctl_start_2d_kernel<<<1, 32, 0, sv->s>>>(ctl + k, d2, 0, 0.0);
+        NPW_CUDA(cudaGetLastError());
+        cudaError_t ce = sv->fp32 ? npw::launch_alpha_init_2d<float>(sv->arena + sv->L.heap_u, d2, sv->tiles2d(k),
+                                                                      ctl + k, sl.req.flux_kind, sv->mp, sv->s)
+                                  : npw::launch_alpha_init_2d<double>(sv->arena + sv->L.heap_u, d2, sv->tiles2d(k),
+                                                                       ctl + k, sl.req.flux_kind, sv->mp, sv->s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "server alpha 2d launch");
+        npw::ctl_start_2d_kernel<<<1, 32, 0, sv->s>>>(ctl + k, d2, 1, 0.0);
+        NPW_CUDA(cudaGetLastError());
+        count_launch(3);
+    }
+    if (!fresh1d.empty()) {
+        const std::vector<int32_t> fresh(fresh1d.begin(), fresh1d.end());
         int32_t* dlist = reinterpret_cast<int32_t*>(sv->arena + sv->L.list);
         NPW_CUDA(cudaMemcpyAsync(dlist, fresh.data(), sizeof(int32_t) * fresh.size(), cudaMemcpyHostToDevice, sv->s));
         NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.newtiles, newtiles.data(), sizeof(npw::Tile) * newtiles.size(),
@@ -1575,13 +1659,13 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
                 b2 = e2;
             }
         }
-        for (int k : fresh) sv->slots[k].fresh = false;
     }
+    for (int k : fresh) sv->slots[k].fresh = false;
     // 4. advance everything admitted
     int steps = max_steps;
     if (fresh.empty() && sv->remaining_hint > 0 && sv->remaining_hint < steps) steps = (int)sv->remaining_hint;
-    st = sv->fp32 ? server_launch_steps<float>(sv, kind_tiles, kind_off, steps)
-                  : server_launch_steps<double>(sv, kind_tiles, kind_off, steps);
+    st = sv->fp32 ? server_launch_steps<float>(sv, kind_tiles, kind_off, slots2d, steps)
+                  : server_launch_steps<double>(sv, kind_tiles, kind_off, slots2d, steps);
     if (st) return st;
     // 5. read the control words, retire finished requests
     NPW_CUDA(cudaMemcpyAsync(sv->host_ctl.data(), ctl, sizeof(npw::Ctl) * sv->max_slots, cudaMemcpyDeviceToHost, sv->s));
@@ -1602,11 +1686,11 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
         }
     }
     sv->remaining_hint = rem;
-    for (int k : finished) {  // the compensated float kernels leave the final state in s
+    for (int k : finished) {  // the compensated 1D float kernels leave the final state in s
         const npw_server::Slot& sl = sv->slots[k];
-        const size_t region = sv->comp ? sv->L.heap_s : sv->L.heap_u;
+        const size_t region = (sv->comp && !sl.is2d) ? sv->L.heap_s : sv->L.heap_u;
         NPW_CUDA(cudaMemcpyAsync(sl.req.out_host, sv->arena + region + (size_t)sl.off * sv->esz,
-                                 (size_t)(sl.req.n * sl.m) * sv->esz, cudaMemcpyDeviceToHost, sv->s));
+                                 (size_t)sl.cells * sv->esz, cudaMemcpyDeviceToHost, sv->s));
     }
     if (!finished.empty() && (st = bounded_sync(sv->s))) return st;
     const double tdone = now_s(sv->t0);
@@ -1623,7 +1707,7 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
         r.admit_s = sl.admit_s;
         r.done_s = tdone;
         sv->results.push_back(r);
-        sv->heap_free(sl.off, sl.req.n * sl.m);
+        sv->heap_free(sl.off, sl.cells);
         sl.used = false;
     }
     if (active) *active = n_active - (int32_t)finished.size();

@@ -370,7 +370,8 @@ def npweno_solve_2d(u, dx: float, dy: float, t_end: float, cfl: float, flux_kind
 class npw_request(C.Structure):
     _fields_ = [("flux_kind", C.c_int32), ("bc", C.c_int32), ("n", C.c_int64), ("dx", C.c_double),
                 ("t_end", C.c_double), ("cfl", C.c_double), ("u0_host", C.c_void_p), ("out_host", C.c_void_p),
-                ("tag", C.c_uint64)]
+                ("tag", C.c_uint64), ("ny", C.c_int64), ("dy", C.c_double), ("bc_y", C.c_int32),
+                ("reserved_", C.c_int32)]
 
 
 class npw_result(C.Structure):
@@ -399,8 +400,8 @@ def _server_protos(lib):
 
 
 class Server:
-    """npw_server_*: continuous batching of 1D solves on one device arena (allocated here with
-    torch, owned by this object).  Host arrays of each request are kept alive until polled."""
+    """npw_server_*: continuous batching of 1D and 2D solves on one device arena (allocated here
+    with torch, owned by this object).  Host arrays of each request are kept alive until polled."""
 
     def __init__(self, heap_cells: int, max_slots: int, params: Params, device=None):
         torch = _torch()
@@ -418,13 +419,18 @@ class Server:
         self._keep = {}
         self._np_dtype = "float32" if params.precision == NPW_FP32_MIXED else "float64"
 
-    def submit(self, u0, flux_kind: int, bc: int, dx: float, t_end: float, cfl: float, tag: int = 0) -> int:
+    def submit(self, u0, flux_kind: int, bc: int, dx: float, t_end: float, cfl: float, tag: int = 0,
+               dy: float = 0.0, bc_y: int = -1) -> int:
+        """1D: u0 is [m][n] (or [n]); 2D (dy > 0): u0 is [m][ny][nx] (or [ny][nx])."""
         import numpy as np
         a = np.ascontiguousarray(np.asarray(u0, dtype=self._np_dtype))
-        m = 3 if flux_kind == NPW_FLUX_EULER1D else 1
-        n = a.size // m
+        m = {NPW_FLUX_EULER1D: 3, NPW_FLUX_EULER2D: 4}.get(flux_kind, 1)
+        if dy > 0.0:
+            ny, n = a.shape[-2], a.shape[-1]
+        else:
+            ny, n = 0, a.size // m
         out = np.empty_like(a)
-        r = npw_request(flux_kind, bc, n, dx, t_end, cfl, a.ctypes.data, out.ctypes.data, tag)
+        r = npw_request(flux_kind, bc, n, dx, t_end, cfl, a.ctypes.data, out.ctypes.data, tag, ny, dy, bc_y, 0)
         rid = C.c_uint64(0)
         _check(load().npw_server_submit(self._h, C.byref(r), C.byref(rid)))
         self._keep[rid.value] = (a, out)

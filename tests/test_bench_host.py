@@ -20,4 +20,9 @@ def test_serving_stream_is_the_same_requests_at_every_rate():
     assert all(np.array_equal(x["u0"], y["u0"]) for x, y in zip(a, b))
     # arrival times scale with 1 / rate
     np.testing.assert_allclose([r["arrival"] for r in a], [100.0 * r["arrival"] for r in b], rtol=1e-12)
-    assert {r["kind"] for r in a} <= {1, 2}
+    assert {r["kind"] for r in a} <= {1, 2, 3}
+    for r in a:  # 2D requests are square Euler domains, [4][n][n]
+        if r["kind"] == 3:
+            assert r["ny"] == r["n"] and r["u0"].shape == (4, r["n"], r["n"]) and r["m"] == 4
+        else:
+            assert r["ny"] == 0 and r["u0"].size == r["m"] * r["n"]

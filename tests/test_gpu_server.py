@@ -1,4 +1,4 @@
-"""The request server: continuous batching of 1D solves over one device arena.
+"""The request server: continuous batching of 1D and 2D solves over one device arena.
 
 Each request's result must be the same bits alone and in any mix (its arithmetic depends
 only on its own data and its own time step), equal to the batch solve of the same
@@ -137,3 +137,73 @@ def test_failed_request_does_not_disturb_others(npw):
         srv.submit(good[0].u0[0], npw.NPW_FLUX_BURGERS, 0, good[0].dx, 0.2, 0.5)
     assert e.value.status == npw.NPW_EBUSY
     _drain(srv)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_2d_requests_alone_equal_the_2d_solve(npw, precision):
+    """2D requests (Euler vortex and four-quadrant data, k = 3; the Sec. 7 Example 2 advection
+    with a per-direction boundary, k = 2 on the cross) served between 1D requests: each result
+    equals npweno_solve_2d of the same domain bit for bit, with the same step count."""
+    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=precision, batch_mode=1)
+    dtype = torch.float32 if precision else torch.float64
+    doms = I.euler2d_batch(40, 2, seed_index=11)
+    n2 = 36
+    edges = np.linspace(0, 1, n2 + 1)
+    ex2 = np.repeat(np.where(edges[1:] <= 0.5, 1.0, -1.0)[:, None], n2, axis=1)[None]
+    reqs = [(doms[0][0], npw.NPW_FLUX_EULER2D, npw.NPW_BC_PERIODIC, -1, doms[0][1], 0.3, p),
+            (doms[1][0], npw.NPW_FLUX_EULER2D, npw.NPW_BC_TRANSMISSIVE, -1, doms[1][1], 0.05, p)]
+    pk2 = npw.Params(k=2, scheme=npw.NPW_RBF_ENO, cross_2d=1, precision=precision, inflow=(1.0, 0, 0, 0), batch_mode=1)
+    # standalone references
+    refs = []
+    for U, kind, bc, bcy, d, t, pp in reqs:
+        u = torch.tensor(U, dtype=dtype, device="cuda")
+        st = npw.npweno_solve_2d(u, d, d, t, 0.4, kind, bc, pp)
+        refs.append((u.cpu().numpy(), st))
+    u = torch.tensor(ex2, dtype=dtype, device="cuda")
+    pk2_ref = npw.Params(**{**pk2.__dict__, "bc_y": npw.NPW_BC_INFLOW})
+    st = npw.npweno_solve_2d(u, 1.0 / n2, 1.0 / n2, 0.2, 0.4, npw.NPW_FLUX_ADVECTION, npw.NPW_BC_PERIODIC, pk2_ref)
+    ref_ex2 = (u.cpu().numpy(), st)
+    torch.cuda.synchronize()
+    # served in a mix with 1D requests (the server's method parameters are those of the Euler
+    # requests; the Example 2 request goes to its own k = 2 server)
+    ones = I.burgers_batch(count=4, nmin=64, nmax=3000, seed_index=12)
+    srv = npw.Server(heap_cells=60000, max_slots=8, params=p)
+    srv.submit(ones[0].u0[0], npw.NPW_FLUX_BURGERS, 0, ones[0].dx, 0.3, 0.5, tag=100)
+    srv.step(4)
+    got = srv.poll()
+    for i, (U, kind, bc, bcy, d, t, _) in enumerate(reqs):
+        srv.submit(U, kind, bc, d, t, 0.4, tag=i + 1, dy=d, bc_y=bcy)
+        srv.submit(ones[i + 1].u0[0], npw.NPW_FLUX_BURGERS, 0, ones[i + 1].dx, 0.2, 0.5, tag=200 + i)
+        srv.step(3)
+        got += srv.poll()
+    got += _drain(srv, max_steps=5)
+    srv.close()
+    by_tag = {r["tag"]: r for r in got}
+    assert all(r["status"] == 0 for r in got) and len(by_tag) == 5
+    for i, (ref, st) in enumerate(refs):
+        r = by_tag[i + 1]
+        assert r["steps"] == st["steps"]
+        assert np.array_equal(r["u"], ref.astype(r["u"].dtype))
+    srv = npw.Server(heap_cells=20000, max_slots=4, params=pk2)
+    srv.submit(ones[3].u0[0], npw.NPW_FLUX_BURGERS, 0, ones[3].dx, 0.1, 0.5, tag=300)
+    srv.submit(ex2, npw.NPW_FLUX_ADVECTION, npw.NPW_BC_PERIODIC, 1.0 / n2, 0.2, 0.4, tag=9, dy=1.0 / n2,
+               bc_y=npw.NPW_BC_INFLOW)
+    res = {r["tag"]: r for r in _drain(srv, max_steps=6)}
+    srv.close()
+    assert res[9]["status"] == 0 and res[9]["steps"] == ref_ex2[1]["steps"]
+    assert np.array_equal(res[9]["u"], ref_ex2[0].astype(res[9]["u"].dtype))
+
+
+def test_2d_request_validation(npw):
+    p = npw.Params(batch_mode=1)
+    srv = npw.Server(heap_cells=5000, max_slots=2, params=p)
+    u = np.zeros((4, 8, 8))
+    with pytest.raises(npw.NpwError):  # 1D Euler flux in 2D
+        srv.submit(u, npw.NPW_FLUX_EULER1D, 0, 0.1, 0.1, 0.4, dy=0.1)
+    with pytest.raises(npw.NpwError):  # 2D Euler flux in 1D
+        srv.submit(u, npw.NPW_FLUX_EULER2D, 0, 0.1, 0.1, 0.4)
+    with pytest.raises(npw.NpwError):  # larger than the heap
+        srv.submit(np.zeros((4, 40, 40)), npw.NPW_FLUX_EULER2D, 0, 0.1, 0.1, 0.4, dy=0.1)
+    with pytest.raises(npw.NpwError):  # bad y boundary
+        srv.submit(u, npw.NPW_FLUX_EULER2D, 0, 0.1, 0.1, 0.4, dy=0.1, bc_y=9)
+    srv.close()
