@@ -557,7 +557,8 @@ def run_euler1d(args, rank, world, local_rank):
                            "as CUDA graphs", "l2": "flushed before every timed step"},
         "roofline": {"bound": "alu", "achieved": fp64, "peak": FP64_PIPE_PEAK / 1e9, "unit": "G FP64-pipe instr/s",
                      "frac": (fp64 / (FP64_PIPE_PEAK / 1e9)) if fp64 else None, "traffic": None,
-                     "kernel": "stage1d_fast_kernel<EULER1D>",
+                     "kernel": ("stage1d_kernel<float, EULER1D> (characteristic, face-based)" if args.characteristic
+                                else "stage1d_fast_kernel<EULER1D>"),
                      "hbm_view": {"achieved_gbs": alg_bytes / st_s / 1e9 if st_s > 0 else None,
                                   "peak_gbs": _peaks()[0], "bytes_per_cell_update": 132},
                      "stage_launches": int(pr.stage_launches), "stage_ms": pr.stage_ms},
