@@ -93,9 +93,12 @@ typedef struct {
                                 value npw_autotune_1d chose for this flux kind, m, k, precision and
                                 characteristic flag on this device, else 1024.  Results do not depend on
                                 it (each face gets the same arithmetic in any tiling) */
-    double eta_max;          /* eta = 0 where |eta| > eta_max: the perturbation argument (Sec. 3) needs a small
-                                eta, and a monotone stencil with zero slope at the face makes the Table k3
-                                denominator vanish (eta ~ num / eps_M); 0 = automatic (1.0), < 0 = off */
+    double eta_max;          /* optional bound, not in the paper: eta = 0 where |eta| > eta_max.  The printed eta
+                                (Table k3, Table k2) is singular where its denominator crosses zero (a monotone
+                                stencil with zero slope at the face for k = 3, v ~ 0 at the face for k = 2), and
+                                the perturbation argument of Sec. 3 assumes a small eta.  <= 0 (the default) = off:
+                                the shape parameter exactly as printed.  Faces it zeroes are counted in
+                                npw_solve_stats.eta_bound and flagged by npweno_reconstruct */
     int32_t cross_2d;        /* 2D runs with k = 2 and an RBF scheme: 1 = the shape parameter of Sec. 6 on the
                                 5-cell cross, which also cancels the transverse curvature of the cell averages
                                 at the face midpoint (third-order face values); 0 = the line form of Table k2 */
@@ -103,6 +106,13 @@ typedef struct {
                                 (npw_default_params: -1) = the bc argument, which then applies to both
                                 directions and otherwise to x only.  An inflow side (left for x, bottom
                                 for y) holds params.inflow; 1D entry points ignore it */
+    double tie_tol;          /* npweno_reconstruct: relative margin of the near-tie flag bit (a switch, ENO,
+                                guard or bound decision whose deciding quantity lies within tie_tol of its
+                                threshold); <= 0 = 1e-10 */
+    int64_t max_steps;       /* step limit of every solve (npweno_solve, _solve_2d, _batch_solve, the server):
+                                a run that reaches it, or whose time stops advancing (t + dt == t), ends
+                                with status NPW_ETIMEOUT instead of looping on the device; <= 0 = automatic:
+                                64 x the step count the first time step implies + 1024, at most 2^24 */
 } npw_params;
 
 typedef struct {
@@ -111,6 +121,13 @@ typedef struct {
     double alpha_max; /* largest Lax-Friedrichs alpha seen */
     int32_t status;   /* npw_status of this problem */
     int32_t pad_;
+    /* Shape-parameter decisions of the RBF schemes over the run, every stage of every step:
+     * per face and field for k = 3, per face value (v^- and v^+ of a face) for k = 2.  A line of
+     * n cells has n + 1 faces per stage (a 2D grid: rows x (nx + 1) + columns x (ny + 1)).
+     * eta_switch: the monotone switch (Sec. 4) set eta = 0; eta_eval: eta was evaluated; of
+     * those, eta_guard / eta_bound were set to 0 by the round-off guard / the optional bound.
+     * All four are 0 for ENO and WENO-JS. */
+    int64_t eta_switch, eta_eval, eta_guard, eta_bound;
 } npw_solve_stats;
 
 /* One problem of a batch: a 1D field set of n cells at element `offset` of the arena,
@@ -127,7 +144,7 @@ typedef struct {
 
 /* Fill *p with the defaults: k = 3, RBF-WENO5, multiquadric, switch on (variant 0),
  * component-wise, FP64, eps_M = 1e-12, eps_weno = 1e-6, gamma = 1.4, a = (1, 1),
- * eta_eval = 0, eta_guard = 0 (automatic), eta_max = 0 (automatic: 1). */
+ * eta_eval = 0, eta_guard = 0 (automatic), eta_max = 0 (no bound), tie_tol = 0 (1e-10). */
 void npw_default_params(npw_params* p);
 
 /* Text of the last error on the calling thread ("" if none). */
@@ -145,11 +162,17 @@ int32_t npw_version(void);
  *           bits 2-3 = ENO stencil r of cell f-1, bits 4-5 = ENO stencil r of cell f.
  *           k = 2: bit0 / bit3 = switch fired for cell f-1 / cell f, bit2 / bit4 = ENO
  *           stencil r (0 or 1) of cell f-1 / cell f.
+ *           Both: bit1 = near tie (a decision at the face within params->tie_tol of its
+ *           threshold, where another correct rounding order may decide otherwise); bit6 /
+ *           bit7 = an evaluated eta set to 0 by the guard / the bound (k = 2: of either face
+ *           value).  Characteristic runs: per characteristic field.
+ *   eta     [m][n+1] out, may be NULL: the shape parameter used at each face (k = 2: that of
+ *           v^-_f, the central row), after the switch, guard and bound; state element type.
  * m = 1, or m = 3 with params->characteristic for the 1D Euler characteristic fields.
  * Returns NPW_EINVAL for n < 6, m outside 1..4, characteristic with m != 3, null pointers.
  */
 npw_status npweno_reconstruct(const void* vbar, int64_t n, int32_t m, int32_t bc, const npw_params* params,
-                              void* v_minus, void* v_plus, uint8_t* flags, void* stream);
+                              void* v_minus, void* v_plus, uint8_t* flags, void* eta, void* stream);
 
 /*
  * Lax-Friedrichs numerical flux (Sec. 5.1): h = (f(v^-) + f(v^+) - alpha (v^+ - v^-)) / 2
@@ -306,13 +329,16 @@ npw_status npw_autotune_1d(int32_t flux_kind, int32_t m, const npw_params* param
  * that loads the library and kept there until the process exits.
  *   - Allocates no device memory (no cudaMalloc, cudaFree or allocating library call).
  *   - Limit: npw_workspace_size(n, m, params) must not exceed npw_noalloc_scratch_bytes()
- *     (8 MiB: n * m up to about 5.2e5 in NPW_FP64, 1.0e6 in NPW_FP32_MIXED); larger sizes
- *     return NPW_EINVAL with an explanatory npw_last_error().
+ *     (8 MiB: n * m up to about 5.2e5 cells in either precision -- two 8-byte stage buffers in
+ *     NPW_FP64, four 4-byte arrays in NPW_FP32_MIXED); larger sizes return NPW_EINVAL with an
+ *     explanatory npw_last_error().
  *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress,
  *     with that device current) and caches it; make that first call before any stream capture.
  *   - Every call on a device uses the same array and the array keeps the last call's contents
  *     (each call re-initialises what it reads), so calls that overlap on the GPU -- on
  *     different streams or host threads at the same time -- race and must be serialised.
+ *   - The cached address does not survive cudaDeviceReset: after a reset in the same process
+ *     this entry point must not be called again on that device.
  *   - u, n, m, dx, dt, flux_kind, bc, params and stream have the meaning of npweno_rk3_step.
  */
 npw_status npweno_rk3_step_noalloc(void* u, int64_t n, int32_t m, double dx, double dt, int32_t flux_kind,

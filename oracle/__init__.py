@@ -32,6 +32,11 @@ PERIODIC, TRANSMISSIVE, INFLOW = 0, 1, 2
 ADVECTION, BURGERS, EULER1D, EULER2D = 0, 1, 2, 3
 FLAG_SWITCH, FLAG_SWITCH_TIE, FLAG_ENO_TIE_L, FLAG_ENO_TIE_R = 0x01, 0x02, 0x40, 0x80
 FLAG_SWITCH_R_K2 = 0x08  # k = 2: switch of the right cell of the face (bit 0: left cell)
+# zero-reason byte of reconstruct(with_reason=True): the guard or the bound (neither is in the
+# paper) set an evaluated shape parameter to 0; _L: eta of v^- (k = 3: the face's eta), _R: of
+# v^+ (k = 2)
+ZERO_GUARD_L, ZERO_BOUND_L, ZERO_GUARD_R, ZERO_BOUND_R = 0x01, 0x02, 0x04, 0x08
+COUNTERS = ("switch", "eval", "guard", "bound")  # order of the counters of npw_oracle.h
 
 SCHEMES = {"eno": ENO, "weno_js": WENO_JS, "rbf_eno": RBF_ENO, "rbf_weno": RBF_WENO}
 
@@ -43,6 +48,7 @@ class _Params(C.Structure):
         ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
         ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4),
         ("tie_tol", C.c_double), ("eta_guard", C.c_double), ("eta_max", C.c_double),
+        ("counters", C.POINTER(C.c_long)),
     ]
 
 
@@ -70,7 +76,7 @@ class Params:
     inflow: tuple = (0.0, 0.0, 0.0, 0.0)
     tie_tol: float = 1e-10
     eta_guard: float = 0.0
-    eta_max: float = 1.0
+    eta_max: float = 0.0  # 0: off, the paper's eta (Table k3); > 0: optional bound |eta| <= eta_max
 
     def _c(self) -> _Params:
         p = _Params()
@@ -80,7 +86,19 @@ class Params:
             setattr(p, f, float(getattr(self, f)))
         for k in range(4):
             p.inflow[k] = float(self.inflow[k]) if k < len(self.inflow) else 0.0
+        p.counters = None
         return p
+
+
+def _with_counters(p: _Params):
+    """Attach a fresh counter array (shape-parameter decisions) to the C params."""
+    cnt = (C.c_long * len(COUNTERS))()
+    p.counters = C.cast(cnt, C.POINTER(C.c_long))
+    return cnt
+
+
+def _counts(cnt) -> dict:
+    return {name: int(cnt[k]) for k, name in enumerate(COUNTERS)}
 
 
 def build(force: bool = False) -> str:
@@ -117,7 +135,8 @@ def lib():
         _lib.orc_eno_choice.argtypes = [P(d), d, P(i)]
         _lib.orc_beta_k3.argtypes = [P(d), P(d)]
         _lib.orc_euler_eigvec.argtypes = [P(d), P(d), d, P(d), P(d)]
-        _lib.orc_reconstruct.argtypes = [P(d), l, i, i, P(_Params), P(d), P(d), P(C.c_uint8), P(d), P(C.c_uint8)]
+        _lib.orc_reconstruct.argtypes = [P(d), l, i, i, P(_Params), P(d), P(d), P(C.c_uint8), P(d), P(C.c_uint8),
+                                         P(C.c_uint8)]
         _lib.orc_flux.argtypes = [P(d), P(d), l, i, i, i, d, P(_Params), P(d)]
         _lib.orc_max_speed.restype = d
         _lib.orc_max_speed.argtypes = [P(d), l, i, i, i, P(_Params)]
@@ -238,9 +257,11 @@ def euler_eigvec(UL, UR, gamma: float = 1.4):
 # ---------------------------------------------------------------------------------------
 # the method
 # ---------------------------------------------------------------------------------------
-def reconstruct(u, bc: int, params: Params, replay=None):
+def reconstruct(u, bc: int, params: Params, replay=None, with_reason: bool = False):
     """Face values of a 1D field set u[m][n] (or u[n]).  Returns (vm, vp, flags, eta),
-    each [m][n+1]; face f lies between cell f-1 and cell f."""
+    each [m][n+1]; face f lies between cell f-1 and cell f.  replay: a flag array of the same
+    shape whose switch and ENO decisions are taken instead of the oracle's own.  with_reason:
+    also return the zero-reason bytes (ZERO_*) and the decision counts (a dict)."""
     u = _f64(u)
     squeeze = u.ndim == 1
     if squeeze:
@@ -250,13 +271,16 @@ def reconstruct(u, bc: int, params: Params, replay=None):
     vp = np.zeros((m, n + 1))
     flags = np.zeros((m, n + 1), dtype=np.uint8)
     eta = np.zeros((m, n + 1))
+    reason = np.zeros((m, n + 1), dtype=np.uint8)
     rp = None if replay is None else np.ascontiguousarray(np.asarray(replay, dtype=np.uint8).reshape(m, n + 1))
     p = params._c()
-    _check(lib().orc_reconstruct(_dp(u), n, m, bc, C.byref(p), _dp(vm), _dp(vp), _u8p(flags), _dp(eta), _u8p(rp)),
-           "reconstruct")
-    if squeeze:
-        return vm[0], vp[0], flags[0], eta[0]
-    return vm, vp, flags, eta
+    cnt = _with_counters(p)
+    _check(lib().orc_reconstruct(_dp(u), n, m, bc, C.byref(p), _dp(vm), _dp(vp), _u8p(flags), _dp(eta), _u8p(rp),
+                                 _u8p(reason)), "reconstruct")
+    out = (vm, vp, flags, eta, reason) if not squeeze else (vm[0], vp[0], flags[0], eta[0], reason[0])
+    if with_reason:
+        return out + (_counts(cnt),)
+    return out[:4]
 
 
 def flux(vm, vp, kind: int, alpha: float, params: Params, direction: int = 0):
@@ -310,8 +334,10 @@ def solve(u, dx: float, t_end: float, cfl: float, kind: int, bc: int, params: Pa
     m, n = uu.shape
     st = _Stats()
     p = params._c()
+    cnt = _with_counters(p)
     _check(lib().orc_solve(_dp(uu), n, m, dx, t_end, cfl, kind, bc, C.byref(p), max_steps, C.byref(st)), "solve")
-    return (uu[0] if squeeze else uu), dict(steps=st.steps, t=st.t, alpha_max=st.alpha_max, status=st.status)
+    return (uu[0] if squeeze else uu), dict(steps=st.steps, t=st.t, alpha_max=st.alpha_max, status=st.status,
+                                            eta=_counts(cnt))
 
 
 def solve_2d(u, dx: float, dy: float, t_end: float, cfl: float, kind: int, bc: int, params: Params,
@@ -322,6 +348,8 @@ def solve_2d(u, dx: float, dy: float, t_end: float, cfl: float, kind: int, bc: i
     m, ny, nx = uu.shape
     st = _Stats()
     p = params._c()
+    cnt = _with_counters(p)
     _check(lib().orc_solve_2d(_dp(uu), nx, ny, m, dx, dy, t_end, cfl, kind, bc, C.byref(p), max_steps,
                               C.byref(st)), "solve_2d")
-    return (uu[0] if squeeze else uu), dict(steps=st.steps, t=st.t, alpha_max=st.alpha_max, status=st.status)
+    return (uu[0] if squeeze else uu), dict(steps=st.steps, t=st.t, alpha_max=st.alpha_max, status=st.status,
+                                            eta=_counts(cnt))

@@ -169,6 +169,8 @@ static int small_solve(int n, double A[4][4], double b[4], double x[4]) {
 /* a deciding quantity lies within tol * scale of its threshold.                          */
 /* ------------------------------------------------------------------------------------ */
 static int k2_ratio_fires(double a, double b, double c, double tol, int* near) {
+    /* three equal averages: p is constant, hence monotone, in exact arithmetic (no tie) */
+    if (a == b && b == c) return 0;
     /* x_p / dx = (-2a + 3b - c) / (-a + 2b - c), eq. root_value, cells a, b, c. */
     double num = -2.0 * a + 3.0 * b - c;
     double den = -a + 2.0 * b - c;
@@ -186,6 +188,11 @@ int orc_switch_k3(const double w[4], int variant, double tol, int* near_tie) {
         int f1 = k2_ratio_fires(w[0], w[1], w[2], tol, &near);
         int f2 = k2_ratio_fires(w[1], w[2], w[3], tol, &near);
         fires = f1 || f2;
+    } else if (w[0] == w[1] && w[1] == w[2] && w[2] == w[3]) {
+        /* four equal averages: p is constant, hence monotone; decided exactly (the elimination
+         * below would leave rounding noise in the coefficients of s, s^2, s^3 and decide by its
+         * signs) */
+        fires = 0;
     } else {
         double A[4][4], b[4], lam[4];
         for (int k = 0; k < 4; ++k) {
@@ -312,17 +319,28 @@ static double cell_face_value(const double c[5], int side, double eta, const orc
 /* Writes v^- (from cell i), v^+ (from cell i+1), the flag byte and eta.                  */
 /* ------------------------------------------------------------------------------------ */
 static void face_field_k2(const double w[6], const orc_params* p, const uint8_t* replay, double* vm, double* vp,
-                          uint8_t* flag, double* eta_out, double tl, double tr);
+                          uint8_t* flag, double* eta_out, double tl, double tr, uint8_t* reason);
+
+/* Counts of the shape-parameter decisions (orc_params.counters, optional): where the switch
+ * set eta = 0, where eta was evaluated, and where the optional guard or bound (neither is in
+ * the paper) set the evaluated eta to 0. */
+static void count_eta(const orc_params* p, int fired, int guard, int bound) {
+    if (!p->counters) return;
+    p->counters[ORC_CNT_SWITCH] += fired;
+    p->counters[ORC_CNT_EVAL] += !fired;
+    p->counters[ORC_CNT_GUARD] += guard;
+    p->counters[ORC_CNT_BOUND] += bound;
+}
 
 /* tl, tr: transverse second differences of the two cells of the face (used by k = 2 with the
- * 5-cell cross of Sec. 6; 0 on a line) */
+ * 5-cell cross of Sec. 6; 0 on a line).  reason (may be NULL): ORC_ZERO_* bits of the face. */
 static void face_field(const double w[6], const orc_params* p, const uint8_t* replay, double* vm, double* vp,
-                       uint8_t* flag, double* eta_out, double tl, double tr) {
+                       uint8_t* flag, double* eta_out, double tl, double tr, uint8_t* reason) {
     if (p->k == 2) {
-        face_field_k2(w, p, replay, vm, vp, flag, eta_out, tl, tr);
+        face_field_k2(w, p, replay, vm, vp, flag, eta_out, tl, tr, reason);
         return;
     }
-    uint8_t fl = 0;
+    uint8_t fl = 0, zr = 0;
     double eta = 0.0;
     int rbf_scheme = (p->scheme == ORC_RBF_ENO || p->scheme == ORC_RBF_WENO);
     if (rbf_scheme) {
@@ -341,14 +359,22 @@ static void face_field(const double w[6], const orc_params* p, const uint8_t* re
             double mag = fabs(w[1]) + 15.0 * fabs(w[2]) + 15.0 * fabs(w[3]) + fabs(w[4]);
             if (!(p->eta_guard > 0.0 && fabs(den0) <= p->eta_guard * mag)) {
                 double den = den0 + p->eps_M;
-                eta = eta_numerator(&w[1]) / den;
-                /* optional bound (not in the paper): the perturbation argument of Sec. 3 needs a
-                 * small eta; a monotone stencil with zero slope at the face sends eta to num/eps_M */
-                if (p->eta_max > 0.0 && fabs(eta) > p->eta_max) eta = 0.0;
+                eta = eta_numerator(&w[1]) / den; /* Table k3 */
+                /* optional bound (not in the paper, off by default): the perturbation argument of
+                 * Sec. 3 needs a small eta; a monotone stencil with zero slope at the face sends
+                 * eta to num/eps_M */
+                if (p->eta_max > 0.0 && fabs(eta) > p->eta_max) {
+                    eta = 0.0;
+                    zr |= ORC_ZERO_BOUND_L;
+                }
+            } else {
+                zr |= ORC_ZERO_GUARD_L;
             }
         }
+        count_eta(p, fires, (zr & ORC_ZERO_GUARD_L) != 0, (zr & ORC_ZERO_BOUND_L) != 0);
         if (near) fl |= ORC_FLAG_SWITCH_TIE;
     }
+    if (reason) *reason = zr;
     int rl = 0, rr = 0, nl = 0, nr = 0;
     int fl_r = -1, fr_r = -1;
     if (replay && (p->scheme == ORC_ENO || p->scheme == ORC_RBF_ENO)) {
@@ -392,17 +418,29 @@ int orc_switch_k2(const double c[3], double tol, int* near_tie) {
  * t = -1/4 for the central stencil and 1/8 for the extrapolating one.  With trans = 0 this is
  * the line formula of Table k2.  (The printed denominator of eq. i+1/2_eps_approx_2d lists the
  * coefficients -2, 1, -5, a permutation of the 1, -5, -2 that the derivation gives.) */
-double orc_eta_k2_cross(const double c[3], int side, int central, double trans, const orc_params* p) {
+/* zr (may be NULL) receives 1 where the guard, 2 where the bound set the eta to 0 */
+static double eta_k2_cross_z(const double c[3], int side, int central, double trans, const orc_params* p, int* zr) {
     double a = (side == 0) ? c[0] : c[2]; /* far cell behind the face's cell */
     double b = c[1];
     double d = (side == 0) ? c[2] : c[0]; /* cell across the face */
     double num = -a + 2.0 * b - d + (central ? -0.25 : 0.125) * trans;
     double den0 = -a + 5.0 * b + 2.0 * d;
     double mag = fabs(a) + 5.0 * fabs(b) + 2.0 * fabs(d);
-    if (p->eta_guard > 0.0 && fabs(den0) <= p->eta_guard * mag) return 0.0;
+    if (zr) *zr = 0;
+    if (p->eta_guard > 0.0 && fabs(den0) <= p->eta_guard * mag) {
+        if (zr) *zr = 1;
+        return 0.0;
+    }
     double eta = ((p->rbf == ORC_RBF_GA) ? 1.0 : 2.0) * num / (den0 + p->eps_M);
-    if (p->eta_max > 0.0 && fabs(eta) > p->eta_max) eta = 0.0;
+    if (p->eta_max > 0.0 && fabs(eta) > p->eta_max) {
+        eta = 0.0;
+        if (zr) *zr = 2;
+    }
     return eta;
+}
+
+double orc_eta_k2_cross(const double c[3], int side, int central, double trans, const orc_params* p) {
+    return eta_k2_cross_z(c, side, central, trans, p, NULL);
 }
 
 double orc_eta_k2(const double c[3], int side, const orc_params* p) { return orc_eta_k2_cross(c, side, 1, 0.0, p); }
@@ -453,8 +491,8 @@ static double cell_face_value_k2(const double c[3], int side, double eta_c, doub
  * cell i (stencil w[1..3]) with that cell's side-0 eta, v^+ from cell i+1 (stencil w[2..4])
  * with its side-1 eta.  eta_out receives the eta of v^-. */
 static void face_field_k2(const double w[6], const orc_params* p, const uint8_t* replay, double* vm, double* vp,
-                          uint8_t* flag, double* eta_out, double tl, double tr) {
-    uint8_t fl = 0;
+                          uint8_t* flag, double* eta_out, double tl, double tr, uint8_t* reason) {
+    uint8_t fl = 0, zr = 0;
     double eta_l = 0.0, eta_r = 0.0, eta_lx = 0.0, eta_rx = 0.0;
     if (p->scheme == ORC_RBF_ENO || p->scheme == ORC_RBF_WENO) {
         int near_l = 0, near_r = 0, fires_l = 0, fires_r = 0;
@@ -466,20 +504,26 @@ static void face_field_k2(const double w[6], const orc_params* p, const uint8_t*
                 fires_r = (*replay & ORC_FLAG_SWITCH_R_K2) ? 1 : 0;
             }
         }
+        int z1 = 0, z2 = 0;
         if (fires_l) {
             fl |= ORC_FLAG_SWITCH;
         } else {
-            eta_l = orc_eta_k2_cross(&w[1], 0, 1, tl, p);
-            eta_lx = orc_eta_k2_cross(&w[1], 0, 0, tl, p);
+            eta_l = eta_k2_cross_z(&w[1], 0, 1, tl, p, &z1);
+            eta_lx = eta_k2_cross_z(&w[1], 0, 0, tl, p, &z2);
+            zr |= (uint8_t)(z1 | z2); /* ORC_ZERO_GUARD_L = 1, ORC_ZERO_BOUND_L = 2 */
         }
+        count_eta(p, fires_l, (zr & ORC_ZERO_GUARD_L) != 0, (zr & ORC_ZERO_BOUND_L) != 0);
         if (fires_r) {
             fl |= ORC_FLAG_SWITCH_R_K2;
         } else {
-            eta_r = orc_eta_k2_cross(&w[2], 1, 1, tr, p);
-            eta_rx = orc_eta_k2_cross(&w[2], 1, 0, tr, p);
+            eta_r = eta_k2_cross_z(&w[2], 1, 1, tr, p, &z1);
+            eta_rx = eta_k2_cross_z(&w[2], 1, 0, tr, p, &z2);
+            zr |= (uint8_t)((z1 | z2) << 2); /* ORC_ZERO_GUARD_R, ORC_ZERO_BOUND_R */
         }
+        count_eta(p, fires_r, (zr & ORC_ZERO_GUARD_R) != 0, (zr & ORC_ZERO_BOUND_R) != 0);
         if (near_l || near_r) fl |= ORC_FLAG_SWITCH_TIE;
     }
+    if (reason) *reason = zr;
     int rl = 0, rr = 0, nl = 0, nr = 0, fl_r = -1, fr_r = -1;
     if (replay && (p->scheme == ORC_ENO || p->scheme == ORC_RBF_ENO)) {
         fl_r = (*replay >> 2) & 1;
@@ -560,7 +604,7 @@ int orc_euler_eigvec(const double UL[3], const double UR[3], double gamma, doubl
 /* trans: [m][n] transverse second differences of the cells of the line (NULL: none). */
 static int recon_line(const double* u, long n, int m, long stride, long m_stride, int bc, const orc_params* p,
                       double* vm, double* vp, uint8_t* flags, double* eta, const uint8_t* replay, long out_stride,
-                      const double* trans) {
+                      const double* trans, uint8_t* reason) {
     for (long f = 0; f <= n; ++f) {
         if (p->characteristic && m == 3) {
             double U[6][3], W[6][3], R[3][3], L[3][3];
@@ -581,7 +625,7 @@ static int recon_line(const double* u, long n, int m, long stride, long m_stride
                 uint8_t fl;
                 double et;
                 const uint8_t* rp = replay ? &replay[a * out_stride + f] : NULL;
-                face_field(line, p, rp, &wm[a], &wp[a], &fl, &et, 0.0, 0.0);
+                face_field(line, p, rp, &wm[a], &wp[a], &fl, &et, 0.0, 0.0, reason ? &reason[a * out_stride + f] : NULL);
                 if (flags) flags[a * out_stride + f] = fl;
                 if (eta) eta[a * out_stride + f] = et;
             }
@@ -606,7 +650,8 @@ static int recon_line(const double* u, long n, int m, long stride, long m_stride
                     tl = line_get(trans + k * n, n, 1, f - 1, bc, 0.0);
                     tr = line_get(trans + k * n, n, 1, f, bc, 0.0);
                 }
-                face_field(line, p, rp, &vm[k * out_stride + f], &vp[k * out_stride + f], &fl, &et, tl, tr);
+                face_field(line, p, rp, &vm[k * out_stride + f], &vp[k * out_stride + f], &fl, &et, tl, tr,
+                           reason ? &reason[k * out_stride + f] : NULL);
                 if (flags) flags[k * out_stride + f] = fl;
                 if (eta) eta[k * out_stride + f] = et;
             }
@@ -625,10 +670,10 @@ static int check_params(long n, int m, const orc_params* p) {
 }
 
 int orc_reconstruct(const double* u, long n, int m, int bc, const orc_params* p, double* vm, double* vp,
-                    uint8_t* flags, double* eta, const uint8_t* replay) {
+                    uint8_t* flags, double* eta, const uint8_t* replay, uint8_t* reason) {
     int st = check_params(n, m, p);
     if (st) return st;
-    return recon_line(u, n, m, 1, n, bc, p, vm, vp, flags, eta, replay, n + 1, NULL);
+    return recon_line(u, n, m, 1, n, bc, p, vm, vp, flags, eta, replay, n + 1, NULL, reason);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -729,7 +774,7 @@ static int rhs_1d(const double* u, long n, int m, double dx, int kind, int bc, d
     double* vp = malloc(sizeof(double) * m * nf);
     double* h = malloc(sizeof(double) * m * nf);
     int st = (vm && vp && h) ? ORC_OK : ORC_ENOMEM;
-    if (!st) st = recon_line(u, n, m, 1, n, bc, p, vm, vp, NULL, NULL, NULL, nf, NULL);
+    if (!st) st = recon_line(u, n, m, 1, n, bc, p, vm, vp, NULL, NULL, NULL, nf, NULL, NULL);
     if (!st) st = orc_flux(vm, vp, nf, m, kind, 0, alpha, p, h);
     if (!st)
         for (int k = 0; k < m; ++k)
@@ -783,7 +828,7 @@ int orc_reconstruct_2d(const double* u, long nx, long ny, int m, int bc, const o
     st = (vm && vp && tr) ? ORC_OK : ORC_ENOMEM;
     for (long j = 0; j < ny && !st; ++j) {
         if (use_cross(p)) transverse_line(u, nx, ny, m, bc, bcy, p, 0, j, tr);
-        st = recon_line(u + j * nx, nx, m, 1, cells, bc, p, vm, vp, NULL, NULL, NULL, nx + 1, use_cross(p) ? tr : NULL);
+        st = recon_line(u + j * nx, nx, m, 1, cells, bc, p, vm, vp, NULL, NULL, NULL, nx + 1, use_cross(p) ? tr : NULL, NULL);
         for (int k = 0; k < m && !st; ++k)
             for (long i = 0; i <= nx; ++i) {
                 vmx[(k * ny + j) * (nx + 1) + i] = vm[k * (nx + 1) + i];
@@ -792,7 +837,7 @@ int orc_reconstruct_2d(const double* u, long nx, long ny, int m, int bc, const o
     }
     for (long i = 0; i < nx && !st; ++i) {
         if (use_cross(p)) transverse_line(u, nx, ny, m, bc, bcy, p, 1, i, tr);
-        st = recon_line(u + i, ny, m, nx, cells, bcy, p, vm, vp, NULL, NULL, NULL, ny + 1, use_cross(p) ? tr : NULL);
+        st = recon_line(u + i, ny, m, nx, cells, bcy, p, vm, vp, NULL, NULL, NULL, ny + 1, use_cross(p) ? tr : NULL, NULL);
         for (int k = 0; k < m && !st; ++k)
             for (long j = 0; j <= ny; ++j) {
                 vmy[(k * (ny + 1) + j) * nx + i] = vm[k * (ny + 1) + j];
@@ -822,7 +867,7 @@ static int rhs_2d(const double* u, long nx, long ny, int m, double dx, double dy
     /* x sweeps: row j */
     for (long j = 0; j < ny && !st; ++j) {
         if (use_cross(p)) transverse_line(u, nx, ny, m, bc, bcy, p, 0, j, tr);
-        st = recon_line(u + j * nx, nx, m, 1, cells, bc, p, vm, vp, NULL, NULL, NULL, nx + 1, use_cross(p) ? tr : NULL);
+        st = recon_line(u + j * nx, nx, m, 1, cells, bc, p, vm, vp, NULL, NULL, NULL, nx + 1, use_cross(p) ? tr : NULL, NULL);
         if (!st) st = orc_flux(vm, vp, nx + 1, m, kind, 0, ax, p, h);
         for (int k = 0; k < m && !st; ++k)
             for (long i = 0; i < nx; ++i) L[k * cells + j * nx + i] -= (h[k * (nx + 1) + i + 1] - h[k * (nx + 1) + i]) / dx;
@@ -830,7 +875,7 @@ static int rhs_2d(const double* u, long nx, long ny, int m, double dx, double dy
     /* y sweeps: column i */
     for (long i = 0; i < nx && !st; ++i) {
         if (use_cross(p)) transverse_line(u, nx, ny, m, bc, bcy, p, 1, i, tr);
-        st = recon_line(u + i, ny, m, nx, cells, bcy, p, vm, vp, NULL, NULL, NULL, ny + 1, use_cross(p) ? tr : NULL);
+        st = recon_line(u + i, ny, m, nx, cells, bcy, p, vm, vp, NULL, NULL, NULL, ny + 1, use_cross(p) ? tr : NULL, NULL);
         if (!st) st = orc_flux(vm, vp, ny + 1, m, kind, 1, ay, p, h);
         for (int k = 0; k < m && !st; ++k)
             for (long j = 0; j < ny; ++j) L[k * cells + j * nx + i] -= (h[k * (ny + 1) + j + 1] - h[k * (ny + 1) + j]) / dy;

@@ -26,6 +26,19 @@ enum { ORC_FLUX_ADVECTION = 0, ORC_FLUX_BURGERS = 1, ORC_FLUX_EULER1D = 2, ORC_F
  * ENO stencil r (0 or 1) of the left / right cell; bit 1 marks a near tie of either switch. */
 #define ORC_FLAG_SWITCH_R_K2 0x08
 
+/* per-face "zero reason" byte of orc_reconstruct: an evaluated shape parameter set to 0 by the
+ * optional guard or bound (neither is in the paper; both are off by default).  k = 3 has one
+ * eta per face (the _L bits); k = 2 has one per face value: _L for v^- (the left cell), _R for
+ * v^+ (the right cell). */
+#define ORC_ZERO_GUARD_L 0x01
+#define ORC_ZERO_BOUND_L 0x02
+#define ORC_ZERO_GUARD_R 0x04
+#define ORC_ZERO_BOUND_R 0x08
+
+/* orc_params.counters[ORC_NCOUNTERS] (optional): shape-parameter decisions, per face (k = 3)
+ * or per face value (k = 2), accumulated over every reconstruction that sees the params */
+enum { ORC_CNT_SWITCH = 0, ORC_CNT_EVAL = 1, ORC_CNT_GUARD = 2, ORC_CNT_BOUND = 3, ORC_NCOUNTERS = 4 };
+
 typedef struct {
     int scheme;          /* ORC_ENO .. ORC_RBF_WENO */
     int rbf;             /* ORC_RBF_MQ / ORC_RBF_GA */
@@ -43,7 +56,8 @@ typedef struct {
     double inflow[4]; /* ghost state for the inflow boundary */
     double tie_tol;   /* relative margin that marks a decision as a near tie */
     double eta_guard; /* eta = 0 where |den| <= eta_guard * (|w0| + 15|w1| + 15|w2| + |w3|); 0 = off */
-    double eta_max;   /* eta = 0 where |eta| > eta_max; 0 = off */
+    double eta_max;   /* eta = 0 where |eta| > eta_max; 0 = off (the paper's eta) */
+    long* counters;   /* NULL, or ORC_NCOUNTERS counts that the reconstructions add to */
 } orc_params;
 
 typedef struct {
@@ -66,7 +80,7 @@ int orc_eno_choice(const double c[5], double tol, int* near_tie);
 void orc_beta_k3(const double c[5], double beta[3]);
 int orc_euler_eigvec(const double UL[3], const double UR[3], double gamma, double R[3][3], double L[3][3]);
 int orc_reconstruct(const double* u, long n, int m, int bc, const orc_params* p, double* vm, double* vp,
-                    uint8_t* flags, double* eta, const uint8_t* replay);
+                    uint8_t* flags, double* eta, const uint8_t* replay, uint8_t* reason);
 int orc_flux(const double* vm, const double* vp, long nf, int m, int kind, int dir, double alpha,
              const orc_params* p, double* h);
 double orc_max_speed(const double* u, long ncell, int m, int kind, int dir, const orc_params* p);

@@ -92,7 +92,10 @@ npw::MethodParams method(const npw_params* p) {
         mp.eta_guard = 8.0 * 5.9604644775390625e-08;
     else
         mp.eta_guard = 0.0;
-    mp.eta_max = p->eta_max > 0.0 ? p->eta_max : (p->eta_max == 0.0 ? 1.0 : 0.0);
+    // the shape parameter exactly as printed unless a bound is asked for
+    mp.eta_max = p->eta_max > 0.0 ? p->eta_max : 0.0;
+    mp.tie_tol = p->tie_tol > 0.0 ? p->tie_tol : 1e-10;
+    mp.max_steps = p->max_steps > 0 ? p->max_steps : 0;
     mp.eps_weno_f = (float)mp.eps_weno;
     mp.eps_M_f = (float)mp.eps_M;
     mp.eps_M_lo_f = (float)(mp.eps_M - (double)mp.eps_M_f);
@@ -283,7 +286,8 @@ void profile_collect() {
 namespace npw {
 
 // mode 0: reset; mode 1: start a solve (dt from alpha^0); mode 2: one step with fixed dt
-__global__ void ctl_start_kernel(Ctl* ctl, const InstDev* inst, int count, int mode, double dt_fixed) {
+__global__ void ctl_start_kernel(Ctl* ctl, const InstDev* inst, int count, int mode, double dt_fixed,
+                                 int64_t max_steps) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     Ctl* c = ctl + i;
@@ -322,9 +326,10 @@ __global__ void ctl_start_kernel(Ctl* ctl, const InstDev* inst, int count, int m
     }
     c->dt = dt;
     c->last = last;
+    c->step_cap = step_cap(in.t_end - c->t, dt, max_steps);
 }
 
-__global__ void ctl_start_2d_kernel(Ctl* c, const Inst2D* inst, int mode, double dt_fixed) {
+__global__ void ctl_start_2d_kernel(Ctl* c, const Inst2D* inst, int mode, double dt_fixed, int64_t max_steps) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (mode == 0) {
         memset(c, 0, sizeof(Ctl));
@@ -364,6 +369,7 @@ __global__ void ctl_start_2d_kernel(Ctl* c, const Inst2D* inst, int mode, double
     }
     c->dt = dt;
     c->last = last;
+    c->step_cap = step_cap(in.t_end - c->t, dt, max_steps);
 }
 
 // poll[0] = active instances, poll[1] = largest remaining step estimate
@@ -399,7 +405,8 @@ __global__ void count_active_kernel(const Ctl* ctl, const InstDev* inst, int cou
 
 // Server slots: mode 0 zeroes the control words of the listed slots; mode 1 starts them
 // (alpha^0 from the running max bits, first dt).
-__global__ void ctl_slots_kernel(Ctl* ctl, const InstDev* inst, const int32_t* list, int count, int mode) {
+__global__ void ctl_slots_kernel(Ctl* ctl, const InstDev* inst, const int32_t* list, int count, int mode,
+                                 int64_t max_steps) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= count) return;
     const int i = list[k];
@@ -433,6 +440,7 @@ __global__ void ctl_slots_kernel(Ctl* ctl, const InstDev* inst, const int32_t* l
     }
     c->dt = dt;
     c->last = last;
+    c->step_cap = step_cap(in.t_end - c->t, dt, max_steps);
 }
 
 }  // namespace npw
@@ -560,7 +568,7 @@ npw_status setup_1d(Run1D& r, const npw_instance* inst, int count, double dt_fix
     npw::Ctl* ctl = reinterpret_cast<npw::Ctl*>(r.ws + r.L.ctl);
     const npw::InstDev* di = reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst);
     const unsigned blocks = (unsigned)((count + 127) / 128);
-    npw::ctl_start_kernel<<<blocks, 128, 0, r.s>>>(ctl, di, count, 0, 0.0);
+    npw::ctl_start_kernel<<<blocks, 128, 0, r.s>>>(ctl, di, count, 0, 0.0, 0);
     NPW_CUDA(cudaGetLastError());
     cudaError_t e = r.ntiles == 0 ? cudaSuccess
                   : r.fp32 ? npw::launch_alpha_init<float>(r.arena, di, ctl,
@@ -570,7 +578,7 @@ npw_status setup_1d(Run1D& r, const npw_instance* inst, int count, double dt_fix
                                                             reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles),
                                                             (int)r.ntiles, r.tile, r.m, r.kind, r.mp, r.s);
     if (e != cudaSuccess) return cuda_fail(e, "alpha kernel launch");
-    npw::ctl_start_kernel<<<blocks, 128, 0, r.s>>>(ctl, di, count, mode, dt_fixed);
+    npw::ctl_start_kernel<<<blocks, 128, 0, r.s>>>(ctl, di, count, mode, dt_fixed, r.mp.max_steps);
     NPW_CUDA(cudaGetLastError());
     count_launch(3);
     if (r.comp && r.ntiles > 0) {
@@ -590,30 +598,38 @@ npw_status poll(const Run1D& r, long long* act, long long* rem, const npw::Inst2
                                                  r.count, inst2d, dpoll);
     NPW_CUDA(cudaGetLastError());
     count_launch();
-    long long h[2] = {0, 0};
-    NPW_CUDA(cudaMemcpyAsync(h, dpoll, sizeof h, cudaMemcpyDeviceToHost, r.s));
+    // wait (bounded) before the copy: a copy into pageable host memory returns only when the
+    // stream has drained, so issued first it would be an unbounded wait
     npw_status st = bounded_sync(r.s);
     if (st) return st;
+    long long h[2] = {0, 0};
+    NPW_CUDA(cudaMemcpyAsync(h, dpoll, sizeof h, cudaMemcpyDeviceToHost, r.s));
     profile_collect();
     *act = h[0];
     *rem = h[1];
     return NPW_OK;
 }
 
+void fill_stats(const npw::Ctl& c, npw_solve_stats* o) {
+    o->steps = c.steps;
+    o->t = c.t;
+    o->alpha_max = c.alpha_max;
+    o->status = c.status;
+    o->eta_switch = (int64_t)c.n_switch;
+    o->eta_eval = (int64_t)c.n_eval;
+    o->eta_guard = (int64_t)c.n_guard;
+    o->eta_bound = (int64_t)c.n_bound;
+}
+
 npw_status collect_stats(const Run1D& r, npw_solve_stats* out) {
     std::vector<npw::Ctl> hc(r.count);
-    NPW_CUDA(cudaMemcpyAsync(hc.data(), r.ws + r.L.ctl, sizeof(npw::Ctl) * r.count, cudaMemcpyDeviceToHost, r.s));
-    npw_status st = bounded_sync(r.s);
+    npw_status st = bounded_sync(r.s);  // before the (blocking) copy into pageable memory
     if (st) return st;
+    NPW_CUDA(cudaMemcpyAsync(hc.data(), r.ws + r.L.ctl, sizeof(npw::Ctl) * r.count, cudaMemcpyDeviceToHost, r.s));
     profile_collect();
     npw_status first = NPW_OK;
     for (int i = 0; i < r.count; ++i) {
-        if (out) {
-            out[i].steps = hc[i].steps;
-            out[i].t = hc[i].t;
-            out[i].alpha_max = hc[i].alpha_max;
-            out[i].status = hc[i].status;
-        }
+        if (out) fill_stats(hc[i], &out[i]);
         if (hc[i].status != NPW_OK && first == NPW_OK) first = (npw_status)hc[i].status;
     }
     if (first != NPW_OK) return fail(first, "an instance became non-finite");
@@ -735,6 +751,9 @@ struct StepGraph {
     ~StepGraph() {
         if (exec) cudaGraphExecDestroy(exec);
     }
+    // after a wait ran out the graph may still have launches queued: it is not destroyed
+    // (a small leak on that error path instead of destroying a graph that is in use)
+    void abandon() { exec = nullptr; }
 };
 
 npw_status capture_steps(const Run1D& r, StepGraph& g) {
@@ -791,6 +810,7 @@ npw_status run_to_end(Run1D& r, npw_solve_stats* out) {
         direct_done = true;
         if (st == NPW_OK) st = poll(r, &act, &rem);
     }
+    if (st == NPW_ETIMEOUT) graph.abandon();
     if (st == NPW_OK) st = comp_end(r);
     for (cudaEvent_t ev : r.joins) {  // resident kernels on the side streams
         cudaError_t e = cudaStreamWaitEvent(r.s, ev, 0);
@@ -863,10 +883,10 @@ void npw_profile_read(npw_profile* out) {
     }
 }
 
-int32_t npw_version(void) { return 10100; }
+int32_t npw_version(void) { return 10200; }
 
 npw_status npweno_reconstruct(const void* vbar, int64_t n, int32_t m, int32_t bc, const npw_params* params,
-                              void* v_minus, void* v_plus, uint8_t* flags, void* stream) {
+                              void* v_minus, void* v_plus, uint8_t* flags, void* eta, void* stream) {
     npw_status st = check_params(params);
     if (st) return st;
     if (!vbar || !v_minus || !v_plus) return fail(NPW_EINVAL, "null array pointer");
@@ -878,9 +898,9 @@ npw_status npweno_reconstruct(const void* vbar, int64_t n, int32_t m, int32_t bc
     npw::MethodParams mp = method(params);
     cudaError_t e = params->precision == NPW_FP32_MIXED
                         ? npw::launch_reconstruct<float>((const float*)vbar, n, m, bc, mp, (float*)v_minus,
-                                                         (float*)v_plus, flags, s)
+                                                         (float*)v_plus, flags, (float*)eta, s)
                         : npw::launch_reconstruct<double>((const double*)vbar, n, m, bc, mp, (double*)v_minus,
-                                                          (double*)v_plus, flags, s);
+                                                          (double*)v_plus, flags, (double*)eta, s);
     if (e != cudaSuccess) return cuda_fail(e, "reconstruct launch");
     count_launch();
     return NPW_OK;
@@ -961,8 +981,8 @@ npw_status npweno_rk3_step(void* u, int64_t n, int32_t m, double dx, double dt, 
     if ((st = comp_end(r))) return st;
     if (alpha_out) {
         npw::Ctl c;
-        NPW_CUDA(cudaMemcpyAsync(&c, r.ws + r.L.ctl, sizeof c, cudaMemcpyDeviceToHost, s));
         if ((st = bounded_sync(s))) return st;
+        NPW_CUDA(cudaMemcpyAsync(&c, r.ws + r.L.ctl, sizeof c, cudaMemcpyDeviceToHost, s));
         *alpha_out = c.alpha;
         if (c.status) return fail((npw_status)c.status, "state is not finite");
     }
@@ -1175,12 +1195,12 @@ static npw_status run_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx, 
     const int tiles = hi.tiles_x * hi.tiles_y;
     NPW_CUDA(cudaMemcpyAsync(dinst, &hi, sizeof hi, cudaMemcpyHostToDevice, s));
     npw::MethodParams mp = method(params);
-    npw::ctl_start_2d_kernel<<<1, 32, 0, s>>>(ctl, dinst, 0, 0.0);
+    npw::ctl_start_2d_kernel<<<1, 32, 0, s>>>(ctl, dinst, 0, 0.0, 0);
     NPW_CUDA(cudaGetLastError());
     cudaError_t e = fp32 ? npw::launch_alpha_init_2d<float>(u, dinst, tiles, ctl, flux_kind, mp, s)
                          : npw::launch_alpha_init_2d<double>(u, dinst, tiles, ctl, flux_kind, mp, s);
     if (e != cudaSuccess) return cuda_fail(e, "alpha 2d launch");
-    npw::ctl_start_2d_kernel<<<1, 32, 0, s>>>(ctl, dinst, mode, dt_fixed);
+    npw::ctl_start_2d_kernel<<<1, 32, 0, s>>>(ctl, dinst, mode, dt_fixed, mp.max_steps);
     NPW_CUDA(cudaGetLastError());
     count_launch(3);
 
@@ -1221,14 +1241,9 @@ static npw_status run_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx, 
     }
     if (st) return st;
     npw::Ctl hc;
-    NPW_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, s));
     if ((st = bounded_sync(s))) return st;
-    if (out) {
-        out->steps = hc.steps;
-        out->t = hc.t;
-        out->alpha_max = hc.alpha_max;
-        out->status = hc.status;
-    }
+    NPW_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, s));
+    if (out) fill_stats(hc, out);
     if (hc.status) return fail((npw_status)hc.status, "state is not finite");
     return NPW_OK;
 }
@@ -1607,14 +1622,14 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
         h2.tiles_y = (int32_t)((sl.req.ny + npw::TY_2D - 1) / npw::TY_2D);
         npw::Inst2D* d2 = reinterpret_cast<npw::Inst2D*>(sv->arena + sv->L.inst2d) + k;
         NPW_CUDA(cudaMemcpyAsync(d2, &h2, sizeof h2, cudaMemcpyHostToDevice, sv->s));
-        npw::ctl_start_2d_kernel<<<1, 32, 0, sv->s>>>(ctl + k, d2, 0, 0.0);
+        npw::ctl_start_2d_kernel<<<1, 32, 0, sv->s>>>(ctl + k, d2, 0, 0.0, 0);
         NPW_CUDA(cudaGetLastError());
         cudaError_t ce = sv->fp32 ? npw::launch_alpha_init_2d<float>(sv->arena + sv->L.heap_u, d2, sv->tiles2d(k),
                                                                       ctl + k, sl.req.flux_kind, sv->mp, sv->s)
                                   : npw::launch_alpha_init_2d<double>(sv->arena + sv->L.heap_u, d2, sv->tiles2d(k),
                                                                        ctl + k, sl.req.flux_kind, sv->mp, sv->s);
         if (ce != cudaSuccess) return cuda_fail(ce, "server alpha 2d launch");
-        npw::ctl_start_2d_kernel<<<1, 32, 0, sv->s>>>(ctl + k, d2, 1, 0.0);
+        npw::ctl_start_2d_kernel<<<1, 32, 0, sv->s>>>(ctl + k, d2, 1, 0.0, sv->mp.max_steps);
         NPW_CUDA(cudaGetLastError());
         count_launch(3);
     }
@@ -1625,7 +1640,7 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
         NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.newtiles, newtiles.data(), sizeof(npw::Tile) * newtiles.size(),
                                  cudaMemcpyHostToDevice, sv->s));
         const unsigned blocks = (unsigned)((fresh.size() + 127) / 128);
-        npw::ctl_slots_kernel<<<blocks, 128, 0, sv->s>>>(ctl, dinst, dlist, (int)fresh.size(), 0);
+        npw::ctl_slots_kernel<<<blocks, 128, 0, sv->s>>>(ctl, dinst, dlist, (int)fresh.size(), 0, 0);
         NPW_CUDA(cudaGetLastError());
         // alpha^0 per fresh request, one launch per flux kind over its fresh tiles
         size_t b = 0;
@@ -1642,7 +1657,7 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
             count_launch();
             b = e;
         }
-        npw::ctl_slots_kernel<<<blocks, 128, 0, sv->s>>>(ctl, dinst, dlist, (int)fresh.size(), 1);
+        npw::ctl_slots_kernel<<<blocks, 128, 0, sv->s>>>(ctl, dinst, dlist, (int)fresh.size(), 1, sv->mp.max_steps);
         NPW_CUDA(cudaGetLastError());
         count_launch(2);
         if (sv->comp) {  // compensated float kernels: s = u, c = 0 for the admitted requests
@@ -1668,8 +1683,8 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
                   : server_launch_steps<double>(sv, kind_tiles, kind_off, slots2d, steps);
     if (st) return st;
     // 5. read the control words, retire finished requests
-    NPW_CUDA(cudaMemcpyAsync(sv->host_ctl.data(), ctl, sizeof(npw::Ctl) * sv->max_slots, cudaMemcpyDeviceToHost, sv->s));
     if ((st = bounded_sync(sv->s))) return st;
+    NPW_CUDA(cudaMemcpyAsync(sv->host_ctl.data(), ctl, sizeof(npw::Ctl) * sv->max_slots, cudaMemcpyDeviceToHost, sv->s));
     profile_collect();
     std::vector<int> finished;
     long long rem = 0;

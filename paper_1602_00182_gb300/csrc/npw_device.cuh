@@ -269,17 +269,25 @@ __device__ __forceinline__ T lin_weight2(int side, int r) {
 // trans of the cell, with weight -1/4 for the stencil of the two cells at the face (central)
 // and 1/8 for the extrapolating one: the terms that cancel the transverse curvature of the
 // cell averages at the face midpoint.
+// *zr receives FL_ZERO_GUARD / FL_ZERO_BOUND where the guard / the bound set eta to 0
 template <typename D>
-__device__ __forceinline__ D eta_k2_cross(const D* c, int side, bool central, D trans, const MethodParams& mp) {
+__device__ __forceinline__ D eta_k2_cross(const D* c, int side, bool central, D trans, const MethodParams& mp,
+                                          uint32_t* zr) {
     const D a = side == 0 ? c[0] : c[2];
     const D b = c[1];
     const D d = side == 0 ? c[2] : c[0];
     const D num = -a + D(2.0) * b - d + (central ? D(-0.25) : D(0.125)) * trans;
     const D den0 = -a + D(5.0) * b + D(2.0) * d;
     const D mag = fabs(a) + D(5.0) * fabs(b) + D(2.0) * fabs(d);
-    if (mp.eta_guard > 0.0 && fabs(den0) <= D(mp.eta_guard) * mag) return D(0.0);
+    if (mp.eta_guard > 0.0 && fabs(den0) <= D(mp.eta_guard) * mag) {
+        *zr |= FL_ZERO_GUARD;
+        return D(0.0);
+    }
     const D e = (mp.rbf == NPW_RBF_GA_ ? D(1.0) : D(2.0)) * num / (den0 + D(mp.eps_M));
-    if (mp.eta_max > 0.0 && fabs(e) > D(mp.eta_max)) return D(0.0);
+    if (mp.eta_max > 0.0 && fabs(e) > D(mp.eta_max)) {
+        *zr |= FL_ZERO_BOUND;
+        return D(0.0);
+    }
     return e;
 }
 
@@ -321,47 +329,54 @@ __device__ __forceinline__ R cell_face_value_k2(const R* c, int side, R eta_c, R
 // One field at one face, k = 2.  w[0..5] = cells i-2..i+3 around face i+1/2; v^- from cell i
 // (stencil w[1..3]), v^+ from cell i+1 (stencil w[2..4]); tl, tr: transverse second
 // differences of cells i and i+1 (0 on a line).  Flag bits: 0 switch of cell i, 3 switch of
-// cell i+1, 2 / 4 ENO r of cell i / i+1.
+// cell i+1, 2 / 4 ENO r of cell i / i+1, 6 / 7 an eta of v^- zeroed by the guard / the bound,
+// 8 / 9 the same for v^+.
 template <typename R, typename D>
-__device__ __forceinline__ uint32_t face_field_k2(const R* w, const MethodParams& mp, R* vm, R* vp, R tl, R tr) {
+__device__ __forceinline__ uint32_t face_field_k2(const R* w, const MethodParams& mp, R* vm, R* vp, R tl, R tr,
+                                                  R* eta_out) {
     uint32_t fl = 0;
     R el = R(0.0), er = R(0.0), elx = R(0.0), erx = R(0.0);
     if (mp.scheme == NPW_RBF_ENO_ || mp.scheme == NPW_RBF_WENO_) {
         const D cl[3] = {D(w[1]), D(w[2]), D(w[3])};
         const D cr[3] = {D(w[2]), D(w[3]), D(w[4])};
         if (mp.monotone_switch && k2_ratio_fires<D>(cl[0], cl[1], cl[2])) {
-            fl |= 1u;
+            fl |= FL_SWITCH;
         } else {
-            el = R(eta_k2_cross<D>(cl, 0, true, D(tl), mp));
-            elx = tl == R(0.0) ? el : R(eta_k2_cross<D>(cl, 0, false, D(tl), mp));
+            el = R(eta_k2_cross<D>(cl, 0, true, D(tl), mp, &fl));
+            elx = tl == R(0.0) ? el : R(eta_k2_cross<D>(cl, 0, false, D(tl), mp, &fl));
         }
         if (mp.monotone_switch && k2_ratio_fires<D>(cr[0], cr[1], cr[2])) {
-            fl |= 8u;
+            fl |= FL_SWITCH_R_K2;
         } else {
-            er = R(eta_k2_cross<D>(cr, 1, true, D(tr), mp));
-            erx = tr == R(0.0) ? er : R(eta_k2_cross<D>(cr, 1, false, D(tr), mp));
+            uint32_t zr = 0;
+            er = R(eta_k2_cross<D>(cr, 1, true, D(tr), mp, &zr));
+            erx = tr == R(0.0) ? er : R(eta_k2_cross<D>(cr, 1, false, D(tr), mp, &zr));
+            fl |= zr << 2;  // FL_ZERO_GUARD_R_K2, FL_ZERO_BOUND_R_K2
         }
     }
     int rl = 0, rr = 0;
     *vm = cell_face_value_k2<R, D>(w + 1, 0, el, elx, mp, &rl);
     *vp = cell_face_value_k2<R, D>(w + 2, 1, er, erx, mp, &rr);
     fl |= (uint32_t(rl & 1) << 2) | (uint32_t(rr & 1) << 4);
+    if (eta_out) *eta_out = el;
     return fl;
 }
 
 // One field at one face.  w[0..5] = cells i-2..i+3 around face i+1/2.  Returns the flag
-// byte (bit0 switch, bits 2-3 / 4-5 ENO r of the left / right cell).
+// byte (bit0 switch, bits 2-3 / 4-5 ENO r of the left / right cell, bit 6 / 7 the evaluated eta
+// zeroed by the guard / the bound).
+// eta_out (may be NULL): the face's shape parameter as used (k = 2: that of v^-, central row)
 template <typename R, typename D>
 __device__ __forceinline__ uint32_t face_field(const R* w, const MethodParams& mp, R* vm, R* vp, R tl = R(0.0),
-                                               R tr = R(0.0)) {
-    if (mp.k == 2) return face_field_k2<R, D>(w, mp, vm, vp, tl, tr);
+                                               R tr = R(0.0), R* eta_out = nullptr) {
+    if (mp.k == 2) return face_field_k2<R, D>(w, mp, vm, vp, tl, tr, eta_out);
     uint32_t fl = 0;
     R eta = R(0.0);
     if (mp.scheme == NPW_RBF_ENO_ || mp.scheme == NPW_RBF_WENO_) {
         const D w1 = D(w[1]), w2 = D(w[2]), w3 = D(w[3]), w4 = D(w[4]);
         bool fires = mp.monotone_switch ? switch_fires<D>(w1, w2, w3, w4, mp.switch_variant) : false;
         if (fires) {
-            fl |= 1u;
+            fl |= FL_SWITCH;
         } else {
             D den0 = eta_den<D>(w1, w2, w3, w4);
             bool unresolved = mp.eta_guard > 0.0 &&
@@ -369,7 +384,12 @@ __device__ __forceinline__ uint32_t face_field(const R* w, const MethodParams& m
             if (!unresolved) {
                 D den = den0 + D(mp.eps_M);
                 D e = eta_num<D>(w1, w2, w3, w4) / den;
-                if (!(mp.eta_max > 0.0 && fabs(e) > D(mp.eta_max))) eta = R(e);
+                if (!(mp.eta_max > 0.0 && fabs(e) > D(mp.eta_max)))
+                    eta = R(e);
+                else
+                    fl |= FL_ZERO_BOUND;
+            } else {
+                fl |= FL_ZERO_GUARD;
             }
         }
     }
@@ -377,7 +397,93 @@ __device__ __forceinline__ uint32_t face_field(const R* w, const MethodParams& m
     *vm = cell_face_value<R, D>(w, 0, eta, mp, &rl);
     *vp = cell_face_value<R, D>(w + 1, 1, eta, mp, &rr);
     fl |= (uint32_t(rl & 3) << 2) | (uint32_t(rr & 3) << 4);
+    if (eta_out) *eta_out = eta;
     return fl;
+}
+
+// ---------------------------------------------------------------------------------------
+// Near ties of the decisions at one face (the FL_NEAR_TIE bit of npweno_reconstruct): a
+// quantity that decides the switch, the ENO choice, the guard or the bound lies within tol
+// (relative) of its threshold, so that two correct evaluations in different rounding orders
+// may decide differently.  Margins (all in double, from the cell averages):
+//   ENO (Sec. 2): ||d_L| - |d_R|| <= tol max(|d_L|, |d_R|) for the first and both second
+//     divided-difference comparisons;
+//   switch variant 0 (Sec. 4, the cubic on the eta stencil): 12 p' at either end or at an
+//     inside vertex within 8 tol (|w0| + .. + |w3|) of 0 (times 12), or the vertex within
+//     8 tol of an end of the stencil;  the ratio test (variant 1, k = 2): its denominator
+//     within tol (|a| + |b| + |c|) of 0, or the ratio within 4 tol of 0 or 3;
+//   guard: |den| within tol of the guard threshold; bound: |eta| within tol of eta_max.
+// w[0..5] = cells i-2..i+3 of face i+1/2.
+// ---------------------------------------------------------------------------------------
+// two exactly equal zeros (a plateau) compare the same way in any evaluation: not a tie
+__device__ __forceinline__ bool tie_rel(double a, double b, double tol) {
+    const double m = fmax(fabs(a), fabs(b));
+    return m > 0.0 && fabs(a - b) <= tol * m;
+}
+__device__ __forceinline__ bool k2_ratio_near(double a, double b, double c, double tol) {
+    if (a == b && b == c) return false;  // constant stencil: monotone, decided exactly
+    const double num = -2.0 * a + 3.0 * b - c, den = -a + 2.0 * b - c;
+    if (fabs(den) <= tol * (fabs(a) + fabs(b) + fabs(c))) return true;
+    if (den == 0.0) return false;
+    const double r = num / den;
+    return fabs(r) <= 4.0 * tol || fabs(r - 3.0) <= 4.0 * tol;
+}
+__device__ __forceinline__ bool eno_near(const double* c, double tol) {
+    const double dl = fabs(c[2] - c[1]), dr = fabs(c[3] - c[2]);
+    return tie_rel(dl, dr, tol) || tie_rel(fabs(c[0] - 2.0 * c[1] + c[2]), fabs(c[1] - 2.0 * c[2] + c[3]), tol) ||
+           tie_rel(fabs(c[1] - 2.0 * c[2] + c[3]), fabs(c[2] - 2.0 * c[3] + c[4]), tol);
+}
+__device__ __forceinline__ bool switch_v0_near(const double* w, double tol) {
+    if (w[0] == w[1] && w[1] == w[2] && w[2] == w[3]) return false;  // constant stencil
+    const double A = 6.0 * ((w[3] - w[0]) + 3.0 * (w[1] - w[2]));
+    const double B = 6.0 * ((w[0] - w[1]) + (w[3] - w[2]));
+    const double C = (w[0] - w[3]) + 15.0 * (w[2] - w[1]);
+    const double lim = 12.0 * 8.0 * tol * (fabs(w[0]) + fabs(w[1]) + fabs(w[2]) + fabs(w[3]));
+    bool near = fabs(4.0 * A - 2.0 * B + C) <= lim || fabs(4.0 * A + 2.0 * B + C) <= lim;
+    if (A != 0.0) {
+        const double sv = -B / (2.0 * A);
+        near = near || fabs(fabs(sv) - 2.0) <= 8.0 * tol;
+        if (fabs(sv) < 2.0) near = near || fabs(C - B * B / (4.0 * A)) <= lim;
+    }
+    return near;
+}
+template <typename R>
+__device__ __forceinline__ bool face_near_tie(const R* wr, const MethodParams& mp, double tol) {
+    double w[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) w[j] = (double)wr[j];
+    const bool rbf = mp.scheme == NPW_RBF_ENO_ || mp.scheme == NPW_RBF_WENO_;
+    const bool eno = mp.scheme == NPW_ENO_ || mp.scheme == NPW_RBF_ENO_;
+    bool near = false;
+    if (mp.k == 2) {
+        if (eno) near = tie_rel(fabs(w[2] - w[1]), fabs(w[3] - w[2]), tol) || tie_rel(fabs(w[3] - w[2]), fabs(w[4] - w[3]), tol);
+        if (rbf && mp.monotone_switch) near = near || k2_ratio_near(w[1], w[2], w[3], tol) || k2_ratio_near(w[2], w[3], w[4], tol);
+        if (rbf) {
+            for (int side = 0; side < 2; ++side) {
+                const double* c = w + 1 + side;  // cell i (side 0, v^-) or i + 1 (side 1, v^+)
+                const double a = side == 0 ? c[0] : c[2], b = c[1], d = side == 0 ? c[2] : c[0];
+                const double den0 = -a + 5.0 * b + 2.0 * d, mag = fabs(a) + 5.0 * fabs(b) + 2.0 * fabs(d);
+                if (mp.eta_guard > 0.0) near = near || tie_rel(fabs(den0), mp.eta_guard * mag, tol);
+                if (mp.eta_max > 0.0) {
+                    const double e = (mp.rbf == NPW_RBF_GA_ ? 1.0 : 2.0) * (-a + 2.0 * b - d) / (den0 + mp.eps_M);
+                    near = near || tie_rel(fabs(e), mp.eta_max, tol);
+                }
+            }
+        }
+        return near;
+    }
+    if (eno) near = eno_near(w, tol) || eno_near(w + 1, tol);
+    if (rbf && mp.monotone_switch)
+        near = near || (mp.switch_variant == 1 ? (k2_ratio_near(w[1], w[2], w[3], tol) || k2_ratio_near(w[2], w[3], w[4], tol))
+                                               : switch_v0_near(w + 1, tol));
+    if (rbf) {
+        const double den0 = eta_den<double>(w[1], w[2], w[3], w[4]);
+        const double mag = fabs(w[1]) + 15.0 * fabs(w[2]) + 15.0 * fabs(w[3]) + fabs(w[4]);
+        if (mp.eta_guard > 0.0) near = near || tie_rel(fabs(den0), mp.eta_guard * mag, tol);
+        if (mp.eta_max > 0.0)
+            near = near || tie_rel(fabs(eta_num<double>(w[1], w[2], w[3], w[4]) / (den0 + mp.eps_M)), mp.eta_max, tol);
+    }
+    return near;
 }
 
 // ---------------------------------------------------------------------------------------

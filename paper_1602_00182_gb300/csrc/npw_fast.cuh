@@ -284,12 +284,16 @@ __device__ __forceinline__ float eta_quot(float nh, float nl, float eh, float el
 static __device__ __noinline__ float eta_quot_any(float nh, float nl, float eh, float el) {
     return eta_quot<false>(nh, nl, eh, el);
 }
-__device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3, const FParams& fp, float guard) {
+__device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3, const FParams& fp, float guard,
+                                          uint32_t* fl) {
     float nh, nl, dh, dl;
     eta_pairs(w0, w1, w2, w3, nh, nl, dh, dl);
     if (guard > 0.0f && fabsf(dh + dl) <= guard * (1.0f + 2.0f * kU)) {
         // near or below the guard: decide in double
-        if (fabs(widen(dh) + widen(dl)) <= widen(guard)) return 0.0f;
+        if (fabs(widen(dh) + widen(dl)) <= widen(guard)) {
+            *fl |= FL_ZERO_GUARD;
+            return 0.0f;
+        }
     }
     float eh, et;
     two_sum(dh, fp.eps_M_f, eh, et);
@@ -301,10 +305,14 @@ __device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3
 
 // Double-float evaluation (no FP64 instruction): the pairs of eta_pairs, eps_M added by
 // two_sum, renormalised, and the double-float quotient (one correction of the float quotient).
-__device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, float w3, float eps_M, float guard) {
+__device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, float w3, float eps_M, float guard,
+                                                 uint32_t* fl) {
     float nh, nl, dh, dl;
     eta_pairs(w0, w1, w2, w3, nh, nl, dh, dl);
-    if (guard > 0.0f && fabsf(dh + dl) <= guard) return 0.0f;
+    if (guard > 0.0f && fabsf(dh + dl) <= guard) {
+        *fl |= FL_ZERO_GUARD;
+        return 0.0f;
+    }
     float t;
     two_sum(dh, eps_M, dh, t);
     dl += t;
@@ -327,21 +335,27 @@ __device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, f
 // The guard sets eta = 0 where the denominator is below eta_guard times the sum of the
 // magnitudes of its terms: such a denominator is round-off of the cell averages, and the
 // quotient would be noise amplified by 1/eps_M.
-__device__ __forceinline__ float eta_eval(float w0, float w1, float w2, float w3, const FParams& fp) {
+__device__ __forceinline__ float eta_eval(float w0, float w1, float w2, float w3, const FParams& fp, uint32_t* fl) {
     const float guard = fp.eta_guard * (fabsf(w0) + 15.f * fabsf(w1) + 15.f * fabsf(w2) + fabsf(w3));
-    return fp.eta_eval == 1 ? eta_doublefloat(w0, w1, w2, w3, fp.eps_M_f, guard) : eta_fp64(w0, w1, w2, w3, fp, guard);
+    return fp.eta_eval == 1 ? eta_doublefloat(w0, w1, w2, w3, fp.eps_M_f, guard, fl)
+                            : eta_fp64(w0, w1, w2, w3, fp, guard, fl);
 }
 
-// eta of the face whose eta stencil is (w0..w3), 0 where the switch fires; flag bit0 = switch
+// eta of the face whose eta stencil is (w0..w3), 0 where the switch fires; flag bits: FL_SWITCH,
+// FL_ZERO_GUARD, FL_ZERO_BOUND
 __device__ __forceinline__ float face_eta(float w0, float w1, float w2, float w3, const FParams& fp,
                                           uint32_t* flag) {
     if (fp.scheme != NPW_RBF_ENO_ && fp.scheme != NPW_RBF_WENO_) return 0.0f;
     if (fp.monotone_switch && switch_fires_f(w0, w1, w2, w3, fp.switch_variant)) {
-        *flag |= 1u;
+        *flag |= FL_SWITCH;
         return 0.0f;
     }
-    const float e = eta_eval(w0, w1, w2, w3, fp);
-    return (fp.eta_max > 0.0f && fabsf(e) > fp.eta_max) ? 0.0f : e;
+    const float e = eta_eval(w0, w1, w2, w3, fp, flag);
+    if (fp.eta_max > 0.0f && fabsf(e) > fp.eta_max) {
+        *flag |= FL_ZERO_BOUND;
+        return 0.0f;
+    }
+    return e;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -467,7 +481,7 @@ __device__ __forceinline__ float cell_value_k2_f(const float* c, int side, float
 // cross, 2 more for the two numerators).
 template <bool NZ>
 __device__ __forceinline__ void eta_k2_quot(float bh, float bl, float dh, float dl, double trans, const FParams& fp,
-                                            float* ec, float* ex) {
+                                            float* ec, float* ex, uint32_t* fl) {
     const double base = widen_as<NZ>(bh) + widen_as<NZ>(bl);
     const double den = widen_as<NZ>(dh) + widen_as<NZ>(dl);
     float denf, vc, vx;
@@ -492,15 +506,18 @@ __device__ __forceinline__ void eta_k2_quot(float bh, float bl, float dh, float 
         vx *= 2.0f;
     }
     const float bound = fp.eta_max;
-    *ec = (bound > 0.0f && fabsf(vc) > bound) ? 0.0f : vc;
-    *ex = (bound > 0.0f && fabsf(vx) > bound) ? 0.0f : vx;
+    const bool zc = bound > 0.0f && fabsf(vc) > bound, zx = bound > 0.0f && fabsf(vx) > bound;
+    *ec = zc ? 0.0f : vc;
+    *ex = zx ? 0.0f : vx;
+    if (zc | zx) *fl |= FL_ZERO_BOUND;
 }
 static __device__ __noinline__ void eta_k2_quot_any(float bh, float bl, float dh, float dl, double trans,
-                                                    const FParams& fp, float* ec, float* ex) {
-    eta_k2_quot<false>(bh, bl, dh, dl, trans, fp, ec, ex);
+                                                    const FParams& fp, float* ec, float* ex, uint32_t* fl) {
+    eta_k2_quot<false>(bh, bl, dh, dl, trans, fp, ec, ex, fl);
 }
+// fl: FL_ZERO_GUARD / FL_ZERO_BOUND where the guard / the bound set a shape parameter to 0
 __device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double trans, const MethodParams& mp,
-                                            const FParams& fp, float* ec, float* ex) {
+                                            const FParams& fp, float* ec, float* ex, uint32_t* fl) {
     const float af = side == 0 ? cf[0] : cf[2], bf = cf[1], df = side == 0 ? cf[2] : cf[0];
     *ec = *ex = 0.0f;
     if (fp.eta_guard > 0.0f) {
@@ -509,7 +526,10 @@ __device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double tr
         const float gm = fp.eta_guard * magf;
         if (!(fabsf(den0f) > gm + kE * magf * (1.0f + fp.eta_guard))) {
             const double a = widen(af), b = widen(bf), d = widen(df);
-            if (fabs((-a + 5.0 * b) + 2.0 * d) <= mp.eta_guard * ((fabs(a) + 5.0 * fabs(b)) + 2.0 * fabs(d))) return;
+            if (fabs((-a + 5.0 * b) + 2.0 * d) <= mp.eta_guard * ((fabs(a) + 5.0 * fabs(b)) + 2.0 * fabs(d))) {
+                *fl |= FL_ZERO_GUARD;
+                return;
+            }
         }
     }
     float p, pe, q, qe, bh, be, s1, e1, s2, e2, dh, dt;
@@ -522,59 +542,85 @@ __device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double tr
     two_sum(s2, fp.eps_M_f, dh, dt);
     const float dl = ((e1 + e2) + pe) + (dt + fp.eps_M_lo);
     if (zero_or_normal(bh) & zero_or_normal(bl) & zero_or_normal(dh) & zero_or_normal(dl))
-        eta_k2_quot<true>(bh, bl, dh, dl, trans, fp, ec, ex);
+        eta_k2_quot<true>(bh, bl, dh, dl, trans, fp, ec, ex, fl);
     else
-        eta_k2_quot_any(bh, bl, dh, dl, trans, fp, ec, ex);
+        eta_k2_quot_any(bh, bl, dh, dl, trans, fp, ec, ex, fl);
 }
+
+// Decisions of a k = 2 cell, as returned by cell_recon_k2: FL_SWITCH (the cell's switch fired:
+// both its shape parameters are 0), FL_ZERO_GUARD / FL_ZERO_BOUND for the side-0 (v^-) value and
+// the same bits shifted by K2_SIDE1 for the side-1 (v^+) value; 0 for schemes without eta.
+constexpr int K2_SIDE1 = 8;
+constexpr uint32_t K2_EVAL = 0x10000u;  // the cell's shape parameters were evaluated
 
 // Both face values of one k = 2 cell (c3 = cells i-1..i+1, trans its transverse second
 // difference or 0): v^- at its right face and v^+ at its left face, with the arithmetic that
-// face_field_k2 gives them face by face.
-__device__ __forceinline__ void cell_recon_k2(const float* c3, double trans, const MethodParams& mp0, const FParams& fp,
-                                              float* vm, float* vp) {
+// face_field_k2 gives them face by face.  Returns the cell's decision bits.
+__device__ __forceinline__ uint32_t cell_recon_k2(const float* c3, double trans, const MethodParams& mp0,
+                                                  const FParams& fp, float* vm, float* vp) {
     float e0c = 0.0f, e0x = 0.0f, e1c = 0.0f, e1x = 0.0f;
-    if ((fp.scheme == NPW_RBF_ENO_ || fp.scheme == NPW_RBF_WENO_) &&
-        !(fp.monotone_switch && switch_k2_f(c3[0], c3[1], c3[2]))) {
-        eta_k2_pair(c3, 0, trans, mp0, fp, &e0c, &e0x);
-        eta_k2_pair(c3, 1, trans, mp0, fp, &e1c, &e1x);
+    uint32_t d = 0, f0 = 0, f1 = 0;
+    if (fp.scheme == NPW_RBF_ENO_ || fp.scheme == NPW_RBF_WENO_) {
+        if (fp.monotone_switch && switch_k2_f(c3[0], c3[1], c3[2])) {
+            d = FL_SWITCH;
+        } else {
+            eta_k2_pair(c3, 0, trans, mp0, fp, &e0c, &e0x, &f0);
+            eta_k2_pair(c3, 1, trans, mp0, fp, &e1c, &e1x, &f1);
+            d = K2_EVAL | f0 | (f1 << K2_SIDE1);
+        }
     }
     int r;
     *vm = cell_value_k2_f(c3, 0, e0c, e0x, fp, &r);
     *vp = cell_value_k2_f(c3, 1, e1c, e1x, fp, &r);
+    return d;
+}
+
+// counts of one face value of a k = 2 cell from its decision bits (side 0: v^-, 1: v^+)
+__device__ __forceinline__ void count_k2(EtaCount& c, uint32_t d, int side) {
+    c.sw += d & FL_SWITCH;
+    c.ev += d >> 16;
+    const uint32_t z = side ? (d >> K2_SIDE1) : d;
+    c.guard += (z >> 6) & 1u;
+    c.bound += (z >> 7) & 1u;
 }
 
 // tl, tr: transverse second differences of the two cells (the 5-cell cross of Sec. 6; 0 on a
 // line), taken in double from the float cell averages like the rest of the shape parameter
 __device__ __forceinline__ uint32_t face_field_k2(const float* w, const MethodParams& mp0, float* vm, float* vp,
-                                                  double tl, double tr) {
+                                                  double tl, double tr, float* eta_out) {
     const FParams fp = fparams(mp0);
     uint32_t fl = 0;
     float el = 0.0f, er = 0.0f, elx = 0.0f, erx = 0.0f;
     if (fp.scheme == NPW_RBF_ENO_ || fp.scheme == NPW_RBF_WENO_) {
         if (fp.monotone_switch && switch_k2_f(w[1], w[2], w[3]))
-            fl |= 1u;
+            fl |= FL_SWITCH;
         else
-            eta_k2_pair(w + 1, 0, tl, mp0, fp, &el, &elx);
+            eta_k2_pair(w + 1, 0, tl, mp0, fp, &el, &elx, &fl);
+        uint32_t zr = 0;
         if (fp.monotone_switch && switch_k2_f(w[2], w[3], w[4]))
-            fl |= 8u;
+            fl |= FL_SWITCH_R_K2;
         else
-            eta_k2_pair(w + 2, 1, tr, mp0, fp, &er, &erx);
+            eta_k2_pair(w + 2, 1, tr, mp0, fp, &er, &erx, &zr);
+        fl |= zr << 2;  // FL_ZERO_GUARD_R_K2, FL_ZERO_BOUND_R_K2
     }
     int rl = 0, rr = 0;
     *vm = cell_value_k2_f(w + 1, 0, el, elx, fp, &rl);
     *vp = cell_value_k2_f(w + 2, 1, er, erx, fp, &rr);
+    if (eta_out) *eta_out = el;
     return fl | (uint32_t(rl & 1) << 2) | (uint32_t(rr & 1) << 4);
 }
 
+// eta_out (may be NULL): the face's shape parameter as used (k = 2: that of v^-, central row)
 __device__ __forceinline__ uint32_t face_field(const float* w, const MethodParams& mp0, float* vm, float* vp,
-                                               double tl = 0.0, double tr = 0.0) {
-    if (mp0.k == 2) return face_field_k2(w, mp0, vm, vp, tl, tr);
+                                               double tl = 0.0, double tr = 0.0, float* eta_out = nullptr) {
+    if (mp0.k == 2) return face_field_k2(w, mp0, vm, vp, tl, tr, eta_out);
     uint32_t fl = 0;
     const FParams mp = fparams(mp0);
     const float eta = face_eta(w[1], w[2], w[3], w[4], mp, &fl);
     float dummy;
     const int rl = cell_recon(w, eta, eta, mp, vm, &dummy);
     const int rr = cell_recon(w + 1, eta, eta, mp, &dummy, vp);
+    if (eta_out) *eta_out = eta;
     return fl | (uint32_t(rl & 3) << 2) | (uint32_t(rr & 3) << 4);
 }
 
@@ -583,21 +629,22 @@ __device__ __forceinline__ uint32_t face_field(const float* w, const MethodParam
 // the literal double-precision arithmetic for R = double, the mixed path for R = float
 template <typename R, typename D>
 __device__ __forceinline__ uint32_t face_field_any(const R* w, const MethodParams& mp, R* vm, R* vp, D tl = D(0.0),
-                                                   D tr = D(0.0)) {
+                                                   D tr = D(0.0), R* eta_out = nullptr) {
     if constexpr (sizeof(R) == sizeof(float)) {
-        return fast::face_field(w, mp, vm, vp, tl, tr);
+        return fast::face_field(w, mp, vm, vp, tl, tr, eta_out);
     } else {
-        return face_field<R, D>(w, mp, vm, vp, R(tl), R(tr));
+        return face_field<R, D>(w, mp, vm, vp, R(tl), R(tr), eta_out);
     }
 }
 
 // All M fields at one face from the 6 x M stencil W[j*M + k] (cells i-2..i+3).  For the
 // characteristic variant the fields are projected by L, reconstructed, and mapped back by R.
 // T (optional, component-wise): transverse second differences [2][M] of the face's left and
-// right cells, for the k = 2 shape parameter on the 5-cell cross (Sec. 6).
+// right cells, for the k = 2 shape parameter on the 5-cell cross (Sec. 6).  eta (optional):
+// the M shape parameters of the face (characteristic: of the characteristic fields).
 template <typename R, typename D, int KIND, int M, bool CHAR>
 __device__ __forceinline__ bool face_all(const R* S, const MethodParams& mp, R* vm, R* vp, uint32_t* flags,
-                                         const D* T = nullptr) {
+                                         const D* T = nullptr, R* eta = nullptr) {
     if (CHAR) {
         R Rm[3][3], Lm[3][3];
         if (!euler_eig<R>(S + 2 * M, S + 3 * M, mp_val<R>(mp.gamma, mp.gamma_f), Rm, Lm)) return false;
@@ -612,7 +659,7 @@ __device__ __forceinline__ bool face_all(const R* S, const MethodParams& mp, R* 
                 for (int k = 0; k < 3; ++k) s += Lm[a][k] * S[j * M + k];
                 line[j] = s;
             }
-            flags[a] = face_field_any<R, D>(line, mp, &wm[a], &wp[a]);
+            flags[a] = face_field_any<R, D>(line, mp, &wm[a], &wp[a], D(0.0), D(0.0), eta ? eta + a : nullptr);
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -632,8 +679,8 @@ __device__ __forceinline__ bool face_all(const R* S, const MethodParams& mp, R* 
         R line[6];
 #pragma unroll
         for (int j = 0; j < 6; ++j) line[j] = S[j * M + k];
-        flags[k] = T ? face_field_any<R, D>(line, mp, &vm[k], &vp[k], T[k], T[M + k])
-                     : face_field_any<R, D>(line, mp, &vm[k], &vp[k]);
+        flags[k] = T ? face_field_any<R, D>(line, mp, &vm[k], &vp[k], T[k], T[M + k], eta ? eta + k : nullptr)
+                     : face_field_any<R, D>(line, mp, &vm[k], &vp[k], D(0.0), D(0.0), eta ? eta + k : nullptr);
     }
     return true;
 }

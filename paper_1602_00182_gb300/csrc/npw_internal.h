@@ -19,6 +19,47 @@ constexpr int NPW_FLUX_BURGERS_ = NPW_FLUX_BURGERS;
 constexpr int NPW_FLUX_EULER1D_ = NPW_FLUX_EULER1D;
 constexpr int NPW_FLUX_EULER2D_ = NPW_FLUX_EULER2D;
 
+// Flag byte of a face (npweno_reconstruct's flags output; the kernels count from it).
+constexpr uint32_t FL_SWITCH = 0x01u;       // monotone switch fired (k = 2: of the left cell)
+constexpr uint32_t FL_NEAR_TIE = 0x02u;     // a switch or ENO decision within the tie margin
+constexpr uint32_t FL_SWITCH_R_K2 = 0x08u;  // k = 2: switch of the right cell
+constexpr uint32_t FL_ZERO_GUARD = 0x40u;   // an evaluated eta set to 0 by the guard (k = 2: of v^-)
+constexpr uint32_t FL_ZERO_BOUND = 0x80u;   // an evaluated eta set to 0 by the bound (k = 2: of v^-)
+// k = 2, in the 32-bit flag word only: the same for the eta of v^+ (the byte of
+// npweno_reconstruct folds them into bits 6 and 7)
+constexpr uint32_t FL_ZERO_GUARD_R_K2 = 0x100u;
+constexpr uint32_t FL_ZERO_BOUND_R_K2 = 0x200u;
+__host__ __device__ __forceinline__ uint8_t flag_byte(uint32_t fl) {
+    return (uint8_t)((fl & 0xFFu) | ((fl >> 2) & 0xC0u));
+}
+
+// Per-thread counts of the shape-parameter decisions (per face for k = 3, per face value for
+// k = 2): the switch fired, eta evaluated, and of those zeroed by the guard / the bound.
+struct EtaCount {
+    uint32_t sw = 0, ev = 0, guard = 0, bound = 0;
+    // one face of k = 3 from its flag word
+    __device__ __forceinline__ void face_k3(uint32_t fl) {
+        sw += fl & FL_SWITCH;
+        ev += (fl & FL_SWITCH) ^ 1u;
+        guard += (fl >> 6) & 1u;
+        bound += (fl >> 7) & 1u;
+    }
+    // both face values (v^- of the left cell, v^+ of the right cell) of a k = 2 face
+    __device__ __forceinline__ void face_k2(uint32_t fl) {
+        const uint32_t s = (fl & FL_SWITCH) + ((fl >> 3) & 1u);
+        sw += s;
+        ev += 2u - s;
+        guard += ((fl >> 6) & 1u) + ((fl >> 8) & 1u);
+        bound += ((fl >> 7) & 1u) + ((fl >> 9) & 1u);
+    }
+    __device__ __forceinline__ void face(uint32_t fl, int k) {
+        if (k == 2)
+            face_k2(fl);
+        else
+            face_k3(fl);
+    }
+};
+
 // Method parameters as the kernels see them (by value in the launch arguments).
 struct MethodParams {
     int scheme;
@@ -37,6 +78,8 @@ struct MethodParams {
     double inflow[4];
     double eta_guard;  // resolved threshold (0 = off)
     double eta_max;    // resolved bound on |eta| (0 = off)
+    double tie_tol;    // relative margin of the near-tie bit of npweno_reconstruct
+    int64_t max_steps; // step limit of a solve (0 = automatic, see step_cap)
     // the same values rounded once to float on the host, for the float state (a conversion
     // in the kernels would take FP64-pipe slots)
     float eps_weno_f, eps_M_f, eps_M_lo_f, eta_guard_f, eta_max_f;  // eps_M ~ eps_M_f + eps_M_lo_f
@@ -79,7 +122,20 @@ struct Ctl {
     int32_t status;
     int32_t last;
     uint32_t tiles_done;
+    // shape-parameter decisions of the RBF schemes over the run (see EtaCount)
+    unsigned long long n_switch, n_eval, n_guard, n_bound;
+    int64_t step_cap;   // the run ends with NPW_ETIMEOUT after this many steps
 };
+
+// Step limit of a solve: the caller's max_steps, or 64 times the step count that the first
+// time step implies plus 1024, at most 2^24.  A run that reaches it, or whose time stops
+// advancing (t + dt == t), ends with NPW_ETIMEOUT instead of looping on the device.
+__host__ __device__ __forceinline__ int64_t step_cap(double t_rem, double dt, int64_t max_steps) {
+    if (max_steps > 0) return max_steps;
+    const double est = dt > 0.0 ? t_rem / dt : 1.0;
+    const double cap = 64.0 * (est < 1e12 ? est : 1e12) + 1024.0;
+    return cap < 16777216.0 ? (int64_t)cap : (int64_t)16777216;
+}
 
 // Work item: (instance, first cell of the tile).
 struct Tile {
@@ -145,7 +201,7 @@ struct Stage2DArgs {
 // ---- launchers (one definition per precision translation unit) ---------------------------
 template <typename R>
 cudaError_t launch_reconstruct(const R* u, int64_t n, int m, int bc, const MethodParams& mp, R* vm, R* vp,
-                               uint8_t* flags, cudaStream_t s);
+                               uint8_t* flags, R* eta, cudaStream_t s);
 template <typename R>
 cudaError_t launch_flux(const R* vm, const R* vp, int64_t nf, int m, int kind, double alpha,
                         const MethodParams& mp, R* h, cudaStream_t s);

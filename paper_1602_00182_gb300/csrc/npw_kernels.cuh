@@ -43,6 +43,28 @@ __device__ __forceinline__ bool finite_(R x) {
     return x - x == R(0.0);
 }
 
+// Adds this warp's decision counts to the instance's control word (one atomic per nonzero
+// counter and warp).  Every lane of the warp must call it; schemes without a shape parameter
+// add nothing.
+__device__ __forceinline__ void flush_counts(const EtaCount& c, Ctl* ctl, const MethodParams& mp) {
+    if (mp.scheme != NPW_RBF_ENO_ && mp.scheme != NPW_RBF_WENO_) return;
+    const unsigned sw = __reduce_add_sync(0xffffffffu, c.sw), ev = __reduce_add_sync(0xffffffffu, c.ev);
+    const unsigned gd = __reduce_add_sync(0xffffffffu, c.guard), bd = __reduce_add_sync(0xffffffffu, c.bound);
+    if ((threadIdx.x & 31) == 0) {
+        if (sw) atomicAdd(&ctl->n_switch, (unsigned long long)sw);
+        if (ev) atomicAdd(&ctl->n_eval, (unsigned long long)ev);
+        if (gd) atomicAdd(&ctl->n_guard, (unsigned long long)gd);
+        if (bd) atomicAdd(&ctl->n_bound, (unsigned long long)bd);
+    }
+}
+
+// A face is counted once per line: by the tile (or warp) whose cells start at it, and the last
+// face n by the tile that ends there.  q = local face index (face between local cells q-1 and
+// q), cnt = cells of the tile, last = the tile ends the line.
+__device__ __forceinline__ bool face_owned(int q, int cnt, bool last) {
+    return (q >= 0 && q < cnt) || (q == cnt && last);
+}
+
 // Weights of the last Shu-Osher stage, u^{n+1} = w1 u^n + w2 (u2 + dt L(u2)).  They must sum to
 // one exactly, or every step scales the conserved sum: in float, RN(1/3) + RN(2/3) = 1 + 3e-8,
 // so the float kernels take w2 = RN(2/3) and w1 = 1 - w2 (exact).  Double keeps 1/3 and 2/3
@@ -144,6 +166,14 @@ __device__ __forceinline__ bool take_alpha(Ctl* c, double* ax, double* ay, bool 
     return true;
 }
 
+// the step limit or a time that no longer advances ends the run (see step_cap)
+__device__ __forceinline__ void check_progress(Ctl* c) {
+    if (c->steps >= c->step_cap || !(c->t + c->dt > c->t)) {
+        c->status = NPW_ETIMEOUT;
+        c->done = 1;
+    }
+}
+
 __device__ __forceinline__ void finalize_1d(Ctl* c, const InstDev& in) {
     c->tiles_done = 0u;
     c->steps += 1;
@@ -155,6 +185,7 @@ __device__ __forceinline__ void finalize_1d(Ctl* c, const InstDev& in) {
         return;
     }
     next_dt(c, ax / in.dx, in.t_end, in.cfl);
+    check_progress(c);
 }
 
 __device__ __forceinline__ void finalize_2d(Ctl* c, const Inst2D& in) {
@@ -168,14 +199,17 @@ __device__ __forceinline__ void finalize_2d(Ctl* c, const Inst2D& in) {
         return;
     }
     next_dt(c, ax / in.dx + ay / in.dy, in.t_end, in.cfl);
+    check_progress(c);
 }
 
 // ---------------------------------------------------------------------------------------
-// npweno_reconstruct: one thread per face, all fields
+// npweno_reconstruct: one thread per face, all fields.  The flag byte also carries the
+// near-tie bit of every decision at the face (face_near_tie; characteristic: on the projected
+// fields), and eta (optional) the shape parameters as used.
 // ---------------------------------------------------------------------------------------
 template <typename R, typename D, int M, bool CHAR>
 __global__ void reconstruct_kernel(const R* __restrict__ u, int64_t n, int bc, MethodParams mp, R* __restrict__ vm,
-                                   R* __restrict__ vp, uint8_t* __restrict__ flags) {
+                                   R* __restrict__ vp, uint8_t* __restrict__ flags, R* __restrict__ eta) {
     int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f > n) return;
     R S[6 * M];
@@ -183,15 +217,40 @@ __global__ void reconstruct_kernel(const R* __restrict__ u, int64_t n, int bc, M
     for (int j = 0; j < 6; ++j)
 #pragma unroll
         for (int k = 0; k < M; ++k) S[j * M + k] = line_get<R>(u + k * n, n, 1, f - 3 + j, bc, mp.inflow[k]);
-    R a[M], b[M];
+    R a[M], b[M], e[M];
     uint32_t fl[M];
-    bool ok = face_all<R, D, NPW_FLUX_EULER1D_, M, CHAR>(S, mp, a, b, fl);
+    bool ok = face_all<R, D, NPW_FLUX_EULER1D_, M, CHAR>(S, mp, a, b, fl, (const D*)nullptr, e);
+    if (flags) {
+        R line[M][6];
+        if constexpr (CHAR) {
+            R Rm[3][3], Lm[3][3];
+            euler_eig<R>(S + 2 * M, S + 3 * M, mp_val<R>(mp.gamma, mp.gamma_f), Rm, Lm);
+#pragma unroll
+            for (int q = 0; q < M; ++q)
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    R s = R(0.0);
+#pragma unroll
+                    for (int k = 0; k < M; ++k) s += Lm[q][k] * S[j * M + k];
+                    line[q][j] = s;
+                }
+        } else {
+#pragma unroll
+            for (int k = 0; k < M; ++k)
+#pragma unroll
+                for (int j = 0; j < 6; ++j) line[k][j] = S[j * M + k];
+        }
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            if (face_near_tie<R>(line[k], mp, mp.tie_tol)) fl[k] |= FL_NEAR_TIE;
+    }
 #pragma unroll
     for (int k = 0; k < M; ++k) {
         R nan = R(__longlong_as_double(0x7ff8000000000000ll));
         vm[k * (n + 1) + f] = ok ? a[k] : nan;
         vp[k * (n + 1) + f] = ok ? b[k] : nan;
-        if (flags) flags[k * (n + 1) + f] = (uint8_t)fl[k];
+        if (flags) flags[k * (n + 1) + f] = flag_byte(fl[k]);
+        if (eta) eta[k * (n + 1) + f] = ok ? e[k] : nan;
     }
 }
 
@@ -279,6 +338,8 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_kernel(Stage1DArgs a) {
     __syncthreads();
 
     // faces c0 - 1/2 .. c0 + cnt - 1/2 (local q = 0..cnt): stencil su[q .. q+5]
+    EtaCount ec;
+    const bool last_tile = c0 + cnt == n;
     for (int q = threadIdx.x; q <= cnt; q += blockDim.x) {
         R vm[M], vp[M], h[M];
         uint32_t fl[M];
@@ -286,7 +347,11 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_kernel(Stage1DArgs a) {
         lf_flux<R, KIND, M>(vm, vp, alpha, a.mp, 0, h);
 #pragma unroll
         for (int k = 0; k < M; ++k) sh[q * M + k] = ok ? h[k] : R(__longlong_as_double(0x7ff8000000000000ll));
+        if (face_owned(q, cnt, last_tile))
+#pragma unroll
+            for (int k = 0; k < M; ++k) ec.face(fl[k], a.mp.k);
     }
+    flush_counts(ec, ctl, a.mp);
     __syncthreads();
 
     // cells: eq. PDE1 and the Shu-Osher combination
@@ -349,8 +414,8 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_kernel(Stage1DArgs a) {
 // bit.  X(k, i) is the stage input of field k at cell i, for i in lo-3..hi+2.
 // ---------------------------------------------------------------------------------------
 template <int KIND, int K, int M, typename LoadX, typename Upd>
-__device__ __forceinline__ void warp_line_pass(int lo, int hi, int lane, const fast::FParams& fp,
-                                               const MethodParams& mp, float alpha, LoadX X, Upd upd) {
+__device__ __forceinline__ void warp_line_pass(int lo, int hi, int n, int lane, const fast::FParams& fp,
+                                               const MethodParams& mp, float alpha, LoadX X, Upd upd, EtaCount& ec) {
     float c_eta[M], c_vm[M], c_h[M];
 #pragma unroll
     for (int k = 0; k < M; ++k) c_eta[k] = c_vm[k] = c_h[k] = 0.0f;
@@ -368,6 +433,7 @@ __device__ __forceinline__ void warp_line_pass(int lo, int hi, int lane, const f
                 if (K == 3 && face_ok) {
                     uint32_t fl = 0;
                     eta = fast::face_eta(c[1], c[2], c[3], c[4], fp, &fl);
+                    if (f < hi || f == n) ec.face_k3(fl);
                 }
             }
             if constexpr (K == 3) {
@@ -376,7 +442,12 @@ __device__ __forceinline__ void warp_line_pass(int lo, int hi, int lane, const f
                 c_eta[k] = __shfl_sync(0xffffffffu, eta, 31);
                 if (cell_ok) fast::cell_recon(c, eta, i >= lo ? eprev : 0.0f, fp, &vm[k], &vp[k]);
             } else {
-                if (cell_ok) fast::cell_recon_k2(c + 1, 0.0, mp, fp, &vm[k], &vp[k]);
+                if (cell_ok) {
+                    // v^- of cell i at face f, v^+ at face f - 1
+                    const uint32_t d = fast::cell_recon_k2(c + 1, 0.0, mp, fp, &vm[k], &vp[k]);
+                    if (f < hi || f == n) fast::count_k2(ec, d, 0);
+                    if (f - 1 >= lo && (f - 1 < hi || f - 1 == n)) fast::count_k2(ec, d, 1);
+                }
             }
         }
         // flux of face f - 1
@@ -465,13 +536,16 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
     const fast::FParams fp = fast::fparams(a.mp);
     __syncthreads();
 
-    // F: faces between extended cells e-1 and e
+    // F: faces between extended cells e-1 and e (local face q = e - 3)
+    EtaCount ec;
+    const bool last_tile = c0 + cnt == n;
     if constexpr (K == 3) {
         for (int idx = threadIdx.x; idx < (cnt + 3) * M; idx += blockDim.x) {
             const int e = 2 + idx / M, k = idx - (e - 2) * M;
             uint32_t fl = 0;
             se[e * M + k] = fast::face_eta(su[(e - 2) * M + k], su[(e - 1) * M + k], su[e * M + k],
                                            su[(e + 1) * M + k], fp, &fl);
+            if (face_owned(e - 3, cnt, last_tile)) ec.face_k3(fl);
         }
         __syncthreads();
     }
@@ -482,13 +556,18 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
 #pragma unroll
         for (int j = 0; j < 5; ++j) c[j] = su[(e - 2 + j) * M + k];
         float vm, vp;
-        if constexpr (K == 3)
+        if constexpr (K == 3) {
             fast::cell_recon(c, se[(e + 1) * M + k], se[e * M + k], fp, &vm, &vp);
-        else
-            fast::cell_recon_k2(c + 1, 0.0, a.mp, fp, &vm, &vp);
+        } else {
+            // v^- at the cell's right face (local face e - 2), v^+ at its left face (e - 3)
+            const uint32_t d = fast::cell_recon_k2(c + 1, 0.0, a.mp, fp, &vm, &vp);
+            if (face_owned(e - 2, cnt, last_tile)) fast::count_k2(ec, d, 0);
+            if (face_owned(e - 3, cnt, last_tile)) fast::count_k2(ec, d, 1);
+        }
         svm[e * M + k] = vm;
         svp[e * M + k] = vp;
     }
+    flush_counts(ec, ctl, a.mp);
     __syncthreads();
     // U: cells
     const float lam = s_lam;
@@ -629,6 +708,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
     float inflow[M];
 #pragma unroll
     for (int k = 0; k < M; ++k) inflow[k] = a.mp.inflow_f[k];
+    EtaCount ec;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int per = (n + nwarps - 1) / nwarps;
     const int lo = min(n, warp * per), hi = min(n, lo + per);
@@ -658,7 +738,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
         vmaxf = sp > vmaxf ? sp : vmaxf;
     }
     double t = 0.0, dt = 0.0, alpha = 0.0, alpha_max = 0.0;  // thread 0's copies
-    int64_t steps = 0;
+    int64_t steps = 0, cap = 0;
     int last = 0, status = 0;
     {
         const double b = block_max_nan_f(vmaxf, bad, red, redbad);
@@ -675,6 +755,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
                     dt = in.t_end - t;
                     last = 1;
                 }
+                cap = step_cap(in.t_end - t, dt, a.mp.max_steps);
             }
             s_lam = (float)(dt / in.dx);
             s_alpha = (float)alpha;
@@ -725,7 +806,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
                         vmaxf = sp > vmaxf ? sp : vmaxf;
                     }
                 };
-                warp_line_pass<KIND, K, M>(lo, hi, lane, fp, a.mp, alphaf, X, upd);
+                warp_line_pass<KIND, K, M>(lo, hi, n, lane, fp, a.mp, alphaf, X, upd, ec);
             }
             __syncthreads();
 #undef NPW_X
@@ -754,6 +835,10 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
                         dt = in.t_end - t;
                         last = 1;
                     }
+                    if (steps >= cap || !(t + dt > t)) {  // step limit, or time stopped advancing
+                        status = NPW_ETIMEOUT;
+                        s_done = 1;
+                    }
                     s_lam = (float)(dt / in.dx);
                     s_alpha = (float)alpha;
                 }
@@ -762,6 +847,7 @@ __global__ void __launch_bounds__(1024) solve1d_resident_kernel(ResidentArgs a) 
         __syncthreads();
     }
     for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) g[idx] = un[idx + (idx / n) * 2 * RES_GHOST + RES_GHOST];
+    flush_counts(ec, ctl, a.mp);
     if (threadIdx.x == 0) {
         ctl->t = t;
         ctl->dt = dt;
@@ -873,6 +959,14 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
     }
     __syncthreads();
     const float ax = s_par[0], ay = s_par[1];
+    // counted faces: x face (qx, qy) of grid row ty0 + qy, y face of grid column tx0 + qx
+    EtaCount ec;
+    auto own_x = [&](int qx, int qy) {
+        return ty0 + qy < ny && face_owned(qx, (int)min((int64_t)TX_2D, nx - tx0), tx0 + TX_2D >= nx);
+    };
+    auto own_y = [&](int qx, int qy) {
+        return tx0 + qx < nx && face_owned(qy, (int)min((int64_t)TY_2D, ny - ty0), ty0 + TY_2D >= ny);
+    };
 #define NPW_SU(bx, by, k) su[((by) * BX + (bx)) * M + (k)]
     // E: item = (face, field); x face (qx, qy) has the eta stencil su[qy+3][qx+1 .. qx+4],
     // y face (qx, qy) su[qy+1 .. qy+4][qx+3]
@@ -895,6 +989,8 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
         }
         uint32_t fl = 0;
         ef[it] = fast::face_eta(w0, w1, w2, w3, fp, &fl);
+        const bool own = f < NFX ? own_x(f % (TX_2D + 1), f / (TX_2D + 1)) : own_y((f - NFX) % TX_2D, (f - NFX) / TX_2D);
+        if (own) ec.face_k3(fl);
     }
     __syncthreads();
     // C: item = (cell, field); x: cells cx = -1..TX of each row (TX + 2 per row), y: cells
@@ -906,12 +1002,15 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
         float cc[5];
         double trans = 0.0;  // k = 2 cross: transverse second difference of the cell
         int fl_idx, fr_idx;  // faces left / right of the cell (-1 when outside the tile)
+        bool own_l, own_r;   // those faces are counted by this tile
         if (c < NCX) {
             const int qy = c / (TX_2D + 2), cx = c - qy * (TX_2D + 2) - 1;
 #pragma unroll
             for (int j = 0; j < 5; ++j) cc[j] = NPW_SU(cx + 1 + j, qy + 3, k);
             fl_idx = cx >= 0 ? qy * (TX_2D + 1) + cx : -1;
             fr_idx = cx < TX_2D ? qy * (TX_2D + 1) + cx + 1 : -1;
+            own_l = cx >= 0 && own_x(cx, qy);
+            own_r = cx < TX_2D && own_x(cx + 1, qy);
             if (cross)
                 trans = (fast::widen(NPW_SU(cx + 3, qy + 2, k)) - 2.0 * fast::widen(NPW_SU(cx + 3, qy + 3, k))) +
                         fast::widen(NPW_SU(cx + 3, qy + 4, k));
@@ -922,6 +1021,8 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
             for (int j = 0; j < 5; ++j) cc[j] = NPW_SU(qx + 3, cy + 1 + j, k);
             fl_idx = cy >= 0 ? NFX + cy * TX_2D + qx : -1;
             fr_idx = cy < TY_2D ? NFX + (cy + 1) * TX_2D + qx : -1;
+            own_l = cy >= 0 && own_y(qx, cy);
+            own_r = cy < TY_2D && own_y(qx, cy + 1);
             if (cross)
                 trans = (fast::widen(NPW_SU(qx + 2, cy + 3, k)) - 2.0 * fast::widen(NPW_SU(qx + 3, cy + 3, k))) +
                         fast::widen(NPW_SU(qx + 4, cy + 3, k));
@@ -932,11 +1033,14 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
             const float el = fl_idx >= 0 ? ef[fl_idx * M + k] : 0.0f;
             fast::cell_recon(cc, er, el, fp, &vm, &vp);
         } else {
-            fast::cell_recon_k2(cc + 1, trans, a.mp, fp, &vm, &vp);
+            const uint32_t d = fast::cell_recon_k2(cc + 1, trans, a.mp, fp, &vm, &vp);
+            if (own_r) fast::count_k2(ec, d, 0);
+            if (own_l) fast::count_k2(ec, d, 1);
         }
         if (fr_idx >= 0) vmf[fr_idx * M + k] = vm;
         if (fl_idx >= 0) vpf[fl_idx * M + k] = vp;
     }
+    flush_counts(ec, ctl, a.mp);
     __syncthreads();
     // F: item = face (all fields); the fluxes overwrite the eta array
     for (int f = tid; f < NFX + NFY; f += nthr) {
@@ -1046,6 +1150,9 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
     const double dt = *(volatile double*)&ctl->dt;
     const R ax = R(*(volatile double*)&ctl->alpha);
     const R ay = R(*(volatile double*)&ctl->alpha_y);
+    EtaCount ec;
+    const int cnt_x = (int)min((int64_t)TX_2D, nx - tx0), cnt_y = (int)min((int64_t)TY_2D, ny - ty0);
+    const bool last_x = tx0 + TX_2D >= nx, last_y = ty0 + TY_2D >= ny;
     __syncthreads();
     // x faces: (qx, qy), qx = 0..TX, qy = 0..TY-1, stencil su[qy+3][qx .. qx+5]
     for (int f = tid; f < (TX_2D + 1) * TY_2D; f += blockDim.x) {
@@ -1074,6 +1181,9 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
         lf_flux<R, KIND, M>(vm, vp, ax, a.mp, 0, h);
 #pragma unroll
         for (int k = 0; k < M; ++k) hx[(qy * (TX_2D + 1) + qx) * M + k] = h[k];
+        if (qy < cnt_y && face_owned(qx, cnt_x, last_x))
+#pragma unroll
+            for (int k = 0; k < M; ++k) ec.face(fl[k], a.mp.k);
     }
     // y faces: (qx, qy), qx = 0..TX-1, qy = 0..TY, stencil su[qy .. qy+5][qx+3]
     for (int f = tid; f < TX_2D * (TY_2D + 1); f += blockDim.x) {
@@ -1102,7 +1212,11 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
         lf_flux<R, KIND, M>(vm, vp, ay, a.mp, 1, h);
 #pragma unroll
         for (int k = 0; k < M; ++k) hy[(qy * TX_2D + qx) * M + k] = h[k];
+        if (qx < cnt_x && face_owned(qy, cnt_y, last_y))
+#pragma unroll
+            for (int k = 0; k < M; ++k) ec.face(fl[k], a.mp.k);
     }
+    flush_counts(ec, ctl, a.mp);
     __syncthreads();
     R* uout = reinterpret_cast<R*>(a.uout) + in.off;
     const R* un = reinterpret_cast<const R*>(a.un) + in.off;
@@ -1214,17 +1328,17 @@ __global__ void tune_init_kernel(R* u, int64_t n, int m) {
 template <typename R, typename D>
 struct Launchers {
     static cudaError_t reconstruct(const R* u, int64_t n, int m, int bc, const MethodParams& mp, R* vm, R* vp,
-                                   uint8_t* flags, cudaStream_t s) {
+                                   uint8_t* flags, R* eta, cudaStream_t s) {
         const int threads = 128;
         const unsigned blocks = (unsigned)((n + 1 + threads - 1) / threads);
         if (m == 1)
-            reconstruct_kernel<R, D, 1, false><<<blocks, threads, 0, s>>>(u, n, bc, mp, vm, vp, flags);
+            reconstruct_kernel<R, D, 1, false><<<blocks, threads, 0, s>>>(u, n, bc, mp, vm, vp, flags, eta);
         else if (m == 3 && mp.characteristic)
-            reconstruct_kernel<R, D, 3, true><<<blocks, threads, 0, s>>>(u, n, bc, mp, vm, vp, flags);
+            reconstruct_kernel<R, D, 3, true><<<blocks, threads, 0, s>>>(u, n, bc, mp, vm, vp, flags, eta);
         else if (m == 3)
-            reconstruct_kernel<R, D, 3, false><<<blocks, threads, 0, s>>>(u, n, bc, mp, vm, vp, flags);
+            reconstruct_kernel<R, D, 3, false><<<blocks, threads, 0, s>>>(u, n, bc, mp, vm, vp, flags, eta);
         else if (m == 4)
-            reconstruct_kernel<R, D, 4, false><<<blocks, threads, 0, s>>>(u, n, bc, mp, vm, vp, flags);
+            reconstruct_kernel<R, D, 4, false><<<blocks, threads, 0, s>>>(u, n, bc, mp, vm, vp, flags, eta);
         else
             return cudaErrorInvalidValue;
         return cudaGetLastError();

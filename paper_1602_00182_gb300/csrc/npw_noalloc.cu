@@ -28,7 +28,8 @@ void* g_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device.  The first call on a device
 // looks it up with cudaGetSymbolAddress (the array's name in host code is only a host-side
-// stand-in, never a device address) and caches it.
+// stand-in, never a device address) and caches it.  The cache is not invalidated by
+// cudaDeviceReset (which reloads the module): calls after a reset are not supported.
 cudaError_t scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

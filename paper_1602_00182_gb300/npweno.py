@@ -29,12 +29,14 @@ class npw_params(C.Structure):
                 ("eta_eval", C.c_int32), ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
                 ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4),
                 ("eta_guard", C.c_double), ("batch_mode", C.c_int32), ("tile_1d", C.c_int32),
-                ("eta_max", C.c_double), ("cross_2d", C.c_int32), ("bc_y", C.c_int32)]
+                ("eta_max", C.c_double), ("cross_2d", C.c_int32), ("bc_y", C.c_int32), ("tie_tol", C.c_double),
+                ("max_steps", C.c_int64)]
 
 
 class npw_solve_stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("t", C.c_double), ("alpha_max", C.c_double), ("status", C.c_int32),
-                ("pad_", C.c_int32)]
+                ("pad_", C.c_int32), ("eta_switch", C.c_int64), ("eta_eval", C.c_int64), ("eta_guard", C.c_int64),
+                ("eta_bound", C.c_int64)]
 
 
 class npw_instance(C.Structure):
@@ -71,13 +73,15 @@ class Params:
     tile_1d: int = 0
     cross_2d: int = 0
     bc_y: int = -1  # 2D: boundary of the y direction (-1: the bc argument)
+    tie_tol: float = 0.0  # near-tie margin of npweno_reconstruct's flags (0: 1e-10)
+    max_steps: int = 0  # step limit of a solve (0: automatic); NPW_ETIMEOUT when reached
 
     def c(self) -> npw_params:
         p = npw_params()
         for f in ("k", "scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "precision",
-                  "eta_eval", "batch_mode", "tile_1d", "cross_2d", "bc_y"):
+                  "eta_eval", "batch_mode", "tile_1d", "cross_2d", "bc_y", "max_steps"):
             setattr(p, f, int(getattr(self, f)))
-        for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "eta_guard", "eta_max"):
+        for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "eta_guard", "eta_max", "tie_tol"):
             setattr(p, f, float(getattr(self, f)))
         for i in range(4):
             p.inflow[i] = float(self.inflow[i]) if i < len(self.inflow) else 0.0
@@ -102,7 +106,7 @@ def load():
     lib.npw_default_params.restype = None
     lib.npw_last_error.restype = C.c_char_p
     lib.npw_version.restype = i32
-    lib.npweno_reconstruct.argtypes = [vp, i64, i32, i32, P(npw_params), vp, vp, vp, vp]
+    lib.npweno_reconstruct.argtypes = [vp, i64, i32, i32, P(npw_params), vp, vp, vp, vp, vp]
     lib.npweno_flux.argtypes = [vp, vp, i64, i32, i32, d, P(npw_params), vp, vp]
     lib.npw_workspace_size.argtypes = [i64, i32, P(npw_params)]
     lib.npw_workspace_size.restype = sz
@@ -168,8 +172,8 @@ def npw_version() -> int:
     return load().npw_version()
 
 
-def npweno_reconstruct(vbar, bc: int, params: Params, with_flags: bool = True):
-    """Face values of vbar [m][n] (or [n]) -> (v_minus, v_plus, flags), each [m][n+1]."""
+def npweno_reconstruct(vbar, bc: int, params: Params, with_flags: bool = True, with_eta: bool = False):
+    """Face values of vbar [m][n] (or [n]) -> (v_minus, v_plus, flags[, eta]), each [m][n+1]."""
     torch = _torch()
     squeeze = vbar.dim() == 1
     v = vbar[None] if squeeze else vbar
@@ -177,13 +181,15 @@ def npweno_reconstruct(vbar, bc: int, params: Params, with_flags: bool = True):
     vm = torch.empty((m, n + 1), dtype=v.dtype, device=v.device)
     vp = torch.empty_like(vm)
     fl = torch.empty((m, n + 1), dtype=torch.uint8, device=v.device) if with_flags else None
+    eta = torch.empty_like(vm) if with_eta else None
     p = params.c()
-    _check(load().npweno_reconstruct(_dev(v, params, "vbar"), n, m, bc, C.byref(p), C.c_void_p(vm.data_ptr()),
-                                     C.c_void_p(vp.data_ptr()), C.c_void_p(fl.data_ptr()) if fl is not None else None,
-                                     _stream()))
+    ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    _check(load().npweno_reconstruct(_dev(v, params, "vbar"), n, m, bc, C.byref(p), ptr(vm), ptr(vp), ptr(fl),
+                                     ptr(eta), _stream()))
+    out = (vm, vp, fl) + ((eta,) if with_eta else ())
     if squeeze:
-        return vm[0], vp[0], (fl[0] if fl is not None else None)
-    return vm, vp, fl
+        return tuple(x[0] if x is not None else None for x in out)
+    return out
 
 
 def npweno_flux(v_minus, v_plus, flux_kind: int, alpha: float, params: Params):
@@ -264,7 +270,9 @@ def npw_format_check(f_in, d_in):
 
 
 def _stats(s: npw_solve_stats) -> dict:
-    return dict(steps=int(s.steps), t=float(s.t), alpha_max=float(s.alpha_max), status=int(s.status))
+    return dict(steps=int(s.steps), t=float(s.t), alpha_max=float(s.alpha_max), status=int(s.status),
+                eta=dict(switch=int(s.eta_switch), eval=int(s.eta_eval), guard=int(s.eta_guard),
+                         bound=int(s.eta_bound)))
 
 
 def npweno_solve(u, dx: float, t_end: float, cfl: float, flux_kind: int, bc: int, params: Params, workspace=None):

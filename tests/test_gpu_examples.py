@@ -5,7 +5,10 @@ Example 2 (a jump across y = 0.5 on [0, 1]^2, inflow value 1 at y = 0, periodic 
   * NPW_FP64 against the oracle: relative L_inf <= 1e-12.
   * NPW_FP32_MIXED: near the oracle (mean difference per cell <= 1e-4, largest <= 5e-3: decisions
     at the jump are near ties, see MIXED_MEAN), and ENO / RBF-ENO stay non-oscillatory (within
-    [-1, 1] up to float rounding, no new variation), as the paper states.
+    [-1, 1] up to float rounding, no new variation), as the paper states.  These runs drop the
+    few face values where the printed k = 2 eta is singular (its denominator crosses zero inside
+    the jump from 1 to -1) with the optional bound |eta| <= 100 on both sides, the setting under
+    which the oracle reproduces the paper's statements about this example.
 """
 import numpy as np
 import pytest
@@ -34,10 +37,10 @@ def _example2(n=200):
     return np.where(edges[1:] <= 0, 1.0, -1.0), 2.0 / n
 
 
-def _gpu_solve(npw, u0, dx, k, scheme, precision):
+def _gpu_solve(npw, u0, dx, k, scheme, precision, eta_max=0.0):
     dtype = torch.float64 if precision == 0 else torch.float32
     u = torch.tensor(u0, dtype=dtype, device="cuda")
-    p = npw.Params(k=k, scheme=scheme, precision=precision, inflow=(1.0, 0, 0, 0))
+    p = npw.Params(k=k, scheme=scheme, precision=precision, inflow=(1.0, 0, 0, 0), eta_max=eta_max)
     st = npw.npweno_solve(u, dx, 0.5, 0.1, npw.NPW_FLUX_ADVECTION, npw.NPW_BC_INFLOW, p)
     assert st["status"] == 0
     torch.cuda.synchronize()
@@ -72,9 +75,9 @@ def _close(got, ref):
 @pytest.mark.parametrize("scheme", SCHEMES)
 def test_example2_mixed_matches_oracle_and_eno_stays_monotone(npw, k, scheme):
     u0, dx = _example2()
-    p = O.Params(k=k, scheme=scheme, inflow=(1.0, 0, 0, 0), eta_guard=8.0 * 2.0 ** -24)
+    p = O.Params(k=k, scheme=scheme, inflow=(1.0, 0, 0, 0), eta_guard=8.0 * 2.0 ** -24, eta_max=100.0)
     ref, _ = O.solve(u0, dx, 0.5, 0.1, O.ADVECTION, O.INFLOW, p)
-    got, _ = _gpu_solve(npw, u0, dx, k, scheme, 1)
+    got, _ = _gpu_solve(npw, u0, dx, k, scheme, 1, eta_max=100.0)
     assert _close(got, ref)
     if scheme in (O.ENO, O.RBF_ENO):
         tol = 4 * 2.0 ** -24
@@ -110,10 +113,12 @@ def test_example2_2d_mixed_stays_monotone(npw, scheme, cross):
     """k = 2 as in the paper's figure: the float path stays within [-1, 1] (up to float rounding)
     with no new variation along y, and near the oracle (the bar of the 1D test)."""
     u0, d = _example2_2d(100)
-    op = O.Params(k=2, scheme=scheme, cross_2d=cross, inflow=(1.0, 0, 0, 0), bc_y=O.INFLOW, eta_guard=8.0 * 2.0 ** -24)
+    op = O.Params(k=2, scheme=scheme, cross_2d=cross, inflow=(1.0, 0, 0, 0), bc_y=O.INFLOW, eta_guard=8.0 * 2.0 ** -24,
+                  eta_max=100.0)
     ref, _ = O.solve_2d(u0, d, d, 0.25, 0.1, O.ADVECTION, O.PERIODIC, op)
     u = torch.tensor(u0, dtype=torch.float32, device="cuda")
-    p = npw.Params(k=2, scheme=scheme, cross_2d=cross, precision=1, inflow=(1.0, 0, 0, 0), bc_y=npw.NPW_BC_INFLOW)
+    p = npw.Params(k=2, scheme=scheme, cross_2d=cross, precision=1, inflow=(1.0, 0, 0, 0), bc_y=npw.NPW_BC_INFLOW,
+                   eta_max=100.0)
     st = npw.npweno_solve_2d(u, d, d, 0.25, 0.1, npw.NPW_FLUX_ADVECTION, npw.NPW_BC_PERIODIC, p)
     torch.cuda.synchronize()
     assert st["status"] == 0

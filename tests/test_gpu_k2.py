@@ -12,14 +12,13 @@ import pytest
 
 import oracle as O
 from paper_1602_00182_gb300 import inputs as I
+from tests.parity_util import compare_faces
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 MIXED_GUARD = 8.0 * 2.0 ** -24
-TIES = O.FLAG_SWITCH_TIE | O.FLAG_ENO_TIE_L | O.FLAG_ENO_TIE_R
-DECISIONS = 0x01 | 0x04 | 0x08 | 0x10
 
 
 @pytest.fixture(scope="module")
@@ -66,26 +65,33 @@ def test_k2_reconstruct_fp64(npw, scheme, rbf, switch, bc):
     op = O.Params(k=2, scheme=scheme, rbf=rbf, monotone_switch=switch, inflow=(0.7, 0, 0, 0))
     for n in (6, 37, 1025, 3001):
         u = _data(n, n)
-        vm, vp, fl, _ = O.reconstruct(u, bc, op)
-        gvm, gvp, gfl = npw.npweno_reconstruct(_dev(u), bc, _gp(npw, op))
-        gvm, gvp, gfl = gvm.cpu().numpy(), gvp.cpu().numpy(), gfl.cpu().numpy()
-        ok = (fl & TIES) == 0
-        assert np.array_equal(gfl[ok] & DECISIONS, fl[ok] & DECISIONS), n
-        scale = np.abs(u).max()
-        assert np.abs(gvm[ok] - vm[ok]).max() <= FP64_TOL * scale, n
-        assert np.abs(gvp[ok] - vp[ok]).max() <= FP64_TOL * scale, n
+        gvm, gvp, gfl, geta = npw.npweno_reconstruct(_dev(u), bc, _gp(npw, op), with_eta=True)
+        # the linear ramp of _data (5% of the cells) makes the ratio test's denominator rounding
+        # noise: those faces are switch near ties
+        compare_faces(u, bc, op, gvm.cpu().numpy(), gvp.cpu().numpy(), gfl.cpu().numpy(), FP64_TOL,
+                      1.0 if n < 64 else 0.06, geta=geta.cpu().numpy(), eta_exact=True, label=f"k2 n={n}")
+
+
+@pytest.mark.parametrize("eta_max,eta_guard", [(0.05, 0.0), (0.0, 1e-3)])
+def test_k2_reconstruct_guard_and_bound(npw, eta_max, eta_guard):
+    op = O.Params(k=2, eta_max=eta_max, eta_guard=eta_guard)
+    g = np.random.default_rng(3)
+    x = (np.arange(2000) + 0.5) / 2000
+    u = 1.0 + 0.4 * np.sin(2 * np.pi * 3 * x + g.uniform(0, 6)) + 0.5 * (x > 1 / np.sqrt(3))
+    gvm, gvp, gfl, geta = npw.npweno_reconstruct(_dev(u), O.PERIODIC, _gp(npw, op), with_eta=True)
+    gfl = gfl.cpu().numpy()
+    assert ((gfl & 0xC0) != 0).any()
+    compare_faces(u, O.PERIODIC, op, gvm.cpu().numpy(), gvp.cpu().numpy(), gfl, FP64_TOL, 0.005,
+                  geta=geta.cpu().numpy(), eta_exact=True, label="k2 guard/bound")
 
 
 @pytest.mark.parametrize("char", [0, 1])
 def test_k2_reconstruct_euler_fp64(npw, char):
     for inst in I.euler_batch(count=4, nmin=64, nmax=2500):
         op = O.Params(k=2, characteristic=char)
-        vm, vp, fl, _ = O.reconstruct(inst.u0, O.TRANSMISSIVE, op)
-        gvm, gvp, gfl = npw.npweno_reconstruct(_dev(inst.u0), O.TRANSMISSIVE, _gp(npw, op))
-        ok = (fl & TIES) == 0
-        for a, b in ((gvm.cpu().numpy(), vm), (gvp.cpu().numpy(), vp)):
-            for k in range(3):
-                assert np.abs(a[k][ok[k]] - b[k][ok[k]]).max() <= FP64_TOL * np.abs(b[k]).max()
+        gvm, gvp, gfl, geta = npw.npweno_reconstruct(_dev(inst.u0), O.TRANSMISSIVE, _gp(npw, op), with_eta=True)
+        compare_faces(inst.u0, O.TRANSMISSIVE, op, gvm.cpu().numpy(), gvp.cpu().numpy(), gfl.cpu().numpy(),
+                      FP64_TOL, 0.02, geta=geta.cpu().numpy(), eta_exact=not char, label=f"k2 euler {inst.kind}")
 
 
 @pytest.mark.parametrize("scheme", [O.ENO, O.WENO_JS, O.RBF_ENO, O.RBF_WENO])
@@ -131,16 +137,10 @@ def test_k2_mixed_decisions_match_fp64(npw, scheme):
         u = _data(n, n).astype(np.float32).astype(np.float64)
         u[n // 2: n // 2 + 40] = np.round(u[n // 2: n // 2 + 40] * 64) / 64  # plateaus and exact steps
         op = O.Params(k=2, scheme=scheme, eta_guard=MIXED_GUARD)
-        vm, vp, fl, _ = O.reconstruct(u, O.PERIODIC, op)
-        gvm, gvp, gfl = npw.npweno_reconstruct(_dev(u, torch.float32), O.PERIODIC, _gp(npw, op, precision=1))
-        gvm = gvm.cpu().numpy().astype(np.float64)
-        gvp = gvp.cpu().numpy().astype(np.float64)
-        gfl = gfl.cpu().numpy()
-        ok = (fl & TIES) == 0
-        assert np.array_equal(gfl[ok] & DECISIONS, fl[ok] & DECISIONS), n
-        scale = np.abs(u).max()
-        assert np.abs(gvm[ok] - vm[ok]).max() <= 2e-6 * scale, n
-        assert np.abs(gvp[ok] - vp[ok]).max() <= 2e-6 * scale, n
+        gvm, gvp, gfl, geta = npw.npweno_reconstruct(_dev(u, torch.float32), O.PERIODIC, _gp(npw, op, precision=1),
+                                                     with_eta=True)
+        compare_faces(u, O.PERIODIC, op, gvm.cpu().numpy(), gvp.cpu().numpy(), gfl.cpu().numpy(), 2e-6,
+                      1.0 if n < 100 else 0.06, geta=geta.cpu().numpy(), label=f"k2 mixed n={n}")
 
 
 def test_k2_mixed_burgers_batch(npw):

@@ -1,9 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
 Bars (written here, derived in the design doc):
-  * NPW_FP64 vs oracle: relative L_inf <= 1e-12; ENO stencil choices and switch flags
-    identical except at faces the oracle marks as near ties (only the switch, evaluated in
-    closed form on the GPU and by a 4x4 solve in the oracle, can differ there).
+  * NPW_FP64 vs oracle: relative L_inf <= 1e-12 on every face; ENO stencil choices identical on
+    every face, switch flags identical except at faces either side marks as switch near ties
+    (closed form on the GPU, a 4x4 elimination in the oracle), whose share is bounded per data
+    set; at those faces the oracle replays the GPU's decisions (tests/parity_util.py).
   * NPW_FP32_MIXED vs oracle: the per-config L1 / L_inf bounds stated in each test.
 Sizes span several 1024-cell tiles and a ragged last tile; edge cases: the minimum n = 6,
 tile boundaries, invalid arguments and non-finite states.
@@ -13,6 +14,7 @@ import pytest
 
 import oracle as O
 from paper_1602_00182_gb300 import inputs as I
+from tests.parity_util import compare_faces
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -55,11 +57,28 @@ def _mixed_data(n, seed):
     return u
 
 
+def _generic_data(n, seed):
+    """Smooth waves and two jumps at irrational positions, no plateaus: decisions near their
+    thresholds only by chance."""
+    g = np.random.default_rng(seed)
+    x = (np.arange(n) + 0.5) / n
+    u = 1.0 + 0.4 * np.sin(2 * np.pi * 2 * x + g.uniform(0, 6)) + 0.15 * np.cos(2 * np.pi * 9 * x + g.uniform(0, 6))
+    u += 0.6 * (x > 1 / np.sqrt(5)) - 0.3 * (x > 1 / np.sqrt(2))
+    return u
+
+
 def _rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-TIES = O.FLAG_SWITCH_TIE | O.FLAG_ENO_TIE_L | O.FLAG_ENO_TIE_R
+# shares of faces where a switch decision may be a near tie: the generic data have none by
+# construction; _mixed_data has a linear ramp over 5% of its cells, where the ratio test of
+# switch variant 1 divides rounding noise by rounding noise
+TIE_FRAC_GENERIC = 0.005
+TIE_FRAC_MIXED = 0.06
+TIE_FRAC_NEAR = 0.05
+
+
 
 
 # ------------------------------------------------------------------------------ reconstruct
@@ -69,30 +88,38 @@ TIES = O.FLAG_SWITCH_TIE | O.FLAG_ENO_TIE_L | O.FLAG_ENO_TIE_R
 @pytest.mark.parametrize("bc", [O.PERIODIC, O.TRANSMISSIVE, O.INFLOW])
 def test_reconstruct_fp64(npw, scheme, rbf, switch, variant, bc):
     op = O.Params(scheme=scheme, rbf=rbf, monotone_switch=switch, switch_variant=variant, inflow=(0.7, 0, 0, 0))
-    for n in (6, 37, 1025, 3001):
-        u = _mixed_data(n, n)
-        vm, vp, fl, _ = O.reconstruct(u, bc, op)
-        gvm, gvp, gfl = npw.npweno_reconstruct(_dev(u), bc, _gparams(npw, op))
-        gvm, gvp, gfl = gvm.cpu().numpy(), gvp.cpu().numpy(), gfl.cpu().numpy()
-        tie = (fl & TIES) != 0
-        ok = ~tie
-        assert np.array_equal(gfl[ok] & 0x3D, fl[ok] & 0x3D), n
-        scale = np.abs(u).max()
-        assert np.abs(gvm[ok] - vm[ok]).max() <= FP64_TOL * scale, n
-        assert np.abs(gvp[ok] - vp[ok]).max() <= FP64_TOL * scale, n
+    for data, frac in ((_mixed_data, TIE_FRAC_MIXED), (_generic_data, TIE_FRAC_GENERIC)):
+        for n in (6, 37, 1025, 3001):
+            u = data(n, n)
+            gvm, gvp, gfl, geta = npw.npweno_reconstruct(_dev(u), bc, _gparams(npw, op), with_eta=True)
+            compare_faces(u, bc, op, gvm.cpu().numpy(), gvp.cpu().numpy(), gfl.cpu().numpy(), FP64_TOL,
+                          1.0 if n < 64 else frac, geta=geta.cpu().numpy(), eta_exact=True,
+                          label=f"{data.__name__} n={n}")
+
+
+@pytest.mark.parametrize("eta_max,eta_guard", [(0.05, 0.0), (0.0, 1e-3), (0.02, 1e-3)])
+def test_reconstruct_fp64_guard_and_bound(npw, eta_max, eta_guard):
+    """The optional guard and bound (not in the paper) zero the same faces on both sides, and the
+    GPU flags them (bits 6 / 7)."""
+    op = O.Params(eta_max=eta_max, eta_guard=eta_guard)
+    u = _generic_data(3001, 5)
+    gvm, gvp, gfl, geta = npw.npweno_reconstruct(_dev(u), O.PERIODIC, _gparams(npw, op), with_eta=True)
+    gfl = gfl.cpu().numpy()
+    assert ((gfl & 0xC0) != 0).any()
+    compare_faces(u, O.PERIODIC, op, gvm.cpu().numpy(), gvp.cpu().numpy(), gfl, FP64_TOL, TIE_FRAC_GENERIC,
+                  geta=geta.cpu().numpy(), eta_exact=True, label="guard/bound")
 
 
 @pytest.mark.parametrize("char", [0, 1])
 def test_reconstruct_euler_fp64(npw, char):
+    """Riemann and Shu-Osher-type Euler data, component- and characteristic-wise.  Piecewise
+    constant states are decided exactly (a constant stencil is monotone), so near ties are rare
+    even here."""
     for inst in I.euler_batch(count=4, nmin=64, nmax=2500):
         op = O.Params(characteristic=char)
-        vm, vp, fl, _ = O.reconstruct(inst.u0, O.TRANSMISSIVE, op)
-        gvm, gvp, gfl = npw.npweno_reconstruct(_dev(inst.u0), O.TRANSMISSIVE, _gparams(npw, op))
-        ok = (fl & TIES) == 0
-        tol = FP64_TOL
-        for a, b in ((gvm.cpu().numpy(), vm), (gvp.cpu().numpy(), vp)):
-            for k in range(3):
-                assert np.abs(a[k][ok[k]] - b[k][ok[k]]).max() <= tol * np.abs(b[k]).max()
+        gvm, gvp, gfl, geta = npw.npweno_reconstruct(_dev(inst.u0), O.TRANSMISSIVE, _gparams(npw, op), with_eta=True)
+        compare_faces(inst.u0, O.TRANSMISSIVE, op, gvm.cpu().numpy(), gvp.cpu().numpy(), gfl.cpu().numpy(),
+                      FP64_TOL, 0.02, geta=geta.cpu().numpy(), eta_exact=not char, label=f"euler {inst.kind}")
 
 
 def test_flux_fp64(npw):
@@ -182,6 +209,47 @@ def test_euler_batch_fp64(npw, char):
         assert s["steps"] == rst["steps"]
         assert _rel(got, ref) <= 1e-11
         off += 3 * it.n
+
+
+# ------------------------------------------------------------------------------ decision counts
+@pytest.mark.parametrize("k", [3, 2])
+@pytest.mark.parametrize("scheme", [O.RBF_ENO, O.RBF_WENO])
+def test_solve_decision_counts_match_oracle_fp64(npw, k, scheme):
+    """npw_solve_stats counts the shape-parameter decisions of every stage (switch fired, eta
+    evaluated, zeroed by the guard, zeroed by the bound); in FP64 they equal the oracle's counts
+    over the same run.  A bound and a guard are set so that both fire."""
+    u0, dx = I.advection_sin(201)
+    u0 = u0 + 0.3 * (np.arange(201) > 120)
+    op = O.Params(k=k, scheme=scheme, eta_max=0.05, eta_guard=1e-3)
+    ref, rst = O.solve(u0, dx, 0.3, 0.5, O.ADVECTION, O.PERIODIC, op)
+    gu = _dev(u0)
+    st = npw.npweno_solve(gu, dx, 0.3, 0.5, O.ADVECTION, O.PERIODIC, _gparams(npw, op))
+    assert st["steps"] == rst["steps"]
+    assert _rel(gu.cpu().numpy(), ref) <= FP64_TOL
+    print(f"k={k}: oracle {rst['eta']}, GPU {st['eta']}")
+    assert st["eta"] == rst["eta"]
+    assert rst["eta"]["bound"] > 0 and rst["eta"]["guard"] > 0 and rst["eta"]["switch"] > 0
+    per_step = (2 if k == 2 else 1) * 3 * 202  # faces (k = 2: face values) per step
+    assert sum(st["eta"][x] for x in ("switch", "eval")) == per_step * st["steps"]
+
+
+def test_batch_and_2d_decision_counts_match_oracle_fp64(npw):
+    inst = I.burgers_batch(count=5, nmin=64, nmax=2600, seed_index=4)
+    op = O.Params(rbf=O.GA, eta_max=0.2)
+    table, total = npw.make_instances([it.n for it in inst], [it.dx for it in inst], [0.4] * 5, [0.5] * 5, [0] * 5)
+    arena = _dev(np.concatenate([it.u0[0] for it in inst]))
+    status, stats = npw.npweno_batch_solve(arena, table, 1, O.BURGERS, _gparams(npw, op))
+    assert status == 0
+    for it, s in zip(inst, stats):
+        _, rst = O.solve(it.u0[0], it.dx, 0.4, 0.5, O.BURGERS, O.PERIODIC, op)
+        assert s["eta"] == rst["eta"], (it.n, s["eta"], rst["eta"])
+    U, d = I.four_quadrant(40, np.random.default_rng(4))
+    U = np.ascontiguousarray(U[:, :, :37])
+    op = O.Params(eta_max=0.3)
+    _, rst = O.solve_2d(U, d, d, 0.02, 0.5, O.EULER2D, O.PERIODIC, op)
+    st = npw.npweno_solve_2d(_dev(U), d, d, 0.02, 0.5, O.EULER2D, O.PERIODIC, _gparams(npw, op))
+    assert st["steps"] == rst["steps"]
+    assert st["eta"] == rst["eta"], (st["eta"], rst["eta"])
 
 
 # ------------------------------------------------------------------------------ 2D
@@ -318,18 +386,11 @@ def test_reconstruct_mixed_decisions_match_fp64(npw, scheme, variant, eta_eval):
     for n in (64, 1500, 4097):
         u = _near_tie_data(n, n) if n != 64 else _mixed_data(n, 5).astype(np.float32).astype(np.float64)
         op = O.Params(scheme=scheme, switch_variant=variant, eta_guard=MIXED_GUARD)
-        vm, vp, fl, _ = O.reconstruct(u, O.PERIODIC, op)
         gp = _gparams(npw, op, precision=1)
         gp.eta_eval = eta_eval
-        gvm, gvp, gfl = npw.npweno_reconstruct(_dev(u, torch.float32), O.PERIODIC, gp)
-        gvm = gvm.cpu().numpy().astype(np.float64)
-        gvp = gvp.cpu().numpy().astype(np.float64)
-        gfl = gfl.cpu().numpy()
-        ok = (fl & TIES) == 0
-        assert np.array_equal(gfl[ok] & 0x3D, fl[ok] & 0x3D), n
-        scale = np.abs(u).max()
-        assert np.abs(gvm[ok] - vm[ok]).max() <= 2e-6 * scale, n
-        assert np.abs(gvp[ok] - vp[ok]).max() <= 2e-6 * scale, n
+        gvm, gvp, gfl, geta = npw.npweno_reconstruct(_dev(u, torch.float32), O.PERIODIC, gp, with_eta=True)
+        compare_faces(u, O.PERIODIC, op, gvm.cpu().numpy(), gvp.cpu().numpy(), gfl.cpu().numpy(), 2e-6,
+                      1.0 if n < 100 else TIE_FRAC_NEAR, geta=geta.cpu().numpy(), label=f"mixed n={n}")
 
 
 def test_mixed_precision_full_burgers_instance_stays_finite(npw):
@@ -383,6 +444,7 @@ def test_resident_matches_per_stage_kernels(npw, family, k):
     assert np.array_equal(outs[0][0], outs[1][0])
     for a, b in zip(outs[0][1], outs[1][1]):
         assert a["steps"] == b["steps"] and a["t"] == b["t"] and a["alpha_max"] == b["alpha_max"]
+        assert a["eta"] == b["eta"]
 
 
 def test_per_stage_mixed_burgers_accuracy(npw):

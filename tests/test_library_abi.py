@@ -41,19 +41,21 @@ def test_default_params_and_errors_without_gpu():
     lib.npw_default_params(ctypes.byref(p))
     assert (p.k, p.scheme, p.rbf, p.monotone_switch, p.precision) == (3, npw.NPW_RBF_WENO, npw.NPW_RBF_MQ, 1, npw.NPW_FP64)
     assert p.eps_weno == 1e-6 and p.gamma == 1.4 and p.eps_M == 1e-12
+    # the shape parameter as printed: no bound, no step limit, the default tie margin
+    assert p.eta_max == 0.0 and p.max_steps == 0 and p.tie_tol == 0.0
     # argument validation happens before any CUDA call
     bad = npw.Params(k=4).c()
     st = lib.npweno_reconstruct(ctypes.c_void_p(16), 100, 1, 0, ctypes.byref(bad), ctypes.c_void_p(16),
-                                ctypes.c_void_p(16), None, None)
+                                ctypes.c_void_p(16), None, None, None)
     assert st == npw.NPW_EINVAL and b"k must be 2" in lib.npw_last_error()
     badtile = npw.Params(tile_1d=300).c()
     st = lib.npweno_reconstruct(ctypes.c_void_p(16), 100, 1, 0, ctypes.byref(badtile), ctypes.c_void_p(16),
-                                ctypes.c_void_p(16), None, None)
+                                ctypes.c_void_p(16), None, None, None)
     assert st == npw.NPW_EINVAL and b"tile_1d" in lib.npw_last_error()
     assert lib.npw_autotune_scratch_bytes(1, ctypes.byref(npw.Params(precision=1).c())) > (1 << 21) * 4
     good = npw.Params().c()
     st = lib.npweno_reconstruct(ctypes.c_void_p(16), 5, 1, 0, ctypes.byref(good), ctypes.c_void_p(16),
-                                ctypes.c_void_p(16), None, None)
+                                ctypes.c_void_p(16), None, None, None)
     assert st == npw.NPW_EINVAL
     assert lib.npw_workspace_size(1000, 1, ctypes.byref(good)) > 2 * 1000 * 8
     assert lib.npw_version() >= 10000

@@ -215,20 +215,42 @@ def test_eta_guard_on_unresolved_denominator():
 def test_eta_bound_on_monotone_zero_slope_stencil():
     """A monotone stencil with nearly zero slope at the face, (-1, -1/15 - 1e-3, 1/15 + 1e-3, 1):
     12 p'(s) = 9.56 s^2 + 0.03 > 0 (the switch does not fire) while the Table k3 denominator is
-    only 0.03, so eta = -53 (at (-1, -1/15, 1/15, 1) it would be num / eps_M ~ 1e12).  The bound
-    eta_max (a reading, default 1) returns the polynomial reconstruction there; the smooth data
-    of the paper's tests have |eta| < 0.05 and are untouched."""
+    only 0.03, so eta = -53 (at (-1, -1/15, 1/15, 1) it would be num / eps_M ~ 1e12).  The
+    optional bound eta_max (a reading, off by default) returns the polynomial reconstruction
+    there and marks the face; the smooth data of the paper's tests have |eta| < 0.05 and are
+    untouched."""
     w = np.array([3.0, 3.0, -1.0, -1.0 / 15.0 - 1e-3, 1.0 / 15.0 + 1e-3, 1.0, 1.0, 1.0])
     fires, near = O.switch_k3(w[2:6], tol=1e-9)
     assert not fires and not near
-    _, _, _, eta_off = O.reconstruct(w, O.TRANSMISSIVE, O.Params(eta_max=0.0))
-    _, _, _, eta_on = O.reconstruct(w, O.TRANSMISSIVE, O.Params())
+    _, _, _, eta_off, z_off, c_off = O.reconstruct(w, O.TRANSMISSIVE, O.Params(), with_reason=True)
+    _, _, _, eta_on, z_on, c_on = O.reconstruct(w, O.TRANSMISSIVE, O.Params(eta_max=1.0), with_reason=True)
     face = 4  # between cells 3 and 4: stencil cells 2..5
     assert eta_off[face] == pytest.approx(-1.594 / 0.03, rel=1e-6) and eta_on[face] == 0.0
+    assert z_on[face] == O.ZERO_BOUND_L and c_on["bound"] == np.count_nonzero(z_on) >= 1
+    assert not z_off.any() and c_off["bound"] == 0 and c_off["guard"] == 0
     u, dx = I.advection_sin(40)
-    _, _, _, e1 = O.reconstruct(u, O.PERIODIC, O.Params())
-    _, _, _, e0 = O.reconstruct(u, O.PERIODIC, O.Params(eta_max=0.0))
+    _, _, _, e1 = O.reconstruct(u, O.PERIODIC, O.Params(eta_max=1.0))
+    _, _, _, e0 = O.reconstruct(u, O.PERIODIC, O.Params())
     np.testing.assert_array_equal(e1, e0)
+
+
+def test_decision_counters_add_up():
+    """The counters of a reconstruction: every face of an RBF scheme either has its eta zeroed by
+    the switch or evaluated (k = 3: one per face; k = 2: one per face value); the guard and the
+    bound count among the evaluated ones, and agree with the zero-reason bytes."""
+    g = np.random.default_rng(7)
+    u = np.concatenate([np.linspace(0.0, 1.0, 30) ** 3, np.full(10, 1.0), 1.0 + 0.1 * np.sin(np.arange(40)),
+                        np.cumsum(g.uniform(0.0, 1.0, 40))])
+    for k, per_face in ((3, 1), (2, 2)):
+        p = O.Params(k=k, eta_guard=1e-3, eta_max=0.02)
+        _, _, fl, _, z, c = O.reconstruct(u, O.TRANSMISSIVE, p, with_reason=True)
+        assert c["switch"] + c["eval"] == per_face * u.size + per_face
+        gl, bl = O.ZERO_GUARD_L, O.ZERO_BOUND_L
+        assert c["guard"] == np.count_nonzero(z & gl) + np.count_nonzero(z & (gl << 2))
+        assert c["bound"] == np.count_nonzero(z & bl) + np.count_nonzero(z & (bl << 2))
+        assert c["guard"] > 0 and c["bound"] > 0
+        sw = np.count_nonzero(fl & O.FLAG_SWITCH) + (np.count_nonzero(fl & O.FLAG_SWITCH_R_K2) if k == 2 else 0)
+        assert c["switch"] == sw
 
 
 # --------------------------------------------------------------------------------------- k = 2
