@@ -26,7 +26,7 @@ namespace fast {
 // float copies of the method parameters (rounded on the host)
 struct FParams {
     float eps_weno, eps_M_f, eps_M_lo, eta_guard, eta_max;
-    double eps_M;
+    double eps_M, eta_guard_d;
     int scheme, rbf, monotone_switch, switch_variant, eta_eval;
 };
 __device__ __forceinline__ FParams fparams(const MethodParams& mp) {
@@ -37,6 +37,7 @@ __device__ __forceinline__ FParams fparams(const MethodParams& mp) {
     f.eta_guard = mp.eta_guard_f;
     f.eta_max = mp.eta_max_f;
     f.eps_M = mp.eps_M;
+    f.eta_guard_d = mp.eta_guard;
     f.scheme = mp.scheme;
     f.rbf = mp.rbf;
     f.monotone_switch = mp.monotone_switch;
@@ -259,21 +260,43 @@ __device__ __forceinline__ void eta_pairs(float w0, float w1, float w2, float w3
     dl = de + (al + (p15e + 15.f * bl));
 }
 
-// FP64 evaluation of the quotient.  Numerator and denominator come from the float pairs of
-// eta_pairs, with eps_M (as its float pair, within 2^-48 of the double value) folded into the
-// denominator pair by two_sum; each pair is widened exactly and summed by one FP64 add.  The
-// quotient is the Newton-Raphson reciprocal iteration in double: the seed r0 is the fast float
-// reciprocal of den truncated to float (|1 - den r0| < 2^-21); with e = 1 - den r0 (one
-// multiply-add) and q0 = num r0, the quotient num r0 (1 + e) = (num / den)(1 - e^2) is within
-// 2^-42 of num / den before the rounding to float.  FP64-pipe instructions: 2 adds (numerator,
-// denominator), 1 multiply and 2 multiply-adds; the format changes are integer work.
-// NZ: the four pair components are zero or normal (the cheaper widening applies); the other
-// case, possible only for cell averages below 2^-100 in magnitude or not finite, takes the
-// same arithmetic out of line.
+// FP64 evaluation of the Table k3 shape parameter from the float cell averages.  The four
+// averages are widened exactly (integer format changes), a = w0 - w3 and b = w2 - w1 are FP64
+// differences (exact unless the exponents differ by more than 29), and num = a + 3 b and
+// den0 = a + 15 b are single-rounding multiply-adds, den = den0 + eps_M.  Numerator and
+// denominator thus carry only the rounding of an FP64 evaluation of the undivided differences
+// (2^-53 relative to |a| + 3|b| and |a| + 15|b|), however much they cancel.  The quotient is the
+// Newton-Raphson reciprocal iteration in double: the seed r0 is the fast float reciprocal of den
+// truncated to float (|1 - den r0| < 2^-21); with e = 1 - den r0 (one multiply-add) and
+// q0 = num r0, num r0 (1 + e) = (num / den)(1 - e^2) is within 2^-41 of num / den before the
+// rounding to float.  FP64-pipe instructions: 2 adds (a, b), 2 multiply-adds (num, den0), 1 add
+// (eps_M), 1 multiply and 2 multiply-adds (the quotient).
+// The guard compares |den0| with eta_guard (|w0| + 15|w1| + 15|w2| + |w3|): decided from the
+// float product where it is more than 2^-20 away (the float value is within 6 u of the exact
+// one), else by the FP64 path's own expression, out of line.
+// NZ: the four averages are zero or normal (the cheaper widening applies); the other case
+// (subnormal, infinite or NaN averages) takes the same arithmetic out of line.
+static __device__ __noinline__ bool guard_exact(float w0, float w1, float w2, float w3, double eta_guard) {
+    const double v0 = widen(w0), v1 = widen(w1), v2 = widen(w2), v3 = widen(w3);
+    const double den0 = v0 - 15.0 * v1 + 15.0 * v2 - v3;
+    return fabs(den0) <= eta_guard * (fabs(v0) + 15.0 * fabs(v1) + 15.0 * fabs(v2) + fabs(v3));
+}
 template <bool NZ>
-__device__ __forceinline__ float eta_quot(float nh, float nl, float eh, float el) {
-    const double num = widen_as<NZ>(nh) + widen_as<NZ>(nl);
-    const double den = widen_as<NZ>(eh) + widen_as<NZ>(el);
+__device__ __forceinline__ float eta_quot(float w0, float w1, float w2, float w3, const FParams& fp, float guard,
+                                          uint32_t* fl) {
+    const double a = widen_as<NZ>(w0) - widen_as<NZ>(w3);
+    const double b = widen_as<NZ>(w2) - widen_as<NZ>(w1);
+    const double den0 = fma(15.0, b, a);
+    if (guard > 0.0f) {
+        const double g = widen_nz(guard);
+        const double d0 = fabs(den0);
+        if (d0 <= g * (1.0 + 0x1p-20) && (d0 < g * (1.0 - 0x1p-20) || guard_exact(w0, w1, w2, w3, fp.eta_guard_d))) {
+            *fl |= FL_ZERO_GUARD;
+            return 0.0f;
+        }
+    }
+    const double num = fma(3.0, b, a);
+    const double den = den0 + fp.eps_M;
     float denf;
     if (!seed_f(den, &denf)) return div_rn_f(num, den);
     const double r0 = widen_nz(__fdividef(1.0f, denf));  // |r0| in (2^-99, 2^99]: normal
@@ -281,30 +304,22 @@ __device__ __forceinline__ float eta_quot(float nh, float nl, float eh, float el
     const double e = fma(-den, r0, 1.0);
     return narrow(fma(q0, e, q0));
 }
-static __device__ __noinline__ float eta_quot_any(float nh, float nl, float eh, float el) {
-    return eta_quot<false>(nh, nl, eh, el);
+static __device__ __noinline__ float eta_quot_any(float w0, float w1, float w2, float w3, const FParams& fp,
+                                                  float guard, uint32_t* fl) {
+    return eta_quot<false>(w0, w1, w2, w3, fp, guard, fl);
 }
 __device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3, const FParams& fp, float guard,
                                           uint32_t* fl) {
-    float nh, nl, dh, dl;
-    eta_pairs(w0, w1, w2, w3, nh, nl, dh, dl);
-    if (guard > 0.0f && fabsf(dh + dl) <= guard * (1.0f + 2.0f * kU)) {
-        // near or below the guard: decide in double
-        if (fabs(widen(dh) + widen(dl)) <= widen(guard)) {
-            *fl |= FL_ZERO_GUARD;
-            return 0.0f;
-        }
-    }
-    float eh, et;
-    two_sum(dh, fp.eps_M_f, eh, et);
-    const float el = dl + (et + fp.eps_M_lo);
-    if (!(zero_or_normal(nh) & zero_or_normal(nl) & zero_or_normal(eh) & zero_or_normal(el)))
-        return eta_quot_any(nh, nl, eh, el);
-    return eta_quot<true>(nh, nl, eh, el);
+    if (!(zero_or_normal(w0) & zero_or_normal(w1) & zero_or_normal(w2) & zero_or_normal(w3)))
+        return eta_quot_any(w0, w1, w2, w3, fp, guard, fl);
+    return eta_quot<true>(w0, w1, w2, w3, fp, guard, fl);
 }
 
-// Double-float evaluation (no FP64 instruction): the pairs of eta_pairs, eps_M added by
-// two_sum, renormalised, and the double-float quotient (one correction of the float quotient).
+// Double-float evaluation (eta_eval 1, no FP64 instruction): the pairs of eta_pairs, eps_M added
+// by two_sum, renormalised, and the double-float quotient (one correction of the float
+// quotient).  Its numerator and denominator are within ~2^-47 of the magnitudes of their terms
+// (|a| + 3|b|, |a| + 15|b|), against 2^-53 for the FP64 evaluation: where they cancel strongly
+// the quotient is correspondingly less accurate than eta_eval 0.
 __device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, float w3, float eps_M, float guard,
                                                  uint32_t* fl) {
     float nh, nl, dh, dl;
@@ -469,21 +484,21 @@ __device__ __forceinline__ float cell_value_k2_f(const float* c, int side, float
 //     and the double evaluation within 2^-52 of it): only a float margin smaller than that
 //     bound sends the test to double, where it is the FP64 path's expression, so the outcome
 //     is the FP64 path's.
-//   * The numerator (b - a) + (b - d) and the denominator 4b + 2d + (b - a) + eps_M are formed
-//     as float pairs (exact two_sum differences, the leading terms added by two_sum, eps_M as
-//     its float pair), each within ~2^-46 of its largest term, and widened to double by one
-//     FP64 add each.
+//   * The averages are widened exactly; the numerator -a + 2b - d is 2b - (a + d) by one add and
+//     one multiply-add, the denominator -a + 5b + 2d by two multiply-adds plus eps_M: the
+//     rounding of an FP64 evaluation of the undivided differences, however much they cancel.
 //   * One reciprocal serves both quotients: r0, the fast float reciprocal of den truncated to
 //     float (|1 - den r0| < 2^-21), and e = 1 - den r0; each quotient is q0 (1 + e) with
-//     q0 = num r0, within 2^-42 of num / den.
+//     q0 = num r0, within 2^-41 of num / den.
 //   * The factor 2 of the multiquadric row is applied to the rounded float value (exact).
-// FP64-pipe instructions per face value: 2 for the pairs, 1 for e and 2 per quotient (on the
-// cross, 2 more for the two numerators).
+// FP64-pipe instructions per face value: 5 for numerator and denominator, 1 for e and 2 per
+// quotient (on the cross, 2 more for the two numerators and 2 for the second quotient).
 template <bool NZ>
-__device__ __forceinline__ void eta_k2_quot(float bh, float bl, float dh, float dl, double trans, const FParams& fp,
-                                            float* ec, float* ex, uint32_t* fl) {
-    const double base = widen_as<NZ>(bh) + widen_as<NZ>(bl);
-    const double den = widen_as<NZ>(dh) + widen_as<NZ>(dl);
+__device__ __forceinline__ void eta_k2_quot(float af, float bf, float df, double trans, const FParams& fp, float* ec,
+                                            float* ex, uint32_t* fl) {
+    const double a = widen_as<NZ>(af), b = widen_as<NZ>(bf), d = widen_as<NZ>(df);
+    const double base = fma(2.0, b, -(a + d));
+    const double den = fma(5.0, b, fma(2.0, d, -a)) + fp.eps_M;
     float denf, vc, vx;
     if (seed_f(den, &denf)) {
         const double r0 = widen_nz(__fdividef(1.0f, denf));
@@ -511,9 +526,9 @@ __device__ __forceinline__ void eta_k2_quot(float bh, float bl, float dh, float 
     *ex = zx ? 0.0f : vx;
     if (zc | zx) *fl |= FL_ZERO_BOUND;
 }
-static __device__ __noinline__ void eta_k2_quot_any(float bh, float bl, float dh, float dl, double trans,
-                                                    const FParams& fp, float* ec, float* ex, uint32_t* fl) {
-    eta_k2_quot<false>(bh, bl, dh, dl, trans, fp, ec, ex, fl);
+static __device__ __noinline__ void eta_k2_quot_any(float af, float bf, float df, double trans, const FParams& fp,
+                                                    float* ec, float* ex, uint32_t* fl) {
+    eta_k2_quot<false>(af, bf, df, trans, fp, ec, ex, fl);
 }
 // fl: FL_ZERO_GUARD / FL_ZERO_BOUND where the guard / the bound set a shape parameter to 0
 __device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double trans, const MethodParams& mp,
@@ -532,19 +547,10 @@ __device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double tr
             }
         }
     }
-    float p, pe, q, qe, bh, be, s1, e1, s2, e2, dh, dt;
-    two_sum(bf, -af, p, pe);  // b - a
-    two_sum(bf, -df, q, qe);  // b - d
-    two_sum(p, q, bh, be);
-    const float bl = be + (pe + qe);
-    two_sum(4.0f * bf, 2.0f * df, s1, e1);
-    two_sum(s1, p, s2, e2);
-    two_sum(s2, fp.eps_M_f, dh, dt);
-    const float dl = ((e1 + e2) + pe) + (dt + fp.eps_M_lo);
-    if (zero_or_normal(bh) & zero_or_normal(bl) & zero_or_normal(dh) & zero_or_normal(dl))
-        eta_k2_quot<true>(bh, bl, dh, dl, trans, fp, ec, ex, fl);
+    if (zero_or_normal(af) & zero_or_normal(bf) & zero_or_normal(df))
+        eta_k2_quot<true>(af, bf, df, trans, fp, ec, ex, fl);
     else
-        eta_k2_quot_any(bh, bl, dh, dl, trans, fp, ec, ex, fl);
+        eta_k2_quot_any(af, bf, df, trans, fp, ec, ex, fl);
 }
 
 // Decisions of a k = 2 cell, as returned by cell_recon_k2: FL_SWITCH (the cell's switch fired:

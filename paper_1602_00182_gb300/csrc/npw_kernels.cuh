@@ -308,18 +308,16 @@ __global__ void __launch_bounds__(THREADS_1D) alpha_init_kernel(const R* __restr
 // The fused stage kernel (1D).  Shared memory: su[(tile + 6) * M] cell-major stage input
 // with 3 ghost cells per side, sh[(tile + 1) * M] face fluxes.
 // ---------------------------------------------------------------------------------------
+// One work item (instance td.inst, tile starting at cell td.start) of one stage; the CTA calls
+// it together.  smem: (a.tile + 6 + a.tile + 1) * M elements of R.
 template <typename R, typename D, int KIND, bool CHAR>
-__global__ void __launch_bounds__(THREADS_1D) stage1d_kernel(Stage1DArgs a) {
+__device__ __forceinline__ void stage1d_body(const Stage1DArgs& a, const Tile td, const InstDev& in, Ctl* ctl,
+                                             unsigned char* smem_raw) {
     constexpr int M = kind_m<KIND>();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     __shared__ int redbad[32];
     R* su = reinterpret_cast<R*>(smem_raw);
     R* sh = su + (a.tile + 6) * M;
-
-    const Tile td = a.tiles[blockIdx.x];
-    const InstDev in = a.inst[td.inst];
-    Ctl* ctl = a.ctl + td.inst;
     if (*(volatile int32_t*)&ctl->done) return;  // uniform over the CTA
     const int64_t n = in.n;
     const int c0 = td.start;
@@ -491,9 +489,9 @@ __device__ __forceinline__ void warp_line_pass(int lo, int hi, int n, int lane, 
 // phase is skipped.
 // ---------------------------------------------------------------------------------------
 template <int KIND, int K>
-__global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a) {
+__device__ __forceinline__ void stage1d_fast_body(const Stage1DArgs& a, const Tile td, const InstDev& in, Ctl* ctl,
+                                                  unsigned char* smem_raw) {
     constexpr int M = kind_m<KIND>();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float red[32];
     __shared__ int redbad[32];
     __shared__ float s_lam;
@@ -502,10 +500,6 @@ __global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a)
     float* se = su + span_max * M;
     float* svm = se + span_max * M;
     float* svp = svm + span_max * M;
-
-    const Tile td = a.tiles[blockIdx.x];
-    const InstDev in = a.inst[td.inst];
-    Ctl* ctl = a.ctl + td.inst;
     if (*(volatile int32_t*)&ctl->done) return;  // uniform over the CTA
     const int64_t n = in.n;
     const int c0 = td.start;
@@ -916,26 +910,32 @@ __device__ __forceinline__ float halo_get(const float* u, const Inst2D& in, int 
 // face-by-face kernel's; the phases avoid reconstructing a cell once per face and the uneven
 // per-thread face counts of that kernel.
 // ---------------------------------------------------------------------------------------
+// shared memory (floats) of the 2D fast body: the (TX+6) x (TY+6) block and three face arrays
+template <int M>
+__host__ __device__ constexpr int stage2d_fast_smem_floats() {
+    return ((TY_2D + 6) * (TX_2D + 6) + 3 * ((TX_2D + 1) * TY_2D + TX_2D * (TY_2D + 1))) * M;
+}
+
+// One tile (index `tile` of the instance's tiles_x x tiles_y tiles) of one stage.
 template <int KIND, int K>
-__global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs a) {
+__device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const Inst2D& in, Ctl* ctl, int tile,
+                                                  float* smem) {
     constexpr int M = kind_m<KIND>();
     constexpr int BX = TX_2D + 6, BY = TY_2D + 6;
     constexpr int NFX = (TX_2D + 1) * TY_2D;  // x faces: (qx, qy), qx = 0..TX between cells qx-1, qx
     constexpr int NFY = TX_2D * (TY_2D + 1);  // y faces: (qx, qy), qy = 0..TY
-    __shared__ float su[BY * BX * M];
-    __shared__ float ef[(NFX + NFY) * M];    // eta per (face, field); then the fluxes
-    __shared__ float vmf[(NFX + NFY) * M];   // v^- per (face, field)
-    __shared__ float vpf[(NFX + NFY) * M];   // v^+ per (face, field)
+    float* su = smem;                          // [BY * BX * M]
+    float* ef = su + BY * BX * M;              // [(NFX + NFY) * M] eta per (face, field); then the fluxes
+    float* vmf = ef + (NFX + NFY) * M;         // v^- per (face, field)
+    float* vpf = vmf + (NFX + NFY) * M;        // v^+ per (face, field)
     __shared__ float red[32];
     __shared__ int redbad[32];
     __shared__ float red2[32];
     __shared__ int redbad2[32];
     __shared__ float s_par[5];               // alpha_x, alpha_y, dt, dx, dy in float
-    const Inst2D in = *a.inst;
-    Ctl* ctl = a.ctl;
     if (*(volatile int32_t*)&ctl->done) return;
-    const int tx0 = (blockIdx.x % in.tiles_x) * TX_2D;
-    const int ty0 = (blockIdx.x / in.tiles_x) * TY_2D;
+    const int tx0 = (tile % in.tiles_x) * TX_2D;
+    const int ty0 = (tile / in.tiles_x) * TY_2D;
     const int64_t nx = in.nx, ny = in.ny, cells = nx * ny;
     const float* uin = reinterpret_cast<const float*>(a.uin) + in.off;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -1114,22 +1114,27 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs
     }
 }
 
+// shared memory (elements of R) of the 2D plain body: the block and the two face-flux arrays
+template <int M>
+__host__ __device__ constexpr int stage2d_smem_elems() {
+    return ((TY_2D + 6) * (TX_2D + 6) + TY_2D * (TX_2D + 1) + (TY_2D + 1) * TX_2D) * M;
+}
+
 template <typename R, typename D, int KIND>
-__global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
+__device__ __forceinline__ void stage2d_body(const Stage2DArgs& a, const Inst2D& in, Ctl* ctl, int tile,
+                                             unsigned char* smem_raw) {
     constexpr int M = kind_m<KIND>();
     constexpr int BX = TX_2D + 6, BY = TY_2D + 6;
-    __shared__ R su[BY * BX * M];
-    __shared__ R hx[TY_2D * (TX_2D + 1) * M];
-    __shared__ R hy[(TY_2D + 1) * TX_2D * M];
+    R* su = reinterpret_cast<R*>(smem_raw);   // [BY * BX * M]
+    R* hx = su + BY * BX * M;                 // [TY * (TX + 1) * M]
+    R* hy = hx + TY_2D * (TX_2D + 1) * M;     // [(TY + 1) * TX * M]
     __shared__ double red[32];
     __shared__ int redbad[32];
     __shared__ double red2[32];
     __shared__ int redbad2[32];
-    const Inst2D in = *a.inst;
-    Ctl* ctl = a.ctl;
     if (*(volatile int32_t*)&ctl->done) return;
-    const int tx0 = (blockIdx.x % in.tiles_x) * TX_2D;
-    const int ty0 = (blockIdx.x / in.tiles_x) * TY_2D;
+    const int tx0 = (tile % in.tiles_x) * TX_2D;
+    const int ty0 = (tile / in.tiles_x) * TY_2D;
     const int64_t nx = in.nx, ny = in.ny, cells = nx * ny;
     const R* uin = reinterpret_cast<const R*>(a.uin) + in.off;
     const int tid = threadIdx.x;
@@ -1307,6 +1312,36 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) alpha_init_2d_kernel(const R* _
 }
 
 // ---------------------------------------------------------------------------------------
+// One CTA per work item: the per-stage kernels of the 1D runtime (tile table) and of a single
+// 2D instance (blockIdx.x = tile index).
+// ---------------------------------------------------------------------------------------
+template <typename R, typename D, int KIND, bool CHAR>
+__global__ void __launch_bounds__(THREADS_1D) stage1d_kernel(Stage1DArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Tile td = a.tiles[blockIdx.x];
+    stage1d_body<R, D, KIND, CHAR>(a, td, a.inst[td.inst], a.ctl + td.inst, smem_raw);
+}
+
+template <int KIND, int K>
+__global__ void __launch_bounds__(THREADS_1D) stage1d_fast_kernel(Stage1DArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Tile td = a.tiles[blockIdx.x];
+    stage1d_fast_body<KIND, K>(a, td, a.inst[td.inst], a.ctl + td.inst, smem_raw);
+}
+
+template <int KIND, int K>
+__global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_fast_kernel(Stage2DArgs a) {
+    extern __shared__ __align__(16) float smem_f[];
+    stage2d_fast_body<KIND, K>(a, *a.inst, a.ctl, blockIdx.x, smem_f);
+}
+
+template <typename R, typename D, int KIND>
+__global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stage2d_body<R, D, KIND>(a, *a.inst, a.ctl, blockIdx.x, smem_raw);
+}
+
+// ---------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------
 // smooth data for the tile autotuner: m = 1: 1 + 0.5 sin(16 pi x); m = 3: a quiet Euler state
@@ -1462,22 +1497,22 @@ struct Launchers {
             // the mixed path: the phased kernel, k = 3 or k = 2
             switch (kind * 4 + a.mp.k) {
                 case NPW_FLUX_ADVECTION * 4 + 3:
-                    stage2d_fast_kernel<NPW_FLUX_ADVECTION_, 3><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                    stage2d_fast_kernel<NPW_FLUX_ADVECTION_, 3><<<tiles, TX_2D * TY_2D, stage2d_fast_smem_floats<1>() * sizeof(float), s>>>(a);
                     break;
                 case NPW_FLUX_BURGERS * 4 + 3:
-                    stage2d_fast_kernel<NPW_FLUX_BURGERS_, 3><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                    stage2d_fast_kernel<NPW_FLUX_BURGERS_, 3><<<tiles, TX_2D * TY_2D, stage2d_fast_smem_floats<1>() * sizeof(float), s>>>(a);
                     break;
                 case NPW_FLUX_EULER2D * 4 + 3:
-                    stage2d_fast_kernel<NPW_FLUX_EULER2D_, 3><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                    stage2d_fast_kernel<NPW_FLUX_EULER2D_, 3><<<tiles, TX_2D * TY_2D, stage2d_fast_smem_floats<4>() * sizeof(float), s>>>(a);
                     break;
                 case NPW_FLUX_ADVECTION * 4 + 2:
-                    stage2d_fast_kernel<NPW_FLUX_ADVECTION_, 2><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                    stage2d_fast_kernel<NPW_FLUX_ADVECTION_, 2><<<tiles, TX_2D * TY_2D, stage2d_fast_smem_floats<1>() * sizeof(float), s>>>(a);
                     break;
                 case NPW_FLUX_BURGERS * 4 + 2:
-                    stage2d_fast_kernel<NPW_FLUX_BURGERS_, 2><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                    stage2d_fast_kernel<NPW_FLUX_BURGERS_, 2><<<tiles, TX_2D * TY_2D, stage2d_fast_smem_floats<1>() * sizeof(float), s>>>(a);
                     break;
                 case NPW_FLUX_EULER2D * 4 + 2:
-                    stage2d_fast_kernel<NPW_FLUX_EULER2D_, 2><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                    stage2d_fast_kernel<NPW_FLUX_EULER2D_, 2><<<tiles, TX_2D * TY_2D, stage2d_fast_smem_floats<4>() * sizeof(float), s>>>(a);
                     break;
                 default:
                     return cudaErrorInvalidValue;
@@ -1486,13 +1521,13 @@ struct Launchers {
         }
         switch (kind) {
             case NPW_FLUX_ADVECTION:
-                stage2d_kernel<R, D, NPW_FLUX_ADVECTION_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                stage2d_kernel<R, D, NPW_FLUX_ADVECTION_><<<tiles, TX_2D * TY_2D, stage2d_smem_elems<1>() * sizeof(R), s>>>(a);
                 break;
             case NPW_FLUX_BURGERS:
-                stage2d_kernel<R, D, NPW_FLUX_BURGERS_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                stage2d_kernel<R, D, NPW_FLUX_BURGERS_><<<tiles, TX_2D * TY_2D, stage2d_smem_elems<1>() * sizeof(R), s>>>(a);
                 break;
             case NPW_FLUX_EULER2D:
-                stage2d_kernel<R, D, NPW_FLUX_EULER2D_><<<tiles, TX_2D * TY_2D, 0, s>>>(a);
+                stage2d_kernel<R, D, NPW_FLUX_EULER2D_><<<tiles, TX_2D * TY_2D, stage2d_smem_elems<4>() * sizeof(R), s>>>(a);
                 break;
             default:
                 return cudaErrorInvalidValue;

@@ -1,13 +1,17 @@
 """Direct pin of the mixed-precision shape parameter (NPW_FP32_MIXED) against the correctly
 rounded quotient.
 
-The mixed path does not divide in the obvious way: it forms the Table k3 (k = 3) or Table k2
-(k = 2) numerator and denominator from the float cell averages as float pairs, widens them, and
-takes a Newton-Raphson quotient seeded by a fast float reciprocal (eta_eval 0), or a
-double-float quotient (eta_eval 1).  The claim is that the result equals the exact quotient of
-the exact numerator and denominator (with eps_M) rounded once to float, up to one float ulp,
-and that results below the float normal range are flushed to zero.  The reference here is exact
-rational arithmetic (fractions) on the same float data: no part of it comes from the library.
+The mixed path does not divide in the obvious way.  With eta_eval 0 it widens the float cell
+averages, forms the Table k3 (k = 3) or Table k2 (k = 2) numerator and denominator in FP64 by
+differences and single-rounding multiply-adds, and takes a Newton-Raphson quotient seeded by a
+fast float reciprocal; with eta_eval 1 it keeps numerator and denominator as float pairs and
+takes a double-float quotient.  The claim: the result is the exact quotient rounded once to
+float, up to the rounding an FP64 evaluation of the undivided differences carries -- u (|a| +
+3|b|) / |num| + u (|a| + 15|b|) / |den| relative for k = 3 (u = 2^-53; a = w0 - w3,
+b = w2 - w1), which is below one float ulp unless the differences cancel strongly -- plus
+2^-41 for the quotient; eta_eval 1 carries ~2^-47 instead of u.  Results below the float
+normal range are flushed to zero.  The reference is exact rational arithmetic (fractions) on
+the same float data: no part of it comes from the library.
 
 Cases: random stencils, cancelling denominators, denominators near zero relative to the data,
 cell averages below 2^-100 (subnormal pair components), and denominators outside the reciprocal
@@ -69,25 +73,34 @@ def _blocks(seed):
 
 def _exact_eta(u32, k, rbf):
     """Exact-rational quotient of each face (face f between cells f-1 and f, periodic), rounded
-    once to double.  k = 3: (w0 - 3 w1 + 3 w2 - w3) / (w0 - 15 w1 + 15 w2 - w3 + eps_M) on cells
-    f-2..f+1; k = 2 (v^- of cell f-1, cells f-2, f-1, f = a, b, d):
-    F (-a + 2 b - d) / (-a + 5 b + 2 d + eps_M), F = 2 (MQ) or 1 (Gaussian)."""
+    once to double, and the conditioning kappa = S_num / |num| + S_den / |den| of an FP64
+    evaluation.  k = 3: (w0 - 3 w1 + 3 w2 - w3) / (w0 - 15 w1 + 15 w2 - w3 + eps_M) on cells
+    f-2..f+1, S_num = |a| + 3|b|, S_den = |a| + 15|b| + eps_M (a = w0 - w3, b = w2 - w1);
+    k = 2 (v^- of cell f-1, cells f-2, f-1, f = a, b, d): F (-a + 2 b - d) / (-a + 5 b + 2 d +
+    eps_M), F = 2 (MQ) or 1 (Gaussian), S_num = |a| + 2|b| + |d|, S_den = |a| + 5|b| + 2|d| + eps_M."""
     n = u32.size
     fr = [Fraction(float(x)) for x in u32]
     em = Fraction(EPS_M)
     out = np.zeros(n + 1)
+    kap = np.zeros(n + 1)
     for f in range(n + 1):
         c = lambda j: fr[(f + j) % n]
         if k == 3:
-            num = c(-2) - 3 * c(-1) + 3 * c(0) - c(1)
-            den = c(-2) - 15 * c(-1) + 15 * c(0) - c(1) + em
-            out[f] = float(num / den) if den != 0 else np.nan
+            a, b = c(-2) - c(1), c(0) - c(-1)
+            num, den = a + 3 * b, a + 15 * b + em
+            sn, sd = abs(a) + 3 * abs(b), abs(a) + 15 * abs(b) + em
+            fac = 1
         else:
             a, b, d = c(-2), c(-1), c(0)
-            num = -a + 2 * b - d
-            den = -a + 5 * b + 2 * d + em
-            out[f] = float((2 if rbf == O.MQ else 1) * num / den) if den != 0 else np.nan
-    return out
+            num, den = -a + 2 * b - d, -a + 5 * b + 2 * d + em
+            sn, sd = abs(a) + 2 * abs(b) + abs(d), abs(a) + 5 * abs(b) + 2 * abs(d) + em
+            fac = 2 if rbf == O.MQ else 1
+        if den == 0:
+            out[f], kap[f] = np.nan, np.inf
+            continue
+        out[f] = float(fac * num / den)
+        kap[f] = float(sn / abs(num)) + float(sd / abs(den)) if num != 0 else np.inf
+    return out, kap
 
 
 def _ulp32(x):
@@ -104,17 +117,24 @@ def test_mixed_eta_is_the_rounded_exact_quotient(npw, k, eta_eval, rbf):
     _, _, gfl, geta = npw.npweno_reconstruct(torch.tensor(u, device="cuda"), O.PERIODIC, p, with_eta=True)
     geta = geta.cpu().numpy().astype(np.float64)
     assert not (gfl.cpu().numpy() & (GPU_ZERO_GUARD | GPU_ZERO_BOUND)).any()
-    q = _exact_eta(u, k, rbf)
-    fin = np.isfinite(q)
+    q, kap = _exact_eta(u, k, rbf)
+    fin = np.isfinite(q) & np.isfinite(kap)
     normal = fin & (np.abs(q) >= F32_MIN_NORMAL) & (np.abs(q) < 3e38)
     err = np.abs(geta[normal] - q[normal])
-    worst = float((err / _ulp32(q[normal])).max())
-    print(f"k={k} eta_eval={eta_eval} rbf={rbf}: {normal.sum()} faces, worst {worst:.3f} float ulp")
-    assert np.all(err <= _ulp32(q[normal])), worst
+    ulp = _ulp32(q[normal])
+    unit = 2.0 ** -52 if eta_eval == 0 else 2.0 ** -46  # FP64 evaluation / float pairs (with margin)
+    bound = 0.5 * ulp + np.abs(q[normal]) * (unit * (kap[normal] + 5.0) + 2.0 ** -40)
+    worst = float((err / bound).max())
+    well = kap[normal] < 2.0 ** 20  # no strong cancellation: the bound is below one ulp
+    exact = float(np.mean(err[well] <= 0.5 * ulp[well] * (1 + 2.0 ** -20)))
+    print(f"k={k} eta_eval={eta_eval} rbf={rbf}: {normal.sum()} faces ({well.sum()} well conditioned, "
+          f"{exact:.4f} of them rounded to nearest), worst err / bound {worst:.3f}")
+    assert np.all(err <= bound), worst
+    assert np.all(err[well] <= ulp[well])
     # below the float normal range: flushed to a (signed) zero or within the smallest normal
     tiny = fin & (np.abs(q) < F32_MIN_NORMAL)
     assert np.all(np.abs(geta[tiny]) <= F32_MIN_NORMAL)
-    assert normal.sum() > 0.9 * fin.sum()
+    assert normal.sum() > 0.9 * fin.sum() and well.sum() > 0.5 * normal.sum()
 
 
 @pytest.mark.parametrize("k", [3, 2])
