@@ -242,6 +242,38 @@ npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx
                            size_t workspace_bytes, npw_solve_stats* out, void* stream);
 
 /*
+ * Work-queue batch: uneven 1D and 2D instances of any flux kind (the batching pattern around
+ * the method; the paper has no counterpart) advanced together, each with its own dt, alpha,
+ * t_end and step count.  Every RK3 stage is one launch of a persistent kernel whose CTAs take
+ * (instance, tile) work items from a device counter until none is left -- 1D tiles of
+ * params->tile_1d cells (0: the autotuned or default size), 2D tiles of 32 x 8 cells -- and run
+ * the per-stage body of that instance's kind (the same arithmetic as npweno_batch_solve and
+ * npweno_solve_2d, so the same bits); steps are replayed as CUDA graphs between bounded polls.
+ * NPW_FP32_MIXED component-wise runs solve 1D instances that fit in shared memory whole in one
+ * CTA (the resident kernel, batch_mode 0) beside the queue.  Characteristic runs take 1D Euler
+ * instances only.
+ *   arena: device, the instances' fields ([m][n] or [m][ny][nx] at `offset`, element type of
+ *          params->precision); in/out.
+ *   inst:  host, count descriptors (ny = 0 for a 1D instance; m follows the flux kind).
+ *   out:   host, count statistics (may be NULL).
+ * Returns NPW_OK when every instance finished, else the first failing instance's status.
+ */
+typedef struct {
+    int64_t offset;    /* element offset of the instance in the arena */
+    int64_t nx;        /* cells (1D) or cells per row (2D) */
+    int64_t ny;        /* 0: a 1D instance; >= 6: rows of a 2D instance */
+    double dx, dy;     /* cell sizes (dy: 2D only) */
+    double t_end, cfl; /* dt = cfl dx / alpha (1D), cfl / (alpha_x / dx + alpha_y / dy) (2D) */
+    int32_t flux_kind; /* 1D: NPW_FLUX_ADVECTION, _BURGERS, _EULER1D; 2D: _ADVECTION, _BURGERS, _EULER2D */
+    int32_t bc;        /* npw_bc (2D: of x) */
+    int32_t bc_y;      /* 2D: npw_bc of y; < 0: bc */
+    int32_t pad_;
+} npw_queue_instance;
+size_t npw_queue_workspace_size(const npw_queue_instance* inst, int32_t count, const npw_params* params);
+npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32_t count, const npw_params* params,
+                              void* workspace, size_t workspace_bytes, npw_solve_stats* out, void* stream);
+
+/*
  * Request server: continuous batching of 1D solves (no counterpart in the paper; the serving
  * loop around the method).  The server sub-allocates a caller-provided device arena: per
  * request it needs 3 * m * n elements (state and two stage buffers) of the server's precision,

@@ -632,14 +632,15 @@ npw_status collect_stats(const Run1D& r, npw_solve_stats* out) {
         if (out) fill_stats(hc[i], &out[i]);
         if (hc[i].status != NPW_OK && first == NPW_OK) first = (npw_status)hc[i].status;
     }
-    if (first != NPW_OK) return fail(first, "an instance became non-finite");
+    if (first == NPW_ENONFINITE) return fail(first, "an instance became non-finite");
+    if (first != NPW_OK) return fail(first, "an instance reached its step limit or stopped advancing");
     return NPW_OK;
 }
 
 // Library-owned side streams (created once per device) for the resident launches.
 struct SideStreams {
     cudaStream_t st[4];
-    cudaEvent_t fork, join[4];
+    cudaEvent_t fork;
     bool ok = false;
 };
 std::mutex g_side_mu;
@@ -654,7 +655,6 @@ npw_status side_streams(SideStreams** out) {
     if (!s.ok) {
         for (int k = 0; k < 4; ++k) {
             NPW_CUDA(cudaStreamCreateWithFlags(&s.st[k], cudaStreamNonBlocking));
-            NPW_CUDA(cudaEventCreateWithFlags(&s.join[k], cudaEventDisableTiming));
         }
         NPW_CUDA(cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming));
         s.ok = true;
@@ -663,17 +663,27 @@ npw_status side_streams(SideStreams** out) {
     return NPW_OK;
 }
 
-// Launch the resident instances in four size classes (largest first within a class), each on
-// its own side stream after the set-up on the caller's stream; returns the number of streams
-// the caller's stream must join.
-npw_status launch_resident(Run1D& r, const npw_instance* inst, SideStreams* ss, int* joined) {
-    *joined = 0;
+// Launch resident instances (all of one flux kind) in four size classes (largest first within
+// a class), each on its own side stream after the set-up on the caller's stream.  ids: the
+// instances (indices into inst / ctl), n_of / cost_of: their cells and expected work; dlist:
+// device scratch for the index list.  The join events are appended to joins.
+struct ResidentLaunch {
+    void* arena;
+    float* carry;
+    const npw::InstDev* inst;
+    npw::Ctl* ctl;
+    int32_t* dlist;
+    int m;
+    int kind;
+    npw::MethodParams mp;
+};
+npw_status launch_resident_set(const ResidentLaunch& rl, const std::vector<int32_t>& ids,
+                               const std::vector<int64_t>& n_of, const std::vector<double>& cost_of,
+                               SideStreams* ss, cudaStream_t s, std::vector<cudaEvent_t>& joins) {
     std::vector<int32_t> cls[4];
-    for (int i = 0; i < r.count; ++i) {
-        if (!r.resident[i]) continue;
-        const int64_t n = inst[i].n;
-        const int c = n > 4096 ? 0 : (n > 2048 ? 1 : (n > 1024 ? 2 : 3));
-        cls[c].push_back(i);
+    for (int32_t i : ids) {
+        const int64_t n = n_of[i];
+        cls[n > 4096 ? 0 : (n > 2048 ? 1 : (n > 1024 ? 2 : 3))].push_back(i);
     }
     // two 512-thread CTAs per SM for the largest class (64 registers per thread fill the register
     // file either way) measured 10% faster than one 1024-thread CTA
@@ -682,43 +692,58 @@ npw_status launch_resident(Run1D& r, const npw_instance* inst, SideStreams* ss, 
     size_t offs[5] = {0, 0, 0, 0, 0};
     for (int c = 0; c < 4; ++c) {
         auto& v = cls[c];
-        // longest runs first: work ~ n * (t_end / dt) ~ n^2 t_end / (cfl L)
-        std::sort(v.begin(), v.end(), [&](int a, int b) {
-            const double wa = (double)inst[a].n * inst[a].t_end / (inst[a].cfl * inst[a].dx);
-            const double wb = (double)inst[b].n * inst[b].t_end / (inst[b].cfl * inst[b].dx);
-            return wa > wb;
-        });
+        std::sort(v.begin(), v.end(), [&](int a, int b) { return cost_of[a] > cost_of[b]; });  // longest first
         offs[c] = all.size();
         all.insert(all.end(), v.begin(), v.end());
     }
     offs[4] = all.size();
     if (all.empty()) return NPW_OK;
-    int32_t* dlist = reinterpret_cast<int32_t*>(r.ws + r.L.list);
-    NPW_CUDA(cudaMemcpyAsync(dlist, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, r.s));
-    NPW_CUDA(cudaEventRecord(ss->fork, r.s));
+    NPW_CUDA(cudaMemcpyAsync(rl.dlist, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, s));
+    NPW_CUDA(cudaEventRecord(ss->fork, s));
     for (int c = 0; c < 4; ++c) {
         const int cnt = (int)(offs[c + 1] - offs[c]);
         if (cnt == 0) continue;
         int64_t max_n = 0;
-        for (size_t k = offs[c]; k < offs[c + 1]; ++k) max_n = inst[all[k]].n > max_n ? inst[all[k]].n : max_n;
+        for (size_t k = offs[c]; k < offs[c + 1]; ++k) max_n = n_of[all[k]] > max_n ? n_of[all[k]] : max_n;
         NPW_CUDA(cudaStreamWaitEvent(ss->st[c], ss->fork, 0));
         npw::ResidentArgs a{};
-        a.arena = r.arena;
-        a.carry = reinterpret_cast<float*>(r.ws + r.L.cbuf);
-        a.inst = reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst);
-        a.ctl = reinterpret_cast<npw::Ctl*>(r.ws + r.L.ctl);
-        a.list = dlist + offs[c];
+        a.arena = rl.arena;
+        a.carry = rl.carry;
+        a.inst = rl.inst;
+        a.ctl = rl.ctl;
+        a.list = rl.dlist + offs[c];
         a.count = cnt;
-        a.mp = r.mp;
+        a.mp = rl.mp;
         auto ev = stage_begin(ss->st[c], c);
-        cudaError_t e = npw::launch_resident_f32(a, r.m, r.kind, max_n, threads[c], ss->st[c]);
+        cudaError_t e = npw::launch_resident_f32(a, rl.m, rl.kind, max_n, threads[c], ss->st[c]);
         stage_end(ev, ss->st[c], c);
         if (e != cudaSuccess) return cuda_fail(e, "resident kernel launch");
-        NPW_CUDA(cudaEventRecord(ss->join[c], ss->st[c]));
-        r.joins.push_back(ss->join[c]);
-        ++*joined;
+        // one event per launch: a later launch set on the same side stream records its own
+        cudaEvent_t je = nullptr;
+        NPW_CUDA(cudaEventCreateWithFlags(&je, cudaEventDisableTiming));
+        NPW_CUDA(cudaEventRecord(je, ss->st[c]));
+        joins.push_back(je);
     }
     return NPW_OK;
+}
+
+// the 1D batch runtime's resident instances (one flux kind)
+npw_status launch_resident(Run1D& r, const npw_instance* inst, SideStreams* ss, int* joined) {
+    std::vector<int32_t> ids;
+    std::vector<int64_t> n_of(r.count);
+    std::vector<double> cost(r.count);
+    for (int i = 0; i < r.count; ++i) {
+        n_of[i] = inst[i].n;
+        cost[i] = (double)inst[i].n * inst[i].t_end / (inst[i].cfl * inst[i].dx);  // ~ n * steps
+        if (r.resident[i]) ids.push_back(i);
+    }
+    ResidentLaunch rl{r.arena, reinterpret_cast<float*>(r.ws + r.L.cbuf), reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst),
+                      reinterpret_cast<npw::Ctl*>(r.ws + r.L.ctl), reinterpret_cast<int32_t*>(r.ws + r.L.list), r.m,
+                      r.kind, r.mp};
+    const size_t before = r.joins.size();
+    npw_status st = launch_resident_set(rl, ids, n_of, cost, ss, r.s, r.joins);
+    *joined = (int)(r.joins.size() - before);
+    return st;
 }
 
 // compensated float path: the final states are in s; copy them back into the arena
@@ -815,7 +840,9 @@ npw_status run_to_end(Run1D& r, npw_solve_stats* out) {
     for (cudaEvent_t ev : r.joins) {  // resident kernels on the side streams
         cudaError_t e = cudaStreamWaitEvent(r.s, ev, 0);
         if (e != cudaSuccess && st == NPW_OK) st = cuda_fail(e, "cudaStreamWaitEvent");
+        cudaEventDestroy(ev);  // released once the recorded work completes
     }
+    r.joins.clear();
     if (st) return st;
     return collect_stats(r, out);
 }
@@ -1262,6 +1289,478 @@ npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx
     if (!(cfl > 0.0)) return fail(NPW_EINVAL, "cfl must be > 0");
     return run_2d(u, nx, ny, m, dx, dy, 0.0, t_end, cfl, flux_kind, bc, params, workspace, workspace_bytes, out,
                   reinterpret_cast<cudaStream_t>(stream), 1);
+}
+
+}  // extern "C"
+
+// =======================================================================================
+// Work-queue runtime: 1D and 2D instances of any flux kind in one batch, every stage one
+// launch of the persistent queue kernel over all (instance, tile) items; mixed-precision 1D
+// instances that fit in shared memory run whole in the resident kernel beside it.
+// =======================================================================================
+namespace npw {
+
+// mode 0: zero the control words; mode 1: start (alpha^0 from the running maxima, first dt,
+// step limit).  1D instances without items (solved by the resident kernel) are marked done.
+__global__ void queue_ctl_kernel(Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d, int count,
+                                 int mode, int64_t max_steps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    Ctl* c = ctl + i;
+    if (mode == 0) {
+        memset(c, 0, sizeof(Ctl));
+        return;
+    }
+    const bool two_d = is2d[i] != 0;
+    const double ax = __longlong_as_double((long long)c->alpha_next_bits);
+    const double ay = two_d ? __longlong_as_double((long long)c->alpha_y_next_bits) : 0.0;
+    c->alpha_next_bits = 0ull;
+    c->alpha_y_next_bits = 0ull;
+    c->tiles_done = 0u;
+    if (!(ax - ax == 0.0) || !(ay - ay == 0.0)) {
+        c->status = NPW_ENONFINITE;
+        c->done = 1;
+        return;
+    }
+    c->alpha = ax;
+    c->alpha_y = ay;
+    c->alpha_max = ax > ay ? ax : ay;
+    c->t = 0.0;
+    double t_end, cfl, rate;
+    if (two_d) {
+        const Inst2D& in = inst2[i];
+        t_end = in.t_end;
+        cfl = in.cfl;
+        rate = ax / in.dx + ay / in.dy;
+    } else {
+        const InstDev& in = inst1[i];
+        if (in.ntiles == 0) {  // resident instance: its kernel owns the control word
+            c->done = 1;
+            return;
+        }
+        t_end = in.t_end;
+        cfl = in.cfl;
+        rate = ax / in.dx;
+    }
+    if (!(c->t < t_end)) {
+        c->done = 1;
+        return;
+    }
+    double dt = (rate > 0.0) ? cfl / rate : t_end - c->t;
+    int last = 0;
+    if (c->t + dt * (1.0 + 1e-10) >= t_end) {
+        dt = t_end - c->t;
+        last = 1;
+    }
+    c->dt = dt;
+    c->last = last;
+    c->step_cap = step_cap(t_end - c->t, dt, max_steps);
+}
+
+// poll[0] = active instances, poll[1] = largest remaining step estimate
+__global__ void queue_poll_kernel(const Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d,
+                                  int count, long long* poll) {
+    __shared__ long long s_act[256], s_rem[256];
+    long long act = 0, rem = 0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const Ctl& c = ctl[i];
+        if (!c.done) {
+            ++act;
+            const double t_end = is2d[i] ? inst2[i].t_end : inst1[i].t_end;
+            const double r = (c.dt > 0.0) ? (t_end - c.t) / c.dt : 1.0;
+            const long long ri = (long long)(r < 1e9 ? r : 1e9) + 1;
+            rem = ri > rem ? ri : rem;
+        }
+    }
+    s_act[threadIdx.x] = act;
+    s_rem[threadIdx.x] = rem;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s_act[threadIdx.x] += s_act[threadIdx.x + o];
+            s_rem[threadIdx.x] = s_rem[threadIdx.x + o] > s_rem[threadIdx.x] ? s_rem[threadIdx.x + o] : s_rem[threadIdx.x];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        poll[0] = s_act[0];
+        poll[1] = s_rem[0];
+    }
+}
+
+cudaError_t launch_queue_ctl(Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d, int count,
+                             int mode, int64_t max_steps, cudaStream_t s) {
+    queue_ctl_kernel<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(ctl, inst1, inst2, is2d, count, mode, max_steps);
+    return cudaGetLastError();
+}
+cudaError_t launch_queue_poll(const Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d,
+                              int count, long long* poll, cudaStream_t s) {
+    queue_poll_kernel<<<1, 256, 0, s>>>(ctl, inst1, inst2, is2d, count, poll);
+    return cudaGetLastError();
+}
+
+}  // namespace npw
+
+namespace {
+
+struct QLayout {
+    size_t u1, u2, sbuf, cbuf, inst1, inst2, kind, is2d, ctl, items, head, poll, list, total;
+};
+
+QLayout queue_layout(int64_t arena_elems, int count, int64_t nitems, size_t esz, bool comp) {
+    QLayout L{};
+    size_t o = 0;
+    L.u1 = o;
+    o = align256(o + (size_t)arena_elems * esz);
+    L.u2 = o;
+    o = align256(o + (size_t)arena_elems * esz);
+    L.sbuf = o;  // compensated float 1D: next state and carry
+    o = align256(o + (comp ? (size_t)arena_elems * sizeof(float) : 0));
+    L.cbuf = o;
+    o = align256(o + (comp ? (size_t)arena_elems * sizeof(float) : 0));
+    L.inst1 = o;
+    o = align256(o + sizeof(npw::InstDev) * (size_t)count);
+    L.inst2 = o;
+    o = align256(o + sizeof(npw::Inst2D) * (size_t)count);
+    L.kind = o;
+    o = align256(o + sizeof(int32_t) * (size_t)count);
+    L.is2d = o;
+    o = align256(o + (size_t)count);
+    L.ctl = o;
+    o = align256(o + sizeof(npw::Ctl) * (size_t)count);
+    L.items = o;
+    o = align256(o + sizeof(npw::Tile) * (size_t)nitems);
+    L.head = o;
+    o = align256(o + 2 * sizeof(unsigned int));
+    L.poll = o;
+    o = align256(o + 4 * sizeof(long long));
+    L.list = o;
+    o = align256(o + sizeof(int32_t) * (size_t)count);
+    L.total = o;
+    return L;
+}
+
+bool is_2d_kind(const npw_queue_instance& q) { return q.ny != 0; }
+int64_t items_of(const npw_queue_instance& q, int tile) {
+    if (is_2d_kind(q)) return ((q.nx + npw::TX_2D - 1) / npw::TX_2D) * ((q.ny + npw::TY_2D - 1) / npw::TY_2D);
+    return (q.nx + tile - 1) / tile;
+}
+int64_t cells_of(const npw_queue_instance& q) { return q.nx * (q.ny ? q.ny : 1) * flux_m(q.flux_kind); }
+
+npw_status check_queue(const npw_queue_instance* inst, int count, const npw_params* p, int64_t* arena_elems,
+                       int64_t* items_bound) {
+    if (!inst || count < 1) return fail(NPW_EINVAL, "null or empty instance list");
+    int64_t arena = 0, items = 0;
+    for (int i = 0; i < count; ++i) {
+        const npw_queue_instance& q = inst[i];
+        npw_status st;
+        if (q.ny == 0) {
+            if (q.flux_kind != NPW_FLUX_ADVECTION && q.flux_kind != NPW_FLUX_BURGERS && q.flux_kind != NPW_FLUX_EULER1D)
+                return fail(NPW_EINVAL, "instance %d: flux kind %d is not a 1D flux", i, q.flux_kind);
+            if (p->characteristic && q.flux_kind != NPW_FLUX_EULER1D)
+                return fail(NPW_EINVAL, "instance %d: characteristic reconstruction needs the 1D Euler flux", i);
+            if (q.nx < 6 || q.nx > ((int64_t)1 << 30)) return fail(NPW_EINVAL, "instance %d: bad n", i);
+        } else {
+            if (q.flux_kind != NPW_FLUX_ADVECTION && q.flux_kind != NPW_FLUX_BURGERS && q.flux_kind != NPW_FLUX_EULER2D)
+                return fail(NPW_EINVAL, "instance %d: flux kind %d is not a 2D flux", i, q.flux_kind);
+            if (q.nx < 6 || q.ny < 6 || q.nx * q.ny > ((int64_t)1 << 31) || !(q.dy > 0.0))
+                return fail(NPW_EINVAL, "instance %d: bad 2D size or dy", i);
+            if (q.bc_y >= 0 && (st = check_bc(q.bc_y))) return st;
+        }
+        if ((st = check_bc(q.bc))) return st;
+        if (!(q.dx > 0.0) || !(q.cfl > 0.0)) return fail(NPW_EINVAL, "instance %d: bad dx or cfl", i);
+        if (q.offset < 0) return fail(NPW_EINVAL, "instance %d: negative offset", i);
+        const int64_t end = q.offset + cells_of(q);
+        arena = end > arena ? end : arena;
+        items += items_of(q, npw::TILE_1D_MIN);
+    }
+    if (items > ((int64_t)1 << 30)) return fail(NPW_EINVAL, "too many work items");
+    *arena_elems = arena;
+    *items_bound = items;
+    return NPW_OK;
+}
+
+struct QueueRun {
+    unsigned char* ws = nullptr;
+    QLayout L{};
+    cudaStream_t s = nullptr;
+    npw::QueueArgs q{};
+    bool fp32 = false;
+    bool characteristic = false;
+    size_t smem = 0;
+    int count = 0;
+    // 1D items of each flux kind are contiguous: [begin, end) per kind, for the compensated copies
+    int64_t kind_begin[3] = {0, 0, 0}, kind_end[3] = {0, 0, 0};
+    bool comp = false;
+    std::vector<cudaEvent_t> joins;
+};
+
+npw_status queue_step(const QueueRun& r) {
+    npw::QueueArgs q = r.q;
+    for (int st = 0; st < 3; ++st) {
+        q.stage = st;
+        auto ev = stage_begin(r.s);
+        const cudaError_t e = r.fp32 ? npw::launch_queue_stage<float>(q, r.characteristic, r.smem, 0, r.s)
+                                     : npw::launch_queue_stage<double>(q, r.characteristic, r.smem, 0, r.s);
+        stage_end(ev, r.s);
+        if (e != cudaSuccess) return cuda_fail(e, "queue stage launch");
+    }
+    return NPW_OK;
+}
+
+npw_status queue_poll(const QueueRun& r, long long* act, long long* rem) {
+    long long* dpoll = reinterpret_cast<long long*>(r.ws + r.L.poll);
+    NPW_CUDA(npw::launch_queue_poll(r.q.ctl, r.q.inst1, r.q.inst2, r.q.is2d, r.count, dpoll, r.s));
+    count_launch();
+    npw_status st = bounded_sync(r.s);  // before the (blocking) copy into pageable memory
+    if (st) return st;
+    long long h[2] = {0, 0};
+    NPW_CUDA(cudaMemcpyAsync(h, dpoll, sizeof h, cudaMemcpyDeviceToHost, r.s));
+    profile_collect();
+    *act = h[0];
+    *rem = h[1];
+    return NPW_OK;
+}
+
+npw_status queue_capture(const QueueRun& r, StepGraph& g) {
+    cudaStream_t cs = nullptr;
+    NPW_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    QueueRun rc;
+    rc.ws = r.ws;
+    rc.L = r.L;
+    rc.s = cs;
+    rc.q = r.q;
+    rc.fp32 = r.fp32;
+    rc.characteristic = r.characteristic;
+    rc.smem = r.smem;
+    cudaGraph_t graph = nullptr;
+    npw_status st = NPW_OK;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        t_capturing = true;
+        for (int k = 0; k < GRAPH_STEPS && st == NPW_OK; ++k) st = queue_step(rc);
+        t_capturing = false;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e2 != cudaSuccess) e = e2;
+    }
+    if (st == NPW_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (st) return st;
+    if (e != cudaSuccess) {
+        g.exec = nullptr;
+        return cuda_fail(e, "capture of the queue step graph");
+    }
+    return NPW_OK;
+}
+
+npw_status queue_run_to_end(QueueRun& r, npw_solve_stats* out) {
+    long long act = 0, rem = 0;
+    npw_status st = queue_poll(r, &act, &rem);
+    StepGraph graph;
+    bool direct_done = false;
+    while (st == NPW_OK && act > 0) {
+        long long chunk = rem < 1 ? 1 : (rem > 256 ? 256 : rem);
+        if (chunk > GRAPH_STEPS && direct_done) {
+            if (!graph.exec && (st = queue_capture(r, graph))) break;
+            for (long long k = 0; k < chunk / GRAPH_STEPS && st == NPW_OK; ++k) {
+                auto ev = stage_begin(r.s, -1, 3 * GRAPH_STEPS);
+                const cudaError_t e = cudaGraphLaunch(graph.exec, r.s);
+                stage_end(ev, r.s);
+                if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphLaunch");
+            }
+            chunk %= GRAPH_STEPS;
+        }
+        for (long long k = 0; k < chunk && st == NPW_OK; ++k) st = queue_step(r);
+        direct_done = true;
+        if (st == NPW_OK) st = queue_poll(r, &act, &rem);
+    }
+    if (st == NPW_ETIMEOUT) graph.abandon();
+    if (st == NPW_OK && r.comp) {  // compensated 1D items: the final states are in s
+        for (int kind = 0; kind < 3 && st == NPW_OK; ++kind) {
+            const int64_t b = r.kind_begin[kind], e = r.kind_end[kind];
+            if (e <= b) continue;
+            const cudaError_t ce = npw::launch_comp_end(reinterpret_cast<float*>(r.q.u), r.q.s, r.q.inst1, r.q.items + b,
+                                                        (int)(e - b), r.q.tile, flux_m(kind), r.s);
+            if (ce != cudaSuccess) st = cuda_fail(ce, "compensated end copy");
+            count_launch();
+        }
+    }
+    for (cudaEvent_t ev : r.joins) {
+        const cudaError_t e = cudaStreamWaitEvent(r.s, ev, 0);
+        if (e != cudaSuccess && st == NPW_OK) st = cuda_fail(e, "cudaStreamWaitEvent");
+        cudaEventDestroy(ev);
+    }
+    r.joins.clear();
+    if (st) return st;
+    std::vector<npw::Ctl> hc(r.count);
+    if ((st = bounded_sync(r.s))) return st;
+    NPW_CUDA(cudaMemcpyAsync(hc.data(), r.q.ctl, sizeof(npw::Ctl) * r.count, cudaMemcpyDeviceToHost, r.s));
+    profile_collect();
+    npw_status first = NPW_OK;
+    for (int i = 0; i < r.count; ++i) {
+        if (out) fill_stats(hc[i], &out[i]);
+        if (hc[i].status != NPW_OK && first == NPW_OK) first = (npw_status)hc[i].status;
+    }
+    if (first == NPW_ENONFINITE) return fail(first, "an instance became non-finite");
+    if (first != NPW_OK) return fail(first, "an instance reached its step limit or stopped advancing");
+    return NPW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t npw_queue_workspace_size(const npw_queue_instance* inst, int32_t count, const npw_params* params) {
+    if (!params) return 0;
+    int64_t arena = 0, items = 0;
+    if (check_queue(inst, count, params, &arena, &items) != NPW_OK) return 0;
+    return queue_layout(arena, count, items, elem_size(params), compensated(params)).total;
+}
+
+npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32_t count, const npw_params* params,
+                              void* workspace, size_t workspace_bytes, npw_solve_stats* out, void* stream) {
+    npw_status st = check_params(params);
+    if (st) return st;
+    if (!arena || !workspace) return fail(NPW_EINVAL, "null pointer");
+    int64_t arena_elems = 0, items_bound = 0;
+    if ((st = check_queue(inst, count, params, &arena_elems, &items_bound))) return st;
+    QueueRun r;
+    r.count = count;
+    r.fp32 = params->precision == NPW_FP32_MIXED;
+    r.characteristic = params->characteristic != 0;
+    r.comp = compensated(params);
+    r.s = reinterpret_cast<cudaStream_t>(stream);
+    r.ws = static_cast<unsigned char*>(workspace);
+    r.L = queue_layout(arena_elems, count, items_bound, elem_size(params), r.comp);
+    if (workspace_bytes < r.L.total)
+        return fail(NPW_EINVAL, "workspace too small: %zu < %zu bytes", workspace_bytes, r.L.total);
+    // 1D tile: the autotuned (or given) tile of the 1D kind with the most cells
+    int64_t kind_cells[3] = {0, 0, 0};
+    for (int i = 0; i < count; ++i)
+        if (inst[i].ny == 0) kind_cells[inst[i].flux_kind] += cells_of(inst[i]);
+    int main_kind = 0;
+    for (int k = 1; k < 3; ++k) main_kind = kind_cells[k] > kind_cells[main_kind] ? k : main_kind;
+    const int tile = resolve_tile(params, main_kind, flux_m(main_kind));
+    // descriptors; mixed-precision 1D instances that fit in shared memory run resident
+    std::vector<npw::InstDev> h1(count);
+    std::vector<npw::Inst2D> h2(count);
+    std::vector<int32_t> hk(count);
+    std::vector<uint8_t> h2d(count);
+    std::vector<char> resident(count, 0);
+    bool has1d = false, has2d = false;
+    int m1d = 1, m2d = 1;
+    for (int i = 0; i < count; ++i) {
+        const npw_queue_instance& q = inst[i];
+        hk[i] = q.flux_kind;
+        h2d[i] = q.ny != 0;
+        if (q.ny == 0) {
+            const int m = flux_m(q.flux_kind);
+            resident[i] = resident_ok(params, m, q.nx) ? 1 : 0;
+            h1[i] = npw::InstDev{q.offset, q.nx, q.dx, q.t_end, q.cfl, q.bc,
+                                 resident[i] ? 0 : (int32_t)((q.nx + tile - 1) / tile)};
+            if (!resident[i]) {
+                has1d = true;
+                m1d = m > m1d ? m : m1d;
+            }
+        } else {
+            npw::Inst2D& d = h2[i];
+            d.off = q.offset;
+            d.nx = q.nx;
+            d.ny = q.ny;
+            d.dx = q.dx;
+            d.dy = q.dy;
+            d.t_end = q.t_end;
+            d.cfl = q.cfl;
+            d.bc = q.bc;
+            d.bc_y = q.bc_y < 0 ? q.bc : q.bc_y;
+            d.tiles_x = (int32_t)((q.nx + npw::TX_2D - 1) / npw::TX_2D);
+            d.tiles_y = (int32_t)((q.ny + npw::TY_2D - 1) / npw::TY_2D);
+            has2d = true;
+            m2d = flux_m(q.flux_kind) > m2d ? flux_m(q.flux_kind) : m2d;
+        }
+    }
+    // work items: 1D tiles grouped by flux kind, then 2D tiles
+    std::vector<npw::Tile> items;
+    for (int kind = 0; kind < 3; ++kind) {
+        r.kind_begin[kind] = (int64_t)items.size();
+        for (int i = 0; i < count; ++i) {
+            if (h2d[i] || hk[i] != kind) continue;
+            for (int32_t t = 0; t < h1[i].ntiles; ++t) items.push_back(npw::Tile{i, t * tile});
+        }
+        r.kind_end[kind] = (int64_t)items.size();
+    }
+    for (int i = 0; i < count; ++i)
+        if (h2d[i])
+            for (int32_t t = 0; t < h2[i].tiles_x * h2[i].tiles_y; ++t) items.push_back(npw::Tile{i, t});
+    unsigned char* ws = r.ws;
+    NPW_CUDA(cudaMemcpyAsync(ws + r.L.inst1, h1.data(), sizeof(npw::InstDev) * count, cudaMemcpyHostToDevice, r.s));
+    NPW_CUDA(cudaMemcpyAsync(ws + r.L.inst2, h2.data(), sizeof(npw::Inst2D) * count, cudaMemcpyHostToDevice, r.s));
+    NPW_CUDA(cudaMemcpyAsync(ws + r.L.kind, hk.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, r.s));
+    NPW_CUDA(cudaMemcpyAsync(ws + r.L.is2d, h2d.data(), (size_t)count, cudaMemcpyHostToDevice, r.s));
+    if (!items.empty())
+        NPW_CUDA(cudaMemcpyAsync(ws + r.L.items, items.data(), sizeof(npw::Tile) * items.size(), cudaMemcpyHostToDevice,
+                                 r.s));
+    NPW_CUDA(cudaMemsetAsync(ws + r.L.head, 0, 2 * sizeof(unsigned int), r.s));
+    npw::QueueArgs& q = r.q;
+    q.u = arena;
+    q.u1 = ws + r.L.u1;
+    q.u2 = ws + r.L.u2;
+    q.s = reinterpret_cast<float*>(ws + r.L.sbuf);
+    q.c = reinterpret_cast<float*>(ws + r.L.cbuf);
+    q.inst1 = reinterpret_cast<const npw::InstDev*>(ws + r.L.inst1);
+    q.inst2 = reinterpret_cast<const npw::Inst2D*>(ws + r.L.inst2);
+    q.kind = reinterpret_cast<const int32_t*>(ws + r.L.kind);
+    q.is2d = reinterpret_cast<const uint8_t*>(ws + r.L.is2d);
+    q.ctl = reinterpret_cast<npw::Ctl*>(ws + r.L.ctl);
+    q.items = reinterpret_cast<const npw::Tile*>(ws + r.L.items);
+    q.nitems = (int32_t)items.size();
+    q.advance = 1;
+    q.tile = tile;
+    q.head = reinterpret_cast<unsigned int*>(ws + r.L.head);
+    q.mp = method(params);
+    r.smem = r.fp32 ? npw::queue_smem_bytes<float>(tile, has1d, m1d, has2d, m2d, r.characteristic)
+                    : npw::queue_smem_bytes<double>(tile, has1d, m1d, has2d, m2d, r.characteristic);
+    // start: reset, alpha^0 over the items, first dt
+    NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, count, 0, 0, r.s));
+    cudaError_t e = r.fp32 ? npw::launch_queue_alpha<float>(q, r.s) : npw::launch_queue_alpha<double>(q, r.s);
+    if (e != cudaSuccess) return cuda_fail(e, "queue alpha launch");
+    NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, count, 1, q.mp.max_steps, r.s));
+    count_launch(3);
+    if (r.comp) {  // compensated 1D items: s = u, c = 0
+        for (int kind = 0; kind < 3; ++kind) {
+            const int64_t b = r.kind_begin[kind], en = r.kind_end[kind];
+            if (en <= b) continue;
+            NPW_CUDA(npw::launch_comp_begin(reinterpret_cast<const float*>(arena), q.s, q.c, q.inst1, q.items + b,
+                                            (int)(en - b), tile, flux_m(kind), r.s));
+            count_launch();
+        }
+    }
+    // resident 1D instances, one launch set per flux kind, on the side streams
+    bool any_res = false;
+    for (int i = 0; i < count; ++i) any_res |= resident[i] != 0;
+    if (any_res) {
+        SideStreams* ss = nullptr;
+        if ((st = side_streams(&ss))) return st;
+        std::vector<int64_t> n_of(count, 0);
+        std::vector<double> cost(count, 0.0);
+        for (int i = 0; i < count; ++i) {
+            n_of[i] = inst[i].nx;
+            cost[i] = (double)inst[i].nx * inst[i].t_end / (inst[i].cfl * inst[i].dx);
+        }
+        int64_t list_off = 0;  // the kinds' index lists occupy disjoint parts of the list buffer
+        for (int kind = 0; kind < 3; ++kind) {
+            std::vector<int32_t> ids;
+            for (int i = 0; i < count; ++i)
+                if (resident[i] && hk[i] == kind) ids.push_back(i);
+            if (ids.empty()) continue;
+            ResidentLaunch rl{arena, q.c, q.inst1, q.ctl, reinterpret_cast<int32_t*>(ws + r.L.list) + list_off,
+                              flux_m(kind), kind, q.mp};
+            if ((st = launch_resident_set(rl, ids, n_of, cost, ss, r.s, r.joins))) return st;
+            list_off += (int64_t)ids.size();
+        }
+    }
+    return queue_run_to_end(r, out);
 }
 
 }  // extern "C"

@@ -402,16 +402,18 @@ __device__ __forceinline__ uint32_t face_field(const R* w, const MethodParams& m
 }
 
 // ---------------------------------------------------------------------------------------
-// Near ties of the decisions at one face (the FL_NEAR_TIE bit of npweno_reconstruct): a
-// quantity that decides the switch, the ENO choice, the guard or the bound lies within tol
-// (relative) of its threshold, so that two correct evaluations in different rounding orders
-// may decide differently.  Margins (all in double, from the cell averages):
-//   ENO (Sec. 2): ||d_L| - |d_R|| <= tol max(|d_L|, |d_R|) for the first and both second
-//     divided-difference comparisons;
+// Near ties of the threshold decisions at one face (the FL_NEAR_TIE bit of npweno_reconstruct):
+// a quantity that decides the monotone switch, the guard or the bound lies within tol
+// (relative) of its threshold, so that two correct evaluations in different forms (the
+// switch's closed form here, an elimination elsewhere; the guard in float or in double) may
+// decide differently.  The ENO choice is not among them: it compares two differences of the
+// same cell averages, which every correct evaluation rounds alike, so it is expected to agree
+// everywhere.  Margins (all in double, from the cell averages):
 //   switch variant 0 (Sec. 4, the cubic on the eta stencil): 12 p' at either end or at an
 //     inside vertex within 8 tol (|w0| + .. + |w3|) of 0 (times 12), or the vertex within
 //     8 tol of an end of the stencil;  the ratio test (variant 1, k = 2): its denominator
-//     within tol (|a| + |b| + |c|) of 0, or the ratio within 4 tol of 0 or 3;
+//     within tol (|a| + |b| + |c|) of 0, or the ratio within 4 tol of 0 or 3;  a stencil of
+//     equal averages is constant, hence monotone, and not a tie;
 //   guard: |den| within tol of the guard threshold; bound: |eta| within tol of eta_max.
 // w[0..5] = cells i-2..i+3 of face i+1/2.
 // ---------------------------------------------------------------------------------------
@@ -427,11 +429,6 @@ __device__ __forceinline__ bool k2_ratio_near(double a, double b, double c, doub
     if (den == 0.0) return false;
     const double r = num / den;
     return fabs(r) <= 4.0 * tol || fabs(r - 3.0) <= 4.0 * tol;
-}
-__device__ __forceinline__ bool eno_near(const double* c, double tol) {
-    const double dl = fabs(c[2] - c[1]), dr = fabs(c[3] - c[2]);
-    return tie_rel(dl, dr, tol) || tie_rel(fabs(c[0] - 2.0 * c[1] + c[2]), fabs(c[1] - 2.0 * c[2] + c[3]), tol) ||
-           tie_rel(fabs(c[1] - 2.0 * c[2] + c[3]), fabs(c[2] - 2.0 * c[3] + c[4]), tol);
 }
 __device__ __forceinline__ bool switch_v0_near(const double* w, double tol) {
     if (w[0] == w[1] && w[1] == w[2] && w[2] == w[3]) return false;  // constant stencil
@@ -453,11 +450,9 @@ __device__ __forceinline__ bool face_near_tie(const R* wr, const MethodParams& m
 #pragma unroll
     for (int j = 0; j < 6; ++j) w[j] = (double)wr[j];
     const bool rbf = mp.scheme == NPW_RBF_ENO_ || mp.scheme == NPW_RBF_WENO_;
-    const bool eno = mp.scheme == NPW_ENO_ || mp.scheme == NPW_RBF_ENO_;
     bool near = false;
     if (mp.k == 2) {
-        if (eno) near = tie_rel(fabs(w[2] - w[1]), fabs(w[3] - w[2]), tol) || tie_rel(fabs(w[3] - w[2]), fabs(w[4] - w[3]), tol);
-        if (rbf && mp.monotone_switch) near = near || k2_ratio_near(w[1], w[2], w[3], tol) || k2_ratio_near(w[2], w[3], w[4], tol);
+        if (rbf && mp.monotone_switch) near = k2_ratio_near(w[1], w[2], w[3], tol) || k2_ratio_near(w[2], w[3], w[4], tol);
         if (rbf) {
             for (int side = 0; side < 2; ++side) {
                 const double* c = w + 1 + side;  // cell i (side 0, v^-) or i + 1 (side 1, v^+)
@@ -472,7 +467,6 @@ __device__ __forceinline__ bool face_near_tie(const R* wr, const MethodParams& m
         }
         return near;
     }
-    if (eno) near = eno_near(w, tol) || eno_near(w + 1, tol);
     if (rbf && mp.monotone_switch)
         near = near || (mp.switch_variant == 1 ? (k2_ratio_near(w[1], w[2], w[3], tol) || k2_ratio_near(w[2], w[3], w[4], tol))
                                                : switch_v0_near(w + 1, tol));

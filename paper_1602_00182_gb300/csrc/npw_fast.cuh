@@ -287,10 +287,17 @@ __device__ __forceinline__ float eta_quot(float w0, float w1, float w2, float w3
     const double a = widen_as<NZ>(w0) - widen_as<NZ>(w3);
     const double b = widen_as<NZ>(w2) - widen_as<NZ>(w1);
     const double den0 = fma(15.0, b, a);
-    if (guard > 0.0f) {
-        const double g = widen_nz(guard);
+    if (fp.eta_guard > 0.0f) {
+        // below 2^-100 the float threshold may have lost precision (subnormal products): exact path
         const double d0 = fabs(den0);
-        if (d0 <= g * (1.0 + 0x1p-20) && (d0 < g * (1.0 - 0x1p-20) || guard_exact(w0, w1, w2, w3, fp.eta_guard_d))) {
+        bool zero;
+        if (guard >= 0x1p-100f) {
+            const double g = widen_nz(guard);
+            zero = d0 <= g * (1.0 + 0x1p-20) && (d0 < g * (1.0 - 0x1p-20) || guard_exact(w0, w1, w2, w3, fp.eta_guard_d));
+        } else {
+            zero = guard_exact(w0, w1, w2, w3, fp.eta_guard_d);
+        }
+        if (zero) {
             *fl |= FL_ZERO_GUARD;
             return 0.0f;
         }
@@ -320,13 +327,21 @@ __device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3
 // quotient).  Its numerator and denominator are within ~2^-47 of the magnitudes of their terms
 // (|a| + 3|b|, |a| + 15|b|), against 2^-53 for the FP64 evaluation: where they cancel strongly
 // the quotient is correspondingly less accurate than eta_eval 0.
-__device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, float w3, float eps_M, float guard,
-                                                 uint32_t* fl) {
+__device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, float w3, const FParams& fp,
+                                                 float guard, uint32_t* fl) {
+    const float eps_M = fp.eps_M_f;
     float nh, nl, dh, dl;
     eta_pairs(w0, w1, w2, w3, nh, nl, dh, dl);
-    if (guard > 0.0f && fabsf(dh + dl) <= guard) {
-        *fl |= FL_ZERO_GUARD;
-        return 0.0f;
+    if (fp.eta_guard > 0.0f) {  // certified as in eta_quot: exact where the float test is too close
+        const float d0 = fabsf(dh + dl);
+        const bool zero = guard >= 0x1p-100f && d0 <= guard * (1.0f - 0x1p-19f)
+                              ? true
+                              : ((guard < 0x1p-100f || d0 <= guard * (1.0f + 0x1p-19f)) &&
+                                 guard_exact(w0, w1, w2, w3, fp.eta_guard_d));
+        if (zero) {
+            *fl |= FL_ZERO_GUARD;
+            return 0.0f;
+        }
     }
     float t;
     two_sum(dh, eps_M, dh, t);
@@ -352,7 +367,7 @@ __device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, f
 // quotient would be noise amplified by 1/eps_M.
 __device__ __forceinline__ float eta_eval(float w0, float w1, float w2, float w3, const FParams& fp, uint32_t* fl) {
     const float guard = fp.eta_guard * (fabsf(w0) + 15.f * fabsf(w1) + 15.f * fabsf(w2) + fabsf(w3));
-    return fp.eta_eval == 1 ? eta_doublefloat(w0, w1, w2, w3, fp.eps_M_f, guard, fl)
+    return fp.eta_eval == 1 ? eta_doublefloat(w0, w1, w2, w3, fp, guard, fl)
                             : eta_fp64(w0, w1, w2, w3, fp, guard, fl);
 }
 
@@ -539,7 +554,7 @@ __device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double tr
         const float magf = (fabsf(af) + 5.0f * fabsf(bf)) + 2.0f * fabsf(df);
         const float den0f = fmaf(2.0f, df, fmaf(5.0f, bf, -af));
         const float gm = fp.eta_guard * magf;
-        if (!(fabsf(den0f) > gm + kE * magf * (1.0f + fp.eta_guard))) {
+        if (!(magf >= 0x1p-90f && fabsf(den0f) > gm + kE * magf * (1.0f + fp.eta_guard))) {
             const double a = widen(af), b = widen(bf), d = widen(df);
             if (fabs((-a + 5.0 * b) + 2.0 * d) <= mp.eta_guard * ((fabs(a) + 5.0 * fabs(b)) + 2.0 * fabs(d))) {
                 *fl |= FL_ZERO_GUARD;

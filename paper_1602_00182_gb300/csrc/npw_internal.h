@@ -198,6 +198,31 @@ struct Stage2DArgs {
     MethodParams mp;
 };
 
+// Persistent work-queue stage kernel: the CTAs of one launch pull work items (instance, tile)
+// from a device counter until the list is exhausted; 1D items are tiles of `tile` cells (start
+// cell in Tile.start), 2D items tiles of TX_2D x TY_2D cells (tile index in Tile.start).  Every
+// instance has its own descriptor, control word and step; items of finished instances return
+// at once.  The last CTA to leave resets the counter for the next launch.
+struct QueueArgs {
+    void* u;                 // state of all instances (arena, element type of the run)
+    void* u1;                // stage buffers (arena-shaped); the compensated 1D float items
+    void* u2;                //   keep their increments d1, d2 there
+    float* s;                // compensated 1D float items: next state and carry (arena-shaped)
+    float* c;
+    const InstDev* inst1;    // [count] 1D descriptor (used when !is2d)
+    const Inst2D* inst2;     // [count] 2D descriptor (used when is2d)
+    const int32_t* kind;     // [count] flux kind
+    const uint8_t* is2d;     // [count]
+    Ctl* ctl;                // [count]
+    const Tile* items;
+    int32_t nitems;
+    int32_t stage;
+    int32_t advance;
+    int32_t tile;            // cells per 1D item
+    unsigned int* head;      // [2]: next item, CTAs finished
+    MethodParams mp;
+};
+
 // ---- launchers (one definition per precision translation unit) ---------------------------
 template <typename R>
 cudaError_t launch_reconstruct(const R* u, int64_t n, int m, int bc, const MethodParams& mp, R* vm, R* vp,
@@ -215,6 +240,14 @@ cudaError_t launch_alpha_init_2d(const void* u, const Inst2D* inst, int tiles, C
                                  const MethodParams& mp, cudaStream_t s);
 template <typename R>
 cudaError_t launch_stage2d(const Stage2DArgs& a, int tiles, int kind, cudaStream_t s);
+// queue kernels: smem_bytes for the instance kinds present (see queue_smem_bytes); blocks = 0
+// asks for one wave of resident CTAs (occupancy x SMs)
+template <typename R>
+cudaError_t launch_queue_stage(const QueueArgs& q, bool characteristic, size_t smem_bytes, int blocks, cudaStream_t s);
+template <typename R>
+cudaError_t launch_queue_alpha(const QueueArgs& q, cudaStream_t s);
+template <typename R>
+size_t queue_smem_bytes(int tile, bool has1d, int m1d, bool has2d, int m2d, bool characteristic);
 // resident whole-solve launch (float state only); max_n = largest n in the list
 cudaError_t launch_resident_f32(const ResidentArgs& a, int m, int kind, int64_t max_n, int threads, cudaStream_t s);
 size_t resident_smem_bytes(int64_t n, int m);
@@ -223,9 +256,10 @@ size_t resident_smem_bytes(int64_t n, int m);
 npw_status set_error(npw_status st, const char* msg);
 
 // precision-independent helpers (npw_api.cu)
-cudaError_t launch_ctl_start(Ctl* ctl, const InstDev* inst, int count, int mode, double dt, cudaStream_t s);
-cudaError_t launch_ctl_start_2d(Ctl* ctl, const Inst2D* inst, int mode, double dt, cudaStream_t s);
-cudaError_t launch_count_active(const Ctl* ctl, int count, int* active, cudaStream_t s);
+cudaError_t launch_queue_ctl(Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d, int count,
+                             int mode, int64_t max_steps, cudaStream_t s);
+cudaError_t launch_queue_poll(const Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d,
+                              int count, long long* poll, cudaStream_t s);
 // compensated float path: before the first step s = u and c = 0; after the last, u = s
 cudaError_t launch_comp_begin(const float* u, float* s, float* c, const InstDev* inst, const Tile* tiles, int ntiles,
                               int tile, int m, cudaStream_t st);

@@ -1342,6 +1342,165 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Persistent work-queue kernel (QueueArgs): one launch per stage for every instance of a batch,
+// 1D and 2D together.  Each CTA takes the next item from q.head[0] until the list is exhausted
+// and runs the per-item body of the instance's kind: for the float state the compensated 1D
+// body (or the face-based characteristic body) and the phased 2D body, for the double state the
+// face-based bodies.  The bodies are those of the one-CTA-per-item kernels, so the results are
+// the same bits.  The last CTA to finish resets the counters for the next launch (the next
+// launch is ordered after this one on the stream).
+// ---------------------------------------------------------------------------------------
+template <typename R, int K, bool CHAR, int KIND>
+__device__ __forceinline__ void queue_item_1d(const Stage1DArgs& a1, const Tile w, const InstDev& in, Ctl* ctl,
+                                              unsigned char* smem) {
+    if constexpr (sizeof(R) == sizeof(float) && !CHAR)
+        stage1d_fast_body<KIND, K>(a1, w, in, ctl, smem);
+    else
+        stage1d_body<R, double, KIND, CHAR && KIND == NPW_FLUX_EULER1D_>(a1, w, in, ctl, smem);
+}
+template <typename R, int K, int KIND>
+__device__ __forceinline__ void queue_item_2d(const Stage2DArgs& a2, const Inst2D& in, Ctl* ctl, int tile,
+                                              unsigned char* smem) {
+    if constexpr (sizeof(R) == sizeof(float))
+        stage2d_fast_body<KIND, K>(a2, in, ctl, tile, reinterpret_cast<float*>(smem));
+    else
+        stage2d_body<R, double, KIND>(a2, in, ctl, tile, smem);
+}
+
+template <typename R, int K, bool CHAR>
+__global__ void __launch_bounds__(THREADS_1D) queue_stage_kernel(QueueArgs q) {
+    static_assert(THREADS_1D == TX_2D * TY_2D, "1D and 2D items share the CTA shape");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    const void* in_[3] = {q.u, q.u1, q.u2};
+    void* out_[3] = {q.u1, q.u2, q.u};
+    Stage1DArgs a1{};
+    a1.uin = in_[q.stage];
+    a1.un = q.u;
+    a1.uout = out_[q.stage];
+    a1.u = reinterpret_cast<float*>(q.u);
+    a1.d1 = reinterpret_cast<float*>(q.u1);
+    a1.d2 = reinterpret_cast<float*>(q.u2);
+    a1.s = q.s;
+    a1.c = q.c;
+    a1.stage = q.stage;
+    a1.advance = q.advance;
+    a1.tile = q.tile;
+    a1.mp = q.mp;
+    Stage2DArgs a2{};
+    a2.uin = in_[q.stage];
+    a2.un = q.u;
+    a2.uout = out_[q.stage];
+    a2.stage = q.stage;
+    a2.advance = q.advance;
+    a2.mp = q.mp;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(&q.head[0], 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= q.nitems) break;  // uniform over the CTA
+        const Tile w = q.items[it];
+        Ctl* ctl = q.ctl + w.inst;
+        const int kind = q.kind[w.inst];
+        if (q.is2d[w.inst]) {
+            const Inst2D& in = q.inst2[w.inst];
+            if (kind == NPW_FLUX_EULER2D_)
+                queue_item_2d<R, K, NPW_FLUX_EULER2D_>(a2, in, ctl, w.start, smem_raw);
+            else if (kind == NPW_FLUX_BURGERS_)
+                queue_item_2d<R, K, NPW_FLUX_BURGERS_>(a2, in, ctl, w.start, smem_raw);
+            else
+                queue_item_2d<R, K, NPW_FLUX_ADVECTION_>(a2, in, ctl, w.start, smem_raw);
+        } else {
+            const InstDev& in = q.inst1[w.inst];
+            if (kind == NPW_FLUX_EULER1D_)
+                queue_item_1d<R, K, CHAR, NPW_FLUX_EULER1D_>(a1, w, in, ctl, smem_raw);
+            else if (kind == NPW_FLUX_BURGERS_)
+                queue_item_1d<R, K, CHAR, NPW_FLUX_BURGERS_>(a1, w, in, ctl, smem_raw);
+            else
+                queue_item_1d<R, K, CHAR, NPW_FLUX_ADVECTION_>(a1, w, in, ctl, smem_raw);
+        }
+        __syncthreads();  // shared memory and s_item are reused by the next item
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&q.head[1], 1u) == gridDim.x - 1u) {  // every CTA has left the loop
+            q.head[0] = 0u;
+            q.head[1] = 0u;
+        }
+    }
+}
+
+// alpha^0 of every instance of a queue batch: one CTA per item, the wave speeds of its cells
+// (2D: both directions) into the instance's running maxima
+template <typename R, int KIND>
+__device__ __forceinline__ void queue_speed_cell(const R* base, int64_t stride, int64_t i, const MethodParams& mp,
+                                                 bool two_d, double* sx, double* sy, bool* bad) {
+    constexpr int M = kind_m<KIND>();
+    R U[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        U[k] = base[k * stride + i];
+        *bad |= !finite_(U[k]);
+    }
+    const double x = (double)wave_speed<R, KIND>(U, mp, 0);
+    const double y = two_d ? (double)wave_speed<R, KIND>(U, mp, 1) : 0.0;
+    *bad |= !finite_(x) || !finite_(y);
+    *sx = x > *sx ? x : *sx;
+    *sy = y > *sy ? y : *sy;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(THREADS_1D) queue_alpha_kernel(QueueArgs q) {
+    __shared__ double red[32];
+    __shared__ int redbad[32];
+    __shared__ double red2[32];
+    __shared__ int redbad2[32];
+    const Tile w = q.items[blockIdx.x];
+    const bool two_d = q.is2d[w.inst] != 0;
+    const int kind = q.kind[w.inst];
+    const R* u = reinterpret_cast<const R*>(q.u);
+    double sx = 0.0, sy = 0.0;
+    bool bad = false;
+    if (two_d) {
+        const Inst2D in = q.inst2[w.inst];
+        const int64_t cells = in.nx * in.ny;
+        const int tx0 = (w.start % in.tiles_x) * TX_2D, ty0 = (w.start / in.tiles_x) * TY_2D;
+        const int qy = threadIdx.x / TX_2D, qx = threadIdx.x - qy * TX_2D;
+        const int64_t gi = tx0 + qx, gj = ty0 + qy;
+        if (gi < in.nx && gj < in.ny) {
+            const R* base = u + in.off;
+            const int64_t i = gj * in.nx + gi;
+            if (kind == NPW_FLUX_EULER2D_)
+                queue_speed_cell<R, NPW_FLUX_EULER2D_>(base, cells, i, q.mp, true, &sx, &sy, &bad);
+            else if (kind == NPW_FLUX_BURGERS_)
+                queue_speed_cell<R, NPW_FLUX_BURGERS_>(base, cells, i, q.mp, true, &sx, &sy, &bad);
+            else
+                queue_speed_cell<R, NPW_FLUX_ADVECTION_>(base, cells, i, q.mp, true, &sx, &sy, &bad);
+        }
+    } else {
+        const InstDev in = q.inst1[w.inst];
+        const int cnt = (int)((in.n - w.start) < q.tile ? (in.n - w.start) : q.tile);
+        const R* base = u + in.off;
+        for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
+            const int64_t i = w.start + c;
+            if (kind == NPW_FLUX_EULER1D_)
+                queue_speed_cell<R, NPW_FLUX_EULER1D_>(base, in.n, i, q.mp, false, &sx, &sy, &bad);
+            else if (kind == NPW_FLUX_BURGERS_)
+                queue_speed_cell<R, NPW_FLUX_BURGERS_>(base, in.n, i, q.mp, false, &sx, &sy, &bad);
+            else
+                queue_speed_cell<R, NPW_FLUX_ADVECTION_>(base, in.n, i, q.mp, false, &sx, &sy, &bad);
+        }
+    }
+    const double bx = block_max_nan(sx, bad, red, redbad);
+    const double by = block_max_nan(sy, bad, red2, redbad2);
+    if (threadIdx.x == 0) {
+        Ctl* ctl = q.ctl + w.inst;
+        atomicMax(&ctl->alpha_next_bits, (unsigned long long)__double_as_longlong(bx));
+        if (two_d) atomicMax(&ctl->alpha_y_next_bits, (unsigned long long)__double_as_longlong(by));
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------
 // smooth data for the tile autotuner: m = 1: 1 + 0.5 sin(16 pi x); m = 3: a quiet Euler state

@@ -127,9 +127,12 @@ def load():
     lib.npw_autotune_scratch_bytes.restype = sz
     lib.npw_autotune_1d.argtypes = [i32, i32, P(npw_params), vp, sz, vp, P(i32)]
     lib.npw_format_check.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.npw_queue_workspace_size.argtypes = [P(npw_queue_instance), i32, P(npw_params)]
+    lib.npw_queue_workspace_size.restype = sz
+    lib.npweno_queue_solve.argtypes = [vp, P(npw_queue_instance), i32, P(npw_params), vp, sz, P(npw_solve_stats), vp]
     for f in ("npweno_reconstruct", "npweno_flux", "npweno_rk3_step", "npweno_solve", "npweno_batch_solve",
               "npweno_rk3_step_2d", "npweno_solve_2d", "npweno_rk3_step_noalloc", "npw_autotune_1d",
-              "npw_format_check"):
+              "npw_format_check", "npweno_queue_solve"):
         getattr(lib, f).restype = i32
     _lib = lib
     return lib
@@ -339,6 +342,60 @@ def npweno_batch_solve(arena, instances, m: int, flux_kind: int, params: Params,
     st = load().npweno_batch_solve(_dev(arena, params, "arena"), instances, count, m, flux_kind, C.byref(p),
                                    C.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size(), out, _stream())
     if raise_on_error and st not in (NPW_OK, NPW_ENONFINITE):
+        _check(st)
+    return st, [_stats(out[i]) for i in range(count)]
+
+
+class npw_queue_instance(C.Structure):
+    _fields_ = [("offset", C.c_int64), ("nx", C.c_int64), ("ny", C.c_int64), ("dx", C.c_double), ("dy", C.c_double),
+                ("t_end", C.c_double), ("cfl", C.c_double), ("flux_kind", C.c_int32), ("bc", C.c_int32),
+                ("bc_y", C.c_int32), ("pad_", C.c_int32)]
+
+
+_KIND_M = {NPW_FLUX_ADVECTION: 1, NPW_FLUX_BURGERS: 1, NPW_FLUX_EULER1D: 3, NPW_FLUX_EULER2D: 4}
+
+
+def make_queue_instances(specs):
+    """Descriptor table of a work-queue batch packed into one arena.  specs: dicts with keys
+    kind, nx, (ny, dy for 2D), dx, t_end, cfl, bc, (bc_y); instance i occupies
+    [off_i, off_i + m * nx * max(ny, 1)).  Returns (table, total elements, offsets)."""
+    arr = (npw_queue_instance * len(specs))()
+    off, offs = 0, []
+    for i, sp in enumerate(specs):
+        ny = int(sp.get("ny", 0))
+        arr[i].offset = off
+        arr[i].nx = int(sp["nx"])
+        arr[i].ny = ny
+        arr[i].dx = float(sp["dx"])
+        arr[i].dy = float(sp.get("dy", 0.0))
+        arr[i].t_end = float(sp["t_end"])
+        arr[i].cfl = float(sp["cfl"])
+        arr[i].flux_kind = int(sp["kind"])
+        arr[i].bc = int(sp.get("bc", NPW_BC_PERIODIC))
+        arr[i].bc_y = int(sp.get("bc_y", -1))
+        offs.append(off)
+        off += _KIND_M[int(sp["kind"])] * int(sp["nx"]) * max(ny, 1)
+    return arr, off, offs
+
+
+def npw_queue_workspace_size(instances, params: Params) -> int:
+    p = params.c()
+    return int(load().npw_queue_workspace_size(instances, len(instances), C.byref(p)))
+
+
+def npweno_queue_solve(arena, instances, params: Params, workspace=None, raise_on_error: bool = True):
+    """Advance every instance (1D and 2D) of the packed arena through the work-queue kernel;
+    returns (status, list of per-instance stats)."""
+    count = len(instances)
+    nbytes = npw_queue_workspace_size(instances, params)
+    if nbytes == 0:
+        raise NpwError(NPW_EINVAL, "npw_queue_workspace_size: bad instances or params")
+    ws = _workspace(nbytes, arena.device, workspace)
+    p = params.c()
+    out = (npw_solve_stats * count)()
+    st = load().npweno_queue_solve(_dev(arena, params, "arena"), instances, count, C.byref(p),
+                                   C.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size(), out, _stream())
+    if raise_on_error and st not in (NPW_OK, NPW_ENONFINITE, NPW_ETIMEOUT):
         _check(st)
     return st, [_stats(out[i]) for i in range(count)]
 

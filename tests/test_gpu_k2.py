@@ -74,7 +74,7 @@ def test_k2_reconstruct_fp64(npw, scheme, rbf, switch, bc):
 
 @pytest.mark.parametrize("eta_max,eta_guard", [(0.05, 0.0), (0.0, 1e-3)])
 def test_k2_reconstruct_guard_and_bound(npw, eta_max, eta_guard):
-    op = O.Params(k=2, eta_max=eta_max, eta_guard=eta_guard)
+    op = O.Params(k=2, eta_max=eta_max, eta_guard=eta_guard, monotone_switch=0)
     g = np.random.default_rng(3)
     x = (np.arange(2000) + 0.5) / 2000
     u = 1.0 + 0.4 * np.sin(2 * np.pi * 3 * x + g.uniform(0, 6)) + 0.5 * (x > 1 / np.sqrt(3))

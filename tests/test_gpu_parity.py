@@ -40,7 +40,8 @@ def _dev(x, dtype=torch.float64):
 
 
 def _gparams(npw, o: "O.Params", precision=0):
-    return npw.Params(scheme=o.scheme, rbf=o.rbf, monotone_switch=o.monotone_switch, switch_variant=o.switch_variant,
+    return npw.Params(k=o.k, cross_2d=o.cross_2d, scheme=o.scheme, rbf=o.rbf, monotone_switch=o.monotone_switch,
+                      switch_variant=o.switch_variant,
                       characteristic=o.characteristic, precision=precision, eps_M=o.eps_M, eps_weno=o.eps_weno,
                       gamma=o.gamma, adv_speed=o.adv_speed, adv_speed_y=o.adv_speed_y, inflow=o.inflow,
                       eta_guard=o.eta_guard if o.eta_guard > 0 else 0.0, eta_max=o.eta_max if o.eta_max > 0 else -1.0)
@@ -100,8 +101,9 @@ def test_reconstruct_fp64(npw, scheme, rbf, switch, variant, bc):
 @pytest.mark.parametrize("eta_max,eta_guard", [(0.05, 0.0), (0.0, 1e-3), (0.02, 1e-3)])
 def test_reconstruct_fp64_guard_and_bound(npw, eta_max, eta_guard):
     """The optional guard and bound (not in the paper) zero the same faces on both sides, and the
-    GPU flags them (bits 6 / 7)."""
-    op = O.Params(eta_max=eta_max, eta_guard=eta_guard)
+    GPU flags them (bits 6 / 7).  Switch off, so that the extrema of the data give large
+    shape parameters and small denominators."""
+    op = O.Params(eta_max=eta_max, eta_guard=eta_guard, monotone_switch=0)
     u = _generic_data(3001, 5)
     gvm, gvp, gfl, geta = npw.npweno_reconstruct(_dev(u), O.PERIODIC, _gparams(npw, op), with_eta=True)
     gfl = gfl.cpu().numpy()
@@ -495,7 +497,9 @@ def test_2d_mixed_step_matches_oracle(npw, switch, kind):
     direction): one RK3 step against the oracle from the same float data on a ragged grid (tiles
     cut at both edges).  Without the switch the bar is float rounding (2e-6 relative); with it,
     decisions of stages 2 and 3 taken on float stage values may differ at near ties (mean 1e-6,
-    max 3e-5 relative)."""
+    max 3e-5 relative).  Both sides bound |eta| by 1: without the switch the printed eta is
+    unbounded at the extrema of the data (num / eps_M where the denominator vanishes), and a
+    float candidate with a coefficient of 1e6 is not within float rounding of the FP64 one."""
     nx, ny = 70, 45
     if kind == O.EULER2D:
         nx = ny = 70  # the whole periodic vortex (a cropped one would have a jump at the wrap)
@@ -508,7 +512,7 @@ def test_2d_mixed_step_matches_oracle(npw, switch, kind):
         U[0, ny // 3:, nx // 2:] += 0.3 * g.uniform()
         d = 1.0 / nx
     U = U.astype(np.float32).astype(np.float64)
-    op = O.Params(monotone_switch=switch, eta_guard=MIXED_GUARD, adv_speed=1.0, adv_speed_y=0.5)
+    op = O.Params(monotone_switch=switch, eta_guard=MIXED_GUARD, adv_speed=1.0, adv_speed_y=0.5, eta_max=1.0)
     dt = 0.2 * d
     ref = O.rk3_step_2d(U, d, d, dt, kind, O.PERIODIC, op)
     gu = _dev(U, torch.float32)
