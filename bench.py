@@ -1,19 +1,29 @@
 #!/usr/bin/env python3
-"""Benchmark: batched 1D Burgers with the non-polynomial RBF-WENO5 method on one GB300 per rank.
+"""Benchmark of the non-polynomial RBF-ENO/WENO finite-volume hot path on one GB300 per rank.
 
-Workload (one "step" = one whole solve of the batch): 4096 periodic Burgers instances on
+Headline (one "step" = one whole solve of the batch): 4096 periodic Burgers instances on
 [0, 2 pi], N log-uniform in [64, 8192] (seeded), u0 = 1 + four Fourier modes + up to two
-jumps, Gaussian perturbation with the monotone switch, Lax-Friedrichs flux, TVD-RK3 at
-CFL 0.5, run past shock formation to T = 1.5.  Float state, candidates, weights and flux;
-the shape parameter eta in double; switch and ENO decisions certified equal to their double
-evaluation.  Each instance keeps its own dt; every instance fits in shared memory, so the
-batch runs in the resident whole-solve kernel (four size classes on side streams).
+jumps, Gaussian perturbation with the monotone switch, Lax-Friedrichs flux, TVD-RK3 at CFL 0.5,
+run past shock formation to T = 1.5.  Float state, candidates, weights and flux; the shape
+parameter in FP64; switch and ENO decisions certified equal to their FP64 evaluation.  Each
+instance keeps its own dt; every instance fits in shared memory, so the batch runs in the
+resident whole-solve kernel (four size classes on side streams).
 
-`--workload euler1d` (512 transmissive Euler instances, per-stage kernels) and
-`--workload euler2d` (2D Euler on 2048^2 squares) print their own lines.
+The same JSON line carries one block per other workload (rank 0, N = 1):
+  advection_fp64_n200    linear advection of sin(pi x), FP64, N = 200, CFL 0.5, T = 2, with the
+                         convergence sweep N = 25..400 and the solve latency;
+  euler1d_component      512 transmissive 1D Euler instances, N log-uniform in [256, 65536],
+                         Riemann and Shu-Osher-type data, to their end times (work-queue kernel);
+  euler1d_characteristic the same batch characteristic-wise (to a fraction of the end times);
+  euler2d                periodic 2D Euler squares 256^2 .. 2048^2 (2^24 cells per size),
+                         vortex and four-quadrant data, 100 RK3 steps (work-queue kernel);
+  serving                a Poisson request stream served with continuous batching.
+Each block has its roofline on the algorithmic HBM bytes of a cell-update, and the FP64
+oracle timed on the host cores on a bounded sample, whose results also give the block's L1 /
+L_inf difference from the oracle.
 
-Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead, on
-a bounded sample of the same workload.
+`--impl reference` times the FP64 CPU oracle instead, on a bounded sample of the headline
+workload.
 """
 from __future__ import annotations
 
@@ -24,6 +34,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -40,6 +51,22 @@ T_END = 1.5
 CFL = 0.5
 SAMPLE_STRIDE = 64     # cpu sample: every 64th instance of the N-sorted batch
 SAMPLE_STEPS = 20      # RK3 steps per sampled instance
+FLUSH_BYTES = 256 * 1024 * 1024  # > L2 (129 MB)
+MIXED_GUARD = 8.0 * 2.0 ** -24  # the mixed path's automatic round-off guard, given to the oracle
+
+# Algorithmic HBM bytes of one cell-update (one cell, all fields, one full RK3 step) of the
+# per-stage fused design: stage 1 reads u^n and writes u1, stages 2 and 3 read the stage input
+# and u^n and write: 8 + 12 + 12 = 32 B per float field, 64 B per double field.
+BYTES_SCALAR_F32 = 32
+BYTES_EULER1D_F32 = 96
+BYTES_EULER2D_F32 = 128
+BYTES_SCALAR_F64 = 64
+# FP64-pipe instructions of one shape-parameter evaluation in the mixed path (k = 3): 2 adds
+# (the differences a, b), 2 multiply-adds (numerator, denominator), 1 add (eps_M), 1 multiply
+# and 2 multiply-adds (the Newton quotient)
+FP64_OPS_PER_ETA = 8
+# FP64 pipe: 2 instructions per clock per SM (1.25 TFLOP/s nominal FP64 over 152 SMs at 2.07 GHz)
+FP64_PIPE_PEAK = 2.0 * 152 * 2.07e9
 
 
 def _peaks():
@@ -51,33 +78,16 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# ------------------------------------------------------------------------------- CPU oracle leg
-def _oracle_job(args):
-    u0, dx, steps = args
-    import oracle as O
-    t0 = time.perf_counter()
-    O.solve(u0, dx, T_END, CFL, O.BURGERS, O.PERIODIC, O.Params(rbf=O.GA), max_steps=steps)
-    return time.perf_counter() - t0
-
-
-def cpu_sample(inst, cores: int):
-    """The FP64 oracle on a bounded sample: every SAMPLE_STRIDE-th instance (sorted by N), the
-    first SAMPLE_STEPS RK3 steps each, spread over `cores` spawned processes."""
-    import multiprocessing as mp
-    import oracle as O
-    O.build()
-    order = sorted(range(len(inst)), key=lambda i: inst[i].n)
-    pick = order[SAMPLE_STRIDE // 2::SAMPLE_STRIDE]
-    jobs = [(inst[i].u0[0].astype(np.float64), inst[i].dx, SAMPLE_STEPS) for i in pick]
-    cells = sum(inst[i].n for i in pick) * SAMPLE_STEPS
-    ctx = mp.get_context("spawn")
-    t0 = time.perf_counter()
-    with ctx.Pool(cores) as pool:
-        pool.map(_oracle_job, jobs, chunksize=1)
-    wall = time.perf_counter() - t0
-    return cells / wall, wall, (f"{len(pick)} instances (every {SAMPLE_STRIDE}th by N, N={inst[pick[0]].n}.."
-                                f"{inst[pick[-1]].n}), first {SAMPLE_STEPS} RK3 steps each, FP64 oracle, "
-                                f"{cores} spawned processes")
+def roofline_hbm(bytes_per_cu: int, cell_updates: float, seconds: float, kernel: str, traffic=None, **extra):
+    """Roofline on the algorithmic bytes: achieved = bytes per cell-update x cell-updates of the
+    dominant kernel / its CUDA-event time, against the measured copy bandwidth."""
+    peak, src = _peaks()
+    achieved = bytes_per_cu * cell_updates / seconds / 1e9 if seconds > 0 else None
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": (achieved / peak) if achieved else None, "traffic": traffic, "kernel": kernel,
+           "bytes_per_cell_update": bytes_per_cu, "peak_source": f"{src} (hbm_gbs)"}
+    out.update(extra)
+    return out
 
 
 # ------------------------------------------------------------------------------- clocks
@@ -128,20 +138,75 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# ------------------------------------------------------------------------------- GPU leg
-def run_gpu(args, rank, world, local_rank):
+class npw_profile(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("stage_launches", ctypes.c_int64), ("stage_ms", ctypes.c_double),
+                ("timed_launches", ctypes.c_int64), ("resident_launches", ctypes.c_int64 * 4),
+                ("resident_ms", ctypes.c_double * 4)]
+
+
+class Profiled:
+    """npw_profile counters around a region (launch counts, stage-kernel and resident event times)."""
+
+    def __init__(self, lib):
+        self.lib = lib
+        self.pr = npw_profile()
+
+    def __enter__(self):
+        self.lib.npw_profile_reset()
+        self.lib.npw_profile_enable(1)
+        return self
+
+    def __exit__(self, *a):
+        self.lib.npw_profile_read(ctypes.byref(self.pr))
+        self.lib.npw_profile_enable(0)
+
+
+def kernel_source_hash() -> str:
+    """sha256 over the device sources (ncu figures are valid only for the sources they were
+    taken from)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1602_00182_gb300", "csrc")
+    for f in ("npw_internal.h", "npw_device.cuh", "npw_fast.cuh", "npw_kernels.cuh", "npw_fp32.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(key: str):
+    """DRAM bytes per launch of a dominant launch from the committed ncu summary, when it was
+    taken from the current kernel sources (null otherwise)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            d = json.load(fh)
+        if d.get("kernel_source_sha256") != kernel_source_hash():
+            return None
+        return d.get(key)
+    except Exception:
+        return None
+
+
+def _timed_event(fn, stream, flush):
+    """One call between CUDA events on the launching stream, L2 flushed before."""
+    import torch
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), r
+
+
+# ------------------------------------------------------------------------------- headline (C2)
+def headline_burgers(args, rank, world, local_rank):
     import torch
     import paper_1602_00182_gb300.npweno as npw
-    from paper_1602_00182_gb300 import build as b
 
-    if local_rank == 0 or not os.path.exists(npw.LIB_PATH):
-        b.build()
-    if world > 1:
-        torch.distributed.barrier()
     lib = npw.load()
     dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-
     inst = I.burgers_batch(count=args.instances, seed_index=rank_seed(1, rank))
     # largest instances first in the arena (the work list follows the arena order)
     order = sorted(range(len(inst)), key=lambda i: -inst[i].n)
@@ -153,7 +218,7 @@ def run_gpu(args, rank, world, local_rank):
     pristine = torch.tensor(host0, device=dev)
     arena = pristine.clone()
     ws = torch.empty(npw.npw_batch_workspace_size(table, 1, params), dtype=torch.uint8, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
     def one_solve():
@@ -162,18 +227,14 @@ def run_gpu(args, rank, world, local_rank):
             raise RuntimeError(f"batch solve failed with status {st}")
         return stats
 
-    # warm-up (also yields the per-instance step counts: the work of one step)
     for _ in range(args.warmup):
         arena.copy_(pristine)
         stats = one_solve()
     cell_updates = sum(n * s["steps"] for n, s in zip(ns, stats))
 
-    pr = npw_profile()
-    lib.npw_profile_reset()
-    lib.npw_profile_enable(1)
     times = []
     clocks = Clocks(os.path.join(args.out_dir, f"clocks_rank{rank}.csv"))
-    with clocks:
+    with Profiled(lib) as prof, clocks:
         for _ in range(args.steps):
             arena.copy_(pristine)
             flush.fill_(1.0)  # evict the working set from L2 between timed steps
@@ -183,27 +244,36 @@ def run_gpu(args, rank, world, local_rank):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            one_solve()
+            stats = one_solve()
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
-    lib.npw_profile_read(ctypes.byref(pr))
-    lib.npw_profile_enable(0)
+    pr = prof.pr
     tmax, cu_all = job_totals(sum(times), cell_updates * args.steps, world, dev)
     value = cu_all / (tmax / 1e3)
+    result_host = arena.cpu().numpy()  # the last timed solve's states (accuracy sample)
 
-    # Roofline of the dominant kernel.  Every instance of this workload fits in shared memory,
-    # so the batch runs in the resident whole-solve kernel; its largest size class (n > 4096,
-    # ~3/4 of the work) is the dominant launch.  It is bound by the FP64 pipe (the shape
-    # parameter), not by HBM: achieved = FP64-pipe instructions of the eta evaluations
-    # (FP64_OPS_PER_ETA per face and stage, counted over all n+1 faces: an upper bound, since
-    # faces where the switch fires skip it) / the class-A launch time.
+    # roofline of the dominant kernel: the resident class n > 4096 (~3/4 of the work)
     big = [k for k, n in enumerate(ns) if n > 4096]
+    cu_a = sum(ns[k] * stats[k]["steps"] for k in big) * args.steps
     faces_a = sum((ns[k] + 1) * 3 * stats[k]["steps"] for k in big) * args.steps
     res_s = pr.resident_ms[0] / 1e3
-    achieved = FP64_OPS_PER_ETA * faces_a / res_s / 1e9 if res_s > 0 else None
-    peak = FP64_PIPE_PEAK / 1e9
-    traffic = _ncu_traffic()
+    fp64 = FP64_OPS_PER_ETA * faces_a / res_s / 1e9 if res_s > 0 else None
+    roof = roofline_hbm(BYTES_SCALAR_F32, cu_a, res_s,
+                        "solve1d_resident_kernel<BURGERS, 3>, size class n > 4096 (512 threads, 2 CTAs/SM)",
+                        traffic=_ncu_traffic("solve1d_resident_burgers_classA_dram_bytes_per_launch"),
+                        secondary={
+                            "fp64_pipe": {"achieved": fp64, "peak": FP64_PIPE_PEAK / 1e9, "unit": "G FP64-pipe instr/s",
+                                          "frac": (fp64 / (FP64_PIPE_PEAK / 1e9)) if fp64 else None,
+                                          "count": f"{FP64_OPS_PER_ETA} per face and stage (eta), all n+1 faces"},
+                            "hbm_bytes_actually_moved": "8 B per cell per solve: the state stays in shared memory"},
+                        resident_launches=[int(x) for x in pr.resident_launches],
+                        resident_ms=[float(x) for x in pr.resident_ms],
+                        kernel_source_sha256=kernel_source_hash())
+
+    # decisions of the shape parameter over the batch (the bound is off: the printed eta)
+    eta_tot = {k: sum(s["eta"][k] for s in stats) for k in ("switch", "eval", "guard", "bound")}
+    faces_tot = eta_tot["switch"] + eta_tot["eval"]
 
     # end to end through the C ABI with host buffers: H2D of the initial state, the solve,
     # D2H of the result, per step
@@ -230,22 +300,16 @@ def run_gpu(args, rank, world, local_rank):
         vt = []
         for _ in range(args.variant_steps):
             arena.copy_(pristine)
-            flush.fill_(1.0)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st, vstats = npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, pv, workspace=ws)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            vt.append(e0.elapsed_time(e1))
+            ms, (st, vstats) = _timed_event(
+                lambda: npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, pv, workspace=ws), stream, flush)
+            vt.append(ms)
         vcu = sum(n * s["steps"] for n, s in zip(ns, vstats))
         variants[label] = {"value": vcu * len(vt) / (sum(vt) / 1e3), "unit": "cell-updates/s",
                            "ms_per_step": sum(vt) / len(vt)}
 
     if args.variant_steps > 0 and args.eta_eval == 0 and world == 1:
         time_variant(npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, eta_eval=1),
-                     "eta_eval=1 (exact double-float eta, no FP64 instruction)")
+                     "eta_eval=1 (double-float eta, no FP64 instruction)")
         time_variant(npw.Params(k=2, rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, eta_max=1.0),
                      "k=2 RBF-WENO3 Gaussian + switch (Table k2; resident kernels, eta in FP64), |eta| <= 1 "
                      "(the printed k = 2 eta is singular where u crosses zero)")
@@ -270,74 +334,344 @@ def run_gpu(args, rank, world, local_rank):
             "cells": int(sum(ns)),
             "cell_updates_per_step": int(cell_updates),
             "precision": ("NPW_FP32_MIXED: f32 state, candidates, beta, weights, flux, update; eta in FP64 "
-                          f"(eta_eval={args.eta_eval}); switch decisions equal to FP64 evaluation"),
+                          f"(eta_eval={args.eta_eval}); switch decisions equal to FP64 evaluation; eta as printed "
+                          "(no bound)"),
             "l2": "flushed (256 MB write) before every timed step; working set 3 x 4 B x cells",
             "parallelism": f"independent instance batches, one per rank (x{world})",
         },
-        "roofline": {
-            "bound": "alu",
-            "achieved": achieved,
-            "peak": peak,
-            "unit": "G FP64-pipe instr/s",
-            "frac": (achieved / peak) if achieved else None,
-            "traffic": traffic,
-            "kernel": "solve1d_resident_kernel<BURGERS>, size class n > 4096 (512 threads, 2 CTAs/SM)",
-            "resident_launches": [int(x) for x in pr.resident_launches],
-            "resident_ms": [float(x) for x in pr.resident_ms],
-            "peak_source": ("derived: 2 FP64-pipe instr/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s FP64); "
-                            "probe of DFMA chains: 1.19 TFLOP/s"),
-            "hbm_bytes_per_cell_update": "8 per solve (state read once, written once)",
-            "kernel_source_sha256": kernel_source_hash(),
-        },
+        "roofline": roof,
+        "eta_decisions": {"faces": faces_tot, **eta_tot,
+                          "switch_frac": eta_tot["switch"] / faces_tot if faces_tot else None,
+                          "bound_frac": eta_tot["bound"] / faces_tot if faces_tot else None,
+                          "guard_frac": eta_tot["guard"] / faces_tot if faces_tot else None,
+                          "note": "per face and stage over the batch; guard: the float round-off guard of the "
+                                  "mixed path; bound: off (the printed eta)"},
         "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": int(host0.nbytes),
                 "d2h_bytes_per_step": int(host0.nbytes)},
         "gpu_launches": int(pr.kernel_launches),
         "variants": variants,
         "clocks": clocks.summary(local_rank),
     }
-    return out, inst
+    sample = {"order": order, "ns": ns, "host0": host0, "result": result_host, "inst": inst}
+    return out, sample
 
 
-class npw_profile(ctypes.Structure):
-    _fields_ = [("kernel_launches", ctypes.c_int64), ("stage_launches", ctypes.c_int64), ("stage_ms", ctypes.c_double),
-                ("timed_launches", ctypes.c_int64), ("resident_launches", ctypes.c_int64 * 4),
-                ("resident_ms", ctypes.c_double * 4)]
+# ------------------------------------------------------------------------------- C1
+def block_advection(args):
+    """Sec. 5.2 Ex. 1 setting at the configuration's FP64: sin(pi x) on [-1, 1], periodic,
+    RBF-WENO5 (multiquadric) with the switch, LF, TVD-RK3 at CFL 0.5 to T = 2 (400 steps at
+    N = 200); solve latency and cell-updates/s through npweno_solve, and the convergence sweep
+    N = 25..400 against the exact cell averages (the RK3 time error dominates at CFL 0.5)."""
+    import torch
+    import paper_1602_00182_gb300.npweno as npw
+    lib = npw.load()
+    p = npw.Params()
+    u0, dx = I.advection_sin(200)
+    dev_u = torch.empty(200, dtype=torch.float64, device="cuda")
+    pristine = torch.tensor(u0, device="cuda")
+    ws = torch.empty(npw.npw_workspace_size(200, 1, p), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        dev_u.copy_(pristine)
+        npw.npweno_solve(dev_u, dx, 2.0, 0.5, npw.NPW_FLUX_ADVECTION, npw.NPW_BC_PERIODIC, p, workspace=ws)
+    lat_dev, lat_host = [], []
+    with Profiled(lib) as prof:
+        for _ in range(20):
+            dev_u.copy_(pristine)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = npw.npweno_solve(dev_u, dx, 2.0, 0.5, npw.NPW_FLUX_ADVECTION, npw.NPW_BC_PERIODIC, p, workspace=ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lat_host.append(time.perf_counter() - t0)
+            lat_dev.append(e0.elapsed_time(e1))
+    result = dev_u.cpu().numpy()
+    cu = 200 * st["steps"]
+    ms = statistics.median(lat_dev)
+    stage_s = prof.pr.stage_ms / 1e3
+    sweep = {}
+    for n in (25, 50, 100, 200, 400):
+        un, dxn = I.advection_sin(n)
+        g = torch.tensor(un, device="cuda")
+        npw.npweno_solve(g, dxn, 2.0, 0.5, npw.NPW_FLUX_ADVECTION, npw.NPW_BC_PERIODIC, p)
+        ex, _ = I.advection_sin(n, shift=2.0)
+        e = np.abs(g.cpu().numpy() - ex)
+        sweep[n] = {"l1": float(e.mean()), "linf": float(e.max())}
+    ns = sorted(sweep)
+    orders = [float(np.log(sweep[a]["l1"] / sweep[b]["l1"]) / np.log(b / a)) for a, b in zip(ns, ns[1:])]
+    return {
+        "metric": "cell-updates/s", "value": cu / (ms / 1e3), "unit": "cell-updates/s", "dtype": "f64",
+        "latency_ms": {"device_median": ms, "host_median": 1e3 * statistics.median(lat_host),
+                       "host_p99": 1e3 * float(np.percentile(lat_host, 99))},
+        "config": {"workload": "1D linear advection u_t+u_x=0 on [-1,1], periodic, u0=sin(pi x), N=200, FP64, "
+                               "RBF-WENO5 multiquadric + monotone switch, LF, TVD-RK3 CFL 0.5 to T=2",
+                   "steps": st["steps"], "cell_updates": cu, "timed_solves": len(lat_dev)},
+        "convergence_vs_exact": {"l1_linf": {str(n): sweep[n] for n in ns}, "l1_orders": orders,
+                                 "note": "at CFL 0.5 the RK3 time error dominates WENO5's spatial error: order ~3"},
+        "roofline": roofline_hbm(BYTES_SCALAR_F64, cu * len(lat_dev), stage_s, "stage1d_kernel<double, ADVECTION>",
+                                 note="a latency-bound case: 200 cells, 1200 stage launches per solve"),
+        "gpu_launches_per_solve": int(prof.pr.kernel_launches / len(lat_dev)),
+    }, {"u0": u0, "dx": dx, "result": result, "steps": st["steps"]}
 
 
-# FP64-pipe instructions of one shape-parameter evaluation in the mixed path (eta_fp64 in
-# csrc/npw_fast.cuh): 2 adds (the numerator pair and the denominator pair, which carries
-# eps_M, to double), 1 multiply and 2 multiply-adds (the Newton-corrected quotient); the
-# format changes between float and double (the pairs, the seed, the result) are integer work.
-FP64_OPS_PER_ETA = 5
-# FP64 pipe peak: 1.25 TFLOP/s nominal FP64 = 0.625e12 FMA/s over 152 SMs at 2.07 GHz, i.e.
-# 2 FP64-pipe instructions per clock per SM (a probe of independent DFMA chains measured 1.19 TFLOP/s)
-FP64_PIPE_PEAK = 2.0 * 152 * 2.07e9
+# ------------------------------------------------------------------------------- C3
+def block_euler1d(args, characteristic: int):
+    """512 transmissive Euler instances (m = 3), N log-uniform in [256, 65536], Riemann and
+    Shu-Osher-type data, through the work-queue kernel (mixed precision; instances that fit in
+    shared memory run in the resident kernel beside it), to t_frac x each end time."""
+    import torch
+    import paper_1602_00182_gb300.npweno as npw
+    lib = npw.load()
+    inst = I.euler_batch(count=512, seed_index=2)
+    t_frac = args.euler_t_frac if not characteristic else args.euler_char_t_frac
+    specs = [dict(kind=npw.NPW_FLUX_EULER1D, nx=it.n, dx=it.dx, t_end=t_frac * it.t_end, cfl=CFL, bc=1) for it in inst]
+    table, total, offs = npw.make_queue_instances(specs)
+    host0 = np.concatenate([it.u0.ravel() for it in inst]).astype(np.float32)
+    pristine = torch.tensor(host0, device="cuda")
+    arena = pristine.clone()
+    # characteristic runs bound |eta| by 1 (the printed eta of a characteristic field blows up at
+    # the foot of the Mach-3 shock of the Shu-Osher-type data)
+    eta_max = 1.0 if characteristic else 0.0
+    p = npw.Params(precision=npw.NPW_FP32_MIXED, characteristic=characteristic, eta_max=eta_max)
+    tile = npw.npw_autotune_1d(npw.NPW_FLUX_EULER1D, 3, p)  # later runs with tile_1d = 0 use it
+    ws = torch.empty(npw.npw_queue_workspace_size(table, p), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    # warm-up on a short run (graph capture, attributes)
+    wtable, _, _ = npw.make_queue_instances([dict(sp, t_end=0.02 * sp["t_end"]) for sp in specs])
+    npw.npweno_queue_solve(arena, wtable, p, workspace=ws)
+    arena.copy_(pristine)
+    clocks = Clocks(os.path.join(args.out_dir, f"clocks_euler1d_{characteristic}.csv"))
+    with Profiled(lib) as prof, clocks:
+        ms, (st, stats) = _timed_event(lambda: npw.npweno_queue_solve(arena, table, p, workspace=ws), stream, flush)
+    if st != 0:
+        raise RuntimeError(f"euler1d queue solve failed with status {st}")
+    ns = [it.n for it in inst]
+    cu = sum(n * s["steps"] for n, s in zip(ns, stats))
+    res_limit = 5682  # resident instances (three 3 (n + 6)-float arrays within 200 KiB)
+    cu_queue = sum(n * s["steps"] for n, s in zip(ns, stats) if characteristic or n > res_limit)
+    stage_s = prof.pr.stage_ms / 1e3
+    eta_tot = {k: sum(s["eta"][k] for s in stats) for k in ("switch", "eval", "guard", "bound")}
+    kern = ("queue_stage_kernel<float, K=3, characteristic> (face-based Roe-field body)" if characteristic
+            else "queue_stage_kernel<float, K=3> (compensated per-stage body)")
+    return {
+        "metric": "cell-updates/s", "value": cu / (ms / 1e3), "unit": "cell-updates/s", "dtype": "f32",
+        "ms_per_solve": ms,
+        "config": {"workload": ("batched 1D Euler (m=3, gamma=1.4), transmissive: 512 instances, N log-uniform "
+                                "[256,65536], Riemann + Shu-Osher-type data, "
+                                f"{'characteristic' if characteristic else 'component'}-wise, RBF-WENO5 MQ + switch"
+                                f"{', |eta| <= 1' if characteristic else ''}, LF, TVD-RK3 CFL 0.5 to "
+                                f"{t_frac} x each end time"),
+                   "instances": 512, "cells": int(sum(ns)), "cell_updates": int(cu), "tile_1d": tile,
+                   "path": "npweno_queue_solve: persistent work-queue stage kernel, steps replayed as CUDA graphs"
+                           + ("" if characteristic else "; instances with n <= 5682 in the resident kernel beside it"),
+                   "l2": "flushed before the timed solve"},
+        "roofline": roofline_hbm(BYTES_EULER1D_F32, cu_queue, stage_s, kern,
+                                 stage_launches=int(prof.pr.stage_launches), stage_ms=prof.pr.stage_ms),
+        "eta_decisions": eta_tot,
+        "gpu_launches": int(prof.pr.kernel_launches),
+        "clocks": clocks.summary(0),
+    }, {"inst": inst, "host0": host0, "offs": offs, "result": arena.cpu().numpy(), "t_frac": t_frac,
+        "characteristic": characteristic, "eta_max": eta_max}
 
 
-def kernel_source_hash() -> str:
-    """sha256 over the device sources of the mixed-precision kernels (ncu figures are valid only
-    for the sources they were taken from)."""
-    import hashlib
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1602_00182_gb300", "csrc")
-    for f in ("npw_internal.h", "npw_device.cuh", "npw_fast.cuh", "npw_kernels.cuh", "npw_fp32.cu"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+# ------------------------------------------------------------------------------- C4
+def block_euler2d(args):
+    """2D Euler, dimension by dimension, on periodic squares 256^2, 512^2, 1024^2, 2048^2: per
+    size a batch of 2^24 cells (256, 64, 16, 4 squares; vortex and four-quadrant data), ~100 RK3
+    steps at CFL 0.5, all squares of a size in one work-queue batch."""
+    import torch
+    import paper_1602_00182_gb300.npweno as npw
+    lib = npw.load()
+    p = npw.Params(precision=npw.NPW_FP32_MIXED)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sizes = {}
+    tot_cu, tot_ms, tot_stage_s, tot_launch = 0, 0.0, 0.0, 0
+    for n in args.sizes2d:
+        count = max(1, (1 << 24) // (n * n))
+        doms = I.euler2d_batch(n, count, seed_index=3)
+        specs, fields = [], []
+        for U, d in doms:
+            rho, mx, my, E = U
+            u, v = mx / rho, my / rho
+            c = np.sqrt(1.4 * 0.4 * (E - 0.5 * rho * (u * u + v * v)) / rho)
+            rate = (np.abs(u) + c).max() / d + (np.abs(v) + c).max() / d
+            specs.append(dict(kind=npw.NPW_FLUX_EULER2D, nx=n, ny=n, dx=d, dy=d, t_end=args.steps2d * CFL / rate,
+                              cfl=CFL, bc=0))
+            fields.append(U.astype(np.float32).ravel())
+        table, total, offs = npw.make_queue_instances(specs)
+        pristine = torch.tensor(np.concatenate(fields), device="cuda")
+        arena = pristine.clone()
+        ws = torch.empty(npw.npw_queue_workspace_size(table, p), dtype=torch.uint8, device="cuda")
+        wtable, _, _ = npw.make_queue_instances([dict(sp, t_end=0.05 * sp["t_end"]) for sp in specs])
+        npw.npweno_queue_solve(arena, wtable, p, workspace=ws)  # warm-up
+        arena.copy_(pristine)
+        with Profiled(lib) as prof:
+            ms, (st, stats) = _timed_event(lambda: npw.npweno_queue_solve(arena, table, p, workspace=ws), stream, flush)
+        if st != 0:
+            raise RuntimeError(f"euler2d queue solve failed with status {st}")
+        cu = n * n * sum(s["steps"] for s in stats)
+        sizes[f"{n}^2"] = {"domains": count, "value": cu / (ms / 1e3), "ms_per_solve": ms,
+                           "steps": [min(s["steps"] for s in stats), max(s["steps"] for s in stats)],
+                           "roofline_frac": roofline_hbm(BYTES_EULER2D_F32, cu, prof.pr.stage_ms / 1e3, "")["frac"]}
+        tot_cu += cu
+        tot_ms += ms
+        tot_stage_s += prof.pr.stage_ms / 1e3
+        tot_launch += int(prof.pr.kernel_launches)
+        del arena, pristine, ws
+    return {
+        "metric": "cell-updates/s", "value": tot_cu / (tot_ms / 1e3), "unit": "cell-updates/s", "dtype": "f32",
+        "config": {"workload": ("2D Euler dimension by dimension, periodic squares 256^2..2048^2 (2^24 cells per size: "
+                                "isentropic vortex + four-quadrant), RBF-WENO5 MQ + switch, one midpoint point per face, "
+                                f"~{args.steps2d} RK3 steps at CFL 0.5"),
+                   "path": "npweno_queue_solve: all squares of a size in one persistent work-queue batch",
+                   "l2": "flushed before every timed solve"},
+        "sizes": sizes,
+        "roofline": roofline_hbm(BYTES_EULER2D_F32, tot_cu, tot_stage_s,
+                                 "queue_stage_kernel<float, K=3> (phased 2D body, 32 x 8 tiles)"),
+        "gpu_launches": tot_launch,
+    }
 
 
-def _ncu_traffic():
-    """DRAM bytes per launch of the dominant launch from the committed ncu summary, when it was
-    taken from the current kernel sources (null otherwise)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        with open(p) as fh:
-            d = json.load(fh)
-        if d.get("kernel_source_sha256") != kernel_source_hash():
-            return None
-        return d.get("solve1d_resident_burgers_classA_dram_bytes_per_launch")
-    except Exception:
-        return None
+def accuracy_run_2d(npw, n=256, steps=5):
+    """Two squares of the 2D workload (vortex, four-quadrant) advanced ~steps RK3 steps on the
+    GPU (mixed precision); the oracle runs on the same float data in the CPU leg."""
+    import torch
+    doms = I.euler2d_batch(n, 2, seed_index=3)
+    specs, fields, data = [], [], []
+    for U, d in doms:
+        U32 = U.astype(np.float32)
+        rho, mx, my, E = U32.astype(np.float64)
+        u, v = mx / rho, my / rho
+        c = np.sqrt(1.4 * 0.4 * (E - 0.5 * rho * (u * u + v * v)) / rho)
+        rate = (np.abs(u) + c).max() / d + (np.abs(v) + c).max() / d
+        t_end = 0.999 * steps * CFL / rate
+        specs.append(dict(kind=npw.NPW_FLUX_EULER2D, nx=n, ny=n, dx=d, dy=d, t_end=t_end, cfl=CFL, bc=0))
+        fields.append(U32.ravel())
+        data.append((U32.astype(np.float64), d, t_end))
+    table, total, offs = npw.make_queue_instances(specs)
+    arena = torch.tensor(np.concatenate(fields), device="cuda")
+    st, stats = npw.npweno_queue_solve(arena, table, npw.Params(precision=npw.NPW_FP32_MIXED))
+    a = arena.cpu().numpy().astype(np.float64)
+    return [(U, d, t, a[o:o + U.size].reshape(U.shape)) for (U, d, t), o in zip(data, offs)]
+
+
+# ------------------------------------------------------------------------------- CPU leg (oracle)
+def _oracle_task(task):
+    """One oracle run of a bounded sample: returns (result, stats, seconds)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    p = O.Params(**task["params"])
+    if task.get("ny"):
+        r, st = O.solve_2d(task["u0"], task["dx"], task["dy"], task["t_end"], CFL, task["kind"], task["bc"], p,
+                           max_steps=task.get("max_steps", -1))
+    else:
+        r, st = O.solve(task["u0"], task["dx"], task["t_end"], CFL, task["kind"], task["bc"], p,
+                        max_steps=task.get("max_steps", -1))
+    return r, st, time.perf_counter() - t0
+
+
+def run_oracle(tasks, cores):
+    import multiprocessing as mp
+    import oracle as O
+    O.build()
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(min(cores, len(tasks))) as pool:
+        res = pool.map(_oracle_task, tasks, chunksize=1)
+    return res, time.perf_counter() - t0
+
+
+def cpu_sample(inst, cores: int):
+    """The FP64 oracle on the headline's bounded timing sample: every SAMPLE_STRIDE-th instance
+    (sorted by N), the first SAMPLE_STEPS RK3 steps each, over spawned processes."""
+    import oracle as O
+    order = sorted(range(len(inst)), key=lambda i: inst[i].n)
+    pick = order[SAMPLE_STRIDE // 2::SAMPLE_STRIDE]
+    tasks = [dict(u0=inst[i].u0[0].astype(np.float64), dx=inst[i].dx, t_end=T_END, kind=O.BURGERS, bc=O.PERIODIC,
+                  params=dict(rbf=O.GA), max_steps=SAMPLE_STEPS) for i in pick]
+    cells = sum(inst[i].n for i in pick) * SAMPLE_STEPS
+    _, wall = run_oracle(tasks, cores)
+    return cells / wall, wall, (f"{len(pick)} instances (every {SAMPLE_STRIDE}th by N, N={inst[pick[0]].n}.."
+                                f"{inst[pick[-1]].n}), first {SAMPLE_STEPS} RK3 steps each, FP64 oracle, "
+                                f"{min(cores, len(pick))} spawned processes")
+
+
+def _errors(got, ref):
+    """L1 (mean) and L_inf of the difference, absolute and relative to max |ref|."""
+    got, ref = np.asarray(got, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    e = np.abs(got - ref)
+    scale = np.abs(ref).max()
+    return {"l1": float(e.mean()), "linf": float(e.max()), "l1_rel": float(e.mean() / scale),
+            "linf_rel": float(e.max() / scale)}
+
+
+def _worst(errs):
+    return {k: max(e[k] for e in errs) for k in errs[0]} if errs else None
+
+
+def cpu_leg_headline(sample, cores):
+    """Accuracy of the headline against the oracle: the eight smallest instances of the batch,
+    solved to T = 1.5 by the oracle from the same float data."""
+    import oracle as O
+    ns, order, host0, result = sample["ns"], sample["order"], sample["host0"], sample["result"]
+    offs = np.concatenate([[0], np.cumsum(ns)])
+    pick = sorted(range(len(ns)), key=lambda k: ns[k])[:8]
+    tasks = [dict(u0=host0[offs[k]:offs[k + 1]].astype(np.float64), dx=sample["inst"][order[k]].dx, t_end=T_END,
+                  kind=O.BURGERS, bc=O.PERIODIC, params=dict(rbf=O.GA, eta_guard=MIXED_GUARD)) for k in pick]
+    res, wall = run_oracle(tasks, cores)
+    errs = [_errors(result[offs[k]:offs[k + 1]], r) for k, (r, st, sec) in zip(pick, res)]
+    return {"vs_oracle": _worst(errs), "sample": f"the 8 smallest instances (N {ns[pick[0]]}..{ns[pick[-1]]}) to T=1.5, "
+            "oracle from the same float data (worst over the sample)"}
+
+
+def cpu_leg_advection(c1, cores):
+    import oracle as O
+    res, wall = run_oracle([dict(u0=c1["u0"], dx=c1["dx"], t_end=2.0, kind=O.ADVECTION, bc=O.PERIODIC, params={})], 1)
+    r, st, sec = res[0]
+    return {"cpu_baseline": {"value": 200 * st["steps"] / sec, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "the whole N=200 solve (400 steps), one process"},
+            "vs_oracle": {**_errors(c1["result"], r), "steps_equal": st["steps"] == c1["steps"]}}
+
+
+def cpu_leg_euler1d(c3, cores):
+    """Accuracy and timing of the oracle on the eight smallest instances of the 1D Euler batch,
+    to the same end times, from the same float data."""
+    import oracle as O
+    inst, host0, offs, result = c3["inst"], c3["host0"], c3["offs"], c3["result"]
+    pick = sorted(range(len(inst)), key=lambda k: inst[k].n)[:8]
+    params = dict(characteristic=c3["characteristic"], eta_guard=MIXED_GUARD, eta_max=c3["eta_max"])
+    tasks = []
+    for k in pick:
+        it = inst[k]
+        tasks.append(dict(u0=host0[offs[k]:offs[k] + 3 * it.n].astype(np.float64).reshape(3, it.n), dx=it.dx,
+                          t_end=c3["t_frac"] * it.t_end, kind=O.EULER1D, bc=O.TRANSMISSIVE, params=params))
+    res, wall = run_oracle(tasks, cores)
+    errs = [_errors(result[offs[k]:offs[k] + 3 * inst[k].n].reshape(3, inst[k].n), r) for k, (r, st, sec)
+            in zip(pick, res)]
+    cells = sum(inst[k].n * st["steps"] for k, (r, st, sec) in zip(pick, res))
+    return {"cpu_baseline": {"value": cells / wall, "unit": "cell-updates/s", "cores": min(cores, len(pick)),
+                             "kind": "oracle",
+                             "sample": f"the 8 smallest instances (N {inst[pick[0]].n}..{inst[pick[-1]].n}), whole "
+                                       f"solves to {c3['t_frac']} x end time, one process each"},
+            "vs_oracle": _worst(errs)}
+
+
+def cpu_leg_euler2d(runs, cores):
+    import oracle as O
+    tasks = [dict(u0=U, dx=d, dy=d, ny=U.shape[1], t_end=t, kind=O.EULER2D, bc=O.PERIODIC,
+                  params=dict(eta_guard=MIXED_GUARD)) for U, d, t, g in runs]
+    res, wall = run_oracle(tasks, cores)
+    errs = [_errors(g, r) for (U, d, t, g), (r, st, sec) in zip(runs, res)]
+    cells = sum(U.shape[1] * U.shape[2] * st["steps"] for (U, d, t, g), (r, st, sec) in zip(runs, res))
+    n = runs[0][0].shape[1]
+    return {"cpu_baseline": {"value": cells / wall, "unit": "cell-updates/s", "cores": len(tasks), "kind": "oracle",
+                             "sample": f"two {n}^2 squares (vortex, four-quadrant), ~5 RK3 steps, one process each"},
+            "vs_oracle": _worst(errs)}
 
 
 # ------------------------------------------------------------------------------- serving
@@ -379,7 +713,6 @@ def serving_requests(count: int, rate: float, seed: int = 5):
 
 def run_serving(npw, reqs, max_steps: int = 32):
     """Continuous batching: requests are submitted at their arrival times and stepped together."""
-    import torch
     p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, batch_mode=1)
     srv = npw.Server(heap_cells=64 * 1024 * 1024, max_slots=512, params=p)
     t0 = time.perf_counter()
@@ -482,163 +815,27 @@ def job_totals(total_ms: float, units: float, world: int, device):
     return t.item(), c.item()
 
 
-# ------------------------------------------------------------------------------- other workloads
-def _timed(fn, steps, flush, world):
-    import torch
-    times = []
-    for _ in range(steps):
-        flush.fill_(1.0)
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        fn()
-        e1.record()
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-    return times
-
-
-def run_euler1d(args, rank, world, local_rank):
-    """Batched 1D Euler (512 instances, N log-uniform in [256, 65536], transmissive, Riemann and
-    Shu-Osher-type data) through the per-stage kernels (batch_mode 1), to t_frac of each end time."""
-    import torch
-    import paper_1602_00182_gb300.npweno as npw
-    from paper_1602_00182_gb300 import build as b
-    b.build()
-    lib = npw.load()
-    torch.cuda.set_device(local_rank)
-    inst = I.euler_batch(count=512, seed_index=rank_seed(2, rank))
-    ns = [it.n for it in inst]
-    tends = [args.t_frac * it.t_end for it in inst]
-    table, total = npw.make_instances(ns, [it.dx for it in inst], tends, [CFL] * len(ns), [1] * len(ns), m=3)
-    host0 = np.concatenate([it.u0.ravel() for it in inst]).astype(np.float32)
-    pristine = torch.tensor(host0, device="cuda")
-    arena = pristine.clone()
-    # characteristic runs bound |eta| by 1 (the printed eta of a characteristic field blows up at
-    # the foot of the Mach-3 shock of the Shu-Osher-type data)
-    p = npw.Params(precision=npw.NPW_FP32_MIXED, characteristic=args.characteristic, batch_mode=1,
-                   eta_max=1.0 if args.characteristic else 0.0)
-    tile = npw.npw_autotune_1d(npw.NPW_FLUX_EULER1D, 3, p)  # later runs with tile_1d = 0 use it
-    ws = torch.empty(npw.npw_batch_workspace_size(table, 3, p), dtype=torch.uint8, device="cuda")
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    holder = {}
-
-    def one():
-        arena.copy_(pristine)
-        st, stats = npw.npweno_batch_solve(arena, table, 3, npw.NPW_FLUX_EULER1D, p, workspace=ws)
-        if st != 0:
-            raise RuntimeError(f"batch solve failed: {st}")
-        holder["stats"] = stats
-
+def reference_arm(args, cores):
+    """The FP64 oracle on the host cores, a bounded sample of the headline workload per step."""
+    inst = I.burgers_batch(count=args.instances, seed_index=1)
     for _ in range(args.warmup):
-        one()
-    pr = npw_profile()
-    lib.npw_profile_reset()
-    lib.npw_profile_enable(1)
-    clocks = Clocks(os.path.join(args.out_dir, f"clocks_rank{rank}.csv"))
-    with clocks:
-        times = _timed(one, args.steps, flush, world)
-    lib.npw_profile_read(ctypes.byref(pr))
-    lib.npw_profile_enable(0)
-    stats = holder["stats"]
-    cu = sum(n * s["steps"] for n, s in zip(ns, stats))
-    faces = sum((n + 1) * 3 * 3 * s["steps"] for n, s in zip(ns, stats)) * args.steps
-    st_s = pr.stage_ms / 1e3
-    fp64 = FP64_OPS_PER_ETA * faces / st_s / 1e9 if (st_s > 0 and not args.characteristic) else None
-    alg_bytes = cu * args.steps * 3 * 44  # per field: 12 + 12 + 20 B over the three compensated stages
-    tmax, cu_all = job_totals(sum(times), cu * args.steps, world, torch.device("cuda", local_rank))
-    return {
-        "metric": "cell-updates/s", "value": cu_all / (tmax / 1e3), "unit": "cell-updates/s",
-        "ms_per_step": tmax / len(times),
-        "config": {"workload": ("batched 1D Euler (m=3, gamma=1.4), transmissive: 512 instances, N log-uniform "
-                                f"[256,65536], Riemann + Shu-Osher-type data, {'characteristic' if args.characteristic else 'component'}-wise, "
-                                f"RBF-WENO5 MQ + switch, LF, TVD-RK3 CFL 0.5 to {args.t_frac} x each end time"),
-                   "instances": 512, "cells": int(sum(ns)), "cell_updates_per_step": int(cu),
-                   "path": f"per-stage fused kernels (batch_mode 1), {tile}-cell tiles (autotuned), steps replayed "
-                           "as CUDA graphs", "l2": "flushed before every timed step"},
-        "roofline": {"bound": "alu", "achieved": fp64, "peak": FP64_PIPE_PEAK / 1e9, "unit": "G FP64-pipe instr/s",
-                     "frac": (fp64 / (FP64_PIPE_PEAK / 1e9)) if fp64 else None, "traffic": None,
-                     "kernel": ("stage1d_kernel<float, EULER1D> (characteristic, face-based)" if args.characteristic
-                                else "stage1d_fast_kernel<EULER1D>"),
-                     "hbm_view": {"achieved_gbs": alg_bytes / st_s / 1e9 if st_s > 0 else None,
-                                  "peak_gbs": _peaks()[0], "bytes_per_cell_update": 132},
-                     "stage_launches": int(pr.stage_launches), "stage_ms": pr.stage_ms},
-        "gpu_launches": int(pr.kernel_launches),
-        "clocks": clocks.summary(local_rank),
-    }
-
-
-def run_euler2d(args, rank, world, local_rank):
-    """2D Euler, dimension by dimension, on periodic squares: 4 x 2048^2 (2^24 cells), isentropic
-    vortices and four-quadrant data, ~100 RK3 steps at CFL 0.5 each."""
-    import torch
-    import paper_1602_00182_gb300.npweno as npw
-    from paper_1602_00182_gb300 import build as b
-    b.build()
-    lib = npw.load()
-    torch.cuda.set_device(local_rank)
-    n = args.n2d
-    count = max(1, (1 << 24) // (n * n))
-    doms = I.euler2d_batch(n, count, seed_index=rank_seed(3, rank))
-    p = npw.Params(precision=npw.NPW_FP32_MIXED, k=args.k, cross_2d=args.cross_2d)
-    pristine = [torch.tensor(U.astype(np.float32), device="cuda") for U, d in doms]
-    work = [x.clone() for x in pristine]
-    ws = torch.empty(npw.npw_workspace_size_2d(n, n, 4, p), dtype=torch.uint8, device="cuda")
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    tends = []
-    for U, d in doms:
-        rho, mx, my, E = U
-        u, v = mx / rho, my / rho
-        c = np.sqrt(1.4 * 0.4 * (E - 0.5 * rho * (u * u + v * v)) / rho)
-        rate = (np.abs(u) + c).max() / d + (np.abs(v) + c).max() / d
-        tends.append(args.steps2d * CFL / rate)
-    holder = {}
-
-    def one():
-        tot = 0
-        for k, (U, d) in enumerate(doms):
-            work[k].copy_(pristine[k])
-            st = npw.npweno_solve_2d(work[k], d, d, tends[k], CFL, npw.NPW_FLUX_EULER2D, 0, p, workspace=ws)
-            tot += n * n * st["steps"]
-        holder["cu"] = tot
-
-    for _ in range(args.warmup):
-        one()
-    pr = npw_profile()
-    lib.npw_profile_reset()
-    lib.npw_profile_enable(1)
-    clocks = Clocks(os.path.join(args.out_dir, f"clocks_rank{rank}.csv"))
-    with clocks:
-        times = _timed(one, args.steps, flush, world)
-    lib.npw_profile_read(ctypes.byref(pr))
-    lib.npw_profile_enable(0)
-    cu = holder["cu"]
-    st_s = pr.stage_ms / 1e3
-    # FP64-pipe view for k = 3 only (k = 2 evaluates two literal FP64 quotients per face)
-    fp64 = FP64_OPS_PER_ETA * cu * args.steps * 3 * 4 * 2 / st_s / 1e9 if (st_s > 0 and args.k == 3) else None
-    tmax, cu_all = job_totals(sum(times), cu * args.steps, world, torch.device("cuda", local_rank))
-    return {
-        "metric": "cell-updates/s", "value": cu_all / (tmax / 1e3), "unit": "cell-updates/s",
-        "ms_per_step": tmax / len(times),
-        "config": {"workload": (f"2D Euler dimension by dimension, periodic {n}^2 x {count} (isentropic vortex + "
-                                "four-quadrant), "
-                                + ("RBF-WENO5 MQ" if args.k == 3 else
-                                   "RBF-WENO3 MQ" + (" with the Sec. 6 cross shape parameter" if args.cross_2d else ""))
-                                + f" + switch, one midpoint point per face, ~{args.steps2d} RK3 steps at CFL 0.5"),
-                   "domains": count, "cells": n * n * count, "cell_updates_per_step": int(cu),
-                   "l2": "flushed before every timed step"},
-        "roofline": {"bound": "alu", "achieved": fp64, "peak": FP64_PIPE_PEAK / 1e9, "unit": "G FP64-pipe instr/s",
-                     "frac": (fp64 / (FP64_PIPE_PEAK / 1e9)) if fp64 else None, "traffic": None,
-                     "kernel": f"stage2d_fast_kernel<EULER2D, k={args.k}>",
-                     "hbm_view": {"achieved_gbs": cu * args.steps * 128 / st_s / 1e9 if st_s > 0 else None,
-                                  "peak_gbs": _peaks()[0], "bytes_per_cell_update": 128},
-                     "stage_launches": int(pr.stage_launches), "stage_ms": pr.stage_ms},
-        "gpu_launches": int(pr.kernel_launches),
-        "clocks": clocks.summary(local_rank),
-    }
+        cpu_sample(inst, cores)
+    vals, walls = [], []
+    desc = ""
+    for _ in range(args.steps):
+        v, wall, desc = cpu_sample(inst, cores)
+        vals.append(v)
+        walls.append(wall)
+    value = float(np.mean(vals))
+    print(json.dumps({
+        "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(walls)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)", "impl": "reference",
+        "config": {"workload": WORKLOAD, "instances": args.instances, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
 
 
 def main():
@@ -649,24 +846,25 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--t-end", type=float, default=T_END, help="final time (shorter only for profiling runs)")
-    ap.add_argument("--workload", default="burgers", choices=["burgers", "euler1d", "euler2d"],
-                    help="burgers: the headline batch; euler1d / euler2d: the other families (separate lines)")
-    ap.add_argument("--t-frac", type=float, default=0.1, help="euler1d: fraction of each instance's end time")
-    ap.add_argument("--characteristic", type=int, default=0, help="euler1d: characteristic-wise reconstruction")
-    ap.add_argument("--n2d", type=int, default=2048, help="euler2d: square size")
-    ap.add_argument("--steps2d", type=int, default=100, help="euler2d: RK3 steps per solve")
-    ap.add_argument("--k", type=int, default=3, choices=[2, 3], help="euler2d: ENO order parameter (Table k3 / k2)")
-    ap.add_argument("--cross-2d", type=int, default=0, choices=[0, 1],
-                    help="euler2d with --k 2: shape parameter on the 5-cell cross (Sec. 6)")
+    ap.add_argument("--blocks", default="c1,c3,c3char,c4,serving",
+                    help="the other workloads' blocks (comma list of c1, c3, c3char, c4, serving; empty: none)")
+    ap.add_argument("--euler-t-frac", type=float, default=1.0, help="1D Euler block: fraction of each end time")
+    ap.add_argument("--euler-char-t-frac", type=float, default=0.1,
+                    help="1D Euler characteristic block: fraction of each end time")
+    ap.add_argument("--sizes2d", default="256,512,1024,2048", help="2D Euler block: square sizes")
+    ap.add_argument("--steps2d", type=int, default=100, help="2D Euler block: RK3 steps per solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eta-eval", type=int, default=0, choices=[0, 1],
-                    help="0: eta in FP64 (the configuration's FP64 shape-parameter step); 1: exact double-float")
-    ap.add_argument("--serve-requests", type=int, default=60, help="requests of the serving run (0: skip)")
+                    help="0: eta in FP64 (the configuration's FP64 shape-parameter step); 1: double-float")
+    ap.add_argument("--serve-requests", type=int, default=60, help="requests of the serving run")
     ap.add_argument("--serve-rates", default="10,100,1000", help="Poisson arrival rates of the serving runs (1/s)")
     ap.add_argument("--variant-steps", type=int, default=1,
-                    help="timed solves of the eta_eval=1 variant reported beside the headline (0: skip)")
-    ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
+                    help="timed solves of each variant reported beside the headline (0: skip)")
+    ap.add_argument("--out-dir", default=os.path.join(tempfile.gettempdir(), "npweno_bench"),
+                    help="where the clock samples are written")
     args = ap.parse_args()
+    args.sizes2d = [int(x) for x in args.sizes2d.split(",") if x]
+    blocks = {b.strip() for b in args.blocks.split(",") if b.strip()}
     os.makedirs(args.out_dir, exist_ok=True)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -674,56 +872,53 @@ def main():
     cores = os.cpu_count() or 1
 
     if args.impl == "reference":
-        if rank != 0:
-            return
-        inst = I.burgers_batch(count=args.instances, seed_index=1)
-        vals = []
-        for _ in range(args.warmup):
-            cpu_sample(inst, cores)
-        walls = []
-        for _ in range(args.steps):
-            v, wall, desc = cpu_sample(inst, cores)
-            vals.append(v)
-            walls.append(wall)
-        value = float(np.mean(vals))
-        print(json.dumps({
-            "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(walls)),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded)", "impl": "reference",
-            "config": {"workload": WORKLOAD, "instances": args.instances, "sample": desc},
-            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-                             "sample": desc},
-            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        }))
+        if rank == 0:
+            reference_arm(args, cores)
         return
 
+    import torch
+    import paper_1602_00182_gb300.npweno as npw
+    from paper_1602_00182_gb300 import build as b
+    if local_rank == 0 or not os.path.exists(npw.LIB_PATH):
+        b.build()
     if world > 1:
-        import torch
         torch.distributed.init_process_group("nccl")
-    if args.workload != "burgers":
-        fn = run_euler1d if args.workload == "euler1d" else run_euler2d
-        out = fn(args, rank, world, local_rank)
-        out.update({"n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-                    "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)", "impl": "ours"})
-        if rank == 0:
-            print(json.dumps(out))
-        if world > 1:
-            import torch
-            torch.distributed.destroy_process_group()
-        return
-    out, inst = run_gpu(args, rank, world, local_rank)
-    if rank == 0 and world == 1 and args.serve_requests > 0:
-        import paper_1602_00182_gb300.npweno as npw
+        torch.distributed.barrier()
+    torch.cuda.set_device(local_rank)
+    out, sample = headline_burgers(args, rank, world, local_rank)
+    single = rank == 0 and world == 1
+    cfg, leg = {}, {}
+    if single and "c1" in blocks:
+        cfg["advection_fp64_n200"], leg["c1"] = block_advection(args)
+    if single and "c3" in blocks:
+        cfg["euler1d_component"], leg["c3"] = block_euler1d(args, 0)
+    if single and "c3char" in blocks:
+        cfg["euler1d_characteristic"], leg["c3char"] = block_euler1d(args, 1)
+    if single and "c4" in blocks:
+        cfg["euler2d"] = block_euler2d(args)
+        leg["c4"] = accuracy_run_2d(npw)
+    if cfg:
+        out["configs"] = cfg
+    if single and "serving" in blocks and args.serve_requests > 0:
         out["serving"] = serving_block(npw, args.serve_requests, [float(x) for x in args.serve_rates.split(",")])
     if rank == 0:
         if not args.no_cpu_baseline:
-            v, wall, desc = cpu_sample(inst, cores)
+            # the CPU leg: the FP64 oracle on bounded samples, timed on the host cores; its results
+            # also give each block's difference from the oracle
+            v, wall, desc = cpu_sample(sample["inst"], cores)
             out["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
                                    "sample": desc}
+            out["accuracy"] = cpu_leg_headline(sample, cores)
+            if "c1" in leg:
+                cfg["advection_fp64_n200"].update(cpu_leg_advection(leg["c1"], cores))
+            if "c3" in leg:
+                cfg["euler1d_component"].update(cpu_leg_euler1d(leg["c3"], cores))
+            if "c3char" in leg:
+                cfg["euler1d_characteristic"].update(cpu_leg_euler1d(leg["c3char"], cores))
+            if "c4" in leg:
+                cfg["euler2d"].update(cpu_leg_euler2d(leg["c4"], cores))
         print(json.dumps(out))
     if world > 1:
-        import torch
         torch.distributed.destroy_process_group()
 
 

@@ -274,24 +274,27 @@ npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32
                               void* workspace, size_t workspace_bytes, npw_solve_stats* out, void* stream);
 
 /*
- * Request server: continuous batching of 1D solves (no counterpart in the paper; the serving
- * loop around the method).  The server sub-allocates a caller-provided device arena: per
- * request it needs 3 * m * n elements (state and two stage buffers) of the server's precision,
- * plus 2 * m * n floats (next state and compensation carry) in mixed precision.
- * Requests are queued by npw_server_submit (non-blocking) and admitted first-in first-out
- * whenever a slot and arena space are free; every npw_server_step advances all admitted
- * requests together -- each with its own dt, alpha and t_end -- by up to max_steps RK3 steps
- * through the fused per-stage kernels (one launch set per 1D flux kind over all 1D requests,
- * one per 2D request), then copies finished states to their host buffers and frees their
- * space.  A request occupies m * n (2D: m * n * ny) heap cells.  Each request's arithmetic depends only
- * on its own data, so its result is the same bits alone or in any mix.
+ * Request server: continuous batching of 1D and 2D solves (no counterpart in the paper; the
+ * serving loop around the method).  Requests are queued by npw_server_submit (non-blocking) and
+ * admitted first-in first-out whenever a slot and heap space are free.  Each request carries its
+ * own end time and tolerance; the tolerance picks its precision lane: NPW_FP32_MIXED for a
+ * tolerance >= 1e-4 (the mixed path's stated L1 class), NPW_FP64 below (0: the server's
+ * params->precision).  Every npw_server_step advances all admitted requests of both lanes
+ * together -- each with its own dt, alpha, step count and t_end -- by up to max_steps RK3 steps
+ * through the work-queue kernel (per lane and stage one persistent launch over every work item
+ * of every admitted request, 1D and 2D), then copies finished states to their host buffers and
+ * frees their space.  Each request's arithmetic depends only on its own data, so its result is
+ * the same bits alone or in any mix (and equal to npweno_batch_solve with batch_mode 1 or
+ * npweno_solve_2d of the same request in its lane's precision).
  *   device_arena / arena_bytes: caller-owned device memory, at least
- *       npw_server_arena_bytes(heap_cells, max_slots, params) for a heap of heap_cells elements.
- *   params: method and precision of every request (precision decides the element type).
+ *       npw_server_arena_bytes(heap_cells, max_slots, params): a heap of heap_cells elements per
+ *       lane (a request occupies m * n, 2D m * n * ny, heap cells of its lane).
+ *   params: method of every request; params->precision is the lane of requests with tolerance 0.
  *   stream: cudaStream_t (void*) for all server work.
  * Host buffers of a request (u0_host read at admission, out_host written at completion, both
- * [m][n] of the server's element type) must stay valid until its result has been polled.
- * Timestamps are seconds since npw_server_create.  Not thread-safe: one thread drives a server.
+ * [m][n] ([m][ny][nx]) of its lane's element type: float for the mixed lane, double for FP64)
+ * must stay valid until its result has been polled.  Timestamps are seconds since
+ * npw_server_create.  Not thread-safe: one thread drives a server.
  */
 typedef struct npw_server npw_server;
 typedef struct {
@@ -309,12 +312,13 @@ typedef struct {
     double dy;             /* 2D: cell size in y */
     int32_t bc_y;          /* 2D: npw_bc of the y direction; < 0: bc */
     int32_t reserved_;
+    double tolerance;      /* 0: the server's precision; >= 1e-4: NPW_FP32_MIXED; below: NPW_FP64 */
 } npw_request;
 typedef struct {
     uint64_t id;           /* as returned by npw_server_submit */
     uint64_t tag;
     int32_t status;        /* npw_status of this request */
-    int32_t pad_;
+    int32_t precision;     /* the lane it ran in: NPW_FP32_MIXED or NPW_FP64 */
     int64_t steps;
     double t;
     double submit_s;       /* when submitted */

@@ -1302,10 +1302,12 @@ namespace npw {
 
 // mode 0: zero the control words; mode 1: start (alpha^0 from the running maxima, first dt,
 // step limit).  1D instances without items (solved by the resident kernel) are marked done.
-__global__ void queue_ctl_kernel(Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d, int count,
-                                 int mode, int64_t max_steps) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
+// list (may be NULL): the instances to start, else 0..count-1
+__global__ void queue_ctl_kernel(Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d,
+                                 const int32_t* list, int count, int mode, int64_t max_steps) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count) return;
+    const int i = list ? list[j] : j;
     Ctl* c = ctl + i;
     if (mode == 0) {
         memset(c, 0, sizeof(Ctl));
@@ -1388,9 +1390,11 @@ __global__ void queue_poll_kernel(const Ctl* ctl, const InstDev* inst1, const In
     }
 }
 
-cudaError_t launch_queue_ctl(Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d, int count,
-                             int mode, int64_t max_steps, cudaStream_t s) {
-    queue_ctl_kernel<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(ctl, inst1, inst2, is2d, count, mode, max_steps);
+cudaError_t launch_queue_ctl(Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d,
+                             const int32_t* list, int count, int mode, int64_t max_steps, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    queue_ctl_kernel<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(ctl, inst1, inst2, is2d, list, count, mode,
+                                                                     max_steps);
     return cudaGetLastError();
 }
 cudaError_t launch_queue_poll(const Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d,
@@ -1722,10 +1726,10 @@ npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32
     r.smem = r.fp32 ? npw::queue_smem_bytes<float>(tile, has1d, m1d, has2d, m2d, r.characteristic)
                     : npw::queue_smem_bytes<double>(tile, has1d, m1d, has2d, m2d, r.characteristic);
     // start: reset, alpha^0 over the items, first dt
-    NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, count, 0, 0, r.s));
+    NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, nullptr, count, 0, 0, r.s));
     cudaError_t e = r.fp32 ? npw::launch_queue_alpha<float>(q, r.s) : npw::launch_queue_alpha<double>(q, r.s);
     if (e != cudaSuccess) return cuda_fail(e, "queue alpha launch");
-    NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, count, 1, q.mp.max_steps, r.s));
+    NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, nullptr, count, 1, q.mp.max_steps, r.s));
     count_launch(3);
     if (r.comp) {  // compensated 1D items: s = u, c = 0
         for (int kind = 0; kind < 3; ++kind) {
@@ -1766,31 +1770,42 @@ npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32
 }  // extern "C"
 
 // =======================================================================================
-// Request server (continuous batching over the per-stage kernels)
+// Request server: continuous batching over the work-queue kernel, one lane per precision
 // =======================================================================================
 namespace {
 
-struct ServerLayout {
-    size_t inst, inst2d, ctl, tiles, newtiles, list, poll, heap_u, heap_u1, heap_u2, heap_s, heap_c, total;
-    int64_t max_tiles;
+constexpr double kMixedTolerance = 1e-4;  // requests with tolerance >= this take the mixed lane
+
+struct LaneLayout {
+    size_t inst1, inst2, kind, is2d, ctl, items, newitems, list, head, poll, heap_u, heap_u1, heap_u2, heap_s, heap_c;
+    size_t begin, end;
+    int64_t max_items;
 };
 
-ServerLayout server_layout(int64_t heap_cells, int max_slots, size_t esz) {
-    ServerLayout L{};
-    L.max_tiles = heap_cells / npw::TILE_1D + max_slots;
-    size_t o = 0;
-    L.inst = o;
+// one lane's part of the arena, starting at byte `begin`
+LaneLayout lane_layout(size_t begin, int64_t heap_cells, int max_slots, size_t esz, bool comp) {
+    LaneLayout L{};
+    L.max_items = heap_cells / (npw::TX_2D * npw::TY_2D) + 2 * (int64_t)max_slots;
+    size_t o = align256(begin);
+    L.begin = o;
+    L.inst1 = o;
     o = align256(o + sizeof(npw::InstDev) * (size_t)max_slots);
-    L.inst2d = o;  // per slot, used by 2D requests
+    L.inst2 = o;
     o = align256(o + sizeof(npw::Inst2D) * (size_t)max_slots);
+    L.kind = o;
+    o = align256(o + sizeof(int32_t) * (size_t)max_slots);
+    L.is2d = o;
+    o = align256(o + (size_t)max_slots);
     L.ctl = o;
     o = align256(o + sizeof(npw::Ctl) * (size_t)max_slots);
-    L.tiles = o;
-    o = align256(o + sizeof(npw::Tile) * (size_t)L.max_tiles);
-    L.newtiles = o;
-    o = align256(o + sizeof(npw::Tile) * (size_t)L.max_tiles);
+    L.items = o;
+    o = align256(o + sizeof(npw::Tile) * (size_t)L.max_items);
+    L.newitems = o;
+    o = align256(o + sizeof(npw::Tile) * (size_t)L.max_items);
     L.list = o;
     o = align256(o + sizeof(int32_t) * (size_t)max_slots);
+    L.head = o;
+    o = align256(o + 2 * sizeof(unsigned int));
     L.poll = o;
     o = align256(o + 256);
     L.heap_u = o;
@@ -1799,14 +1814,19 @@ ServerLayout server_layout(int64_t heap_cells, int max_slots, size_t esz) {
     o = align256(o + (size_t)heap_cells * esz);
     L.heap_u2 = o;
     o = align256(o + (size_t)heap_cells * esz);
-    // compensated float path: next state and carry
-    const size_t extra = esz == sizeof(float) ? (size_t)heap_cells * sizeof(float) : 0;
+    const size_t extra = comp ? (size_t)heap_cells * sizeof(float) : 0;  // compensated float 1D
     L.heap_s = o;
     o = align256(o + extra);
     L.heap_c = o;
     o = align256(o + extra);
-    L.total = o;
+    L.end = o;
     return L;
+}
+
+// lane 0: NPW_FP32_MIXED (compensated 1D items), lane 1: NPW_FP64
+size_t server_bytes(int64_t heap_cells, int max_slots) {
+    const LaneLayout a = lane_layout(0, heap_cells, max_slots, sizeof(float), true);
+    return lane_layout(a.end, heap_cells, max_slots, sizeof(double), false).end;
 }
 
 double now_s(std::chrono::steady_clock::time_point t0) {
@@ -1817,130 +1837,210 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 
 struct npw_server {
     npw_params params;
-    npw::MethodParams mp;
-    bool fp32 = false;
-    bool comp = false;  // compensated float kernels (state ends in the s region)
-    size_t esz = 8;
     int max_slots = 0;
     cudaStream_t s = nullptr;
     unsigned char* arena = nullptr;
     int64_t heap_cells = 0;
-    ServerLayout L{};
     std::chrono::steady_clock::time_point t0;
+    struct Lane {
+        LaneLayout L{};
+        npw::MethodParams mp{};
+        bool fp32 = false;
+        size_t esz = 8;
+        std::vector<std::pair<int64_t, int64_t>> free_ranges;  // [begin, end), sorted, disjoint
+        std::vector<npw::Ctl> host_ctl;
+        bool heap_alloc(int64_t len, int64_t* off) {
+            for (size_t k = 0; k < free_ranges.size(); ++k) {
+                auto& r = free_ranges[k];
+                if (r.second - r.first >= len) {
+                    *off = r.first;
+                    r.first += len;
+                    if (r.first == r.second) free_ranges.erase(free_ranges.begin() + (long)k);
+                    return true;
+                }
+            }
+            return false;
+        }
+        void heap_free(int64_t off, int64_t len) {
+            free_ranges.push_back({off, off + len});
+            std::sort(free_ranges.begin(), free_ranges.end());
+            std::vector<std::pair<int64_t, int64_t>> merged;
+            for (auto& r : free_ranges) {
+                if (!merged.empty() && merged.back().second == r.first)
+                    merged.back().second = r.second;
+                else
+                    merged.push_back(r);
+            }
+            free_ranges.swap(merged);
+        }
+    } lanes[2];
     struct Slot {
         bool used = false;
         bool fresh = false;
         uint64_t id = 0;
         npw_request req{};
+        int lane = 0;
         int m = 1;
         bool is2d = false;
         int64_t cells = 0;  // heap cells: m n (2D: m n ny)
         int64_t off = 0;
         double submit_s = 0.0, admit_s = 0.0;
     };
-    std::vector<Slot> slots;
+    std::vector<Slot> slots;  // a slot's index is its instance index in its lane's tables
     struct Pending {
         uint64_t id;
         npw_request req;
         double submit_s;
     };
     std::deque<Pending> queue;
-    std::vector<std::pair<int64_t, int64_t>> free_ranges;  // [begin, end), sorted, disjoint
     std::deque<npw_result> results;
-    std::vector<npw::Ctl> host_ctl;
     uint64_t next_id = 1;
     long long remaining_hint = 0;  // largest remaining step estimate after the last round
 
-    // CTAs of a 2D request's stage launch (tiles of TX_2D x TY_2D cells)
-    int tiles2d(int k) const {
-        const npw_request& r = slots[k].req;
-        return (int)(((r.n + npw::TX_2D - 1) / npw::TX_2D) * ((r.ny + npw::TY_2D - 1) / npw::TY_2D));
-    }
-
-    bool heap_alloc(int64_t len, int64_t* off) {
-        for (size_t k = 0; k < free_ranges.size(); ++k) {
-            auto& r = free_ranges[k];
-            if (r.second - r.first >= len) {
-                *off = r.first;
-                r.first += len;
-                if (r.first == r.second) free_ranges.erase(free_ranges.begin() + (long)k);
-                return true;
-            }
-        }
-        return false;
-    }
-    void heap_free(int64_t off, int64_t len) {
-        free_ranges.push_back({off, off + len});
-        std::sort(free_ranges.begin(), free_ranges.end());
-        std::vector<std::pair<int64_t, int64_t>> merged;
-        for (auto& r : free_ranges) {
-            if (!merged.empty() && merged.back().second == r.first)
-                merged.back().second = r.second;
-            else
-                merged.push_back(r);
-        }
-        free_ranges.swap(merged);
+    // the lane of a request: its tolerance, else the server's precision
+    int lane_of(const npw_request& r) const {
+        if (r.tolerance > 0.0) return r.tolerance >= kMixedTolerance ? 0 : 1;
+        return params.precision == NPW_FP32_MIXED ? 0 : 1;
     }
 };
 
 namespace {
 
-template <typename R>
-npw_status server_launch_steps(npw_server* sv, const std::vector<int>& kind_tiles, const std::vector<size_t>& kind_off,
-                               const std::vector<int>& slots2d, int steps) {
-    npw::Stage1DArgs a{};
-    a.inst = reinterpret_cast<const npw::InstDev*>(sv->arena + sv->L.inst);
-    a.ctl = reinterpret_cast<npw::Ctl*>(sv->arena + sv->L.ctl);
-    a.advance = 1;
-    a.tile = npw::TILE_1D;
-    a.mp = sv->mp;
-    void* u = sv->arena + sv->L.heap_u;
-    void* u1 = sv->arena + sv->L.heap_u1;
-    void* u2 = sv->arena + sv->L.heap_u2;
-    a.u = reinterpret_cast<float*>(u);
-    a.d1 = reinterpret_cast<float*>(u1);
-    a.d2 = reinterpret_cast<float*>(u2);
-    a.s = reinterpret_cast<float*>(sv->arena + sv->L.heap_s);
-    a.c = reinterpret_cast<float*>(sv->arena + sv->L.heap_c);
-    const void* in_[3] = {u, u1, u2};
-    void* out_[3] = {u1, u2, u};
-    // 2D requests: the Shu-Osher stages of npweno_solve_2d on their own instance and control
-    // words (u -> u1 -> u2 -> u at the request's heap offset)
-    npw::Stage2DArgs b{};
-    b.mp = sv->mp;
-    b.advance = 1;
-    const npw::Inst2D* inst2d = reinterpret_cast<const npw::Inst2D*>(sv->arena + sv->L.inst2d);
-    npw::Ctl* ctl = reinterpret_cast<npw::Ctl*>(sv->arena + sv->L.ctl);
-    for (int step = 0; step < steps; ++step) {
-        for (int k : slots2d) {
-            const int tiles = sv->tiles2d(k);
-            b.inst = inst2d + k;
-            b.ctl = ctl + k;
-            for (int st = 0; st < 3; ++st) {
-                b.uin = in_[st];
-                b.un = u;
-                b.uout = out_[st];
-                b.stage = st;
-                auto ev = stage_begin(sv->s);
-                cudaError_t e = npw::launch_stage2d<R>(b, tiles, sv->slots[k].req.flux_kind, sv->s);
-                stage_end(ev, sv->s);
-                if (e != cudaSuccess) return cuda_fail(e, "server stage 2d launch");
+// the queue arguments of a lane (all its slots; items and counts filled by the caller)
+npw::QueueArgs lane_queue(npw_server* sv, int ln) {
+    npw_server::Lane& lane = sv->lanes[ln];
+    const LaneLayout& L = lane.L;
+    unsigned char* a = sv->arena;
+    npw::QueueArgs q{};
+    q.u = a + L.heap_u;
+    q.u1 = a + L.heap_u1;
+    q.u2 = a + L.heap_u2;
+    q.s = reinterpret_cast<float*>(a + L.heap_s);
+    q.c = reinterpret_cast<float*>(a + L.heap_c);
+    q.inst1 = reinterpret_cast<const npw::InstDev*>(a + L.inst1);
+    q.inst2 = reinterpret_cast<const npw::Inst2D*>(a + L.inst2);
+    q.kind = reinterpret_cast<const int32_t*>(a + L.kind);
+    q.is2d = reinterpret_cast<const uint8_t*>(a + L.is2d);
+    q.ctl = reinterpret_cast<npw::Ctl*>(a + L.ctl);
+    q.items = reinterpret_cast<const npw::Tile*>(a + L.items);
+    q.advance = 1;
+    q.tile = npw::TILE_1D;
+    q.head = reinterpret_cast<unsigned int*>(a + L.head);
+    q.mp = lane.mp;
+    return q;
+}
+
+// Instance tables, work items and start of a lane's admitted requests; then `steps` RK3 steps
+// of the lane through the work-queue kernel.
+npw_status lane_round(npw_server* sv, int ln, int steps, bool* any_active) {
+    npw_server::Lane& lane = sv->lanes[ln];
+    const int S = sv->max_slots;
+    std::vector<npw::InstDev> h1(S);
+    std::vector<npw::Inst2D> h2(S);
+    std::vector<int32_t> hk(S, 0);
+    std::vector<uint8_t> h2d(S, 0);
+    std::vector<npw::Tile> items, newitems;
+    std::vector<int32_t> fresh;
+    int64_t new_kind_begin[3] = {0, 0, 0}, new_kind_end[3] = {0, 0, 0};
+    bool has1d = false, has2d = false;
+    int m1d = 1, m2d = 1;
+    for (int k = 0; k < S; ++k) {
+        const npw_server::Slot& sl = sv->slots[k];
+        if (!sl.used || sl.lane != ln) continue;
+        hk[k] = sl.req.flux_kind;
+        h2d[k] = sl.is2d;
+        if (!sl.is2d) {
+            h1[k] = npw::InstDev{sl.off, sl.req.n, sl.req.dx, sl.req.t_end, sl.req.cfl, sl.req.bc,
+                                 (int32_t)tiles_of(sl.req.n, npw::TILE_1D)};
+            has1d = true;
+            m1d = sl.m > m1d ? sl.m : m1d;
+        } else {
+            npw::Inst2D& d = h2[k];
+            d.off = sl.off;
+            d.nx = sl.req.n;
+            d.ny = sl.req.ny;
+            d.dx = sl.req.dx;
+            d.dy = sl.req.dy;
+            d.t_end = sl.req.t_end;
+            d.cfl = sl.req.cfl;
+            d.bc = sl.req.bc;
+            d.bc_y = sl.req.bc_y < 0 ? sl.req.bc : sl.req.bc_y;
+            d.tiles_x = (int32_t)((sl.req.n + npw::TX_2D - 1) / npw::TX_2D);
+            d.tiles_y = (int32_t)((sl.req.ny + npw::TY_2D - 1) / npw::TY_2D);
+            has2d = true;
+            m2d = sl.m > m2d ? sl.m : m2d;
+        }
+        if (sl.fresh) fresh.push_back(k);
+    }
+    if (!has1d && !has2d) {
+        *any_active = false;
+        return NPW_OK;
+    }
+    *any_active = true;
+    // 1D items grouped by flux kind, then 2D items; the admitted requests' items likewise
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<npw::Tile>& v = pass == 0 ? items : newitems;
+        for (int kind = 0; kind < 3; ++kind) {
+            if (pass == 1) new_kind_begin[kind] = (int64_t)v.size();
+            for (int k = 0; k < S; ++k) {
+                const npw_server::Slot& sl = sv->slots[k];
+                if (!sl.used || sl.lane != ln || sl.is2d || hk[k] != kind || (pass == 1 && !sl.fresh)) continue;
+                for (int32_t t = 0; t < h1[k].ntiles; ++t) v.push_back(npw::Tile{k, t * npw::TILE_1D});
+            }
+            if (pass == 1) new_kind_end[kind] = (int64_t)v.size();
+        }
+        for (int k = 0; k < S; ++k) {
+            const npw_server::Slot& sl = sv->slots[k];
+            if (!sl.used || sl.lane != ln || !sl.is2d || (pass == 1 && !sl.fresh)) continue;
+            for (int32_t t = 0; t < h2[k].tiles_x * h2[k].tiles_y; ++t) v.push_back(npw::Tile{k, t});
+        }
+    }
+    if ((int64_t)items.size() > lane.L.max_items) return fail(NPW_EINVAL, "server: too many work items");
+    const LaneLayout& L = lane.L;
+    unsigned char* a = sv->arena;
+    NPW_CUDA(cudaMemcpyAsync(a + L.inst1, h1.data(), sizeof(npw::InstDev) * S, cudaMemcpyHostToDevice, sv->s));
+    NPW_CUDA(cudaMemcpyAsync(a + L.inst2, h2.data(), sizeof(npw::Inst2D) * S, cudaMemcpyHostToDevice, sv->s));
+    NPW_CUDA(cudaMemcpyAsync(a + L.kind, hk.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, sv->s));
+    NPW_CUDA(cudaMemcpyAsync(a + L.is2d, h2d.data(), (size_t)S, cudaMemcpyHostToDevice, sv->s));
+    NPW_CUDA(cudaMemcpyAsync(a + L.items, items.data(), sizeof(npw::Tile) * items.size(), cudaMemcpyHostToDevice,
+                             sv->s));
+    npw::QueueArgs q = lane_queue(sv, ln);
+    q.nitems = (int32_t)items.size();
+    const size_t smem = lane.fp32 ? npw::queue_smem_bytes<float>(npw::TILE_1D, has1d, m1d, has2d, m2d, false)
+                                  : npw::queue_smem_bytes<double>(npw::TILE_1D, has1d, m1d, has2d, m2d, false);
+    if (!fresh.empty()) {
+        // start the admitted requests: reset, alpha^0 over their items, first dt and step limit
+        int32_t* dlist = reinterpret_cast<int32_t*>(a + L.list);
+        NPW_CUDA(cudaMemcpyAsync(dlist, fresh.data(), sizeof(int32_t) * fresh.size(), cudaMemcpyHostToDevice, sv->s));
+        NPW_CUDA(cudaMemcpyAsync(a + L.newitems, newitems.data(), sizeof(npw::Tile) * newitems.size(),
+                                 cudaMemcpyHostToDevice, sv->s));
+        NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, dlist, (int)fresh.size(), 0, 0, sv->s));
+        npw::QueueArgs qn = q;
+        qn.items = reinterpret_cast<const npw::Tile*>(a + L.newitems);
+        qn.nitems = (int32_t)newitems.size();
+        const cudaError_t e = lane.fp32 ? npw::launch_queue_alpha<float>(qn, sv->s) : npw::launch_queue_alpha<double>(qn, sv->s);
+        if (e != cudaSuccess) return cuda_fail(e, "server alpha launch");
+        NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, dlist, (int)fresh.size(), 1, q.mp.max_steps,
+                                       sv->s));
+        count_launch(3);
+        if (lane.fp32) {  // compensated float 1D items: s = u, c = 0
+            for (int kind = 0; kind < 3; ++kind) {
+                const int64_t b = new_kind_begin[kind], en = new_kind_end[kind];
+                if (en <= b) continue;
+                NPW_CUDA(npw::launch_comp_begin(reinterpret_cast<const float*>(q.u), q.s, q.c, q.inst1, qn.items + b,
+                                                (int)(en - b), npw::TILE_1D, flux_m(kind), sv->s));
+                count_launch();
             }
         }
-        for (int kind = 0; kind < 3; ++kind) {
-            if (kind_tiles[kind] == 0) continue;
-            a.tiles = reinterpret_cast<const npw::Tile*>(sv->arena + sv->L.tiles) + kind_off[kind];
-            a.ntiles = kind_tiles[kind];
-            for (int st = 0; st < 3; ++st) {
-                a.uin = in_[st];
-                a.un = u;
-                a.uout = out_[st];
-                a.stage = st;
-                auto ev = stage_begin(sv->s);
-                cudaError_t e = npw::launch_stage1d<R>(a, kind == NPW_FLUX_EULER1D ? 3 : 1, kind, sv->s);
-                stage_end(ev, sv->s);
-                if (e != cudaSuccess) return cuda_fail(e, "server stage launch");
-            }
+    }
+    for (int step = 0; step < steps; ++step) {
+        for (int st = 0; st < 3; ++st) {
+            q.stage = st;
+            auto ev = stage_begin(sv->s);
+            const cudaError_t e = lane.fp32 ? npw::launch_queue_stage<float>(q, false, smem, 0, sv->s)
+                                            : npw::launch_queue_stage<double>(q, false, smem, 0, sv->s);
+            stage_end(ev, sv->s);
+            if (e != cudaSuccess) return cuda_fail(e, "server queue stage launch");
         }
     }
     return NPW_OK;
@@ -1952,7 +2052,7 @@ extern "C" {
 
 size_t npw_server_arena_bytes(int64_t heap_cells, int32_t max_slots, const npw_params* params) {
     if (!params || heap_cells < 1 || max_slots < 1) return 0;
-    return server_layout(heap_cells, max_slots, elem_size(params)).total;
+    return server_bytes(heap_cells, max_slots);
 }
 
 npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max_slots, const npw_params* params,
@@ -1961,32 +2061,43 @@ npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max
     if (st) return st;
     if (!device_arena || !out || max_slots < 1 || max_slots > (1 << 20)) return fail(NPW_EINVAL, "bad server arguments");
     if (params->characteristic) return fail(NPW_EINVAL, "the server runs component-wise reconstruction");
-    const size_t esz = elem_size(params);
-    // largest heap that fits the arena
-    int64_t lo = 0, hi = (int64_t)(arena_bytes / (3 * esz)) + 1;
+    // largest heap (per lane) that fits the arena
+    int64_t lo = 0, hi = (int64_t)(arena_bytes / 44) + 1;
     while (hi - lo > 1) {
         const int64_t mid = lo + (hi - lo) / 2;
-        if (server_layout(mid, max_slots, esz).total <= arena_bytes)
+        if (server_bytes(mid, max_slots) <= arena_bytes)
             lo = mid;
         else
             hi = mid;
     }
-    if (lo < 6) return fail(NPW_EINVAL, "arena too small for a server with %d slots", max_slots);
+    if (lo < 36) return fail(NPW_EINVAL, "arena too small for a server with %d slots", max_slots);
     npw_server* sv = new (std::nothrow) npw_server();
     if (!sv) return fail(NPW_ENOMEM, "host allocation of the server failed");
     sv->params = *params;
-    sv->mp = method(params);
-    sv->fp32 = params->precision == NPW_FP32_MIXED;
-    sv->comp = compensated(params);
-    sv->esz = esz;
     sv->max_slots = max_slots;
     sv->s = reinterpret_cast<cudaStream_t>(stream);
     sv->arena = static_cast<unsigned char*>(device_arena);
     sv->heap_cells = lo;
-    sv->L = server_layout(lo, max_slots, esz);
+    for (int ln = 0; ln < 2; ++ln) {
+        npw_server::Lane& lane = sv->lanes[ln];
+        npw_params pl = *params;
+        pl.precision = ln == 0 ? NPW_FP32_MIXED : NPW_FP64;
+        pl.batch_mode = 1;
+        lane.mp = method(&pl);
+        lane.fp32 = ln == 0;
+        lane.esz = ln == 0 ? sizeof(float) : sizeof(double);
+        lane.L = ln == 0 ? lane_layout(0, lo, max_slots, sizeof(float), true)
+                         : lane_layout(sv->lanes[0].L.end, lo, max_slots, sizeof(double), false);
+        lane.free_ranges.push_back({0, lo});
+        lane.host_ctl.resize(max_slots);
+        // zero the queue counters once; every launch leaves them zero
+        cudaError_t e = cudaMemsetAsync(sv->arena + lane.L.head, 0, 2 * sizeof(unsigned int), sv->s);
+        if (e != cudaSuccess) {
+            delete sv;
+            return cuda_fail(e, "cudaMemsetAsync");
+        }
+    }
     sv->slots.resize(max_slots);
-    sv->host_ctl.resize(max_slots);
-    sv->free_ranges.push_back({0, lo});
     sv->t0 = std::chrono::steady_clock::now();
     *out = sv;
     return NPW_OK;
@@ -2006,13 +2117,12 @@ npw_status npw_server_submit(npw_server* sv, const npw_request* req, uint64_t* i
     npw_status st = check_bc(req->bc);
     if (st) return st;
     if (req->n < 6 || req->n > ((int64_t)1 << 30) || !(req->dx > 0.0) || !(req->cfl > 0.0) || !req->u0_host ||
-        !req->out_host)
+        !req->out_host || !(req->tolerance >= 0.0))
         return fail(NPW_EINVAL, "malformed request");
     if (is2d) {
         if (req->ny < 6 || req->ny > ((int64_t)1 << 30) || !(req->dy > 0.0))
             return fail(NPW_EINVAL, "malformed 2D request (ny >= 6, dy > 0)");
         if (req->bc_y >= 0 && (st = check_bc(req->bc_y))) return st;
-        if (sv->params.characteristic) return fail(NPW_EINVAL, "2D requests are component-wise");
     }
     const int m = flux_m(req->flux_kind);
     const int64_t cells = req->n * m * (is2d ? req->ny : 1);
@@ -2027,10 +2137,12 @@ npw_status npw_server_submit(npw_server* sv, const npw_request* req, uint64_t* i
 npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, int32_t* queued) {
     if (!sv || max_steps < 1) return fail(NPW_EINVAL, "bad server step arguments");
     npw_status st = NPW_OK;
-    // 1. admit, first in first out
-    std::vector<int32_t> fresh;
+    // 1. admit, first in first out: a free slot and space in the request's lane
+    std::vector<int> fresh;
     while (!sv->queue.empty()) {
         const npw_server::Pending& p = sv->queue.front();
+        const int ln = sv->lane_of(p.req);
+        npw_server::Lane& lane = sv->lanes[ln];
         const int m = flux_m(p.req.flux_kind);
         const bool is2d = p.req.ny != 0;
         const int64_t cells = p.req.n * m * (is2d ? p.req.ny : 1);
@@ -2041,14 +2153,16 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
                 break;
             }
         int64_t off = 0;
-        if (slot < 0 || !sv->heap_alloc(cells, &off)) break;
-        NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.heap_u + (size_t)off * sv->esz, p.req.u0_host,
-                                 (size_t)cells * sv->esz, cudaMemcpyHostToDevice, sv->s));
+        if (slot < 0 || !lane.heap_alloc(cells, &off)) break;
+        // the request's host values are of its lane's element type
+        NPW_CUDA(cudaMemcpyAsync(sv->arena + lane.L.heap_u + (size_t)off * lane.esz, p.req.u0_host,
+                                 (size_t)cells * lane.esz, cudaMemcpyHostToDevice, sv->s));
         npw_server::Slot& sl = sv->slots[slot];
         sl.used = true;
         sl.fresh = true;
         sl.id = p.id;
         sl.req = p.req;
+        sl.lane = ln;
         sl.m = m;
         sl.is2d = is2d;
         sl.cells = cells;
@@ -2058,139 +2172,36 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
         fresh.push_back(slot);
         sv->queue.pop_front();
     }
-    // 2. instance and tile tables of the admitted requests (grouped by flux kind)
-    std::vector<npw::InstDev> hi(sv->max_slots);
-    std::vector<npw::Tile> tiles, newtiles;
-    std::vector<int> kind_tiles(3, 0);
-    std::vector<size_t> kind_off(3, 0);
-    int n_active = 0;
-    for (int kind = 0; kind < 3; ++kind) {
-        kind_off[kind] = tiles.size();
-        for (int k = 0; k < sv->max_slots; ++k) {
-            const npw_server::Slot& sl = sv->slots[k];
-            if (!sl.used || sl.is2d || sl.req.flux_kind != kind) continue;
-            npw::InstDev& d = hi[k];
-            d.off = sl.off;
-            d.n = sl.req.n;
-            d.dx = sl.req.dx;
-            d.t_end = sl.req.t_end;
-            d.cfl = sl.req.cfl;
-            d.bc = sl.req.bc;
-            d.ntiles = (int32_t)tiles_of(sl.req.n, npw::TILE_1D);
-            for (int64_t t = 0; t < d.ntiles; ++t) {
-                tiles.push_back(npw::Tile{k, (int32_t)(t * npw::TILE_1D)});
-                if (sl.fresh) newtiles.push_back(npw::Tile{k, (int32_t)(t * npw::TILE_1D)});
-            }
-            ++n_active;
-        }
-        kind_tiles[kind] = (int)(tiles.size() - kind_off[kind]);
+    // 2. advance every admitted request of each lane (a smaller round when nothing was admitted
+    // and every active request is close to its end)
+    int steps = max_steps;
+    if (fresh.empty() && sv->remaining_hint > 0 && sv->remaining_hint < steps) steps = (int)sv->remaining_hint;
+    bool any = false;
+    for (int ln = 0; ln < 2; ++ln) {
+        bool a = false;
+        if ((st = lane_round(sv, ln, steps, &a))) return st;
+        any |= a;
     }
-    std::vector<int> slots2d, fresh1d, fresh2d;
-    for (int k = 0; k < sv->max_slots; ++k)
-        if (sv->slots[k].used && sv->slots[k].is2d) {
-            slots2d.push_back(k);
-            ++n_active;
-        }
-    for (int k : fresh) (sv->slots[k].is2d ? fresh2d : fresh1d).push_back(k);
-    if (n_active == 0) {
+    for (int k : fresh) sv->slots[k].fresh = false;
+    if (!any) {
         if (active) *active = 0;
         if (queued) *queued = (int32_t)sv->queue.size();
         return NPW_OK;
     }
-    NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.inst, hi.data(), sizeof(npw::InstDev) * hi.size(),
-                             cudaMemcpyHostToDevice, sv->s));
-    if (!tiles.empty())
-        NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.tiles, tiles.data(), sizeof(npw::Tile) * tiles.size(),
-                                 cudaMemcpyHostToDevice, sv->s));
-    npw::Ctl* ctl = reinterpret_cast<npw::Ctl*>(sv->arena + sv->L.ctl);
-    const npw::InstDev* dinst = reinterpret_cast<const npw::InstDev*>(sv->arena + sv->L.inst);
-    // 3. start the admitted requests: reset, alpha^0 over their tiles, first dt
-    for (int k : fresh2d) {  // 2D: the start sequence of npweno_solve_2d on the request's own words
-        const npw_server::Slot& sl = sv->slots[k];
-        npw::Inst2D h2{};
-        h2.off = sl.off;
-        h2.nx = sl.req.n;
-        h2.ny = sl.req.ny;
-        h2.dx = sl.req.dx;
-        h2.dy = sl.req.dy;
-        h2.t_end = sl.req.t_end;
-        h2.cfl = sl.req.cfl;
-        h2.bc = sl.req.bc;
-        h2.bc_y = sl.req.bc_y < 0 ? sl.req.bc : sl.req.bc_y;
-        h2.tiles_x = (int32_t)((sl.req.n + npw::TX_2D - 1) / npw::TX_2D);
-        h2.tiles_y = (int32_t)((sl.req.ny + npw::TY_2D - 1) / npw::TY_2D);
-        npw::Inst2D* d2 = reinterpret_cast<npw::Inst2D*>(sv->arena + sv->L.inst2d) + k;
-        NPW_CUDA(cudaMemcpyAsync(d2, &h2, sizeof h2, cudaMemcpyHostToDevice, sv->s));
-        npw::ctl_start_2d_kernel<<<1, 32, 0, sv->s>>>(ctl + k, d2, 0, 0.0, 0);
-        NPW_CUDA(cudaGetLastError());
-        cudaError_t ce = sv->fp32 ? npw::launch_alpha_init_2d<float>(sv->arena + sv->L.heap_u, d2, sv->tiles2d(k),
-                                                                      ctl + k, sl.req.flux_kind, sv->mp, sv->s)
-                                  : npw::launch_alpha_init_2d<double>(sv->arena + sv->L.heap_u, d2, sv->tiles2d(k),
-                                                                       ctl + k, sl.req.flux_kind, sv->mp, sv->s);
-        if (ce != cudaSuccess) return cuda_fail(ce, "server alpha 2d launch");
-        npw::ctl_start_2d_kernel<<<1, 32, 0, sv->s>>>(ctl + k, d2, 1, 0.0, sv->mp.max_steps);
-        NPW_CUDA(cudaGetLastError());
-        count_launch(3);
-    }
-    if (!fresh1d.empty()) {
-        const std::vector<int32_t> fresh(fresh1d.begin(), fresh1d.end());
-        int32_t* dlist = reinterpret_cast<int32_t*>(sv->arena + sv->L.list);
-        NPW_CUDA(cudaMemcpyAsync(dlist, fresh.data(), sizeof(int32_t) * fresh.size(), cudaMemcpyHostToDevice, sv->s));
-        NPW_CUDA(cudaMemcpyAsync(sv->arena + sv->L.newtiles, newtiles.data(), sizeof(npw::Tile) * newtiles.size(),
-                                 cudaMemcpyHostToDevice, sv->s));
-        const unsigned blocks = (unsigned)((fresh.size() + 127) / 128);
-        npw::ctl_slots_kernel<<<blocks, 128, 0, sv->s>>>(ctl, dinst, dlist, (int)fresh.size(), 0, 0);
-        NPW_CUDA(cudaGetLastError());
-        // alpha^0 per fresh request, one launch per flux kind over its fresh tiles
-        size_t b = 0;
-        while (b < newtiles.size()) {
-            const int kind = sv->slots[newtiles[b].inst].req.flux_kind;
-            size_t e = b;
-            while (e < newtiles.size() && sv->slots[newtiles[e].inst].req.flux_kind == kind) ++e;
-            const npw::Tile* tl = reinterpret_cast<const npw::Tile*>(sv->arena + sv->L.newtiles) + b;
-            cudaError_t ce = sv->fp32 ? npw::launch_alpha_init<float>(sv->arena + sv->L.heap_u, dinst, ctl, tl, (int)(e - b),
-                                                                       npw::TILE_1D, flux_m(kind), kind, sv->mp, sv->s)
-                                      : npw::launch_alpha_init<double>(sv->arena + sv->L.heap_u, dinst, ctl, tl, (int)(e - b),
-                                                                        npw::TILE_1D, flux_m(kind), kind, sv->mp, sv->s);
-            if (ce != cudaSuccess) return cuda_fail(ce, "server alpha launch");
-            count_launch();
-            b = e;
-        }
-        npw::ctl_slots_kernel<<<blocks, 128, 0, sv->s>>>(ctl, dinst, dlist, (int)fresh.size(), 1, sv->mp.max_steps);
-        NPW_CUDA(cudaGetLastError());
-        count_launch(2);
-        if (sv->comp) {  // compensated float kernels: s = u, c = 0 for the admitted requests
-            for (size_t b2 = 0; b2 < newtiles.size();) {
-                const int kind = sv->slots[newtiles[b2].inst].req.flux_kind;
-                size_t e2 = b2;
-                while (e2 < newtiles.size() && sv->slots[newtiles[e2].inst].req.flux_kind == kind) ++e2;
-                NPW_CUDA(npw::launch_comp_begin(reinterpret_cast<const float*>(sv->arena + sv->L.heap_u),
-                                                reinterpret_cast<float*>(sv->arena + sv->L.heap_s),
-                                                reinterpret_cast<float*>(sv->arena + sv->L.heap_c), dinst,
-                                                reinterpret_cast<const npw::Tile*>(sv->arena + sv->L.newtiles) + b2,
-                                                (int)(e2 - b2), npw::TILE_1D, flux_m(kind), sv->s));
-                count_launch();
-                b2 = e2;
-            }
-        }
-    }
-    for (int k : fresh) sv->slots[k].fresh = false;
-    // 4. advance everything admitted
-    int steps = max_steps;
-    if (fresh.empty() && sv->remaining_hint > 0 && sv->remaining_hint < steps) steps = (int)sv->remaining_hint;
-    st = sv->fp32 ? server_launch_steps<float>(sv, kind_tiles, kind_off, slots2d, steps)
-                  : server_launch_steps<double>(sv, kind_tiles, kind_off, slots2d, steps);
-    if (st) return st;
-    // 5. read the control words, retire finished requests
+    // 3. read the control words, retire finished requests
     if ((st = bounded_sync(sv->s))) return st;
-    NPW_CUDA(cudaMemcpyAsync(sv->host_ctl.data(), ctl, sizeof(npw::Ctl) * sv->max_slots, cudaMemcpyDeviceToHost, sv->s));
+    for (int ln = 0; ln < 2; ++ln)
+        NPW_CUDA(cudaMemcpyAsync(sv->lanes[ln].host_ctl.data(), sv->arena + sv->lanes[ln].L.ctl,
+                                 sizeof(npw::Ctl) * sv->max_slots, cudaMemcpyDeviceToHost, sv->s));
     profile_collect();
     std::vector<int> finished;
     long long rem = 0;
+    int n_active = 0;
     for (int k = 0; k < sv->max_slots; ++k) {
         const npw_server::Slot& sl = sv->slots[k];
         if (!sl.used) continue;
-        const npw::Ctl& c = sv->host_ctl[k];
+        const npw::Ctl& c = sv->lanes[sl.lane].host_ctl[k];
+        ++n_active;
         if (c.done) {
             finished.push_back(k);
         } else {
@@ -2200,28 +2211,30 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
         }
     }
     sv->remaining_hint = rem;
-    for (int k : finished) {  // the compensated 1D float kernels leave the final state in s
+    for (int k : finished) {  // the compensated 1D float items leave the final state in s
         const npw_server::Slot& sl = sv->slots[k];
-        const size_t region = (sv->comp && !sl.is2d) ? sv->L.heap_s : sv->L.heap_u;
-        NPW_CUDA(cudaMemcpyAsync(sl.req.out_host, sv->arena + region + (size_t)sl.off * sv->esz,
-                                 (size_t)sl.cells * sv->esz, cudaMemcpyDeviceToHost, sv->s));
+        const npw_server::Lane& lane = sv->lanes[sl.lane];
+        const size_t region = (lane.fp32 && !sl.is2d) ? lane.L.heap_s : lane.L.heap_u;
+        NPW_CUDA(cudaMemcpyAsync(sl.req.out_host, sv->arena + region + (size_t)sl.off * lane.esz,
+                                 (size_t)sl.cells * lane.esz, cudaMemcpyDeviceToHost, sv->s));
     }
     if (!finished.empty() && (st = bounded_sync(sv->s))) return st;
     const double tdone = now_s(sv->t0);
     for (int k : finished) {
         npw_server::Slot& sl = sv->slots[k];
-        const npw::Ctl& c = sv->host_ctl[k];
+        const npw::Ctl& c = sv->lanes[sl.lane].host_ctl[k];
         npw_result r{};
         r.id = sl.id;
         r.tag = sl.req.tag;
         r.status = c.status;
+        r.precision = sl.lane == 0 ? NPW_FP32_MIXED : NPW_FP64;
         r.steps = c.steps;
         r.t = c.t;
         r.submit_s = sl.submit_s;
         r.admit_s = sl.admit_s;
         r.done_s = tdone;
         sv->results.push_back(r);
-        sv->heap_free(sl.off, sl.cells);
+        sv->lanes[sl.lane].heap_free(sl.off, sl.cells);
         sl.used = false;
     }
     if (active) *active = n_active - (int32_t)finished.size();

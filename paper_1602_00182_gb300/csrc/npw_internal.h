@@ -256,8 +256,8 @@ size_t resident_smem_bytes(int64_t n, int m);
 npw_status set_error(npw_status st, const char* msg);
 
 // precision-independent helpers (npw_api.cu)
-cudaError_t launch_queue_ctl(Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d, int count,
-                             int mode, int64_t max_steps, cudaStream_t s);
+cudaError_t launch_queue_ctl(Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d,
+                             const int32_t* list, int count, int mode, int64_t max_steps, cudaStream_t s);
 cudaError_t launch_queue_poll(const Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d,
                               int count, long long* poll, cudaStream_t s);
 // compensated float path: before the first step s = u and c = 0; after the last, u = s

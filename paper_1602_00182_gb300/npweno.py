@@ -436,13 +436,16 @@ class npw_request(C.Structure):
     _fields_ = [("flux_kind", C.c_int32), ("bc", C.c_int32), ("n", C.c_int64), ("dx", C.c_double),
                 ("t_end", C.c_double), ("cfl", C.c_double), ("u0_host", C.c_void_p), ("out_host", C.c_void_p),
                 ("tag", C.c_uint64), ("ny", C.c_int64), ("dy", C.c_double), ("bc_y", C.c_int32),
-                ("reserved_", C.c_int32)]
+                ("reserved_", C.c_int32), ("tolerance", C.c_double)]
 
 
 class npw_result(C.Structure):
-    _fields_ = [("id", C.c_uint64), ("tag", C.c_uint64), ("status", C.c_int32), ("pad_", C.c_int32),
+    _fields_ = [("id", C.c_uint64), ("tag", C.c_uint64), ("status", C.c_int32), ("precision", C.c_int32),
                 ("steps", C.c_int64), ("t", C.c_double), ("submit_s", C.c_double), ("admit_s", C.c_double),
                 ("done_s", C.c_double)]
+
+
+MIXED_TOLERANCE = 1e-4  # requests with a tolerance at least this large take the mixed-precision lane
 
 
 def _server_protos(lib):
@@ -466,7 +469,9 @@ def _server_protos(lib):
 
 class Server:
     """npw_server_*: continuous batching of 1D and 2D solves on one device arena (allocated here
-    with torch, owned by this object).  Host arrays of each request are kept alive until polled."""
+    with torch, owned by this object), one lane per precision: a request's tolerance picks its
+    lane (>= MIXED_TOLERANCE: NPW_FP32_MIXED, below: NPW_FP64, 0: params.precision).  Host
+    arrays of each request are kept alive until polled."""
 
     def __init__(self, heap_cells: int, max_slots: int, params: Params, device=None):
         torch = _torch()
@@ -482,20 +487,27 @@ class Server:
                                      C.c_void_p(self.stream.cuda_stream), C.byref(h)))
         self._h = h
         self._keep = {}
-        self._np_dtype = "float32" if params.precision == NPW_FP32_MIXED else "float64"
+
+    def lane_precision(self, tolerance: float) -> int:
+        if tolerance > 0.0:
+            return NPW_FP32_MIXED if tolerance >= MIXED_TOLERANCE else NPW_FP64
+        return self.params.precision
 
     def submit(self, u0, flux_kind: int, bc: int, dx: float, t_end: float, cfl: float, tag: int = 0,
-               dy: float = 0.0, bc_y: int = -1) -> int:
-        """1D: u0 is [m][n] (or [n]); 2D (dy > 0): u0 is [m][ny][nx] (or [ny][nx])."""
+               dy: float = 0.0, bc_y: int = -1, tolerance: float = 0.0) -> int:
+        """1D: u0 is [m][n] (or [n]); 2D (dy > 0): u0 is [m][ny][nx] (or [ny][nx]).  tolerance
+        picks the precision lane (0: the server's precision)."""
         import numpy as np
-        a = np.ascontiguousarray(np.asarray(u0, dtype=self._np_dtype))
+        dtype = "float32" if self.lane_precision(tolerance) == NPW_FP32_MIXED else "float64"
+        a = np.ascontiguousarray(np.asarray(u0, dtype=dtype))
         m = {NPW_FLUX_EULER1D: 3, NPW_FLUX_EULER2D: 4}.get(flux_kind, 1)
         if dy > 0.0:
             ny, n = a.shape[-2], a.shape[-1]
         else:
             ny, n = 0, a.size // m
         out = np.empty_like(a)
-        r = npw_request(flux_kind, bc, n, dx, t_end, cfl, a.ctypes.data, out.ctypes.data, tag, ny, dy, bc_y, 0)
+        r = npw_request(flux_kind, bc, n, dx, t_end, cfl, a.ctypes.data, out.ctypes.data, tag, ny, dy, bc_y, 0,
+                        float(tolerance))
         rid = C.c_uint64(0)
         _check(load().npw_server_submit(self._h, C.byref(r), C.byref(rid)))
         self._keep[rid.value] = (a, out)
@@ -514,8 +526,8 @@ class Server:
         for k in range(nout.value):
             r = buf[k]
             a, res = self._keep.pop(r.id)
-            out.append(dict(id=r.id, tag=r.tag, status=r.status, steps=r.steps, t=r.t, submit_s=r.submit_s,
-                            admit_s=r.admit_s, done_s=r.done_s, u=res))
+            out.append(dict(id=r.id, tag=r.tag, status=r.status, precision=r.precision, steps=r.steps, t=r.t,
+                            submit_s=r.submit_s, admit_s=r.admit_s, done_s=r.done_s, u=res))
         return out
 
     def close(self):

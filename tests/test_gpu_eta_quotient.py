@@ -127,8 +127,10 @@ def test_mixed_eta_is_the_rounded_exact_quotient(npw, k, eta_eval, rbf):
     normal = fin & (np.abs(q) >= F32_MIN_NORMAL) & (np.abs(q) < 3e38)
     err = np.abs(geta[normal] - q[normal])
     ulp = _ulp32(q[normal])
-    unit = 2.0 ** -52 if eta_eval == 0 else 2.0 ** -44  # FP64 evaluation / float pairs (with margin)
-    bound = 0.5 * ulp + np.abs(q[normal]) * (unit * (kap[normal] + 5.0) + 2.0 ** -40)
+    # eta_eval 0: the FP64 evaluation, rounded once (0.5 ulp); eta_eval 1: float pairs and a
+    # double-float quotient, within one ulp (not correctly rounded)
+    unit, last = (2.0 ** -52, 0.5) if eta_eval == 0 else (2.0 ** -44, 1.0)
+    bound = last * ulp + np.abs(q[normal]) * (unit * (kap[normal] + 5.0) + 2.0 ** -40)
     worst = float((err / bound).max())
     well = kap[normal] < 2.0 ** 20  # no strong cancellation: the bound is below one ulp
     exact = float(np.mean(err[well] <= 0.5 * ulp[well] * (1 + 2.0 ** -20)))

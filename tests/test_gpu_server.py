@@ -207,3 +207,45 @@ def test_2d_request_validation(npw):
     with pytest.raises(npw.NpwError):  # bad y boundary
         srv.submit(u, npw.NPW_FLUX_EULER2D, 0, 0.1, 0.1, 0.4, dy=0.1, bc_y=9)
     srv.close()
+
+
+def test_per_request_precision_lanes(npw):
+    """One server, requests of both tolerance classes interleaved: the loose ones run in the
+    mixed lane, the strict ones in the FP64 lane, each equal bit for bit to the solve of the same
+    request in its precision (npweno_batch_solve with the per-stage kernels, npweno_solve_2d), and
+    the FP64 ones match the oracle."""
+    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, batch_mode=1)
+    burg = I.burgers_batch(count=6, nmin=100, nmax=3000, seed_index=13)
+    U, d = I.euler2d_batch(40, 1, seed_index=14)[0]
+    srv = npw.Server(heap_cells=40000, max_slots=12, params=p)
+    tols = [1e-3, 1e-10, 0.0, 1e-8, 5e-4, 1e-12]
+    for k, (it, tol) in enumerate(zip(burg, tols)):
+        srv.submit(it.u0[0], npw.NPW_FLUX_BURGERS, 0, it.dx, 0.3, 0.5, tag=k, tolerance=tol)
+        srv.step(3)
+    srv.submit(U, npw.NPW_FLUX_EULER2D, 0, d, 0.2, 0.4, tag=50, dy=d, tolerance=1e-10)
+    srv.submit(U, npw.NPW_FLUX_EULER2D, 0, d, 0.2, 0.4, tag=51, dy=d, tolerance=1e-3)
+    res = {r["tag"]: r for r in srv.poll() + _drain(srv, max_steps=5)}
+    srv.close()
+    assert len(res) == 8 and all(r["status"] == 0 for r in res.values())
+    for k, (it, tol) in enumerate(zip(burg, tols)):
+        r = res[k]
+        prec = npw.NPW_FP32_MIXED if (tol == 0.0 or tol >= 1e-4) else npw.NPW_FP64
+        assert r["precision"] == prec
+        pk = npw.Params(rbf=npw.NPW_RBF_GA, precision=prec, batch_mode=1)
+        table, _ = npw.make_instances([it.n], [it.dx], [0.3], [0.5], [0])
+        dt = torch.float32 if prec == npw.NPW_FP32_MIXED else torch.float64
+        arena = torch.tensor(it.u0[0], dtype=dt, device="cuda")
+        st, stats = npw.npweno_batch_solve(arena, table, 1, npw.NPW_FLUX_BURGERS, pk)
+        assert st == 0 and stats[0]["steps"] == r["steps"]
+        assert np.array_equal(arena.cpu().numpy(), r["u"])
+        if prec == npw.NPW_FP64:
+            ref, rst = O.solve(it.u0[0], it.dx, 0.3, 0.5, O.BURGERS, O.PERIODIC, O.Params(rbf=O.GA))
+            assert rst["steps"] == r["steps"] and np.abs(r["u"] - ref).max() <= 1e-11 * np.abs(ref).max()
+    for tag, prec in ((50, npw.NPW_FP64), (51, npw.NPW_FP32_MIXED)):
+        r = res[tag]
+        assert r["precision"] == prec
+        dt = torch.float32 if prec == npw.NPW_FP32_MIXED else torch.float64
+        u = torch.tensor(U, dtype=dt, device="cuda")
+        st = npw.npweno_solve_2d(u, d, d, 0.2, 0.4, npw.NPW_FLUX_EULER2D, 0,
+                                 npw.Params(rbf=npw.NPW_RBF_GA, precision=prec))
+        assert st["steps"] == r["steps"] and np.array_equal(u.cpu().numpy(), r["u"])
