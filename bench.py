@@ -61,9 +61,9 @@ BYTES_SCALAR_F32 = 32
 BYTES_EULER1D_F32 = 96
 BYTES_EULER2D_F32 = 128
 BYTES_SCALAR_F64 = 64
-# FP64-pipe instructions of one shape-parameter evaluation in the mixed path (k = 3): 2 adds
-# (the differences a, b), 2 multiply-adds (numerator, denominator), 1 add (eps_M), 1 multiply
-# and 2 multiply-adds (the Newton quotient)
+# FP64-pipe instructions of one shape-parameter evaluation in the mixed path with eta_eval 1
+# (k = 3): 2 adds (the differences a, b), 2 multiply-adds (numerator, denominator), 1 add
+# (eps_M), 1 multiply and 2 multiply-adds (the Newton quotient); the default eta_eval 0 uses none
 FP64_OPS_PER_ETA = 8
 # FP64 pipe: 2 instructions per clock per SM (1.25 TFLOP/s nominal FP64 over 152 SMs at 2.07 GHz)
 FP64_PIPE_PEAK = 2.0 * 152 * 2.07e9
@@ -258,15 +258,18 @@ def headline_burgers(args, rank, world, local_rank):
     cu_a = sum(ns[k] * stats[k]["steps"] for k in big) * args.steps
     faces_a = sum((ns[k] + 1) * 3 * stats[k]["steps"] for k in big) * args.steps
     res_s = pr.resident_ms[0] / 1e3
-    fp64 = FP64_OPS_PER_ETA * faces_a / res_s / 1e9 if res_s > 0 else None
+    secondary = {"hbm_bytes_actually_moved": "8 B per cell per solve: the state stays in shared memory"}
+    if args.eta_eval == 1 and res_s > 0:
+        fp64 = FP64_OPS_PER_ETA * faces_a / res_s / 1e9
+        secondary["fp64_pipe"] = {"achieved": fp64, "peak": FP64_PIPE_PEAK / 1e9, "unit": "G FP64-pipe instr/s",
+                                  "frac": fp64 / (FP64_PIPE_PEAK / 1e9),
+                                  "count": f"{FP64_OPS_PER_ETA} per face and stage (eta), all n+1 faces"}
+    else:
+        secondary["fp64_pipe"] = "no FP64 instruction on the common path (eta from float pairs)"
     roof = roofline_hbm(BYTES_SCALAR_F32, cu_a, res_s,
                         "solve1d_resident_kernel<BURGERS, 3>, size class n > 4096 (512 threads, 2 CTAs/SM)",
                         traffic=_ncu_traffic("solve1d_resident_burgers_classA_dram_bytes_per_launch"),
-                        secondary={
-                            "fp64_pipe": {"achieved": fp64, "peak": FP64_PIPE_PEAK / 1e9, "unit": "G FP64-pipe instr/s",
-                                          "frac": (fp64 / (FP64_PIPE_PEAK / 1e9)) if fp64 else None,
-                                          "count": f"{FP64_OPS_PER_ETA} per face and stage (eta), all n+1 faces"},
-                            "hbm_bytes_actually_moved": "8 B per cell per solve: the state stays in shared memory"},
+                        secondary=secondary,
                         resident_launches=[int(x) for x in pr.resident_launches],
                         resident_ms=[float(x) for x in pr.resident_ms],
                         kernel_source_sha256=kernel_source_hash())
@@ -309,7 +312,7 @@ def headline_burgers(args, rank, world, local_rank):
 
     if args.variant_steps > 0 and args.eta_eval == 0 and world == 1:
         time_variant(npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, eta_eval=1),
-                     "eta_eval=1 (double-float eta, no FP64 instruction)")
+                     f"eta_eval=1 (eta in FP64, {FP64_OPS_PER_ETA} FP64-pipe instructions per face and stage)")
         time_variant(npw.Params(k=2, rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, eta_max=1.0),
                      "k=2 RBF-WENO3 Gaussian + switch (Table k2; resident kernels, eta in FP64), |eta| <= 1 "
                      "(the printed k = 2 eta is singular where u crosses zero)")
@@ -333,8 +336,10 @@ def headline_burgers(args, rank, world, local_rank):
             "instances": len(ns),
             "cells": int(sum(ns)),
             "cell_updates_per_step": int(cell_updates),
-            "precision": ("NPW_FP32_MIXED: f32 state, candidates, beta, weights, flux, update; eta in FP64 "
-                          f"(eta_eval={args.eta_eval}); switch decisions equal to FP64 evaluation; eta as printed "
+            "precision": ("NPW_FP32_MIXED: f32 state, candidates, beta, weights, flux, update; eta "
+                          + ("from exact differences as float pairs, double-float quotient" if args.eta_eval == 0
+                             else "in FP64") +
+                          f" (eta_eval={args.eta_eval}); switch decisions equal to FP64 evaluation; eta as printed "
                           "(no bound)"),
             "l2": "flushed (256 MB write) before every timed step; working set 3 x 4 B x cells",
             "parallelism": f"independent instance batches, one per rank (x{world})",
@@ -855,7 +860,8 @@ def main():
     ap.add_argument("--steps2d", type=int, default=100, help="2D Euler block: RK3 steps per solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eta-eval", type=int, default=0, choices=[0, 1],
-                    help="0: eta in FP64 (the configuration's FP64 shape-parameter step); 1: double-float")
+                    help="mixed path: 0 = eta from float pairs, double-float quotient (the library default); "
+                         "1 = eta in FP64")
     ap.add_argument("--serve-requests", type=int, default=60, help="requests of the serving run")
     ap.add_argument("--serve-rates", default="10,100,1000", help="Poisson arrival rates of the serving runs (1/s)")
     ap.add_argument("--variant-steps", type=int, default=1,

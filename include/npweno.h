@@ -56,8 +56,9 @@ typedef enum { NPW_BC_PERIODIC = 0, NPW_BC_TRANSMISSIVE = 1, NPW_BC_INFLOW = 2 }
 typedef enum { NPW_ENO = 0, NPW_WENO_JS = 1, NPW_RBF_ENO = 2, NPW_RBF_WENO = 3 } npw_scheme;
 typedef enum { NPW_RBF_MQ = 0, NPW_RBF_GA = 1 } npw_rbf;
 /* NPW_FP64: everything in double.  NPW_FP32_MIXED: float state, candidates, WENO weights and
- * smoothness indicators, flux and update; the shape parameter eta is evaluated in FP64 (see
- * eta_eval), and the monotone-switch and ENO decisions are those of FP64 evaluation (taken from
+ * smoothness indicators, flux and update; the shape parameter eta is evaluated from exact
+ * differences in extended precision (see eta_eval), and the monotone-switch and ENO decisions
+ * are those of FP64 evaluation (taken from
  * float values with a certified error bound, recomputed in double when the bound does not
  * decide them). */
 typedef enum { NPW_FP64 = 0, NPW_FP32_MIXED = 1 } npw_precision;
@@ -72,11 +73,13 @@ typedef struct {
     int32_t switch_variant;  /* 0: cubic on the 4-cell eta stencil; 1: eq. root_value on both 3-cell halves */
     int32_t characteristic;  /* 1D Euler only: reconstruct Roe characteristic fields */
     int32_t precision;       /* npw_precision */
-    int32_t eta_eval;        /* NPW_FP32_MIXED only: 0 = eta in FP64 (numerator and denominator formed
-                                exactly as float pairs and summed in FP64, Newton-Raphson quotient in
-                                FP64, within 2^-42 before rounding to float); 1 = from the same numerator
-                                and denominator held as float pairs, double-float quotient (no FP64
-                                instruction, ~2^-46 relative before rounding to float) */
+    int32_t eta_eval;        /* NPW_FP32_MIXED, k = 3: 0 = eta from the exact differences a = w0 - w3,
+                                b = w2 - w1 held as float pairs, double-float quotient (no FP64
+                                instruction; within one float ulp plus ~2^-44 of the conditioning
+                                (|a| + 3|b|) / |num| + (|a| + 15|b|) / |den|); 1 = in FP64 (numerator
+                                and denominator from the widened averages by FP64 differences and
+                                multiply-adds, Newton quotient; within half an ulp plus 2^-52 of the
+                                conditioning).  k = 2 always takes the FP64 form. */
     double eps_M;            /* additive guard of the eta denominator (Table k3), e.g. 1e-12 */
     double eps_weno;         /* WENO epsilon of Sec. 2, 1e-6 */
     double gamma;            /* ratio of specific heats, 1.4 */

@@ -9,8 +9,8 @@ Paper passages followed (see npw_oracle.c for the per-routine citations):
 Sec. 2 (cell averages, stencils, WENO combination eq. weno_re), Sec. 3.5 Table k3
 (coefficients and eta; the printed 6/11 is read as 11/6), Sec. 3.3 (Gaussian recipe, k=3
 rows derived), Sec. 4 (monotone switch eq. root_value / eq. adaptation), Sec. 5.1 (eq. PDE1,
-Lax-Friedrichs flux, TVD-RK3), Sec. 5.2 Example 4 (Euler), Sec. 7 (eq. 2DIntegral, midpoint
-quadrature).
+Lax-Friedrichs flux, TVD-RK3), Sec. 5.2 Example 4 (Euler), Sec. 6 (the 5-cell cross, at the
+midpoint or any point of a face), Sec. 7 (eq. 2DIntegral, midpoint or two-point Gauss quadrature).
 """
 from __future__ import annotations
 
@@ -45,7 +45,7 @@ class _Params(C.Structure):
     _fields_ = [
         ("scheme", C.c_int), ("rbf", C.c_int), ("monotone_switch", C.c_int), ("switch_variant", C.c_int),
         ("characteristic", C.c_int), ("k", C.c_int), ("cross_2d", C.c_int), ("bc_y", C.c_int),
-        ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
+        ("gauss_2d", C.c_int), ("eps_M", C.c_double), ("eps_weno", C.c_double), ("gamma", C.c_double),
         ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4),
         ("tie_tol", C.c_double), ("eta_guard", C.c_double), ("eta_max", C.c_double),
         ("counters", C.POINTER(C.c_long)),
@@ -68,6 +68,7 @@ class Params:
     k: int = 3
     cross_2d: int = 0
     bc_y: int = -1  # 2D: boundary of the y direction (-1: the same as the bc argument)
+    gauss_2d: int = 0  # 2D, k = 2: two Gauss points per face in eq. 2DIntegral (0: the midpoint)
     eps_M: float = 1e-12
     eps_weno: float = 1e-6
     gamma: float = 1.4
@@ -80,7 +81,7 @@ class Params:
 
     def _c(self) -> _Params:
         p = _Params()
-        for f in ("scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "k", "cross_2d", "bc_y"):
+        for f in ("scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "k", "cross_2d", "bc_y", "gauss_2d"):
             setattr(p, f, int(getattr(self, f)))
         for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "tie_tol", "eta_guard", "eta_max"):
             setattr(p, f, float(getattr(self, f)))
@@ -132,6 +133,9 @@ def lib():
         _lib.orc_eta_k2_cross.restype = d
         _lib.orc_eta_k2_cross.argtypes = [P(d), i, i, d, P(_Params)]
         _lib.orc_reconstruct_2d.argtypes = [P(d), l, l, i, i, P(_Params), P(d), P(d), P(d), P(d)]
+        _lib.orc_reconstruct_2d_at.argtypes = [P(d), l, l, i, i, P(_Params), d, P(d), P(d), P(d), P(d)]
+        _lib.orc_eta_k2_point.restype = d
+        _lib.orc_eta_k2_point.argtypes = [P(d), i, i, d, d, d, d, P(_Params)]
         _lib.orc_eno_choice.argtypes = [P(d), d, P(i)]
         _lib.orc_beta_k3.argtypes = [P(d), P(d)]
         _lib.orc_euler_eigvec.argtypes = [P(d), P(d), d, P(d), P(d)]
@@ -206,9 +210,25 @@ def eta_k2_cross(c3, side: int, central: bool, trans: float, params: "Params") -
     return lib().orc_eta_k2_cross(_dp(c), side, int(central), float(trans), C.byref(p))
 
 
-def reconstruct_2d(u, bc: int, params: "Params"):
-    """Face values of u [m][ny][nx] (or [ny][nx]): (vmx, vpx) [m][ny][nx+1] at the x faces and
-    (vmy, vpy) [m][ny+1][nx] at the y faces."""
+def eta_k2_point(c3, side: int, central: bool, trans: float, sg: float, xy: float, sigma: float,
+                 params: "Params") -> float:
+    """k = 2 shape parameter on the 5-cell cross (Sec. 6) at the point sigma (cell widths from
+    the face midpoint) of the face: sg = ENO side (+1 / -1) of the transverse neighbour, xy =
+    mixed difference with the cell across the face."""
+    c = _f64(c3)
+    p = params._c()
+    return lib().orc_eta_k2_point(_dp(c), side, int(central), float(trans), float(sg), float(xy), float(sigma),
+                                  C.byref(p))
+
+
+GAUSS2 = 0.28867513459481288225  # the two Gauss points of a face: +-1/(2 sqrt 3) cell widths
+
+
+def reconstruct_2d(u, bc: int, params: "Params", sigma: float = 0.0):
+    """Face values of u [m][ny][nx] (or [ny][nx]) at the point sigma of every face (cell widths
+    from the midpoint along the face, |sigma| <= 1/2; sigma != 0 needs k = 2): (vmx, vpx)
+    [m][ny][nx+1] at the x faces (points at y_j + sigma dy) and (vmy, vpy) [m][ny+1][nx] at the
+    y faces (x_i + sigma dx)."""
     u = _f64(u)
     squeeze = u.ndim == 2
     if squeeze:
@@ -217,8 +237,8 @@ def reconstruct_2d(u, bc: int, params: "Params"):
     vmx, vpx = np.zeros((m, ny, nx + 1)), np.zeros((m, ny, nx + 1))
     vmy, vpy = np.zeros((m, ny + 1, nx)), np.zeros((m, ny + 1, nx))
     p = params._c()
-    _check(lib().orc_reconstruct_2d(_dp(u), nx, ny, m, bc, C.byref(p), _dp(vmx), _dp(vpx), _dp(vmy), _dp(vpy)),
-           "reconstruct_2d")
+    _check(lib().orc_reconstruct_2d_at(_dp(u), nx, ny, m, bc, C.byref(p), float(sigma), _dp(vmx), _dp(vpx),
+                                       _dp(vmy), _dp(vpy)), "reconstruct_2d")
     if squeeze:
         return vmx[0], vpx[0], vmy[0], vpy[0]
     return vmx, vpx, vmy, vpy

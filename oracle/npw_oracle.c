@@ -34,8 +34,10 @@
  *   Sec. 6   2D perturbed reconstruction for k = 2 at a face midpoint (eq. rbf_recon_2d,
  *            eq. i+1/2_eps_2d, eq. i+1/2_eps_approx_2d): the shape parameter also cancels the
  *            transverse term v_yy dy^2 / 24 of the cell averages, using the 5-cell cross.
- *   Sec. 7   2D finite volume form (eq. 2DIntegral) with one midpoint quadrature point
- *            per cell boundary, applied dimension by dimension.
+ *            The same stencil and cancellation at any point of the face (cross_side).
+ *   Sec. 7   2D finite volume form (eq. 2DIntegral), applied dimension by dimension, with one
+ *            midpoint quadrature point per cell boundary (the paper's experiments) or the two
+ *            Gauss points that Sec. 7 names as needed for third order (gauss_2d).
  */
 #include <math.h>
 #include <stdint.h>
@@ -318,8 +320,9 @@ static double cell_face_value(const double c[5], int side, double eta, const orc
 /* One face, one field.  w[0..5] = cells i-2..i+3 around face i+1/2 (left cell i = w[2]). */
 /* Writes v^- (from cell i), v^+ (from cell i+1), the flag byte and eta.                  */
 /* ------------------------------------------------------------------------------------ */
+typedef struct cross_face_ cross_face;
 static void face_field_k2(const double w[6], const orc_params* p, const uint8_t* replay, double* vm, double* vp,
-                          uint8_t* flag, double* eta_out, double tl, double tr, uint8_t* reason);
+                          uint8_t* flag, double* eta_out, const cross_face* cf, uint8_t* reason);
 
 /* Counts of the shape-parameter decisions (orc_params.counters, optional): where the switch
  * set eta = 0, where eta was evaluated, and where the optional guard or bound (neither is in
@@ -332,12 +335,12 @@ static void count_eta(const orc_params* p, int fired, int guard, int bound) {
     p->counters[ORC_CNT_BOUND] += bound;
 }
 
-/* tl, tr: transverse second differences of the two cells of the face (used by k = 2 with the
- * 5-cell cross of Sec. 6; 0 on a line).  reason (may be NULL): ORC_ZERO_* bits of the face. */
+/* cf: transverse data of the face for k = 2 on the 5-cell cross of Sec. 6 (NULL on a line).
+ * reason (may be NULL): ORC_ZERO_* bits of the face. */
 static void face_field(const double w[6], const orc_params* p, const uint8_t* replay, double* vm, double* vp,
-                       uint8_t* flag, double* eta_out, double tl, double tr, uint8_t* reason) {
+                       uint8_t* flag, double* eta_out, const cross_face* cf, uint8_t* reason) {
     if (p->k == 2) {
-        face_field_k2(w, p, replay, vm, vp, flag, eta_out, tl, tr, reason);
+        face_field_k2(w, p, replay, vm, vp, flag, eta_out, cf, reason);
         return;
     }
     uint8_t fl = 0, zr = 0;
@@ -409,21 +412,43 @@ int orc_switch_k2(const double c[3], double tol, int* near_tie) {
  * estimates v and v'' at x_{i+1/2} from the cells i-1, i, i+1; side 1: eta of v^+_{i-1/2},
  * the mirror image (the same cells read from the right).  Applies the optional guard and
  * bound of the k = 3 path, with the magnitudes of the denominator's terms. */
-/* Sec. 6 (k = 2, 2D): at a face midpoint the polynomial row of the stencil has the error
- * e v_xx dx^2 + v_yy dy^2 / 24 (e = 1/6 for the stencil of the two cells at the face, -1/3 for
- * the extrapolating one) and the perturbation adds (sum of its q) eta v.  With the second
- * differences a2 (along the face normal) and trans (across it) for v_xx dx^2 and v_yy dy^2, and
+/* Sec. 6 (k = 2, 2D): the 3-cell polynomial stencil of eq. poly_recon2d (the two cells of the
+ * ENO row along the face normal and the transverse neighbour that ENO picks) evaluated at a point
+ * of the face, offset sigma transverse cell widths from its midpoint: the value of the Table k2
+ * row plus sigma times the one-sided transverse difference sy toward that neighbour (side sg =
+ * +1 or -1).  A Taylor expansion at the point (the row's cells sit half a cell behind the face)
+ * gives the error e v_xx dx^2 + (1/24 + sg sigma/2 - sigma^2/2) v_yy dy^2 - (sigma/2) v_xy dx dy,
+ * e = 1/6 for the stencil of the two cells at the face and -1/3 for the extrapolating one; the
+ * perturbation of eq. rbf_recon_2d adds (sum of its q) eta v.  With the second differences a2
+ * (along the normal) and trans (across it) for v_xx dx^2 and v_yy dy^2, the mixed difference xy
+ * (the cell, the cell across the face and their neighbours on the sg side) for v_xy dx dy, and
  * the face value v from the cells far, centre, across (eq. i+1/2_eps_approx), the cancelling
- * eta is F (-a2 + t trans) / (-far + 5 centre + 2 across + eps_M): F = 2 (MQ), 1 (Gaussian),
- * t = -1/4 for the central stencil and 1/8 for the extrapolating one.  With trans = 0 this is
- * the line formula of Table k2.  (The printed denominator of eq. i+1/2_eps_approx_2d lists the
- * coefficients -2, 1, -5, a permutation of the 1, -5, -2 that the derivation gives.) */
+ * eta is F (-a2 + t trans + x xy) / (-far + 5 centre + 2 across + eps_M), F = 2 (MQ), 1
+ * (Gaussian); central stencil: t = -1/4 - 3 sg sigma + 3 sigma^2, x = 3 sigma; extrapolating
+ * (whose q sum to -2 times those of the central row): t = 1/8 + 3/2 sg sigma - 3/2 sigma^2,
+ * x = -3/2 sigma.  At the midpoint (sigma = 0) this is eq. i+1/2_eps_approx_2d, whose printed
+ * denominator lists the coefficients -2, 1, -5, a permutation of the 1, -5, -2 that the
+ * derivation gives; with trans = 0 it is the line formula of Table k2.  At sigma = +-1/(2 sqrt 3)
+ * (the Gauss points of eq. 2DIntegral) the v_yy term of the midpoint cancels and the sg term
+ * remains; a v_xy estimate needs one cell off the 5-cell cross (the diagonal neighbour). */
+typedef struct {
+    double trans, sg, sy, xy; /* of one cell of the face; see above */
+} cross_side;
+struct cross_face_ {
+    cross_side l, r; /* l: the cell behind v^- (left / lower), r: behind v^+ */
+    double sigma;
+};
+
 /* zr (may be NULL) receives 1 where the guard, 2 where the bound set the eta to 0 */
-static double eta_k2_cross_z(const double c[3], int side, int central, double trans, const orc_params* p, int* zr) {
+static double eta_k2_point_z(const double c[3], int side, int central, const cross_side* cs, double sigma,
+                             const orc_params* p, int* zr) {
     double a = (side == 0) ? c[0] : c[2]; /* far cell behind the face's cell */
     double b = c[1];
     double d = (side == 0) ? c[2] : c[0]; /* cell across the face */
-    double num = -a + 2.0 * b - d + (central ? -0.25 : 0.125) * trans;
+    double s = cs->sg;
+    double t_tr = central ? (-0.25 + 3.0 * sigma * sigma - 3.0 * s * sigma) : (0.125 - 1.5 * sigma * sigma + 1.5 * s * sigma);
+    double t_xy = central ? 3.0 * sigma : -1.5 * sigma;
+    double num = -a + 2.0 * b - d + t_tr * cs->trans + t_xy * cs->xy;
     double den0 = -a + 5.0 * b + 2.0 * d;
     double mag = fabs(a) + 5.0 * fabs(b) + 2.0 * fabs(d);
     if (zr) *zr = 0;
@@ -439,8 +464,14 @@ static double eta_k2_cross_z(const double c[3], int side, int central, double tr
     return eta;
 }
 
+double orc_eta_k2_point(const double c[3], int side, int central, double trans, double sg, double xy, double sigma,
+                        const orc_params* p) {
+    cross_side cs = {trans, sg, 0.0, xy};
+    return eta_k2_point_z(c, side, central, &cs, sigma, p, NULL);
+}
+
 double orc_eta_k2_cross(const double c[3], int side, int central, double trans, const orc_params* p) {
-    return eta_k2_cross_z(c, side, central, trans, p, NULL);
+    return orc_eta_k2_point(c, side, central, trans, 1.0, 0.0, 0.0, p);
 }
 
 double orc_eta_k2(const double c[3], int side, const orc_params* p) { return orc_eta_k2_cross(c, side, 1, 0.0, p); }
@@ -449,9 +480,10 @@ double orc_eta_k2(const double c[3], int side, const orc_params* p) { return orc
 /* v^+_{i-1/2}, rows r - 1), k = 2.  c[0..2] = cells i-1, i, i+1; stencil r uses cells     */
 /* i-r, i-r+1.                                                                             */
 /* eta_c: shape parameter of the stencil of the two cells at the face (row 0), eta_x: of the   */
-/* extrapolating stencil (rows -1, 1); equal except on the 5-cell cross of Sec. 6.              */
+/* extrapolating stencil (rows -1, 1); equal except on the 5-cell cross of Sec. 6.  shift: the  */
+/* transverse term sigma sy of a point off the face midpoint (Sec. 6), added to each candidate. */
 static double cell_face_value_k2(const double c[3], int side, double eta_c, double eta_x, const orc_params* p,
-                                 int forced_r, int* r_out, int* near_out) {
+                                 int forced_r, int* r_out, int* near_out, double shift) {
     const double(*q)[2] = (p->rbf == ORC_RBF_GA) ? PERT2_GA : PERT2_MQ;
     double cand[2];
     for (int r = 0; r < 2; ++r) {
@@ -459,7 +491,7 @@ static double cell_face_value_k2(const double c[3], int side, double eta_c, doub
         double eta = (row == 0) ? eta_c : eta_x;
         double s = 0.0;
         for (int j = 0; j < 2; ++j) s += (POLY2[row + 1][j] + q[row + 1][j] * eta) * c[1 - r + j];
-        cand[r] = s;
+        cand[r] = s + shift;
     }
     *near_out = 0;
     *r_out = 0;
@@ -491,7 +523,9 @@ static double cell_face_value_k2(const double c[3], int side, double eta_c, doub
  * cell i (stencil w[1..3]) with that cell's side-0 eta, v^+ from cell i+1 (stencil w[2..4])
  * with its side-1 eta.  eta_out receives the eta of v^-. */
 static void face_field_k2(const double w[6], const orc_params* p, const uint8_t* replay, double* vm, double* vp,
-                          uint8_t* flag, double* eta_out, double tl, double tr, uint8_t* reason) {
+                          uint8_t* flag, double* eta_out, const cross_face* cf, uint8_t* reason) {
+    static const cross_face line = {{0.0, 1.0, 0.0, 0.0}, {0.0, 1.0, 0.0, 0.0}, 0.0};
+    if (!cf) cf = &line;
     uint8_t fl = 0, zr = 0;
     double eta_l = 0.0, eta_r = 0.0, eta_lx = 0.0, eta_rx = 0.0;
     if (p->scheme == ORC_RBF_ENO || p->scheme == ORC_RBF_WENO) {
@@ -508,16 +542,16 @@ static void face_field_k2(const double w[6], const orc_params* p, const uint8_t*
         if (fires_l) {
             fl |= ORC_FLAG_SWITCH;
         } else {
-            eta_l = eta_k2_cross_z(&w[1], 0, 1, tl, p, &z1);
-            eta_lx = eta_k2_cross_z(&w[1], 0, 0, tl, p, &z2);
+            eta_l = eta_k2_point_z(&w[1], 0, 1, &cf->l, cf->sigma, p, &z1);
+            eta_lx = eta_k2_point_z(&w[1], 0, 0, &cf->l, cf->sigma, p, &z2);
             zr |= (uint8_t)(z1 | z2); /* ORC_ZERO_GUARD_L = 1, ORC_ZERO_BOUND_L = 2 */
         }
         count_eta(p, fires_l, (zr & ORC_ZERO_GUARD_L) != 0, (zr & ORC_ZERO_BOUND_L) != 0);
         if (fires_r) {
             fl |= ORC_FLAG_SWITCH_R_K2;
         } else {
-            eta_r = eta_k2_cross_z(&w[2], 1, 1, tr, p, &z1);
-            eta_rx = eta_k2_cross_z(&w[2], 1, 0, tr, p, &z2);
+            eta_r = eta_k2_point_z(&w[2], 1, 1, &cf->r, cf->sigma, p, &z1);
+            eta_rx = eta_k2_point_z(&w[2], 1, 0, &cf->r, cf->sigma, p, &z2);
             zr |= (uint8_t)((z1 | z2) << 2); /* ORC_ZERO_GUARD_R, ORC_ZERO_BOUND_R */
         }
         count_eta(p, fires_r, (zr & ORC_ZERO_GUARD_R) != 0, (zr & ORC_ZERO_BOUND_R) != 0);
@@ -529,8 +563,8 @@ static void face_field_k2(const double w[6], const orc_params* p, const uint8_t*
         fl_r = (*replay >> 2) & 1;
         fr_r = (*replay >> 4) & 1;
     }
-    *vm = cell_face_value_k2(&w[1], 0, eta_l, eta_lx, p, fl_r, &rl, &nl);
-    *vp = cell_face_value_k2(&w[2], 1, eta_r, eta_rx, p, fr_r, &rr, &nr);
+    *vm = cell_face_value_k2(&w[1], 0, eta_l, eta_lx, p, fl_r, &rl, &nl, cf->sigma * cf->l.sy);
+    *vp = cell_face_value_k2(&w[2], 1, eta_r, eta_rx, p, fr_r, &rr, &nr, cf->sigma * cf->r.sy);
     fl |= (uint8_t)((rl & 1) << 2) | (uint8_t)((rr & 1) << 4);
     if (nl) fl |= ORC_FLAG_ENO_TIE_L;
     if (nr) fl |= ORC_FLAG_ENO_TIE_R;
@@ -601,10 +635,19 @@ int orc_euler_eigvec(const double UL[3], const double UR[3], double gamma, doubl
 /* field k of cell i.  Face f (f = 0..n) separates cell f-1 and cell f.  Outputs          */
 /* vm/vp/flags/eta are [m][n+1].                                                           */
 /* ------------------------------------------------------------------------------------ */
-/* trans: [m][n] transverse second differences of the cells of the line (NULL: none). */
+/* Transverse data of the cells and faces of one grid line for k = 2 on the 5-cell cross of
+ * Sec. 6 (see cross_side): per cell [m][n] the second difference, ENO side and one-sided
+ * difference across the line; per face [m][n+1] the mixed difference seen from the cell
+ * behind v^- (xyl) and from the cell behind v^+ (xyr); sigma: the point on the faces. */
+typedef struct {
+    const double *trans, *sg, *sy, *xyl, *xyr;
+    double sigma;
+} cross_line;
+
+/* cx: transverse data of the line (NULL: a line of its own, no cross). */
 static int recon_line(const double* u, long n, int m, long stride, long m_stride, int bc, const orc_params* p,
                       double* vm, double* vp, uint8_t* flags, double* eta, const uint8_t* replay, long out_stride,
-                      const double* trans, uint8_t* reason) {
+                      const cross_line* cx, uint8_t* reason) {
     for (long f = 0; f <= n; ++f) {
         if (p->characteristic && m == 3) {
             double U[6][3], W[6][3], R[3][3], L[3][3];
@@ -625,7 +668,7 @@ static int recon_line(const double* u, long n, int m, long stride, long m_stride
                 uint8_t fl;
                 double et;
                 const uint8_t* rp = replay ? &replay[a * out_stride + f] : NULL;
-                face_field(line, p, rp, &wm[a], &wp[a], &fl, &et, 0.0, 0.0, reason ? &reason[a * out_stride + f] : NULL);
+                face_field(line, p, rp, &wm[a], &wp[a], &fl, &et, NULL, reason ? &reason[a * out_stride + f] : NULL);
                 if (flags) flags[a * out_stride + f] = fl;
                 if (eta) eta[a * out_stride + f] = et;
             }
@@ -645,12 +688,21 @@ static int recon_line(const double* u, long n, int m, long stride, long m_stride
                 uint8_t fl;
                 double et;
                 const uint8_t* rp = replay ? &replay[k * out_stride + f] : NULL;
-                double tl = 0.0, tr = 0.0;
-                if (trans) {
-                    tl = line_get(trans + k * n, n, 1, f - 1, bc, 0.0);
-                    tr = line_get(trans + k * n, n, 1, f, bc, 0.0);
+                cross_face cf = {{0.0, 1.0, 0.0, 0.0}, {0.0, 1.0, 0.0, 0.0}, 0.0};
+                if (cx) {
+                    /* a ghost cell carries the data of the cell it copies (an inflow ghost:
+                     * a constant state, no differences, side +1) */
+                    cf.l.trans = line_get(cx->trans + k * n, n, 1, f - 1, bc, 0.0);
+                    cf.r.trans = line_get(cx->trans + k * n, n, 1, f, bc, 0.0);
+                    cf.l.sg = line_get(cx->sg + k * n, n, 1, f - 1, bc, 1.0);
+                    cf.r.sg = line_get(cx->sg + k * n, n, 1, f, bc, 1.0);
+                    cf.l.sy = line_get(cx->sy + k * n, n, 1, f - 1, bc, 0.0);
+                    cf.r.sy = line_get(cx->sy + k * n, n, 1, f, bc, 0.0);
+                    cf.l.xy = cx->xyl[k * (n + 1) + f];
+                    cf.r.xy = cx->xyr[k * (n + 1) + f];
+                    cf.sigma = cx->sigma;
                 }
-                face_field(line, p, rp, &vm[k * out_stride + f], &vp[k * out_stride + f], &fl, &et, tl, tr,
+                face_field(line, p, rp, &vm[k * out_stride + f], &vp[k * out_stride + f], &fl, &et, cx ? &cf : NULL,
                            reason ? &reason[k * out_stride + f] : NULL);
                 if (flags) flags[k * out_stride + f] = fl;
                 if (eta) eta[k * out_stride + f] = et;
@@ -785,105 +837,232 @@ static int rhs_1d(const double* u, long n, int m, double dx, int kind, int bc, d
     return st;
 }
 
-/* Transverse second differences of the cells of one grid line (Sec. 6, k = 2 on the cross):  */
-/* dir 0: row j, out[k*nx + i] = u(i, j-1) - 2 u(i, j) + u(i, j+1); dir 1: column i,             */
-/* out[k*ny + j] = u(i-1, j) - 2 u(i, j) + u(i+1, j).  Neighbours follow the boundary condition  */
-/* of their direction (bc along x, bc_y along y).                                                */
-static void transverse_line(const double* u, long nx, long ny, int m, int bc, int bc_y, const orc_params* p, int dir,
-                            long line, double* out) {
-    long cells = nx * ny;
+/* Cell (i, j) of one field of an nx x ny grid, for any integers i, j: columns follow bc, rows
+ * bc_y (periodic: wrapped; otherwise the nearest cell of the grid), and an inflow side (the
+ * left for bc, the bottom for bc_y) gives the inflow state whatever the other index. */
+static double grid_cell(const double* uk, long nx, long ny, long i, long j, int bc, int bcy, double inflow) {
+    if (bcy == ORC_BC_INFLOW && j < 0) return inflow;
+    if (bc == ORC_BC_INFLOW && i < 0) return inflow;
+    if (bc == ORC_BC_PERIODIC) {
+        i %= nx;
+        if (i < 0) i += nx;
+    } else {
+        i = (i < 0) ? 0 : (i >= nx ? nx - 1 : i);
+    }
+    if (bcy == ORC_BC_PERIODIC) {
+        j %= ny;
+        if (j < 0) j += ny;
+    } else {
+        j = (j < 0) ? 0 : (j >= ny ? ny - 1 : j);
+    }
+    return uk[j * nx + i];
+}
+
+/* Cell a of grid line `line` (a row for dir 0, a column for dir 1) shifted b cells across it. */
+static double line_cell(const double* uk, long nx, long ny, int dir, long line, long a, long b, int bc, int bcy,
+                        double inflow) {
+    return (dir == 0) ? grid_cell(uk, nx, ny, a, line + b, bc, bcy, inflow)
+                      : grid_cell(uk, nx, ny, line + b, a, bc, bcy, inflow);
+}
+
+/* ENO side across the line of cell a (Sec. 6: the transverse neighbour that Newton's divided
+ * differences pick, the lower one only where its difference is strictly smaller, as in 1D). */
+static double cross_side_of(const double* uk, long nx, long ny, int dir, long line, long a, int bc, int bcy,
+                            double inflow, double* sy) {
+    double c = line_cell(uk, nx, ny, dir, line, a, 0, bc, bcy, inflow);
+    double dn = c - line_cell(uk, nx, ny, dir, line, a, -1, bc, bcy, inflow);
+    double up = line_cell(uk, nx, ny, dir, line, a, 1, bc, bcy, inflow) - c;
+    double s = (fabs(dn) < fabs(up)) ? -1.0 : 1.0;
+    if (sy) *sy = (s < 0.0) ? dn : up;
+    return s;
+}
+
+/* Transverse data of grid line `line` for k = 2 on the 5-cell cross (Sec. 6), see cross_line:
+ * dir 0 = row j (faces of the x sweep, points along y), dir 1 = column i.  Buffers: tr, sg, sy
+ * [m][n], xyl, xyr [m][n+1], n the cells of the line. */
+static void cross_data(const double* u, long nx, long ny, int m, int bc, int bcy, const orc_params* p, int dir,
+                       long line, double sigma, double* tr, double* sg, double* sy, double* xyl, double* xyr,
+                       cross_line* cx) {
+    long cells = nx * ny, n = (dir == 0) ? nx : ny;
     for (int k = 0; k < m; ++k) {
         const double* uk = u + k * cells;
-        if (dir == 0) {
-            for (long i = 0; i < nx; ++i) {
-                double dn = line_get(uk + i, ny, nx, line - 1, bc_y, p->inflow[k]);
-                double up = line_get(uk + i, ny, nx, line + 1, bc_y, p->inflow[k]);
-                out[k * nx + i] = dn - 2.0 * uk[line * nx + i] + up;
-            }
-        } else {
-            for (long j = 0; j < ny; ++j) {
-                double lf = line_get(uk + j * nx, nx, 1, line - 1, bc, p->inflow[k]);
-                double rt = line_get(uk + j * nx, nx, 1, line + 1, bc, p->inflow[k]);
-                out[k * ny + j] = lf - 2.0 * uk[j * nx + line] + rt;
-            }
+        double in = p->inflow[k];
+        for (long a = 0; a < n; ++a) {
+            double dn = line_cell(uk, nx, ny, dir, line, a, -1, bc, bcy, in);
+            double c = line_cell(uk, nx, ny, dir, line, a, 0, bc, bcy, in);
+            double up = line_cell(uk, nx, ny, dir, line, a, 1, bc, bcy, in);
+            tr[k * n + a] = dn - 2.0 * c + up;
+            sg[k * n + a] = cross_side_of(uk, nx, ny, dir, line, a, bc, bcy, in, &sy[k * n + a]);
+        }
+        /* face f between cells f-1 and f of the line: the mixed difference of the cell behind
+         * v^- with the cell across the face, on the cell's ENO side, and the same seen from the
+         * cell behind v^+ (a ghost cell by the boundary rule of grid_cell) */
+        for (long f = 0; f <= n; ++f) {
+            long L = f - 1, R = f;
+            double sl = cross_side_of(uk, nx, ny, dir, line, L, bc, bcy, in, NULL);
+            double sr = cross_side_of(uk, nx, ny, dir, line, R, bc, bcy, in, NULL);
+            long bl = (long)sl, br = (long)sr;
+            double dl = (line_cell(uk, nx, ny, dir, line, R, bl, bc, bcy, in) -
+                         line_cell(uk, nx, ny, dir, line, L, bl, bc, bcy, in)) -
+                        (line_cell(uk, nx, ny, dir, line, R, 0, bc, bcy, in) -
+                         line_cell(uk, nx, ny, dir, line, L, 0, bc, bcy, in));
+            double dr = (line_cell(uk, nx, ny, dir, line, L, br, bc, bcy, in) -
+                         line_cell(uk, nx, ny, dir, line, R, br, bc, bcy, in)) -
+                        (line_cell(uk, nx, ny, dir, line, L, 0, bc, bcy, in) -
+                         line_cell(uk, nx, ny, dir, line, R, 0, bc, bcy, in));
+            xyl[k * (n + 1) + f] = sl * dl;
+            xyr[k * (n + 1) + f] = sr * dr;
         }
     }
+    cx->trans = tr;
+    cx->sg = sg;
+    cx->sy = sy;
+    cx->xyl = xyl;
+    cx->xyr = xyr;
+    cx->sigma = sigma;
 }
 
 static int use_cross(const orc_params* p) {
     return p->cross_2d && p->k == 2 && (p->scheme == ORC_RBF_ENO || p->scheme == ORC_RBF_WENO);
 }
 
-/* Face values of the 2D grid: x faces vmx/vpx [m][ny][nx+1] (face i of row j between cells
- * i-1 and i), y faces vmy/vpy [m][ny+1][nx] (face j of column i between rows j-1 and j). */
-int orc_reconstruct_2d(const double* u, long nx, long ny, int m, int bc, const orc_params* p, double* vmx, double* vpx,
-                       double* vmy, double* vpy) {
+/* 2D parameters: Gauss points need k = 2, and the RBF schemes the shape parameter of the cross */
+static int check_2d(long nx, long ny, int m, const orc_params* p) {
     int st = check_params(nx, m, p);
     if (st || ny < 6 || p->characteristic) return ORC_EINVAL;
-    long cells = nx * ny, nmax = (nx > ny) ? nx : ny;
+    if (p->gauss_2d && (p->k != 2 || ((p->scheme == ORC_RBF_ENO || p->scheme == ORC_RBF_WENO) && !p->cross_2d)))
+        return ORC_EINVAL;
+    return ORC_OK;
+}
+
+/* The two Gauss points of a face of eq. 2DIntegral: +-1/(2 sqrt 3) cell widths from the midpoint */
+#define ORC_GAUSS2 0.28867513459481288225
+
+/* Work buffers of the 2D sweeps */
+typedef struct {
+    double *vm, *vp, *h, *h2, *tr, *sg, *sy, *xyl, *xyr;
+} work2d;
+
+static int work2d_alloc(work2d* w, long nmax, int m) {
+    size_t f = sizeof(double) * m * (nmax + 1), c = sizeof(double) * m * nmax;
+    w->vm = malloc(f);
+    w->vp = malloc(f);
+    w->h = malloc(f);
+    w->h2 = malloc(f);
+    w->xyl = malloc(f);
+    w->xyr = malloc(f);
+    w->tr = malloc(c);
+    w->sg = malloc(c);
+    w->sy = malloc(c);
+    return (w->vm && w->vp && w->h && w->h2 && w->xyl && w->xyr && w->tr && w->sg && w->sy) ? ORC_OK : ORC_ENOMEM;
+}
+
+static void work2d_free(work2d* w) {
+    free(w->vm);
+    free(w->vp);
+    free(w->h);
+    free(w->h2);
+    free(w->xyl);
+    free(w->xyr);
+    free(w->tr);
+    free(w->sg);
+    free(w->sy);
+}
+
+/* Face values of grid line `line` of direction dir at the point sigma of every face (Sec. 6;
+ * sigma = 0: the midpoint).  Outputs vm/vp [m][n+1]. */
+static int line_points(const double* u, long nx, long ny, int m, int bc, int bcy, const orc_params* p, int dir,
+                       long line, double sigma, work2d* w) {
+    long cells = nx * ny;
+    cross_line cx;
+    int need = use_cross(p) || sigma != 0.0;
+    if (need) cross_data(u, nx, ny, m, bc, bcy, p, dir, line, sigma, w->tr, w->sg, w->sy, w->xyl, w->xyr, &cx);
+    if (dir == 0)
+        return recon_line(u + line * nx, nx, m, 1, cells, bc, p, w->vm, w->vp, NULL, NULL, NULL, nx + 1,
+                          need ? &cx : NULL, NULL);
+    return recon_line(u + line, ny, m, nx, cells, bcy, p, w->vm, w->vp, NULL, NULL, NULL, ny + 1, need ? &cx : NULL,
+                      NULL);
+}
+
+/* Face values of the 2D grid at the point sigma of every face (sigma in [-1/2, 1/2] cell
+ * widths from the midpoint along the face; sigma != 0 needs k = 2): x faces vmx/vpx
+ * [m][ny][nx+1] (face i of row j between cells i-1 and i, the point at y_j + sigma dy), y faces
+ * vmy/vpy [m][ny+1][nx] (face j of column i between rows j-1 and j, at x_i + sigma dx). */
+int orc_reconstruct_2d_at(const double* u, long nx, long ny, int m, int bc, const orc_params* p, double sigma,
+                          double* vmx, double* vpx, double* vmy, double* vpy) {
+    int st = check_2d(nx, ny, m, p);
+    if (st || !(fabs(sigma) <= 0.5) || (sigma != 0.0 && p->k != 2)) return ORC_EINVAL;
     const int bcy = p->bc_y < 0 ? bc : p->bc_y; /* boundary of the y sweeps */
-    double* vm = malloc(sizeof(double) * m * (nmax + 1));
-    double* vp = malloc(sizeof(double) * m * (nmax + 1));
-    double* tr = malloc(sizeof(double) * m * nmax);
-    st = (vm && vp && tr) ? ORC_OK : ORC_ENOMEM;
+    work2d w;
+    st = work2d_alloc(&w, (nx > ny) ? nx : ny, m);
     for (long j = 0; j < ny && !st; ++j) {
-        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, bcy, p, 0, j, tr);
-        st = recon_line(u + j * nx, nx, m, 1, cells, bc, p, vm, vp, NULL, NULL, NULL, nx + 1, use_cross(p) ? tr : NULL, NULL);
+        st = line_points(u, nx, ny, m, bc, bcy, p, 0, j, sigma, &w);
         for (int k = 0; k < m && !st; ++k)
             for (long i = 0; i <= nx; ++i) {
-                vmx[(k * ny + j) * (nx + 1) + i] = vm[k * (nx + 1) + i];
-                vpx[(k * ny + j) * (nx + 1) + i] = vp[k * (nx + 1) + i];
+                vmx[(k * ny + j) * (nx + 1) + i] = w.vm[k * (nx + 1) + i];
+                vpx[(k * ny + j) * (nx + 1) + i] = w.vp[k * (nx + 1) + i];
             }
     }
     for (long i = 0; i < nx && !st; ++i) {
-        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, bcy, p, 1, i, tr);
-        st = recon_line(u + i, ny, m, nx, cells, bcy, p, vm, vp, NULL, NULL, NULL, ny + 1, use_cross(p) ? tr : NULL, NULL);
+        st = line_points(u, nx, ny, m, bc, bcy, p, 1, i, sigma, &w);
         for (int k = 0; k < m && !st; ++k)
             for (long j = 0; j <= ny; ++j) {
-                vmy[(k * (ny + 1) + j) * nx + i] = vm[k * (ny + 1) + j];
-                vpy[(k * (ny + 1) + j) * nx + i] = vp[k * (ny + 1) + j];
+                vmy[(k * (ny + 1) + j) * nx + i] = w.vm[k * (ny + 1) + j];
+                vpy[(k * (ny + 1) + j) * nx + i] = w.vp[k * (ny + 1) + j];
             }
     }
-    free(vm);
-    free(vp);
-    free(tr);
+    work2d_free(&w);
     return st;
 }
 
-/* 2D: eq. 2DIntegral with one midpoint point per face, the x and y sweeps each a 1D       */
-/* reconstruction along a grid line (k = 2 with cross_2d: the shape parameter of Sec. 6).   */
-/* u is [m][ny][nx].                                                                         */
+int orc_reconstruct_2d(const double* u, long nx, long ny, int m, int bc, const orc_params* p, double* vmx, double* vpx,
+                       double* vmy, double* vpy) {
+    return orc_reconstruct_2d_at(u, nx, ny, m, bc, p, 0.0, vmx, vpx, vmy, vpy);
+}
+
+/* Numerical flux of every face of grid line `line` (Sec. 7, eq. 2DIntegral divided by the face
+ * length): the Lax-Friedrichs flux at the face midpoint, or (gauss_2d) the mean of the fluxes at
+ * the two Gauss points.  Output w->h [m][n+1]. */
+static int line_flux(const double* u, long nx, long ny, int m, int kind, int bc, int bcy, double alpha,
+                     const orc_params* p, int dir, long line, work2d* w) {
+    long n = (dir == 0) ? nx : ny;
+    if (!p->gauss_2d) {
+        int st = line_points(u, nx, ny, m, bc, bcy, p, dir, line, 0.0, w);
+        return st ? st : orc_flux(w->vm, w->vp, n + 1, m, kind, dir, alpha, p, w->h);
+    }
+    int st = line_points(u, nx, ny, m, bc, bcy, p, dir, line, -ORC_GAUSS2, w);
+    if (!st) st = orc_flux(w->vm, w->vp, n + 1, m, kind, dir, alpha, p, w->h2);
+    if (!st) st = line_points(u, nx, ny, m, bc, bcy, p, dir, line, ORC_GAUSS2, w);
+    if (!st) st = orc_flux(w->vm, w->vp, n + 1, m, kind, dir, alpha, p, w->h);
+    for (long f = 0; f < m * (n + 1) && !st; ++f) w->h[f] = 0.5 * (w->h2[f] + w->h[f]);
+    return st;
+}
+
+/* 2D: eq. 2DIntegral, the x and y sweeps each a reconstruction along a grid line (k = 2 with
+ * cross_2d: the shape parameter of Sec. 6), one quadrature point per face (the midpoint, as in
+ * the paper's experiments) or two Gauss points (gauss_2d).  u is [m][ny][nx]. */
 static int rhs_2d(const double* u, long nx, long ny, int m, double dx, double dy, int kind, int bc, double ax,
                   double ay, const orc_params* p, double* L) {
     long cells = nx * ny;
-    long nmax = (nx > ny) ? nx : ny;
     const int bcy = p->bc_y < 0 ? bc : p->bc_y; /* boundary of the y sweeps */
-    double* vm = malloc(sizeof(double) * m * (nmax + 1));
-    double* vp = malloc(sizeof(double) * m * (nmax + 1));
-    double* h = malloc(sizeof(double) * m * (nmax + 1));
-    double* tr = malloc(sizeof(double) * m * nmax);
-    int st = (vm && vp && h && tr) ? ORC_OK : ORC_ENOMEM;
+    work2d w;
+    int st = work2d_alloc(&w, (nx > ny) ? nx : ny, m);
     for (long i = 0; i < m * cells && !st; ++i) L[i] = 0.0;
     /* x sweeps: row j */
     for (long j = 0; j < ny && !st; ++j) {
-        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, bcy, p, 0, j, tr);
-        st = recon_line(u + j * nx, nx, m, 1, cells, bc, p, vm, vp, NULL, NULL, NULL, nx + 1, use_cross(p) ? tr : NULL, NULL);
-        if (!st) st = orc_flux(vm, vp, nx + 1, m, kind, 0, ax, p, h);
+        st = line_flux(u, nx, ny, m, kind, bc, bcy, ax, p, 0, j, &w);
         for (int k = 0; k < m && !st; ++k)
-            for (long i = 0; i < nx; ++i) L[k * cells + j * nx + i] -= (h[k * (nx + 1) + i + 1] - h[k * (nx + 1) + i]) / dx;
+            for (long i = 0; i < nx; ++i)
+                L[k * cells + j * nx + i] -= (w.h[k * (nx + 1) + i + 1] - w.h[k * (nx + 1) + i]) / dx;
     }
     /* y sweeps: column i */
     for (long i = 0; i < nx && !st; ++i) {
-        if (use_cross(p)) transverse_line(u, nx, ny, m, bc, bcy, p, 1, i, tr);
-        st = recon_line(u + i, ny, m, nx, cells, bcy, p, vm, vp, NULL, NULL, NULL, ny + 1, use_cross(p) ? tr : NULL, NULL);
-        if (!st) st = orc_flux(vm, vp, ny + 1, m, kind, 1, ay, p, h);
+        st = line_flux(u, nx, ny, m, kind, bc, bcy, ay, p, 1, i, &w);
         for (int k = 0; k < m && !st; ++k)
-            for (long j = 0; j < ny; ++j) L[k * cells + j * nx + i] -= (h[k * (ny + 1) + j + 1] - h[k * (ny + 1) + j]) / dy;
+            for (long j = 0; j < ny; ++j)
+                L[k * cells + j * nx + i] -= (w.h[k * (ny + 1) + j + 1] - w.h[k * (ny + 1) + j]) / dy;
     }
-    free(vm);
-    free(vp);
-    free(h);
-    free(tr);
+    work2d_free(&w);
     return st;
 }
 
@@ -934,8 +1113,8 @@ int orc_rk3_step(double* u, long n, int m, double dx, double dt, int kind, int b
 
 int orc_rk3_step_2d(double* u, long nx, long ny, int m, double dx, double dy, double dt, int kind, int bc,
                     const orc_params* p) {
-    int st = check_params(nx, m, p);
-    if (st || ny < 6 || p->characteristic) return ORC_EINVAL;
+    int st = check_2d(nx, ny, m, p);
+    if (st) return st;
     if (m != ((kind == ORC_FLUX_EULER2D) ? 4 : 1) || kind == ORC_FLUX_EULER1D) return ORC_EINVAL;
     double ax = orc_max_speed(u, nx * ny, m, kind, 0, p);
     double ay = orc_max_speed(u, nx * ny, m, kind, 1, p);
@@ -996,8 +1175,8 @@ int orc_solve(double* u, long n, int m, double dx, double t_end, double cfl, int
 
 int orc_solve_2d(double* u, long nx, long ny, int m, double dx, double dy, double t_end, double cfl, int kind,
                  int bc, const orc_params* p, long max_steps, orc_solve_stats* out) {
-    int st = check_params(nx, m, p);
-    if (st || ny < 6 || p->characteristic) return ORC_EINVAL;
+    int st = check_2d(nx, ny, m, p);
+    if (st) return st;
     if (m != ((kind == ORC_FLUX_EULER2D) ? 4 : 1) || kind == ORC_FLUX_EULER1D) return ORC_EINVAL;
     return solve_any(u, nx, ny, m, dx, dy, t_end, cfl, kind, bc, p, max_steps, out);
 }

@@ -48,6 +48,7 @@ typedef struct {
     int k;               /* order parameter of the ENO stencils: 2 or 3 (0 means 3) */
     int cross_2d;        /* 2D, k = 2: shape parameter of Sec. 6 on the 5-cell cross (1) or of the line (0) */
     int bc_y;            /* 2D: boundary condition of the y direction (columns); < 0: the bc argument */
+    int gauss_2d;        /* 2D, k = 2: eq. 2DIntegral with two Gauss points per face (1) or the midpoint (0) */
     double eps_M;     /* additive guard of the eta denominator */
     double eps_weno;  /* WENO epsilon (1e-6) */
     double gamma;     /* ratio of specific heats */
@@ -75,6 +76,10 @@ double orc_eta_k2(const double c[3], int side, const orc_params* p);
 double orc_eta_k2_cross(const double c[3], int side, int central, double trans, const orc_params* p);
 int orc_reconstruct_2d(const double* u, long nx, long ny, int m, int bc, const orc_params* p, double* vmx, double* vpx,
                        double* vmy, double* vpy);
+int orc_reconstruct_2d_at(const double* u, long nx, long ny, int m, int bc, const orc_params* p, double sigma,
+                          double* vmx, double* vpx, double* vmy, double* vpy);
+double orc_eta_k2_point(const double c[3], int side, int central, double trans, double sg, double xy, double sigma,
+                        const orc_params* p);
 double orc_table_coef_k2(int rbf, int r, int j, double eta);
 int orc_eno_choice(const double c[5], double tol, int* near_tie);
 void orc_beta_k3(const double c[5], double beta[3]);

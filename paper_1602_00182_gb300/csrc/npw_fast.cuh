@@ -8,10 +8,12 @@
 //     therefore the sign the double-precision evaluation gives; otherwise the decision is
 //     recomputed in double precision.  The decisions are thus those of FP64 evaluation.
 //   * The shape parameter eta of Table k3 (a ratio of two cancelling differences) is evaluated
-//     either in FP64 (eta_eval 0: exact FP64 numerator and denominator, FP64 Newton quotient) or from
-//     the exactly computed numerator and denominator as float pairs with a double-float
-//     quotient (eta_eval 1: ~2^-46 relative, no FP64 instruction).  Both are rounded once to
-//     float for the perturbed coefficients c_rj + q_rj eta.
+//     either from the exactly computed differences as float pairs with a double-float quotient
+//     (eta_eval 0, the default: within one float ulp plus ~2^-44 of the conditioning, no FP64
+//     instruction) or in FP64 (eta_eval 1: FP64 numerator and denominator from the widened
+//     averages, FP64 Newton quotient, within half an ulp plus 2^-52 of the conditioning).  Both
+//     are rounded once to float for the perturbed coefficients c_rj + q_rj eta.  k = 2 (Table
+//     k2) always takes the FP64 form.
 //   * The WENO smoothness indicators beta_r (Jiang-Shu), the weights, candidates, flux and
 //     update are single precision.
 #pragma once
@@ -322,11 +324,11 @@ __device__ __forceinline__ float eta_fp64(float w0, float w1, float w2, float w3
     return eta_quot<true>(w0, w1, w2, w3, fp, guard, fl);
 }
 
-// Double-float evaluation (eta_eval 1, no FP64 instruction): the pairs of eta_pairs, eps_M added
+// Double-float evaluation (eta_eval 0, no FP64 instruction): the pairs of eta_pairs, eps_M added
 // by two_sum, renormalised, and the double-float quotient (one correction of the float
 // quotient).  Its numerator and denominator are within ~2^-47 of the magnitudes of their terms
 // (|a| + 3|b|, |a| + 15|b|), against 2^-53 for the FP64 evaluation: where they cancel strongly
-// the quotient is correspondingly less accurate than eta_eval 0.
+// the quotient is correspondingly less accurate than eta_eval 1.
 __device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, float w3, const FParams& fp,
                                                  float guard, uint32_t* fl) {
     const float eps_M = fp.eps_M_f;
@@ -367,7 +369,7 @@ __device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, f
 // quotient would be noise amplified by 1/eps_M.
 __device__ __forceinline__ float eta_eval(float w0, float w1, float w2, float w3, const FParams& fp, uint32_t* fl) {
     const float guard = fp.eta_guard * (fabsf(w0) + 15.f * fabsf(w1) + 15.f * fabsf(w2) + fabsf(w3));
-    return fp.eta_eval == 1 ? eta_doublefloat(w0, w1, w2, w3, fp, guard, fl)
+    return fp.eta_eval == 0 ? eta_doublefloat(w0, w1, w2, w3, fp, guard, fl)
                             : eta_fp64(w0, w1, w2, w3, fp, guard, fl);
 }
 

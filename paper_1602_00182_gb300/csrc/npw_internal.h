@@ -67,7 +67,7 @@ struct MethodParams {
     int monotone_switch;
     int switch_variant;
     int characteristic;
-    int eta_eval;  // mixed precision: 0 = FP64 division, 1 = exact double-float quotient
+    int eta_eval;  // mixed precision, k = 3: 0 = double-float quotient (no FP64), 1 = FP64 evaluation
     int k;         // 2 (ENO2 / WENO3) or 3 (ENO3 / WENO5)
     int cross_2d;  // k = 2 in 2D: shape parameter on the 5-cell cross (Sec. 6)
     double eps_M;

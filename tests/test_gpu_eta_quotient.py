@@ -1,15 +1,15 @@
 """Direct pin of the mixed-precision shape parameter (NPW_FP32_MIXED) against the correctly
 rounded quotient.
 
-The mixed path does not divide in the obvious way.  With eta_eval 0 it widens the float cell
-averages, forms the Table k3 (k = 3) or Table k2 (k = 2) numerator and denominator in FP64 by
-differences and single-rounding multiply-adds, and takes a Newton-Raphson quotient seeded by a
-fast float reciprocal; with eta_eval 1 it keeps numerator and denominator as float pairs and
-takes a double-float quotient.  The claim: the result is the exact quotient rounded once to
+The mixed path does not divide in the obvious way.  With eta_eval 1 (and always for k = 2) it
+widens the float cell averages, forms the Table k3 (k = 3) or Table k2 (k = 2) numerator and
+denominator in FP64 by differences and single-rounding multiply-adds, and takes a Newton-Raphson
+quotient seeded by a fast float reciprocal; with eta_eval 0 (the default, k = 3) it keeps
+numerator and denominator as float pairs and takes a double-float quotient.  The claim: the result is the exact quotient rounded once to
 float, up to the rounding an FP64 evaluation of the undivided differences carries -- u (|a| +
 3|b|) / |num| + u (|a| + 15|b|) / |den| relative for k = 3 (u = 2^-53; a = w0 - w3,
 b = w2 - w1), which is below one float ulp unless the differences cancel strongly -- plus
-2^-41 for the quotient; eta_eval 1 carries ~2^-47 instead of u.  Results below the float
+2^-41 for the quotient; the float pairs of eta_eval 0 carry ~2^-47 instead of u.  Results below the float
 normal range are flushed to zero.  The reference is exact rational arithmetic (fractions) on
 the same float data: no part of it comes from the library.
 
@@ -127,9 +127,10 @@ def test_mixed_eta_is_the_rounded_exact_quotient(npw, k, eta_eval, rbf):
     normal = fin & (np.abs(q) >= F32_MIN_NORMAL) & (np.abs(q) < 3e38)
     err = np.abs(geta[normal] - q[normal])
     ulp = _ulp32(q[normal])
-    # eta_eval 0: the FP64 evaluation, rounded once (0.5 ulp); eta_eval 1: float pairs and a
-    # double-float quotient, within one ulp (not correctly rounded)
-    unit, last = (2.0 ** -52, 0.5) if eta_eval == 0 else (2.0 ** -44, 1.0)
+    # the FP64 evaluation (eta_eval 1; k = 2 always), rounded once: 0.5 ulp; float pairs and a
+    # double-float quotient (eta_eval 0, k = 3): within one ulp (not correctly rounded)
+    fp64_form = eta_eval == 1 or k == 2
+    unit, last = (2.0 ** -52, 0.5) if fp64_form else (2.0 ** -44, 1.0)
     bound = last * ulp + np.abs(q[normal]) * (unit * (kap[normal] + 5.0) + 2.0 ** -40)
     worst = float((err / bound).max())
     well = kap[normal] < 2.0 ** 20  # no strong cancellation: the bound is below one ulp

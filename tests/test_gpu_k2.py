@@ -72,13 +72,24 @@ def test_k2_reconstruct_fp64(npw, scheme, rbf, switch, bc):
                       1.0 if n < 64 else 0.06, geta=geta.cpu().numpy(), eta_exact=True, label=f"k2 n={n}")
 
 
+def _guard_data():
+    """Zero-mean data (the face values cross zero, where the k = 2 denominator, about 6 v, is
+    small) with 8-cell blocks whose denominator -a + 5 b + 2 d of v^- cancels to ~1e-6 of its
+    terms, so that both the guard and the bound have faces to act on."""
+    g = np.random.default_rng(3)
+    x = (np.arange(2000) + 0.5) / 2000
+    u = 0.4 * np.sin(2 * np.pi * 3 * x + g.uniform(0, 6)) + 0.5 * (x > 1 / np.sqrt(3)) - 0.25
+    for s in range(100, 1900, 150):
+        for j in range(2, 8):
+            u[s + j] = (u[s + j - 2] - 5.0 * u[s + j - 1]) / 2.0 + g.normal() * 1e-6
+        u[s:s + 8] /= max(1.0, np.abs(u[s:s + 8]).max())
+    return u
+
+
 @pytest.mark.parametrize("eta_max,eta_guard", [(0.05, 0.0), (0.0, 1e-3)])
 def test_k2_reconstruct_guard_and_bound(npw, eta_max, eta_guard):
     op = O.Params(k=2, eta_max=eta_max, eta_guard=eta_guard, monotone_switch=0)
-    g = np.random.default_rng(3)
-    x = (np.arange(2000) + 0.5) / 2000
-    # zero mean: the face values cross zero, where the k = 2 denominator (about 6 v) is small
-    u = 0.4 * np.sin(2 * np.pi * 3 * x + g.uniform(0, 6)) + 0.5 * (x > 1 / np.sqrt(3)) - 0.25
+    u = _guard_data()
     gvm, gvp, gfl, geta = npw.npweno_reconstruct(_dev(u), O.PERIODIC, _gp(npw, op), with_eta=True)
     gfl = gfl.cpu().numpy()
     assert ((gfl & 0xC0) != 0).any()
