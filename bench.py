@@ -800,6 +800,169 @@ def serving_block(npw, count: int, rates):
     return out
 
 
+# ------------------------------------------------------------------------------- serving sweep
+FP64_TOL_CLASS = 1e-10   # a request asking for this tolerance takes the server's FP64 lane
+FP32_TOL_CLASS = 1e-4    # the float lane's class (npweno.MIXED_TOLERANCE)
+
+
+def sweep_payloads(count: int, seed: int = 7):
+    """Payloads of the C5-type stream: each request is, with equal probability, a periodic Burgers
+    instance of the batch family (N log-uniform 64..8192, T = 1.5 U(0.1, 1)), a transmissive 1D
+    Euler instance (Riemann or Shu-Osher-type data, N log-uniform 256..65536, T = its end time x
+    U(0.1, 1)) or a periodic 2D Euler square (vortex or four-quadrant, 128^2..1024^2, T x
+    U(0.1, 1) of ~10-80 steps); a quarter ask for FP64 (tolerance 1e-10), the rest for the float
+    class (1e-4)."""
+    g = np.random.Generator(np.random.PCG64(I.SEED_BASE + 900 + seed))
+    burg = I.burgers_batch(count=count, seed_index=910 + seed)
+    eul = I.euler_batch(count=count, nmin=256, nmax=65536, seed_index=920 + seed)
+    sq = {}
+    items = []
+    for k in range(count):
+        fam = int(g.integers(3))
+        tol = FP64_TOL_CLASS if g.uniform() < 0.25 else FP32_TOL_CLASS
+        if fam == 0:
+            it = burg[k]
+            items.append(dict(family="burgers", kind=1, bc=0, m=1, n=it.n, ny=0, dx=it.dx,
+                              t_end=1.5 * g.uniform(0.1, 1.0), u0=it.u0.ravel(), tol=tol))
+        elif fam == 1:
+            it = eul[k]
+            items.append(dict(family="euler1d", kind=2, bc=1, m=3, n=it.n, ny=0, dx=it.dx,
+                              t_end=it.t_end * g.uniform(0.1, 1.0), u0=it.u0.ravel(), tol=tol))
+        else:
+            n2 = int(g.choice([128, 256, 512, 1024], p=[0.4, 0.3, 0.2, 0.1]))
+            which = int(g.integers(2))
+            if n2 not in sq:  # one vortex and one four-quadrant square per size, shared by the requests
+                sq[n2] = I.euler2d_batch(n2, 2, seed_index=930 + seed)
+            U, d = sq[n2][which]
+            t2 = (0.1 if which == 0 else 0.02) * g.uniform(0.1, 1.0)
+            items.append(dict(family="euler2d", kind=3, bc=0, m=4, n=n2, ny=n2, dx=d, t_end=t2, u0=U, tol=tol))
+    gaps = g.exponential(1.0, size=count)
+    return gaps, items
+
+
+def run_serving_stream(npw, reqs, heap_cells: int, max_slots: int, max_steps: int = 32):
+    """The live server on a stream of requests (arrival, payload): each is submitted at its
+    arrival time (held on the host while the server's queue is full), the server is stepped in
+    rounds of max_steps steps, results are polled; latency = result on the host - arrival."""
+    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, batch_mode=1)
+    srv = npw.Server(heap_cells=heap_cells, max_slots=max_slots, params=p)
+    t0 = time.perf_counter()
+    k, done, backlog = 0, {}, []
+    while len(done) < len(reqs):
+        now = time.perf_counter() - t0
+        while k < len(reqs) and reqs[k]["arrival"] <= now:
+            backlog.append(k)
+            k += 1
+        while backlog:
+            r = reqs[backlog[0]]
+            try:
+                srv.submit(r["u0"], r["kind"], r["bc"], r["dx"], r["t_end"], 0.5, tag=backlog[0],
+                           dy=r["dx"] if r["ny"] else 0.0, tolerance=r["tol"])
+            except npw.NpwError as e:
+                if e.status != npw.NPW_EBUSY:
+                    raise
+                break
+            backlog.pop(0)
+        act, q = srv.step(max_steps)
+        for res in srv.poll():
+            done[res["tag"]] = res
+        if act == 0 and q == 0 and not backlog and k < len(reqs):
+            time.sleep(max(0.0, reqs[k]["arrival"] - (time.perf_counter() - t0)))
+    srv.close()
+    return done
+
+
+def fifo_per_step_model(npw, items, per_family: int = 12, probe_steps: int = 40):
+    """The FP64 first-in first-out comparator's service time: for a sample of each family's
+    requests (spread over their sizes), the FP64 solve (npweno_solve / npweno_solve_2d, host
+    copy in and out, one at a time) is timed for probe_steps steps (max_steps) and for 2 x
+    probe_steps; the difference gives the time per step, the rest the fixed cost.  Per family,
+    time per step = a + b cells (least squares) and fixed cost = the sample mean."""
+    import torch
+    model = {}
+    for fam in ("burgers", "euler1d", "euler2d"):
+        idx = [i for i, r in enumerate(items) if r["family"] == fam]
+        idx = sorted(idx, key=lambda i: items[i]["n"] * max(items[i]["ny"], 1))
+        pick = [idx[int(j)] for j in np.linspace(0, len(idx) - 1, min(per_family, len(idx)))]
+        cells, per_step, fixed = [], [], []
+        for i in pick:
+            r = items[i]
+            ts = []
+            for steps in (probe_steps, 2 * probe_steps):
+                p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP64, max_steps=steps)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                u = torch.tensor(r["u0"], dtype=torch.float64, device="cuda")
+                try:
+                    if r["ny"]:
+                        npw.npweno_solve_2d(u, r["dx"], r["dx"], 1e9, 0.5, r["kind"], r["bc"], p)
+                    else:
+                        npw.npweno_solve(u.view(r["m"], r["n"]), r["dx"], 1e9, 0.5, r["kind"], r["bc"], p)
+                except npw.NpwError as e:
+                    if e.status != npw.NPW_ETIMEOUT:
+                        raise
+                u.cpu()
+                ts.append(time.perf_counter() - t0)
+            c = r["n"] * max(r["ny"], 1) * r["m"]
+            cells.append(c)
+            per_step.append(max((ts[1] - ts[0]) / probe_steps, 0.0))
+            fixed.append(max(ts[0] - probe_steps * per_step[-1], 0.0))
+        A = np.vstack([np.ones(len(cells)), np.array(cells, dtype=float)]).T
+        coef, *_ = np.linalg.lstsq(A, np.array(per_step), rcond=None)
+        model[fam] = {"a_s": float(coef[0]), "b_s_per_cell": float(coef[1]), "fixed_s": float(np.mean(fixed)),
+                      "sampled": len(pick)}
+    return model
+
+
+def serving_sweep(npw, rates, count: int = 2000, horizon_s: float = 60.0):
+    """The C5-type serving sweep: per arrival rate, Poisson arrivals of the same payload sequence
+    until `count` requests or `horizon_s` seconds of arrivals, served live by the two-lane
+    server; the FP64 FIFO comparator (one request at a time) from its per-step model and the
+    step counts the server reported."""
+    q = lambda a, x: float(np.percentile(a, x) * 1e3) if len(a) else None
+    gaps, items = sweep_payloads(count)
+    model = fifo_per_step_model(npw, items)
+    out = {"mode": "serving sweep (C5-type)", "requests_max": count, "horizon_s": horizon_s,
+           "mix": "1/3 periodic Burgers (N 64..8192), 1/3 transmissive 1D Euler (N 256..65536), 1/3 periodic 2D "
+                  "Euler squares (128^2..1024^2); T x U(0.1, 1); 1/4 FP64 class (tol 1e-10), 3/4 float class (1e-4)",
+           "server": "npw_server: two lanes (NPW_FP32_MIXED, NPW_FP64) on one stream, work-queue stage kernels, "
+                     "32-step rounds",
+           "fifo_comparator": "FP64, one request at a time, per-stage kernels, no graphs; service time = fixed + "
+                              "steps x (a + b cells) per family, measured on a size-spread sample",
+           "fifo_model": model, "rates": []}
+    for rate in rates:
+        arr = np.cumsum(gaps) / rate
+        n_req = int(min(count, np.searchsorted(arr, horizon_s)))
+        reqs = [dict(arrival=float(arr[k]), **items[k]) for k in range(n_req)]
+        t_start = time.perf_counter()
+        done = run_serving_stream(npw, reqs, heap_cells=96 * 1024 * 1024, max_slots=1024)
+        wall = time.perf_counter() - t_start
+        lat = np.array([done[i]["done_s"] - reqs[i]["arrival"] for i in range(n_req)])
+        prec = np.array([done[i]["precision"] for i in range(n_req)])
+        steps = np.array([done[i]["steps"] for i in range(n_req)])
+        cu = np.array([reqs[i]["n"] * max(reqs[i]["ny"], 1) * steps[i] for i in range(n_req)], dtype=float)
+        span = max(done[i]["done_s"] for i in done) - reqs[0]["arrival"]
+        # FIFO: the same requests in arrival order, FP64, one at a time
+        svc = []
+        for i in range(n_req):
+            mdl = model[reqs[i]["family"]]
+            c = reqs[i]["n"] * max(reqs[i]["ny"], 1) * reqs[i]["m"]
+            svc.append(mdl["fixed_s"] + steps[i] * max(mdl["a_s"] + mdl["b_s_per_cell"] * c, 0.0))
+        flat, fend = fifo_latencies(np.array(svc), [r["arrival"] for r in reqs])
+        fam_lat = {f: q(lat[[r["family"] == f for r in reqs]], 99) for f in ("burgers", "euler1d", "euler2d")}
+        out["rates"].append({
+            "rate_per_s": rate, "requests": n_req, "wall_s": wall,
+            "server": {"p50_ms": q(lat, 50), "p99_ms": q(lat, 99), "mean_ms": float(lat.mean() * 1e3),
+                       "p99_ms_fp32_lane": q(lat[prec == 1], 99), "p99_ms_fp64_lane": q(lat[prec == 0], 99),
+                       "p99_ms_by_family": fam_lat, "cell_updates_per_s": float(cu.sum() / span),
+                       "all_ok": all(done[i]["status"] == 0 for i in done)},
+            "fp64_fifo": {"p50_ms": q(flat, 50), "p99_ms": q(flat, 99),
+                          "cell_updates_per_s": float(cu.sum() / (fend - reqs[0]["arrival"]))},
+        })
+        print(json.dumps(out["rates"][-1]), file=sys.stderr, flush=True)
+    return out
+
+
 # ------------------------------------------------------------------------------- ranks
 def rank_seed(base: int, rank: int) -> int:
     """Seed index of a rank's batch: every rank solves its own seeded batch of the same family
@@ -868,6 +1031,11 @@ def main():
                     help="timed solves of each variant reported beside the headline (0: skip)")
     ap.add_argument("--out-dir", default=os.path.join(tempfile.gettempdir(), "npweno_bench"),
                     help="where the clock samples are written")
+    ap.add_argument("--serving-sweep", action="store_true",
+                    help="run only the C5-type serving sweep (rates 10..1000 /s, 2000 requests or 60 s each)")
+    ap.add_argument("--sweep-rates", default="10,30,100,300,1000")
+    ap.add_argument("--sweep-requests", type=int, default=2000)
+    ap.add_argument("--sweep-horizon", type=float, default=60.0)
     args = ap.parse_args()
     args.sizes2d = [int(x) for x in args.sizes2d.split(",") if x]
     blocks = {b.strip() for b in args.blocks.split(",") if b.strip()}
@@ -891,6 +1059,11 @@ def main():
         torch.distributed.init_process_group("nccl")
         torch.distributed.barrier()
     torch.cuda.set_device(local_rank)
+    if args.serving_sweep:
+        if rank == 0:
+            print(json.dumps(serving_sweep(npw, [float(x) for x in args.sweep_rates.split(",")],
+                                           args.sweep_requests, args.sweep_horizon)))
+        return
     out, sample = headline_burgers(args, rank, world, local_rank)
     single = rank == 0 and world == 1
     cfg, leg = {}, {}

@@ -116,6 +116,13 @@ typedef struct {
                                 a run that reaches it, or whose time stops advancing (t + dt == t), ends
                                 with status NPW_ETIMEOUT instead of looping on the device; <= 0 = automatic:
                                 64 x the step count the first time step implies + 1024, at most 2^24 */
+    int32_t gauss_2d;        /* 2D entry points, NPW_FP64, k = 2 (RBF schemes: with cross_2d): 1 = the integral
+                                of eq. 2DIntegral by two Gauss points per face (Sec. 7 names two points as
+                                needed for third order): the reconstruction of Sec. 6 at -+ 1/(2 sqrt 3) cell
+                                widths from the face midpoint, its Taylor error there cancelled by the shape
+                                parameter (the v_xy term with the diagonal neighbour), and the mean of the two
+                                Lax-Friedrichs fluxes; 0 = one point at the midpoint, as in the paper's runs */
+    int32_t reserved_;       /* 0 */
 } npw_params;
 
 typedef struct {

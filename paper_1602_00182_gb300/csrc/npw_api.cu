@@ -61,10 +61,22 @@ npw_status check_params(const npw_params* p) {
     if (p->eta_eval < 0 || p->eta_eval > 1) return fail(NPW_EINVAL, "bad eta_eval %d", p->eta_eval);
     if (p->batch_mode < 0 || p->batch_mode > 1) return fail(NPW_EINVAL, "bad batch_mode %d", p->batch_mode);
     if (p->cross_2d < 0 || p->cross_2d > 1) return fail(NPW_EINVAL, "bad cross_2d %d", p->cross_2d);
+    if (p->gauss_2d < 0 || p->gauss_2d > 1) return fail(NPW_EINVAL, "bad gauss_2d %d", p->gauss_2d);
     if (p->tile_1d != 0 && p->tile_1d != 256 && p->tile_1d != 512 && p->tile_1d != 1024 && p->tile_1d != 2048)
         return fail(NPW_EINVAL, "tile_1d must be 0, 256, 512, 1024 or 2048, got %d", p->tile_1d);
     if (!(p->eps_weno > 0.0)) return fail(NPW_EINVAL, "eps_weno must be > 0");
     if (!(p->gamma > 1.0)) return fail(NPW_EINVAL, "gamma must be > 1");
+    return NPW_OK;
+}
+
+// the two-point Gauss rule of the 2D entry points: k = 2, the cross form for the RBF schemes,
+// the FP64 path
+npw_status check_gauss(const npw_params* p) {
+    if (!p->gauss_2d) return NPW_OK;
+    if (p->k != 2) return fail(NPW_EINVAL, "gauss_2d needs k = 2 (the point reconstruction of Sec. 6)");
+    if ((p->scheme == NPW_RBF_ENO || p->scheme == NPW_RBF_WENO) && !p->cross_2d)
+        return fail(NPW_EINVAL, "gauss_2d with an RBF scheme needs cross_2d = 1");
+    if (p->precision != NPW_FP64) return fail(NPW_EINVAL, "gauss_2d is implemented for NPW_FP64");
     return NPW_OK;
 }
 
@@ -78,6 +90,7 @@ npw::MethodParams method(const npw_params* p) {
     mp.eta_eval = p->eta_eval;
     mp.k = p->k;
     mp.cross_2d = p->cross_2d ? 1 : 0;
+    mp.gauss_2d = p->gauss_2d ? 1 : 0;
     mp.eps_M = p->eps_M;
     mp.eps_weno = p->eps_weno;
     mp.gamma = p->gamma;
@@ -1189,6 +1202,7 @@ static npw_status run_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx, 
         return fail(NPW_EINVAL, "flux kind %d is not a 2D flux", flux_kind);
     if (m != flux_m(flux_kind)) return fail(NPW_EINVAL, "m does not match the flux kind");
     if (params->characteristic) return fail(NPW_EINVAL, "2D runs are component-wise");
+    if ((st = check_gauss(params))) return st;
     if ((st = check_bc(bc))) return st;
     if (params->bc_y >= 0 && (st = check_bc(params->bc_y))) return st;
     if (!(dx > 0.0) || !(dy > 0.0)) return fail(NPW_EINVAL, "dx, dy must be > 0");
@@ -1470,6 +1484,7 @@ npw_status check_queue(const npw_queue_instance* inst, int count, const npw_para
             if (q.nx < 6 || q.ny < 6 || q.nx * q.ny > ((int64_t)1 << 31) || !(q.dy > 0.0))
                 return fail(NPW_EINVAL, "instance %d: bad 2D size or dy", i);
             if (q.bc_y >= 0 && (st = check_bc(q.bc_y))) return st;
+            if ((st = check_gauss(p))) return st;
         }
         if ((st = check_bc(q.bc))) return st;
         if (!(q.dx > 0.0) || !(q.cfl > 0.0)) return fail(NPW_EINVAL, "instance %d: bad dx or cfl", i);
@@ -2061,6 +2076,7 @@ npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max
     if (st) return st;
     if (!device_arena || !out || max_slots < 1 || max_slots > (1 << 20)) return fail(NPW_EINVAL, "bad server arguments");
     if (params->characteristic) return fail(NPW_EINVAL, "the server runs component-wise reconstruction");
+    if (params->gauss_2d) return fail(NPW_EINVAL, "the server takes one quadrature point per face (gauss_2d = 0)");
     // largest heap (per lane) that fits the arena
     int64_t lo = 0, hi = (int64_t)(arena_bytes / 44) + 1;
     while (hi - lo > 1) {

@@ -293,9 +293,11 @@ __device__ __forceinline__ D eta_k2_cross(const D* c, int side, bool central, D 
 
 // value of cell i at its right (side 0) or left (side 1) face, k = 2; c[0..2] = cells i-1..i+1;
 // eta_c: shape parameter of the central row (row 0), eta_x: of the extrapolating rows
+// shift (points off the face midpoint, Sec. 6): the transverse term sigma sy, added to each
+// candidate; the midpoint passes none
 template <typename R, typename D>
 __device__ __forceinline__ R cell_face_value_k2(const R* c, int side, R eta_c, R eta_x, const MethodParams& mp,
-                                               int* r_out) {
+                                               int* r_out, R shift = R(0.0), bool shifted = false) {
     R cand[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -304,7 +306,7 @@ __device__ __forceinline__ R cell_face_value_k2(const R* c, int side, R eta_c, R
         R s = R(0.0);
 #pragma unroll
         for (int j = 0; j < 2; ++j) s += (poly2_coef<R>(row + 1, j) + pert2_coef<R>(mp.rbf, row + 1, j) * eta) * c[1 - r + j];
-        cand[r] = s;
+        cand[r] = shifted ? s + shift : s;
     }
     if (mp.scheme == NPW_ENO_ || mp.scheme == NPW_RBF_ENO_) {
         const int r = fabs(D(c[1]) - D(c[0])) < fabs(D(c[2]) - D(c[1])) ? 1 : 0;
@@ -359,6 +361,94 @@ __device__ __forceinline__ uint32_t face_field_k2(const R* w, const MethodParams
     *vp = cell_face_value_k2<R, D>(w + 2, 1, er, erx, mp, &rr);
     fl |= (uint32_t(rl & 1) << 2) | (uint32_t(rr & 1) << 4);
     if (eta_out) *eta_out = el;
+    return fl;
+}
+
+// ---------------------------------------------------------------------------------------
+// k = 2 on the 5-cell cross at a point of the face (Sec. 6; the two Gauss points of eq.
+// 2DIntegral, Sec. 7): the 3-cell stencil of the two cells of the ENO row along the normal and
+// the transverse neighbour that ENO picks, evaluated sigma cell widths from the face midpoint,
+// is the Table k2 row plus sigma times the one-sided transverse difference sy toward that
+// neighbour (side sg = +1 / -1).  Its Taylor error there is e v_xx dx^2 + (1/24 + sg sigma/2 -
+// sigma^2/2) v_yy dy^2 - (sigma/2) v_xy dx dy (e = 1/6 for the two cells at the face, -1/3 for
+// the extrapolating pair, whose perturbation weights sum to -2 times the central row's), and the
+// shape parameter cancels it: numerator -a2 + t trans + x xy, central t = -1/4 + 3 sigma^2 -
+// 3 sg sigma, x = 3 sigma; extrapolating t = 1/8 - 3/2 sigma^2 + 3/2 sg sigma, x = -3/2 sigma;
+// xy is the mixed difference of the cell with the cell across the face on the sg side.
+// ---------------------------------------------------------------------------------------
+template <typename D>
+struct CrossSide {
+    D trans, sg, sy, xy;  // of one cell of the face: second difference, ENO side, one-sided difference, mixed
+};
+
+// transverse data of a cell from its column (lo, c, hi across the line) and, for xy, the cell
+// across the face (alo, a, ahi) on the same rows
+template <typename D>
+__device__ __forceinline__ CrossSide<D> cross_side(D lo, D c, D hi, D alo, D a, D ahi) {
+    CrossSide<D> cs;
+    const D dn = c - lo, up = hi - c;
+    cs.trans = (lo - D(2.0) * c) + hi;
+    const bool lower = fabs(dn) < fabs(up);
+    cs.sg = lower ? D(-1.0) : D(1.0);
+    cs.sy = lower ? dn : up;
+    cs.xy = lower ? -((alo - lo) - (a - c)) : ((ahi - hi) - (a - c));
+    return cs;
+}
+
+template <typename D>
+__device__ __forceinline__ D eta_k2_point(const D* c, int side, bool central, const CrossSide<D>& cs, D sigma,
+                                          const MethodParams& mp, uint32_t* zr) {
+    const D a = side == 0 ? c[0] : c[2];
+    const D b = c[1];
+    const D d = side == 0 ? c[2] : c[0];
+    const D s = cs.sg;
+    const D t_tr = central ? (D(-0.25) + D(3.0) * sigma * sigma) - D(3.0) * s * sigma
+                           : (D(0.125) - D(1.5) * sigma * sigma) + D(1.5) * s * sigma;
+    const D t_xy = central ? D(3.0) * sigma : D(-1.5) * sigma;
+    const D num = ((-a + D(2.0) * b - d) + t_tr * cs.trans) + t_xy * cs.xy;
+    const D den0 = -a + D(5.0) * b + D(2.0) * d;
+    const D mag = fabs(a) + D(5.0) * fabs(b) + D(2.0) * fabs(d);
+    if (mp.eta_guard > 0.0 && fabs(den0) <= D(mp.eta_guard) * mag) {
+        *zr |= FL_ZERO_GUARD;
+        return D(0.0);
+    }
+    const D e = (mp.rbf == NPW_RBF_GA_ ? D(1.0) : D(2.0)) * num / (den0 + D(mp.eps_M));
+    if (mp.eta_max > 0.0 && fabs(e) > D(mp.eta_max)) {
+        *zr |= FL_ZERO_BOUND;
+        return D(0.0);
+    }
+    return e;
+}
+
+// One field at one point of a face (sigma from its midpoint), k = 2 on the cross: as
+// face_field_k2, with l / r the transverse data of the cells behind v^- / v^+.
+template <typename R, typename D>
+__device__ __forceinline__ uint32_t face_point_k2(const R* w, const MethodParams& mp, R* vm, R* vp,
+                                                  const CrossSide<D>& l, const CrossSide<D>& r, D sigma) {
+    uint32_t fl = 0;
+    R el = R(0.0), er = R(0.0), elx = R(0.0), erx = R(0.0);
+    if (mp.scheme == NPW_RBF_ENO_ || mp.scheme == NPW_RBF_WENO_) {
+        const D cl[3] = {D(w[1]), D(w[2]), D(w[3])};
+        const D cr[3] = {D(w[2]), D(w[3]), D(w[4])};
+        if (mp.monotone_switch && k2_ratio_fires<D>(cl[0], cl[1], cl[2])) {
+            fl |= FL_SWITCH;
+        } else {
+            el = R(eta_k2_point<D>(cl, 0, true, l, sigma, mp, &fl));
+            elx = R(eta_k2_point<D>(cl, 0, false, l, sigma, mp, &fl));
+        }
+        if (mp.monotone_switch && k2_ratio_fires<D>(cr[0], cr[1], cr[2])) {
+            fl |= FL_SWITCH_R_K2;
+        } else {
+            uint32_t zr = 0;
+            er = R(eta_k2_point<D>(cr, 1, true, r, sigma, mp, &zr));
+            erx = R(eta_k2_point<D>(cr, 1, false, r, sigma, mp, &zr));
+            fl |= zr << 2;  // FL_ZERO_GUARD_R_K2, FL_ZERO_BOUND_R_K2
+        }
+    }
+    int rl = 0, rr = 0;
+    *vm = cell_face_value_k2<R, D>(w + 1, 0, el, elx, mp, &rl, R(sigma * l.sy), true);
+    *vp = cell_face_value_k2<R, D>(w + 2, 1, er, erx, mp, &rr, R(sigma * r.sy), true);
+    fl |= (uint32_t(rl & 1) << 2) | (uint32_t(rr & 1) << 4);
     return fl;
 }
 

@@ -70,6 +70,7 @@ struct MethodParams {
     int eta_eval;  // mixed precision, k = 3: 0 = double-float quotient (no FP64), 1 = FP64 evaluation
     int k;         // 2 (ENO2 / WENO3) or 3 (ENO3 / WENO5)
     int cross_2d;  // k = 2 in 2D: shape parameter on the 5-cell cross (Sec. 6)
+    int gauss_2d;  // k = 2 in 2D: two Gauss points per face (eq. 2DIntegral), else the midpoint
     double eps_M;
     double eps_weno;
     double gamma;

@@ -1120,6 +1120,40 @@ __host__ __device__ constexpr int stage2d_smem_elems() {
     return ((TY_2D + 6) * (TX_2D + 6) + TY_2D * (TX_2D + 1) + (TY_2D + 1) * TX_2D) * M;
 }
 
+// One face of a 2D tile with the two-point Gauss rule (Sec. 7, k = 2 on the cross of Sec. 6):
+// the face values at -+ 1/(2 sqrt 3) cell widths from the midpoint, their Lax-Friedrichs fluxes
+// and h = (h(-) + h(+)) / 2.  S: the 6-cell stencil along the normal ([j * M + k]); su: the
+// tile's cells with halo ([(by * BX + bx) * M + k]); (bx, by): the cell behind v^-, the cell
+// behind v^+ one step of `along` further; `across`: the step across the line.  Each point
+// counts as a face evaluation.
+template <typename R, typename D, int KIND, int M>
+__device__ __forceinline__ void gauss_face(const R* S, const R* su, int BX, int bx, int by, int along, int across,
+                                           R alpha, const MethodParams& mp, int dir, R* h, R* h1, EtaCount& ec,
+                                           bool counted) {
+    constexpr D G = D(0.28867513459481288225);  // 1 / (2 sqrt 3)
+    const int cl = by * BX + bx, cr = cl + along;
+    R vm0[M], vp0[M], vm1[M], vp1[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        auto at = [&](int c, int t) { return D(su[(c + t * across) * M + k]); };
+        const CrossSide<D> l = cross_side<D>(at(cl, -1), at(cl, 0), at(cl, 1), at(cr, -1), at(cr, 0), at(cr, 1));
+        const CrossSide<D> r = cross_side<D>(at(cr, -1), at(cr, 0), at(cr, 1), at(cl, -1), at(cl, 0), at(cl, 1));
+        R w[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) w[j] = S[j * M + k];
+        const uint32_t f0 = face_point_k2<R, D>(w, mp, &vm0[k], &vp0[k], l, r, -G);
+        const uint32_t f1 = face_point_k2<R, D>(w, mp, &vm1[k], &vp1[k], l, r, G);
+        if (counted) {
+            ec.face(f0, 2);
+            ec.face(f1, 2);
+        }
+    }
+    lf_flux<R, KIND, M>(vm0, vp0, alpha, mp, dir, h1);
+    lf_flux<R, KIND, M>(vm1, vp1, alpha, mp, dir, h);
+#pragma unroll
+    for (int k = 0; k < M; ++k) h[k] = R(0.5) * (h1[k] + h[k]);
+}
+
 template <typename R, typename D, int KIND>
 __device__ __forceinline__ void stage2d_body(const Stage2DArgs& a, const Inst2D& in, Ctl* ctl, int tile,
                                              unsigned char* smem_raw) {
@@ -1138,8 +1172,9 @@ __device__ __forceinline__ void stage2d_body(const Stage2DArgs& a, const Inst2D&
     const int64_t nx = in.nx, ny = in.ny, cells = nx * ny;
     const R* uin = reinterpret_cast<const R*>(a.uin) + in.off;
     const int tid = threadIdx.x;
-    const bool cross = a.mp.k == 2 && a.mp.cross_2d &&
-                       (a.mp.scheme == NPW_RBF_ENO_ || a.mp.scheme == NPW_RBF_WENO_);
+    const bool gauss = a.mp.k == 2 && a.mp.gauss_2d;
+    const bool cross = gauss || (a.mp.k == 2 && a.mp.cross_2d &&
+                                 (a.mp.scheme == NPW_RBF_ENO_ || a.mp.scheme == NPW_RBF_WENO_));
     for (int idx = tid; idx < BX * BY * M; idx += blockDim.x) {
         const int k = idx / (BX * BY);
         const int rem = idx - k * BX * BY;
@@ -1168,6 +1203,17 @@ __device__ __forceinline__ void stage2d_body(const Stage2DArgs& a, const Inst2D&
         for (int j = 0; j < 6; ++j)
 #pragma unroll
             for (int k = 0; k < M; ++k) S[j * M + k] = su[((qy + 3) * BX + qx + j) * M + k];
+        if (gauss) {
+            // two Gauss points (Sec. 7): the cross reconstruction at y_j -+ dy / (2 sqrt 3), the
+            // mean of the two Lax-Friedrichs fluxes; transverse data of the cells qx-1 (v^-) and qx
+            // (v^+) from rows qy-1..qy+1, each with the other as the cell across the face
+            R h1[M];
+            gauss_face<R, D, KIND, M>(S, su, BX, qx + 2, qy + 3, 1, BX, ax, a.mp, 0, h, h1, ec,
+                                      qy < cnt_y && face_owned(qx, cnt_x, last_x));
+#pragma unroll
+            for (int k = 0; k < M; ++k) hx[(qy * (TX_2D + 1) + qx) * M + k] = h[k];
+            continue;
+        }
         if (cross) {
             // transverse (y) second differences of the cells qx-1 and qx of row qy
             D T[2 * M];
@@ -1199,6 +1245,14 @@ __device__ __forceinline__ void stage2d_body(const Stage2DArgs& a, const Inst2D&
         for (int j = 0; j < 6; ++j)
 #pragma unroll
             for (int k = 0; k < M; ++k) S[j * M + k] = su[((qy + j) * BX + qx + 3) * M + k];
+        if (gauss) {
+            R h1[M];
+            gauss_face<R, D, KIND, M>(S, su, BX, qx + 3, qy + 2, BX, 1, ay, a.mp, 1, h, h1, ec,
+                                      qx < cnt_x && face_owned(qy, cnt_y, last_y));
+#pragma unroll
+            for (int k = 0; k < M; ++k) hy[(qy * TX_2D + qx) * M + k] = h[k];
+            continue;
+        }
         if (cross) {
             // transverse (x) second differences of the cells qy-1 and qy of column qx
             D T[2 * M];

@@ -30,7 +30,7 @@ class npw_params(C.Structure):
                 ("adv_speed", C.c_double), ("adv_speed_y", C.c_double), ("inflow", C.c_double * 4),
                 ("eta_guard", C.c_double), ("batch_mode", C.c_int32), ("tile_1d", C.c_int32),
                 ("eta_max", C.c_double), ("cross_2d", C.c_int32), ("bc_y", C.c_int32), ("tie_tol", C.c_double),
-                ("max_steps", C.c_int64)]
+                ("max_steps", C.c_int64), ("gauss_2d", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class npw_solve_stats(C.Structure):
@@ -75,11 +75,13 @@ class Params:
     bc_y: int = -1  # 2D: boundary of the y direction (-1: the bc argument)
     tie_tol: float = 0.0  # near-tie margin of npweno_reconstruct's flags (0: 1e-10)
     max_steps: int = 0  # step limit of a solve (0: automatic); NPW_ETIMEOUT when reached
+    gauss_2d: int = 0  # 2D, FP64, k = 2: two Gauss points per face (0: the midpoint)
 
     def c(self) -> npw_params:
         p = npw_params()
         for f in ("k", "scheme", "rbf", "monotone_switch", "switch_variant", "characteristic", "precision",
-                  "eta_eval", "batch_mode", "tile_1d", "cross_2d", "bc_y", "max_steps"):
+                  "eta_eval", "batch_mode", "tile_1d", "cross_2d", "bc_y", "max_steps",
+                  "gauss_2d"):
             setattr(p, f, int(getattr(self, f)))
         for f in ("eps_M", "eps_weno", "gamma", "adv_speed", "adv_speed_y", "eta_guard", "eta_max", "tie_tol"):
             setattr(p, f, float(getattr(self, f)))

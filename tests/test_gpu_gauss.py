@@ -1,0 +1,158 @@
+"""The two-point Gauss rule of eq. 2DIntegral on the GPU (params.gauss_2d, NPW_FP64, k = 2 on the
+5-cell cross of Sec. 6) against the oracle, and its third-order convergence on Sec. 7 Example 1.
+
+Each face is reconstructed at -+ 1/(2 sqrt 3) cell widths from its midpoint with the shape
+parameter that cancels the Taylor error there, and its flux is the mean of the two
+Lax-Friedrichs fluxes.  Bars: one RK3 step equals the oracle to 1e-12 relative (ragged tiles,
+every boundary condition, scalar and Euler); whole solves to 1e-11 with equal step counts and
+decision counts; the queue equals the solve entry point bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1602_00182_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def npw():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1602_00182_gb300 import build as b
+    b.build()
+    import paper_1602_00182_gb300.npweno as m
+    m.load()
+    return m
+
+
+def _dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _gp(npw, o):
+    return npw.Params(k=2, scheme=o.scheme, rbf=o.rbf, monotone_switch=o.monotone_switch, cross_2d=o.cross_2d,
+                      gauss_2d=1, inflow=o.inflow, bc_y=o.bc_y, eta_max=o.eta_max if o.eta_max > 0 else -1.0)
+
+
+def _avg_sin(n, kx=1, ky=1):
+    """Exact cell averages of sin(2 pi (kx x + ky y)) on the periodic unit square."""
+    h = 1.0 / n
+    x0 = np.arange(n) * h
+    a, b = 2 * np.pi * kx, 2 * np.pi * ky
+    fx = (np.exp(1j * a * (x0 + h)) - np.exp(1j * a * x0)) / (1j * a * h)
+    fy = (np.exp(1j * b * (x0 + h)) - np.exp(1j * b * x0)) / (1j * b * h)
+    return np.imag(fy[:, None] * fx[None, :])
+
+
+def _field(nx, ny, seed):
+    g = np.random.default_rng(seed)
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    U = 1.0 + 0.4 * np.sin(2 * np.pi * (x[None, :] + 0.7 * y[:, None])) + 0.1 * np.cos(6 * np.pi * y)[:, None]
+    U[ny // 2:, nx // 3:] += 0.3 * g.uniform()
+    U += 0.05 * np.cos(2 * np.pi * (2 * x[None, :] - y[:, None]))
+    return U
+
+
+@pytest.mark.parametrize("shape", [(40, 24), (70, 45)])
+@pytest.mark.parametrize("bc", [O.PERIODIC, O.TRANSMISSIVE, O.INFLOW])
+@pytest.mark.parametrize("scheme,rbf,switch", [(O.RBF_ENO, O.MQ, 1), (O.RBF_WENO, O.MQ, 0), (O.RBF_ENO, O.GA, 0),
+                                               (O.ENO, O.MQ, 0), (O.WENO_JS, O.MQ, 0)])
+def test_gauss_step_fp64(npw, shape, bc, scheme, rbf, switch):
+    """One RK3 step of Burgers on a ragged grid (the 32 x 8 tiles end mid-tile) equals the
+    oracle for every boundary condition; the Gauss rule differs from the midpoint rule."""
+    nx, ny = shape
+    U = _field(nx, ny, nx * ny + bc)
+    d = 1.0 / nx
+    op = O.Params(k=2, scheme=scheme, rbf=rbf, monotone_switch=switch, cross_2d=1, gauss_2d=1, inflow=(1.2, 0, 0, 0))
+    ref = O.rk3_step_2d(U, d, d, 0.2 * d, O.BURGERS, bc, op)
+    gu = _dev(U)
+    npw.npweno_rk3_step_2d(gu, d, d, 0.2 * d, O.BURGERS, bc, _gp(npw, op))
+    assert _rel(gu.cpu().numpy(), ref) <= FP64_TOL
+    mid = O.rk3_step_2d(U, d, d, 0.2 * d, O.BURGERS, bc, O.Params(k=2, scheme=scheme, rbf=rbf, monotone_switch=switch,
+                                                                cross_2d=1, inflow=(1.2, 0, 0, 0)))
+    assert _rel(mid, ref) > 1e-9
+
+
+def test_gauss_step_mixed_boundaries(npw):
+    """bc_y differs from bc (periodic x, inflow bottom): the diagonal neighbours of the corner
+    cells follow each direction's rule."""
+    nx, ny = 37, 29
+    U = _field(nx, ny, 5)
+    d = 1.0 / nx
+    op = O.Params(k=2, scheme=O.RBF_ENO, cross_2d=1, gauss_2d=1, inflow=(0.8, 0, 0, 0), bc_y=O.INFLOW)
+    ref = O.rk3_step_2d(U, d, d, 0.2 * d, O.ADVECTION, O.PERIODIC, op)
+    gu = _dev(U)
+    npw.npweno_rk3_step_2d(gu, d, d, 0.2 * d, O.ADVECTION, O.PERIODIC, _gp(npw, op))
+    assert _rel(gu.cpu().numpy(), ref) <= FP64_TOL
+
+
+def test_gauss_euler_vortex_solve(npw):
+    U, d = I.isentropic_vortex(48, 4.0, 5.0, 5.0, npts=2)
+    op = O.Params(k=2, scheme=O.RBF_ENO, cross_2d=1, gauss_2d=1)
+    ref, rst = O.solve_2d(U, d, d, 10 * 0.1 * d, 0.4, O.EULER2D, O.PERIODIC, op)
+    gu = _dev(U)
+    st = npw.npweno_solve_2d(gu, d, d, 10 * 0.1 * d, 0.4, O.EULER2D, O.PERIODIC, _gp(npw, op))
+    assert st["status"] == 0 and st["steps"] == rst["steps"]
+    assert _rel(gu.cpu().numpy(), ref) <= 1e-11
+    assert st["eta"] == rst["eta"]
+
+
+def test_example1_third_order_on_the_gpu(npw):
+    """Sec. 7 Example 1 to T = 0.5 (dt = 0.1 dx), RBF-ENO k = 2 (MQ) on the cross, switch off,
+    |eta| <= 1: with the Gauss rule the L1 and Linf errors against the exact solution fall at
+    third order up to N = 320 (the midpoint rule: second); at N <= 40 the run equals the
+    oracle's."""
+    pg = O.Params(k=2, scheme=O.RBF_ENO, cross_2d=1, gauss_2d=1, monotone_switch=0, eta_max=1.0)
+    errs, errs_mid = [], []
+    ns = (20, 40, 80, 160, 320)
+    for n in ns:
+        u0 = _avg_sin(n)  # also the exact solution at T = 0.5
+        gu = _dev(u0)
+        st = npw.npweno_solve_2d(gu, 1.0 / n, 1.0 / n, 0.5, 0.2, O.ADVECTION, O.PERIODIC, _gp(npw, pg))
+        assert st["status"] == 0 and st["t"] == 0.5
+        assert st["eta"]["bound"] <= 0.01 * st["eta"]["eval"]
+        got = gu.cpu().numpy()
+        e = np.abs(got - u0)
+        errs.append((e.mean(), e.max()))
+        pm = npw.Params(k=2, scheme=npw.NPW_RBF_ENO, cross_2d=1, monotone_switch=0, eta_max=1.0)
+        gm = _dev(u0)
+        npw.npweno_solve_2d(gm, 1.0 / n, 1.0 / n, 0.5, 0.2, O.ADVECTION, O.PERIODIC, pm)
+        em = np.abs(gm.cpu().numpy() - u0)
+        errs_mid.append((em.mean(), em.max()))
+        if n <= 40:
+            ref, rst = O.solve_2d(u0, 1.0 / n, 1.0 / n, 0.5, 0.2, O.ADVECTION, O.PERIODIC, pg)
+            assert st["steps"] == rst["steps"] and _rel(got, ref) <= 1e-11 and st["eta"] == rst["eta"]
+    orders = [[np.log2(errs[i][q] / errs[i + 1][q]) for q in range(2)] for i in range(len(ns) - 1)]
+    orders_mid = [[np.log2(errs_mid[i][q] / errs_mid[i + 1][q]) for q in range(2)] for i in range(len(ns) - 1)]
+    print("gauss", errs, orders, "midpoint", errs_mid, orders_mid)
+    assert all(min(o) > 2.75 for o in orders[1:]), orders
+    assert all(max(o) < 2.2 for o in orders_mid[1:]), orders_mid
+    assert errs[-1][0] < errs_mid[-1][0] / 20
+
+
+def test_gauss_through_the_queue(npw):
+    """Two 2D instances with the Gauss rule in one work-queue batch equal npweno_solve_2d."""
+    specs, fields = [], []
+    for n in (40, 64):
+        specs.append(dict(kind=npw.NPW_FLUX_ADVECTION, nx=n, ny=n, dx=1.0 / n, dy=1.0 / n, t_end=0.05, cfl=0.4, bc=0))
+        fields.append(_avg_sin(n, 1, 2).ravel())
+    table, total, offs = npw.make_queue_instances(specs)
+    arena = _dev(np.concatenate(fields))
+    p = npw.Params(k=2, scheme=npw.NPW_RBF_ENO, cross_2d=1, gauss_2d=1, monotone_switch=0, eta_max=1.0)
+    st, stats = npw.npweno_queue_solve(arena, table, p)
+    assert st == 0
+    a = arena.cpu().numpy()
+    for sp, u0, off, s in zip(specs, fields, offs, stats):
+        g = _dev(u0.reshape(sp["ny"], sp["nx"]))
+        rs = npw.npweno_solve_2d(g, sp["dx"], sp["dy"], sp["t_end"], sp["cfl"], sp["kind"], sp["bc"], p)
+        assert s["steps"] == rs["steps"] and np.array_equal(a[off:off + u0.size], g.cpu().numpy().ravel())

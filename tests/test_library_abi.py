@@ -43,6 +43,15 @@ def test_default_params_and_errors_without_gpu():
     assert p.eps_weno == 1e-6 and p.gamma == 1.4 and p.eps_M == 1e-12
     # the shape parameter as printed: no bound, no step limit, the default tie margin
     assert p.eta_max == 0.0 and p.max_steps == 0 and p.tie_tol == 0.0
+    # one quadrature point per face (the paper's runs) unless the Gauss rule is asked for
+    assert p.gauss_2d == 0
+    for kw, msg in ((dict(gauss_2d=1), b"k = 2"), (dict(gauss_2d=1, k=2, scheme=npw.NPW_RBF_ENO), b"cross_2d"),
+                    (dict(gauss_2d=1, k=2, scheme=npw.NPW_ENO, precision=1), b"NPW_FP64"),
+                    (dict(gauss_2d=2), b"gauss_2d")):
+        g = npw.Params(**kw).c()
+        st = lib.npweno_solve_2d(ctypes.c_void_p(16), 32, 32, 1, 0.1, 0.1, 0.1, 0.5, npw.NPW_FLUX_ADVECTION, 0,
+                                 ctypes.byref(g), ctypes.c_void_p(16), 1 << 30, None, None)
+        assert st == npw.NPW_EINVAL and msg in lib.npw_last_error(), (kw, lib.npw_last_error())
     # argument validation happens before any CUDA call
     bad = npw.Params(k=4).c()
     st = lib.npweno_reconstruct(ctypes.c_void_p(16), 100, 1, 0, ctypes.byref(bad), ctypes.c_void_p(16),
