@@ -1,11 +1,13 @@
 """Build libnpweno.so (the CUDA library behind include/npweno.h) in-tree for sm_103a.
 
-Five translation units are compiled in parallel with nvcc and linked into one shared
+Seven translation units are compiled in parallel with nvcc and linked into one shared
 object next to this file:
   npw_fp64.cu  -- double-precision kernels, --fmad=false (each operation rounded as written)
   npw_fp32.cu  -- mixed-precision kernels, also --fmad=false: every fused multiply-add is an
                   explicit fmaf, so the per-stage and the resident kernels (and any batch mix)
                   produce the same bits from the same data
+  npw_queue_fp64.cu, npw_queue_fp32.cu -- the work-queue kernels of each precision, one per
+                  instance shape (also --fmad=false)
   npw_api.cu   -- host runtime and the C ABI
   npw_noalloc.cu -- npweno_rk3_step_noalloc and its fixed device scratch array
   npw_format.cu  -- npw_format_check, the self-check of the integer float<->double format changes
@@ -29,6 +31,8 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}
 UNITS = {
     "npw_fp64.cu": ["--fmad=false"],
     "npw_fp32.cu": ["--fmad=false"],
+    "npw_queue_fp64.cu": ["--fmad=false"],
+    "npw_queue_fp32.cu": ["--fmad=false"],
     "npw_api.cu": [],
     "npw_noalloc.cu": [],
     "npw_format.cu": ["--fmad=false"],

@@ -1506,6 +1506,7 @@ struct QueueRun {
     npw::QueueArgs q{};
     bool fp32 = false;
     bool characteristic = false;
+    int shape = npw::QS_ANY;  // the one shape every queued instance has, else QS_ANY
     size_t smem = 0;
     int count = 0;
     // 1D items of each flux kind are contiguous: [begin, end) per kind, for the compensated copies
@@ -1519,8 +1520,8 @@ npw_status queue_step(const QueueRun& r) {
     for (int st = 0; st < 3; ++st) {
         q.stage = st;
         auto ev = stage_begin(r.s);
-        const cudaError_t e = r.fp32 ? npw::launch_queue_stage<float>(q, r.characteristic, r.smem, 0, r.s)
-                                     : npw::launch_queue_stage<double>(q, r.characteristic, r.smem, 0, r.s);
+        const cudaError_t e = r.fp32 ? npw::launch_queue_stage<float>(q, r.characteristic, r.shape, r.smem, 0, r.s)
+                                     : npw::launch_queue_stage<double>(q, r.characteristic, r.shape, r.smem, 0, r.s);
         stage_end(ev, r.s);
         if (e != cudaSuccess) return cuda_fail(e, "queue stage launch");
     }
@@ -1712,6 +1713,14 @@ npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32
     for (int i = 0; i < count; ++i)
         if (h2d[i])
             for (int32_t t = 0; t < h2[i].tiles_x * h2[i].tiles_y; ++t) items.push_back(npw::Tile{i, t});
+    // one shape for every instance with queue items: the kernel specialised for it
+    r.shape = -1;
+    for (int i = 0; i < count && r.shape != npw::QS_ANY; ++i) {
+        if (!h2d[i] && resident[i]) continue;
+        const int sh = npw::queue_shape_of(h2d[i] != 0, hk[i]);
+        r.shape = (r.shape < 0 || r.shape == sh) ? sh : (int)npw::QS_ANY;
+    }
+    if (r.shape < 0) r.shape = npw::QS_ANY;
     unsigned char* ws = r.ws;
     NPW_CUDA(cudaMemcpyAsync(ws + r.L.inst1, h1.data(), sizeof(npw::InstDev) * count, cudaMemcpyHostToDevice, r.s));
     NPW_CUDA(cudaMemcpyAsync(ws + r.L.inst2, h2.data(), sizeof(npw::Inst2D) * count, cudaMemcpyHostToDevice, r.s));
@@ -1959,11 +1968,14 @@ npw_status lane_round(npw_server* sv, int ln, int steps, bool* any_active) {
     int64_t new_kind_begin[3] = {0, 0, 0}, new_kind_end[3] = {0, 0, 0};
     bool has1d = false, has2d = false;
     int m1d = 1, m2d = 1;
+    int shape = -1;  // the one shape of the lane's active slots, else QS_ANY
     for (int k = 0; k < S; ++k) {
         const npw_server::Slot& sl = sv->slots[k];
         if (!sl.used || sl.lane != ln) continue;
         hk[k] = sl.req.flux_kind;
         h2d[k] = sl.is2d;
+        const int sh = npw::queue_shape_of(sl.is2d, sl.req.flux_kind);
+        shape = (shape < 0 || shape == sh) ? sh : (int)npw::QS_ANY;
         if (!sl.is2d) {
             h1[k] = npw::InstDev{sl.off, sl.req.n, sl.req.dx, sl.req.t_end, sl.req.cfl, sl.req.bc,
                                  (int32_t)tiles_of(sl.req.n, npw::TILE_1D)};
@@ -2052,8 +2064,8 @@ npw_status lane_round(npw_server* sv, int ln, int steps, bool* any_active) {
         for (int st = 0; st < 3; ++st) {
             q.stage = st;
             auto ev = stage_begin(sv->s);
-            const cudaError_t e = lane.fp32 ? npw::launch_queue_stage<float>(q, false, smem, 0, sv->s)
-                                            : npw::launch_queue_stage<double>(q, false, smem, 0, sv->s);
+            const cudaError_t e = lane.fp32 ? npw::launch_queue_stage<float>(q, false, shape, smem, 0, sv->s)
+                                            : npw::launch_queue_stage<double>(q, false, shape, smem, 0, sv->s);
             stage_end(ev, sv->s);
             if (e != cudaSuccess) return cuda_fail(e, "server queue stage launch");
         }

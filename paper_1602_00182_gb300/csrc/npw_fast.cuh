@@ -238,6 +238,13 @@ __device__ __forceinline__ bool seed_f(double v, float* out) {
 }
 
 
+// every argument is +0 or -0: a stencil of zero cell averages (a field at rest, such as the
+// momentum of a quiescent gas), whose denominator and guard threshold are both exactly 0, so the
+// guard (|den| <= eta_guard * magnitudes) holds in any precision
+__device__ __forceinline__ bool all_zero(float a, float b, float c, float d = 0.0f) {
+    return ((__float_as_uint(a) | __float_as_uint(b) | __float_as_uint(c) | __float_as_uint(d)) & 0x7FFFFFFFu) == 0u;
+}
+
 // The rare branches below are kept out of line: a call is executed only when taken, while an
 // inlined short branch may be turned into predicated instructions that take issue slots of
 // the FP64 pipe on every evaluation.
@@ -279,6 +286,7 @@ __device__ __forceinline__ void eta_pairs(float w0, float w1, float w2, float w3
 // NZ: the four averages are zero or normal (the cheaper widening applies); the other case
 // (subnormal, infinite or NaN averages) takes the same arithmetic out of line.
 static __device__ __noinline__ bool guard_exact(float w0, float w1, float w2, float w3, double eta_guard) {
+    // (an all-zero stencil never gets here: see all_zero)
     const double v0 = widen(w0), v1 = widen(w1), v2 = widen(w2), v3 = widen(w3);
     const double den0 = v0 - 15.0 * v1 + 15.0 * v2 - v3;
     return fabs(den0) <= eta_guard * (fabs(v0) + 15.0 * fabs(v1) + 15.0 * fabs(v2) + fabs(v3));
@@ -297,7 +305,7 @@ __device__ __forceinline__ float eta_quot(float w0, float w1, float w2, float w3
             const double g = widen_nz(guard);
             zero = d0 <= g * (1.0 + 0x1p-20) && (d0 < g * (1.0 - 0x1p-20) || guard_exact(w0, w1, w2, w3, fp.eta_guard_d));
         } else {
-            zero = guard_exact(w0, w1, w2, w3, fp.eta_guard_d);
+            zero = all_zero(w0, w1, w2, w3) || guard_exact(w0, w1, w2, w3, fp.eta_guard_d);
         }
         if (zero) {
             *fl |= FL_ZERO_GUARD;
@@ -336,10 +344,11 @@ __device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, f
     eta_pairs(w0, w1, w2, w3, nh, nl, dh, dl);
     if (fp.eta_guard > 0.0f) {  // certified as in eta_quot: exact where the float test is too close
         const float d0 = fabsf(dh + dl);
-        const bool zero = guard >= 0x1p-100f && d0 <= guard * (1.0f - 0x1p-19f)
+        const bool zero = all_zero(w0, w1, w2, w3) ||
+                          (guard >= 0x1p-100f && d0 <= guard * (1.0f - 0x1p-19f)
                               ? true
                               : ((guard < 0x1p-100f || d0 <= guard * (1.0f + 0x1p-19f)) &&
-                                 guard_exact(w0, w1, w2, w3, fp.eta_guard_d));
+                                 guard_exact(w0, w1, w2, w3, fp.eta_guard_d)));
         if (zero) {
             *fl |= FL_ZERO_GUARD;
             return 0.0f;
@@ -556,6 +565,10 @@ __device__ __forceinline__ void eta_k2_pair(const float* cf, int side, double tr
         const float magf = (fabsf(af) + 5.0f * fabsf(bf)) + 2.0f * fabsf(df);
         const float den0f = fmaf(2.0f, df, fmaf(5.0f, bf, -af));
         const float gm = fp.eta_guard * magf;
+        if (all_zero(af, bf, df)) {
+            *fl |= FL_ZERO_GUARD;
+            return;
+        }
         if (!(magf >= 0x1p-90f && fabsf(den0f) > gm + kE * magf * (1.0f + fp.eta_guard))) {
             const double a = widen(af), b = widen(bf), d = widen(df);
             if (fabs((-a + 5.0 * b) + 2.0 * d) <= mp.eta_guard * ((fabs(a) + 5.0 * fabs(b)) + 2.0 * fabs(d))) {

@@ -224,6 +224,14 @@ struct QueueArgs {
     MethodParams mp;
 };
 
+// Instance shape of a queue batch whose instances all have one dimension and flux kind: the
+// queue kernel instantiated for it carries only that body (and that body's register count);
+// QS_ANY dispatches per item.
+enum QueueShape { QS_ANY = 0, QS_1D_ADV, QS_1D_BURG, QS_1D_EULER, QS_2D_ADV, QS_2D_BURG, QS_2D_EULER };
+inline int queue_shape_of(bool is2d, int kind) {
+    return (is2d ? QS_2D_ADV : QS_1D_ADV) + (kind == NPW_FLUX_ADVECTION ? 0 : kind == NPW_FLUX_BURGERS ? 1 : 2);
+}
+
 // ---- launchers (one definition per precision translation unit) ---------------------------
 template <typename R>
 cudaError_t launch_reconstruct(const R* u, int64_t n, int m, int bc, const MethodParams& mp, R* vm, R* vp,
@@ -243,8 +251,10 @@ template <typename R>
 cudaError_t launch_stage2d(const Stage2DArgs& a, int tiles, int kind, cudaStream_t s);
 // queue kernels: smem_bytes for the instance kinds present (see queue_smem_bytes); blocks = 0
 // asks for one wave of resident CTAs (occupancy x SMs)
+// shape: a QueueShape that every instance of the batch has, or QS_ANY
 template <typename R>
-cudaError_t launch_queue_stage(const QueueArgs& q, bool characteristic, size_t smem_bytes, int blocks, cudaStream_t s);
+cudaError_t launch_queue_stage(const QueueArgs& q, bool characteristic, int shape, size_t smem_bytes, int blocks,
+                               cudaStream_t s);
 template <typename R>
 cudaError_t launch_queue_alpha(const QueueArgs& q, cudaStream_t s);
 template <typename R>

@@ -1421,17 +1421,18 @@ __device__ __forceinline__ void queue_item_2d(const Stage2DArgs& a2, const Inst2
         stage2d_body<R, double, KIND>(a2, in, ctl, tile, smem);
 }
 
-template <typename R, int K, bool CHAR>
+template <typename R, int K, bool CHAR, int SHAPE>
 __global__ void __launch_bounds__(THREADS_1D) queue_stage_kernel(QueueArgs q) {
     static_assert(THREADS_1D == TX_2D * TY_2D, "1D and 2D items share the CTA shape");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
-    const void* in_[3] = {q.u, q.u1, q.u2};
-    void* out_[3] = {q.u1, q.u2, q.u};
+    // stage input and output: u -> u1 -> u2 -> u (selects, not an indexed local array)
+    const void* sin = q.stage == 0 ? q.u : (q.stage == 1 ? q.u1 : q.u2);
+    void* sout = q.stage == 0 ? q.u1 : (q.stage == 1 ? q.u2 : q.u);
     Stage1DArgs a1{};
-    a1.uin = in_[q.stage];
+    a1.uin = sin;
     a1.un = q.u;
-    a1.uout = out_[q.stage];
+    a1.uout = sout;
     a1.u = reinterpret_cast<float*>(q.u);
     a1.d1 = reinterpret_cast<float*>(q.u1);
     a1.d2 = reinterpret_cast<float*>(q.u2);
@@ -1442,9 +1443,9 @@ __global__ void __launch_bounds__(THREADS_1D) queue_stage_kernel(QueueArgs q) {
     a1.tile = q.tile;
     a1.mp = q.mp;
     Stage2DArgs a2{};
-    a2.uin = in_[q.stage];
+    a2.uin = sin;
     a2.un = q.u;
-    a2.uout = out_[q.stage];
+    a2.uout = sout;
     a2.stage = q.stage;
     a2.advance = q.advance;
     a2.mp = q.mp;
@@ -1455,8 +1456,20 @@ __global__ void __launch_bounds__(THREADS_1D) queue_stage_kernel(QueueArgs q) {
         if (it >= q.nitems) break;  // uniform over the CTA
         const Tile w = q.items[it];
         Ctl* ctl = q.ctl + w.inst;
-        const int kind = q.kind[w.inst];
-        if (q.is2d[w.inst]) {
+        if constexpr (SHAPE == QS_1D_ADV) {
+            queue_item_1d<R, K, CHAR, NPW_FLUX_ADVECTION_>(a1, w, q.inst1[w.inst], ctl, smem_raw);
+        } else if constexpr (SHAPE == QS_1D_BURG) {
+            queue_item_1d<R, K, CHAR, NPW_FLUX_BURGERS_>(a1, w, q.inst1[w.inst], ctl, smem_raw);
+        } else if constexpr (SHAPE == QS_1D_EULER) {
+            queue_item_1d<R, K, CHAR, NPW_FLUX_EULER1D_>(a1, w, q.inst1[w.inst], ctl, smem_raw);
+        } else if constexpr (SHAPE == QS_2D_ADV) {
+            queue_item_2d<R, K, NPW_FLUX_ADVECTION_>(a2, q.inst2[w.inst], ctl, w.start, smem_raw);
+        } else if constexpr (SHAPE == QS_2D_BURG) {
+            queue_item_2d<R, K, NPW_FLUX_BURGERS_>(a2, q.inst2[w.inst], ctl, w.start, smem_raw);
+        } else if constexpr (SHAPE == QS_2D_EULER) {
+            queue_item_2d<R, K, NPW_FLUX_EULER2D_>(a2, q.inst2[w.inst], ctl, w.start, smem_raw);
+        } else if (q.is2d[w.inst]) {
+            const int kind = q.kind[w.inst];
             const Inst2D& in = q.inst2[w.inst];
             if (kind == NPW_FLUX_EULER2D_)
                 queue_item_2d<R, K, NPW_FLUX_EULER2D_>(a2, in, ctl, w.start, smem_raw);
@@ -1465,6 +1478,7 @@ __global__ void __launch_bounds__(THREADS_1D) queue_stage_kernel(QueueArgs q) {
             else
                 queue_item_2d<R, K, NPW_FLUX_ADVECTION_>(a2, in, ctl, w.start, smem_raw);
         } else {
+            const int kind = q.kind[w.inst];
             const InstDev& in = q.inst1[w.inst];
             if (kind == NPW_FLUX_EULER1D_)
                 queue_item_1d<R, K, CHAR, NPW_FLUX_EULER1D_>(a1, w, in, ctl, smem_raw);
