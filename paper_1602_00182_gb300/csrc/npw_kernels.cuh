@@ -325,11 +325,14 @@ __device__ __forceinline__ void stage1d_body(const Stage1DArgs& a, const Tile td
     const R* uin = reinterpret_cast<const R*>(a.uin) + in.off;
     const int span = cnt + 6;
 
-    // halo load: cell c0 - 3 + j, field k; consecutive threads read consecutive cells
-    for (int idx = threadIdx.x; idx < span * M; idx += blockDim.x) {
-        const int k = idx / span;
-        const int j = idx - k * span;
-        su[j * M + k] = line_get<R>(uin + k * n, n, 1, (int64_t)c0 - 3 + j, in.bc, a.mp.inflow[k]);
+    // halo load: cell c0 - 3 + j, field k; consecutive threads read consecutive cells (the
+    // field index is a compile-time constant: an indexed parameter array would live in local
+    // memory)
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const double inflow_k = a.mp.inflow[k];
+        for (int j = threadIdx.x; j < span; j += blockDim.x)
+            su[j * M + k] = line_get<R>(uin + k * n, n, 1, (int64_t)c0 - 3 + j, in.bc, inflow_k);
     }
     const double dt = *(volatile double*)&ctl->dt;
     const R alpha = R(*(volatile double*)&ctl->alpha);
@@ -924,10 +927,13 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
     constexpr int BX = TX_2D + 6, BY = TY_2D + 6;
     constexpr int NFX = (TX_2D + 1) * TY_2D;  // x faces: (qx, qy), qx = 0..TX between cells qx-1, qx
     constexpr int NFY = TX_2D * (TY_2D + 1);  // y faces: (qx, qy), qy = 0..TY
+    constexpr int NF = NFX + NFY;
+    // field-major layout: su[k][by][bx], and ef, vmf, vpf [k][face] (x faces, then y faces), so
+    // that consecutive threads (consecutive cells or faces of one field) hit consecutive banks
     float* su = smem;                          // [BY * BX * M]
-    float* ef = su + BY * BX * M;              // [(NFX + NFY) * M] eta per (face, field); then the fluxes
-    float* vmf = ef + (NFX + NFY) * M;         // v^- per (face, field)
-    float* vpf = vmf + (NFX + NFY) * M;        // v^+ per (face, field)
+    float* ef = su + BY * BX * M;              // [M][NF] eta per (field, face); then the fluxes
+    float* vmf = ef + NF * M;                  // v^- per (field, face)
+    float* vpf = vmf + NF * M;                 // v^+ per (field, face)
     __shared__ float red[32];
     __shared__ int redbad[32];
     __shared__ float red2[32];
@@ -941,14 +947,18 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
     const int tid = threadIdx.x, nthr = blockDim.x;
     const fast::FParams fp = fast::fparams(a.mp);
     const bool cross = K == 2 && a.mp.cross_2d && (a.mp.scheme == NPW_RBF_ENO_ || a.mp.scheme == NPW_RBF_WENO_);
-    for (int idx = tid; idx < BX * BY * M; idx += nthr) {
-        const int k = idx / (BX * BY);
-        const int rem = idx - k * BX * BY;
-        const int by = rem / BX, bx = rem - by * BX;
-        // the corners are read only by the 5-cell cross (transverse differences of halo cells)
-        const bool corner = (bx < 3 || bx >= TX_2D + 3) && (by < 3 || by >= TY_2D + 3);
-        su[(by * BX + bx) * M + k] =
-            (corner && !cross) ? 0.0f : halo_get(uin + k * cells, in, tx0 - 3 + bx, ty0 - 3 + by, a.mp.inflow_f[k]);
+    // the field index is a compile-time constant in each loop (an indexed parameter array would
+    // put the stage arguments in local memory)
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const float inflow_k = a.mp.inflow_f[k];
+        for (int rem = tid; rem < BX * BY; rem += nthr) {
+            const int by = rem / BX, bx = rem - by * BX;
+            // the corners are read only by the 5-cell cross (transverse differences of halo cells)
+            const bool corner = (bx < 3 || bx >= TX_2D + 3) && (by < 3 || by >= TY_2D + 3);
+            su[(k * BY + by) * BX + bx] =
+                (corner && !cross) ? 0.0f : halo_get(uin + k * cells, in, tx0 - 3 + bx, ty0 - 3 + by, inflow_k);
+        }
     }
     if (tid == 0) {
         s_par[0] = (float)(*(volatile double*)&ctl->alpha);
@@ -967,11 +977,11 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
     auto own_y = [&](int qx, int qy) {
         return tx0 + qx < nx && face_owned(qy, (int)min((int64_t)TY_2D, ny - ty0), ty0 + TY_2D >= ny);
     };
-#define NPW_SU(bx, by, k) su[((by) * BX + (bx)) * M + (k)]
+#define NPW_SU(bx, by, k) su[((k) * BY + (by)) * BX + (bx)]
     // E: item = (face, field); x face (qx, qy) has the eta stencil su[qy+3][qx+1 .. qx+4],
     // y face (qx, qy) su[qy+1 .. qy+4][qx+3]
-    for (int it = tid; K == 3 && it < (NFX + NFY) * M; it += nthr) {
-        const int k = it % M, f = it / M;
+    for (int it = tid; K == 3 && it < NF * M; it += nthr) {
+        const int k = it / NF, f = it - k * NF;
         float w0, w1, w2, w3;
         if (f < NFX) {
             const int qy = f / (TX_2D + 1), qx = f - qy * (TX_2D + 1);
@@ -988,7 +998,7 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
             w3 = NPW_SU(qx + 3, qy + 4, k);
         }
         uint32_t fl = 0;
-        ef[it] = fast::face_eta(w0, w1, w2, w3, fp, &fl);
+        ef[k * NF + f] = fast::face_eta(w0, w1, w2, w3, fp, &fl);
         const bool own = f < NFX ? own_x(f % (TX_2D + 1), f / (TX_2D + 1)) : own_y((f - NFX) % TX_2D, (f - NFX) / TX_2D);
         if (own) ec.face_k3(fl);
     }
@@ -998,7 +1008,7 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
     // last face.
     constexpr int NCX = (TX_2D + 2) * TY_2D, NCY = TX_2D * (TY_2D + 2);
     for (int it = tid; it < (NCX + NCY) * M; it += nthr) {
-        const int k = it % M, c = it / M;
+        const int k = it / (NCX + NCY), c = it - k * (NCX + NCY);
         float cc[5];
         double trans = 0.0;  // k = 2 cross: transverse second difference of the cell
         int fl_idx, fr_idx;  // faces left / right of the cell (-1 when outside the tile)
@@ -1015,8 +1025,10 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
                 trans = (fast::widen(NPW_SU(cx + 3, qy + 2, k)) - 2.0 * fast::widen(NPW_SU(cx + 3, qy + 3, k))) +
                         fast::widen(NPW_SU(cx + 3, qy + 4, k));
         } else {
+            // consecutive threads take consecutive columns of one row (no shared-memory bank
+            // conflicts on the column stencil or on the face arrays)
             const int g = c - NCX;
-            const int qx = g / (TY_2D + 2), cy = g - qx * (TY_2D + 2) - 1;
+            const int cy = g / TX_2D - 1, qx = g - (cy + 1) * TX_2D;
 #pragma unroll
             for (int j = 0; j < 5; ++j) cc[j] = NPW_SU(qx + 3, cy + 1 + j, k);
             fl_idx = cy >= 0 ? NFX + cy * TX_2D + qx : -1;
@@ -1029,16 +1041,16 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
         }
         float vm, vp;
         if constexpr (K == 3) {
-            const float er = fr_idx >= 0 ? ef[fr_idx * M + k] : 0.0f;
-            const float el = fl_idx >= 0 ? ef[fl_idx * M + k] : 0.0f;
+            const float er = fr_idx >= 0 ? ef[k * NF + fr_idx] : 0.0f;
+            const float el = fl_idx >= 0 ? ef[k * NF + fl_idx] : 0.0f;
             fast::cell_recon(cc, er, el, fp, &vm, &vp);
         } else {
             const uint32_t d = fast::cell_recon_k2(cc + 1, trans, a.mp, fp, &vm, &vp);
             if (own_r) fast::count_k2(ec, d, 0);
             if (own_l) fast::count_k2(ec, d, 1);
         }
-        if (fr_idx >= 0) vmf[fr_idx * M + k] = vm;
-        if (fl_idx >= 0) vpf[fl_idx * M + k] = vp;
+        if (fr_idx >= 0) vmf[k * NF + fr_idx] = vm;
+        if (fl_idx >= 0) vpf[k * NF + fl_idx] = vp;
     }
     flush_counts(ec, ctl, a.mp);
     __syncthreads();
@@ -1047,15 +1059,15 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
         float vm[M], vp[M], h[M];
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-            vm[k] = vmf[f * M + k];
-            vp[k] = vpf[f * M + k];
+            vm[k] = vmf[k * NF + f];
+            vp[k] = vpf[k * NF + f];
         }
         if (f < NFX)
             lf_flux<float, KIND, M>(vm, vp, ax, a.mp, 0, h);
         else
             lf_flux<float, KIND, M>(vm, vp, ay, a.mp, 1, h);
 #pragma unroll
-        for (int k = 0; k < M; ++k) ef[f * M + k] = h[k];
+        for (int k = 0; k < M; ++k) ef[k * NF + f] = h[k];
     }
     __syncthreads();
 #undef NPW_SU
@@ -1072,11 +1084,11 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
         float U[M];
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-            const float* hx = ef;
-            const float* hy = ef + NFX * M;
-            float L = -((hx[(qy * (TX_2D + 1) + qx + 1) * M + k] - hx[(qy * (TX_2D + 1) + qx) * M + k]) / dxR);
-            L = L - (hy[((qy + 1) * TX_2D + qx) * M + k] - hy[(qy * TX_2D + qx) * M + k]) / dyR;
-            const float uk = su[((qy + 3) * BX + qx + 3) * M + k];
+            const float* hx = ef + k * NF;
+            const float* hy = hx + NFX;
+            float L = -((hx[qy * (TX_2D + 1) + qx + 1] - hx[qy * (TX_2D + 1) + qx]) / dxR);
+            L = L - (hy[(qy + 1) * TX_2D + qx] - hy[qy * TX_2D + qx]) / dyR;
+            const float uk = su[(k * BY + qy + 3) * BX + qx + 3];
             const int64_t gidx = k * cells + gj * nx + gi;
             float o;
             if (a.stage == 0) {
@@ -1175,17 +1187,19 @@ __device__ __forceinline__ void stage2d_body(const Stage2DArgs& a, const Inst2D&
     const bool gauss = a.mp.k == 2 && a.mp.gauss_2d;
     const bool cross = gauss || (a.mp.k == 2 && a.mp.cross_2d &&
                                  (a.mp.scheme == NPW_RBF_ENO_ || a.mp.scheme == NPW_RBF_WENO_));
-    for (int idx = tid; idx < BX * BY * M; idx += blockDim.x) {
-        const int k = idx / (BX * BY);
-        const int rem = idx - k * BX * BY;
-        const int by = rem / BX, bx = rem - by * BX;
-        // the corners are read only by the 5-cell cross of k = 2 (transverse differences of the
-        // halo cells next to the tile)
-        const bool corner = (bx < 3 || bx >= TX_2D + 3) && (by < 3 || by >= TY_2D + 3);
-        su[(by * BX + bx) * M + k] =
-            (corner && !cross) ? R(0.0)
-                               : grid_get<R>(uin + k * cells, in, (int64_t)tx0 - 3 + bx, (int64_t)ty0 - 3 + by,
-                                             a.mp.inflow[k]);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const double inflow_k = a.mp.inflow[k];
+        for (int rem = tid; rem < BX * BY; rem += blockDim.x) {
+            const int by = rem / BX, bx = rem - by * BX;
+            // the corners are read only by the 5-cell cross of k = 2 (transverse differences of
+            // the halo cells next to the tile)
+            const bool corner = (bx < 3 || bx >= TX_2D + 3) && (by < 3 || by >= TY_2D + 3);
+            su[(by * BX + bx) * M + k] =
+                (corner && !cross) ? R(0.0)
+                                   : grid_get<R>(uin + k * cells, in, (int64_t)tx0 - 3 + bx, (int64_t)ty0 - 3 + by,
+                                                 inflow_k);
+        }
     }
     const double dt = *(volatile double*)&ctl->dt;
     const R ax = R(*(volatile double*)&ctl->alpha);
@@ -1421,8 +1435,15 @@ __device__ __forceinline__ void queue_item_2d(const Stage2DArgs& a2, const Inst2
         stage2d_body<R, double, KIND>(a2, in, ctl, tile, smem);
 }
 
+// CTAs per SM the register allocation aims for: 5 for the specialised mixed-precision k = 3
+// kernels (48 registers a thread; their shared memory allows at least as many), else no bound
 template <typename R, int K, bool CHAR, int SHAPE>
-__global__ void __launch_bounds__(THREADS_1D) queue_stage_kernel(QueueArgs q) {
+constexpr int queue_min_blocks() {
+    return (sizeof(R) == sizeof(float) && K == 3 && !CHAR && SHAPE != QS_ANY && SHAPE != QS_2D_ADV) ? 5 : 1;
+}
+
+template <typename R, int K, bool CHAR, int SHAPE>
+__device__ __forceinline__ void queue_stage_body(const QueueArgs& q) {
     static_assert(THREADS_1D == TX_2D * TY_2D, "1D and 2D items share the CTA shape");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
@@ -1496,6 +1517,17 @@ __global__ void __launch_bounds__(THREADS_1D) queue_stage_kernel(QueueArgs q) {
             q.head[1] = 0u;
         }
     }
+}
+
+
+// the kernels: one without a register bound, one bounded at 5 CTAs per SM (see queue_min_blocks)
+template <typename R, int K, bool CHAR, int SHAPE>
+__global__ void __launch_bounds__(THREADS_1D) queue_stage_kernel(QueueArgs q) {
+    queue_stage_body<R, K, CHAR, SHAPE>(q);
+}
+template <typename R, int K, bool CHAR, int SHAPE>
+__global__ void __launch_bounds__(THREADS_1D, 5) queue_stage_kernel_b5(QueueArgs q) {
+    queue_stage_body<R, K, CHAR, SHAPE>(q);
 }
 
 // alpha^0 of every instance of a queue batch: one CTA per item, the wave speeds of its cells
