@@ -1661,7 +1661,11 @@ npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32
         if (inst[i].ny == 0) kind_cells[inst[i].flux_kind] += cells_of(inst[i]);
     int main_kind = 0;
     for (int k = 1; k < 3; ++k) main_kind = kind_cells[k] > kind_cells[main_kind] ? k : main_kind;
-    const int tile = resolve_tile(params, main_kind, flux_m(main_kind));
+    int tile = resolve_tile(params, main_kind, flux_m(main_kind));
+    // automatic tile of the compensated float items: at most the size whose shared memory (four
+    // arrays of tile + 6 cells per field) still lets the register-bound 5 CTAs share an SM
+    if (params->tile_1d <= 0 && compensated(params))
+        while (tile > npw::TILE_1D_MIN && (size_t)(tile + 6) * 16 * flux_m(main_kind) > (size_t)44 * 1024) tile /= 2;
     // descriptors; mixed-precision 1D instances that fit in shared memory run resident
     std::vector<npw::InstDev> h1(count);
     std::vector<npw::Inst2D> h2(count);
