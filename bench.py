@@ -167,7 +167,8 @@ def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1602_00182_gb300", "csrc")
-    for f in ("npw_internal.h", "npw_device.cuh", "npw_fast.cuh", "npw_kernels.cuh", "npw_fp32.cu"):
+    for f in ("npw_internal.h", "npw_device.cuh", "npw_fast.cuh", "npw_kernels.cuh", "npw_fp32.cu", "npw_queue.inc",
+              "npw_queue_fp32.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -460,8 +461,8 @@ def block_euler1d(args, characteristic: int):
     cu_queue = sum(n * s["steps"] for n, s in zip(ns, stats) if characteristic or n > res_limit)
     stage_s = prof.pr.stage_ms / 1e3
     eta_tot = {k: sum(s["eta"][k] for s in stats) for k in ("switch", "eval", "guard", "bound")}
-    kern = ("queue_stage_kernel<float, K=3, characteristic> (face-based Roe-field body)" if characteristic
-            else "queue_stage_kernel<float, K=3> (compensated per-stage body)")
+    kern = ("queue_stage_kernel<float, K=3, characteristic, 1D Euler> (face-based Roe-field body)" if characteristic
+            else "queue_stage_kernel_b5<float, K=3, 1D Euler> (compensated per-stage body)")
     return {
         "metric": "cell-updates/s", "value": cu / (ms / 1e3), "unit": "cell-updates/s", "dtype": "f32",
         "ms_per_solve": ms,
@@ -475,6 +476,8 @@ def block_euler1d(args, characteristic: int):
                            + ("" if characteristic else "; instances with n <= 5682 in the resident kernel beside it"),
                    "l2": "flushed before the timed solve"},
         "roofline": roofline_hbm(BYTES_EULER1D_F32, cu_queue, stage_s, kern,
+                                 traffic=None if characteristic else _ncu_traffic("queue_stage_euler1d_dram_bytes_per_launch"),
+                                 traffic_unit="bytes per stage launch over the batch's queued items",
                                  stage_launches=int(prof.pr.stage_launches), stage_ms=prof.pr.stage_ms),
         "eta_decisions": eta_tot,
         "gpu_launches": int(prof.pr.kernel_launches),
@@ -537,7 +540,10 @@ def block_euler2d(args):
                    "l2": "flushed before every timed solve"},
         "sizes": sizes,
         "roofline": roofline_hbm(BYTES_EULER2D_F32, tot_cu, tot_stage_s,
-                                 "queue_stage_kernel<float, K=3> (phased 2D body, 32 x 8 tiles)"),
+                                 "queue_stage_kernel_b5<float, K=3, 2D Euler> (phased 2D body, 32 x 8 tiles)",
+                                 traffic=_ncu_traffic("queue_stage_euler2d_512_dram_bytes_per_launch"),
+                                 traffic_unit="bytes per stage launch, 64 squares of 512^2 (2^24 cells, every size's "
+                                              "launch)"),
         "gpu_launches": tot_launch,
     }
 
