@@ -765,7 +765,7 @@ npw_status comp_end(const Run1D& r) {
     NPW_CUDA(npw::launch_comp_end(reinterpret_cast<float*>(r.arena), reinterpret_cast<const float*>(r.ws + r.L.sbuf),
                                   reinterpret_cast<const npw::InstDev*>(r.ws + r.L.inst),
                                   reinterpret_cast<const npw::Tile*>(r.ws + r.L.tiles), (int)r.ntiles, r.tile, r.m,
-                                  r.s));
+                                  nullptr, r.s));
     count_launch();
     return NPW_OK;
 }
@@ -1507,6 +1507,10 @@ struct QueueRun {
     bool fp32 = false;
     bool characteristic = false;
     int shape = npw::QS_ANY;  // the one shape every queued instance has, else QS_ANY
+    // compensated float 1D items only: one launch per RK3 step (step1d_fused_body), the two
+    // state buffers u and s alternating with the step parity
+    bool fused = false;
+    int parity = 0;
     size_t smem = 0;
     int count = 0;
     // 1D items of each flux kind are contiguous: [begin, end) per kind, for the compensated copies
@@ -1515,8 +1519,18 @@ struct QueueRun {
     std::vector<cudaEvent_t> joins;
 };
 
-npw_status queue_step(const QueueRun& r) {
+npw_status queue_step(QueueRun& r) {
     npw::QueueArgs q = r.q;
+    if (r.fused) {
+        q.stage = npw::QUEUE_FUSED_STEP;
+        q.parity = r.parity;
+        auto ev = stage_begin(r.s);
+        const cudaError_t e = npw::launch_queue_stage<float>(q, false, r.shape, r.smem, 0, r.s);
+        stage_end(ev, r.s);
+        if (e != cudaSuccess) return cuda_fail(e, "queue step launch");
+        r.parity ^= 1;
+        return NPW_OK;
+    }
     for (int st = 0; st < 3; ++st) {
         q.stage = st;
         auto ev = stage_begin(r.s);
@@ -1552,6 +1566,9 @@ npw_status queue_capture(const QueueRun& r, StepGraph& g) {
     rc.q = r.q;
     rc.fp32 = r.fp32;
     rc.characteristic = r.characteristic;
+    rc.shape = r.shape;
+    rc.fused = r.fused;
+    rc.parity = 0;  // replays start at parity 0 (GRAPH_STEPS is even)
     rc.smem = r.smem;
     cudaGraph_t graph = nullptr;
     npw_status st = NPW_OK;
@@ -1582,9 +1599,13 @@ npw_status queue_run_to_end(QueueRun& r, npw_solve_stats* out) {
     while (st == NPW_OK && act > 0) {
         long long chunk = rem < 1 ? 1 : (rem > 256 ? 256 : rem);
         if (chunk > GRAPH_STEPS && direct_done) {
+            if (r.parity) {  // the graph's steps start at parity 0
+                if ((st = queue_step(r))) break;
+                --chunk;
+            }
             if (!graph.exec && (st = queue_capture(r, graph))) break;
             for (long long k = 0; k < chunk / GRAPH_STEPS && st == NPW_OK; ++k) {
-                auto ev = stage_begin(r.s, -1, 3 * GRAPH_STEPS);
+                auto ev = stage_begin(r.s, -1, (r.fused ? 1 : 3) * GRAPH_STEPS);
                 const cudaError_t e = cudaGraphLaunch(graph.exec, r.s);
                 stage_end(ev, r.s);
                 if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphLaunch");
@@ -1596,12 +1617,15 @@ npw_status queue_run_to_end(QueueRun& r, npw_solve_stats* out) {
         if (st == NPW_OK) st = queue_poll(r, &act, &rem);
     }
     if (st == NPW_ETIMEOUT) graph.abandon();
-    if (st == NPW_OK && r.comp) {  // compensated 1D items: the final states are in s
+    if (st == NPW_OK && r.comp) {
+        // compensated 1D items: the final states are in s (per-stage steps), or, with fused steps,
+        // in s for the instances that took an odd number of steps
         for (int kind = 0; kind < 3 && st == NPW_OK; ++kind) {
             const int64_t b = r.kind_begin[kind], e = r.kind_end[kind];
             if (e <= b) continue;
             const cudaError_t ce = npw::launch_comp_end(reinterpret_cast<float*>(r.q.u), r.q.s, r.q.inst1, r.q.items + b,
-                                                        (int)(e - b), r.q.tile, flux_m(kind), r.s);
+                                                        (int)(e - b), r.q.tile, flux_m(kind), r.fused ? r.q.ctl : nullptr,
+                                                        r.s);
             if (ce != cudaSuccess) st = cuda_fail(ce, "compensated end copy");
             count_launch();
         }
@@ -1662,10 +1686,19 @@ npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32
     int main_kind = 0;
     for (int k = 1; k < 3; ++k) main_kind = kind_cells[k] > kind_cells[main_kind] ? k : main_kind;
     int tile = resolve_tile(params, main_kind, flux_m(main_kind));
-    // automatic tile of the compensated float items: at most the size whose shared memory (four
-    // arrays of tile + 6 cells per field) still lets the register-bound 5 CTAs share an SM
-    if (params->tile_1d <= 0 && compensated(params))
-        while (tile > npw::TILE_1D_MIN && (size_t)(tile + 6) * 16 * flux_m(main_kind) > (size_t)44 * 1024) tile /= 2;
+    // a batch of compensated float 1D items alone takes one launch per RK3 step
+    bool any2d = false;
+    for (int i = 0; i < count; ++i) any2d |= inst[i].ny != 0;
+    r.fused = r.comp && !any2d;
+    // automatic tile of the compensated float items: at most the size whose shared memory still
+    // lets the register-bound 5 CTAs share an SM
+    if (params->tile_1d <= 0 && r.comp) {
+        const int m = flux_m(main_kind);
+        auto smem_of = [&](int t) {
+            return r.fused ? npw::fused1d_smem_floats(t, m) * sizeof(float) : (size_t)(t + 6) * 16 * m;
+        };
+        while (tile > npw::TILE_1D_MIN && smem_of(tile) > (size_t)44 * 1024) tile /= 2;
+    }
     // descriptors; mixed-precision 1D instances that fit in shared memory run resident
     std::vector<npw::InstDev> h1(count);
     std::vector<npw::Inst2D> h2(count);
@@ -1753,6 +1786,7 @@ npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32
     q.mp = method(params);
     r.smem = r.fp32 ? npw::queue_smem_bytes<float>(tile, has1d, m1d, has2d, m2d, r.characteristic)
                     : npw::queue_smem_bytes<double>(tile, has1d, m1d, has2d, m2d, r.characteristic);
+    if (r.fused) r.smem = npw::fused1d_smem_floats(tile, m1d) * sizeof(float);
     // start: reset, alpha^0 over the items, first dt
     NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, nullptr, count, 0, 0, r.s));
     cudaError_t e = r.fp32 ? npw::launch_queue_alpha<float>(q, r.s) : npw::launch_queue_alpha<double>(q, r.s);

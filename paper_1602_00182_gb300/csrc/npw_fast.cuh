@@ -364,12 +364,16 @@ __device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, f
     two_sum(dh, dl, s, dl);
     dh = s;
     if (dh == 0.0f) return nh / dh;  // same 0/0 or inf behaviour as the plain quotient
-    // double-float quotient (nh + nl) / (dh + dl)
-    const float q1 = nh / dh;
+    // double-float quotient (nh + nl) / (dh + dl): q1 needs only a few ulps (the exact residual r
+    // corrects it), so where |dh| lies in [2^-125, 2^125] the fast reciprocal division (within 2
+    // ulp) serves for q1 and for the small correction q2; elsewhere the correctly rounded one
+    const float adh = fabsf(dh);
+    const bool fast_div = adh >= 0x1p-125f && adh <= 0x1p125f;
+    const float q1 = fast_div ? __fdividef(nh, dh) : nh / dh;
     const float p = q1 * dh;
     const float pe = fmaf(q1, dh, -p);
     const float r = ((nh - p) - pe) + fmaf(-q1, dl, nl);
-    const float q2 = r / dh;
+    const float q2 = fast_div ? __fdividef(r, dh) : r / dh;
     return q1 + q2;
 }
 

@@ -48,13 +48,13 @@ namespace npw {
 cudaError_t launch_comp_begin(const float* u, float* s, float* c, const InstDev* inst, const Tile* tiles, int ntiles,
                               int tile, int m, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
-    comp_copy_kernel<<<ntiles, THREADS_1D, 0, st>>>(s, u, c, inst, tiles, tile, m);
+    comp_copy_kernel<<<ntiles, THREADS_1D, 0, st>>>(s, u, c, inst, tiles, tile, m, nullptr);
     return cudaGetLastError();
 }
 cudaError_t launch_comp_end(float* u, const float* s, const InstDev* inst, const Tile* tiles, int ntiles, int tile,
-                            int m, cudaStream_t st) {
+                            int m, const Ctl* odd, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
-    comp_copy_kernel<<<ntiles, THREADS_1D, 0, st>>>(u, s, nullptr, inst, tiles, tile, m);
+    comp_copy_kernel<<<ntiles, THREADS_1D, 0, st>>>(u, s, nullptr, inst, tiles, tile, m, odd);
     return cudaGetLastError();
 }
 }  // namespace npw

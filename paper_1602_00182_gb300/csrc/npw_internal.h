@@ -220,9 +220,17 @@ struct QueueArgs {
     int32_t stage;
     int32_t advance;
     int32_t tile;            // cells per 1D item
+    int32_t parity;          // QUEUE_FUSED_STEP: 0 = u^n in u, u^{n+1} to s; 1 = the other way round
     unsigned int* head;      // [2]: next item, CTAs finished
     MethodParams mp;
 };
+// QueueArgs.stage of a whole RK3 step of compensated float 1D items in one launch
+// (step1d_fused_body); stages 0..2 are the per-stage launches
+constexpr int QUEUE_FUSED_STEP = 3;
+// halo of a fused step (three stages, each reaching 3 cells) and its shared memory in floats:
+// u^n, the stage input, d, eta, v^-, v^+ over tile + 18 cells per field
+constexpr int FUSE_HALO = 9;
+__host__ __device__ constexpr size_t fused1d_smem_floats(int tile, int m) { return (size_t)6 * (tile + 2 * FUSE_HALO) * m; }
 
 // Instance shape of a queue batch whose instances all have one dimension and flux kind: the
 // queue kernel instantiated for it carries only that body (and that body's register count);
@@ -271,11 +279,12 @@ cudaError_t launch_queue_ctl(Ctl* ctl, const InstDev* inst1, const Inst2D* inst2
                              const int32_t* list, int count, int mode, int64_t max_steps, cudaStream_t s);
 cudaError_t launch_queue_poll(const Ctl* ctl, const InstDev* inst1, const Inst2D* inst2, const uint8_t* is2d,
                               int count, long long* poll, cudaStream_t s);
-// compensated float path: before the first step s = u and c = 0; after the last, u = s
+// compensated float path: before the first step s = u and c = 0; after the last, u = s (odd:
+// only for the instances whose control word counts an odd number of steps, NULL = all)
 cudaError_t launch_comp_begin(const float* u, float* s, float* c, const InstDev* inst, const Tile* tiles, int ntiles,
                               int tile, int m, cudaStream_t st);
 cudaError_t launch_comp_end(float* u, const float* s, const InstDev* inst, const Tile* tiles, int ntiles, int tile,
-                            int m, cudaStream_t st);
+                            int m, const Ctl* odd, cudaStream_t st);
 // fills [m][n] with smooth data for the tile autotuner (m = 3: a quiet Euler state)
 template <typename R>
 cudaError_t launch_tune_init(R* u, int64_t n, int m, cudaStream_t st);

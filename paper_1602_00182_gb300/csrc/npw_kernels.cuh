@@ -618,10 +618,187 @@ __device__ __forceinline__ void stage1d_fast_body(const Stage1DArgs& a, const Ti
     }
 }
 
-// s = u and c = 0 over the tiles (before the first step); u = s (after the last)
+// ---------------------------------------------------------------------------------------
+// One whole RK3 step of one 1D tile (mixed precision, compensated, component-wise), for
+// instances too large for the resident kernel.  The tile loads u^n once with a 9-cell halo
+// (three stages, each reaching 3 cells), and computes in shared memory
+//   stage 1 on the cells within 6 of the tile: d1 = du(u^n),        x1 = u^n + d1;
+//   stage 2 on the cells within 3:              d2 = (d1 + du(x1))/4, x2 = u^n + d2;
+//   stage 3 on the tile:  u^{n+1} = u^n + 2/3 (d2 + du(x2)), compensated by the carry c,
+// with the arithmetic of the per-stage body cell for cell, so that the results are the same
+// bits.  Cells of the halo outside the domain are ghosts: their stage values follow the
+// boundary rule from the tile's own stage values (a periodic ghost is the same computation as
+// the cell it wraps to).  u^n is read from `uin` and u^{n+1} written to `uout`: the two state
+// buffers alternate between steps (neighbouring tiles read the halo of u^n in the same launch).
+// Shared memory (floats, span = tile + 18 cells per field): u^n, the stage input, d, eta, v^-,
+// v^+.
+// ---------------------------------------------------------------------------------------
+// the stage values of the ghost cells of [lo, hi) (extended indices; cell e is global cell
+// c0 - FUSE_HALO + e) from the boundary rule: transmissive and the right end of an inflow
+// line repeat the end cell, the left end of an inflow line holds the inflow state
+template <int M>
+__device__ __forceinline__ void fused_fill_ghosts(float* x, int lo, int hi, int c0, int64_t n, int bc,
+                                                  const MethodParams& mp) {
+    const int e0 = FUSE_HALO - c0;                   // extended index of cell 0
+    const int64_t e1 = (int64_t)e0 + n - 1;          // of cell n - 1
+    for (int e = lo + (int)threadIdx.x; e < hi; e += blockDim.x) {
+        if (e >= e0 && e <= e1) continue;
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            x[e * M + k] = e < e0 ? (bc == NPW_BC_INFLOW ? mp.inflow_f[k] : x[e0 * M + k]) : x[(int)e1 * M + k];
+    }
+}
+
+template <int KIND, int K>
+__device__ __forceinline__ void step1d_fused_body(const Stage1DArgs& a, const Tile td, const InstDev& in, Ctl* ctl,
+                                                  unsigned char* smem_raw) {
+    constexpr int M = kind_m<KIND>();
+    constexpr int H = FUSE_HALO;
+    __shared__ float red[32];
+    __shared__ int redbad[32];
+    __shared__ float s_lam;
+    const int span_max = a.tile + 2 * H;
+    float* su0 = reinterpret_cast<float*>(smem_raw);  // u^n
+    float* sx = su0 + span_max * M;                    // input of the current stage
+    float* sd = sx + span_max * M;                     // d1, then d2
+    float* se = sd + span_max * M;                     // eta of face e (between e-1 and e)
+    float* svm = se + span_max * M;                    // v^- at the right face of cell e
+    float* svp = svm + span_max * M;                   // v^+ at the left face of cell e
+    if (*(volatile int32_t*)&ctl->done) return;       // uniform over the CTA
+    const int64_t n = in.n;
+    const int c0 = td.start;
+    const int cnt = (int)((n - c0) < a.tile ? (n - c0) : a.tile);
+    const int span = cnt + 2 * H;
+    const float* uin = reinterpret_cast<const float*>(a.uin) + in.off;
+    float* uout = reinterpret_cast<float*>(a.uout) + in.off;
+    float* cr = a.c + in.off;
+    const bool periodic = in.bc == NPW_BC_PERIODIC;
+    // halo load of u^n (a periodic index may wrap more than once on a short line)
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const float inflow_k = a.mp.inflow_f[k];
+        for (int j = threadIdx.x; j < span; j += blockDim.x) {
+            int64_t g = (int64_t)c0 - H + j;
+            float x;
+            if (periodic) {
+                g %= n;
+                if (g < 0) g += n;
+                x = uin[k * n + g];
+            } else if (g < 0 && in.bc == NPW_BC_INFLOW) {
+                x = inflow_k;
+            } else {
+                g = g < 0 ? 0 : (g >= n ? n - 1 : g);
+                x = uin[k * n + g];
+            }
+            su0[j * M + k] = x;
+            sx[j * M + k] = x;
+        }
+    }
+    if (threadIdx.x == 0) s_lam = (float)(*(volatile double*)&ctl->dt / in.dx);
+    const float alpha = (float)*(volatile double*)&ctl->alpha;
+    const fast::FParams fp = fast::fparams(a.mp);
+    const bool last_tile = c0 + cnt == n;
+    const int e0 = H - c0;  // extended index of global cell 0
+    EtaCount ec;
+    float vmaxf = 0.0f;
+    bool bad = false;
+    __syncthreads();
+    const float lam = s_lam;
+#pragma unroll 1
+    for (int st = 0; st < 3; ++st) {
+        const int L = 3 * (st + 1), R = span - 3 * (st + 1);  // cells updated by this stage: [L, R)
+        // F: eta of the faces q in [L - 1, R + 2) (face q between cells q - 1 and q)
+        if constexpr (K == 3) {
+            for (int idx = threadIdx.x; idx < (R - L + 3) * M; idx += blockDim.x) {
+                const int q = L - 1 + idx / M, k = idx - (q - L + 1) * M;
+                uint32_t fl = 0;
+                se[q * M + k] = fast::face_eta(sx[(q - 2) * M + k], sx[(q - 1) * M + k], sx[q * M + k],
+                                               sx[(q + 1) * M + k], fp, &fl);
+                if (face_owned(q - H, cnt, last_tile)) ec.face_k3(fl);
+            }
+            __syncthreads();
+        }
+        // C: cells e in [L - 1, R + 1): v^- at face e + 1, v^+ at face e
+        for (int idx = threadIdx.x; idx < (R - L + 2) * M; idx += blockDim.x) {
+            const int e = L - 1 + idx / M, k = idx - (e - L + 1) * M;
+            float c[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) c[j] = sx[(e - 2 + j) * M + k];
+            float vm, vp;
+            if constexpr (K == 3) {
+                fast::cell_recon(c, se[(e + 1) * M + k], se[e * M + k], fp, &vm, &vp);
+            } else {
+                const uint32_t d = fast::cell_recon_k2(c + 1, 0.0, a.mp, fp, &vm, &vp);
+                if (face_owned(e + 1 - H, cnt, last_tile)) fast::count_k2(ec, d, 0);
+                if (face_owned(e - H, cnt, last_tile)) fast::count_k2(ec, d, 1);
+            }
+            svm[e * M + k] = vm;
+            svp[e * M + k] = vp;
+        }
+        __syncthreads();
+        // U: fluxes of both faces, eq. PDE1, the stage in increment form
+        for (int e = L + (int)threadIdx.x; e < R; e += blockDim.x) {
+            const int64_t g = (int64_t)c0 - H + e;
+            if (!periodic && (g < 0 || g >= n)) continue;  // a ghost: filled below
+            float hl[M], hr[M];
+            lf_flux<float, KIND, M>(svm + (e - 1) * M, svp + e * M, alpha, a.mp, 0, hl);
+            lf_flux<float, KIND, M>(svm + e * M, svp + (e + 1) * M, alpha, a.mp, 0, hr);
+            if (st < 2) {
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const float du = lam * (hl[k] - hr[k]);
+                    const float d = st == 0 ? du : 0.25f * (sd[e * M + k] + du);
+                    sd[e * M + k] = d;
+                    sx[e * M + k] = su0[e * M + k] + d;
+                }
+            } else {
+                float U[M];
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const float du = lam * (hl[k] - hr[k]);
+                    const int64_t ix = k * n + g;
+                    const float base = su0[e * M + k];
+                    const float y = kTwoThirdsF * (sd[e * M + k] + du) + cr[ix];
+                    const float t = base + y;
+                    cr[ix] = y - (t - base);
+                    uout[ix] = t;
+                    U[k] = t;
+                    bad |= !finite_(t);
+                }
+                const float sp = wave_speed<float, KIND>(U, a.mp, 0);
+                bad |= !finite_(sp);
+                vmaxf = sp > vmaxf ? sp : vmaxf;
+            }
+        }
+        if (st < 2) {
+            __syncthreads();
+            if (!periodic && (e0 > L || e0 + n < (int64_t)R)) {
+                fused_fill_ghosts<M>(sx, L, R, c0, n, in.bc, a.mp);
+                __syncthreads();
+            }
+        }
+    }
+    flush_counts(ec, ctl, a.mp);
+    if (a.advance) {
+        const double b = block_max_nan_f(vmaxf, bad, red, redbad);
+        if (threadIdx.x == 0) {
+            atomicMax(&ctl->alpha_next_bits, (unsigned long long)__double_as_longlong(b));
+            __threadfence();
+            const unsigned prev = atomicAdd(&ctl->tiles_done, 1u);
+            if (prev == (unsigned)in.ntiles - 1u) {
+                __threadfence();
+                finalize_1d(ctl, in);
+            }
+        }
+    }
+}
+
+// s = u and c = 0 over the tiles (before the first step); u = s (after the last; odd: only
+// for the instances that took an odd number of fused steps, whose last step wrote s)
 static __global__ void comp_copy_kernel(float* dst, const float* src, float* zero, const InstDev* __restrict__ inst,
-                                 const Tile* __restrict__ tiles, int tile, int m) {
+                                        const Tile* __restrict__ tiles, int tile, int m, const Ctl* odd) {
     const Tile td = tiles[blockIdx.x];
+    if (odd && (odd[td.inst].steps & 1) == 0) return;
     const InstDev in = inst[td.inst];
     const int64_t n = in.n;
     const int c0 = td.start;
@@ -971,24 +1148,24 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
     const float ax = s_par[0], ay = s_par[1];
     // counted faces: x face (qx, qy) of grid row ty0 + qy, y face of grid column tx0 + qx
     EtaCount ec;
-    auto own_x = [&](int qx, int qy) {
-        return ty0 + qy < ny && face_owned(qx, (int)min((int64_t)TX_2D, nx - tx0), tx0 + TX_2D >= nx);
-    };
-    auto own_y = [&](int qx, int qy) {
-        return tx0 + qx < nx && face_owned(qy, (int)min((int64_t)TY_2D, ny - ty0), ty0 + TY_2D >= ny);
-    };
+    const int cols_in = (int)min((int64_t)TX_2D, nx - tx0), rows_in = (int)min((int64_t)TY_2D, ny - ty0);
+    const bool last_x = tx0 + TX_2D >= nx, last_y = ty0 + TY_2D >= ny;
+    auto own_x = [=](int qx, int qy) { return qy < rows_in && face_owned(qx, cols_in, last_x); };
+    auto own_y = [=](int qx, int qy) { return qx < cols_in && face_owned(qy, rows_in, last_y); };
 #define NPW_SU(bx, by, k) su[((k) * BY + (by)) * BX + (bx)]
     // E: item = (face, field); x face (qx, qy) has the eta stencil su[qy+3][qx+1 .. qx+4],
     // y face (qx, qy) su[qy+1 .. qy+4][qx+3]
     for (int it = tid; K == 3 && it < NF * M; it += nthr) {
         const int k = it / NF, f = it - k * NF;
         float w0, w1, w2, w3;
+        bool own;
         if (f < NFX) {
             const int qy = f / (TX_2D + 1), qx = f - qy * (TX_2D + 1);
             w0 = NPW_SU(qx + 1, qy + 3, k);
             w1 = NPW_SU(qx + 2, qy + 3, k);
             w2 = NPW_SU(qx + 3, qy + 3, k);
             w3 = NPW_SU(qx + 4, qy + 3, k);
+            own = own_x(qx, qy);
         } else {
             const int g = f - NFX;
             const int qy = g / TX_2D, qx = g - qy * TX_2D;
@@ -996,10 +1173,10 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
             w1 = NPW_SU(qx + 3, qy + 2, k);
             w2 = NPW_SU(qx + 3, qy + 3, k);
             w3 = NPW_SU(qx + 3, qy + 4, k);
+            own = own_y(qx, qy);
         }
         uint32_t fl = 0;
         ef[k * NF + f] = fast::face_eta(w0, w1, w2, w3, fp, &fl);
-        const bool own = f < NFX ? own_x(f % (TX_2D + 1), f / (TX_2D + 1)) : own_y((f - NFX) % TX_2D, (f - NFX) / TX_2D);
         if (own) ec.face_k3(fl);
     }
     __syncthreads();
@@ -1421,9 +1598,12 @@ __global__ void __launch_bounds__(TX_2D * TY_2D) stage2d_kernel(Stage2DArgs a) {
 template <typename R, int K, bool CHAR, int KIND>
 __device__ __forceinline__ void queue_item_1d(const Stage1DArgs& a1, const Tile w, const InstDev& in, Ctl* ctl,
                                               unsigned char* smem) {
-    if constexpr (sizeof(R) == sizeof(float) && !CHAR)
-        stage1d_fast_body<KIND, K>(a1, w, in, ctl, smem);
-    else
+    if constexpr (sizeof(R) == sizeof(float) && !CHAR) {
+        if (a1.stage == QUEUE_FUSED_STEP)
+            step1d_fused_body<KIND, K>(a1, w, in, ctl, smem);
+        else
+            stage1d_fast_body<KIND, K>(a1, w, in, ctl, smem);
+    } else
         stage1d_body<R, double, KIND, CHAR && KIND == NPW_FLUX_EULER1D_>(a1, w, in, ctl, smem);
 }
 template <typename R, int K, int KIND>
@@ -1447,9 +1627,11 @@ __device__ __forceinline__ void queue_stage_body(const QueueArgs& q) {
     static_assert(THREADS_1D == TX_2D * TY_2D, "1D and 2D items share the CTA shape");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
-    // stage input and output: u -> u1 -> u2 -> u (selects, not an indexed local array)
-    const void* sin = q.stage == 0 ? q.u : (q.stage == 1 ? q.u1 : q.u2);
-    void* sout = q.stage == 0 ? q.u1 : (q.stage == 1 ? q.u2 : q.u);
+    // stage input and output: u -> u1 -> u2 -> u (selects, not an indexed local array); the
+    // fused 1D step reads the state buffer of this step's parity and writes the other
+    const bool fused = q.stage == QUEUE_FUSED_STEP;
+    const void* sin = fused ? (q.parity ? (const void*)q.s : q.u) : (q.stage == 0 ? q.u : (q.stage == 1 ? q.u1 : q.u2));
+    void* sout = fused ? (q.parity ? q.u : (void*)q.s) : (q.stage == 0 ? q.u1 : (q.stage == 1 ? q.u2 : q.u));
     Stage1DArgs a1{};
     a1.uin = sin;
     a1.un = q.u;

@@ -154,3 +154,55 @@ def test_queue_step_limit(npw):
         assert s["steps"] <= 3 and s["status"] in (0, npw.NPW_ETIMEOUT)
     assert sum(s["status"] == npw.NPW_ETIMEOUT for s in stats) >= len(stats) // 2
     assert torch.isfinite(arena).all()
+
+
+@pytest.mark.parametrize("kind", ["burgers", "euler", "advection"])
+@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("batch_mode", [0, 1])
+def test_queue_fused_step_equals_per_stage(npw, kind, bc, batch_mode):
+    """A batch of 1D float instances alone takes one fused launch per RK3 step (u^n loaded once
+    with a 9-cell halo, three stages in shared memory, the two state buffers alternating): every
+    instance equals the per-stage kernels of npweno_batch_solve (batch_mode 1) bit for bit, with
+    the same steps and decision counts.  Sizes from 6 cells (a periodic halo wrapping more than
+    once) through several tiles with a ragged end; end times giving odd and even step counts;
+    batch_mode 0 also runs the small instances in the resident kernel beside the queue."""
+    g = np.random.default_rng(7 + bc)
+    ns = [6, 7, 40, 513, 1500, 5000, 9001]
+    if kind == "euler":
+        kk, m = npw.NPW_FLUX_EULER1D, 3
+        fields = []
+        for n in ns:
+            x = (np.arange(n) + 0.5) / n
+            rho = 1.0 + 0.2 * np.sin(2 * np.pi * 3 * x + g.uniform(0, 6)) + 0.5 * (x > 0.6)
+            u = 0.3 * np.cos(2 * np.pi * x)
+            p = 1.0 + 0.5 * (x < 0.3)
+            fields.append(np.concatenate([rho, rho * u, p / 0.4 + 0.5 * rho * u * u]))
+    else:
+        kk, m = (npw.NPW_FLUX_BURGERS, 1) if kind == "burgers" else (npw.NPW_FLUX_ADVECTION, 1)
+        fields = []
+        for n in ns:
+            x = (np.arange(n) + 0.5) / n
+            fields.append(1.0 + 0.5 * np.sin(2 * np.pi * x + g.uniform(0, 6)) + 0.4 * (x > 0.55))
+    dxs = [1.0 / n for n in ns]
+    t_ends = [0.013 + 0.004 * j for j in range(len(ns))]
+    specs = [dict(kind=kk, nx=n, dx=d, t_end=t, cfl=0.5, bc=bc) for n, d, t in zip(ns, dxs, t_ends)]
+    table, total, offs = npw.make_queue_instances(specs)
+    p = npw.Params(precision=npw.NPW_FP32_MIXED, rbf=npw.NPW_RBF_GA, batch_mode=batch_mode,
+                   inflow=(1.3, 0.2, 2.6, 0.0) if kind == "euler" else (1.3, 0, 0, 0))
+    arena = torch.tensor(np.concatenate(fields), dtype=torch.float32, device="cuda")
+    st, stats = npw.npweno_queue_solve(arena, table, p)
+    assert st == 0
+    a = arena.cpu().numpy()
+    pb = npw.Params(precision=npw.NPW_FP32_MIXED, rbf=npw.NPW_RBF_GA, batch_mode=1, inflow=p.inflow)
+    parity = set()
+    for sp, u0, off, s in zip(specs, fields, offs, stats):
+        tb, _ = npw.make_instances([sp["nx"]], [sp["dx"]], [sp["t_end"]], [sp["cfl"]], [sp["bc"]], m=m)
+        u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        stb, rs = npw.npweno_batch_solve(u, tb, m, kk, pb)
+        assert stb == 0
+        rs = rs[0]
+        assert s["status"] == 0 and s["steps"] == rs["steps"] and s["t"] == rs["t"], (sp["nx"], s, rs)
+        assert np.array_equal(a[off:off + u0.size], u.cpu().numpy()), (sp["nx"], s["steps"])
+        assert s["eta"] == rs["eta"], sp["nx"]
+        parity.add(s["steps"] % 2)
+    assert parity == {0, 1}
