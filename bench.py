@@ -443,6 +443,13 @@ def block_euler1d(args, characteristic: int):
     eta_max = 1.0 if characteristic else 0.0
     p = npw.Params(precision=npw.NPW_FP32_MIXED, characteristic=characteristic, eta_max=eta_max)
     tile = npw.npw_autotune_1d(npw.NPW_FLUX_EULER1D, 3, p)  # later runs with tile_1d = 0 use it
+    if args.euler_tile > 0:
+        p.tile_1d = tile = args.euler_tile
+    elif not characteristic:
+        # the library's rule for fused steps: the tuned tile, halved while six arrays of
+        # tile + 18 cells x 3 fields exceed 76 KB
+        while tile > 256 and 6 * (tile + 18) * 3 * 4 > 76 * 1024:
+            tile //= 2
     ws = torch.empty(npw.npw_queue_workspace_size(table, p), dtype=torch.uint8, device="cuda")
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -462,7 +469,7 @@ def block_euler1d(args, characteristic: int):
     stage_s = prof.pr.stage_ms / 1e3
     eta_tot = {k: sum(s["eta"][k] for s in stats) for k in ("switch", "eval", "guard", "bound")}
     kern = ("queue_stage_kernel<float, K=3, characteristic, 1D Euler> (face-based Roe-field body)" if characteristic
-            else "queue_stage_kernel_b5<float, K=3, 1D Euler> (compensated per-stage body)")
+            else "queue_stage_kernel_b5<float, K=3, 1D Euler> (fused RK3 step body)")
     return {
         "metric": "cell-updates/s", "value": cu / (ms / 1e3), "unit": "cell-updates/s", "dtype": "f32",
         "ms_per_solve": ms,
@@ -472,8 +479,11 @@ def block_euler1d(args, characteristic: int):
                                 f"{', |eta| <= 1' if characteristic else ''}, LF, TVD-RK3 CFL 0.5 to "
                                 f"{t_frac} x each end time"),
                    "instances": 512, "cells": int(sum(ns)), "cell_updates": int(cu), "tile_1d": tile,
-                   "path": "npweno_queue_solve: persistent work-queue stage kernel, steps replayed as CUDA graphs"
-                           + ("" if characteristic else "; instances with n <= 5682 in the resident kernel beside it"),
+                   "path": ("npweno_queue_solve: persistent work-queue stage kernel, steps replayed as CUDA graphs"
+                            if characteristic else
+                            "npweno_queue_solve: persistent work-queue kernel, one fused launch per RK3 step (u^n "
+                            "loaded once with a 9-cell halo, three stages in shared memory), steps replayed as CUDA "
+                            "graphs; instances with n <= 5682 in the resident kernel beside it"),
                    "l2": "flushed before the timed solve"},
         "roofline": roofline_hbm(BYTES_EULER1D_F32, cu_queue, stage_s, kern,
                                  traffic=None if characteristic else _ncu_traffic("queue_stage_euler1d_dram_bytes_per_launch"),
@@ -809,6 +819,10 @@ def serving_block(npw, count: int, rates):
 # ------------------------------------------------------------------------------- serving sweep
 FP64_TOL_CLASS = 1e-10   # a request asking for this tolerance takes the server's FP64 lane
 FP32_TOL_CLASS = 1e-4    # the float lane's class (npweno.MIXED_TOLERANCE)
+SWEEP_FP64_SHARE = 0.1   # share of the sweep's requests in the FP64 class
+# the sweep's servers and comparator drop faces with |eta| > 100: with the printed eta a
+# four-quadrant square in FP64 goes non-finite from one face whose denominator vanishes
+SWEEP_ETA_MAX = 100.0
 
 
 def sweep_payloads(count: int, seed: int = 7):
@@ -816,7 +830,7 @@ def sweep_payloads(count: int, seed: int = 7):
     instance of the batch family (N log-uniform 64..8192, T = 1.5 U(0.1, 1)), a transmissive 1D
     Euler instance (Riemann or Shu-Osher-type data, N log-uniform 256..65536, T = its end time x
     U(0.1, 1)) or a periodic 2D Euler square (vortex or four-quadrant, 128^2..1024^2, T x
-    U(0.1, 1) of ~10-80 steps); a quarter ask for FP64 (tolerance 1e-10), the rest for the float
+    U(0.1, 1) of ~10-80 steps); a tenth ask for FP64 (tolerance 1e-10), the rest for the float
     class (1e-4)."""
     g = np.random.Generator(np.random.PCG64(I.SEED_BASE + 900 + seed))
     burg = I.burgers_batch(count=count, seed_index=910 + seed)
@@ -825,7 +839,7 @@ def sweep_payloads(count: int, seed: int = 7):
     items = []
     for k in range(count):
         fam = int(g.integers(3))
-        tol = FP64_TOL_CLASS if g.uniform() < 0.25 else FP32_TOL_CLASS
+        tol = FP64_TOL_CLASS if g.uniform() < SWEEP_FP64_SHARE else FP32_TOL_CLASS
         if fam == 0:
             it = burg[k]
             items.append(dict(family="burgers", kind=1, bc=0, m=1, n=it.n, ny=0, dx=it.dx,
@@ -850,7 +864,7 @@ def run_serving_stream(npw, reqs, heap_cells: int, max_slots: int, max_steps: in
     """The live server on a stream of requests (arrival, payload): each is submitted at its
     arrival time (held on the host while the server's queue is full), the server is stepped in
     rounds of max_steps steps, results are polled; latency = result on the host - arrival."""
-    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, batch_mode=1)
+    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, batch_mode=1, eta_max=SWEEP_ETA_MAX)
     srv = npw.Server(heap_cells=heap_cells, max_slots=max_slots, params=p)
     t0 = time.perf_counter()
     k, done, backlog = 0, {}, []
@@ -895,7 +909,7 @@ def fifo_per_step_model(npw, items, per_family: int = 12, probe_steps: int = 40)
             r = items[i]
             ts = []
             for steps in (probe_steps, 2 * probe_steps):
-                p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP64, max_steps=steps)
+                p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP64, max_steps=steps, eta_max=SWEEP_ETA_MAX)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 u = torch.tensor(r["u0"], dtype=torch.float64, device="cuda")
@@ -930,7 +944,8 @@ def serving_sweep(npw, rates, count: int = 2000, horizon_s: float = 60.0):
     model = fifo_per_step_model(npw, items)
     out = {"mode": "serving sweep (C5-type)", "requests_max": count, "horizon_s": horizon_s,
            "mix": "1/3 periodic Burgers (N 64..8192), 1/3 transmissive 1D Euler (N 256..65536), 1/3 periodic 2D "
-                  "Euler squares (128^2..1024^2); T x U(0.1, 1); 1/4 FP64 class (tol 1e-10), 3/4 float class (1e-4)",
+                  "Euler squares (128^2..1024^2); T x U(0.1, 1); 1/10 FP64 class (tol 1e-10), 9/10 float class "
+                  "(1e-4); |eta| <= 100 in both lanes and the comparator",
            "server": "npw_server: two lanes (NPW_FP32_MIXED, NPW_FP64) on one stream, work-queue stage kernels, "
                      "32-step rounds",
            "fifo_comparator": "FP64, one request at a time, per-stage kernels, no graphs; service time = fixed + "
@@ -961,7 +976,9 @@ def serving_sweep(npw, rates, count: int = 2000, horizon_s: float = 60.0):
             "server": {"p50_ms": q(lat, 50), "p99_ms": q(lat, 99), "mean_ms": float(lat.mean() * 1e3),
                        "p99_ms_fp32_lane": q(lat[prec == 1], 99), "p99_ms_fp64_lane": q(lat[prec == 0], 99),
                        "p99_ms_by_family": fam_lat, "cell_updates_per_s": float(cu.sum() / span),
-                       "all_ok": all(done[i]["status"] == 0 for i in done)},
+                       "all_ok": all(done[i]["status"] == 0 for i in done),
+                       "status_counts": {str(k): int(v) for k, v in zip(*np.unique(
+                           [done[i]["status"] for i in done], return_counts=True))}},
             "fp64_fifo": {"p50_ms": q(flat, 50), "p99_ms": q(flat, 99),
                           "cell_updates_per_s": float(cu.sum() / (fend - reqs[0]["arrival"]))},
         })
@@ -1027,6 +1044,7 @@ def main():
                     help="1D Euler characteristic block: fraction of each end time")
     ap.add_argument("--sizes2d", default="256,512,1024,2048", help="2D Euler block: square sizes")
     ap.add_argument("--steps2d", type=int, default=100, help="2D Euler block: RK3 steps per solve")
+    ap.add_argument("--euler-tile", type=int, default=0, help="1D Euler blocks: cells per tile (0: the library's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eta-eval", type=int, default=0, choices=[0, 1],
                     help="mixed path: 0 = eta from float pairs, double-float quotient (the library default); "

@@ -1690,15 +1690,12 @@ npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32
     bool any2d = false;
     for (int i = 0; i < count; ++i) any2d |= inst[i].ny != 0;
     r.fused = r.comp && !any2d;
-    // automatic tile of the compensated float items: at most the size whose shared memory still
-    // lets the register-bound 5 CTAs share an SM
-    if (params->tile_1d <= 0 && r.comp) {
-        const int m = flux_m(main_kind);
-        auto smem_of = [&](int t) {
-            return r.fused ? npw::fused1d_smem_floats(t, m) * sizeof(float) : (size_t)(t + 6) * 16 * m;
-        };
-        while (tile > npw::TILE_1D_MIN && smem_of(tile) > (size_t)44 * 1024) tile /= 2;
-    }
+    // automatic tile of fused steps: at most the size whose shared memory (six arrays of
+    // tile + 18 cells per field) still lets 3 CTAs share an SM
+    if (params->tile_1d <= 0 && r.fused)
+        while (tile > npw::TILE_1D_MIN && npw::fused1d_smem_floats(tile, flux_m(main_kind)) * sizeof(float) >
+                                              (size_t)76 * 1024)
+            tile /= 2;
     // descriptors; mixed-precision 1D instances that fit in shared memory run resident
     std::vector<npw::InstDev> h1(count);
     std::vector<npw::Inst2D> h2(count);
