@@ -317,6 +317,15 @@ def headline_burgers(args, rank, world, local_rank):
         time_variant(npw.Params(k=2, rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, eta_max=1.0),
                      "k=2 RBF-WENO3 Gaussian + switch (Table k2; resident kernels, eta in FP64), |eta| <= 1 "
                      "(the printed k = 2 eta is singular where u crosses zero)")
+        # the schemes the paper compares, side by side on the same batch (Sec. 5.2: RBF-ENO costs
+        # a little more than ENO and less than WENO)
+        for k, sch, name in ((3, npw.NPW_ENO, "ENO3"), (3, npw.NPW_WENO_JS, "WENO-JS5"), (3, npw.NPW_RBF_ENO, "RBF-ENO3"),
+                             (2, npw.NPW_ENO, "ENO2"), (2, npw.NPW_WENO_JS, "WENO-JS3"), (2, npw.NPW_RBF_ENO, "RBF-ENO2")):
+            rbf_k2 = k == 2 and sch == npw.NPW_RBF_ENO
+            time_variant(npw.Params(k=k, scheme=sch, rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED,
+                                    eta_max=1.0 if rbf_k2 else 0.0),
+                         f"scheme {name}" + (" (Gaussian, switch, |eta| <= 1)" if rbf_k2 else
+                                             " (Gaussian, switch)" if sch == npw.NPW_RBF_ENO else ""))
 
     out = {
         "metric": "cell-updates/s",
@@ -447,8 +456,8 @@ def block_euler1d(args, characteristic: int):
         p.tile_1d = tile = args.euler_tile
     elif not characteristic:
         # the library's rule for fused steps: the tuned tile, halved while six arrays of
-        # tile + 18 cells x 3 fields exceed 76 KB
-        while tile > 256 and 6 * (tile + 18) * 3 * 4 > 76 * 1024:
+        # tile + 18 cells x 3 fields exceed 44 KB
+        while tile > 256 and 6 * (tile + 18) * 3 * 4 > 44 * 1024:
             tile //= 2
     ws = torch.empty(npw.npw_queue_workspace_size(table, p), dtype=torch.uint8, device="cuda")
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")

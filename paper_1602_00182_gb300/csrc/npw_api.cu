@@ -1691,10 +1691,11 @@ npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32
     for (int i = 0; i < count; ++i) any2d |= inst[i].ny != 0;
     r.fused = r.comp && !any2d;
     // automatic tile of fused steps: at most the size whose shared memory (six arrays of
-    // tile + 18 cells per field) still lets 3 CTAs share an SM
+    // tile + 18 cells per field) still lets the register-bound 5 CTAs share an SM (on the 1D
+    // Euler batch: 512 cells 5.3e9 cell-updates/s, 1024 4.6e9, 2048 2.3e9)
     if (params->tile_1d <= 0 && r.fused)
         while (tile > npw::TILE_1D_MIN && npw::fused1d_smem_floats(tile, flux_m(main_kind)) * sizeof(float) >
-                                              (size_t)76 * 1024)
+                                              (size_t)44 * 1024)
             tile /= 2;
     // descriptors; mixed-precision 1D instances that fit in shared memory run resident
     std::vector<npw::InstDev> h1(count);

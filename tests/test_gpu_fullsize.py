@@ -56,7 +56,8 @@ def test_burgers_batch_full_size(npw):
         dx = inst[order[k]].dx
         ref, rst = O.solve(u0, dx, 1.5, 0.5, O.BURGERS, O.PERIODIC, op)
         e = np.abs(a[offs[k]:offs[k + 1]] - ref)
-        assert e.mean() <= 1e-4 and e.max() <= 2e-2, (k, ns[k], e.mean(), e.max())
+        print(f"full-size Burgers batch, n={ns[k]}: L1 {e.mean():.3e}, Linf {e.max():.3e}")
+        assert e.mean() <= 5e-5 and e.max() <= 5e-3, (k, ns[k], e.mean(), e.max())
 
 
 @pytest.mark.parametrize("char", [0, 1])
@@ -92,6 +93,7 @@ def test_euler_batch_full_size(npw, char):
             u0 = host0[off:off + 3 * it.n].astype(np.float64).reshape(3, it.n)
             ref, _ = O.solve(u0, it.dx, tends[k], 0.5, O.EULER1D, O.TRANSMISSIVE, op)
             e = np.abs(U - ref) / np.abs(ref).max(axis=1, keepdims=True)
+            print(f"full-size Euler batch (characteristic {char}), n={it.n}: L1 {e.mean():.3e}, Linf {e.max():.3e}")
             assert e.mean() <= 1e-4 and e.max() <= 2e-2, (k, it.n, e.mean(), e.max())
             sampled += 1
         off += 3 * it.n
