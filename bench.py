@@ -741,9 +741,11 @@ def serving_requests(count: int, rate: float, seed: int = 5):
     return [dict(arrival=float(t), **it) for t, it in zip(arrivals, items)]
 
 
-def run_serving(npw, reqs, max_steps: int = 32):
-    """Continuous batching: requests are submitted at their arrival times and stepped together."""
-    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED, batch_mode=1)
+def run_serving(npw, reqs, max_steps: int = 32, precision=None):
+    """Continuous batching: requests are submitted at their arrival times and stepped together
+    (every request in the lane of the server's precision: mixed by default)."""
+    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP32_MIXED if precision is None else precision,
+                   batch_mode=1, eta_max=SWEEP_ETA_MAX)
     srv = npw.Server(heap_cells=64 * 1024 * 1024, max_slots=512, params=p)
     t0 = time.perf_counter()
     k, done = 0, {}
@@ -771,7 +773,7 @@ def fifo_service_times(npw, reqs):
     """The comparator's service time of every request: the plain FP64 per-instance solve, one
     request at a time (host copy in, solve, host copy out)."""
     import torch
-    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP64)
+    p = npw.Params(rbf=npw.NPW_RBF_GA, precision=npw.NPW_FP64, eta_max=SWEEP_ETA_MAX)
     svc, cells = [], []
     for r in reqs:
         torch.cuda.synchronize()
@@ -808,17 +810,23 @@ def serving_block(npw, count: int, rates):
     out = {"requests": count,
            "mix": "0.4 periodic Burgers (N 64..8192, T 0.15..1.5), 0.4 transmissive 1D Euler (N 256..8192), "
                   "0.2 periodic 2D Euler squares (128^2..1024^2, vortex or four-quadrant)",
-           "server_mode": "continuous batching, NPW_FP32_MIXED, per-stage kernels, 32-step rounds",
+           "server_mode": "continuous batching, NPW_FP32_MIXED, work-queue kernel, 32-step rounds; every arm "
+                          "drops faces with |eta| > 100",
            "fp64_fifo_mode": "one request at a time, npweno_solve / npweno_solve_2d NPW_FP64; latencies from "
                              "measured service times",
+           "fp64_server_mode": "the same continuous-batching server with every request in its FP64 lane, on the "
+                               "same stream: batching alone, against the FP64 FIFO",
            "rates": []}
     for rate in rates:
         reqs = serving_requests(count, rate)
         lat, thr, ok = run_serving(npw, reqs)
+        lat64, thr64, ok64 = run_serving(npw, reqs, precision=npw.NPW_FP64)
         flat, fend = fifo_latencies(svc, [r["arrival"] for r in reqs])
         out["rates"].append({
             "rate_per_s": rate,
             "server": {"p50_ms": q(lat, 50), "p99_ms": q(lat, 99), "cell_updates_per_s": thr, "all_ok": ok},
+            "fp64_server": {"p50_ms": q(lat64, 50), "p99_ms": q(lat64, 99), "cell_updates_per_s": thr64,
+                            "all_ok": ok64},
             "fp64_fifo": {"p50_ms": q(flat, 50), "p99_ms": q(flat, 99),
                           "cell_updates_per_s": float(fcells.sum() / (fend - reqs[0]["arrival"]))},
         })

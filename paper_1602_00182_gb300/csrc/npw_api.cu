@@ -1898,7 +1898,14 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 struct npw_server {
     npw_params params;
     int max_slots = 0;
-    cudaStream_t s = nullptr;
+    cudaStream_t s = nullptr;   // the caller's stream: admission, lane 0 (float), results
+    cudaStream_t s1 = nullptr;  // lane 1 (FP64), forked from s and joined back each step
+    cudaEvent_t fork = nullptr, join = nullptr;
+    ~npw_server() {
+        if (join) cudaEventDestroy(join);
+        if (fork) cudaEventDestroy(fork);
+        if (s1) cudaStreamDestroy(s1);
+    }
     unsigned char* arena = nullptr;
     int64_t heap_cells = 0;
     std::chrono::steady_clock::time_point t0;
@@ -1994,6 +2001,7 @@ npw::QueueArgs lane_queue(npw_server* sv, int ln) {
 // of the lane through the work-queue kernel.
 npw_status lane_round(npw_server* sv, int ln, int steps, bool* any_active) {
     npw_server::Lane& lane = sv->lanes[ln];
+    const cudaStream_t ls = ln == 0 ? sv->s : sv->s1;  // the lanes run concurrently
     const int S = sv->max_slots;
     std::vector<npw::InstDev> h1(S);
     std::vector<npw::Inst2D> h2(S);
@@ -2061,12 +2069,12 @@ npw_status lane_round(npw_server* sv, int ln, int steps, bool* any_active) {
     if ((int64_t)items.size() > lane.L.max_items) return fail(NPW_EINVAL, "server: too many work items");
     const LaneLayout& L = lane.L;
     unsigned char* a = sv->arena;
-    NPW_CUDA(cudaMemcpyAsync(a + L.inst1, h1.data(), sizeof(npw::InstDev) * S, cudaMemcpyHostToDevice, sv->s));
-    NPW_CUDA(cudaMemcpyAsync(a + L.inst2, h2.data(), sizeof(npw::Inst2D) * S, cudaMemcpyHostToDevice, sv->s));
-    NPW_CUDA(cudaMemcpyAsync(a + L.kind, hk.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, sv->s));
-    NPW_CUDA(cudaMemcpyAsync(a + L.is2d, h2d.data(), (size_t)S, cudaMemcpyHostToDevice, sv->s));
+    NPW_CUDA(cudaMemcpyAsync(a + L.inst1, h1.data(), sizeof(npw::InstDev) * S, cudaMemcpyHostToDevice, ls));
+    NPW_CUDA(cudaMemcpyAsync(a + L.inst2, h2.data(), sizeof(npw::Inst2D) * S, cudaMemcpyHostToDevice, ls));
+    NPW_CUDA(cudaMemcpyAsync(a + L.kind, hk.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, ls));
+    NPW_CUDA(cudaMemcpyAsync(a + L.is2d, h2d.data(), (size_t)S, cudaMemcpyHostToDevice, ls));
     NPW_CUDA(cudaMemcpyAsync(a + L.items, items.data(), sizeof(npw::Tile) * items.size(), cudaMemcpyHostToDevice,
-                             sv->s));
+                             ls));
     npw::QueueArgs q = lane_queue(sv, ln);
     q.nitems = (int32_t)items.size();
     const size_t smem = lane.fp32 ? npw::queue_smem_bytes<float>(npw::TILE_1D, has1d, m1d, has2d, m2d, false)
@@ -2074,24 +2082,24 @@ npw_status lane_round(npw_server* sv, int ln, int steps, bool* any_active) {
     if (!fresh.empty()) {
         // start the admitted requests: reset, alpha^0 over their items, first dt and step limit
         int32_t* dlist = reinterpret_cast<int32_t*>(a + L.list);
-        NPW_CUDA(cudaMemcpyAsync(dlist, fresh.data(), sizeof(int32_t) * fresh.size(), cudaMemcpyHostToDevice, sv->s));
+        NPW_CUDA(cudaMemcpyAsync(dlist, fresh.data(), sizeof(int32_t) * fresh.size(), cudaMemcpyHostToDevice, ls));
         NPW_CUDA(cudaMemcpyAsync(a + L.newitems, newitems.data(), sizeof(npw::Tile) * newitems.size(),
-                                 cudaMemcpyHostToDevice, sv->s));
-        NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, dlist, (int)fresh.size(), 0, 0, sv->s));
+                                 cudaMemcpyHostToDevice, ls));
+        NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, dlist, (int)fresh.size(), 0, 0, ls));
         npw::QueueArgs qn = q;
         qn.items = reinterpret_cast<const npw::Tile*>(a + L.newitems);
         qn.nitems = (int32_t)newitems.size();
-        const cudaError_t e = lane.fp32 ? npw::launch_queue_alpha<float>(qn, sv->s) : npw::launch_queue_alpha<double>(qn, sv->s);
+        const cudaError_t e = lane.fp32 ? npw::launch_queue_alpha<float>(qn, ls) : npw::launch_queue_alpha<double>(qn, ls);
         if (e != cudaSuccess) return cuda_fail(e, "server alpha launch");
         NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, dlist, (int)fresh.size(), 1, q.mp.max_steps,
-                                       sv->s));
+                                       ls));
         count_launch(3);
         if (lane.fp32) {  // compensated float 1D items: s = u, c = 0
             for (int kind = 0; kind < 3; ++kind) {
                 const int64_t b = new_kind_begin[kind], en = new_kind_end[kind];
                 if (en <= b) continue;
                 NPW_CUDA(npw::launch_comp_begin(reinterpret_cast<const float*>(q.u), q.s, q.c, q.inst1, qn.items + b,
-                                                (int)(en - b), npw::TILE_1D, flux_m(kind), sv->s));
+                                                (int)(en - b), npw::TILE_1D, flux_m(kind), ls));
                 count_launch();
             }
         }
@@ -2099,10 +2107,10 @@ npw_status lane_round(npw_server* sv, int ln, int steps, bool* any_active) {
     for (int step = 0; step < steps; ++step) {
         for (int st = 0; st < 3; ++st) {
             q.stage = st;
-            auto ev = stage_begin(sv->s);
-            const cudaError_t e = lane.fp32 ? npw::launch_queue_stage<float>(q, false, shape, smem, 0, sv->s)
-                                            : npw::launch_queue_stage<double>(q, false, shape, smem, 0, sv->s);
-            stage_end(ev, sv->s);
+            auto ev = stage_begin(ls);
+            const cudaError_t e = lane.fp32 ? npw::launch_queue_stage<float>(q, false, shape, smem, 0, ls)
+                                            : npw::launch_queue_stage<double>(q, false, shape, smem, 0, ls);
+            stage_end(ev, ls);
             if (e != cudaSuccess) return cuda_fail(e, "server queue stage launch");
         }
     }
@@ -2160,6 +2168,13 @@ npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max
             delete sv;
             return cuda_fail(e, "cudaMemsetAsync");
         }
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&sv->s1, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete sv;
+        return cuda_fail(e, "server stream");
     }
     sv->slots.resize(max_slots);
     sv->t0 = std::chrono::steady_clock::now();
@@ -2241,10 +2256,21 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
     int steps = max_steps;
     if (fresh.empty() && sv->remaining_hint > 0 && sv->remaining_hint < steps) steps = (int)sv->remaining_hint;
     bool any = false;
+    // the FP64 lane runs on its own stream, forked after the admissions and joined back before
+    // the results are read, so that the two lanes' rounds overlap on the GPU
+    NPW_CUDA(cudaEventRecord(sv->fork, sv->s));
+    NPW_CUDA(cudaStreamWaitEvent(sv->s1, sv->fork, 0));
     for (int ln = 0; ln < 2; ++ln) {
         bool a = false;
-        if ((st = lane_round(sv, ln, steps, &a))) return st;
+        st = lane_round(sv, ln, steps, &a);
         any |= a;
+        if (st) break;
+    }
+    {
+        const cudaError_t e1 = cudaEventRecord(sv->join, sv->s1);
+        const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(sv->s, sv->join, 0) : e1;
+        if (st) return st;
+        if (e2 != cudaSuccess) return cuda_fail(e2, "server join");
     }
     for (int k : fresh) sv->slots[k].fresh = false;
     if (!any) {
