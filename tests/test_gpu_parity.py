@@ -285,7 +285,8 @@ def test_burgers_batch_mixed_precision_accuracy(npw):
     3 S stage updates rounds the state to 2^-24 relative (|u| <= 2.5, S <= 1100 steps here),
     so smooth regions drift by at most ~3 S 2^-24 |u| ~ 5e-4 (L_inf) and far less on average;
     a shock displaced by a fraction of a cell adds jump x fraction to one cell.  Stated bars:
-    L1 <= 5e-5, L_inf <= 5e-3 per instance (observed worst: 2.4e-5 and 1.8e-3)."""
+    L1 <= 5e-6, L_inf <= 2e-3 per instance (observed worst: 2.5e-7 and 4.6e-6; the L_inf bar
+    leaves room for a shock cell)."""
     inst = I.burgers_batch(count=16, nmin=64, nmax=1024)
     table, total = npw.make_instances([it.n for it in inst], [it.dx for it in inst], [1.5] * 16, [0.5] * 16,
                                       [O.PERIODIC] * 16)
@@ -302,7 +303,7 @@ def test_burgers_batch_mixed_precision_accuracy(npw):
         worst_l1, worst_linf = max(worst_l1, e.mean()), max(worst_linf, e.max())
         off += it.n
     print(f"mixed precision Burgers T=1.5: worst L1 {worst_l1:.3e}, worst Linf {worst_linf:.3e}")
-    assert worst_l1 <= 5e-5 and worst_linf <= 5e-3
+    assert worst_l1 <= 5e-6 and worst_linf <= 2e-3
 
 
 def test_mixed_precision_single_stage(npw):
@@ -466,7 +467,7 @@ def test_per_stage_mixed_burgers_accuracy(npw):
         ref, _ = O.solve(it.u0[0].astype(np.float32).astype(np.float64), it.dx, 0.5, 0.5, O.BURGERS, O.PERIODIC, op)
         e = np.abs(a[off:off + it.n] - ref)
         print(f"per-stage mixed Burgers T=0.5, n={it.n}: L1 {e.mean():.3e}, Linf {e.max():.3e}")
-        assert e.mean() <= 5e-5 and e.max() <= 5e-3
+        assert e.mean() <= 5e-6 and e.max() <= 2e-3  # observed worst: 5.6e-7, 2.3e-4 (a shock cell)
         off += it.n
 
 
