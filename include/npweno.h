@@ -260,8 +260,12 @@ npw_status npweno_solve_2d(void* u, int64_t nx, int64_t ny, int32_t m, double dx
  * the per-stage body of that instance's kind (the same arithmetic as npweno_batch_solve and
  * npweno_solve_2d, so the same bits); steps are replayed as CUDA graphs between bounded polls.
  * NPW_FP32_MIXED component-wise runs solve 1D instances that fit in shared memory whole in one
- * CTA (the resident kernel, batch_mode 0) beside the queue.  Characteristic runs take 1D Euler
- * instances only.
+ * CTA (the resident kernel, batch_mode 0) beside the queue; when the queued instances are all
+ * 1D, each RK3 step is a single launch (u^n loaded once per tile with a 9-cell halo, the three
+ * stages in shared memory, the same bits as the per-stage launches; tile_1d 0 then takes at most
+ * the tile whose 44 KB of shared memory leaves 5 CTAs per SM).  A batch whose instances share one
+ * dimension and flux kind runs a kernel compiled for that shape.  Characteristic runs take 1D
+ * Euler instances only.
  *   arena: device, the instances' fields ([m][n] or [m][ny][nx] at `offset`, element type of
  *          params->precision); in/out.
  *   inst:  host, count descriptors (ny = 0 for a 1D instance; m follows the flux kind).
