@@ -1251,7 +1251,9 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
     // U: one cell per thread (the same arithmetic as stage2d_kernel)
     float* uout = reinterpret_cast<float*>(a.uout) + in.off;
     const float* un = reinterpret_cast<const float*>(a.un) + in.off;
-    const float dtR = s_par[2], dxR = s_par[3], dyR = s_par[4];
+    // the flux differences are scaled by 1/dx and 1/dy (two multiplies per field and cell in
+    // place of two correctly rounded divisions: 3% of this kernel's time on 2D Euler)
+    const float dtR = s_par[2], idxR = 1.0f / s_par[3], idyR = 1.0f / s_par[4];
     float vmx = 0.0f, vmy = 0.0f;
     bool bad = false;
     for (int cidx = tid; cidx < TX_2D * TY_2D; cidx += nthr) {
@@ -1263,8 +1265,8 @@ __device__ __forceinline__ void stage2d_fast_body(const Stage2DArgs& a, const In
         for (int k = 0; k < M; ++k) {
             const float* hx = ef + k * NF;
             const float* hy = hx + NFX;
-            float L = -((hx[qy * (TX_2D + 1) + qx + 1] - hx[qy * (TX_2D + 1) + qx]) / dxR);
-            L = L - (hy[(qy + 1) * TX_2D + qx] - hy[qy * TX_2D + qx]) / dyR;
+            float L = -((hx[qy * (TX_2D + 1) + qx + 1] - hx[qy * (TX_2D + 1) + qx]) * idxR);
+            L = L - (hy[(qy + 1) * TX_2D + qx] - hy[qy * TX_2D + qx]) * idyR;
             const float uk = su[(k * BY + qy + 3) * BX + qx + 3];
             const int64_t gidx = k * cells + gj * nx + gi;
             float o;
