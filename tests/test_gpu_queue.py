@@ -206,3 +206,39 @@ def test_queue_fused_step_equals_per_stage(npw, kind, bc, batch_mode):
         assert s["eta"] == rs["eta"], sp["nx"]
         parity.add(s["steps"] % 2)
     assert parity == {0, 1}
+
+
+def test_queue_fused_step_mixed_kinds_and_step_limit(npw):
+    """1D instances of three flux kinds in one queue batch (the kernel that dispatches per
+    item, fused steps): each equals its per-stage solve; with a step limit every instance stops
+    after that many fused steps with NPW_ETIMEOUT and its state is the per-stage state after
+    the same steps."""
+    g = np.random.default_rng(11)
+    specs, fields, ms = [], [], []
+    for kind, m, n in ((npw.NPW_FLUX_BURGERS, 1, 7000), (npw.NPW_FLUX_ADVECTION, 1, 9000),
+                       (npw.NPW_FLUX_EULER1D, 3, 6500), (npw.NPW_FLUX_BURGERS, 1, 300)):
+        x = (np.arange(n) + 0.5) / n
+        if m == 3:
+            rho = 1.0 + 0.2 * np.sin(2 * np.pi * 2 * x) + 0.5 * (x > 0.5)
+            f = np.concatenate([rho, 0.1 * rho, 1.0 / 0.4 + 0.005 * rho])
+        else:
+            f = 1.0 + 0.5 * np.sin(2 * np.pi * x + g.uniform(0, 6))
+        specs.append(dict(kind=kind, nx=n, dx=1.0 / n, t_end=0.02, cfl=0.5, bc=0))
+        fields.append(f)
+        ms.append(m)
+    table, total, offs = npw.make_queue_instances(specs)
+    for max_steps in (0, 5):
+        p = npw.Params(precision=npw.NPW_FP32_MIXED, batch_mode=1, max_steps=max_steps)
+        arena = torch.tensor(np.concatenate(fields), dtype=torch.float32, device="cuda")
+        st, stats = npw.npweno_queue_solve(arena, table, p, raise_on_error=False)
+        assert st == (npw.NPW_ETIMEOUT if max_steps else 0)
+        a = arena.cpu().numpy()
+        for sp, u0, off, s, m in zip(specs, fields, offs, stats, ms):
+            tb, _ = npw.make_instances([sp["nx"]], [sp["dx"]], [sp["t_end"]], [sp["cfl"]], [sp["bc"]], m=m)
+            u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+            stb, rs = npw.npweno_batch_solve(u, tb, m, sp["kind"], p, raise_on_error=False)
+            rs = rs[0]
+            assert s["status"] == rs["status"] and s["steps"] == rs["steps"], (sp, s, rs)
+            if max_steps:
+                assert s["steps"] == max_steps and s["status"] == npw.NPW_ETIMEOUT
+            assert np.array_equal(a[off:off + u0.size], u.cpu().numpy()), (sp["kind"], sp["nx"])
