@@ -810,12 +810,13 @@ def serving_block(npw, count: int, rates):
     out = {"requests": count,
            "mix": "0.4 periodic Burgers (N 64..8192, T 0.15..1.5), 0.4 transmissive 1D Euler (N 256..8192), "
                   "0.2 periodic 2D Euler squares (128^2..1024^2, vortex or four-quadrant)",
-           "server_mode": "continuous batching, NPW_FP32_MIXED, work-queue kernel, 32-step rounds; every arm "
+           "server_mode": "continuous batching, NPW_FP32_MIXED, work-queue kernels specialised per instance shape "
+                          "(one stream each; fused RK3 steps for the 1D requests), 32-step rounds; every arm "
                           "drops faces with |eta| > 100",
            "fp64_fifo_mode": "one request at a time, npweno_solve / npweno_solve_2d NPW_FP64; latencies from "
                              "measured service times",
-           "fp64_server_mode": "the same continuous-batching server with every request in its FP64 lane, on the "
-                               "same stream: batching alone, against the FP64 FIFO",
+           "fp64_server_mode": "the same continuous-batching server with every request in its FP64 lane: "
+                               "batching alone, against the FP64 FIFO",
            "rates": []}
     for rate in rates:
         reqs = serving_requests(count, rate)
@@ -963,8 +964,9 @@ def serving_sweep(npw, rates, count: int = 2000, horizon_s: float = 60.0):
            "mix": "1/3 periodic Burgers (N 64..8192), 1/3 transmissive 1D Euler (N 256..65536), 1/3 periodic 2D "
                   "Euler squares (128^2..1024^2); T x U(0.1, 1); 1/10 FP64 class (tol 1e-10), 9/10 float class "
                   "(1e-4); |eta| <= 100 in both lanes and the comparator",
-           "server": "npw_server: two lanes (NPW_FP32_MIXED, NPW_FP64) on one stream, work-queue stage kernels, "
-                     "32-step rounds",
+           "server": "npw_server: two lanes (NPW_FP32_MIXED, NPW_FP64), each with its own stream and rounds; per "
+                     "lane the requests grouped by instance shape, each group on a stream with the queue kernel "
+                     "specialised for it (fused RK3 steps for the float lane's 1D requests); 32-step rounds",
            "fifo_comparator": "FP64, one request at a time, per-stage kernels, no graphs; service time = fixed + "
                               "steps x (a + b cells) per family, measured on a size-spread sample",
            "fifo_model": model, "rates": []}

@@ -116,12 +116,16 @@ typedef struct {
                                 a run that reaches it, or whose time stops advancing (t + dt == t), ends
                                 with status NPW_ETIMEOUT instead of looping on the device; <= 0 = automatic:
                                 64 x the step count the first time step implies + 1024, at most 2^24 */
-    int32_t gauss_2d;        /* 2D entry points, NPW_FP64, k = 2 (RBF schemes: with cross_2d): 1 = the integral
+    int32_t gauss_2d;        /* 2D entry points, k = 2 (RBF schemes: with cross_2d): 1 = the integral
                                 of eq. 2DIntegral by two Gauss points per face (Sec. 7 names two points as
                                 needed for third order): the reconstruction of Sec. 6 at -+ 1/(2 sqrt 3) cell
                                 widths from the face midpoint, its Taylor error there cancelled by the shape
                                 parameter (the v_xy term with the diagonal neighbour), and the mean of the two
-                                Lax-Friedrichs fluxes; 0 = one point at the midpoint, as in the paper's runs */
+                                Lax-Friedrichs fluxes; 0 = one point at the midpoint, as in the paper's runs.
+                                NPW_FP32_MIXED: float state, candidates, weights, flux and update, the shape
+                                parameters, switch, ENO choices and smoothness indicators in double from the
+                                float averages (npweno_rk3_step_2d / npweno_solve_2d; the work queue and the
+                                server take it in NPW_FP64 only, else NPW_EINVAL) */
     int32_t reserved_;       /* 0 */
 } npw_params;
 
@@ -293,18 +297,25 @@ npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32
  * admitted first-in first-out whenever a slot and heap space are free.  Each request carries its
  * own end time and tolerance; the tolerance picks its precision lane: NPW_FP32_MIXED for a
  * tolerance >= 1e-4 (the mixed path's stated L1 class), NPW_FP64 below (0: the server's
- * params->precision).  Every npw_server_step advances all admitted requests of both lanes
- * together -- each with its own dt, alpha, step count and t_end -- by up to max_steps RK3 steps
- * through the work-queue kernel (per lane and stage one persistent launch over every work item
- * of every admitted request, 1D and 2D), then copies finished states to their host buffers and
- * frees their space.  Each request's arithmetic depends only on its own data, so its result is
- * the same bits alone or in any mix (and equal to npweno_batch_solve with batch_mode 1 or
- * npweno_solve_2d of the same request in its lane's precision).
+ * params->precision).  Each lane runs rounds on its own stream (the mixed lane on `stream`, the
+ * FP64 lane on a stream of the server's), independently of the other lane: a round advances
+ * every admitted request of the lane -- each with its own dt, alpha, step count and t_end -- by
+ * an even number of RK3 steps (max_steps rounded down to even, at least 2) through the work-
+ * queue kernel, with the requests grouped by instance shape (1D or 2D, flux kind), each group on
+ * a stream of its own with the kernel specialised for that shape (per stage one persistent
+ * launch over the group's work items; the mixed lane's 1D requests take one launch per fused
+ * RK3 step).  npw_server_step retires every lane whose round has ended (copies finished states
+ * to their host buffers, frees their space), admits that lane's queued requests and launches its
+ * next round; when no round has ended yet it waits (bounded) for the first that does.  Each
+ * request's arithmetic depends only on its own data, so its result is the same bits alone or in
+ * any mix (and equal to npweno_batch_solve with batch_mode 1 or npweno_solve_2d of the same
+ * request in its lane's precision).
  *   device_arena / arena_bytes: caller-owned device memory, at least
  *       npw_server_arena_bytes(heap_cells, max_slots, params): a heap of heap_cells elements per
  *       lane (a request occupies m * n, 2D m * n * ny, heap cells of its lane).
  *   params: method of every request; params->precision is the lane of requests with tolerance 0.
- *   stream: cudaStream_t (void*) for all server work.
+ *   stream: cudaStream_t (void*) of the mixed lane and of creation; npw_server_destroy waits
+ *       (bounded) for both lanes' rounds before it returns.
  * Host buffers of a request (u0_host read at admission, out_host written at completion, both
  * [m][n] ([m][ny][nx]) of its lane's element type: float for the mixed lane, double for FP64)
  * must stay valid until its result has been polled.  Timestamps are seconds since
@@ -345,8 +356,9 @@ npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max
 /* Queue a request.  NPW_EINVAL for a malformed request or one larger than the whole heap;
  * NPW_EBUSY when max_slots requests are already waiting. */
 npw_status npw_server_submit(npw_server* s, const npw_request* req, uint64_t* id);
-/* One round: admit, advance every admitted request by up to max_steps steps, retire finished
- * ones.  *active / *queued (may be NULL) receive the counts after the round. */
+/* Retire the lanes whose rounds have ended (waiting for one if none has), admit their queued
+ * requests and launch their next rounds of max_steps steps (rounded down to even, at least 2).
+ * *active / *queued (may be NULL) receive the admitted and the queued request counts. */
 npw_status npw_server_step(npw_server* s, int32_t max_steps, int32_t* active, int32_t* queued);
 /* Completed results, oldest first; *nout <= max. */
 npw_status npw_server_poll(npw_server* s, npw_result* out, int32_t max, int32_t* nout);

@@ -69,14 +69,15 @@ npw_status check_params(const npw_params* p) {
     return NPW_OK;
 }
 
-// the two-point Gauss rule of the 2D entry points: k = 2, the cross form for the RBF schemes,
-// the FP64 path
-npw_status check_gauss(const npw_params* p) {
+// the two-point Gauss rule of the 2D entry points: k = 2, the cross form for the RBF schemes;
+// both precisions in npweno_rk3_step_2d / npweno_solve_2d, the FP64 path in the work queue
+npw_status check_gauss(const npw_params* p, bool queue = false) {
     if (!p->gauss_2d) return NPW_OK;
     if (p->k != 2) return fail(NPW_EINVAL, "gauss_2d needs k = 2 (the point reconstruction of Sec. 6)");
     if ((p->scheme == NPW_RBF_ENO || p->scheme == NPW_RBF_WENO) && !p->cross_2d)
         return fail(NPW_EINVAL, "gauss_2d with an RBF scheme needs cross_2d = 1");
-    if (p->precision != NPW_FP64) return fail(NPW_EINVAL, "gauss_2d is implemented for NPW_FP64");
+    if (queue && p->precision != NPW_FP64)
+        return fail(NPW_EINVAL, "the work queue runs gauss_2d in NPW_FP64 (NPW_FP32_MIXED: npweno_solve_2d)");
     return NPW_OK;
 }
 
@@ -1484,7 +1485,7 @@ npw_status check_queue(const npw_queue_instance* inst, int count, const npw_para
             if (q.nx < 6 || q.ny < 6 || q.nx * q.ny > ((int64_t)1 << 31) || !(q.dy > 0.0))
                 return fail(NPW_EINVAL, "instance %d: bad 2D size or dy", i);
             if (q.bc_y >= 0 && (st = check_bc(q.bc_y))) return st;
-            if ((st = check_gauss(p))) return st;
+            if ((st = check_gauss(p, true))) return st;
         }
         if ((st = check_bc(q.bc))) return st;
         if (!(q.dx > 0.0) || !(q.cfl > 0.0)) return fail(NPW_EINVAL, "instance %d: bad dx or cfl", i);
@@ -1835,6 +1836,7 @@ npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32
 namespace {
 
 constexpr double kMixedTolerance = 1e-4;  // requests with tolerance >= this take the mixed lane
+constexpr int kGroups = 7;                // instance shapes (npw::QueueShape): one launch group each
 
 struct LaneLayout {
     size_t inst1, inst2, kind, is2d, ctl, items, newitems, list, head, poll, heap_u, heap_u1, heap_u2, heap_s, heap_c;
@@ -1864,8 +1866,8 @@ LaneLayout lane_layout(size_t begin, int64_t heap_cells, int max_slots, size_t e
     o = align256(o + sizeof(npw::Tile) * (size_t)L.max_items);
     L.list = o;
     o = align256(o + sizeof(int32_t) * (size_t)max_slots);
-    L.head = o;
-    o = align256(o + 2 * sizeof(unsigned int));
+    L.head = o;  // a queue counter pair per launch group
+    o = align256(o + 2 * kGroups * sizeof(unsigned int));
     L.poll = o;
     o = align256(o + 256);
     L.heap_u = o;
@@ -1893,27 +1895,43 @@ double now_s(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// 1D tile of the float lane's fused steps: the largest whose six shared arrays (tile + 18 cells
+// per field) stay within 44 KB, so that five CTAs share an SM (1024 cells for m = 1, 512 for
+// 1D Euler)
+int fused_tile(int m) {
+    int t = npw::TILE_1D;
+    while (t > npw::TILE_1D_MIN && npw::fused1d_smem_floats(t, m) * sizeof(float) > (size_t)44 * 1024) t /= 2;
+    return t;
+}
+
 }  // namespace
 
 struct npw_server {
     npw_params params;
     int max_slots = 0;
-    cudaStream_t s = nullptr;   // the caller's stream: admission, lane 0 (float), results
-    cudaStream_t s1 = nullptr;  // lane 1 (FP64), forked from s and joined back each step
-    cudaEvent_t fork = nullptr, join = nullptr;
-    ~npw_server() {
-        if (join) cudaEventDestroy(join);
-        if (fork) cudaEventDestroy(fork);
-        if (s1) cudaStreamDestroy(s1);
-    }
+    cudaStream_t s = nullptr;  // the caller's stream: creation, lane 0 (float)
     unsigned char* arena = nullptr;
     int64_t heap_cells = 0;
     std::chrono::steady_clock::time_point t0;
+    struct Pending {
+        uint64_t id;
+        npw_request req;
+        double submit_s;
+    };
+    // A lane runs its rounds on its own stream, independently of the other lane: a round is
+    // launched, and retired by a later npw_server_step once its completion event has fired.
     struct Lane {
         LaneLayout L{};
         npw::MethodParams mp{};
         bool fp32 = false;
         size_t esz = 8;
+        cudaStream_t st = nullptr;             // lane 0: the caller's stream; lane 1: its own
+        bool own_stream = false;
+        cudaStream_t sub[kGroups] = {};        // one stream per instance shape within a round
+        cudaEvent_t fork = nullptr, done = nullptr, join[kGroups] = {};
+        bool in_flight = false;                // a round has been launched and not yet retired
+        std::deque<Pending> pending;           // submitted, not yet admitted (first in first out)
+        long long remaining_hint = 0;          // largest remaining step estimate after the last round
         std::vector<std::pair<int64_t, int64_t>> free_ranges;  // [begin, end), sorted, disjoint
         std::vector<npw::Ctl> host_ctl;
         bool heap_alloc(int64_t len, int64_t* off) {
@@ -1940,7 +1958,20 @@ struct npw_server {
             }
             free_ranges.swap(merged);
         }
+        void release() {
+            if (st) bounded_sync(st);  // no round of this lane may outlive the server
+            for (int g = 0; g < kGroups; ++g) {
+                if (join[g]) cudaEventDestroy(join[g]);
+                if (sub[g]) cudaStreamDestroy(sub[g]);
+            }
+            if (fork) cudaEventDestroy(fork);
+            if (done) cudaEventDestroy(done);
+            if (own_stream && st) cudaStreamDestroy(st);
+        }
     } lanes[2];
+    ~npw_server() {
+        for (auto& ln : lanes) ln.release();
+    }
     struct Slot {
         bool used = false;
         bool fresh = false;
@@ -1949,31 +1980,26 @@ struct npw_server {
         int lane = 0;
         int m = 1;
         bool is2d = false;
-        int64_t cells = 0;  // heap cells: m n (2D: m n ny)
+        bool fused = false;  // float lane 1D: fused steps, the state alternating between u and s
+        int64_t cells = 0;   // heap cells: m n (2D: m n ny)
         int64_t off = 0;
         double submit_s = 0.0, admit_s = 0.0;
     };
     std::vector<Slot> slots;  // a slot's index is its instance index in its lane's tables
-    struct Pending {
-        uint64_t id;
-        npw_request req;
-        double submit_s;
-    };
-    std::deque<Pending> queue;
     std::deque<npw_result> results;
     uint64_t next_id = 1;
-    long long remaining_hint = 0;  // largest remaining step estimate after the last round
 
     // the lane of a request: its tolerance, else the server's precision
     int lane_of(const npw_request& r) const {
         if (r.tolerance > 0.0) return r.tolerance >= kMixedTolerance ? 0 : 1;
         return params.precision == NPW_FP32_MIXED ? 0 : 1;
     }
+    size_t pending_count() const { return lanes[0].pending.size() + lanes[1].pending.size(); }
 };
 
 namespace {
 
-// the queue arguments of a lane (all its slots; items and counts filled by the caller)
+// the queue arguments of a lane (all its slots; items, counts, tile and counters filled per group)
 npw::QueueArgs lane_queue(npw_server* sv, int ln) {
     npw_server::Lane& lane = sv->lanes[ln];
     const LaneLayout& L = lane.L;
@@ -1998,33 +2024,42 @@ npw::QueueArgs lane_queue(npw_server* sv, int ln) {
 }
 
 // Instance tables, work items and start of a lane's admitted requests; then `steps` RK3 steps
-// of the lane through the work-queue kernel.
-npw_status lane_round(npw_server* sv, int ln, int steps, bool* any_active) {
+// (an even count) of every active request of the lane.  The requests are grouped by instance
+// shape; each group runs on its own stream, forked from the lane's stream and joined back, with
+// the queue kernel specialised for that shape (one persistent launch per stage; for the float
+// lane's 1D requests one per fused RK3 step, whose two state buffers alternate with the step
+// parity: every round starts at parity 0 because rounds have even length and requests are
+// admitted only between rounds).
+npw_status lane_round(npw_server* sv, int ln, int steps) {
     npw_server::Lane& lane = sv->lanes[ln];
-    const cudaStream_t ls = ln == 0 ? sv->s : sv->s1;  // the lanes run concurrently
+    const cudaStream_t ls = lane.st;
     const int S = sv->max_slots;
+    struct Group {
+        std::vector<int> members;
+        bool is2d = false, fused = false;
+        int m = 1, tile = npw::TILE_1D;
+        int64_t ib = 0, ie = 0, nb = 0, ne = 0;  // [ib, ie) in items, [nb, ne) in newitems
+    } grp[kGroups];
     std::vector<npw::InstDev> h1(S);
     std::vector<npw::Inst2D> h2(S);
     std::vector<int32_t> hk(S, 0);
     std::vector<uint8_t> h2d(S, 0);
     std::vector<npw::Tile> items, newitems;
     std::vector<int32_t> fresh;
-    int64_t new_kind_begin[3] = {0, 0, 0}, new_kind_end[3] = {0, 0, 0};
-    bool has1d = false, has2d = false;
-    int m1d = 1, m2d = 1;
-    int shape = -1;  // the one shape of the lane's active slots, else QS_ANY
     for (int k = 0; k < S; ++k) {
-        const npw_server::Slot& sl = sv->slots[k];
+        npw_server::Slot& sl = sv->slots[k];
         if (!sl.used || sl.lane != ln) continue;
+        Group& g = grp[npw::queue_shape_of(sl.is2d, sl.req.flux_kind)];
+        g.members.push_back(k);
+        g.is2d = sl.is2d;
+        g.m = sl.m;
+        g.fused = sl.fused;
+        g.tile = sl.fused ? fused_tile(sl.m) : npw::TILE_1D;
         hk[k] = sl.req.flux_kind;
         h2d[k] = sl.is2d;
-        const int sh = npw::queue_shape_of(sl.is2d, sl.req.flux_kind);
-        shape = (shape < 0 || shape == sh) ? sh : (int)npw::QS_ANY;
         if (!sl.is2d) {
             h1[k] = npw::InstDev{sl.off, sl.req.n, sl.req.dx, sl.req.t_end, sl.req.cfl, sl.req.bc,
-                                 (int32_t)tiles_of(sl.req.n, npw::TILE_1D)};
-            has1d = true;
-            m1d = sl.m > m1d ? sl.m : m1d;
+                                 (int32_t)tiles_of(sl.req.n, g.tile)};
         } else {
             npw::Inst2D& d = h2[k];
             d.off = sl.off;
@@ -2038,34 +2073,32 @@ npw_status lane_round(npw_server* sv, int ln, int steps, bool* any_active) {
             d.bc_y = sl.req.bc_y < 0 ? sl.req.bc : sl.req.bc_y;
             d.tiles_x = (int32_t)((sl.req.n + npw::TX_2D - 1) / npw::TX_2D);
             d.tiles_y = (int32_t)((sl.req.ny + npw::TY_2D - 1) / npw::TY_2D);
-            has2d = true;
-            m2d = sl.m > m2d ? sl.m : m2d;
         }
         if (sl.fresh) fresh.push_back(k);
     }
-    if (!has1d && !has2d) {
-        *any_active = false;
-        return NPW_OK;
-    }
-    *any_active = true;
-    // 1D items grouped by flux kind, then 2D items; the admitted requests' items likewise
-    for (int pass = 0; pass < 2; ++pass) {
-        std::vector<npw::Tile>& v = pass == 0 ? items : newitems;
-        for (int kind = 0; kind < 3; ++kind) {
-            if (pass == 1) new_kind_begin[kind] = (int64_t)v.size();
-            for (int k = 0; k < S; ++k) {
-                const npw_server::Slot& sl = sv->slots[k];
-                if (!sl.used || sl.lane != ln || sl.is2d || hk[k] != kind || (pass == 1 && !sl.fresh)) continue;
-                for (int32_t t = 0; t < h1[k].ntiles; ++t) v.push_back(npw::Tile{k, t * npw::TILE_1D});
+    // work items, contiguous per group; the admitted requests' items likewise
+    for (int gi = 0; gi < kGroups; ++gi) {
+        Group& g = grp[gi];
+        g.ib = (int64_t)items.size();
+        g.nb = (int64_t)newitems.size();
+        for (int k : g.members) {
+            const bool fr = sv->slots[k].fresh;
+            if (!g.is2d) {
+                for (int32_t t = 0; t < h1[k].ntiles; ++t) {
+                    items.push_back(npw::Tile{k, t * g.tile});
+                    if (fr) newitems.push_back(npw::Tile{k, t * g.tile});
+                }
+            } else {
+                for (int32_t t = 0; t < h2[k].tiles_x * h2[k].tiles_y; ++t) {
+                    items.push_back(npw::Tile{k, t});
+                    if (fr) newitems.push_back(npw::Tile{k, t});
+                }
             }
-            if (pass == 1) new_kind_end[kind] = (int64_t)v.size();
         }
-        for (int k = 0; k < S; ++k) {
-            const npw_server::Slot& sl = sv->slots[k];
-            if (!sl.used || sl.lane != ln || !sl.is2d || (pass == 1 && !sl.fresh)) continue;
-            for (int32_t t = 0; t < h2[k].tiles_x * h2[k].tiles_y; ++t) v.push_back(npw::Tile{k, t});
-        }
+        g.ie = (int64_t)items.size();
+        g.ne = (int64_t)newitems.size();
     }
+    if (items.empty()) return NPW_OK;
     if ((int64_t)items.size() > lane.L.max_items) return fail(NPW_EINVAL, "server: too many work items");
     const LaneLayout& L = lane.L;
     unsigned char* a = sv->arena;
@@ -2075,46 +2108,217 @@ npw_status lane_round(npw_server* sv, int ln, int steps, bool* any_active) {
     NPW_CUDA(cudaMemcpyAsync(a + L.is2d, h2d.data(), (size_t)S, cudaMemcpyHostToDevice, ls));
     NPW_CUDA(cudaMemcpyAsync(a + L.items, items.data(), sizeof(npw::Tile) * items.size(), cudaMemcpyHostToDevice,
                              ls));
-    npw::QueueArgs q = lane_queue(sv, ln);
-    q.nitems = (int32_t)items.size();
-    const size_t smem = lane.fp32 ? npw::queue_smem_bytes<float>(npw::TILE_1D, has1d, m1d, has2d, m2d, false)
-                                  : npw::queue_smem_bytes<double>(npw::TILE_1D, has1d, m1d, has2d, m2d, false);
+    const npw::QueueArgs q0 = lane_queue(sv, ln);
+    const npw::Tile* ditems = q0.items;
+    const npw::Tile* dnew = reinterpret_cast<const npw::Tile*>(a + L.newitems);
     if (!fresh.empty()) {
         // start the admitted requests: reset, alpha^0 over their items, first dt and step limit
         int32_t* dlist = reinterpret_cast<int32_t*>(a + L.list);
         NPW_CUDA(cudaMemcpyAsync(dlist, fresh.data(), sizeof(int32_t) * fresh.size(), cudaMemcpyHostToDevice, ls));
         NPW_CUDA(cudaMemcpyAsync(a + L.newitems, newitems.data(), sizeof(npw::Tile) * newitems.size(),
                                  cudaMemcpyHostToDevice, ls));
-        NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, dlist, (int)fresh.size(), 0, 0, ls));
-        npw::QueueArgs qn = q;
-        qn.items = reinterpret_cast<const npw::Tile*>(a + L.newitems);
-        qn.nitems = (int32_t)newitems.size();
-        const cudaError_t e = lane.fp32 ? npw::launch_queue_alpha<float>(qn, ls) : npw::launch_queue_alpha<double>(qn, ls);
-        if (e != cudaSuccess) return cuda_fail(e, "server alpha launch");
-        NPW_CUDA(npw::launch_queue_ctl(q.ctl, q.inst1, q.inst2, q.is2d, dlist, (int)fresh.size(), 1, q.mp.max_steps,
+        NPW_CUDA(npw::launch_queue_ctl(q0.ctl, q0.inst1, q0.inst2, q0.is2d, dlist, (int)fresh.size(), 0, 0, ls));
+        count_launch();
+        for (int gi = 0; gi < kGroups; ++gi) {
+            const Group& g = grp[gi];
+            if (g.ne <= g.nb) continue;
+            npw::QueueArgs qn = q0;
+            qn.items = dnew + g.nb;
+            qn.nitems = (int32_t)(g.ne - g.nb);
+            qn.tile = g.tile;
+            const cudaError_t e = lane.fp32 ? npw::launch_queue_alpha<float>(qn, ls) : npw::launch_queue_alpha<double>(qn, ls);
+            if (e != cudaSuccess) return cuda_fail(e, "server alpha launch");
+            count_launch();
+        }
+        NPW_CUDA(npw::launch_queue_ctl(q0.ctl, q0.inst1, q0.inst2, q0.is2d, dlist, (int)fresh.size(), 1, q0.mp.max_steps,
                                        ls));
-        count_launch(3);
+        count_launch();
         if (lane.fp32) {  // compensated float 1D items: s = u, c = 0
-            for (int kind = 0; kind < 3; ++kind) {
-                const int64_t b = new_kind_begin[kind], en = new_kind_end[kind];
-                if (en <= b) continue;
-                NPW_CUDA(npw::launch_comp_begin(reinterpret_cast<const float*>(q.u), q.s, q.c, q.inst1, qn.items + b,
-                                                (int)(en - b), npw::TILE_1D, flux_m(kind), ls));
+            for (int gi = 0; gi < kGroups; ++gi) {
+                const Group& g = grp[gi];
+                if (g.is2d || g.ne <= g.nb) continue;
+                NPW_CUDA(npw::launch_comp_begin(reinterpret_cast<const float*>(q0.u), q0.s, q0.c, q0.inst1, dnew + g.nb,
+                                                (int)(g.ne - g.nb), g.tile, g.m, ls));
                 count_launch();
             }
         }
     }
-    for (int step = 0; step < steps; ++step) {
-        for (int st = 0; st < 3; ++st) {
-            q.stage = st;
-            auto ev = stage_begin(ls);
-            const cudaError_t e = lane.fp32 ? npw::launch_queue_stage<float>(q, false, shape, smem, 0, ls)
-                                            : npw::launch_queue_stage<double>(q, false, shape, smem, 0, ls);
-            stage_end(ev, ls);
-            if (e != cudaSuccess) return cuda_fail(e, "server queue stage launch");
+    NPW_CUDA(cudaEventRecord(lane.fork, ls));
+    for (int gi = 0; gi < kGroups; ++gi) {
+        const Group& g = grp[gi];
+        if (g.ie <= g.ib) continue;
+        const cudaStream_t gs = lane.sub[gi];
+        NPW_CUDA(cudaStreamWaitEvent(gs, lane.fork, 0));
+        npw::QueueArgs q = q0;
+        q.items = ditems + g.ib;
+        q.nitems = (int32_t)(g.ie - g.ib);
+        q.tile = g.tile;
+        q.head = q0.head + 2 * gi;
+        size_t smem;
+        if (g.fused)
+            smem = npw::fused1d_smem_floats(g.tile, g.m) * sizeof(float);
+        else if (lane.fp32)
+            smem = npw::queue_smem_bytes<float>(g.tile, !g.is2d, g.m, g.is2d, g.m, false);
+        else
+            smem = npw::queue_smem_bytes<double>(g.tile, !g.is2d, g.m, g.is2d, g.m, false);
+        for (int step = 0; step < steps; ++step) {
+            if (g.fused) {
+                q.stage = npw::QUEUE_FUSED_STEP;
+                q.parity = step & 1;
+                auto ev = stage_begin(gs);
+                const cudaError_t e = npw::launch_queue_stage<float>(q, false, gi, smem, 0, gs);
+                stage_end(ev, gs);
+                if (e != cudaSuccess) return cuda_fail(e, "server fused step launch");
+                continue;
+            }
+            for (int st = 0; st < 3; ++st) {
+                q.stage = st;
+                auto ev = stage_begin(gs);
+                const cudaError_t e = lane.fp32 ? npw::launch_queue_stage<float>(q, false, gi, smem, 0, gs)
+                                                : npw::launch_queue_stage<double>(q, false, gi, smem, 0, gs);
+                stage_end(ev, gs);
+                if (e != cudaSuccess) return cuda_fail(e, "server queue stage launch");
+            }
         }
+        NPW_CUDA(cudaEventRecord(lane.join[gi], gs));
+        NPW_CUDA(cudaStreamWaitEvent(ls, lane.join[gi], 0));
     }
     return NPW_OK;
+}
+
+// The lane's round has ended: read its control words, copy finished states to their host
+// buffers, record their results and free their heap space.
+npw_status lane_retire(npw_server* sv, int ln) {
+    npw_server::Lane& lane = sv->lanes[ln];
+    npw_status st = bounded_sync(lane.st);
+    if (st) return st;
+    lane.in_flight = false;
+    NPW_CUDA(cudaMemcpyAsync(lane.host_ctl.data(), sv->arena + lane.L.ctl, sizeof(npw::Ctl) * sv->max_slots,
+                             cudaMemcpyDeviceToHost, lane.st));
+    if ((st = bounded_sync(lane.st))) return st;
+    profile_collect();
+    std::vector<int> finished;
+    long long rem = 0;
+    for (int k = 0; k < sv->max_slots; ++k) {
+        const npw_server::Slot& sl = sv->slots[k];
+        if (!sl.used || sl.lane != ln) continue;
+        const npw::Ctl& c = lane.host_ctl[k];
+        if (c.done) {
+            finished.push_back(k);
+        } else {
+            const double r = c.dt > 0.0 ? (sl.req.t_end - c.t) / c.dt : 1.0;
+            const long long ri = (long long)(r < 1e9 ? r : 1e9) + 1;
+            rem = ri > rem ? ri : rem;
+        }
+    }
+    lane.remaining_hint = rem;
+    for (int k : finished) {
+        // the float lane's 1D requests end in s after an odd number of fused steps, else in u
+        const npw_server::Slot& sl = sv->slots[k];
+        const size_t region = (sl.fused && (lane.host_ctl[k].steps & 1)) ? lane.L.heap_s : lane.L.heap_u;
+        NPW_CUDA(cudaMemcpyAsync(sl.req.out_host, sv->arena + region + (size_t)sl.off * lane.esz,
+                                 (size_t)sl.cells * lane.esz, cudaMemcpyDeviceToHost, lane.st));
+    }
+    if (!finished.empty() && (st = bounded_sync(lane.st))) return st;
+    const double tdone = now_s(sv->t0);
+    for (int k : finished) {
+        npw_server::Slot& sl = sv->slots[k];
+        const npw::Ctl& c = lane.host_ctl[k];
+        npw_result r{};
+        r.id = sl.id;
+        r.tag = sl.req.tag;
+        r.status = c.status;
+        r.precision = ln == 0 ? NPW_FP32_MIXED : NPW_FP64;
+        r.steps = c.steps;
+        r.t = c.t;
+        r.submit_s = sl.submit_s;
+        r.admit_s = sl.admit_s;
+        r.done_s = tdone;
+        sv->results.push_back(r);
+        lane.heap_free(sl.off, sl.cells);
+        sl.used = false;
+    }
+    return NPW_OK;
+}
+
+// Admit the lane's pending requests (first in first out, while a slot and heap space are
+// free), then launch its next round if it has active requests.
+npw_status lane_next_round(npw_server* sv, int ln, int base_steps) {
+    npw_server::Lane& lane = sv->lanes[ln];
+    bool admitted = false;
+    while (!lane.pending.empty()) {
+        const npw_server::Pending& p = lane.pending.front();
+        const int m = flux_m(p.req.flux_kind);
+        const bool is2d = p.req.ny != 0;
+        const int64_t cells = p.req.n * m * (is2d ? p.req.ny : 1);
+        int slot = -1;
+        for (int k = 0; k < sv->max_slots; ++k)
+            if (!sv->slots[k].used) {
+                slot = k;
+                break;
+            }
+        int64_t off = 0;
+        if (slot < 0 || !lane.heap_alloc(cells, &off)) break;
+        // the request's host values are of its lane's element type
+        NPW_CUDA(cudaMemcpyAsync(sv->arena + lane.L.heap_u + (size_t)off * lane.esz, p.req.u0_host,
+                                 (size_t)cells * lane.esz, cudaMemcpyHostToDevice, lane.st));
+        npw_server::Slot& sl = sv->slots[slot];
+        sl.used = true;
+        sl.fresh = true;
+        sl.id = p.id;
+        sl.req = p.req;
+        sl.lane = ln;
+        sl.m = m;
+        sl.is2d = is2d;
+        sl.fused = lane.fp32 && !is2d;
+        sl.cells = cells;
+        sl.off = off;
+        sl.submit_s = p.submit_s;
+        sl.admit_s = now_s(sv->t0);
+        lane.pending.pop_front();
+        admitted = true;
+    }
+    bool any = false;
+    for (int k = 0; k < sv->max_slots && !any; ++k) any = sv->slots[k].used && sv->slots[k].lane == ln;
+    if (!any) return NPW_OK;
+    // a shorter round when nothing was admitted and every active request is close to its end
+    int steps = base_steps;
+    if (!admitted && lane.remaining_hint > 0 && lane.remaining_hint < steps)
+        steps = (int)((lane.remaining_hint + 1) & ~1LL);
+    if (steps < 2) steps = 2;
+    const npw_status st = lane_round(sv, ln, steps);
+    for (int k = 0; k < sv->max_slots; ++k)
+        if (sv->slots[k].used && sv->slots[k].lane == ln) sv->slots[k].fresh = false;
+    if (st) return st;
+    NPW_CUDA(cudaEventRecord(lane.done, lane.st));
+    lane.in_flight = true;
+    return NPW_OK;
+}
+
+// Wait (bounded) until the round of some lane in flight has ended; *which = that lane, or -1
+// when no lane has a round in flight.
+npw_status wait_any_lane(npw_server* sv, int* which) {
+    *which = -1;
+    if (!sv->lanes[0].in_flight && !sv->lanes[1].in_flight) return NPW_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    const double limit = wait_timeout_s();
+    for (;;) {
+        for (int ln = 0; ln < 2; ++ln) {
+            if (!sv->lanes[ln].in_flight) continue;
+            const cudaError_t e = cudaEventQuery(sv->lanes[ln].done);
+            if (e == cudaSuccess) {
+                *which = ln;
+                return NPW_OK;
+            }
+            if (e != cudaErrorNotReady) return cuda_fail(e, "cudaEventQuery");
+        }
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > limit) return fail(NPW_ETIMEOUT, "no server round completed within %.0f s", limit);
+        if (el > 1e-3) {
+            struct timespec ts = {0, 20000};
+            nanosleep(&ts, nullptr);
+        }
+    }
 }
 
 }  // namespace
@@ -2150,7 +2354,8 @@ npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max
     sv->s = reinterpret_cast<cudaStream_t>(stream);
     sv->arena = static_cast<unsigned char*>(device_arena);
     sv->heap_cells = lo;
-    for (int ln = 0; ln < 2; ++ln) {
+    cudaError_t e = cudaSuccess;
+    for (int ln = 0; ln < 2 && e == cudaSuccess; ++ln) {
         npw_server::Lane& lane = sv->lanes[ln];
         npw_params pl = *params;
         pl.precision = ln == 0 ? NPW_FP32_MIXED : NPW_FP64;
@@ -2163,18 +2368,26 @@ npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max
         lane.free_ranges.push_back({0, lo});
         lane.host_ctl.resize(max_slots);
         // zero the queue counters once; every launch leaves them zero
-        cudaError_t e = cudaMemsetAsync(sv->arena + lane.L.head, 0, 2 * sizeof(unsigned int), sv->s);
-        if (e != cudaSuccess) {
-            delete sv;
-            return cuda_fail(e, "cudaMemsetAsync");
+        e = cudaMemsetAsync(sv->arena + lane.L.head, 0, 2 * kGroups * sizeof(unsigned int), sv->s);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lane.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lane.done, cudaEventDisableTiming);
+        for (int g = 0; g < kGroups && e == cudaSuccess; ++g) {
+            e = cudaStreamCreateWithFlags(&lane.sub[g], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lane.join[g], cudaEventDisableTiming);
+        }
+        if (ln == 0) {
+            lane.st = sv->s;
+        } else if (e == cudaSuccess) {
+            e = cudaStreamCreateWithFlags(&lane.st, cudaStreamNonBlocking);
+            lane.own_stream = e == cudaSuccess;
         }
     }
-    cudaError_t e = cudaStreamCreateWithFlags(&sv->s1, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->join, cudaEventDisableTiming);
+    // the FP64 lane's stream starts after the counters are zeroed on the caller's stream
+    if (e == cudaSuccess) e = cudaEventRecord(sv->lanes[1].fork, sv->s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sv->lanes[1].st, sv->lanes[1].fork, 0);
     if (e != cudaSuccess) {
         delete sv;
-        return cuda_fail(e, "server stream");
+        return cuda_fail(e, "server streams");
     }
     sv->slots.resize(max_slots);
     sv->t0 = std::chrono::steady_clock::now();
@@ -2206,129 +2419,43 @@ npw_status npw_server_submit(npw_server* sv, const npw_request* req, uint64_t* i
     const int m = flux_m(req->flux_kind);
     const int64_t cells = req->n * m * (is2d ? req->ny : 1);
     if (cells > sv->heap_cells) return fail(NPW_EINVAL, "request larger than the server heap");
-    if ((int)sv->queue.size() >= sv->max_slots) return fail(NPW_EBUSY, "request queue full");
+    if ((int)sv->pending_count() >= sv->max_slots) return fail(NPW_EBUSY, "request queue full");
     npw_server::Pending p{sv->next_id++, *req, now_s(sv->t0)};
-    sv->queue.push_back(p);
+    sv->lanes[sv->lane_of(*req)].pending.push_back(p);
     if (id) *id = p.id;
     return NPW_OK;
 }
 
 npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, int32_t* queued) {
     if (!sv || max_steps < 1) return fail(NPW_EINVAL, "bad server step arguments");
+    const int base_steps = max_steps >= 2 ? (max_steps & ~1) : 2;
     npw_status st = NPW_OK;
-    // 1. admit, first in first out: a free slot and space in the request's lane
-    std::vector<int> fresh;
-    while (!sv->queue.empty()) {
-        const npw_server::Pending& p = sv->queue.front();
-        const int ln = sv->lane_of(p.req);
-        npw_server::Lane& lane = sv->lanes[ln];
-        const int m = flux_m(p.req.flux_kind);
-        const bool is2d = p.req.ny != 0;
-        const int64_t cells = p.req.n * m * (is2d ? p.req.ny : 1);
-        int slot = -1;
-        for (int k = 0; k < sv->max_slots; ++k)
-            if (!sv->slots[k].used) {
-                slot = k;
-                break;
-            }
-        int64_t off = 0;
-        if (slot < 0 || !lane.heap_alloc(cells, &off)) break;
-        // the request's host values are of its lane's element type
-        NPW_CUDA(cudaMemcpyAsync(sv->arena + lane.L.heap_u + (size_t)off * lane.esz, p.req.u0_host,
-                                 (size_t)cells * lane.esz, cudaMemcpyHostToDevice, sv->s));
-        npw_server::Slot& sl = sv->slots[slot];
-        sl.used = true;
-        sl.fresh = true;
-        sl.id = p.id;
-        sl.req = p.req;
-        sl.lane = ln;
-        sl.m = m;
-        sl.is2d = is2d;
-        sl.cells = cells;
-        sl.off = off;
-        sl.submit_s = p.submit_s;
-        sl.admit_s = now_s(sv->t0);
-        fresh.push_back(slot);
-        sv->queue.pop_front();
-    }
-    // 2. advance every admitted request of each lane (a smaller round when nothing was admitted
-    // and every active request is close to its end)
-    int steps = max_steps;
-    if (fresh.empty() && sv->remaining_hint > 0 && sv->remaining_hint < steps) steps = (int)sv->remaining_hint;
-    bool any = false;
-    // the FP64 lane runs on its own stream, forked after the admissions and joined back before
-    // the results are read, so that the two lanes' rounds overlap on the GPU
-    NPW_CUDA(cudaEventRecord(sv->fork, sv->s));
-    NPW_CUDA(cudaStreamWaitEvent(sv->s1, sv->fork, 0));
+    bool retired = false;
+    // every lane whose round has ended (or that has none): retire, admit, launch the next round
     for (int ln = 0; ln < 2; ++ln) {
-        bool a = false;
-        st = lane_round(sv, ln, steps, &a);
-        any |= a;
-        if (st) break;
+        npw_server::Lane& lane = sv->lanes[ln];
+        if (lane.in_flight) {
+            const cudaError_t e = cudaEventQuery(lane.done);
+            if (e == cudaErrorNotReady) continue;
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventQuery");
+            if ((st = lane_retire(sv, ln))) return st;
+            retired = true;
+        }
+        if ((st = lane_next_round(sv, ln, base_steps))) return st;
     }
-    {
-        const cudaError_t e1 = cudaEventRecord(sv->join, sv->s1);
-        const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(sv->s, sv->join, 0) : e1;
-        if (st) return st;
-        if (e2 != cudaSuccess) return cuda_fail(e2, "server join");
-    }
-    for (int k : fresh) sv->slots[k].fresh = false;
-    if (!any) {
-        if (active) *active = 0;
-        if (queued) *queued = (int32_t)sv->queue.size();
-        return NPW_OK;
-    }
-    // 3. read the control words, retire finished requests
-    if ((st = bounded_sync(sv->s))) return st;
-    for (int ln = 0; ln < 2; ++ln)
-        NPW_CUDA(cudaMemcpyAsync(sv->lanes[ln].host_ctl.data(), sv->arena + sv->lanes[ln].L.ctl,
-                                 sizeof(npw::Ctl) * sv->max_slots, cudaMemcpyDeviceToHost, sv->s));
-    profile_collect();
-    std::vector<int> finished;
-    long long rem = 0;
-    int n_active = 0;
-    for (int k = 0; k < sv->max_slots; ++k) {
-        const npw_server::Slot& sl = sv->slots[k];
-        if (!sl.used) continue;
-        const npw::Ctl& c = sv->lanes[sl.lane].host_ctl[k];
-        ++n_active;
-        if (c.done) {
-            finished.push_back(k);
-        } else {
-            const double r = c.dt > 0.0 ? (sl.req.t_end - c.t) / c.dt : 1.0;
-            const long long ri = (long long)(r < 1e9 ? r : 1e9) + 1;
-            rem = ri > rem ? ri : rem;
+    // no round ended during this call: wait for the first one that does
+    if (!retired) {
+        int ln = -1;
+        if ((st = wait_any_lane(sv, &ln))) return st;
+        if (ln >= 0) {
+            if ((st = lane_retire(sv, ln))) return st;
+            if ((st = lane_next_round(sv, ln, base_steps))) return st;
         }
     }
-    sv->remaining_hint = rem;
-    for (int k : finished) {  // the compensated 1D float items leave the final state in s
-        const npw_server::Slot& sl = sv->slots[k];
-        const npw_server::Lane& lane = sv->lanes[sl.lane];
-        const size_t region = (lane.fp32 && !sl.is2d) ? lane.L.heap_s : lane.L.heap_u;
-        NPW_CUDA(cudaMemcpyAsync(sl.req.out_host, sv->arena + region + (size_t)sl.off * lane.esz,
-                                 (size_t)sl.cells * lane.esz, cudaMemcpyDeviceToHost, sv->s));
-    }
-    if (!finished.empty() && (st = bounded_sync(sv->s))) return st;
-    const double tdone = now_s(sv->t0);
-    for (int k : finished) {
-        npw_server::Slot& sl = sv->slots[k];
-        const npw::Ctl& c = sv->lanes[sl.lane].host_ctl[k];
-        npw_result r{};
-        r.id = sl.id;
-        r.tag = sl.req.tag;
-        r.status = c.status;
-        r.precision = sl.lane == 0 ? NPW_FP32_MIXED : NPW_FP64;
-        r.steps = c.steps;
-        r.t = c.t;
-        r.submit_s = sl.submit_s;
-        r.admit_s = sl.admit_s;
-        r.done_s = tdone;
-        sv->results.push_back(r);
-        sv->lanes[sl.lane].heap_free(sl.off, sl.cells);
-        sl.used = false;
-    }
-    if (active) *active = n_active - (int32_t)finished.size();
-    if (queued) *queued = (int32_t)sv->queue.size();
+    int n_active = 0;
+    for (int k = 0; k < sv->max_slots; ++k) n_active += sv->slots[k].used ? 1 : 0;
+    if (active) *active = n_active;
+    if (queued) *queued = (int32_t)sv->pending_count();
     return NPW_OK;
 }
 

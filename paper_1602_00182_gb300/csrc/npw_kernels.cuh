@@ -1937,6 +1937,25 @@ struct Launchers {
 
     static cudaError_t stage2d(const Stage2DArgs& a, int tiles, int kind, cudaStream_t s) {
         if constexpr (sizeof(R) == sizeof(float)) {
+            if (a.mp.gauss_2d) {
+                // the two-point Gauss rule with a float state: the face-based body, shape
+                // parameters, ENO choices, switch and smoothness indicators in double from the
+                // float cell averages, candidates, weights, flux and update in float
+                switch (kind) {
+                    case NPW_FLUX_ADVECTION:
+                        stage2d_kernel<float, double, NPW_FLUX_ADVECTION_><<<tiles, TX_2D * TY_2D, stage2d_smem_elems<1>() * sizeof(float), s>>>(a);
+                        break;
+                    case NPW_FLUX_BURGERS:
+                        stage2d_kernel<float, double, NPW_FLUX_BURGERS_><<<tiles, TX_2D * TY_2D, stage2d_smem_elems<1>() * sizeof(float), s>>>(a);
+                        break;
+                    case NPW_FLUX_EULER2D:
+                        stage2d_kernel<float, double, NPW_FLUX_EULER2D_><<<tiles, TX_2D * TY_2D, stage2d_smem_elems<4>() * sizeof(float), s>>>(a);
+                        break;
+                    default:
+                        return cudaErrorInvalidValue;
+                }
+                return cudaGetLastError();
+            }
             // the mixed path: the phased kernel, k = 3 or k = 2
             switch (kind * 4 + a.mp.k) {
                 case NPW_FLUX_ADVECTION * 4 + 3:

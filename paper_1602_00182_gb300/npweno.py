@@ -75,7 +75,7 @@ class Params:
     bc_y: int = -1  # 2D: boundary of the y direction (-1: the bc argument)
     tie_tol: float = 0.0  # near-tie margin of npweno_reconstruct's flags (0: 1e-10)
     max_steps: int = 0  # step limit of a solve (0: automatic); NPW_ETIMEOUT when reached
-    gauss_2d: int = 0  # 2D, FP64, k = 2: two Gauss points per face (0: the midpoint)
+    gauss_2d: int = 0  # 2D, k = 2: two Gauss points per face (0: the midpoint)
 
     def c(self) -> npw_params:
         p = npw_params()

@@ -1,5 +1,6 @@
-"""The two-point Gauss rule of eq. 2DIntegral on the GPU (params.gauss_2d, NPW_FP64, k = 2 on the
-5-cell cross of Sec. 6) against the oracle, and its third-order convergence on Sec. 7 Example 1.
+"""The two-point Gauss rule of eq. 2DIntegral on the GPU (params.gauss_2d, k = 2 on the 5-cell
+cross of Sec. 6) against the oracle, and its third-order convergence on Sec. 7 Example 1, in
+NPW_FP64 and in NPW_FP32_MIXED.
 
 Each face is reconstructed at -+ 1/(2 sqrt 3) cell widths from its midpoint with the shape
 parameter that cancels the Taylor error there, and its flux is the mean of the two
@@ -138,6 +139,88 @@ def test_example1_third_order_on_the_gpu(npw):
     assert all(min(o) > 2.75 for o in orders[1:]), orders
     assert all(max(o) < 2.2 for o in orders_mid[1:]), orders_mid
     assert errs[-1][0] < errs_mid[-1][0] / 20
+
+
+MIXED_GUARD = 8.0 * 2.0 ** -24  # the float state's automatic shape-parameter guard
+
+
+def _gp_mixed(npw, o):
+    return npw.Params(k=2, scheme=o.scheme, rbf=o.rbf, monotone_switch=o.monotone_switch, cross_2d=o.cross_2d,
+                      gauss_2d=1, inflow=o.inflow, bc_y=o.bc_y, precision=npw.NPW_FP32_MIXED, eta_guard=0.0,
+                      eta_max=o.eta_max if o.eta_max > 0 else -1.0)
+
+
+@pytest.mark.parametrize("bc", [O.PERIODIC, O.TRANSMISSIVE, O.INFLOW])
+@pytest.mark.parametrize("kind", [O.BURGERS, O.EULER2D])
+@pytest.mark.parametrize("scheme,rbf,switch", [(O.RBF_ENO, O.MQ, 1), (O.RBF_WENO, O.GA, 0)])
+def test_gauss_step_mixed(npw, bc, kind, scheme, rbf, switch):
+    """NPW_FP32_MIXED with the Gauss rule: one RK3 step from float data on a ragged grid equals
+    the oracle on the same data within float rounding (2e-6 relative: the candidates, weights,
+    fluxes and update round to float; the shape parameters and decisions are formed in double
+    from the float averages, as the oracle forms them)."""
+    nx, ny = 70, 45
+    if kind == O.EULER2D:
+        U, d = I.isentropic_vortex(nx, 4.0, 5.0, 5.0, npts=2)
+        U = U[:, :ny, :].copy()
+        d = float(d)
+    else:
+        U = _field(nx, ny, 11 + bc)
+        d = 1.0 / nx
+    U32 = U.astype(np.float32).astype(np.float64)
+    op = O.Params(k=2, scheme=scheme, rbf=rbf, monotone_switch=switch, cross_2d=1, gauss_2d=1,
+                  inflow=(1.2, 0.1, 0.0, 2.0), eta_guard=MIXED_GUARD)
+    ref = O.rk3_step_2d(U32, d, d, 0.2 * d, kind, bc, op)
+    gu = torch.tensor(np.ascontiguousarray(U32), dtype=torch.float32, device="cuda")
+    npw.npweno_rk3_step_2d(gu, d, d, 0.2 * d, kind, bc, _gp_mixed(npw, op))
+    got = gu.cpu().numpy().astype(np.float64)
+    assert _rel(got, ref) <= 2e-6, _rel(got, ref)
+    # the midpoint rule differs by far more than that
+    mid = O.rk3_step_2d(U32, d, d, 0.2 * d, kind, bc, O.Params(k=2, scheme=scheme, rbf=rbf, monotone_switch=switch,
+                                                               cross_2d=1, inflow=(1.2, 0.1, 0.0, 2.0),
+                                                               eta_guard=MIXED_GUARD))
+    assert _rel(mid, ref) > 1e-5
+
+
+def test_example1_third_order_mixed(npw):
+    """Sec. 7 Example 1 with the Gauss rule in NPW_FP32_MIXED: third order from N = 20 to 160
+    (where the error, 2e-5 at N = 160, is far above float rounding), each error within 2% of the
+    FP64 run's; at N = 20 the whole solve equals the oracle's from the same float data to 1e-5
+    with the same step count."""
+    pg = O.Params(k=2, scheme=O.RBF_ENO, cross_2d=1, gauss_2d=1, monotone_switch=0, eta_max=1.0)
+    pm = O.Params(k=2, scheme=O.RBF_ENO, cross_2d=1, gauss_2d=1, monotone_switch=0, eta_max=1.0,
+                  eta_guard=MIXED_GUARD)
+    ns = (20, 40, 80, 160)
+    errs = []
+    for n in ns:
+        u0 = _avg_sin(n)
+        u32 = u0.astype(np.float32)
+        gm = torch.tensor(u32, device="cuda")
+        st = npw.npweno_solve_2d(gm, 1.0 / n, 1.0 / n, 0.5, 0.2, O.ADVECTION, O.PERIODIC, _gp_mixed(npw, pm))
+        assert st["status"] == 0 and st["t"] == 0.5
+        got = gm.cpu().numpy().astype(np.float64)
+        gd = _dev(u0)
+        npw.npweno_solve_2d(gd, 1.0 / n, 1.0 / n, 0.5, 0.2, O.ADVECTION, O.PERIODIC, _gp(npw, pg))
+        e, e64 = np.abs(got - u0), np.abs(gd.cpu().numpy() - u0)
+        errs.append((e.mean(), e.max()))
+        assert abs(e.mean() - e64.mean()) <= 0.02 * e64.mean() and abs(e.max() - e64.max()) <= 0.02 * e64.max()
+        if n == 20:
+            ref, rst = O.solve_2d(u32.astype(np.float64), 1.0 / n, 1.0 / n, 0.5, 0.2, O.ADVECTION, O.PERIODIC, pm)
+            assert st["steps"] == rst["steps"] and np.abs(got - ref).max() <= 1e-5
+    orders = [[np.log2(errs[i][q] / errs[i + 1][q]) for q in range(2)] for i in range(len(ns) - 1)]
+    print("mixed gauss", errs, orders)
+    assert all(min(o) > 2.75 for o in orders[1:]), orders
+
+
+def test_gauss_mixed_rejected_by_the_queue(npw):
+    """The work queue runs the Gauss rule in FP64 only: NPW_FP32_MIXED is refused (NPW_EINVAL)."""
+    n = 40
+    table, total, offs = npw.make_queue_instances([dict(kind=npw.NPW_FLUX_ADVECTION, nx=n, ny=n, dx=1.0 / n,
+                                                        dy=1.0 / n, t_end=0.05, cfl=0.4, bc=0)])
+    arena = torch.tensor(_avg_sin(n).astype(np.float32).ravel(), device="cuda")
+    p = npw.Params(k=2, scheme=npw.NPW_RBF_ENO, cross_2d=1, gauss_2d=1, precision=npw.NPW_FP32_MIXED)
+    with pytest.raises(npw.NpwError) as ei:
+        npw.npweno_queue_solve(arena, table, p)
+    assert ei.value.status == npw.NPW_EINVAL
 
 
 def test_gauss_through_the_queue(npw):

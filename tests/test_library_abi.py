@@ -46,12 +46,18 @@ def test_default_params_and_errors_without_gpu():
     # one quadrature point per face (the paper's runs) unless the Gauss rule is asked for
     assert p.gauss_2d == 0
     for kw, msg in ((dict(gauss_2d=1), b"k = 2"), (dict(gauss_2d=1, k=2, scheme=npw.NPW_RBF_ENO), b"cross_2d"),
-                    (dict(gauss_2d=1, k=2, scheme=npw.NPW_ENO, precision=1), b"NPW_FP64"),
                     (dict(gauss_2d=2), b"gauss_2d")):
         g = npw.Params(**kw).c()
         st = lib.npweno_solve_2d(ctypes.c_void_p(16), 32, 32, 1, 0.1, 0.1, 0.1, 0.5, npw.NPW_FLUX_ADVECTION, 0,
                                  ctypes.byref(g), ctypes.c_void_p(16), 1 << 30, None, None)
         assert st == npw.NPW_EINVAL and msg in lib.npw_last_error(), (kw, lib.npw_last_error())
+    # the work queue takes the Gauss rule in FP64 only (the 2D entry points in both precisions)
+    table, _, _ = npw.make_queue_instances([dict(kind=npw.NPW_FLUX_ADVECTION, nx=32, ny=32, dx=0.1, dy=0.1,
+                                                 t_end=0.5, cfl=0.4)])
+    g = npw.Params(gauss_2d=1, k=2, scheme=npw.NPW_ENO, precision=1).c()
+    st = lib.npweno_queue_solve(ctypes.c_void_p(16), table, 1, ctypes.byref(g), ctypes.c_void_p(16), 1 << 30, None,
+                                None)
+    assert st == npw.NPW_EINVAL and b"NPW_FP64" in lib.npw_last_error(), lib.npw_last_error()
     # argument validation happens before any CUDA call
     bad = npw.Params(k=4).c()
     st = lib.npweno_reconstruct(ctypes.c_void_p(16), 100, 1, 0, ctypes.byref(bad), ctypes.c_void_p(16),
