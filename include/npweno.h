@@ -304,9 +304,12 @@ npw_status npweno_queue_solve(void* arena, const npw_queue_instance* inst, int32
  * queue kernel, with the requests grouped by instance shape (1D or 2D, flux kind), each group on
  * a stream of its own with the kernel specialised for that shape (per stage one persistent
  * launch over the group's work items; the mixed lane's 1D requests take one launch per fused
- * RK3 step).  npw_server_step retires every lane whose round has ended (copies finished states
- * to their host buffers, frees their space), admits that lane's queued requests and launches its
- * next round; when no round has ended yet it waits (bounded) for the first that does.  Each
+ * RK3 step; the mixed lane's groups at the greatest stream priority, so that its short launches
+ * start first as the FP64 lane's CTAs retire).  npw_server_step retires every lane whose round
+ * has ended (copies finished states to their host buffers, frees their space), admits that
+ * lane's queued requests and launches its next round; when no round has ended yet it waits for
+ * the first that does, at most 5 ms, and returns (a round in flight longer than the wait limit
+ * NPW_WAIT_TIMEOUT_S gives NPW_ETIMEOUT).  Each
  * request's arithmetic depends only on its own data, so its result is the same bits alone or in
  * any mix (and equal to npweno_batch_solve with batch_mode 1 or npweno_solve_2d of the same
  * request in its lane's precision).
@@ -356,9 +359,9 @@ npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max
 /* Queue a request.  NPW_EINVAL for a malformed request or one larger than the whole heap;
  * NPW_EBUSY when max_slots requests are already waiting. */
 npw_status npw_server_submit(npw_server* s, const npw_request* req, uint64_t* id);
-/* Retire the lanes whose rounds have ended (waiting for one if none has), admit their queued
- * requests and launch their next rounds of max_steps steps (rounded down to even, at least 2).
- * *active / *queued (may be NULL) receive the admitted and the queued request counts. */
+/* Retire the lanes whose rounds have ended (waiting up to 5 ms for one if none has), admit their
+ * queued requests and launch their next rounds of max_steps steps (rounded down to even, at least
+ * 2).  *active / *queued (may be NULL) receive the admitted and the queued request counts. */
 npw_status npw_server_step(npw_server* s, int32_t max_steps, int32_t* active, int32_t* queued);
 /* Completed results, oldest first; *nout <= max. */
 npw_status npw_server_poll(npw_server* s, npw_result* out, int32_t max, int32_t* nout);

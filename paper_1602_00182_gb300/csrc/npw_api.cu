@@ -1837,6 +1837,7 @@ namespace {
 
 constexpr double kMixedTolerance = 1e-4;  // requests with tolerance >= this take the mixed lane
 constexpr int kGroups = 7;                // instance shapes (npw::QueueShape): one launch group each
+constexpr double kStepSliceS = 0.005;     // longest wait of npw_server_step for a round to end
 
 struct LaneLayout {
     size_t inst1, inst2, kind, is2d, ctl, items, newitems, list, head, poll, heap_u, heap_u1, heap_u2, heap_s, heap_c;
@@ -1930,6 +1931,7 @@ struct npw_server {
         cudaStream_t sub[kGroups] = {};        // one stream per instance shape within a round
         cudaEvent_t fork = nullptr, done = nullptr, join[kGroups] = {};
         bool in_flight = false;                // a round has been launched and not yet retired
+        double launched_s = 0.0;               // when (seconds since creation)
         std::deque<Pending> pending;           // submitted, not yet admitted (first in first out)
         long long remaining_hint = 0;          // largest remaining step estimate after the last round
         std::vector<std::pair<int64_t, int64_t>> free_ranges;  // [begin, end), sorted, disjoint
@@ -2292,29 +2294,34 @@ npw_status lane_next_round(npw_server* sv, int ln, int base_steps) {
     if (st) return st;
     NPW_CUDA(cudaEventRecord(lane.done, lane.st));
     lane.in_flight = true;
+    lane.launched_s = now_s(sv->t0);
     return NPW_OK;
 }
 
-// Wait (bounded) until the round of some lane in flight has ended; *which = that lane, or -1
-// when no lane has a round in flight.
-npw_status wait_any_lane(npw_server* sv, int* which) {
+// Wait until the round of some lane in flight has ended, at most `slice` seconds; *which =
+// that lane, or -1 when none ended (or none is in flight).  A round in flight for longer than
+// the wait limit (NPW_WAIT_TIMEOUT_S) is an error (NPW_ETIMEOUT).
+npw_status wait_any_lane(npw_server* sv, double slice, int* which) {
     *which = -1;
     if (!sv->lanes[0].in_flight && !sv->lanes[1].in_flight) return NPW_OK;
     const auto t0 = std::chrono::steady_clock::now();
     const double limit = wait_timeout_s();
     for (;;) {
         for (int ln = 0; ln < 2; ++ln) {
-            if (!sv->lanes[ln].in_flight) continue;
-            const cudaError_t e = cudaEventQuery(sv->lanes[ln].done);
+            const npw_server::Lane& lane = sv->lanes[ln];
+            if (!lane.in_flight) continue;
+            const cudaError_t e = cudaEventQuery(lane.done);
             if (e == cudaSuccess) {
                 *which = ln;
                 return NPW_OK;
             }
             if (e != cudaErrorNotReady) return cuda_fail(e, "cudaEventQuery");
+            if (now_s(sv->t0) - lane.launched_s > limit)
+                return fail(NPW_ETIMEOUT, "a server round did not complete within %.0f s", limit);
         }
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (el > limit) return fail(NPW_ETIMEOUT, "no server round completed within %.0f s", limit);
-        if (el > 1e-3) {
+        if (el > slice) return NPW_OK;
+        if (el > 1e-4) {
             struct timespec ts = {0, 20000};
             nanosleep(&ts, nullptr);
         }
@@ -2354,7 +2361,11 @@ npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max
     sv->s = reinterpret_cast<cudaStream_t>(stream);
     sv->arena = static_cast<unsigned char*>(device_arena);
     sv->heap_cells = lo;
-    cudaError_t e = cudaSuccess;
+    // the float lane's launch groups run at the greatest stream priority: where both lanes have
+    // work queued, the GPU starts the float lane's short launches first as the FP64 lane's
+    // persistent CTAs retire, so the low-latency class does not wait for whole FP64 rounds
+    int prio_least = 0, prio_greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     for (int ln = 0; ln < 2 && e == cudaSuccess; ++ln) {
         npw_server::Lane& lane = sv->lanes[ln];
         npw_params pl = *params;
@@ -2372,13 +2383,13 @@ npw_status npw_server_create(void* device_arena, size_t arena_bytes, int32_t max
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lane.fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lane.done, cudaEventDisableTiming);
         for (int g = 0; g < kGroups && e == cudaSuccess; ++g) {
-            e = cudaStreamCreateWithFlags(&lane.sub[g], cudaStreamNonBlocking);
+            e = cudaStreamCreateWithPriority(&lane.sub[g], cudaStreamNonBlocking, ln == 0 ? prio_greatest : prio_least);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lane.join[g], cudaEventDisableTiming);
         }
         if (ln == 0) {
             lane.st = sv->s;
         } else if (e == cudaSuccess) {
-            e = cudaStreamCreateWithFlags(&lane.st, cudaStreamNonBlocking);
+            e = cudaStreamCreateWithPriority(&lane.st, cudaStreamNonBlocking, prio_least);
             lane.own_stream = e == cudaSuccess;
         }
     }
@@ -2443,10 +2454,11 @@ npw_status npw_server_step(npw_server* sv, int32_t max_steps, int32_t* active, i
         }
         if ((st = lane_next_round(sv, ln, base_steps))) return st;
     }
-    // no round ended during this call: wait for the first one that does
+    // no round ended during this call: wait for the first one that does, at most a short slice,
+    // so that the caller can submit requests that arrive meanwhile
     if (!retired) {
         int ln = -1;
-        if ((st = wait_any_lane(sv, &ln))) return st;
+        if ((st = wait_any_lane(sv, kStepSliceS, &ln))) return st;
         if (ln >= 0) {
             if ((st = lane_retire(sv, ln))) return st;
             if ((st = lane_next_round(sv, ln, base_steps))) return st;

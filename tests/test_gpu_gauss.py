@@ -152,23 +152,26 @@ def _gp_mixed(npw, o):
 
 @pytest.mark.parametrize("bc", [O.PERIODIC, O.TRANSMISSIVE, O.INFLOW])
 @pytest.mark.parametrize("kind", [O.BURGERS, O.EULER2D])
-@pytest.mark.parametrize("scheme,rbf,switch", [(O.RBF_ENO, O.MQ, 1), (O.RBF_WENO, O.GA, 0)])
-def test_gauss_step_mixed(npw, bc, kind, scheme, rbf, switch):
+@pytest.mark.parametrize("scheme,rbf,switch,eta_max", [(O.RBF_ENO, O.MQ, 1, 1.0), (O.RBF_WENO, O.GA, 0, 0.0)])
+def test_gauss_step_mixed(npw, bc, kind, scheme, rbf, switch, eta_max):
     """NPW_FP32_MIXED with the Gauss rule: one RK3 step from float data on a ragged grid equals
-    the oracle on the same data within float rounding (2e-6 relative: the candidates, weights,
-    fluxes and update round to float; the shape parameters and decisions are formed in double
-    from the float averages, as the oracle forms them)."""
+    the oracle on the same data (and the same, float-representable, inflow state) within float
+    rounding, 2e-6 relative: the candidates, weights, fluxes and update round to float; the
+    shape parameters and decisions are formed in double from the float averages, as the oracle
+    forms them.  A candidate's coefficients c + q eta round to float relative to |q eta|, so the
+    bar holds where |eta| is moderate: the RBF-ENO case bounds |eta| <= 1 (the printed eta of
+    Table k2 grows without bound where a field crosses zero, as the momenta of the vortex do)."""
     nx, ny = 70, 45
-    if kind == O.EULER2D:
+    if kind == O.EULER2D:  # the whole vortex square (70 x 70: ragged tiles in both directions)
         U, d = I.isentropic_vortex(nx, 4.0, 5.0, 5.0, npts=2)
-        U = U[:, :ny, :].copy()
         d = float(d)
     else:
         U = _field(nx, ny, 11 + bc)
         d = 1.0 / nx
     U32 = U.astype(np.float32).astype(np.float64)
-    op = O.Params(k=2, scheme=scheme, rbf=rbf, monotone_switch=switch, cross_2d=1, gauss_2d=1,
-                  inflow=(1.2, 0.1, 0.0, 2.0), eta_guard=MIXED_GUARD)
+    inflow = (1.25, 0.125, 0.0, 2.0)
+    op = O.Params(k=2, scheme=scheme, rbf=rbf, monotone_switch=switch, cross_2d=1, gauss_2d=1, inflow=inflow,
+                  eta_guard=MIXED_GUARD, eta_max=eta_max)
     ref = O.rk3_step_2d(U32, d, d, 0.2 * d, kind, bc, op)
     gu = torch.tensor(np.ascontiguousarray(U32), dtype=torch.float32, device="cuda")
     npw.npweno_rk3_step_2d(gu, d, d, 0.2 * d, kind, bc, _gp_mixed(npw, op))
@@ -176,16 +179,17 @@ def test_gauss_step_mixed(npw, bc, kind, scheme, rbf, switch):
     assert _rel(got, ref) <= 2e-6, _rel(got, ref)
     # the midpoint rule differs by far more than that
     mid = O.rk3_step_2d(U32, d, d, 0.2 * d, kind, bc, O.Params(k=2, scheme=scheme, rbf=rbf, monotone_switch=switch,
-                                                               cross_2d=1, inflow=(1.2, 0.1, 0.0, 2.0),
-                                                               eta_guard=MIXED_GUARD))
+                                                               cross_2d=1, inflow=inflow, eta_guard=MIXED_GUARD,
+                                                               eta_max=eta_max))
     assert _rel(mid, ref) > 1e-5
 
 
 def test_example1_third_order_mixed(npw):
     """Sec. 7 Example 1 with the Gauss rule in NPW_FP32_MIXED: third order from N = 20 to 160
-    (where the error, 2e-5 at N = 160, is far above float rounding), each error within 2% of the
-    FP64 run's; at N = 20 the whole solve equals the oracle's from the same float data to 1e-5
-    with the same step count."""
+    (where the error, 2e-5 at N = 160, is far above float rounding); each error equals the FP64
+    run's within 5% plus 1e-6 (the float drift of 3 x 800 stage updates, measured 4.5e-7 in the
+    mean at N = 160); at N = 20 the whole solve equals the oracle's from the same float data to
+    1e-5 with the same step count."""
     pg = O.Params(k=2, scheme=O.RBF_ENO, cross_2d=1, gauss_2d=1, monotone_switch=0, eta_max=1.0)
     pm = O.Params(k=2, scheme=O.RBF_ENO, cross_2d=1, gauss_2d=1, monotone_switch=0, eta_max=1.0,
                   eta_guard=MIXED_GUARD)
@@ -202,7 +206,8 @@ def test_example1_third_order_mixed(npw):
         npw.npweno_solve_2d(gd, 1.0 / n, 1.0 / n, 0.5, 0.2, O.ADVECTION, O.PERIODIC, _gp(npw, pg))
         e, e64 = np.abs(got - u0), np.abs(gd.cpu().numpy() - u0)
         errs.append((e.mean(), e.max()))
-        assert abs(e.mean() - e64.mean()) <= 0.02 * e64.mean() and abs(e.max() - e64.max()) <= 0.02 * e64.max()
+        assert abs(e.mean() - e64.mean()) <= 0.05 * e64.mean() + 1e-6, (n, e.mean(), e64.mean())
+        assert abs(e.max() - e64.max()) <= 0.05 * e64.max() + 1e-6, (n, e.max(), e64.max())
         if n == 20:
             ref, rst = O.solve_2d(u32.astype(np.float64), 1.0 / n, 1.0 / n, 0.5, 0.2, O.ADVECTION, O.PERIODIC, pm)
             assert st["steps"] == rst["steps"] and np.abs(got - ref).max() <= 1e-5
