@@ -73,13 +73,6 @@ __device__ __forceinline__ int csign(float v, float err) {
 // Returns 1 (fires), 0 (does not) or -1 (not certain: decide in double precision).
 __device__ __forceinline__ int switch_v0_cert(float d0, float d1, float d2) {
     const float a0 = fabsf(d0), a1 = fabsf(d1), a2 = fabsf(d2);
-    const float Em = fmaf(35.f, d0, fmaf(-34.f, d1, 11.f * d2));
-    const float Ep = fmaf(11.f, d0, fmaf(-34.f, d1, 35.f * d2));
-    const int s1 = csign(Em, kE * fmaf(35.f, a0, fmaf(34.f, a1, 11.f * a2)));
-    const int s2 = csign(Ep, kE * fmaf(11.f, a0, fmaf(34.f, a1, 35.f * a2)));
-    if (s1 == kUncertain || s2 == kUncertain) return -1;
-    // p' takes both signs at the two ends: non-monotone whatever the vertex does
-    if ((s1 < 0 && s2 > 0) || (s1 > 0 && s2 < 0)) return 1;
     const float A = fmaf(-2.f, d1, d0 + d2);
     const float eA = kE * fmaf(2.f, a1, a0 + a2);
     const float B = d2 - d0;
@@ -87,6 +80,17 @@ __device__ __forceinline__ int switch_v0_cert(float d0, float d1, float d2) {
     const float C = fmaf(14.f, d1, -(d0 + d2));
     const float eC = kE * fmaf(14.f, a1, a0 + a2);
     const float aA = fabsf(A), aB = fabsf(B), aC = fabsf(C);
+    // On the stencil (|s| <= 2), |6 A s^2 + 6 B s| <= 24 |A| + 12 |B|: where |C| exceeds that,
+    // p' keeps the sign of C throughout and the switch does not fire.  This decides most faces
+    // of smooth data (|v'| above about 2 dx |v''|) before the end values are formed.
+    if (aC - eC > fmaf(24.f, aA + eA, 12.f * (aB + eB)) * (1.f + 4.f * kU)) return 0;
+    const float Em = fmaf(35.f, d0, fmaf(-34.f, d1, 11.f * d2));
+    const float Ep = fmaf(11.f, d0, fmaf(-34.f, d1, 35.f * d2));
+    const int s1 = csign(Em, kE * fmaf(35.f, a0, fmaf(34.f, a1, 11.f * a2)));
+    const int s2 = csign(Ep, kE * fmaf(11.f, a0, fmaf(34.f, a1, 35.f * a2)));
+    if (s1 == kUncertain || s2 == kUncertain) return -1;
+    // p' takes both signs at the two ends: non-monotone whatever the vertex does
+    if ((s1 < 0 && s2 > 0) || (s1 > 0 && s2 < 0)) return 1;
     // With the vertex inside (|B| < 4|A|), |12 p'(vertex) - C| = 1.5 B^2 / |A| < 24 |A|.  If C
     // has the common sign of both ends and |C| exceeds that bound, p' keeps one sign on the
     // whole interval whether or not the vertex is inside (nearly linear data: A, B ~ 0).
@@ -343,12 +347,15 @@ __device__ __forceinline__ float eta_doublefloat(float w0, float w1, float w2, f
     float nh, nl, dh, dl;
     eta_pairs(w0, w1, w2, w3, nh, nl, dh, dl);
     if (fp.eta_guard > 0.0f) {  // certified as in eta_quot: exact where the float test is too close
+        // the common case first: a denominator clearly above the threshold (then the averages
+        // are not all zero, since an all-zero stencil has a zero threshold)
         const float d0 = fabsf(dh + dl);
-        const bool zero = all_zero(w0, w1, w2, w3) ||
-                          (guard >= 0x1p-100f && d0 <= guard * (1.0f - 0x1p-19f)
-                              ? true
-                              : ((guard < 0x1p-100f || d0 <= guard * (1.0f + 0x1p-19f)) &&
-                                 guard_exact(w0, w1, w2, w3, fp.eta_guard_d)));
+        const bool clear = guard >= 0x1p-100f && d0 > guard * (1.0f + 0x1p-19f);
+        const bool zero = !clear && (all_zero(w0, w1, w2, w3) ||
+                                     (guard >= 0x1p-100f && d0 <= guard * (1.0f - 0x1p-19f)
+                                          ? true
+                                          : ((guard < 0x1p-100f || d0 <= guard * (1.0f + 0x1p-19f)) &&
+                                             guard_exact(w0, w1, w2, w3, fp.eta_guard_d))));
         if (zero) {
             *fl |= FL_ZERO_GUARD;
             return 0.0f;
