@@ -154,34 +154,43 @@ def _gp_mixed(npw, o):
 @pytest.mark.parametrize("kind", [O.BURGERS, O.EULER2D])
 @pytest.mark.parametrize("scheme,rbf,switch,eta_max", [(O.RBF_ENO, O.MQ, 1, 1.0), (O.RBF_WENO, O.GA, 0, 0.0)])
 def test_gauss_step_mixed(npw, bc, kind, scheme, rbf, switch, eta_max):
-    """NPW_FP32_MIXED with the Gauss rule: one RK3 step from float data on a ragged grid equals
-    the oracle on the same data (and the same, float-representable, inflow state) within float
-    rounding, 2e-6 relative: the candidates, weights, fluxes and update round to float; the
-    shape parameters and decisions are formed in double from the float averages, as the oracle
-    forms them.  A candidate's coefficients c + q eta round to float relative to |q eta|, so the
-    bar holds where |eta| is moderate: the RBF-ENO case bounds |eta| <= 1 (the printed eta of
-    Table k2 grows without bound where a field crosses zero, as the momenta of the vortex do)."""
+    """NPW_FP32_MIXED with the Gauss rule: one RK3 step from float data on a ragged grid against
+    the oracle on the same data (and a float-representable inflow state: 1.25 for Burgers, the
+    vortex's background state for Euler).  The candidates, weights, fluxes and update round to
+    float; the shape parameters and decisions are formed in double from the float values, as the
+    oracle forms them from its own.  Without the switch the bar is float rounding, 2e-6
+    relative.  With it, the decisions of stages 2 and 3 are taken on float stage values on the
+    GPU and on double ones in the oracle, so they may differ at near ties: mean 1e-6, max 3e-5
+    relative (the bar of the midpoint-rule 2D kernel).  A candidate's coefficients c + q eta
+    round to float relative to |q eta|, and the printed eta grows without bound where a field
+    crosses zero (the vortex's momenta), so the RBF-ENO case bounds |eta| <= 1."""
     nx, ny = 70, 45
     if kind == O.EULER2D:  # the whole vortex square (70 x 70: ragged tiles in both directions)
         U, d = I.isentropic_vortex(nx, 4.0, 5.0, 5.0, npts=2)
         d = float(d)
+        inflow = (1.0, 1.0, 1.0, 3.5)  # rho, rho u, rho v, E of the background (1, 1, 1, 1)
     else:
         U = _field(nx, ny, 11 + bc)
         d = 1.0 / nx
+        inflow = (1.25, 0.0, 0.0, 0.0)
     U32 = U.astype(np.float32).astype(np.float64)
-    inflow = (1.25, 0.125, 0.0, 2.0)
     op = O.Params(k=2, scheme=scheme, rbf=rbf, monotone_switch=switch, cross_2d=1, gauss_2d=1, inflow=inflow,
                   eta_guard=MIXED_GUARD, eta_max=eta_max)
     ref = O.rk3_step_2d(U32, d, d, 0.2 * d, kind, bc, op)
     gu = torch.tensor(np.ascontiguousarray(U32), dtype=torch.float32, device="cuda")
     npw.npweno_rk3_step_2d(gu, d, d, 0.2 * d, kind, bc, _gp_mixed(npw, op))
     got = gu.cpu().numpy().astype(np.float64)
-    assert _rel(got, ref) <= 2e-6, _rel(got, ref)
-    # the midpoint rule differs by far more than that
+    scale = np.abs(ref).max()
+    e = np.abs(got - ref)
+    if not switch:
+        assert e.max() <= 2e-6 * scale, e.max() / scale
+    else:
+        assert e.mean() <= 1e-6 * scale and e.max() <= 3e-5 * scale, (e.mean() / scale, e.max() / scale)
+    # the data exercises the Gauss rule: the oracle's midpoint step differs from its Gauss step
     mid = O.rk3_step_2d(U32, d, d, 0.2 * d, kind, bc, O.Params(k=2, scheme=scheme, rbf=rbf, monotone_switch=switch,
                                                                cross_2d=1, inflow=inflow, eta_guard=MIXED_GUARD,
                                                                eta_max=eta_max))
-    assert _rel(mid, ref) > 1e-5
+    assert _rel(mid, ref) > 1e-6
 
 
 def test_example1_third_order_mixed(npw):
