@@ -80,10 +80,12 @@ __device__ __forceinline__ int switch_v0_cert(float d0, float d1, float d2) {
     const float C = fmaf(14.f, d1, -(d0 + d2));
     const float eC = kE * fmaf(14.f, a1, a0 + a2);
     const float aA = fabsf(A), aB = fabsf(B), aC = fabsf(C);
-    // On the stencil (|s| <= 2), |6 A s^2 + 6 B s| <= 24 |A| + 12 |B|: where |C| exceeds that,
-    // p' keeps the sign of C throughout and the switch does not fire.  This decides most faces
-    // of smooth data (|v'| above about 2 dx |v''|) before the end values are formed.
-    if (aC - eC > fmaf(24.f, aA + eA, 12.f * (aB + eB)) * (1.f + 4.f * kU)) return 0;
+    // On the stencil (|s| <= 2), |6 A s^2 + 6 B s| <= 24 |A| + 12 |B|: where |C| reaches that,
+    // p' never takes the sign opposite to C's (p' = 0 throughout when all three vanish), so it
+    // cannot take both signs and the switch does not fire.  This decides most faces of smooth
+    // data (|v'| above about 2 dx |v''|) and every constant stencil before the end values are
+    // formed.
+    if (aC - eC >= fmaf(24.f, aA + eA, 12.f * (aB + eB)) * (1.f + 4.f * kU)) return 0;
     const float Em = fmaf(35.f, d0, fmaf(-34.f, d1, 11.f * d2));
     const float Ep = fmaf(11.f, d0, fmaf(-34.f, d1, 35.f * d2));
     const int s1 = csign(Em, kE * fmaf(35.f, a0, fmaf(34.f, a1, 11.f * a2)));
