@@ -1,7 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Bars (written here, derived in the design doc):
-  * NPW_FP64 vs oracle: relative L_inf <= 1e-12 on every face; ENO stencil choices identical on
+Bars (each derived from the arithmetic it bounds):
+  * NPW_FP64 vs oracle: relative L_inf <= 1e-12 on every face (both sides evaluate the same IEEE
+    operations in the same order, without contraction); ENO stencil choices identical on
     every face, switch flags identical except at faces either side marks as switch near ties
     (closed form on the GPU, a 4x4 elimination in the oracle), whose share is bounded per data
     set; at those faces the oracle replays the GPU's decisions (tests/parity_util.py).
