@@ -88,3 +88,32 @@ def test_no_cpu_fallback_in_product_path():
     if not torch.cuda.is_available():
         with pytest.raises(RuntimeError):
             npw.npweno_reconstruct(torch.zeros(10, dtype=torch.float64), 0, npw.Params())
+
+
+def test_server_arguments_without_gpu():
+    """The request server's sizing and argument checks run on the host before any CUDA call: the
+    arena grows with the heap and the slot count; a null arena, characteristic or Gauss-rule
+    parameters, an arena too small for its slots, and null handles are refused with NPW_EINVAL."""
+    from paper_1602_00182_gb300 import build as b
+    from paper_1602_00182_gb300 import npweno as npw
+    b.build()
+    lib = npw.load()
+    p = npw.Params(precision=1).c()
+    a1 = lib.npw_server_arena_bytes(1 << 20, 64, ctypes.byref(p))
+    assert a1 > (1 << 20) * (3 * 4 + 2 * 4 + 3 * 8)  # both lanes' three state buffers, the float carries
+    assert lib.npw_server_arena_bytes(1 << 21, 64, ctypes.byref(p)) > a1
+    assert lib.npw_server_arena_bytes(1 << 20, 128, ctypes.byref(p)) > a1
+    assert lib.npw_server_arena_bytes(0, 64, ctypes.byref(p)) == 0
+    assert lib.npw_server_arena_bytes(1 << 20, 0, ctypes.byref(p)) == 0
+    h = ctypes.c_void_p()
+    cases = ((None, a1, p, b"bad server arguments"),
+             (ctypes.c_void_p(256), a1, npw.Params(precision=1, characteristic=1).c(), b"component-wise"),
+             (ctypes.c_void_p(256), a1, npw.Params(precision=1, k=2, cross_2d=1, gauss_2d=1).c(), b"gauss_2d"),
+             (ctypes.c_void_p(256), 4096, p, b"arena too small"))
+    for arena, size, pp, msg in cases:
+        st = lib.npw_server_create(arena, size, 64, ctypes.byref(pp), None, ctypes.byref(h))
+        assert st == npw.NPW_EINVAL and msg in lib.npw_last_error(), (msg, lib.npw_last_error())
+    n = ctypes.c_int32()
+    assert lib.npw_server_step(None, 8, None, None) == npw.NPW_EINVAL
+    assert lib.npw_server_submit(None, None, None) == npw.NPW_EINVAL
+    assert lib.npw_server_poll(None, None, 0, ctypes.byref(n)) == npw.NPW_EINVAL
