@@ -145,6 +145,71 @@ __device__ __forceinline__ bool switch_fires_f(float w0, float w1, float w2, flo
     return switch_fires<double>((double)w0, (double)w1, (double)w2, (double)w3, variant);
 }
 
+// a - 2 b + c = h + l + eg exactly, by error-free transformations (two-sum; 2 b is exact), with
+// |l| <= u |h| and |eg| <= u^2 (|a| + 2|b| + |c|) roughly
+__device__ __forceinline__ void sdiff_exact(float a, float b, float c, float& h, float& l, float& eg) {
+    float s, e, t, f, g;
+    two_sum(a, c, s, e);
+    two_sum(s, -2.f * b, t, f);
+    two_sum(f, e, g, eg);
+    two_sum(t, g, h, l);
+}
+// sign of h + l + eg as above: +1 or -1, or 0 when not certain
+__device__ __forceinline__ float sdiff_sign(float h, float eg) {
+    if (h != 0.0f) return fabsf(h) * (1.0f - 2.0f * kU) > fabsf(eg) ? copysignf(1.0f, h) : 0.0f;
+    return eg >= 0.0f ? 1.0f : -1.0f;  // l = 0 and the value is eg exactly
+}
+// The second step of the ENO choice on second differences X = a - 2b + c, Y = p - 2q + r whose
+// difference in magnitude is a third difference below float resolution on fine smooth grids:
+// 1 where |Y| > |X|, 0 where not, -1 where not certain.  |Y| - |X| = zh + zl + (em + ez +
+// sY gY - sX gX) exactly, the bracket bounded by R; a decision is returned only where |zh + zl|
+// exceeds R plus a bound on the FP64 evaluation's own error (2^-52 (|a| + 2|b| + |c| + |p| +
+// 2|q| + |r|), doubled), so that it is the exact decision and also that of the FP64 evaluation.
+// An exact tie (every term exact, zh + zl = 0) is decided as a tie (|X| < |Y| is false) where
+// the magnitudes span at most 2^26, so that the FP64 evaluation is exact as well.
+__device__ __forceinline__ int sdiff_abs_less(float a, float b, float c, float p, float q, float r) {
+    float hx, lx, gx, hy, ly, gy;
+    sdiff_exact(a, b, c, hx, lx, gx);
+    sdiff_exact(p, q, r, hy, ly, gy);
+    const float sx = sdiff_sign(hx, gx), sy = sdiff_sign(hy, gy);
+    if (sx == 0.0f || sy == 0.0f) return -1;
+    float zh, ze, m, em, zl, ez;
+    two_sum(sy * hy, -sx * hx, zh, ze);
+    two_sum(sy * ly, -sx * lx, m, em);
+    two_sum(ze, m, zl, ez);
+    const float w = zh + zl;
+    const float R = (fabsf(em) + fabsf(ez)) + (fabsf(gx) + fabsf(gy));
+    const float S = ((fabsf(a) + fabsf(c)) + 2.f * fabsf(b)) + ((fabsf(p) + fabsf(r)) + 2.f * fabsf(q));
+    const float fp64 = S * 0x1p-50f;
+    if (R == 0.0f) {  // |Y| - |X| = zh + zl exactly: w has its sign, and is 0 only at a tie
+        if (w != 0.0f) return fabsf(w) * (1.0f - kU) > fp64 ? (w > 0.0f ? 1 : 0) : -1;
+        const float t[6] = {fabsf(a), 2.f * fabsf(b), fabsf(c), fabsf(p), 2.f * fabsf(q), fabsf(r)};
+        float mx = 0.0f, mn = INFINITY;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (t[k] != 0.0f) {
+                mx = fmaxf(mx, t[k]);
+                mn = fminf(mn, t[k]);
+            }
+        return (mx == 0.0f || mx <= mn * 0x1p26f) ? 0 : -1;
+    }
+    return fabsf(w) * (1.0f - kU) > (R * (1.0f + 8.0f * kU) + fp64) + 0x1p-140f ? (w > 0.0f ? 1 : 0) : -1;
+}
+
+// the ENO choice where the float test of its first (s1 = kUncertain) or second step is not
+// certain, out of line: the second step from the second differences to a few units of u^2,
+// else the FP64 evaluation
+__device__ __forceinline__ int eno_choice_rest(float c0, float c1, float c2, float c3, float c4, int s1) {
+    if (s1 != kUncertain) {
+        const int x = s1 > 0 ? sdiff_abs_less(c0, c1, c2, c1, c2, c3) : sdiff_abs_less(c1, c2, c3, c2, c3, c4);
+        if (x >= 0) {
+            if (s1 > 0) return x ? 2 : 1;
+            return x ? 1 : 0;
+        }
+    }
+    return eno_choice<double>((double)c0, (double)c1, (double)c2, (double)c3, (double)c4);
+}
+
 // ENO stencil choice with the same certification (see eno_choice for the rule)
 __device__ __forceinline__ int eno_choice_f(float c0, float c1, float c2, float c3, float c4) {
     const float dm = c1 - c0, dl = c2 - c1, dr = c3 - c2, dp = c4 - c3;
@@ -168,7 +233,7 @@ __device__ __forceinline__ int eno_choice_f(float c0, float c1, float c2, float 
             return s2 > 0 ? 1 : 0;
         }
     }
-    return eno_choice<double>((double)c0, (double)c1, (double)c2, (double)c3, (double)c4);
+    return eno_choice_rest(c0, c1, c2, c3, c4, s1);
 }
 
 // ---------------------------------------------------------------------------------------
